@@ -1,0 +1,251 @@
+"""FP64 CPU oracle (ctypes front end of ``oracle/oracle.c``).
+
+TEST INFRASTRUCTURE ONLY.  The tests, ``__graft_entry__.smoke()`` and the
+benchmark's CPU-baseline / reference legs import this module; the rendering
+library and its Python binding never do.  It shares no code with the CUDA
+path: the only common module is ``fixtures`` (seeded input generators).
+
+Every float input handed to the C code is first rounded to FP32, because the
+library receives FP32 inputs; the oracle then computes in FP64 from exactly
+the values the library sees.
+
+Parity status of each function (what pins it; see tests/test_oracle_pins.py):
+  ray             pinned: Eq. 2/3 special pixels, round trip through Eq. 2
+  label map       pinned: brute-force point-in-box over the partition boxes
+  march           pinned: analytic chord counts, empty/full grids
+  encode / mlp    pinned: one-hot closed forms, zero-weight closed form,
+                  parameter count 6,212 (Appendix)
+  composite       pinned: two-sample closed form, constant slab exp(-sigma l),
+                  sum of weights = 1 - T_end, empty ray = background
+  loss / grad     pinned: central finite differences (h = 1e-4)
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+from typing import Optional
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SO = os.path.join(_HERE, "liboracle.so")
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile oracle.c into oracle/liboracle.so (gcc, OpenMP, -O2)."""
+    src = os.path.join(_HERE, "oracle.c")
+    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(src):
+        tmp = _SO + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-std=c11",
+                               "-o", tmp, src, "-lm"])
+        os.replace(tmp, _SO)
+    return _SO
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        L = ctypes.CDLL(_SO)
+        P = ctypes.POINTER
+        i32p, u32p, u16p, u8p = P(ctypes.c_int32), P(ctypes.c_uint32), P(ctypes.c_uint16), P(ctypes.c_uint8)
+        f32p, f64p, u64p = P(ctypes.c_float), P(ctypes.c_double), P(ctypes.c_uint64)
+        I, D, I64 = ctypes.c_int, ctypes.c_double, ctypes.c_int64
+        L.orc_param_count.argtypes = [I, I]; L.orc_param_count.restype = I64
+        L.orc_threads.restype = I
+        L.orc_ray.argtypes = [f64p, D, D, f64p, f64p]
+        L.orc_label_map.argtypes = [I, I, I, u32p, u16p, I64, i32p]; L.orc_label_map.restype = I64
+        L.orc_march.argtypes = [i32p, f64p, D, i32p, f64p, f64p, D, I, i32p, i32p, i32p]
+        L.orc_march.restype = I
+        L.orc_encode.argtypes = [f64p, I, f64p]
+        L.orc_mlp.argtypes = [f32p, I, I, I, D, f64p, f64p, f64p, f64p]
+        L.orc_composite.argtypes = [I, f64p, f64p, f64p, D, D, f64p, f64p, f64p]
+        L.orc_composite.restype = I
+        L.orc_render.argtypes = [i32p, f64p, D, i32p, f32p, f32p, I, I, I, D, f64p, I, u32p, I64,
+                                 D, I, D, f64p, f64p, f64p, f64p, i32p, i32p, i32p, f64p]
+        L.orc_render.restype = I
+        L.orc_march_rays.argtypes = [i32p, f64p, D, i32p, f64p, I, u32p, I64, D, I, i32p, i32p, i32p, i32p]
+        L.orc_march_rays.restype = I
+        L.orc_loss_grad.argtypes = [i32p, f64p, D, i32p, f32p, f32p, I, I, I, I, D, f64p, I, u32p, I64,
+                                    D, I, D, f64p, f32p, D, f64p, u64p, f64p]
+        L.orc_loss_grad.restype = D
+        L.orc_rays_touching.argtypes = [i32p, f64p, D, i32p, f64p, I, u32p, I64, D, I, I, u8p]
+        L.orc_rays_touching.restype = I
+        _lib = L
+    return _lib
+
+
+def _p(a, ct):
+    return a.ctypes.data_as(ctypes.POINTER(ct)) if a is not None else None
+
+
+def f32(x) -> float:
+    """Round a Python float to the FP32 value the library receives."""
+    return float(np.float32(x))
+
+
+def threads() -> int:
+    return int(lib().orc_threads())
+
+
+def param_count(W: int, H: int) -> int:
+    return int(lib().orc_param_count(W, H))
+
+
+def ray(cam16: np.ndarray, uc: float, vc: float):
+    cam = np.ascontiguousarray(cam16, dtype=np.float64)
+    o = np.zeros(3); d = np.zeros(3)
+    lib().orc_ray(_p(cam, ctypes.c_double), uc, vc, _p(o, ctypes.c_double), _p(d, ctypes.c_double))
+    return o, d
+
+
+def encode(x, L: int) -> np.ndarray:
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    out = np.zeros(3 + 6 * L)
+    lib().orc_encode(_p(x, ctypes.c_double), L, _p(out, ctypes.c_double))
+    return out
+
+
+def mlp(w_field: np.ndarray, W: int, H: int, sigma_scale: float, aff: np.ndarray, p, d, act: int = 0):
+    w = np.ascontiguousarray(w_field, dtype=np.float32)
+    a = np.ascontiguousarray(np.asarray(aff, dtype=np.float32), dtype=np.float64)
+    p = np.ascontiguousarray(p, dtype=np.float64)
+    d = np.ascontiguousarray(d, dtype=np.float64)
+    out = np.zeros(4)
+    lib().orc_mlp(_p(w, ctypes.c_float), W, H, act, f32(sigma_scale), _p(a, ctypes.c_double),
+                  _p(p, ctypes.c_double), _p(d, ctypes.c_double), _p(out, ctypes.c_double))
+    return out
+
+
+def composite(sigma, rgb, t, delta: float, t_stop: float = 1e-4, bg=(0.0, 0.0, 0.0)):
+    sigma = np.ascontiguousarray(sigma, dtype=np.float64)
+    rgb = np.ascontiguousarray(rgb, dtype=np.float64).reshape(-1)
+    t = np.ascontiguousarray(t, dtype=np.float64)
+    bg = np.ascontiguousarray(bg, dtype=np.float64)
+    out = np.zeros(5)
+    margin = np.zeros(1)
+    used = lib().orc_composite(int(sigma.size), _p(sigma, ctypes.c_double), _p(rgb, ctypes.c_double),
+                               _p(t, ctypes.c_double), delta, t_stop, _p(bg, ctypes.c_double),
+                               _p(out, ctypes.c_double), _p(margin, ctypes.c_double))
+    return out, int(used), float(margin[0])
+
+
+class Grid:
+    """Occupancy grid + labels as the oracle sees them (dense label map)."""
+
+    def __init__(self, scene, part):
+        gx, gy, gz = scene.dims
+        self.dims = np.array(scene.dims, dtype=np.int32)
+        self.origin = np.array([f32(v) for v in scene.origin], dtype=np.float64)
+        self.vox = f32(scene.vox)
+        bits = np.ascontiguousarray(scene.bits, dtype=np.uint32)
+        fr = np.ascontiguousarray(part.field_of_rank, dtype=np.uint16)
+        self.label = np.empty(gx * gy * gz, dtype=np.int32)
+        n = lib().orc_label_map(gx, gy, gz, _p(bits, ctypes.c_uint32), _p(fr, ctypes.c_uint16),
+                                int(fr.size), _p(self.label, ctypes.c_int32))
+        if n < 0:
+            raise ValueError("field_of_rank length does not match the number of occupied voxels")
+        self.n_occupied = int(n)
+
+    def args(self):
+        return (_p(self.dims, ctypes.c_int32), _p(self.origin, ctypes.c_double), self.vox,
+                _p(self.label, ctypes.c_int32))
+
+
+def cams_f32(cam16: np.ndarray) -> np.ndarray:
+    """Camera rows with R and o rounded to FP32 (what the library receives)."""
+    c = np.array(cam16, dtype=np.float64, copy=True).reshape(-1, 16)
+    c[:, 3:] = c[:, 3:].astype(np.float32).astype(np.float64)
+    return np.ascontiguousarray(c)
+
+
+def march(grid: Grid, o, d, delta: float, n_max: int):
+    o = np.ascontiguousarray(o, dtype=np.float64)
+    d = np.ascontiguousarray(d, dtype=np.float64)
+    js = np.zeros(max(n_max, 1), dtype=np.int32)
+    fs = np.zeros(max(n_max, 1), dtype=np.int32)
+    ties = np.zeros(1, dtype=np.int32)
+    n = lib().orc_march(*grid.args(), _p(o, ctypes.c_double), _p(d, ctypes.c_double), f32(delta), n_max,
+                        _p(js, ctypes.c_int32), _p(fs, ctypes.c_int32), _p(ties, ctypes.c_int32))
+    return js[:n].copy(), fs[:n].copy(), int(ties[0])
+
+
+def march_rays(grid: Grid, cams16, rays: Optional[np.ndarray], delta: float, n_max: int):
+    cams = cams_f32(cams16)
+    n_rays = int(rays.shape[0]) if rays is not None else int(sum(c[1] * c[2] for c in cams))
+    r = np.ascontiguousarray(rays, dtype=np.uint32) if rays is not None else None
+    cnt = np.zeros(n_rays, dtype=np.int32)
+    js = np.zeros((n_rays, n_max), dtype=np.int32)
+    fs = np.zeros((n_rays, n_max), dtype=np.int32)
+    ties = np.zeros(n_rays, dtype=np.int32)
+    rc = lib().orc_march_rays(*grid.args(), _p(cams, ctypes.c_double), int(cams.shape[0]),
+                              _p(r, ctypes.c_uint32), n_rays, f32(delta), n_max, _p(cnt, ctypes.c_int32),
+                              _p(js, ctypes.c_int32), _p(fs, ctypes.c_int32), _p(ties, ctypes.c_int32))
+    if rc:
+        raise ValueError("orc_march_rays rejected its arguments")
+    return cnt, js, fs, ties
+
+
+def render(grid: Grid, weights, affine, W: int, H: int, sigma_scale: float, cams16,
+           rays: Optional[np.ndarray], delta: float, n_max: int, t_stop: float = 1e-4,
+           bg=(0.0, 0.0, 0.0), act: int = 0):
+    """Renders (view, pixel) rays, or every pixel of every view (rays=None).
+    Returns a dict of per-ray arrays."""
+    cams = cams_f32(cams16)
+    w = np.ascontiguousarray(weights, dtype=np.float32)
+    aff = np.ascontiguousarray(affine, dtype=np.float32)
+    n_rays = int(rays.shape[0]) if rays is not None else int(sum(c[1] * c[2] for c in cams))
+    r = np.ascontiguousarray(rays, dtype=np.uint32) if rays is not None else None
+    bgv = np.array([f32(b) for b in bg], dtype=np.float64)
+    out = dict(rgb=np.zeros((n_rays, 3)), depth=np.zeros(n_rays), opacity=np.zeros(n_rays),
+               n_kept=np.zeros(n_rays, np.int32), n_used=np.zeros(n_rays, np.int32),
+               ties=np.zeros(n_rays, np.int32), margin=np.zeros(n_rays))
+    rc = lib().orc_render(*grid.args(), _p(w, ctypes.c_float), _p(aff, ctypes.c_float), W, H, act,
+                          f32(sigma_scale), _p(cams, ctypes.c_double), int(cams.shape[0]),
+                          _p(r, ctypes.c_uint32), n_rays, f32(delta), n_max, f32(t_stop),
+                          _p(bgv, ctypes.c_double), _p(out["rgb"], ctypes.c_double),
+                          _p(out["depth"], ctypes.c_double), _p(out["opacity"], ctypes.c_double),
+                          _p(out["n_kept"], ctypes.c_int32), _p(out["n_used"], ctypes.c_int32),
+                          _p(out["ties"], ctypes.c_int32), _p(out["margin"], ctypes.c_double))
+    if rc:
+        raise ValueError("orc_render rejected its arguments")
+    return out
+
+
+def loss_grad(grid: Grid, weights, affine, W: int, H: int, sigma_scale: float, cams16, rays,
+              target, delta: float, n_max: int, t_stop: float = 1e-4, bg=(0.0, 0.0, 0.0),
+              want_grad: bool = True, loss_norm: Optional[float] = None, act: int = 0):
+    """Mean-squared photometric loss over the rays and its gradient w.r.t.
+    every weight ([F][P] float64).  Returns (loss, grad or None, signature,
+    rendered rgb)."""
+    cams = cams_f32(cams16)
+    w = np.ascontiguousarray(weights, dtype=np.float32)
+    n_fields = int(w.shape[0])
+    aff = np.ascontiguousarray(affine, dtype=np.float32)
+    r = np.ascontiguousarray(rays, dtype=np.uint32)
+    n_rays = int(r.shape[0])
+    tg = np.ascontiguousarray(target, dtype=np.float32)
+    bgv = np.array([f32(b) for b in bg], dtype=np.float64)
+    grad = np.zeros(w.shape, dtype=np.float64) if want_grad else None
+    sig = np.zeros(1, dtype=np.uint64)
+    rgb = np.zeros((n_rays, 3))
+    norm = float(loss_norm) if loss_norm is not None else 3.0 * n_rays
+    loss = lib().orc_loss_grad(*grid.args(), _p(w, ctypes.c_float), _p(aff, ctypes.c_float), n_fields, W, H,
+                               act, f32(sigma_scale), _p(cams, ctypes.c_double), int(cams.shape[0]),
+                               _p(r, ctypes.c_uint32), n_rays, f32(delta), n_max, f32(t_stop),
+                               _p(bgv, ctypes.c_double), _p(tg, ctypes.c_float), norm,
+                               _p(grad, ctypes.c_double), _p(sig, ctypes.c_uint64), _p(rgb, ctypes.c_double))
+    if not np.isfinite(loss):
+        raise ValueError("orc_loss_grad failed")
+    return float(loss), grad, int(sig[0]), rgb
+
+
+def rays_touching(grid: Grid, cams16, rays, delta: float, n_max: int, field: int) -> np.ndarray:
+    cams = cams_f32(cams16)
+    r = np.ascontiguousarray(rays, dtype=np.uint32)
+    mask = np.zeros(r.shape[0], dtype=np.uint8)
+    lib().orc_rays_touching(*grid.args(), _p(cams, ctypes.c_double), int(cams.shape[0]), _p(r, ctypes.c_uint32),
+                            int(r.shape[0]), f32(delta), n_max, field, _p(mask, ctypes.c_uint8))
+    return mask.astype(bool)

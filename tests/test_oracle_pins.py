@@ -1,0 +1,491 @@
+"""Pins of the FP64 oracle against facts fixed by the paper and by
+mathematics (closed forms, special values, brute force, invariants), chosen so
+that a dropped term, a wrong sign or index, or a transposed operand anywhere
+in the oracle fails at least one of them.  CPU only."""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import fixtures as F
+import oracle as O
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "paper_values.json")
+
+
+def cam16(model=0, W=64, H=32, fov=0.0, R=None, o=(0.0, 0.0, 0.0)):
+    R = np.eye(3) if R is None else np.asarray(R)
+    return np.concatenate([[model, W, H, fov], R.reshape(9), o]).astype(np.float64)
+
+
+# ----------------------------------------------------------------------------
+# parameter counts (Appendix, network architecture details)
+# ----------------------------------------------------------------------------
+
+def test_param_count_matches_paper():
+    g = json.load(open(GOLDEN))
+    assert O.param_count(32, 2) == g["tiny_mlp_params"]["value"] == 6212
+    # 200 tiny networks ~ 1.2M parameters (ablation on the number of networks)
+    total = 200 * O.param_count(32, 2)
+    assert abs(total - g["n200_total_params_approx"]["value"]) / 1.2e6 < 0.05
+    # the larger widths used by the workloads
+    assert O.param_count(64, 3) == 22724
+    assert O.param_count(128, 4) == 94724
+    assert F.n_params(32, 2) == 6212 and F.n_params(64, 3) == 22724
+
+
+# ----------------------------------------------------------------------------
+# ray generation (Eq. 2, Eq. 3)
+# ----------------------------------------------------------------------------
+
+@pytest.mark.parametrize("uc,vc,expect", [
+    (32.0, 16.0, (0.0, 0.0, 1.0)),      # image centre: phi = 0, theta = 0
+    (48.0, 16.0, (1.0, 0.0, 0.0)),      # u = 3W/4: phi = +pi/2
+    (16.0, 16.0, (-1.0, 0.0, 0.0)),     # u = W/4: phi = -pi/2
+    (0.0, 16.0, (0.0, 0.0, -1.0)),      # left edge: phi = -pi
+    (32.0, 0.0, (0.0, -1.0, 0.0)),      # top edge: theta = +pi/2, y = -sin(theta)
+    (32.0, 32.0, (0.0, 1.0, 0.0)),      # bottom edge: theta = -pi/2
+])
+def test_equirect_special_pixels(uc, vc, expect):
+    o, d = O.ray(cam16(), uc, vc)
+    assert np.allclose(d, expect, atol=1e-12)
+    assert np.allclose(o, 0.0)
+
+
+def test_equirect_round_trip_through_eq2():
+    rng = np.random.default_rng(7)
+    W, H = 128, 64
+    for _ in range(200):
+        uc, vc = rng.uniform(0.01, W - 0.01), rng.uniform(0.01, H - 0.01)
+        _, d = O.ray(cam16(W=W, H=H), uc, vc)
+        assert abs(np.linalg.norm(d) - 1.0) < 1e-13
+        # invert Eq. 3, then apply Eq. 2 forwards
+        phi = math.atan2(d[0], d[2])
+        theta = math.asin(-d[1])
+        u = phi * W / (2 * math.pi) + W / 2
+        v = -theta * H / math.pi + H / 2
+        assert abs(u - uc) < 1e-9 and abs(v - vc) < 1e-9
+
+
+def test_camera_rotation_and_origin():
+    R = F.yaw_pitch(0.7, 0.2)
+    o = np.array([1.0, 2.0, 3.0])
+    rng = np.random.default_rng(3)
+    for _ in range(20):
+        uc, vc = rng.uniform(0, 64), rng.uniform(0, 32)
+        _, d0 = O.ray(cam16(), uc, vc)
+        oo, d1 = O.ray(cam16(R=R, o=o), uc, vc)
+        assert np.allclose(oo, o)
+        assert np.allclose(R.T @ d1, d0, atol=1e-13)
+
+
+def test_perspective_pixels():
+    W, H, fov = 200, 100, math.pi / 2
+    _, d = O.ray(cam16(1, W, H, fov), W / 2, H / 2)
+    assert np.allclose(d, (0, 0, 1), atol=1e-14)
+    # the right edge of a 90 degree view is 45 degrees off axis
+    _, d = O.ray(cam16(1, W, H, fov), W, H / 2)
+    assert np.allclose(d, (math.sqrt(0.5), 0, math.sqrt(0.5)), atol=1e-14)
+    # rows grow downwards (+y), and pixels are square
+    _, d = O.ray(cam16(1, W, H, fov), W / 2, H)
+    assert np.allclose(d, np.array([0, 0.5, 1]) / math.sqrt(1.25), atol=1e-14)
+
+
+# ----------------------------------------------------------------------------
+# labels: rank order versus brute-force point-in-box
+# ----------------------------------------------------------------------------
+
+def test_label_map_matches_partition_boxes(room32, room32_grid):
+    occ = room32.scene.occ
+    lab = room32_grid.label.reshape(occ.shape)
+    assert room32_grid.n_occupied == occ.sum()
+    assert ((lab >= 0) == occ).all()
+    z, y, x = np.nonzero(occ)
+    for xx, yy, zz in zip(x, y, z):
+        inside = [f for f, (lo, hi) in enumerate(room32.part.boxes)
+                  if lo[0] <= xx < hi[0] and lo[1] <= yy < hi[1] and lo[2] <= zz < hi[2]]
+        assert len(inside) == 1
+        assert lab[zz, yy, xx] == inside[0]
+
+
+def test_label_map_kd_partition_brute_force():
+    """A 64^3 floor with a 16-leaf kd partition: every occupied voxel lies in
+    exactly one leaf box and the oracle's rank lookup returns that leaf."""
+    scene = F.floor_scene(9, 64, 2, 2, 0.1)
+    part = F.kd_partition(scene, 16)
+    g = O.Grid(scene, part)
+    lab = g.label.reshape(scene.occ.shape)
+    z, y, x = np.nonzero(scene.occ)
+    xyz = np.stack([x, y, z], 1)
+    hits = np.zeros(xyz.shape[0], dtype=np.int64)
+    expect = np.full(xyz.shape[0], -1)
+    for f, (lo, hi) in enumerate(part.boxes):
+        inside = np.all((xyz >= lo) & (xyz < hi), axis=1)
+        hits += inside
+        expect[inside] = f
+    assert (hits == 1).all()
+    assert (lab[z, y, x] == expect).all()
+    assert (lab[~scene.occ] == -1).all()
+
+
+# ----------------------------------------------------------------------------
+# marching: analytic chord counts, empty and full grids
+# ----------------------------------------------------------------------------
+
+class _Scene:
+    def __init__(self, occ, vox=0.1):
+        self.dims = (occ.shape[2], occ.shape[1], occ.shape[0])
+        self.origin = (0.0, 0.0, 0.0)
+        self.vox = vox
+        self.occ = occ
+        self.bits = F.pack_bits(occ)
+
+
+class _Part:
+    def __init__(self, n):
+        self.field_of_rank = np.zeros(n, dtype=np.uint16)
+
+
+def _grid(occ, vox=0.1):
+    s = _Scene(occ, vox)
+    return O.Grid(s, _Part(int(occ.sum())))
+
+
+def _slab_interval(o, d, lo, hi):
+    t0, t1 = -np.inf, np.inf
+    for a in range(3):
+        ta, tb = (lo[a] - o[a]) / d[a], (hi[a] - o[a]) / d[a]
+        t0, t1 = max(t0, min(ta, tb)), min(t1, max(ta, tb))
+    return t0, t1
+
+
+def test_march_single_voxel_chord_count():
+    rng = np.random.default_rng(11)
+    G, vox = 32, 0.1
+    delta = O.f32(vox / 4)
+    checked = 0
+    for trial in range(300):
+        occ = np.zeros((G, G, G), dtype=bool)
+        iv = rng.integers(4, 28, size=3)
+        occ[iv[2], iv[1], iv[0]] = True
+        g = _grid(occ, vox)
+        o = rng.uniform(0.2, 3.0, size=3)
+        target = (iv + rng.uniform(0.1, 0.9, size=3)) * O.f32(vox)
+        d = target - o
+        d /= np.linalg.norm(d)
+        lo, hi = iv * g.vox, (iv + 1) * g.vox
+        t0, t1 = _slab_interval(o, d, lo, hi)
+        t0 = max(t0, 0.0)
+        # count j with t0 <= (j + 1/2) delta < t1; skip grazing cases
+        js = np.arange(0, int(t1 / delta) + 3)
+        tj = (js + 0.5) * delta
+        if np.min(np.abs(np.concatenate([tj - t0, tj - t1]))) < 1e-9:
+            continue
+        expect = js[(tj >= t0) & (tj < t1)]
+        got, fields, _ = O.march(g, o, d, delta, 64)
+        assert np.array_equal(got, expect), (trial, got, expect)
+        assert (fields == 0).all()
+        checked += 1
+    assert checked > 250
+
+
+def test_march_empty_and_full_grids():
+    G, vox = 32, 0.1
+    delta = O.f32(vox / 4)
+    o = np.array([1.55, 1.62, 1.48])
+    rng = np.random.default_rng(5)
+    g_empty = _grid(np.zeros((G, G, G), dtype=bool), vox)
+    g_full = _grid(np.ones((G, G, G), dtype=bool), vox)
+    for _ in range(50):
+        d = rng.normal(size=3)
+        d /= np.linalg.norm(d)
+        js, _, _ = O.march(g_empty, o, d, delta, 1024)
+        assert js.size == 0
+        # full grid: every j whose point is before the exit of the box
+        t0, t1 = _slab_interval(o, d, np.zeros(3), np.full(3, G * g_full.vox))
+        js, _, _ = O.march(g_full, o, d, delta, 1024)
+        expect = np.arange(0, int(np.ceil(t1 / delta - 0.5)))
+        assert np.array_equal(js, expect)
+        js_cap, _, _ = O.march(g_full, o, d, delta, 17)
+        assert np.array_equal(js_cap, expect[:17])
+
+
+def test_march_fields_match_boxes(room32, room32_grid):
+    """Kept samples of real rays: the field of every sample is the partition
+    box containing its point (brute force over all boxes)."""
+    cams = O.cams_f32(F.camera_array(room32.cams))
+    vox = room32_grid.vox
+    rng = np.random.default_rng(2)
+    for _ in range(200):
+        uc, vc = rng.uniform(0, 128), rng.uniform(0, 64)
+        o, d = O.ray(cams[0], uc, vc)
+        js, fs, ties = O.march(room32_grid, o, d, room32.delta, 64)
+        for j, f in zip(js, fs):
+            p = o + (j + 0.5) * O.f32(room32.delta) * d
+            iv = np.floor(p / vox).astype(int)
+            assert room32.scene.occ[iv[2], iv[1], iv[0]]
+            boxes = [k for k, (lo, hi) in enumerate(room32.part.boxes) if np.all(iv >= lo) and np.all(iv < hi)]
+            assert boxes == [f]
+
+
+# ----------------------------------------------------------------------------
+# positional encoding and the tiny MLP
+# ----------------------------------------------------------------------------
+
+S2, S3 = math.sqrt(2.0) / 2, math.sqrt(3.0) / 2
+
+
+def test_encoding_special_values():
+    # x = (1/6, 1/4, 1/2): exact trigonometric values for pi x, 2 pi x, 4 pi x
+    x = np.array([1.0 / 6, 0.25, 0.5])
+    e = O.encode(x, 3)
+    assert e.shape == (21,)
+    assert np.allclose(e[0:3], x, atol=0)
+    # k = 0: sin(pi/6, pi/4, pi/2), cos(...)
+    assert np.allclose(e[3:6], [0.5, S2, 1.0], atol=1e-15)
+    assert np.allclose(e[6:9], [S3, S2, 0.0], atol=1e-15)
+    # k = 1: angles pi/3, pi/2, pi
+    assert np.allclose(e[9:12], [S3, 1.0, 0.0], atol=1e-15)
+    assert np.allclose(e[12:15], [0.5, 0.0, -1.0], atol=1e-15)
+    # k = 2: angles 2pi/3, pi, 2pi
+    assert np.allclose(e[15:18], [S3, 0.0, 0.0], atol=1e-14)
+    assert np.allclose(e[18:21], [-0.5, -1.0, 1.0], atol=1e-14)
+    assert O.encode(x, 10).shape == (63,) and O.encode(x, 4).shape == (27,)
+
+
+def _offsets(W, H):
+    offs, o = [], 0
+    for (n_out, n_in) in F.layer_shapes(W, H):
+        offs.append((o, o + n_out * n_in, n_out, n_in))
+        o += n_out * n_in + n_out
+    return offs, o
+
+
+def test_mlp_zero_weights_closed_form():
+    W, H = 16, 3
+    offs, P = _offsets(W, H)
+    rng = np.random.default_rng(1)
+    w = np.zeros(P, dtype=np.float32)
+    for (wo, bo, n_out, _) in offs:
+        w[bo:bo + n_out] = rng.uniform(-1, 1, n_out)
+    b_head = w[offs[H][1]:offs[H][1] + 1 + W]
+    b_out = w[offs[H + 2][1]:offs[H + 2][1] + 3]
+    aff = np.array([1, 1, 1, 0, 0, 0], dtype=np.float32)
+    for _ in range(5):
+        p, d = rng.uniform(-1, 1, 3), rng.normal(size=3)
+        out = O.mlp(w, W, H, 2.5, aff, p, d)
+        s = float(b_head[0])
+        assert abs(out[0] - O.f32(2.5) * math.log(1 + math.exp(s))) < 1e-12
+        assert np.allclose(out[1:], 1 / (1 + np.exp(-b_out.astype(np.float64))), atol=1e-15)
+
+
+@pytest.mark.parametrize("m,mp,xl,dv,pe_m,pe_dm", [
+    # index m of F(x_loc) (L = 10) and m' of F(d) (L = 4), with their values
+    # known exactly from trigonometry:
+    #  m=4: sin(pi x1), x1=1/4 -> sqrt(2)/2;     m'=10: sin(2 pi d1), d1=1/4 -> 1
+    (4, 10, (1 / 6, 0.25, 0.5), (0.5, 0.25, 1 / 6), S2, 1.0),
+    #  m=1: raw x1 = -0.7;                         m'=0: raw d0 = 0.6
+    (1, 0, (0.3, -0.7, 0.1), (0.6, 0.0, 0.8), -0.7, 0.6),
+    #  m=8: cos(pi x2), x2=-1/3 -> 1/2;            m'=26: cos(8 pi d2), d2=1/24 -> 1/2
+    (8, 26, (0.2, 0.4, -1 / 3), (0.0, 1.0, 1 / 24), 0.5, 0.5),
+    #  m=62: cos(512 pi x2), x2=1/1536 -> 1/2;     m'=13: cos(2 pi d1), d1=1/6 -> 1/2
+    (62, 13, (0.1, 0.2, 1 / 1536), (0.3, 1 / 6, 0.2), 0.5, 0.5),
+])
+def test_mlp_one_hot_closed_form(m, mp, xl, dv, pe_m, pe_dm):
+    """Weights that route one encoded feature through every layer: the
+    density sees relu(F(x)[m]); the green channel sees
+    relu(relu(F(x)[m]) + F(d)[m']).  Asymmetric row/column choices catch a
+    transposed operand, a shifted layer offset or a misplaced encoding index."""
+    W, H = 8, 2
+    offs, P = _offsets(W, H)
+    w = np.zeros(P, dtype=np.float32)
+    l1, l2, head, col, out = offs
+    w[l1[0] + 0 * 63 + m] = 1.0              # h1[0] = relu(F(x)[m])
+    w[l2[0] + 0 * W + 0] = 1.0               # h2[0] = h1[0]
+    w[head[0] + 0 * W + 0] = 1.0             # s = h2[0]
+    w[head[0] + (1 + 2) * W + 0] = 1.0       # feat[2] = h2[0]
+    Kc = W + 27
+    w[col[0] + 5 * Kc + 2] = 1.0             # g[5] = relu(feat[2] + F(d)[m'])
+    w[col[0] + 5 * Kc + W + mp] = 1.0
+    w[out[0] + 1 * W + 5] = 1.0              # green = sigmoid(g[5])
+    w[out[1] + 2] = 0.75                     # blue bias
+    aff = np.array([1, 1, 1, 0, 0, 0], dtype=np.float32)
+    got = O.mlp(w, W, H, 1.0, aff, np.array(xl, dtype=np.float64), np.array(dv, dtype=np.float64))
+    relu = lambda v: max(v, 0.0)
+    assert abs(got[0] - math.log1p(math.exp(relu(pe_m)))) < 1e-12
+    assert abs(got[1] - 0.5) < 1e-15
+    g5 = relu(relu(pe_m) + pe_dm)
+    assert abs(got[2] - 1 / (1 + math.exp(-g5))) < 1e-12
+    assert abs(got[3] - 1 / (1 + math.exp(-0.75))) < 1e-12
+
+
+def test_mlp_affine_maps_field_box():
+    """x_loc = scale * p + offset: a point at the box centre encodes as 0."""
+    W, H = 8, 2
+    offs, P = _offsets(W, H)
+    w = np.zeros(P, dtype=np.float32)
+    w[offs[0][0] + 0 * 63 + 0] = 1.0   # h1[0] = relu(x_loc[0])
+    w[offs[1][0]] = 1.0
+    w[offs[2][0]] = 1.0                # s = relu(x_loc[0])
+    scale = np.array([4.0, 2.0, 1.0]); off = np.array([-3.0, 0.5, 0.0])
+    aff = np.concatenate([scale, off]).astype(np.float32)
+    for px in (0.5, 0.75, 1.0, 0.9):
+        p = np.array([px, 0.0, 0.0])
+        got = O.mlp(w, W, H, 1.0, aff, p, np.array([0, 0, 1.0]))
+        xl0 = 4.0 * px - 3.0
+        assert abs(got[0] - math.log1p(math.exp(max(xl0, 0.0)))) < 1e-12
+
+
+# ----------------------------------------------------------------------------
+# compositing (Eq. 4, Eq. 5) with early termination
+# ----------------------------------------------------------------------------
+
+def test_composite_two_samples_closed_form():
+    a, b, delta = 3.0, 7.0, 0.05
+    c0, c1 = np.array([0.2, 0.5, 0.9]), np.array([0.7, 0.1, 0.3])
+    bg = np.array([0.1, 0.2, 0.3])
+    out, used, _ = O.composite([a, b], np.stack([c0, c1]), [1.0, 2.0], delta, 0.0, bg)
+    w0 = 1 - math.exp(-a * delta)
+    w1 = math.exp(-a * delta) * (1 - math.exp(-b * delta))
+    Tend = math.exp(-(a + b) * delta)
+    assert used == 2
+    assert np.allclose(out[:3], w0 * c0 + w1 * c1 + Tend * bg, atol=1e-15)
+    assert abs(out[3] - (w0 * 1.0 + w1 * 2.0)) < 1e-15
+    assert abs(out[4] - (1 - Tend)) < 1e-15
+
+
+def test_composite_constant_slab_and_sum_of_weights():
+    sigma, delta, n = 1.7, 0.01, 80
+    rgb = np.tile([0.25, 0.5, 0.75], (n, 1))
+    t = (np.arange(n) + 0.5) * delta
+    out, used, _ = O.composite(np.full(n, sigma), rgb, t, delta, 0.0)
+    ell = n * delta
+    assert used == n
+    assert abs(out[4] - (1 - math.exp(-sigma * ell))) < 1e-14           # opacity
+    assert np.allclose(out[:3], (1 - math.exp(-sigma * ell)) * rgb[0], atol=1e-14)
+    # random densities: sum of weights = 1 - T_end <= 1
+    rng = np.random.default_rng(0)
+    s = rng.uniform(0, 50, 64)
+    out, used, _ = O.composite(s, rng.uniform(0, 1, (64, 3)), np.arange(64.0), 0.02, 0.0)
+    assert 0 <= out[4] <= 1
+    assert abs(out[4] - (1 - math.exp(-s.sum() * 0.02))) < 1e-13
+
+
+def test_composite_termination_and_truncation_bound():
+    rng = np.random.default_rng(4)
+    for _ in range(100):
+        n = int(rng.integers(1, 60))
+        s = rng.uniform(0, 80, n)
+        rgb = rng.uniform(0, 1, (n, 3))
+        t = np.cumsum(rng.uniform(0.01, 0.1, n))
+        full, nf, _ = O.composite(s, rgb, t, 0.05, 0.0)
+        trunc, nu, _ = O.composite(s, rgb, t, 0.05, 1e-4)
+        tau = np.cumsum(s * 0.05)
+        T_after = np.exp(-tau)
+        if (T_after < 1e-4).any():
+            assert nu == int(np.argmax(T_after < 1e-4)) + 1
+        else:
+            assert nu == n
+        assert nf == n
+        assert np.max(np.abs(full[:3] - trunc[:3])) <= 1e-4
+
+
+def test_composite_empty_ray_is_background():
+    out, used, _ = O.composite([], np.zeros((0, 3)), [], 0.1, 1e-4, (0.3, 0.2, 0.1))
+    assert used == 0
+    assert np.allclose(out, [0.3, 0.2, 0.1, 0.0, 0.0])
+
+
+# ----------------------------------------------------------------------------
+# whole rays through the oracle's render
+# ----------------------------------------------------------------------------
+
+def _const_weights(W, H, b_sigma, b_rgb):
+    offs, P = _offsets(W, H)
+    w = np.zeros(P, dtype=np.float32)
+    w[offs[H][1]] = b_sigma
+    w[offs[H + 2][1]:offs[H + 2][1] + 3] = b_rgb
+    return w
+
+
+def test_render_empty_grid_is_background(room32):
+    occ = np.zeros((32, 32, 32), dtype=bool)
+    g = _grid(occ)
+    W, H = 8, 2
+    w = _const_weights(W, H, 1.0, [0, 0, 0])[None, :]
+    aff = np.array([[1, 1, 1, 0, 0, 0]], dtype=np.float32)
+    cams = F.camera_array(room32.cams)
+    r = O.render(g, w, aff, W, H, 10.0, cams, None, 0.025, 64, bg=(0.25, 0.5, 0.75))
+    assert (r["n_kept"] == 0).all()
+    assert np.allclose(r["rgb"], np.array([0.25, 0.5, 0.75], dtype=np.float32), atol=0)
+    assert np.allclose(r["opacity"], 0) and np.allclose(r["depth"], 0)
+
+
+def test_render_slab_transmittance_matches_exp_sigma_l():
+    """A fully occupied slab z in [16, 24) voxels, constant density: the ray's
+    opacity converges to 1 - exp(-sigma * chord) as delta -> 0, and for each
+    delta equals 1 - exp(-sigma * n * delta) with n the samples inside."""
+    G, vox = 32, 0.1
+    occ = np.zeros((G, G, G), dtype=bool)
+    occ[16:24, :, :] = True
+    g = _grid(occ, vox)
+    W, H = 8, 2
+    b_sigma = 0.3
+    w = _const_weights(W, H, b_sigma, [0.4, -0.2, 1.0])[None, :]
+    aff = np.array([[1, 1, 1, 0, 0, 0]], dtype=np.float32)
+    sigma = O.f32(4.0) * math.log1p(math.exp(O.f32(b_sigma)))
+    # camera at (1.6, 1.6, 0.45) looking along +z tilted by 0.3 rad in x
+    R = F.yaw_pitch(0.3, 0.0)
+    cam = np.concatenate([[1, 64, 64, math.pi / 2], R.reshape(9), [1.6, 1.6, 0.45]])[None, :]
+    rays = np.array([[0, 32 * 64 + 32]], dtype=np.uint32)     # the central pixel
+    camf = O.cams_f32(cam)
+    o, d = O.ray(camf[0], 32.5, 32.5)
+    z0, z1 = 16 * O.f32(vox), 24 * O.f32(vox)
+    chord = (z1 - z0) / d[2]
+    errs = []
+    for delta in (0.02, 0.01, 0.005, 0.0025):
+        r = O.render(g, w, aff, W, H, 4.0, cam, rays, delta, 1024, t_stop=0.0)
+        n = int(r["n_kept"][0])
+        df = O.f32(delta)
+        assert abs(r["opacity"][0] - (1 - math.exp(-sigma * n * df))) < 1e-12
+        errs.append(abs(r["opacity"][0] - (1 - math.exp(-sigma * chord))))
+    assert errs[-1] < 0.01 and errs[-1] < errs[0]
+
+
+# ----------------------------------------------------------------------------
+# gradient: analytic reverse mode versus central finite differences
+# ----------------------------------------------------------------------------
+
+def test_loss_gradient_matches_central_differences(room32, room32_grid):
+    W, H = 16, 2
+    n_fields = room32.part.n_fields
+    w = F.xavier_weights(1, F.ROLE_STUDENT, n_fields, W, H, bias_scale=0.1)
+    cams = F.camera_array(room32.cams)
+    rays = F.ray_batch(1, room32.cams, 96)
+    rng = np.random.default_rng(12)
+    target = rng.uniform(0, 1, (96, 3)).astype(np.float32)
+    args = (room32_grid, w, room32.affine, W, H, room32.sigma_scale, cams, rays, target, room32.delta, 64)
+    loss, grad, sig, _ = O.loss_grad(*args)
+    assert loss > 0 and np.abs(grad).max() > 0
+    h = 1e-4
+    gmax = np.abs(grad).max()
+    P = w.shape[1]
+    checked = 0
+    for _ in range(60):
+        f = int(rng.integers(n_fields))
+        k = int(rng.integers(P))
+        wp, wm = w.copy(), w.copy()
+        # perturb in FP64 terms: the oracle reads FP32 weights, so use an
+        # FP32-representable step and measure the step actually taken
+        wp[f, k] = np.float32(w[f, k] + h)
+        wm[f, k] = np.float32(w[f, k] - h)
+        lp, _, sp, _ = O.loss_grad(room32_grid, wp, *args[2:], want_grad=False)
+        lm, _, sm, _ = O.loss_grad(room32_grid, wm, *args[2:], want_grad=False)
+        if sp != sig or sm != sig:
+            continue     # the step crossed a ReLU kink or a termination index
+        fd = (lp - lm) / (float(wp[f, k]) - float(wm[f, k]))
+        assert abs(fd - grad[f, k]) <= 1e-6 * gmax + 1e-7 * abs(grad[f, k]) + 1e-10, (f, k, fd, grad[f, k])
+        checked += 1
+    assert checked >= 40
