@@ -1,0 +1,351 @@
+#!/usr/bin/env python3
+"""Benchmark of the render hot path on the 256^3 eight-room floor workload:
+512 kd fields, W=64/H=3 tiny MLPs, one 1024x512 equirectangular view plus one
+1920x1080 perspective view (90 degree FOV), <= 128 samples per ray.
+
+One step = one roam_render call over both views: ray generation, march,
+field lookup, bucketing, encoding + grouped MLPs, compositing with early
+termination.  Inputs (grid, labels, weights) are resident on the device;
+L2 is flushed (256 MiB write) between timed steps.
+
+value = composited samples per second (samples that reach the image, up to
+each ray's termination), summed over ranks; under torchrun every rank renders
+its own replica of the workload (weak scaling, no collective on the data
+path).
+
+--impl reference times the FP64 CPU oracle (the reference arm of this
+benchmark) on bounded samples of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "samples/s & 1024×512 frame ms, BF16-TC vs FP32 on GB300 at ≥40 dB PSNR vs oracle"
+UNIT = "samples/s"
+
+
+def macs_per_sample(W, H):
+    return 63 * W + (H - 1) * W * W + W * (1 + W) + (W + 27) * W + 3 * W
+
+
+def workload_config(wl, views):
+    return {"workload": "floor256_kd512_w64h3_equirect1024x512_persp1920x1080",
+            "grid": "256^3 bit-packed, %.1f%% occupied" % (100.0 * wl.scene.n_occupied / 256 ** 3),
+            "fields": wl.part.n_fields, "mlp": f"W={wl.W} H={wl.H} ({macs_per_sample(wl.W, wl.H)} MACs/sample)",
+            "views": views, "n_max": wl.n_max, "delta": "vox/4", "t_stop": 1e-4,
+            "l2": "flushed between timed steps (256 MiB write)"}
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(prefix="clocks_", suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def oracle_sample_rays(wl, n, seed):
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    sizes = [c.n_pixels for c in wl.cams]
+    view = rng.integers(0, len(sizes), n)
+    pix = np.array([rng.integers(0, sizes[v]) for v in view], dtype=np.int64)
+    return np.stack([view, pix], 1).astype(np.uint32)
+
+
+def cpu_oracle_rate(wl, target_s: float, seed: int = 1234):
+    """Times the FP64 oracle (as it stands) on a bounded ray sample sized for
+    about target_s seconds.  Returns (samples/s, cores, description)."""
+    import fixtures as F
+    import oracle as O
+    g = O.Grid(wl.scene, wl.part)
+    cams = F.camera_array(wl.cams)
+    probe = oracle_sample_rays(wl, 2000, seed)
+    t0 = time.perf_counter()
+    r = O.render(g, wl.weights, wl.affine, wl.W, wl.H, wl.sigma_scale, cams, probe, wl.delta, wl.n_max)
+    dt = time.perf_counter() - t0
+    n = int(max(2000, min(2_000_000, 2000 * target_s / max(dt, 1e-3))))
+    rays = oracle_sample_rays(wl, n, seed + 1)
+    t0 = time.perf_counter()
+    r = O.render(g, wl.weights, wl.affine, wl.W, wl.H, wl.sigma_scale, cams, rays, wl.delta, wl.n_max)
+    dt = time.perf_counter() - t0
+    used = int(r["n_used"].sum())
+    return used / dt, O.threads(), f"{n} random pixels of both views ({used} composited samples, {dt:.1f} s)"
+
+
+def reference_arm(args):
+    world, rank, _ = dist_setup()
+    if rank != 0:
+        return 0
+    import fixtures as F
+    import oracle as O
+    wl = F.floor256()
+    g = O.Grid(wl.scene, wl.part)
+    cams = F.camera_array(wl.cams)
+    n_rays = 6000
+    times, used = [], []
+    for step in range(args.warmup + args.steps):
+        rays = oracle_sample_rays(wl, n_rays, 100 + step)
+        t0 = time.perf_counter()
+        r = O.render(g, wl.weights, wl.affine, wl.W, wl.H, wl.sigma_scale, cams, rays, wl.delta, wl.n_max)
+        dt = time.perf_counter() - t0
+        if step >= args.warmup:
+            times.append(dt)
+            used.append(int(r["n_used"].sum()))
+    value = sum(used) / sum(times)
+    views = ["equirect 1024x512", "perspective 1920x1080 fov 90"]
+    sample = f"each step: {n_rays} random pixels of both views"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * sum(times) / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": workload_config(wl, views),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": O.threads(), "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def time_steps(r, cams, opts, steps, warmup, flush, stream):
+    import torch
+    for _ in range(warmup):
+        r.render(cams, opts, stream=stream)
+    torch.cuda.synchronize()
+    total = 0.0
+    per = []
+    for _ in range(steps):
+        flush.zero_()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        r.render(cams, opts, stream=stream)
+        b.record(stream)
+        b.synchronize()
+        ms = a.elapsed_time(b)
+        per.append(ms)
+        total += ms
+    return total, per
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="roam", choices=["roam", "reference"])
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    if args.impl == "reference":
+        return reference_arm(args)
+
+    import numpy as np
+    import torch
+
+    import fixtures as F
+    import paper_2208_02705_gb300 as roam
+
+    world, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    wl = F.floor256()
+    r = roam.Roam(local)
+    r.load_workload(wl)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")   # 256 MiB > L2
+    views = ["equirect 1024x512", "perspective 1920x1080 fov 90"]
+
+    try:
+        r.render(wl.cams, roam.render_opts(wl.delta, wl.n_max, precision=roam.ROAM_BF16))
+        head_prec, dtype = roam.ROAM_BF16, "bf16"
+    except roam.RoamError:
+        head_prec, dtype = roam.ROAM_F32, "f32"
+    opts = roam.render_opts(wl.delta, wl.n_max, precision=head_prec)
+
+    # ---- headline: K timed steps, event-timed per-kernel record on ----
+    for _ in range(args.warmup):
+        r.render(wl.cams, opts, stream=stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clk = ClockSampler(local)
+    clk.start()
+    r.profile(True)
+    total_ms, per = time_steps(r, wl.cams, opts, args.steps, 0, flush, stream)
+    prof = r.profile_read()
+    r.profile(False)
+    torch.cuda.synchronize()
+    clocks = clk.stop()
+    st = r.get_stats()
+    if world > 1:
+        t = torch.tensor([total_ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    used_per_step = st.n_used
+    evaluated_per_step = st.n_samples
+    value = world * used_per_step * args.steps / (total_ms / 1000.0)
+    ms_per_step = total_ms / args.steps
+
+    # ---- per-view frame times and the FP32 SIMT form ----
+    frame = {}
+    for prec, tag in ((head_prec, dtype), (roam.ROAM_F32, "f32")):
+        if tag in frame:
+            continue
+        o = roam.render_opts(wl.delta, wl.n_max, precision=prec)
+        frame[tag] = {}
+        for cam, name in zip(wl.cams, ("equirect_1024x512", "persp_1920x1080")):
+            tot, per_v = time_steps(r, [cam], o, max(3, args.steps // 2), 2, flush, stream)
+            frame[tag][name] = statistics.median(per_v)
+    o32 = roam.render_opts(wl.delta, wl.n_max, precision=roam.ROAM_F32)
+    t32, _ = time_steps(r, wl.cams, o32, max(3, args.steps // 2), 2, flush, stream)
+    st32 = r.get_stats()
+    f32_value = st32.n_used * max(3, args.steps // 2) / (t32 / 1000.0)
+
+    # ---- roofline of the dominant kernel, from the live event record ----
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    mlp_key = "mlp_bf16_tcgen05" if head_prec == roam.ROAM_BF16 else "mlp_f32_simt"
+    shares = {k: {"launches": v[0], "ms": round(v[1], 4), "share": round(v[1] / sum(x[1] for x in prof.values()), 4)}
+              for k, v in prof.items()}
+    dom = max(prof.items(), key=lambda kv: kv[1][1])[0] if prof else mlp_key
+    launches, mlp_ms = prof.get(mlp_key, (0, float("nan")))
+    flops = 2.0 * macs_per_sample(wl.W, wl.H) * evaluated_per_step * args.steps
+    achieved = flops / (mlp_ms / 1000.0) / 1e12
+    if head_prec == roam.ROAM_BF16:
+        peak, bound, src = peaks.get("bf16_tflops", 1900.0), "tensor", "measured bf16 burst" if peaks else "fallback"
+    else:
+        sm_mhz = peaks.get("sm_max_mhz", 2070.0)
+        peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+        bound, src = "alu", "152 SMs x 128 FP32 lanes x 2 FLOP x max SM clock"
+    roofline = {"kernel": mlp_key, "bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "peak_source": src, "traffic": None,
+                "flops_per_sample": 2 * macs_per_sample(wl.W, wl.H), "launches": launches,
+                "dominant_kernel": dom, "kernel_shares": shares}
+
+    # ---- accuracy against the FP64 oracle on sampled pixels ----
+    acc = {}
+    if rank == 0:
+        import oracle as O
+        g = O.Grid(wl.scene, wl.part)
+        rays = oracle_sample_rays(wl, 3000, 7)
+        ref = O.render(g, wl.weights, wl.affine, wl.W, wl.H, wl.sigma_scale, F.camera_array(wl.cams), rays,
+                       wl.delta, wl.n_max)
+        starts = np.concatenate([[0], np.cumsum([c.n_pixels for c in wl.cams])])
+        gi = starts[rays[:, 0].astype(np.int64)] + rays[:, 1].astype(np.int64)
+        for prec, tag in ((head_prec, dtype), (roam.ROAM_F32, "f32")):
+            rgb, _, _ = r.render(wl.cams, roam.render_opts(wl.delta, wl.n_max, precision=prec))
+            torch.cuda.synchronize()
+            e = rgb.cpu().numpy()[gi].astype(np.float64) - ref["rgb"]
+            mse = float((e ** 2).mean())
+            acc[tag] = {"psnr_db": 10 * math.log10(1.0 / mse) if mse > 0 else float("inf"),
+                        "max_abs": float(np.abs(e).max()), "pixels": int(len(gi))}
+
+    # ---- end to end through the C ABI with host buffers ----
+    n_pix = sum(c.n_pixels for c in wl.cams)
+    rgb_h = torch.empty((n_pix, 3), dtype=torch.float32, pin_memory=True).numpy()
+    dep_h = torch.empty(n_pix, dtype=torch.float32, pin_memory=True).numpy()
+    op_h = torch.empty(n_pix, dtype=torch.float32, pin_memory=True).numpy()
+    for _ in range(2):
+        r.render_host(wl.cams, opts, rgb_h, dep_h, op_h)
+    e2e_times = []
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r.render_host(wl.cams, opts, rgb_h, dep_h, op_h)
+        e2e_times.append(time.perf_counter() - t0)
+    e2e_value = world * used_per_step * args.steps / sum(e2e_times)
+    e2e = {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 64 * len(wl.cams),
+           "d2h_bytes_per_step": 20 * n_pix, "ms_per_step": 1000 * sum(e2e_times) / args.steps}
+
+    cpu = None
+    if rank == 0 and world == 1:
+        v, cores, desc = cpu_oracle_rate(wl, args.cpu_seconds)
+        cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": dtype, "data": "synthetic (seeded generators)",
+                "config": workload_config(wl, views),
+                "samples_per_step": {"composited": int(used_per_step), "evaluated": int(evaluated_per_step),
+                                     "rays": int(st.n_rays), "rounds": int(st.n_rounds)},
+                "frame_ms": frame,
+                "fp32_simt": {"value": f32_value, "unit": UNIT, "ms_per_step": t32 / max(3, args.steps // 2)},
+                "accuracy_vs_oracle": acc, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": int(6 * st.n_rounds * args.steps), "clocks": clocks}
+        print(json.dumps(line), flush=True)
+    r.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,254 @@
+/*
+ * roam.h -- C ABI of the GB300 renderer for geometry-aware local radiance
+ * fields (360Roam, arXiv 2208.02705): an occupancy grid whose occupied voxels
+ * are labelled with one of n tiny MLPs, rendered by ray casting with
+ * empty-space skipping, parallel per-field MLP queries and volume rendering
+ * with early termination, plus the training step of the fine-tuning stage.
+ *
+ * Conventions for every entry point:
+ *   - Plain pointers and sizes only.  Arguments documented "device" are
+ *     CUDA device pointers on the context's device; "host" are host pointers.
+ *     The caller owns every buffer it passes; the library owns its own copies
+ *     of the grid, labels and weights, and its workspace, and frees them in
+ *     roam_destroy.
+ *   - `stream` is a cudaStream_t (NULL = the legacy default stream).  Work is
+ *     enqueued asynchronously unless the entry point says it synchronises.
+ *   - Every call validates its arguments and returns a roam_status; it never
+ *     aborts the process.  roam_last_error() gives a message for the calling
+ *     thread's last failure.  Kernels that detect bad data or a timed-out wait
+ *     record it in a device status word; synchronising calls (and
+ *     roam_check()) turn it into ROAM_ERR_DATA / ROAM_ERR_TIMEOUT.
+ *   - A context is bound to one device and must be used by one host thread at
+ *     a time.
+ */
+#ifndef ROAM_H
+#define ROAM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct roam_ctx roam_ctx;
+
+typedef enum {
+    ROAM_OK = 0,
+    ROAM_ERR_ARG = -1,         /* invalid argument (size, pointer, alignment, id) */
+    ROAM_ERR_OOM = -2,         /* device allocation failed */
+    ROAM_ERR_CUDA = -3,        /* a CUDA runtime call failed */
+    ROAM_ERR_STATE = -4,       /* call out of order (e.g. render before load) */
+    ROAM_ERR_TIMEOUT = -5,     /* a device-side wait hit its iteration limit */
+    ROAM_ERR_DATA = -6,        /* inconsistent data found on the device */
+    ROAM_ERR_UNSUPPORTED = -7  /* valid request this build does not provide */
+} roam_status;
+
+enum { ROAM_F32 = 0, ROAM_BF16 = 1 };                 /* MLP arithmetic */
+enum { ROAM_EQUIRECT = 0, ROAM_PERSPECTIVE = 1 };     /* camera models */
+enum { ROAM_SOFTPLUS = 0, ROAM_RELU = 1 };            /* density activation */
+
+/* Occupancy grid geometry.  dims = (Gx, Gy, Gz), Gx a multiple of 32, each
+ * dimension a multiple of 8 and at most 2048.  Voxel (x, y, z) covers
+ * [origin + i*vox, origin + (i+1)*vox) on each axis. */
+typedef struct {
+    int32_t dims[3];
+    float origin[3];
+    float vox;
+} roam_grid_desc;
+
+/* Tiny-MLP architecture shared by all fields (slim-network table of the
+ * paper's appendix, read as: layer 1 (63 -> W), n_hidden - 1 layers W -> W,
+ * head W -> 1 + W (density logit, then W features, no activation on the
+ * features), colour layer (W + 27 -> W, ReLU), output W -> 3 (sigmoid)).
+ * Positional encodings: 63 features of the field-local position (L = 10)
+ * and 27 of the world view direction (L = 4), each [x, sin(2^k pi x),
+ * cos(2^k pi x)], three sines then three cosines per frequency.
+ * density = sigma_scale * softplus(s)  (or ReLU(s) with ROAM_RELU). */
+typedef struct {
+    int32_t width;        /* W: 32, 64 or 128 */
+    int32_t n_hidden;     /* H: 1..4 trunk layers */
+    float sigma_scale;
+    int32_t density_act;  /* ROAM_SOFTPLUS or ROAM_RELU */
+} roam_mlp_desc;
+
+/* Camera (Eq. 2 and Eq. 3 for equirectangular views; pinhole with square
+ * pixels and focal length (width/2)/tan(fov_h/2) for perspective views).
+ * Camera frame: x right, y down, z forward; pixel (u, v) has its centre at
+ * (u + 1/2, v + 1/2); the world ray is o + t * R d_cam, t >= 0. */
+typedef struct {
+    int32_t model;        /* ROAM_EQUIRECT or ROAM_PERSPECTIVE */
+    int32_t width, height;
+    float fov_h;          /* radians, perspective only */
+    float R[9];           /* camera-to-world rotation, row-major */
+    float o[3];           /* camera centre, world units */
+} roam_camera;
+
+/* Sampling and compositing options.  Sample j of a ray sits at
+ * t_j = (j + 1/2) * delta and is kept iff its voxel is occupied (dense
+ * sampling of occupied voxels only); at most n_max kept samples per ray.
+ * Compositing (Eq. 4-5) stops after the first sample whose transmittance
+ * falls below t_stop; the background bg is added with the final
+ * transmittance. */
+typedef struct {
+    float delta;          /* > 0, world units */
+    int32_t n_max;        /* 1..1024 */
+    float t_stop;         /* e.g. 1e-4; 0 disables early termination */
+    float bg[3];
+    int32_t precision;    /* ROAM_F32 (SIMT FP32) or ROAM_BF16 (tcgen05 BF16, FP32 accumulate) */
+    int32_t round_size;   /* kept samples marched per ray per round, 0 = library default */
+} roam_render_opts;
+
+/* Counters of the last render / training forward (read with a sync). */
+typedef struct {
+    int64_t n_rays;
+    int64_t n_samples;    /* kept samples evaluated through the MLPs */
+    int64_t n_used;       /* samples composited (up to each ray's termination) */
+    int32_t n_rounds;
+    int32_t n_fields_hit; /* sum over rounds of fields with at least one sample */
+} roam_stats;
+
+/* Device time of one kind of kernel launch, from CUDA events recorded on the
+ * launching stream around each launch while profiling is on. */
+typedef struct {
+    char name[24];
+    int64_t launches;
+    double total_ms;
+} roam_kernel_time;
+
+/* Adam (Sec. "Training Details and Parameters": beta = (0.9, 0.99), learning
+ * rate decaying exponentially from 1e-3 to 5e-5). */
+typedef struct {
+    float lr;             /* learning rate of this step */
+    float beta1, beta2, eps;
+    int32_t step;         /* 1-based step number, for bias correction */
+} roam_adam_cfg;
+
+/* ---- context --------------------------------------------------------- */
+
+/* Creates a context on CUDA device `device`.  *ctx receives the handle. */
+roam_status roam_create(roam_ctx **ctx, int device);
+/* Frees every allocation of the context; NULL is accepted. */
+roam_status roam_destroy(roam_ctx *ctx);
+/* Message of the calling thread's last failed call ("" if none). */
+const char *roam_last_error(void);
+/* Synchronises the context's last stream and reports any device status. */
+roam_status roam_check(roam_ctx *ctx);
+
+/* ---- scene ----------------------------------------------------------- */
+
+/* Loads the occupancy map O (Alg. 1 stage I output; voxels with occupied
+ * probability above 0.97, Sec. "Progressive Probabilistic Geometry
+ * Estimation").  bits: uint32[Gz][Gy][Gx/32], bit b of word w in a row is
+ * voxel x = 32 w + b.  bits_on_device selects device or host memory.
+ * Builds the per-word rank prefix and an 8^3 brick occupancy map on the
+ * device.  Invalidates loaded fields.  Synchronises. */
+roam_status roam_load_grid(roam_ctx *ctx, const roam_grid_desc *desc, const uint32_t *bits,
+                           int bits_on_device);
+
+/* Loads the voxel-to-field labelling (Alg. 1 stage II output: every occupied
+ * voxel names the tiny MLP that models it, Sec. "Real-time Rendering
+ * Speedup").  field_of_rank[r] (uint16) is the field of the r-th
+ * occupied voxel in linear order (z*Gy + y)*Gx + x; n_occupied must equal the
+ * number of set bits.  affine: float[n_fields][6] = (scale xyz, offset xyz),
+ * the field-local position being scale * p + offset.  Arrays are device
+ * memory iff on_device.  Labels >= n_fields give ROAM_ERR_ARG.  Synchronises. */
+roam_status roam_load_fields(roam_ctx *ctx, int n_fields, const uint16_t *field_of_rank,
+                             int64_t n_occupied, const float *affine, int on_device);
+
+/* Loads per-field MLP weights: float[n_fields][P] in layer order W1, b1,
+ * (Wk, bk) x (H-1), Wh, bh, Wc, bc, Wo, bo, matrices row-major [out][in]
+ * (P = 6,212 for W=32/H=2).  Keeps FP32 masters and builds the BF16 tensor
+ * core images.  Device memory iff on_device.  Synchronises. */
+roam_status roam_load_weights(roam_ctx *ctx, const roam_mlp_desc *desc, const float *weights,
+                              int on_device);
+
+/* Copies the FP32 master weights (same layout as roam_load_weights) to `out`
+ * (device memory iff on_device).  Synchronises. */
+roam_status roam_get_weights(roam_ctx *ctx, float *out, int on_device);
+
+/* ---- rendering (Sec. "Real-time Rendering Speedup", Eq. 2-5) ---------- */
+
+/* Renders n_views cameras (host array).  Pixels of all views are
+ * concatenated in view order, row-major within a view: rgb float[N][3],
+ * depth float[N], opacity float[N] (either may be NULL), N = sum of
+ * width*height.  out_on_device = 1: outputs are device pointers and the call
+ * is asynchronous on `stream`; 0: host pointers, the library copies the
+ * result back and synchronises `stream`. */
+roam_status roam_render(roam_ctx *ctx, const roam_camera *cams, int n_views,
+                        const roam_render_opts *opts, float *rgb, float *depth, float *opacity,
+                        int out_on_device, void *stream);
+
+/* Counters of the last roam_render / roam_train_forward (synchronises). */
+roam_status roam_get_stats(roam_ctx *ctx, roam_stats *stats);
+
+/* Turns per-kernel event timing on (clearing earlier records) or off.  While
+ * on, every kernel launch of roam_render / roam_train_* is bracketed by two
+ * CUDA events on its stream (a small overhead). */
+roam_status roam_profile(roam_ctx *ctx, int enable);
+
+/* Reads the accumulated per-kernel times (synchronises): up to max_entries
+ * entries into out, *n_entries receives the number written. */
+roam_status roam_profile_read(roam_ctx *ctx, roam_kernel_time *out, int max_entries, int *n_entries);
+
+/* ---- the steps of the render path, exposed one by one ----------------- */
+
+/* Ray generation + DDA march + field lookup for n_rays rays (view, pixel)
+ * pairs (device uint32[n_rays][2]; NULL = every pixel of every view in
+ * order).  No compositing, no termination: per ray, the first n_max kept
+ * samples.  count: device uint32[n_rays]; recs: device uint32[n_rays][n_max],
+ * entry = j | field << 16.  Asynchronous. */
+roam_status roam_march(roam_ctx *ctx, const roam_camera *cams, int n_views, const uint32_t *rays,
+                       int64_t n_rays, const roam_render_opts *opts, uint32_t *count,
+                       uint32_t *recs, void *stream);
+
+/* Buckets n samples by field: keys device uint16[n] (field ids < n_fields);
+ * perm device uint32[n] receives the sample indices grouped by field in
+ * increasing field order (order within a field unspecified); offsets device
+ * uint32[n_fields + 1] the group boundaries.  Asynchronous. */
+roam_status roam_bucket(roam_ctx *ctx, const uint16_t *keys, int64_t n, uint32_t *perm,
+                        uint32_t *offsets, void *stream);
+
+/* Positional encoding + per-field MLP at n world points: p, d device
+ * float[n][3] (d the world view direction), field device uint16[n];
+ * out device float[n][4] = (sigma, r, g, b).  precision ROAM_F32 or
+ * ROAM_BF16.  Asynchronous. */
+roam_status roam_mlp_eval(roam_ctx *ctx, const float *p, const float *d, const uint16_t *field,
+                          int64_t n, int precision, float *out, void *stream);
+
+/* Compositing with early termination (Eq. 4-5) of n_rays rays holding
+ * count[r] <= n_max samples: sigma_rgb device float[n_rays][n_max][4]
+ * (sigma, r, g, b), t device float[n_rays][n_max] sample depths; outputs as
+ * roam_render (device), n_used device uint32[n_rays] (may be NULL) = samples
+ * composited before termination.  Uses opts->delta, t_stop, bg.
+ * Asynchronous. */
+roam_status roam_composite(roam_ctx *ctx, int64_t n_rays, int n_max, const uint32_t *count,
+                           const float *sigma_rgb, const float *t, const roam_render_opts *opts,
+                           float *rgb, float *depth, float *opacity, uint32_t *n_used, void *stream);
+
+/* ---- training (Sec. "Adaptive Radiance Fields Slimming and Fine-tuning":
+ *      L2 photometric loss over rendered pixels, dense sampling of occupied
+ *      voxels) ---------------------------------------------------------- */
+
+/* Forward pass of the fine-tuning step for n_rays rays (device
+ * uint32[n_rays][2] of (view, pixel)); rgb device float[n_rays][3].  Keeps
+ * what the backward pass needs inside the context.  Asynchronous. */
+roam_status roam_train_forward(roam_ctx *ctx, const roam_camera *cams, int n_views,
+                               const uint32_t *rays, int64_t n_rays, const roam_render_opts *opts,
+                               float *rgb, void *stream);
+
+/* Backward pass of the last roam_train_forward: dl_drgb device
+ * float[n_rays][3]; grad device float[n_fields][P] receives d(loss)/d(weights)
+ * (overwritten), in the layout of roam_load_weights.  Recomputes the
+ * positional encodings and MLP activations instead of storing them.
+ * Asynchronous. */
+roam_status roam_train_backward(roam_ctx *ctx, const float *dl_drgb, float *grad, void *stream);
+
+/* Adam update of the FP32 master weights with grad (device, layout of
+ * roam_load_weights); refreshes the BF16 images.  Asynchronous. */
+roam_status roam_adam_step(roam_ctx *ctx, const float *grad, const roam_adam_cfg *cfg, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ROAM_H */

@@ -1,0 +1,361 @@
+"""Python binding of the roam C ABI (``include/roam.h``): argument marshalling
+only.  Every step of the render and training path runs in the CUDA kernels
+of ``libroam.so``; PyTorch supplies device memory and streams.
+
+There is no CPU fallback: importing works without a GPU (so that the library
+can be inspected), but creating a context needs the built library and a
+GB300, and every failure raises ``RoamError``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libroam.so")
+
+ROAM_F32, ROAM_BF16 = 0, 1
+ROAM_EQUIRECT, ROAM_PERSPECTIVE = 0, 1
+ROAM_SOFTPLUS, ROAM_RELU = 0, 1
+
+STATUS = {0: "ROAM_OK", -1: "ROAM_ERR_ARG", -2: "ROAM_ERR_OOM", -3: "ROAM_ERR_CUDA", -4: "ROAM_ERR_STATE",
+          -5: "ROAM_ERR_TIMEOUT", -6: "ROAM_ERR_DATA", -7: "ROAM_ERR_UNSUPPORTED"}
+
+# every entry point declared in include/roam.h
+ENTRY_POINTS = ("roam_create", "roam_destroy", "roam_last_error", "roam_check", "roam_load_grid",
+                "roam_load_fields", "roam_load_weights", "roam_get_weights", "roam_render", "roam_get_stats",
+                "roam_march", "roam_bucket", "roam_mlp_eval", "roam_composite", "roam_train_forward",
+                "roam_train_backward", "roam_adam_step", "roam_profile", "roam_profile_read")
+
+
+class RoamError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS.get(status, status)}: {message}")
+        self.status = status
+
+
+class roam_grid_desc(ctypes.Structure):
+    _fields_ = [("dims", ctypes.c_int32 * 3), ("origin", ctypes.c_float * 3), ("vox", ctypes.c_float)]
+
+
+class roam_mlp_desc(ctypes.Structure):
+    _fields_ = [("width", ctypes.c_int32), ("n_hidden", ctypes.c_int32), ("sigma_scale", ctypes.c_float),
+                ("density_act", ctypes.c_int32)]
+
+
+class roam_camera(ctypes.Structure):
+    _fields_ = [("model", ctypes.c_int32), ("width", ctypes.c_int32), ("height", ctypes.c_int32),
+                ("fov_h", ctypes.c_float), ("R", ctypes.c_float * 9), ("o", ctypes.c_float * 3)]
+
+
+class roam_render_opts(ctypes.Structure):
+    _fields_ = [("delta", ctypes.c_float), ("n_max", ctypes.c_int32), ("t_stop", ctypes.c_float),
+                ("bg", ctypes.c_float * 3), ("precision", ctypes.c_int32), ("round_size", ctypes.c_int32)]
+
+
+class roam_stats(ctypes.Structure):
+    _fields_ = [("n_rays", ctypes.c_int64), ("n_samples", ctypes.c_int64), ("n_used", ctypes.c_int64),
+                ("n_rounds", ctypes.c_int32), ("n_fields_hit", ctypes.c_int32)]
+
+
+class roam_kernel_time(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 24), ("launches", ctypes.c_int64), ("total_ms", ctypes.c_double)]
+
+
+class roam_adam_cfg(ctypes.Structure):
+    _fields_ = [("lr", ctypes.c_float), ("beta1", ctypes.c_float), ("beta2", ctypes.c_float),
+                ("eps", ctypes.c_float), ("step", ctypes.c_int32)]
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Loads libroam.so (build it with ``paper_2208_02705_gb300.build``)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RoamError(-7, f"{path} is missing: build the CUDA library first "
+                            "(python -c 'import __graft_entry__ as g; g.build()')")
+    L = ctypes.CDLL(path)
+    vp, i64, i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int
+    P = ctypes.POINTER
+    L.roam_create.argtypes = [P(vp), i32]
+    L.roam_destroy.argtypes = [vp]
+    L.roam_last_error.restype = ctypes.c_char_p
+    L.roam_check.argtypes = [vp]
+    L.roam_load_grid.argtypes = [vp, P(roam_grid_desc), vp, i32]
+    L.roam_load_fields.argtypes = [vp, i32, vp, i64, vp, i32]
+    L.roam_load_weights.argtypes = [vp, P(roam_mlp_desc), vp, i32]
+    L.roam_get_weights.argtypes = [vp, vp, i32]
+    L.roam_render.argtypes = [vp, P(roam_camera), i32, P(roam_render_opts), vp, vp, vp, i32, vp]
+    L.roam_get_stats.argtypes = [vp, P(roam_stats)]
+    L.roam_march.argtypes = [vp, P(roam_camera), i32, vp, i64, P(roam_render_opts), vp, vp, vp]
+    L.roam_bucket.argtypes = [vp, vp, i64, vp, vp, vp]
+    L.roam_mlp_eval.argtypes = [vp, vp, vp, vp, i64, i32, vp, vp]
+    L.roam_composite.argtypes = [vp, i64, i32, vp, vp, vp, P(roam_render_opts), vp, vp, vp, vp, vp]
+    L.roam_train_forward.argtypes = [vp, P(roam_camera), i32, vp, i64, P(roam_render_opts), vp, vp]
+    L.roam_train_backward.argtypes = [vp, vp, vp, vp]
+    L.roam_adam_step.argtypes = [vp, vp, P(roam_adam_cfg), vp]
+    L.roam_profile.argtypes = [vp, i32]
+    L.roam_profile_read.argtypes = [vp, P(roam_kernel_time), i32, P(ctypes.c_int)]
+    for name in ENTRY_POINTS:
+        if name != "roam_last_error":
+            getattr(L, name).restype = ctypes.c_int
+    _lib = L
+    return L
+
+
+def _check(status: int):
+    if status != 0:
+        raise RoamError(status, load_library().roam_last_error().decode())
+
+
+def _ptr(t) -> Optional[int]:
+    if t is None:
+        return None
+    if isinstance(t, np.ndarray):
+        return t.ctypes.data
+    return t.data_ptr()
+
+
+def _stream(stream=None) -> Optional[int]:
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return s.cuda_stream
+
+
+def camera_struct(cam) -> roam_camera:
+    """From any object with model, width, height, fov_h, R (3x3), o (3)."""
+    c = roam_camera()
+    c.model = int(cam.model)
+    c.width = int(cam.width)
+    c.height = int(cam.height)
+    c.fov_h = float(cam.fov_h)
+    R = np.asarray(cam.R, dtype=np.float32).reshape(9)
+    o = np.asarray(cam.o, dtype=np.float32).reshape(3)
+    for i in range(9):
+        c.R[i] = float(R[i])
+    for i in range(3):
+        c.o[i] = float(o[i])
+    return c
+
+
+def camera_array(cams: Sequence) -> ctypes.Array:
+    arr = (roam_camera * len(cams))()
+    for i, c in enumerate(cams):
+        arr[i] = camera_struct(c)
+    return arr
+
+
+def render_opts(delta: float, n_max: int, t_stop: float = 1e-4, bg=(0.0, 0.0, 0.0),
+                precision: int = ROAM_F32, round_size: int = 0) -> roam_render_opts:
+    o = roam_render_opts()
+    o.delta = float(delta)
+    o.n_max = int(n_max)
+    o.t_stop = float(t_stop)
+    for i in range(3):
+        o.bg[i] = float(bg[i])
+    o.precision = int(precision)
+    o.round_size = int(round_size)
+    return o
+
+
+class Roam:
+    """One roam context on one CUDA device.  Methods mirror the C entry
+    points (roam_<name>) and take torch tensors on that device."""
+
+    def __init__(self, device: int = 0):
+        self.L = load_library()
+        self.device = device
+        h = ctypes.c_void_p()
+        _check(self.L.roam_create(ctypes.byref(h), device))
+        self.h = h
+        self.n_pixels = 0
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.L.roam_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _dev(self):
+        import torch
+        return torch.device("cuda", self.device)
+
+    # ---- scene ----
+    def load_grid(self, bits, dims, origin, vox):
+        d = roam_grid_desc()
+        for i in range(3):
+            d.dims[i] = int(dims[i])
+            d.origin[i] = float(origin[i])
+        d.vox = float(vox)
+        on_dev = not isinstance(bits, np.ndarray)
+        if not on_dev:
+            bits = np.ascontiguousarray(bits, dtype=np.uint32)
+        _check(self.L.roam_load_grid(self.h, ctypes.byref(d), _ptr(bits), int(on_dev)))
+
+    def load_fields(self, field_of_rank, affine):
+        on_dev = not isinstance(field_of_rank, np.ndarray)
+        if not on_dev:
+            field_of_rank = np.ascontiguousarray(field_of_rank, dtype=np.uint16)
+            affine = np.ascontiguousarray(affine, dtype=np.float32)
+        n_fields = int(affine.shape[0])
+        _check(self.L.roam_load_fields(self.h, n_fields, _ptr(field_of_rank), int(field_of_rank.shape[0]),
+                                       _ptr(affine), int(on_dev)))
+        self.n_fields = n_fields
+
+    def load_weights(self, weights, W: int, H: int, sigma_scale: float, act: int = ROAM_SOFTPLUS):
+        d = roam_mlp_desc()
+        d.width, d.n_hidden, d.sigma_scale, d.density_act = int(W), int(H), float(sigma_scale), int(act)
+        on_dev = not isinstance(weights, np.ndarray)
+        if not on_dev:
+            weights = np.ascontiguousarray(weights, dtype=np.float32)
+        _check(self.L.roam_load_weights(self.h, ctypes.byref(d), _ptr(weights), int(on_dev)))
+        self.W, self.H = W, H
+        self.P = int(weights.shape[-1])
+
+    def get_weights(self):
+        import torch
+        out = torch.empty((self.n_fields, self.P), dtype=torch.float32, device=self._dev())
+        _check(self.L.roam_get_weights(self.h, _ptr(out), 1))
+        return out
+
+    def load_workload(self, wl):
+        """Loads grid, fields and weights of a fixtures.Workload."""
+        self.load_grid(wl.scene.bits, wl.scene.dims, wl.scene.origin, wl.scene.vox)
+        self.load_fields(wl.part.field_of_rank, wl.affine)
+        self.load_weights(wl.weights, wl.W, wl.H, wl.sigma_scale)
+
+    # ---- rendering ----
+    def render(self, cams, opts: roam_render_opts, rgb=None, depth=None, opacity=None, stream=None):
+        """Device outputs; returns (rgb [N,3], depth [N], opacity [N])."""
+        import torch
+        arr = camera_array(cams)
+        n = sum(int(c.width) * int(c.height) for c in cams)
+        dev = self._dev()
+        rgb = rgb if rgb is not None else torch.empty((n, 3), dtype=torch.float32, device=dev)
+        depth = depth if depth is not None else torch.empty(n, dtype=torch.float32, device=dev)
+        opacity = opacity if opacity is not None else torch.empty(n, dtype=torch.float32, device=dev)
+        _check(self.L.roam_render(self.h, arr, len(cams), ctypes.byref(opts), _ptr(rgb), _ptr(depth),
+                                  _ptr(opacity), 1, _stream(stream)))
+        return rgb, depth, opacity
+
+    def render_host(self, cams, opts: roam_render_opts, rgb: np.ndarray, depth=None, opacity=None, stream=None):
+        """Host outputs (pinned or pageable numpy arrays); synchronises."""
+        arr = camera_array(cams)
+        _check(self.L.roam_render(self.h, arr, len(cams), ctypes.byref(opts), _ptr(rgb), _ptr(depth),
+                                  _ptr(opacity), 0, _stream(stream)))
+        return rgb, depth, opacity
+
+    def render_host_ptrs(self, cams_arr, n_views, opts, rgb_ptr, depth_ptr, op_ptr, stream_handle):
+        _check(self.L.roam_render(self.h, cams_arr, n_views, ctypes.byref(opts), rgb_ptr, depth_ptr, op_ptr, 0,
+                                  stream_handle))
+
+    def get_stats(self) -> roam_stats:
+        s = roam_stats()
+        _check(self.L.roam_get_stats(self.h, ctypes.byref(s)))
+        return s
+
+    def check(self):
+        _check(self.L.roam_check(self.h))
+
+    def profile(self, enable: bool):
+        _check(self.L.roam_profile(self.h, int(bool(enable))))
+
+    def profile_read(self) -> dict:
+        arr = (roam_kernel_time * 16)()
+        n = ctypes.c_int()
+        _check(self.L.roam_profile_read(self.h, arr, 16, ctypes.byref(n)))
+        return {arr[i].name.decode(): (int(arr[i].launches), float(arr[i].total_ms)) for i in range(n.value)}
+
+    # ---- single steps ----
+    def march(self, cams, opts: roam_render_opts, rays=None, stream=None):
+        import torch
+        arr = camera_array(cams)
+        n = int(rays.shape[0]) if rays is not None else sum(int(c.width) * int(c.height) for c in cams)
+        dev = self._dev()
+        count = torch.empty(n, dtype=torch.int32, device=dev)
+        recs = torch.empty((n, opts.n_max), dtype=torch.int32, device=dev)
+        _check(self.L.roam_march(self.h, arr, len(cams), _ptr(rays), n, ctypes.byref(opts), _ptr(count), _ptr(recs),
+                                 _stream(stream)))
+        return count, recs
+
+    def bucket(self, keys, stream=None):
+        import torch
+        n = int(keys.shape[0])
+        perm = torch.empty(n, dtype=torch.int32, device=self._dev())
+        offsets = torch.empty(self.n_fields + 1, dtype=torch.int32, device=self._dev())
+        _check(self.L.roam_bucket(self.h, _ptr(keys), n, _ptr(perm), _ptr(offsets), _stream(stream)))
+        return perm, offsets
+
+    def mlp_eval(self, p, d, field, precision: int = ROAM_F32, stream=None):
+        import torch
+        n = int(p.shape[0])
+        out = torch.empty((n, 4), dtype=torch.float32, device=self._dev())
+        _check(self.L.roam_mlp_eval(self.h, _ptr(p), _ptr(d), _ptr(field), n, int(precision), _ptr(out),
+                                    _stream(stream)))
+        return out
+
+    def composite(self, count, sigma_rgb, t, opts: roam_render_opts, stream=None):
+        import torch
+        n, n_max = int(sigma_rgb.shape[0]), int(sigma_rgb.shape[1])
+        dev = self._dev()
+        rgb = torch.empty((n, 3), dtype=torch.float32, device=dev)
+        depth = torch.empty(n, dtype=torch.float32, device=dev)
+        op = torch.empty(n, dtype=torch.float32, device=dev)
+        used = torch.empty(n, dtype=torch.int32, device=dev)
+        _check(self.L.roam_composite(self.h, n, n_max, _ptr(count), _ptr(sigma_rgb), _ptr(t), ctypes.byref(opts),
+                                     _ptr(rgb), _ptr(depth), _ptr(op), _ptr(used), _stream(stream)))
+        return rgb, depth, op, used
+
+    # ---- training ----
+    def train_forward(self, cams, rays, opts: roam_render_opts, rgb=None, stream=None):
+        import torch
+        arr = camera_array(cams)
+        n = int(rays.shape[0])
+        rgb = rgb if rgb is not None else torch.empty((n, 3), dtype=torch.float32, device=self._dev())
+        _check(self.L.roam_train_forward(self.h, arr, len(cams), _ptr(rays), n, ctypes.byref(opts), _ptr(rgb),
+                                         _stream(stream)))
+        return rgb
+
+    def train_backward(self, dl_drgb, grad=None, stream=None):
+        import torch
+        grad = grad if grad is not None else torch.empty((self.n_fields, self.P), dtype=torch.float32,
+                                                         device=self._dev())
+        _check(self.L.roam_train_backward(self.h, _ptr(dl_drgb), _ptr(grad), _stream(stream)))
+        return grad
+
+    def adam_step(self, grad, lr: float, step: int, beta1: float = 0.9, beta2: float = 0.99, eps: float = 1e-8,
+                  stream=None):
+        c = roam_adam_cfg()
+        c.lr, c.beta1, c.beta2, c.eps, c.step = float(lr), float(beta1), float(beta2), float(eps), int(step)
+        _check(self.L.roam_adam_step(self.h, _ptr(grad), ctypes.byref(c), _stream(stream)))
+
+
+def render_function():
+    """torch.autograd.Function over the training forward/backward entry points."""
+    import torch
+
+    class RoamRender(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx_, dummy_weights, roam: Roam, cams, rays, opts):
+            rgb = roam.train_forward(cams, rays, opts)
+            ctx_.roam = roam
+            return rgb
+
+        @staticmethod
+        def backward(ctx_, grad_rgb):
+            grad = ctx_.roam.train_backward(grad_rgb.contiguous())
+            return grad, None, None, None, None
+
+    return RoamRender

@@ -1,0 +1,163 @@
+// Internal declarations of the roam CUDA library (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+
+#include "roam.h"
+
+namespace roam {
+
+constexpr int kPeX = 63;          // 3 + 2*3*10 position features
+constexpr int kPeD = 27;          // 3 + 2*3*4 direction features
+constexpr int kBrickShift = 3;    // 8^3-voxel bricks for empty-space skipping
+constexpr int kMaxViews = 256;
+
+// device status word bits
+constexpr uint32_t kStatusBadLabel = 1u;
+constexpr uint32_t kStatusTimeout = 2u;
+constexpr uint32_t kStatusBadSample = 4u;
+
+// Camera as the kernels use it.
+struct DevCamera {
+    int model, width, height, pad;
+    float R[9];
+    float o[3];
+    float inv_f;          // perspective: 1 / focal length in pixels
+    uint32_t pix_start;   // first global pixel index of this view
+    uint32_t pad2[2];
+};
+
+struct GridDev {
+    int gx, gy, gz, wpr;          // wpr = gx / 32
+    int bx, by, bz, bwpr;         // brick grid, bwpr = ceil(bx / 32)
+    float origin[3];
+    float vox, inv_vox;
+    const uint32_t *bits;         // [gz][gy][wpr]
+    const uint32_t *prefix;       // exclusive popcount before each word
+    const uint32_t *brick;        // [bz][by][bwpr] non-empty brick bits
+    const uint16_t *labels;       // field of each occupied voxel, rank order
+    int n_fields;
+};
+
+// Device counters of one render / training pass.
+struct Counters {
+    uint32_t live_count[2];
+    uint32_t n_tiles;
+    uint32_t status;
+    unsigned long long n_samples;   // samples evaluated through the MLPs
+    unsigned long long n_used;      // samples composited (up to termination)
+    uint32_t fields_hit;
+    uint32_t pad;
+};
+
+// Ray state, structure of arrays, indexed by ray id.
+struct RayState {
+    float4 *orig;       // o (xyz), w unused
+    float4 *dir;        // d (xyz), w unused
+    uint32_t *j_next;   // next sample index to test
+    uint32_t *j_end;    // first sample index past the grid
+    uint32_t *n_kept;   // kept samples so far
+    float4 *acc;        // (r, g, b, depth) accumulated
+    float2 *tw;         // (transmittance, sum of weights)
+};
+
+// Slot of the k-th sample of live ray i in a round of R samples per ray:
+// 32 consecutive rays share a 32-wide column so that per-k accesses coalesce.
+__host__ __device__ inline uint32_t slot_of(uint32_t i, uint32_t k, uint32_t R)
+{
+    return ((i >> 5) * R + k) * 32u + (i & 31u);
+}
+
+struct MarchParams {
+    const DevCamera *cams;
+    int n_views;
+    const uint32_t *rays;       // (view, pixel) pairs or nullptr (all pixels)
+    uint32_t n_rays;
+    const uint32_t *live;       // live ray ids or nullptr (round 0: identity)
+    const uint32_t *live_count; // device count or nullptr (n_rays)
+    int R;                      // samples per ray this round (flat: row length)
+    int n_max;
+    float delta;
+    int init;                   // compute rays and reset state
+    int flat;                   // recs laid out [n_rays][R] instead of slots
+    RayState st;
+    uint32_t *cnt;              // per live index: samples emitted
+    uint32_t *recs;             // j | field << 16
+    Counters *ctr;
+};
+
+// Sample source of the MLP kernels.
+struct SampleSrc {
+    int mode;                   // 0: render slots, 1: direct points
+    // render slots
+    const uint32_t *recs;
+    const uint32_t *live;
+    const uint32_t *live_count;
+    int R;
+    RayState st;
+    float delta;
+    // direct points
+    const float *p;             // [n][3]
+    const float *d;             // [n][3]
+};
+
+struct Tile {
+    uint32_t field, start, count, pad;
+};
+
+struct BucketBufs {
+    uint32_t *hist;       // [F]
+    uint32_t *offsets;    // [F + 1]
+    uint32_t *cursor;     // [F]
+    Tile *tiles;          // [max tiles]
+    uint32_t *sorted;     // [max samples]
+};
+
+struct MlpWeights {
+    int W, H, act, n_fields;
+    int64_t P;                 // parameters per field (API layout)
+    float sigma_scale;
+    const float *w32;          // FP32 masters [F][P]
+    const float *wt;           // FP32 transposed/padded copy for SIMT [F][Pt]
+    int64_t Pt;
+    const void *wimg;          // BF16 tensor-core images [F][img_bytes]
+    int64_t img_bytes;
+    const float *bias;         // FP32 biases for the TC epilogue [F][nb]
+    int nb;
+    const float *affine;       // [F][6]
+};
+
+// ---- kernels launched from the API layer -------------------------------
+
+void launch_grid_prefix(const uint32_t *bits, uint32_t *prefix, uint32_t *block_sums,
+                        int64_t n_words, cudaStream_t s);
+void launch_brick_map(GridDev g, uint32_t *brick, cudaStream_t s);
+void launch_march(const GridDev &g, const MarchParams &p, int grid, cudaStream_t s);
+void launch_bucket(const uint32_t *cnt, const uint32_t *recs, const uint32_t *live_count,
+                   uint32_t n_fixed, int R, int flat_keys16, const uint16_t *keys16,
+                   int n_fields, int tile, const BucketBufs &b, Counters *ctr, int grid,
+                   cudaStream_t s);
+void launch_mlp_simt(const MlpWeights &w, const SampleSrc &src, const BucketBufs &b,
+                     Counters *ctr, float4 *out, int grid, cudaStream_t s);
+void launch_pack_simt(const float *w32, int n_fields, int W, int H, int64_t P, float *wt,
+                      int64_t Pt, cudaStream_t s);
+int64_t simt_transposed_size(int W, int H);
+void launch_composite_round(const MarchParams &mp, const float4 *sr, uint32_t *next_live,
+                            uint32_t *next_count, float t_stop, const float *bg, float *rgb,
+                            float *depth, float *opacity, int grid, cudaStream_t s);
+void launch_composite_flat(int64_t n_rays, int n_max, const uint32_t *count, const float4 *sr,
+                           const float *t, float delta, float t_stop, const float *bg, float *rgb,
+                           float *depth, float *opacity, uint32_t *n_used, cudaStream_t s);
+
+// tcgen05 BF16 path
+bool tc_supported(int W, int H);
+int64_t tc_image_bytes(int W, int H);
+int tc_bias_count(int W, int H);
+int tc_tile_samples();
+void launch_pack_tc(const float *w32, int n_fields, int W, int H, int64_t P, void *wimg,
+                    int64_t img_bytes, float *bias, int nb, cudaStream_t s);
+void launch_mlp_tc(const MlpWeights &w, const SampleSrc &src, const BucketBufs &b, Counters *ctr,
+                   float4 *out, int grid, cudaStream_t s);
+
+}  // namespace roam

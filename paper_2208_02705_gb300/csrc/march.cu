@@ -1,0 +1,301 @@
+// Ray generation, empty-space skipping march over the bit-packed occupancy
+// grid and field lookup (Sec. "Real-time Rendering Speedup": rays are cast
+// through a GPU-resident voxel structure to find occupied voxels, one ray
+// per thread, each occupied voxel carrying the id of its tiny MLP), plus the
+// load-time kernels that build the rank prefix and the brick occupancy map.
+#include "internal.cuh"
+
+namespace roam {
+
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+// Exclusive scan of one value per thread over a block of 1024 threads.
+__device__ uint32_t block_exclusive_scan(uint32_t v, uint32_t *total)
+{
+    __shared__ uint32_t warp_sums[32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    uint32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(kFull, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_sums[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+        uint32_t s = lane < (int)(blockDim.x >> 5) ? warp_sums[lane] : 0u;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(kFull, s, o);
+            if (lane >= o) s += y;
+        }
+        warp_sums[lane] = s;
+    }
+    __syncthreads();
+    uint32_t excl = x - v + (wid > 0 ? warp_sums[wid - 1] : 0u);
+    *total = warp_sums[(blockDim.x >> 5) - 1];
+    __syncthreads();
+    return excl;
+}
+
+// prefix[w] = popcount of all words before w, in blocks of 4096 words
+__global__ void k_prefix_local(const uint32_t *__restrict__ bits, uint32_t *__restrict__ prefix,
+                               uint32_t *__restrict__ block_sums, int64_t n_words)
+{
+    const int64_t base = (int64_t)blockIdx.x * 4096 + threadIdx.x * 4;
+    uint32_t c[4], s = 0;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        c[q] = base + q < n_words ? (uint32_t)__popc(bits[base + q]) : 0u;
+        s += c[q];
+    }
+    uint32_t tot;
+    uint32_t e = block_exclusive_scan(s, &tot);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        if (base + q < n_words) prefix[base + q] = e;
+        e += c[q];
+    }
+    if (threadIdx.x == 0) block_sums[blockIdx.x] = tot;
+}
+
+__global__ void k_prefix_blocks(uint32_t *block_sums, int64_t n_blocks)
+{
+    uint32_t carry = 0;
+    for (int64_t b0 = 0; b0 < n_blocks; b0 += blockDim.x) {
+        int64_t b = b0 + threadIdx.x;
+        uint32_t v = b < n_blocks ? block_sums[b] : 0u;
+        uint32_t tot;
+        uint32_t e = block_exclusive_scan(v, &tot);
+        if (b < n_blocks) block_sums[b] = e + carry;
+        carry += tot;
+    }
+}
+
+__global__ void k_prefix_add(uint32_t *prefix, const uint32_t *block_sums, int64_t n_words)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n_words) prefix[i] += block_sums[i / 4096];
+}
+
+// one thread per 8^3 brick: OR of its 512 voxel bits
+__global__ void k_brick_map(GridDev g, uint32_t *brick)
+{
+    const int64_t n = (int64_t)g.bx * g.by * g.bz;
+    for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < n; b += (int64_t)gridDim.x * blockDim.x) {
+        const int bx = (int)(b % g.bx), by = (int)((b / g.bx) % g.by), bz = (int)(b / ((int64_t)g.bx * g.by));
+        const int x0 = bx << kBrickShift;
+        uint32_t any = 0;
+        for (int z = bz * 8; z < bz * 8 + 8; ++z)
+            for (int y = by * 8; y < by * 8 + 8; ++y) {
+                const uint32_t w = g.bits[((int64_t)z * g.gy + y) * g.wpr + (x0 >> 5)];
+                any |= (w >> (x0 & 31)) & 0xffu;
+            }
+        if (any) atomicOr(&brick[((int64_t)bz * g.by + by) * g.bwpr + (bx >> 5)], 1u << (bx & 31));
+    }
+}
+
+// Pixel -> world ray.  Equirectangular: Eq. 2 gives longitude
+// phi = 2 pi ((u + 1/2)/W - 1/2) and latitude theta = pi (1/2 - (v + 1/2)/H);
+// Eq. 3 gives the camera-frame direction (cos t sin p, -sin t, cos t cos p).
+// Perspective: pinhole, d_cam = normalise((u + 1/2 - W/2)/f, (v + 1/2 - H/2)/f, 1).
+__device__ __forceinline__ void make_ray(const DevCamera &c, uint32_t pix, float3 &o, float3 &d)
+{
+    const uint32_t u = pix % (uint32_t)c.width, v = pix / (uint32_t)c.width;
+    float d0, d1, d2;
+    if (c.model == ROAM_EQUIRECT) {
+        const float pu = 2.0f * (((float)u + 0.5f) / (float)c.width) - 1.0f;   // phi / pi
+        const float tv = 0.5f - ((float)v + 0.5f) / (float)c.height;            // theta / pi
+        float sp, cp, st, ct;
+        sincospif(pu, &sp, &cp);
+        sincospif(tv, &st, &ct);
+        d0 = ct * sp;
+        d1 = -st;
+        d2 = ct * cp;
+    } else {
+        const float x = ((float)u + 0.5f - 0.5f * (float)c.width) * c.inv_f;
+        const float y = ((float)v + 0.5f - 0.5f * (float)c.height) * c.inv_f;
+        const float n = 1.0f / sqrtf(x * x + y * y + 1.0f);
+        d0 = x * n;
+        d1 = y * n;
+        d2 = n;
+    }
+    d.x = c.R[0] * d0 + c.R[1] * d1 + c.R[2] * d2;
+    d.y = c.R[3] * d0 + c.R[4] * d1 + c.R[5] * d2;
+    d.z = c.R[6] * d0 + c.R[7] * d1 + c.R[8] * d2;
+    o = make_float3(c.o[0], c.o[1], c.o[2]);
+}
+
+__device__ __forceinline__ int view_of(const DevCamera *cams, int n_views, uint32_t gpix)
+{
+    int lo = 0, hi = n_views - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (cams[mid].pix_start <= gpix) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Sample j of a ray sits at t_j = (j + 1/2) delta and is kept iff its voxel
+// floor((o + t_j d - origin) / vox) is inside the grid and occupied.  The
+// walk tests samples one by one inside non-empty 8^3 bricks and jumps over
+// empty bricks to the first sample past the brick's exit (minus one, so that
+// a sample rounded onto the exit face is still tested).
+__global__ void __launch_bounds__(256) k_march(GridDev g, MarchParams p)
+{
+    if (blockIdx.x == 0 && threadIdx.x == 0 && p.live_count != nullptr) {
+        // the count slot the composite of this round fills is the one the
+        // previous round read: clear it for reuse
+        uint32_t *other = (p.live_count == &p.ctr->live_count[0]) ? &p.ctr->live_count[1] : &p.ctr->live_count[0];
+        *other = 0u;
+    } else if (blockIdx.x == 0 && threadIdx.x == 0 && p.init && !p.flat) {
+        p.ctr->live_count[1] = 0u;
+    }
+    const uint32_t n_live = p.live_count ? *p.live_count : p.n_rays;
+    const uint32_t stride = gridDim.x * blockDim.x;
+    const float delta = p.delta;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n_live; i += stride) {
+        const uint32_t ray = p.live ? p.live[i] : i;
+        float3 o, d;
+        uint32_t jn, je, nk;
+        if (p.init) {
+            uint32_t view, pix;
+            if (p.rays) {
+                view = p.rays[2 * ray];
+                pix = p.rays[2 * ray + 1];
+                if (view >= (uint32_t)p.n_views ||
+                    pix >= (uint32_t)p.cams[view].width * (uint32_t)p.cams[view].height) {
+                    atomicOr(&p.ctr->status, kStatusBadSample);
+                    p.cnt[i] = 0;
+                    p.st.j_next[ray] = 0;
+                    p.st.j_end[ray] = 0;
+                    p.st.n_kept[ray] = 0;
+                    p.st.acc[ray] = make_float4(0.f, 0.f, 0.f, 0.f);
+                    p.st.tw[ray] = make_float2(1.f, 0.f);
+                    p.st.orig[ray] = make_float4(0.f, 0.f, 0.f, 0.f);
+                    p.st.dir[ray] = make_float4(0.f, 0.f, 1.f, 0.f);
+                    continue;
+                }
+            } else {
+                view = (uint32_t)view_of(p.cams, p.n_views, ray);
+                pix = ray - p.cams[view].pix_start;
+            }
+            make_ray(p.cams[view], pix, o, d);
+            p.st.orig[ray] = make_float4(o.x, o.y, o.z, 0.f);
+            p.st.dir[ray] = make_float4(d.x, d.y, d.z, 0.f);
+            // clip against the grid box in voxel units
+            const float og[3] = {(o.x - g.origin[0]) * g.inv_vox, (o.y - g.origin[1]) * g.inv_vox,
+                                 (o.z - g.origin[2]) * g.inv_vox};
+            const float dg[3] = {d.x * g.inv_vox, d.y * g.inv_vox, d.z * g.inv_vox};
+            const float ext[3] = {(float)g.gx, (float)g.gy, (float)g.gz};
+            float t0 = 0.f, t1 = 3.0e38f;
+            bool miss = false;
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                if (dg[a] == 0.f) {
+                    if (og[a] < 0.f || og[a] >= ext[a]) miss = true;
+                } else {
+                    float ta = (0.f - og[a]) / dg[a], tb = (ext[a] - og[a]) / dg[a];
+                    if (ta > tb) { const float s = ta; ta = tb; tb = s; }
+                    t0 = fmaxf(t0, ta);
+                    t1 = fminf(t1, tb);
+                }
+            }
+            if (miss || t1 < t0) {
+                jn = je = 0;
+            } else {
+                const float js = floorf(t0 / delta - 0.5f) - 1.0f;
+                jn = js > 0.f ? (uint32_t)js : 0u;
+                je = (uint32_t)fmaxf(ceilf(t1 / delta - 0.5f) + 2.0f, 0.f);
+            }
+            nk = 0;
+            p.st.j_end[ray] = je;
+            p.st.acc[ray] = make_float4(0.f, 0.f, 0.f, 0.f);
+            p.st.tw[ray] = make_float2(1.f, 0.f);
+        } else {
+            const float4 o4 = p.st.orig[ray], d4 = p.st.dir[ray];
+            o = make_float3(o4.x, o4.y, o4.z);
+            d = make_float3(d4.x, d4.y, d4.z);
+            jn = p.st.j_next[ray];
+            je = p.st.j_end[ray];
+            nk = p.st.n_kept[ray];
+        }
+        const float ogx = (o.x - g.origin[0]) * g.inv_vox, ogy = (o.y - g.origin[1]) * g.inv_vox,
+                    ogz = (o.z - g.origin[2]) * g.inv_vox;
+        const float dgx = d.x * g.inv_vox, dgy = d.y * g.inv_vox, dgz = d.z * g.inv_vox;
+        const float idx = 1.0f / dgx, idy = 1.0f / dgy, idz = 1.0f / dgz;
+        uint32_t em = 0;
+        const uint32_t R = (uint32_t)p.R, n_max = (uint32_t)p.n_max;
+        while (jn < je && em < R && nk < n_max) {
+            const float t = ((float)jn + 0.5f) * delta;
+            const float gxf = fmaf(t, dgx, ogx), gyf = fmaf(t, dgy, ogy), gzf = fmaf(t, dgz, ogz);
+            const int ix = __float2int_rd(gxf), iy = __float2int_rd(gyf), iz = __float2int_rd(gzf);
+            if ((unsigned)ix >= (unsigned)g.gx || (unsigned)iy >= (unsigned)g.gy || (unsigned)iz >= (unsigned)g.gz) {
+                ++jn;
+                continue;
+            }
+            const int bxi = ix >> kBrickShift, byi = iy >> kBrickShift, bzi = iz >> kBrickShift;
+            const uint32_t bw = __ldg(&g.brick[((int64_t)bzi * g.by + byi) * g.bwpr + (bxi >> 5)]);
+            if (!((bw >> (bxi & 31)) & 1u)) {
+                // exit of the empty brick along the ray (voxel units)
+                const float ex = dgx > 0.f ? (float)((bxi + 1) << kBrickShift) : (float)(bxi << kBrickShift);
+                const float ey = dgy > 0.f ? (float)((byi + 1) << kBrickShift) : (float)(byi << kBrickShift);
+                const float ez = dgz > 0.f ? (float)((bzi + 1) << kBrickShift) : (float)(bzi << kBrickShift);
+                float te = 3.0e38f;
+                if (dgx != 0.f) te = fminf(te, (ex - ogx) * idx);
+                if (dgy != 0.f) te = fminf(te, (ey - ogy) * idy);
+                if (dgz != 0.f) te = fminf(te, (ez - ogz) * idz);
+                const float jf = ceilf(te / delta - 0.5f) - 1.0f;
+                const uint32_t jj = jf > (float)je ? je : (jf > 0.f ? (uint32_t)jf : 0u);
+                jn = jj > jn + 1 ? jj : jn + 1;
+                continue;
+            }
+            const int64_t wi = ((int64_t)iz * g.gy + iy) * g.wpr + (ix >> 5);
+            const uint32_t w = __ldg(&g.bits[wi]);
+            const uint32_t b = (uint32_t)(ix & 31);
+            if ((w >> b) & 1u) {
+                const uint32_t rank = __ldg(&g.prefix[wi]) + (uint32_t)__popc(w & ((1u << b) - 1u));
+                uint32_t f = __ldg(&g.labels[rank]);
+                if (f >= (uint32_t)g.n_fields) {
+                    atomicOr(&p.ctr->status, kStatusBadLabel);
+                    f = 0;
+                }
+                const uint32_t s = p.flat ? i * R + em : slot_of(i, em, R);
+                p.recs[s] = jn | (f << 16);
+                ++em;
+                ++nk;
+            }
+            ++jn;
+        }
+        p.cnt[i] = em;
+        p.st.j_next[ray] = jn;
+        p.st.n_kept[ray] = nk;
+    }
+}
+
+}  // namespace
+
+void launch_grid_prefix(const uint32_t *bits, uint32_t *prefix, uint32_t *block_sums, int64_t n_words,
+                        cudaStream_t s)
+{
+    const int64_t nb = (n_words + 4095) / 4096;
+    k_prefix_local<<<(unsigned)nb, 1024, 0, s>>>(bits, prefix, block_sums, n_words);
+    k_prefix_blocks<<<1, 1024, 0, s>>>(block_sums, nb);
+    k_prefix_add<<<(unsigned)((n_words + 255) / 256), 256, 0, s>>>(prefix, block_sums, n_words);
+}
+
+void launch_brick_map(GridDev g, uint32_t *brick, cudaStream_t s)
+{
+    const int64_t n = (int64_t)g.bx * g.by * g.bz;
+    const int blocks = (int)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096);
+    k_brick_map<<<blocks, 256, 0, s>>>(g, brick);
+}
+
+void launch_march(const GridDev &g, const MarchParams &p, int grid, cudaStream_t s)
+{
+    k_march<<<grid, 256, 0, s>>>(g, p);
+}
+
+}  // namespace roam

@@ -1,0 +1,856 @@
+// C ABI of the roam library: argument validation, device memory of the
+// context, and the order of kernel launches for each entry point.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "internal.cuh"
+
+using namespace roam;
+
+namespace {
+
+thread_local char g_err[512] = "";
+
+roam_status fail(roam_status st, const char *fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+    return st;
+}
+
+#define ROAM_CUDA(x)                                                                         \
+    do {                                                                                     \
+        cudaError_t e_ = (x);                                                                \
+        if (e_ != cudaSuccess) return fail(ROAM_ERR_CUDA, "%s: %s", #x, cudaGetErrorString(e_)); \
+    } while (0)
+
+#define ROAM_TRY(x)                          \
+    do {                                     \
+        roam_status s_ = (x);                \
+        if (s_ != ROAM_OK) return s_;        \
+    } while (0)
+
+template <class T>
+struct DBuf {
+    T *p = nullptr;
+    size_t n = 0;
+};
+
+template <class T>
+roam_status ensure(DBuf<T> &b, size_t n)
+{
+    if (n == 0) n = 1;
+    if (b.p && b.n >= n) return ROAM_OK;
+    if (b.p) cudaFree(b.p);
+    b.p = nullptr;
+    b.n = 0;
+    if (cudaMalloc(&b.p, n * sizeof(T)) != cudaSuccess) {
+        cudaGetLastError();
+        b.p = nullptr;
+        return fail(ROAM_ERR_OOM, "device allocation of %zu bytes failed", n * sizeof(T));
+    }
+    b.n = n;
+    return ROAM_OK;
+}
+
+template <class T>
+void release(DBuf<T> &b)
+{
+    if (b.p) cudaFree(b.p);
+    b.p = nullptr;
+    b.n = 0;
+}
+
+bool finite(float x) { return std::isfinite(x); }
+
+__global__ void k_check_finite(const float *w, int64_t n, uint32_t *bad)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        if (!isfinite(w[i])) { atomicOr(bad, 1u); return; }
+}
+
+__global__ void k_check_labels(const uint16_t *lab, int64_t n, int n_fields, uint32_t *bad)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        if (lab[i] >= n_fields) { atomicOr(bad, 1u); return; }
+}
+
+int64_t param_count(int W, int H)
+{
+    return (int64_t)W * kPeX + W + (int64_t)(H - 1) * ((int64_t)W * W + W) + (int64_t)(1 + W) * W + (1 + W) +
+           (int64_t)W * (W + kPeD) + W + 3 * (int64_t)W + 3;
+}
+
+}  // namespace
+
+struct roam_ctx {
+    int device = 0, n_sm = 0;
+    // occupancy grid
+    bool has_grid = false;
+    roam_grid_desc gd{};
+    GridDev g{};
+    int64_t n_words = 0, n_occ = 0;
+    DBuf<uint32_t> bits, prefix, brick, block_sums;
+    // fields
+    bool has_fields = false;
+    int n_fields = 0;
+    DBuf<uint16_t> labels;
+    DBuf<float> affine;
+    // weights
+    bool has_weights = false;
+    roam_mlp_desc md{};
+    int64_t P = 0, Pt = 0, img_bytes = 0;
+    int nb = 0;
+    bool tc_ok = false;
+    DBuf<float> w32, wt, bias, adam_m, adam_v;
+    DBuf<uint8_t> wimg;
+    // per-call workspace
+    DBuf<float4> orig, dir, acc, sr;
+    DBuf<float2> tw;
+    DBuf<uint32_t> j_next, j_end, n_kept, live0, live1, cnt, recs, sorted, hist, offsets, cursor, scratch_u32;
+    DBuf<Tile> tiles;
+    DBuf<float> o_rgb, o_depth, o_op;
+    DBuf<DevCamera> cams;
+    DevCamera *h_cams = nullptr;
+    cudaEvent_t cam_ev = nullptr;
+    bool cam_pending = false;
+    Counters *ctr = nullptr;
+    Counters *h_ctr = nullptr;
+    uint32_t *d_flag = nullptr;
+    cudaStream_t last = nullptr;
+    int n_views = 0;
+    int64_t last_rays = 0;
+    int last_rounds = 0;
+    // per-kernel event timing
+    bool prof = false;
+    std::vector<cudaEvent_t> ev_pool;
+    std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> prof_pending;
+    std::vector<std::pair<int64_t, double>> prof_acc;
+    // training
+    int64_t train_rays = 0;
+    int train_R = 0;
+};
+
+namespace {
+
+const char *const kProfNames[] = {"march", "bucket", "mlp_f32_simt", "mlp_bf16_tcgen05", "composite",
+                                  "composite_bwd", "mlp_bwd", "adam"};
+constexpr int kProfKinds = 8;
+enum { P_MARCH, P_BUCKET, P_MLP_F32, P_MLP_BF16, P_COMPOSITE, P_COMPOSITE_BWD, P_MLP_BWD, P_ADAM };
+
+cudaEvent_t pool_event(roam_ctx *c)
+{
+    if (!c->ev_pool.empty()) {
+        cudaEvent_t e = c->ev_pool.back();
+        c->ev_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+// Brackets one launch with events when profiling is on.
+struct ProfScope {
+    roam_ctx *c;
+    int kind;
+    cudaStream_t s;
+    cudaEvent_t a = nullptr;
+    ProfScope(roam_ctx *c_, int kind_, cudaStream_t s_) : c(c_), kind(kind_), s(s_)
+    {
+        if (c->prof) {
+            a = pool_event(c);
+            cudaEventRecord(a, s);
+        }
+    }
+    ~ProfScope()
+    {
+        if (a) {
+            cudaEvent_t b = pool_event(c);
+            cudaEventRecord(b, s);
+            c->prof_pending.push_back({kind, {a, b}});
+        }
+    }
+};
+
+roam_status set_dev(roam_ctx *c)
+{
+    if (!c) return fail(ROAM_ERR_ARG, "null context");
+    ROAM_CUDA(cudaSetDevice(c->device));
+    return ROAM_OK;
+}
+
+roam_status launched(const char *what)
+{
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(ROAM_ERR_CUDA, "launch of %s failed: %s", what, cudaGetErrorString(e));
+    return ROAM_OK;
+}
+
+roam_status status_of(uint32_t st)
+{
+    if (st & kStatusTimeout) return fail(ROAM_ERR_TIMEOUT, "a device-side wait hit its iteration limit");
+    if (st & (kStatusBadLabel | kStatusBadSample)) return fail(ROAM_ERR_DATA, "device found an invalid field id or sample");
+    return ROAM_OK;
+}
+
+int grid_blocks(const roam_ctx *c, int per_sm) { return c->n_sm * per_sm; }
+
+MlpWeights weights_of(const roam_ctx *c)
+{
+    MlpWeights w{};
+    w.W = c->md.width;
+    w.H = c->md.n_hidden;
+    w.act = c->md.density_act;
+    w.n_fields = c->n_fields;
+    w.P = c->P;
+    w.sigma_scale = c->md.sigma_scale;
+    w.w32 = c->w32.p;
+    w.wt = c->wt.p;
+    w.Pt = c->Pt;
+    w.wimg = c->wimg.p;
+    w.img_bytes = c->img_bytes;
+    w.bias = c->bias.p;
+    w.nb = c->nb;
+    w.affine = c->affine.p;
+    return w;
+}
+
+roam_status check_ready(const roam_ctx *c)
+{
+    if (!c->has_grid) return fail(ROAM_ERR_STATE, "no occupancy grid loaded");
+    if (!c->has_fields) return fail(ROAM_ERR_STATE, "no field labels loaded");
+    if (!c->has_weights) return fail(ROAM_ERR_STATE, "no weights loaded");
+    return ROAM_OK;
+}
+
+roam_status check_opts(const roam_ctx *c, const roam_render_opts *o)
+{
+    if (!o) return fail(ROAM_ERR_ARG, "null render options");
+    if (!(o->delta > 0.f) || !finite(o->delta)) return fail(ROAM_ERR_ARG, "delta must be positive");
+    if (o->n_max < 1 || o->n_max > 1024) return fail(ROAM_ERR_ARG, "n_max must be in [1, 1024]");
+    if (!(o->t_stop >= 0.f && o->t_stop < 1.f)) return fail(ROAM_ERR_ARG, "t_stop must be in [0, 1)");
+    for (int i = 0; i < 3; ++i)
+        if (!finite(o->bg[i])) return fail(ROAM_ERR_ARG, "background must be finite");
+    if (o->precision != ROAM_F32 && o->precision != ROAM_BF16) return fail(ROAM_ERR_ARG, "unknown precision");
+    if (o->precision == ROAM_BF16 && !c->tc_ok)
+        return fail(ROAM_ERR_UNSUPPORTED, "BF16 tensor-core path not available for W=%d H=%d", c->md.width, c->md.n_hidden);
+    if (o->round_size < 0) return fail(ROAM_ERR_ARG, "round_size must be >= 0");
+    return ROAM_OK;
+}
+
+// Validates the cameras and copies them to the device; *n_pix = all pixels.
+roam_status upload_cams(roam_ctx *c, const roam_camera *cams, int n_views, float delta, int64_t *n_pix,
+                        cudaStream_t s)
+{
+    if (!cams) return fail(ROAM_ERR_ARG, "null cameras");
+    if (n_views < 1 || n_views > kMaxViews) return fail(ROAM_ERR_ARG, "n_views must be in [1, %d]", kMaxViews);
+    if (c->cam_pending) {
+        cudaEventSynchronize(c->cam_ev);
+        c->cam_pending = false;
+    }
+    int64_t total = 0;
+    const float ext[3] = {c->gd.dims[0] * c->gd.vox, c->gd.dims[1] * c->gd.vox, c->gd.dims[2] * c->gd.vox};
+    for (int v = 0; v < n_views; ++v) {
+        const roam_camera &k = cams[v];
+        if (k.model != ROAM_EQUIRECT && k.model != ROAM_PERSPECTIVE) return fail(ROAM_ERR_ARG, "camera %d: bad model", v);
+        if (k.width < 1 || k.height < 1 || k.width > 65536 || k.height > 65536)
+            return fail(ROAM_ERR_ARG, "camera %d: bad size", v);
+        if (k.model == ROAM_PERSPECTIVE && !(k.fov_h > 0.f && k.fov_h < 3.1f))
+            return fail(ROAM_ERR_ARG, "camera %d: fov must be in (0, 3.1) rad", v);
+        for (int i = 0; i < 9; ++i)
+            if (!finite(k.R[i])) return fail(ROAM_ERR_ARG, "camera %d: non-finite rotation", v);
+        double tmax = 0.0;
+        for (int i = 0; i < 3; ++i)
+            if (!finite(k.o[i])) return fail(ROAM_ERR_ARG, "camera %d: non-finite centre", v);
+        for (int corner = 0; corner < 8; ++corner) {
+            double d2 = 0;
+            for (int a = 0; a < 3; ++a) {
+                const double e = c->gd.origin[a] + ((corner >> a) & 1) * ext[a] - k.o[a];
+                d2 += e * e;
+            }
+            tmax = std::max(tmax, std::sqrt(d2));
+        }
+        if (tmax / delta + 8.0 > 65535.0)
+            return fail(ROAM_ERR_ARG, "camera %d: more than 65535 sample positions per ray (delta too small)", v);
+        DevCamera &d = c->h_cams[v];
+        memset(&d, 0, sizeof(d));
+        d.model = k.model;
+        d.width = k.width;
+        d.height = k.height;
+        memcpy(d.R, k.R, sizeof(d.R));
+        memcpy(d.o, k.o, sizeof(d.o));
+        d.inv_f = k.model == ROAM_PERSPECTIVE ? (float)(std::tan(0.5 * (double)k.fov_h) / (0.5 * k.width)) : 0.f;
+        d.pix_start = (uint32_t)total;
+        total += (int64_t)k.width * k.height;
+        if (total > (int64_t)0x7fffffff) return fail(ROAM_ERR_ARG, "too many pixels");
+    }
+    ROAM_TRY(ensure(c->cams, (size_t)n_views));
+    ROAM_CUDA(cudaMemcpyAsync(c->cams.p, c->h_cams, sizeof(DevCamera) * n_views, cudaMemcpyHostToDevice, s));
+    ROAM_CUDA(cudaEventRecord(c->cam_ev, s));
+    c->cam_pending = true;
+    *n_pix = total;
+    c->n_views = n_views;
+    return ROAM_OK;
+}
+
+roam_status ensure_rays(roam_ctx *c, int64_t n_rays, int R)
+{
+    const size_t n = (size_t)n_rays;
+    ROAM_TRY(ensure(c->orig, n));
+    ROAM_TRY(ensure(c->dir, n));
+    ROAM_TRY(ensure(c->acc, n));
+    ROAM_TRY(ensure(c->tw, n));
+    ROAM_TRY(ensure(c->j_next, n));
+    ROAM_TRY(ensure(c->j_end, n));
+    ROAM_TRY(ensure(c->n_kept, n));
+    ROAM_TRY(ensure(c->live0, n));
+    ROAM_TRY(ensure(c->live1, n));
+    ROAM_TRY(ensure(c->cnt, n));
+    const size_t slots = ((n + 31) & ~(size_t)31) * (size_t)R;
+    ROAM_TRY(ensure(c->recs, slots));
+    ROAM_TRY(ensure(c->sr, slots));
+    ROAM_TRY(ensure(c->sorted, slots));
+    ROAM_TRY(ensure(c->tiles, slots / 64 + (size_t)c->n_fields + 1));
+    return ROAM_OK;
+}
+
+roam_status ensure_fields_ws(roam_ctx *c)
+{
+    const size_t F = (size_t)c->n_fields;
+    const bool fresh = !c->hist.p || c->hist.n < F;
+    ROAM_TRY(ensure(c->hist, F));
+    ROAM_TRY(ensure(c->offsets, F + 1));
+    ROAM_TRY(ensure(c->cursor, F));
+    if (fresh) ROAM_CUDA(cudaMemset(c->hist.p, 0, F * sizeof(uint32_t)));
+    return ROAM_OK;
+}
+
+RayState state_of(roam_ctx *c)
+{
+    RayState st;
+    st.orig = c->orig.p;
+    st.dir = c->dir.p;
+    st.j_next = c->j_next.p;
+    st.j_end = c->j_end.p;
+    st.n_kept = c->n_kept.p;
+    st.acc = c->acc.p;
+    st.tw = c->tw.p;
+    return st;
+}
+
+BucketBufs bucket_of(roam_ctx *c)
+{
+    BucketBufs b;
+    b.hist = c->hist.p;
+    b.offsets = c->offsets.p;
+    b.cursor = c->cursor.p;
+    b.tiles = c->tiles.p;
+    b.sorted = c->sorted.p;
+    return b;
+}
+
+int tile_of(int precision) { return precision == ROAM_BF16 ? tc_tile_samples() : 128; }
+
+roam_status run_mlp(roam_ctx *c, int precision, const SampleSrc &src, const BucketBufs &b, float4 *out,
+                    cudaStream_t s)
+{
+    const MlpWeights w = weights_of(c);
+    if (precision == ROAM_BF16) {
+        launch_mlp_tc(w, src, b, c->ctr, out, c->n_sm, s);
+        return launched("mlp_tc");
+    }
+    launch_mlp_simt(w, src, b, c->ctr, out, grid_blocks(c, 4), s);
+    return launched("mlp_simt");
+}
+
+// The render / training-forward pipeline: rounds of march -> bucket -> MLP ->
+// composite; each round marches at most R more kept samples of every live ray.
+roam_status run_rounds(roam_ctx *c, const uint32_t *rays, int64_t n_rays, const roam_render_opts *o, float *rgb,
+                       float *depth, float *opacity, int R, cudaStream_t s)
+{
+    const int n_rounds = (o->n_max + R - 1) / R;
+    MarchParams mp{};
+    mp.cams = c->cams.p;
+    mp.n_views = c->n_views;
+    mp.rays = rays;
+    mp.n_rays = (uint32_t)n_rays;
+    mp.R = R;
+    mp.n_max = o->n_max;
+    mp.delta = o->delta;
+    mp.flat = 0;
+    mp.st = state_of(c);
+    mp.cnt = c->cnt.p;
+    mp.recs = c->recs.p;
+    mp.ctr = c->ctr;
+    const BucketBufs b = bucket_of(c);
+    const int grid = grid_blocks(c, 4);
+    uint32_t *lives[2] = {c->live0.p, c->live1.p};
+    for (int r = 0; r < n_rounds; ++r) {
+        mp.init = r == 0;
+        mp.live = r == 0 ? nullptr : lives[r & 1];
+        mp.live_count = r == 0 ? nullptr : &c->ctr->live_count[r & 1];
+        {
+            ProfScope ps(c, P_MARCH, s);
+            launch_march(c->g, mp, grid, s);
+        }
+        ROAM_TRY(launched("march"));
+        {
+            ProfScope ps(c, P_BUCKET, s);
+            launch_bucket(mp.cnt, mp.recs, mp.live_count, mp.n_rays, R, 0, nullptr, c->n_fields,
+                          tile_of(o->precision), b, c->ctr, grid, s);
+        }
+        ROAM_TRY(launched("bucket"));
+        SampleSrc src{};
+        src.mode = 0;
+        src.recs = mp.recs;
+        src.live = mp.live;
+        src.live_count = mp.live_count;
+        src.R = R;
+        src.st = mp.st;
+        src.delta = o->delta;
+        {
+            ProfScope ps(c, o->precision == ROAM_BF16 ? P_MLP_BF16 : P_MLP_F32, s);
+            ROAM_TRY(run_mlp(c, o->precision, src, b, c->sr.p, s));
+        }
+        {
+            ProfScope ps(c, P_COMPOSITE, s);
+            launch_composite_round(mp, c->sr.p, lives[(r + 1) & 1], &c->ctr->live_count[(r + 1) & 1], o->t_stop,
+                                   o->bg, rgb, depth, opacity, grid, s);
+        }
+        ROAM_TRY(launched("composite"));
+    }
+    return ROAM_OK;
+}
+
+int round_size(const roam_render_opts *o, int64_t n_rays)
+{
+    int R = o->round_size > 0 ? o->round_size : 32;
+    R = std::min(R, o->n_max);
+    // slot indices are 32-bit
+    while (R > 1 && (double)((n_rays + 31) & ~31LL) * R >= 4294967295.0) R >>= 1;
+    return R;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *roam_last_error(void) { return g_err; }
+
+roam_status roam_create(roam_ctx **out, int device)
+{
+    if (!out) return fail(ROAM_ERR_ARG, "null output handle");
+    *out = nullptr;
+    int n_dev = 0;
+    ROAM_CUDA(cudaGetDeviceCount(&n_dev));
+    if (device < 0 || device >= n_dev) return fail(ROAM_ERR_ARG, "device %d out of range (%d devices)", device, n_dev);
+    ROAM_CUDA(cudaSetDevice(device));
+    cudaDeviceProp prop;
+    ROAM_CUDA(cudaGetDeviceProperties(&prop, device));
+    if (prop.major != 10 || prop.minor != 3)
+        return fail(ROAM_ERR_UNSUPPORTED, "device %d is sm_%d%d; this library is built for sm_103a only", device,
+                    prop.major, prop.minor);
+    roam_ctx *c = new roam_ctx();
+    c->device = device;
+    c->n_sm = prop.multiProcessorCount;
+    if (cudaMalloc(&c->ctr, sizeof(Counters)) != cudaSuccess || cudaMallocHost(&c->h_ctr, sizeof(Counters)) != cudaSuccess ||
+        cudaMallocHost(&c->h_cams, sizeof(DevCamera) * kMaxViews) != cudaSuccess ||
+        cudaMalloc(&c->d_flag, sizeof(uint32_t)) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->cam_ev, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        roam_destroy(c);
+        return fail(ROAM_ERR_OOM, "context allocation failed");
+    }
+    cudaMemset(c->ctr, 0, sizeof(Counters));
+    *out = c;
+    return ROAM_OK;
+}
+
+roam_status roam_destroy(roam_ctx *c)
+{
+    if (!c) return ROAM_OK;
+    cudaSetDevice(c->device);
+    cudaDeviceSynchronize();
+    release(c->bits); release(c->prefix); release(c->brick); release(c->block_sums);
+    release(c->labels); release(c->affine);
+    release(c->w32); release(c->wt); release(c->bias); release(c->adam_m); release(c->adam_v); release(c->wimg);
+    release(c->orig); release(c->dir); release(c->acc); release(c->sr); release(c->tw);
+    release(c->j_next); release(c->j_end); release(c->n_kept); release(c->live0); release(c->live1);
+    release(c->cnt); release(c->recs); release(c->sorted); release(c->hist); release(c->offsets);
+    release(c->cursor); release(c->scratch_u32); release(c->tiles);
+    release(c->o_rgb); release(c->o_depth); release(c->o_op); release(c->cams);
+    if (c->h_cams) cudaFreeHost(c->h_cams);
+    if (c->h_ctr) cudaFreeHost(c->h_ctr);
+    if (c->ctr) cudaFree(c->ctr);
+    if (c->d_flag) cudaFree(c->d_flag);
+    if (c->cam_ev) cudaEventDestroy(c->cam_ev);
+    for (auto e : c->ev_pool) cudaEventDestroy(e);
+    for (auto &p : c->prof_pending) {
+        cudaEventDestroy(p.second.first);
+        cudaEventDestroy(p.second.second);
+    }
+    delete c;
+    return ROAM_OK;
+}
+
+roam_status roam_check(roam_ctx *c)
+{
+    ROAM_TRY(set_dev(c));
+    ROAM_CUDA(cudaStreamSynchronize(c->last));
+    ROAM_CUDA(cudaMemcpy(c->h_ctr, c->ctr, sizeof(Counters), cudaMemcpyDeviceToHost));
+    return status_of(c->h_ctr->status);
+}
+
+roam_status roam_load_grid(roam_ctx *c, const roam_grid_desc *desc, const uint32_t *bits, int on_device)
+{
+    ROAM_TRY(set_dev(c));
+    if (!desc || !bits) return fail(ROAM_ERR_ARG, "null grid descriptor or bits");
+    for (int a = 0; a < 3; ++a)
+        if (desc->dims[a] < 8 || desc->dims[a] > 2048 || desc->dims[a] % 8)
+            return fail(ROAM_ERR_ARG, "grid dims must be multiples of 8 in [8, 2048]");
+    if (desc->dims[0] % 32) return fail(ROAM_ERR_ARG, "grid x dimension must be a multiple of 32");
+    if (!(desc->vox > 0.f) || !finite(desc->vox)) return fail(ROAM_ERR_ARG, "voxel size must be positive");
+    for (int a = 0; a < 3; ++a)
+        if (!finite(desc->origin[a])) return fail(ROAM_ERR_ARG, "grid origin must be finite");
+    c->has_grid = c->has_fields = c->has_weights = false;
+    const int64_t n_words = (int64_t)desc->dims[0] / 32 * desc->dims[1] * desc->dims[2];
+    ROAM_TRY(ensure(c->bits, (size_t)n_words));
+    ROAM_TRY(ensure(c->prefix, (size_t)n_words));
+    ROAM_TRY(ensure(c->block_sums, (size_t)((n_words + 4095) / 4096)));
+    ROAM_CUDA(cudaMemcpy(c->bits.p, bits, n_words * sizeof(uint32_t),
+                         on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice));
+    GridDev &g = c->g;
+    g.gx = desc->dims[0]; g.gy = desc->dims[1]; g.gz = desc->dims[2];
+    g.wpr = g.gx / 32;
+    g.bx = g.gx >> kBrickShift; g.by = g.gy >> kBrickShift; g.bz = g.gz >> kBrickShift;
+    g.bwpr = (g.bx + 31) / 32;
+    for (int a = 0; a < 3; ++a) g.origin[a] = desc->origin[a];
+    g.vox = desc->vox;
+    g.inv_vox = 1.0f / desc->vox;
+    const int64_t n_brick_words = (int64_t)g.bwpr * g.by * g.bz;
+    ROAM_TRY(ensure(c->brick, (size_t)n_brick_words));
+    ROAM_CUDA(cudaMemset(c->brick.p, 0, n_brick_words * sizeof(uint32_t)));
+    g.bits = c->bits.p;
+    g.prefix = c->prefix.p;
+    g.brick = c->brick.p;
+    g.labels = nullptr;
+    g.n_fields = 0;
+    launch_grid_prefix(c->bits.p, c->prefix.p, c->block_sums.p, n_words, 0);
+    ROAM_TRY(launched("grid prefix"));
+    launch_brick_map(g, c->brick.p, 0);
+    ROAM_TRY(launched("brick map"));
+    uint32_t last_pre = 0, last_word = 0;
+    ROAM_CUDA(cudaMemcpy(&last_pre, c->prefix.p + n_words - 1, 4, cudaMemcpyDeviceToHost));
+    ROAM_CUDA(cudaMemcpy(&last_word, c->bits.p + n_words - 1, 4, cudaMemcpyDeviceToHost));
+    c->n_words = n_words;
+    c->n_occ = (int64_t)last_pre + __builtin_popcount(last_word);
+    c->gd = *desc;
+    c->has_grid = true;
+    return ROAM_OK;
+}
+
+roam_status roam_load_fields(roam_ctx *c, int n_fields, const uint16_t *labels, int64_t n_occupied,
+                             const float *affine, int on_device)
+{
+    ROAM_TRY(set_dev(c));
+    if (!c->has_grid) return fail(ROAM_ERR_STATE, "load the occupancy grid first");
+    if (n_fields < 1 || n_fields > 8192) return fail(ROAM_ERR_ARG, "n_fields must be in [1, 8192]");
+    if (n_occupied != c->n_occ)
+        return fail(ROAM_ERR_ARG, "n_occupied=%lld but the grid has %lld occupied voxels", (long long)n_occupied,
+                    (long long)c->n_occ);
+    if ((n_occupied > 0 && !labels) || !affine) return fail(ROAM_ERR_ARG, "null labels or affine");
+    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    std::vector<float> aff_h(6 * (size_t)n_fields);
+    if (on_device) ROAM_CUDA(cudaMemcpy(aff_h.data(), affine, aff_h.size() * 4, cudaMemcpyDeviceToHost));
+    else memcpy(aff_h.data(), affine, aff_h.size() * 4);
+    for (float v : aff_h)
+        if (!finite(v)) return fail(ROAM_ERR_ARG, "non-finite field affine");
+    c->has_fields = c->has_weights = false;
+    ROAM_TRY(ensure(c->labels, (size_t)std::max<int64_t>(n_occupied, 1)));
+    ROAM_TRY(ensure(c->affine, 6 * (size_t)n_fields));
+    if (n_occupied > 0) ROAM_CUDA(cudaMemcpy(c->labels.p, labels, n_occupied * sizeof(uint16_t), kind));
+    ROAM_CUDA(cudaMemcpy(c->affine.p, aff_h.data(), aff_h.size() * 4, cudaMemcpyHostToDevice));
+    if (n_occupied > 0) {
+        ROAM_CUDA(cudaMemset(c->d_flag, 0, 4));
+        k_check_labels<<<256, 256>>>(c->labels.p, n_occupied, n_fields, c->d_flag);
+        ROAM_TRY(launched("label check"));
+        uint32_t bad = 0;
+        ROAM_CUDA(cudaMemcpy(&bad, c->d_flag, 4, cudaMemcpyDeviceToHost));
+        if (bad) return fail(ROAM_ERR_ARG, "a field label is >= n_fields");
+    }
+    c->n_fields = n_fields;
+    c->g.labels = c->labels.p;
+    c->g.n_fields = n_fields;
+    ROAM_TRY(ensure_fields_ws(c));
+    c->has_fields = true;
+    return ROAM_OK;
+}
+
+roam_status roam_load_weights(roam_ctx *c, const roam_mlp_desc *desc, const float *weights, int on_device)
+{
+    ROAM_TRY(set_dev(c));
+    if (!c->has_fields) return fail(ROAM_ERR_STATE, "load the field labels first");
+    if (!desc || !weights) return fail(ROAM_ERR_ARG, "null MLP descriptor or weights");
+    if (desc->width != 32 && desc->width != 64 && desc->width != 128)
+        return fail(ROAM_ERR_ARG, "width must be 32, 64 or 128");
+    if (desc->n_hidden < 1 || desc->n_hidden > 4) return fail(ROAM_ERR_ARG, "n_hidden must be in [1, 4]");
+    if (!(desc->sigma_scale > 0.f) || !finite(desc->sigma_scale)) return fail(ROAM_ERR_ARG, "sigma_scale must be positive");
+    if (desc->density_act != ROAM_SOFTPLUS && desc->density_act != ROAM_RELU)
+        return fail(ROAM_ERR_ARG, "unknown density activation");
+    c->has_weights = false;
+    const int W = desc->width, H = desc->n_hidden;
+    const int64_t P = param_count(W, H);
+    const int64_t total = P * c->n_fields;
+    ROAM_TRY(ensure(c->w32, (size_t)total));
+    ROAM_CUDA(cudaMemcpy(c->w32.p, weights, total * sizeof(float),
+                         on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice));
+    ROAM_CUDA(cudaMemset(c->d_flag, 0, 4));
+    k_check_finite<<<1024, 256>>>(c->w32.p, total, c->d_flag);
+    ROAM_TRY(launched("weight check"));
+    uint32_t bad = 0;
+    ROAM_CUDA(cudaMemcpy(&bad, c->d_flag, 4, cudaMemcpyDeviceToHost));
+    if (bad) return fail(ROAM_ERR_ARG, "weights contain NaN or Inf");
+    c->md = *desc;
+    c->P = P;
+    c->Pt = simt_transposed_size(W, H);
+    ROAM_TRY(ensure(c->wt, (size_t)(c->Pt * c->n_fields)));
+    launch_pack_simt(c->w32.p, c->n_fields, W, H, P, c->wt.p, c->Pt, 0);
+    ROAM_TRY(launched("pack simt"));
+    c->tc_ok = tc_supported(W, H);
+    if (c->tc_ok) {
+        c->img_bytes = tc_image_bytes(W, H);
+        c->nb = tc_bias_count(W, H);
+        ROAM_TRY(ensure(c->wimg, (size_t)(c->img_bytes * c->n_fields)));
+        ROAM_TRY(ensure(c->bias, (size_t)c->nb * c->n_fields));
+        launch_pack_tc(c->w32.p, c->n_fields, W, H, P, c->wimg.p, c->img_bytes, c->bias.p, c->nb, 0);
+        ROAM_TRY(launched("pack tc"));
+    }
+    ROAM_CUDA(cudaDeviceSynchronize());
+    c->has_weights = true;
+    return ROAM_OK;
+}
+
+roam_status roam_get_weights(roam_ctx *c, float *out, int on_device)
+{
+    ROAM_TRY(set_dev(c));
+    if (!c->has_weights) return fail(ROAM_ERR_STATE, "no weights loaded");
+    if (!out) return fail(ROAM_ERR_ARG, "null output");
+    ROAM_CUDA(cudaDeviceSynchronize());
+    ROAM_CUDA(cudaMemcpy(out, c->w32.p, (size_t)(c->P * c->n_fields) * sizeof(float),
+                         on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost));
+    return ROAM_OK;
+}
+
+roam_status roam_render(roam_ctx *c, const roam_camera *cams, int n_views, const roam_render_opts *opts, float *rgb,
+                        float *depth, float *opacity, int out_on_device, void *stream)
+{
+    ROAM_TRY(set_dev(c));
+    ROAM_TRY(check_ready(c));
+    ROAM_TRY(check_opts(c, opts));
+    cudaStream_t s = (cudaStream_t)stream;
+    int64_t n_pix = 0;
+    ROAM_TRY(upload_cams(c, cams, n_views, opts->delta, &n_pix, s));
+    const int R = round_size(opts, n_pix);
+    ROAM_TRY(ensure_rays(c, n_pix, R));
+    float *d_rgb = rgb, *d_depth = depth, *d_op = opacity;
+    if (!out_on_device) {
+        if (rgb) { ROAM_TRY(ensure(c->o_rgb, 3 * (size_t)n_pix)); d_rgb = c->o_rgb.p; }
+        if (depth) { ROAM_TRY(ensure(c->o_depth, (size_t)n_pix)); d_depth = c->o_depth.p; }
+        if (opacity) { ROAM_TRY(ensure(c->o_op, (size_t)n_pix)); d_op = c->o_op.p; }
+    }
+    ROAM_CUDA(cudaMemsetAsync(c->ctr, 0, sizeof(Counters), s));
+    ROAM_TRY(run_rounds(c, nullptr, n_pix, opts, d_rgb, d_depth, d_op, R, s));
+    c->last = s;
+    c->last_rays = n_pix;
+    c->last_rounds = (opts->n_max + R - 1) / R;
+    c->train_rays = 0;
+    if (!out_on_device) {
+        if (rgb) ROAM_CUDA(cudaMemcpyAsync(rgb, d_rgb, 12 * (size_t)n_pix, cudaMemcpyDeviceToHost, s));
+        if (depth) ROAM_CUDA(cudaMemcpyAsync(depth, d_depth, 4 * (size_t)n_pix, cudaMemcpyDeviceToHost, s));
+        if (opacity) ROAM_CUDA(cudaMemcpyAsync(opacity, d_op, 4 * (size_t)n_pix, cudaMemcpyDeviceToHost, s));
+        ROAM_CUDA(cudaMemcpyAsync(c->h_ctr, c->ctr, sizeof(Counters), cudaMemcpyDeviceToHost, s));
+        ROAM_CUDA(cudaStreamSynchronize(s));
+        return status_of(c->h_ctr->status);
+    }
+    return ROAM_OK;
+}
+
+roam_status roam_get_stats(roam_ctx *c, roam_stats *st)
+{
+    ROAM_TRY(set_dev(c));
+    if (!st) return fail(ROAM_ERR_ARG, "null stats");
+    ROAM_CUDA(cudaStreamSynchronize(c->last));
+    ROAM_CUDA(cudaMemcpy(c->h_ctr, c->ctr, sizeof(Counters), cudaMemcpyDeviceToHost));
+    st->n_samples = (int64_t)c->h_ctr->n_samples;
+    st->n_used = (int64_t)c->h_ctr->n_used;
+    st->n_fields_hit = (int32_t)c->h_ctr->fields_hit;
+    st->n_rays = c->last_rays;
+    st->n_rounds = c->last_rounds;
+    return status_of(c->h_ctr->status);
+}
+
+roam_status roam_profile(roam_ctx *c, int enable)
+{
+    ROAM_TRY(set_dev(c));
+    ROAM_CUDA(cudaDeviceSynchronize());
+    for (auto &p : c->prof_pending) {
+        c->ev_pool.push_back(p.second.first);
+        c->ev_pool.push_back(p.second.second);
+    }
+    c->prof_pending.clear();
+    c->prof_acc.assign(kProfKinds, {0, 0.0});
+    c->prof = enable != 0;
+    return ROAM_OK;
+}
+
+roam_status roam_profile_read(roam_ctx *c, roam_kernel_time *out, int max_entries, int *n_entries)
+{
+    ROAM_TRY(set_dev(c));
+    if (!out || !n_entries || max_entries < 0) return fail(ROAM_ERR_ARG, "null output");
+    ROAM_CUDA(cudaDeviceSynchronize());
+    if (c->prof_acc.size() != (size_t)kProfKinds) c->prof_acc.assign(kProfKinds, {0, 0.0});
+    for (auto &p : c->prof_pending) {
+        float ms = 0.f;
+        ROAM_CUDA(cudaEventElapsedTime(&ms, p.second.first, p.second.second));
+        c->prof_acc[p.first].first += 1;
+        c->prof_acc[p.first].second += ms;
+        c->ev_pool.push_back(p.second.first);
+        c->ev_pool.push_back(p.second.second);
+    }
+    c->prof_pending.clear();
+    int n = 0;
+    for (int k = 0; k < kProfKinds && n < max_entries; ++k) {
+        if (!c->prof_acc[k].first) continue;
+        memset(out[n].name, 0, sizeof(out[n].name));
+        strncpy(out[n].name, kProfNames[k], sizeof(out[n].name) - 1);
+        out[n].launches = c->prof_acc[k].first;
+        out[n].total_ms = c->prof_acc[k].second;
+        ++n;
+    }
+    *n_entries = n;
+    return ROAM_OK;
+}
+
+roam_status roam_march(roam_ctx *c, const roam_camera *cams, int n_views, const uint32_t *rays, int64_t n_rays,
+                       const roam_render_opts *opts, uint32_t *count, uint32_t *recs, void *stream)
+{
+    ROAM_TRY(set_dev(c));
+    if (!c->has_grid || !c->has_fields) return fail(ROAM_ERR_STATE, "load grid and fields first");
+    if (!opts || !(opts->delta > 0.f) || opts->n_max < 1 || opts->n_max > 1024)
+        return fail(ROAM_ERR_ARG, "bad options");
+    if (!count || !recs) return fail(ROAM_ERR_ARG, "null outputs");
+    cudaStream_t s = (cudaStream_t)stream;
+    int64_t n_pix = 0;
+    ROAM_TRY(upload_cams(c, cams, n_views, opts->delta, &n_pix, s));
+    if (!rays) n_rays = n_pix;
+    if (n_rays < 0 || n_rays > 0x7fffffff) return fail(ROAM_ERR_ARG, "bad ray count");
+    if (n_rays == 0) return ROAM_OK;
+    ROAM_TRY(ensure_rays(c, n_rays, 1));
+    MarchParams mp{};
+    mp.cams = c->cams.p;
+    mp.n_views = n_views;
+    mp.rays = rays;
+    mp.n_rays = (uint32_t)n_rays;
+    mp.R = opts->n_max;
+    mp.n_max = opts->n_max;
+    mp.delta = opts->delta;
+    mp.init = 1;
+    mp.flat = 1;
+    mp.st = state_of(c);
+    mp.cnt = count;
+    mp.recs = recs;
+    mp.ctr = c->ctr;
+    ROAM_CUDA(cudaMemsetAsync(c->ctr, 0, sizeof(Counters), s));
+    launch_march(c->g, mp, grid_blocks(c, 4), s);
+    c->last = s;
+    return launched("march");
+}
+
+roam_status roam_bucket(roam_ctx *c, const uint16_t *keys, int64_t n, uint32_t *perm, uint32_t *offsets, void *stream)
+{
+    ROAM_TRY(set_dev(c));
+    if (!c->has_fields) return fail(ROAM_ERR_STATE, "load field labels first");
+    if (n < 0 || n > 0x7fffffff) return fail(ROAM_ERR_ARG, "bad sample count");
+    if (!offsets || (n > 0 && (!keys || !perm))) return fail(ROAM_ERR_ARG, "null pointer");
+    cudaStream_t s = (cudaStream_t)stream;
+    ROAM_TRY(ensure(c->tiles, (size_t)n / 64 + c->n_fields + 1));
+    BucketBufs b = bucket_of(c);
+    b.offsets = offsets;
+    b.sorted = perm;
+    ROAM_CUDA(cudaMemsetAsync(c->ctr, 0, sizeof(Counters), s));
+    launch_bucket(nullptr, nullptr, nullptr, (uint32_t)n, 1, 1, keys, c->n_fields, 128, b, c->ctr, grid_blocks(c, 2), s);
+    c->last = s;
+    return launched("bucket");
+}
+
+roam_status roam_mlp_eval(roam_ctx *c, const float *p, const float *d, const uint16_t *field, int64_t n, int precision,
+                          float *out, void *stream)
+{
+    ROAM_TRY(set_dev(c));
+    ROAM_TRY(check_ready(c));
+    if (n < 0 || n > 0x7fffffff) return fail(ROAM_ERR_ARG, "bad sample count");
+    if (n == 0) return ROAM_OK;
+    if (!p || !d || !field || !out) return fail(ROAM_ERR_ARG, "null pointer");
+    if (precision != ROAM_F32 && precision != ROAM_BF16) return fail(ROAM_ERR_ARG, "unknown precision");
+    if (precision == ROAM_BF16 && !c->tc_ok) return fail(ROAM_ERR_UNSUPPORTED, "BF16 path not available");
+    cudaStream_t s = (cudaStream_t)stream;
+    ROAM_TRY(ensure(c->sorted, (size_t)n));
+    ROAM_TRY(ensure(c->tiles, (size_t)n / 64 + c->n_fields + 1));
+    const BucketBufs b = bucket_of(c);
+    ROAM_CUDA(cudaMemsetAsync(c->ctr, 0, sizeof(Counters), s));
+    launch_bucket(nullptr, nullptr, nullptr, (uint32_t)n, 1, 1, field, c->n_fields, tile_of(precision), b, c->ctr,
+                  grid_blocks(c, 2), s);
+    ROAM_TRY(launched("bucket"));
+    SampleSrc src{};
+    src.mode = 1;
+    src.p = p;
+    src.d = d;
+    c->last = s;
+    return run_mlp(c, precision, src, b, reinterpret_cast<float4 *>(out), s);
+}
+
+roam_status roam_composite(roam_ctx *c, int64_t n_rays, int n_max, const uint32_t *count, const float *sigma_rgb,
+                           const float *t, const roam_render_opts *opts, float *rgb, float *depth, float *opacity,
+                           uint32_t *n_used, void *stream)
+{
+    ROAM_TRY(set_dev(c));
+    if (!opts || !(opts->delta > 0.f) || !(opts->t_stop >= 0.f && opts->t_stop < 1.f))
+        return fail(ROAM_ERR_ARG, "bad options");
+    if (n_rays < 0 || n_max < 1) return fail(ROAM_ERR_ARG, "bad sizes");
+    if (n_rays == 0) return ROAM_OK;
+    if (!count || !sigma_rgb || !t) return fail(ROAM_ERR_ARG, "null input");
+    if (((uintptr_t)sigma_rgb) & 15) return fail(ROAM_ERR_ARG, "sigma_rgb must be 16-byte aligned");
+    cudaStream_t s = (cudaStream_t)stream;
+    launch_composite_flat(n_rays, n_max, count, reinterpret_cast<const float4 *>(sigma_rgb), t, opts->delta,
+                          opts->t_stop, opts->bg, rgb, depth, opacity, n_used, s);
+    c->last = s;
+    return launched("composite");
+}
+
+roam_status roam_train_forward(roam_ctx *c, const roam_camera *, int, const uint32_t *, int64_t,
+                               const roam_render_opts *, float *, void *)
+{
+    ROAM_TRY(set_dev(c));
+    return fail(ROAM_ERR_UNSUPPORTED, "training forward not built yet");
+}
+
+roam_status roam_train_backward(roam_ctx *c, const float *, float *, void *)
+{
+    ROAM_TRY(set_dev(c));
+    return fail(ROAM_ERR_UNSUPPORTED, "training backward not built yet");
+}
+
+roam_status roam_adam_step(roam_ctx *c, const float *, const roam_adam_cfg *, void *)
+{
+    ROAM_TRY(set_dev(c));
+    return fail(ROAM_ERR_UNSUPPORTED, "adam not built yet");
+}
+
+}  // extern "C"
