@@ -25,7 +25,7 @@ struct DevCamera {
     float o[3];
     float inv_f;          // perspective: 1 / focal length in pixels
     uint32_t pix_start;   // first global pixel index of this view
-    uint32_t pad2[2];
+    double inv_f64;       // the same focal factor in FP64 (FP32 render path)
 };
 
 struct GridDev {
@@ -55,6 +55,7 @@ struct Counters {
 struct RayState {
     float4 *orig;       // o (xyz), w unused
     float4 *dir;        // d (xyz), w unused
+    float4 *dir_lo;     // FP64 direction minus d (FP32 render path only)
     uint32_t *j_next;   // next sample index to test
     uint32_t *j_end;    // first sample index past the grid
     uint32_t *n_kept;   // kept samples so far
@@ -81,6 +82,7 @@ struct MarchParams {
     float delta;
     int init;                   // compute rays and reset state
     int flat;                   // recs laid out [n_rays][R] instead of slots
+    int accurate;               // also keep the FP64 direction residual
     RayState st;
     uint32_t *cnt;              // per live index: samples emitted
     uint32_t *recs;             // j | field << 16
@@ -97,6 +99,7 @@ struct SampleSrc {
     int R;
     RayState st;
     float delta;
+    int accurate;               // sample positions from the direction residual
     // direct points
     const float *p;             // [n][3]
     const float *d;             // [n][3]

@@ -86,6 +86,26 @@ __device__ __forceinline__ void store_relu(const float (&acc)[N], int n, float *
         if (o < n) sx[(base + o) * kThreads + tid] = fmaxf(acc[o], 0.f);
 }
 
+// Field-local coordinate scale * (o + t d) + offset of sample j, with
+// t = (j + 1/2) delta and d = dh + dl carried as unevaluated FP32 pairs
+// (error-free products and sums, explicitly rounded operations so that no
+// step is contracted): accurate to about one FP32 ulp of the result.
+__device__ __forceinline__ float local_coord(float th0, float delta, float o, float dh, float dl, float scale,
+                                             float offset)
+{
+    const float t_hi = __fmul_rn(th0, delta);
+    const float t_lo = __fmaf_rn(th0, delta, -t_hi);
+    const float ph = __fmul_rn(t_hi, dh);
+    const float pl = __fadd_rn(__fmaf_rn(t_hi, dh, -ph), __fadd_rn(__fmul_rn(t_hi, dl), __fmul_rn(t_lo, dh)));
+    const float sh = __fadd_rn(o, ph);
+    const float bv = __fsub_rn(sh, o);
+    const float se = __fadd_rn(__fsub_rn(o, __fsub_rn(sh, bv)), __fsub_rn(ph, bv));
+    const float sl = __fadd_rn(se, pl);
+    const float qh = __fmul_rn(scale, sh);
+    const float ql = __fadd_rn(__fmaf_rn(scale, sh, -qh), __fmul_rn(scale, sl));
+    return __fadd_rn(__fadd_rn(qh, offset), ql);
+}
+
 __device__ __forceinline__ float softplus_f(float s) { return s > 20.f ? s : log1pf(expf(s)); }
 __device__ __forceinline__ float sigmoid_f(float s) { return 1.f / (1.f + expf(-s)); }
 
@@ -104,24 +124,37 @@ __global__ void __launch_bounds__(kThreads) k_mlp_simt(MlpWeights w, SampleSrc s
         const Tile tl = b.tiles[t];
         const bool valid = (uint32_t)tid < tl.count;
         const uint32_t idx = valid ? b.sorted[tl.start + tid] : 0u;
-        float px = 0.f, py = 0.f, pz = 0.f, dx = 0.f, dy = 0.f, dz = 1.f;
+        const float *aff = w.affine + 6 * (int64_t)tl.field;
+        float xl0 = 0.f, xl1 = 0.f, xl2 = 0.f, dx = 0.f, dy = 0.f, dz = 1.f;
         if (valid) {
             if (src.mode == 0) {
                 const uint32_t col = idx >> 5;
                 const uint32_t i = (col / (uint32_t)src.R) * 32u + (idx & 31u);
                 const uint32_t ray = src.live ? src.live[i] : i;
                 const uint32_t j = src.recs[idx] & 0xffffu;
-                const float tt = ((float)j + 0.5f) * src.delta;
                 const float4 o = src.st.orig[ray], d = src.st.dir[ray];
-                px = fmaf(tt, d.x, o.x); py = fmaf(tt, d.y, o.y); pz = fmaf(tt, d.z, o.z);
                 dx = d.x; dy = d.y; dz = d.z;
+                if (src.accurate) {
+                    const float4 dl = src.st.dir_lo[ray];
+                    const float th0 = (float)j + 0.5f;
+                    xl0 = local_coord(th0, src.delta, o.x, d.x, dl.x, aff[0], aff[3]);
+                    xl1 = local_coord(th0, src.delta, o.y, d.y, dl.y, aff[1], aff[4]);
+                    xl2 = local_coord(th0, src.delta, o.z, d.z, dl.z, aff[2], aff[5]);
+                } else {
+                    const float tt = ((float)j + 0.5f) * src.delta;
+                    xl0 = fmaf(aff[0], fmaf(tt, d.x, o.x), aff[3]);
+                    xl1 = fmaf(aff[1], fmaf(tt, d.y, o.y), aff[4]);
+                    xl2 = fmaf(aff[2], fmaf(tt, d.z, o.z), aff[5]);
+                }
             } else {
-                px = src.p[3 * (int64_t)idx]; py = src.p[3 * (int64_t)idx + 1]; pz = src.p[3 * (int64_t)idx + 2];
+                const float px = src.p[3 * (int64_t)idx], py = src.p[3 * (int64_t)idx + 1],
+                            pz = src.p[3 * (int64_t)idx + 2];
                 dx = src.d[3 * (int64_t)idx]; dy = src.d[3 * (int64_t)idx + 1]; dz = src.d[3 * (int64_t)idx + 2];
+                xl0 = fmaf(aff[0], px, aff[3]);
+                xl1 = fmaf(aff[1], py, aff[4]);
+                xl2 = fmaf(aff[2], pz, aff[5]);
             }
         }
-        const float *aff = w.affine + 6 * (int64_t)tl.field;
-        const float xl0 = fmaf(aff[0], px, aff[3]), xl1 = fmaf(aff[1], py, aff[4]), xl2 = fmaf(aff[2], pz, aff[5]);
         const float *wf = w.wt + (int64_t)tl.field * w.Pt;
 
         encode<10>(xl0, xl1, xl2, sx, 0, tid);

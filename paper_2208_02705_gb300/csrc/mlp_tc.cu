@@ -1,10 +1,604 @@
-// placeholder until the tcgen05 kernel lands
+// tcgen05 BF16 evaluation of the per-field tiny MLPs (the concurrent MLP
+// queries of Sec. "Real-time Rendering Speedup" as a grouped GEMM chain on
+// the 5th-generation tensor cores).  One tile = 128 samples of one field =
+// one M=128 MMA row block; every layer of the chain is
+//   D[128 x N] (TMEM, FP32) = X[128 x K] (SMEM, BF16) * B[K x N] (SMEM, BF16)
+// issued by one thread with tcgen05.mma kind::f16.  The epilogue warps read
+// D back with tcgen05.ld (one row per thread), add bias, apply the
+// activation, round to BF16 and write the next layer's X in the 128-byte
+// swizzled K-major layout.  The field's weight image (all layers, already in
+// the swizzled layout, built once by launch_pack_tc) is copied to shared
+// memory by the bulk-copy (TMA) engine whenever the field changes; a CTA
+// walks a contiguous range of the field-sorted tiles so weights are reused.
+//
+// Layer shapes (K padded to the MMA's 16, N to a multiple of 16):
+//   L1      X = [F(x_loc) (63) | 1]            K = 64      N = W      (bias folded)
+//   hidden  X = h                              K = W       N = W
+//   head    X = h_H                            K = W       N = W + 16 (W features, then density)
+//   colour  X = [feat (W) | F(d) (27) | 1 | 0] K = W + 32  N = W      (bias folded)
+//   output  X = g                              K = W       N = 16     (3 used)
 #include "internal.cuh"
+
 namespace roam {
-bool tc_supported(int, int) { return false; }
-int64_t tc_image_bytes(int, int) { return 0; }
-int tc_bias_count(int, int) { return 0; }
+
+namespace {
+
+constexpr int kEpiWarps = 4;
+constexpr int kThreads = (kEpiWarps + 1) * 32;    // 4 epilogue warps + 1 MMA warp
+constexpr int kMmaWarp = kEpiWarps;
+constexpr unsigned long long kWaitNs = 2000000000ull;   // 2 s per wait
+
+__host__ __device__ constexpr int cdiv(int a, int b) { return (a + b - 1) / b; }
+
+// ---- shapes of the weight image ----
+template <int W, int H>
+struct TcShape {
+    static constexpr int N_HEAD = W + 16;
+    static constexpr int K_COL = W + 32;
+    static constexpr int N_OUT = 16;
+    static constexpr int kLayers = H + 3;
+    __host__ __device__ static constexpr int K(int l) { return l == 0 ? 64 : (l == H + 1 ? K_COL : W); }
+    __host__ __device__ static constexpr int N(int l) { return l == H ? N_HEAD : (l == H + 2 ? N_OUT : W); }
+    __host__ __device__ static constexpr int chunks(int l) { return cdiv(K(l), 64); }
+    __host__ __device__ static constexpr int bytes(int l) { return chunks(l) * N(l) * 128; }
+    __host__ __device__ static constexpr int offset(int l)
+    {
+        int o = 0;
+        for (int i = 0; i < l; ++i) o += bytes(i);
+        return o;
+    }
+    static constexpr int kImageBytes = offset(H + 3);
+    static constexpr int kXChunks = cdiv(K_COL, 64) > 1 ? cdiv(K_COL, 64) : 1;
+    static constexpr int kXBytes = kXChunks * 128 * 128;
+    static constexpr int kNBias = ((H - 1) * W + W + 1 + 3 + 3) & ~3;
+    static constexpr int kTmemCols = N_HEAD <= 32 ? 32 : (N_HEAD <= 64 ? 64 : (N_HEAD <= 128 ? 128 : 256));
+    static constexpr int kSmem = 1024 + kXBytes + kImageBytes + 64;
+};
+
+// byte offset of element (n, k) in a K-major, 128B-swizzled operand whose
+// K-chunks of 64 elements are stored as consecutive [rows][128 B] regions
+__host__ __device__ inline int swz_offset(int n, int k, int rows)
+{
+    const int chunk = k >> 6, kk = k & 63;
+    return chunk * rows * 128 + (n >> 3) * 1024 + (n & 7) * 128 + ((((kk >> 3) ^ (n & 7)) & 7) << 4) + (kk & 7) * 2;
+}
+
+// ---- PTX wrappers ----
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(uint64_t *bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ unsigned long long now_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Waits for the phase of `parity` to complete; gives up after kWaitNs or as
+// soon as another thread has flagged an abort.  Returns false on give-up.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *abort_flag,
+                                          uint32_t *status, bool drain = false)
+{
+    if (mbar_try(bar, parity)) return true;
+    const unsigned long long t0 = now_ns();
+    for (uint32_t it = 0;; ++it) {
+        if (mbar_try(bar, parity)) return true;
+        if ((it & 63u) == 63u) {
+            if (*abort_flag && !drain) return false;
+            if (now_ns() - t0 > kWaitNs) {
+                *abort_flag = 1;
+                atomicOr(status, kStatusTimeout);
+                return false;
+            }
+        }
+    }
+}
+
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+
+// shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups
+// 1024 bytes apart
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)1 << 16;                 // leading byte offset (unused for swizzled K-major)
+    d |= (uint64_t)(1024 >> 4) << 32;       // stride byte offset
+    d |= (uint64_t)1 << 46;                 // descriptor version
+    d |= (uint64_t)2 << 61;                 // 128-byte swizzle
+    return d;
+}
+
+// instruction descriptor: kind::f16, A = B = BF16, D = F32, both K-major, M = 128
+__host__ __device__ constexpr uint32_t idesc_bf16(int N)
+{
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+}
+
+__device__ __forceinline__ void umma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+}
+
+__device__ __forceinline__ void umma_commit(uint64_t *bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16])
+{
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ uint32_t pack_bf16(float a, float b)
+{
+    uint32_t r;
+    asm("cvt.rn.bf16x2.f32 %0, %2, %1;" : "=r"(r) : "f"(a), "f"(b));
+    return r;
+}
+
+// 8 consecutive BF16 columns [c8*8, c8*8+8) of row `row` of a swizzled X
+__device__ __forceinline__ void st_x8(uint8_t *X, int row, int c8, uint4 v)
+{
+    const int chunk = c8 >> 3, cc = c8 & 7;
+    uint8_t *p = X + chunk * 16384 + (row >> 3) * 1024 + (row & 7) * 128 + (((cc ^ (row & 7)) & 7) << 4);
+    *reinterpret_cast<uint4 *>(p) = v;
+}
+
+__device__ __forceinline__ void st_x16(uint8_t *X, int row, int col, const float (&v)[16])
+{
+    uint4 a, b;
+    a.x = pack_bf16(v[0], v[1]); a.y = pack_bf16(v[2], v[3]); a.z = pack_bf16(v[4], v[5]); a.w = pack_bf16(v[6], v[7]);
+    b.x = pack_bf16(v[8], v[9]); b.y = pack_bf16(v[10], v[11]); b.z = pack_bf16(v[12], v[13]);
+    b.w = pack_bf16(v[14], v[15]);
+    st_x8(X, row, col >> 3, a);
+    st_x8(X, row, (col >> 3) + 1, b);
+}
+
+// sin(pi y), cos(pi y) for |y| up to 2^9: exact reduction of y to
+// r in [-1, 1] (y - 2 rint(y/2) is exact in FP32), then the hardware
+// approximations on [-pi, pi] (absolute error < 1e-6).
+__device__ __forceinline__ void sincospi_fast(float y, float &s, float &c)
+{
+    const float r = y - 2.0f * rintf(0.5f * y);
+    __sincosf(3.14159265358979f * r, &s, &c);
+}
+
+// F(v) for one coordinate, frequencies 2^0 .. 2^(L-1): direct evaluation at
+// k = 0 and k = 5, angle doubling (sin 2a = 2 sin a cos a,
+// cos 2a = 1 - 2 sin^2 a) in between, so the doubling error stays below
+// 2^4 times the direct error.
+template <int L>
+__device__ __forceinline__ void encode1(float v, float (&s)[L], float (&c)[L])
+{
+#pragma unroll
+    for (int k = 0; k < L; ++k) {
+        if (k == 0 || k == 5) {
+            sincospi_fast(ldexpf(v, k), s[k], c[k]);
+        } else {
+            const float sp = s[k - 1], cp = c[k - 1];
+            s[k] = 2.0f * sp * cp;
+            c[k] = fmaf(-2.0f * sp, sp, 1.0f);
+        }
+    }
+}
+
+__device__ __forceinline__ float softplus_f(float s) { return s > 20.f ? s : log1pf(__expf(s)); }
+__device__ __forceinline__ float sigmoid_f(float s) { return 1.f / (1.f + __expf(-s)); }
+
+template <int W, int H>
+__global__ void __launch_bounds__(kThreads, 1) k_mlp_tc(MlpWeights w, SampleSrc src, BucketBufs b, Counters *ctr,
+                                                        float4 *out)
+{
+    using S = TcShape<W, H>;
+    extern __shared__ uint8_t smem_raw[];
+    __shared__ uint64_t bar_x, bar_d, bar_w, bar_fin;
+    __shared__ uint32_t tmem_slot;
+    __shared__ int abort_flag;
+
+    const uint32_t base = (smem_u32(smem_raw) + 1023u) & ~1023u;
+    uint8_t *X = smem_raw + (base - smem_u32(smem_raw));
+    uint8_t *IMG = X + S::kXBytes;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    volatile int *abortp = &abort_flag;
+    uint32_t *status = &ctr->status;
+
+    if (threadIdx.x == 0) {
+        mbar_init(&bar_x, kEpiWarps * 32);
+        mbar_init(&bar_d, 1);
+        mbar_init(&bar_w, 1);
+        mbar_init(&bar_fin, 1);
+        abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == kMmaWarp) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
+                     "r"(S::kTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_slot;
+
+    const uint32_t n_tiles = ctr->n_tiles;
+    const uint32_t t0 = (uint32_t)((uint64_t)n_tiles * blockIdx.x / gridDim.x);
+    const uint32_t t1 = (uint32_t)((uint64_t)n_tiles * (blockIdx.x + 1) / gridDim.x);
+
+    if (warp == kMmaWarp) {
+        // ------------------------------------------------------------ MMA
+        if (lane == 0) {
+            uint32_t x_waits = 0, d_issued = 0, w_loads = 0;
+            uint32_t cur_field = 0xffffffffu;
+            bool w_pending = false;
+            for (uint32_t t = t0; t < t1 && !*abortp; ++t) {
+                const uint32_t f = b.tiles[t].field;
+                if (f != cur_field) {
+                    // the previous tile's last MMA must be done before the image is overwritten
+                    if (d_issued && !mbar_wait(&bar_d, (d_issued - 1) & 1u, abortp, status)) break;
+                    mbar_expect_tx(&bar_w, (uint32_t)S::kImageBytes);
+                    const uint8_t *g = reinterpret_cast<const uint8_t *>(w.wimg) + (int64_t)f * w.img_bytes;
+                    for (int off = 0; off < S::kImageBytes; off += 16384) {
+                        const int n = S::kImageBytes - off < 16384 ? S::kImageBytes - off : 16384;
+                        bulk_g2s(IMG + off, g + off, (uint32_t)n, &bar_w);
+                    }
+                    w_pending = true;
+                    cur_field = f;
+                }
+#pragma unroll 1
+                for (int l = 0; l < S::kLayers; ++l) {
+                    if (!mbar_wait(&bar_x, x_waits & 1u, abortp, status)) break;
+                    ++x_waits;
+                    if (w_pending) {
+                        if (!mbar_wait(&bar_w, w_loads & 1u, abortp, status)) break;
+                        ++w_loads;
+                        w_pending = false;
+                    }
+                    tc_fence_after();
+                    const int K = S::K(l), N = S::N(l);
+                    const uint32_t idesc = idesc_bf16(N);
+                    const uint32_t xa = smem_u32(X), ba = smem_u32(IMG + S::offset(l));
+#pragma unroll 1
+                    for (int ks = 0; ks < K / 16; ++ks) {
+                        const int ch = ks >> 2, kin = ks & 3;
+                        const uint64_t ad = sdesc(xa + ch * 16384 + kin * 32);
+                        const uint64_t bd = sdesc(ba + ch * N * 128 + kin * 32);
+                        umma(tmem, ad, bd, idesc, ks > 0 ? 1u : 0u);
+                    }
+                    umma_commit(&bar_d);
+                    ++d_issued;
+                }
+            }
+            // drain: every issued MMA and bulk copy completes before TMEM is freed
+            umma_commit(&bar_fin);
+            mbar_wait(&bar_fin, 0, abortp, status, true);
+            if (w_pending) mbar_wait(&bar_w, w_loads & 1u, abortp, status, true);
+        }
+        __syncwarp();
+    } else {
+        // ------------------------------------------------------- epilogue
+        const int row = warp * 32 + lane;                 // TMEM lane == tile row
+        const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
+        uint32_t d_waits = 0;
+        const float sig_scale = w.sigma_scale;
+        for (uint32_t t = t0; t < t1 && !*abortp; ++t) {
+            const Tile tl = b.tiles[t];
+            const bool valid = (uint32_t)row < tl.count;
+            uint32_t idx = 0;
+            float px = 0.f, py = 0.f, pz = 0.f, dx = 0.f, dy = 0.f, dz = 1.f;
+            if (valid) {
+                idx = b.sorted[tl.start + row];
+                if (src.mode == 0) {
+                    const uint32_t col = idx >> 5;
+                    const uint32_t i = (col / (uint32_t)src.R) * 32u + (idx & 31u);
+                    const uint32_t ray = src.live ? src.live[i] : i;
+                    const uint32_t j = src.recs[idx] & 0xffffu;
+                    const float tt = ((float)j + 0.5f) * src.delta;
+                    const float4 o = src.st.orig[ray], d = src.st.dir[ray];
+                    px = fmaf(tt, d.x, o.x); py = fmaf(tt, d.y, o.y); pz = fmaf(tt, d.z, o.z);
+                    dx = d.x; dy = d.y; dz = d.z;
+                } else {
+                    px = src.p[3 * (int64_t)idx]; py = src.p[3 * (int64_t)idx + 1]; pz = src.p[3 * (int64_t)idx + 2];
+                    dx = src.d[3 * (int64_t)idx]; dy = src.d[3 * (int64_t)idx + 1]; dz = src.d[3 * (int64_t)idx + 2];
+                }
+            }
+            const float *aff = w.affine + 6 * (int64_t)tl.field;
+            const float *bias = w.bias + (int64_t)tl.field * w.nb;
+            // ---- L1 input: [F(x_loc) | 1] ----
+            {
+                const float xl[3] = {fmaf(__ldg(aff + 0), px, __ldg(aff + 3)), fmaf(__ldg(aff + 1), py, __ldg(aff + 4)),
+                                     fmaf(__ldg(aff + 2), pz, __ldg(aff + 5))};
+                float e[64];
+                e[0] = xl[0]; e[1] = xl[1]; e[2] = xl[2];
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    float s[10], c[10];
+                    encode1<10>(xl[a], s, c);
+#pragma unroll
+                    for (int k = 0; k < 10; ++k) {
+                        e[3 + 6 * k + a] = s[k];
+                        e[6 + 6 * k + a] = c[k];
+                    }
+                }
+                e[63] = 1.0f;
+                if (!valid) {
+#pragma unroll
+                    for (int q = 0; q < 64; ++q) e[q] = 0.f;
+                }
+#pragma unroll
+                for (int c16 = 0; c16 < 4; ++c16) {
+                    float v[16];
+#pragma unroll
+                    for (int q = 0; q < 16; ++q) v[q] = e[16 * c16 + q];
+                    st_x16(X, row, 16 * c16, v);
+                }
+            }
+            fence_proxy_async();
+            mbar_arrive(&bar_x);
+            float sigma = 0.f;
+#pragma unroll 1
+            for (int l = 0; l < S::kLayers; ++l) {
+                // all lanes of the warp leave together (tcgen05.ld is warp-collective)
+                if (!__all_sync(0xffffffffu, mbar_wait(&bar_d, d_waits & 1u, abortp, status))) break;
+                ++d_waits;
+                tc_fence_after();
+                if (l < H + 2) {
+                    // layers writing the next X: L1, hidden, head, colour
+                    const float *bl = nullptr;
+                    if (l >= 1 && l < H) bl = bias + (l - 1) * W;          // hidden
+                    else if (l == H) bl = bias + (H - 1) * W;              // head features, then density
+#pragma unroll
+                    for (int c0 = 0; c0 < W; c0 += 16) {
+                        float v[16];
+                        tmem_ld16(trow + c0, v);
+                        if (bl) {
+#pragma unroll
+                            for (int q = 0; q < 16; ++q) v[q] += __ldg(bl + c0 + q);
+                        }
+                        if (l != H) {
+#pragma unroll
+                            for (int q = 0; q < 16; ++q) v[q] = fmaxf(v[q], 0.f);
+                        }
+                        st_x16(X, row, c0, v);
+                    }
+                    if (l == H) {
+                        float v[16];
+                        tmem_ld16(trow + W, v);
+                        const float s = v[0] + __ldg(bl + W);
+                        sigma = sig_scale * (w.act == ROAM_RELU ? fmaxf(s, 0.f) : softplus_f(s));
+                    }
+                    if (l == 0) {
+                        // colour-layer tail of X: [F(d) | 1 | 0 0 0 0] at columns W .. W+31
+                        float e[32];
+                        e[0] = dx; e[1] = dy; e[2] = dz;
+                        const float dv[3] = {dx, dy, dz};
+#pragma unroll
+                        for (int a = 0; a < 3; ++a) {
+                            float s[4], c[4];
+                            encode1<4>(dv[a], s, c);
+#pragma unroll
+                            for (int k = 0; k < 4; ++k) {
+                                e[3 + 6 * k + a] = s[k];
+                                e[6 + 6 * k + a] = c[k];
+                            }
+                        }
+                        e[27] = valid ? 1.0f : 0.0f;
+                        e[28] = e[29] = e[30] = e[31] = 0.f;
+                        float v[16];
+#pragma unroll
+                        for (int q = 0; q < 16; ++q) v[q] = e[q];
+                        st_x16(X, row, W, v);
+#pragma unroll
+                        for (int q = 0; q < 16; ++q) v[q] = e[16 + q];
+                        st_x16(X, row, W + 16, v);
+                    }
+                    tc_fence_before();
+                    fence_proxy_async();
+                    mbar_arrive(&bar_x);
+                } else {
+                    // output layer: rgb = sigmoid(z + b)
+                    float v[16];
+                    tmem_ld16(trow, v);
+                    tc_fence_before();
+                    const float *bo = bias + (H - 1) * W + W + 1;
+                    if (valid)
+                        out[idx] = make_float4(sigma, sigmoid_f(v[0] + __ldg(bo + 0)), sigmoid_f(v[1] + __ldg(bo + 1)),
+                                               sigmoid_f(v[2] + __ldg(bo + 2)));
+                }
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == kMmaWarp) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(S::kTmemCols)
+                     : "memory");
+    }
+}
+
+// API layout -> BF16 image of every layer + FP32 bias table.
+template <int W, int H>
+__global__ void k_pack_tc(const float *__restrict__ w32, int n_fields, int64_t P, uint8_t *__restrict__ img,
+                          int64_t img_bytes, float *__restrict__ bias, int nb)
+{
+    using S = TcShape<W, H>;
+    // offsets of the API layout
+    const int64_t o_l1 = 0, o_hid = (int64_t)W * kPeX + W;
+    const int64_t o_head = o_hid + (int64_t)(H - 1) * (W * W + W);
+    const int64_t o_col = o_head + (int64_t)(1 + W) * W + (1 + W);
+    const int64_t o_out = o_col + (int64_t)W * (W + kPeD) + W;
+    const int64_t per = img_bytes / 2;           // BF16 elements per field image
+    const int64_t n = (int64_t)n_fields * per;
+    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t f = g / per;
+        const int byte = (int)((g % per) * 2);
+        // find the layer and (n, k) of this byte
+        int l = 0;
+        while (l + 1 < S::kLayers && byte >= S::offset(l + 1)) ++l;
+        const int lb = byte - S::offset(l);
+        const int N = S::N(l), K = S::K(l);
+        const int chunk = lb / (N * 128);
+        const int in_chunk = lb % (N * 128);
+        const int nrow = (in_chunk / 1024) * 8 + (in_chunk % 1024) / 128;
+        const int sw16 = (in_chunk % 128) / 16;
+        const int k8 = (sw16 ^ (nrow & 7)) & 7;
+        const int k = chunk * 64 + k8 * 8 + (in_chunk % 16) / 2;
+        const float *wf = w32 + f * P;
+        float v = 0.f;
+        if (k < K) {
+            if (l == 0) {
+                if (k < kPeX) v = wf[o_l1 + (int64_t)nrow * kPeX + k];
+                else if (k == kPeX) v = wf[o_l1 + (int64_t)W * kPeX + nrow];
+            } else if (l < H) {
+                const int64_t ob = o_hid + (int64_t)(l - 1) * (W * W + W);
+                v = wf[ob + (int64_t)nrow * W + k];
+            } else if (l == H) {
+                if (nrow < W) v = wf[o_head + (int64_t)(1 + nrow) * W + k];
+                else if (nrow == W) v = wf[o_head + k];
+            } else if (l == H + 1) {
+                const int kc = W + kPeD;
+                if (k < kc) v = wf[o_col + (int64_t)nrow * kc + k];
+                else if (k == kc) v = wf[o_col + (int64_t)W * kc + nrow];
+            } else {
+                if (nrow < 3) v = wf[o_out + (int64_t)nrow * W + k];
+            }
+        }
+        const uint32_t bits = __float_as_uint(v);
+        // round to nearest even
+        const uint32_t r = bits + 0x7fffu + ((bits >> 16) & 1u);
+        reinterpret_cast<uint16_t *>(img)[g] = (uint16_t)(r >> 16);
+    }
+    // bias table: hidden (H-1)*W, head features W, head density 1, output 3
+    const int64_t nbt = (int64_t)n_fields * nb;
+    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < nbt; g += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t f = g / nb;
+        const int q = (int)(g % nb);
+        const float *wf = w32 + f * P;
+        float v = 0.f;
+        if (q < (H - 1) * W) {
+            const int l = q / W, o = q % W;
+            v = wf[o_hid + (int64_t)l * (W * W + W) + (int64_t)W * W + o];
+        } else if (q < (H - 1) * W + W) {
+            v = wf[o_head + (int64_t)(1 + W) * W + 1 + (q - (H - 1) * W)];
+        } else if (q == (H - 1) * W + W) {
+            v = wf[o_head + (int64_t)(1 + W) * W];
+        } else if (q < (H - 1) * W + W + 4) {
+            v = wf[o_out + 3 * W + (q - (H - 1) * W - W - 1)];
+        }
+        bias[g] = v;
+    }
+}
+
+template <int W, int H>
+void launch_t(const MlpWeights &w, const SampleSrc &src, const BucketBufs &b, Counters *ctr, float4 *out, int n_sm,
+              cudaStream_t s)
+{
+    using S = TcShape<W, H>;
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_mlp_tc<W, H>, cudaFuncAttributeMaxDynamicSharedMemorySize, S::kSmem);
+        attr = true;
+    }
+    const int per_sm = (2 * (S::kSmem + 1024) <= 227 * 1024 && 2 * S::kTmemCols <= 512) ? 2 : 1;
+    k_mlp_tc<W, H><<<n_sm * per_sm, kThreads, S::kSmem, s>>>(w, src, b, ctr, out);
+}
+
+}  // namespace
+
+bool tc_supported(int W, int H)
+{
+    if (H < 1 || H > 4) return false;
+    if (W == 32) return TcShape<32, 4>::kSmem <= 227 * 1024;
+    if (W == 64) return TcShape<64, 4>::kSmem <= 227 * 1024;
+    return false;   // W = 128: the full image does not fit next to the activations
+}
+
+int64_t tc_image_bytes(int W, int H)
+{
+#define ROAM_CASE(WW, HH) \
+    if (W == WW && H == HH) return TcShape<WW, HH>::kImageBytes;
+    ROAM_CASE(32, 1) ROAM_CASE(32, 2) ROAM_CASE(32, 3) ROAM_CASE(32, 4)
+    ROAM_CASE(64, 1) ROAM_CASE(64, 2) ROAM_CASE(64, 3) ROAM_CASE(64, 4)
+#undef ROAM_CASE
+    return 0;
+}
+
+int tc_bias_count(int W, int H) { return ((H - 1) * W + W + 1 + 3 + 3) & ~3; }
+
 int tc_tile_samples() { return 128; }
-void launch_pack_tc(const float *, int, int, int, int64_t, void *, int64_t, float *, int, cudaStream_t) {}
-void launch_mlp_tc(const MlpWeights &, const SampleSrc &, const BucketBufs &, Counters *, float4 *, int, cudaStream_t) {}
+
+void launch_pack_tc(const float *w32, int n_fields, int W, int H, int64_t P, void *wimg, int64_t img_bytes,
+                    float *bias, int nb, cudaStream_t s)
+{
+#define ROAM_CASE(WW, HH) \
+    if (W == WW && H == HH) { k_pack_tc<WW, HH><<<2048, 256, 0, s>>>(w32, n_fields, P, (uint8_t *)wimg, img_bytes, bias, nb); return; }
+    ROAM_CASE(32, 1) ROAM_CASE(32, 2) ROAM_CASE(32, 3) ROAM_CASE(32, 4)
+    ROAM_CASE(64, 1) ROAM_CASE(64, 2) ROAM_CASE(64, 3) ROAM_CASE(64, 4)
+#undef ROAM_CASE
+}
+
+void launch_mlp_tc(const MlpWeights &w, const SampleSrc &src, const BucketBufs &b, Counters *ctr, float4 *out,
+                   int n_sm, cudaStream_t s)
+{
+#define ROAM_CASE(WW, HH) \
+    if (w.W == WW && w.H == HH) { launch_t<WW, HH>(w, src, b, ctr, out, n_sm, s); return; }
+    ROAM_CASE(32, 1) ROAM_CASE(32, 2) ROAM_CASE(32, 3) ROAM_CASE(32, 4)
+    ROAM_CASE(64, 1) ROAM_CASE(64, 2) ROAM_CASE(64, 3) ROAM_CASE(64, 4)
+#undef ROAM_CASE
+}
+
 }  // namespace roam

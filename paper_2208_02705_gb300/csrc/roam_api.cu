@@ -111,7 +111,7 @@ struct roam_ctx {
     DBuf<float> w32, wt, bias, adam_m, adam_v;
     DBuf<uint8_t> wimg;
     // per-call workspace
-    DBuf<float4> orig, dir, acc, sr;
+    DBuf<float4> orig, dir, dir_lo, acc, sr;
     DBuf<float2> tw;
     DBuf<uint32_t> j_next, j_end, n_kept, live0, live1, cnt, recs, sorted, hist, offsets, cursor, scratch_u32;
     DBuf<Tile> tiles;
@@ -286,7 +286,8 @@ roam_status upload_cams(roam_ctx *c, const roam_camera *cams, int n_views, float
         d.height = k.height;
         memcpy(d.R, k.R, sizeof(d.R));
         memcpy(d.o, k.o, sizeof(d.o));
-        d.inv_f = k.model == ROAM_PERSPECTIVE ? (float)(std::tan(0.5 * (double)k.fov_h) / (0.5 * k.width)) : 0.f;
+        d.inv_f64 = k.model == ROAM_PERSPECTIVE ? std::tan(0.5 * (double)k.fov_h) / (0.5 * k.width) : 0.0;
+        d.inv_f = (float)d.inv_f64;
         d.pix_start = (uint32_t)total;
         total += (int64_t)k.width * k.height;
         if (total > (int64_t)0x7fffffff) return fail(ROAM_ERR_ARG, "too many pixels");
@@ -305,6 +306,7 @@ roam_status ensure_rays(roam_ctx *c, int64_t n_rays, int R)
     const size_t n = (size_t)n_rays;
     ROAM_TRY(ensure(c->orig, n));
     ROAM_TRY(ensure(c->dir, n));
+    ROAM_TRY(ensure(c->dir_lo, n));
     ROAM_TRY(ensure(c->acc, n));
     ROAM_TRY(ensure(c->tw, n));
     ROAM_TRY(ensure(c->j_next, n));
@@ -337,6 +339,7 @@ RayState state_of(roam_ctx *c)
     RayState st;
     st.orig = c->orig.p;
     st.dir = c->dir.p;
+    st.dir_lo = c->dir_lo.p;
     st.j_next = c->j_next.p;
     st.j_end = c->j_end.p;
     st.n_kept = c->n_kept.p;
@@ -385,6 +388,7 @@ roam_status run_rounds(roam_ctx *c, const uint32_t *rays, int64_t n_rays, const 
     mp.n_max = o->n_max;
     mp.delta = o->delta;
     mp.flat = 0;
+    mp.accurate = o->precision == ROAM_F32;
     mp.st = state_of(c);
     mp.cnt = c->cnt.p;
     mp.recs = c->recs.p;
@@ -415,6 +419,7 @@ roam_status run_rounds(roam_ctx *c, const uint32_t *rays, int64_t n_rays, const 
         src.R = R;
         src.st = mp.st;
         src.delta = o->delta;
+        src.accurate = mp.accurate;
         {
             ProfScope ps(c, o->precision == ROAM_BF16 ? P_MLP_BF16 : P_MLP_F32, s);
             ROAM_TRY(run_mlp(c, o->precision, src, b, c->sr.p, s));
@@ -481,7 +486,7 @@ roam_status roam_destroy(roam_ctx *c)
     release(c->bits); release(c->prefix); release(c->brick); release(c->block_sums);
     release(c->labels); release(c->affine);
     release(c->w32); release(c->wt); release(c->bias); release(c->adam_m); release(c->adam_v); release(c->wimg);
-    release(c->orig); release(c->dir); release(c->acc); release(c->sr); release(c->tw);
+    release(c->orig); release(c->dir); release(c->dir_lo); release(c->acc); release(c->sr); release(c->tw);
     release(c->j_next); release(c->j_end); release(c->n_kept); release(c->live0); release(c->live1);
     release(c->cnt); release(c->recs); release(c->sorted); release(c->hist); release(c->offsets);
     release(c->cursor); release(c->scratch_u32); release(c->tiles);

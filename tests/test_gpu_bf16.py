@@ -1,0 +1,163 @@
+"""Parity of the tcgen05 BF16 MLP path with the FP64 oracle.
+
+BF16 rounds every activation and weight to 8 significant bits (relative
+2^-9 per rounding); the bar is the one stated for this path: rendered
+colours >= 40 dB PSNR against the oracle and <= 2e-2 max abs.  Per-sample
+MLP outputs are held to bounds derived from the same rounding: colours
+within 2e-2, density within 5% (of max(1, sigma))."""
+import math
+
+import numpy as np
+import pytest
+
+import fixtures as F
+import oracle as O
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def roam():
+    import paper_2208_02705_gb300 as roam
+    from paper_2208_02705_gb300 import build
+    build.build()
+    return roam
+
+
+def _points_in_fields(wl, n, rng, fields=None):
+    boxes = wl.part.boxes
+    f = rng.integers(0, boxes.shape[0], n) if fields is None else fields
+    lo = boxes[f, 0, :] * wl.scene.vox
+    hi = boxes[f, 1, :] * wl.scene.vox
+    p = lo + rng.uniform(0, 1, (n, 3)) * (hi - lo)
+    d = rng.normal(size=(n, 3))
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    return p.astype(np.float32), d.astype(np.float32), f.astype(np.uint16)
+
+
+def _psnr(a, b):
+    mse = float(((a - b) ** 2).mean())
+    return 10 * math.log10(1.0 / mse) if mse > 0 else float("inf")
+
+
+@pytest.mark.parametrize("W,H,n", [(32, 2, 1531), (64, 3, 2049), (64, 1, 300), (32, 4, 129), (64, 4, 1)])
+def test_mlp_eval_bf16_matches_oracle(roam, room32, W, H, n):
+    w = F.xavier_weights(1, F.ROLE_STUDENT, room32.part.n_fields, W, H, bias_scale=0.3)
+    r = roam.Roam(0)
+    r.load_grid(room32.scene.bits, room32.scene.dims, room32.scene.origin, room32.scene.vox)
+    r.load_fields(room32.part.field_of_rank, room32.affine)
+    r.load_weights(w, W, H, room32.sigma_scale)
+    rng = np.random.default_rng(W * 10 + H)
+    p, d, f = _points_in_fields(room32, n, rng)
+    args = (torch.from_numpy(p).cuda(), torch.from_numpy(d).cuda(), torch.from_numpy(f.astype(np.int16)).cuda())
+    out = r.mlp_eval(*args, roam.ROAM_BF16)
+    out32 = r.mlp_eval(*args, roam.ROAM_F32)
+    torch.cuda.synchronize()
+    r.check()
+    out = out.cpu().numpy().astype(np.float64)
+    out32 = out32.cpu().numpy().astype(np.float64)
+    ref = np.array([O.mlp(w[f[i]], W, H, room32.sigma_scale, room32.affine[f[i]], p[i].astype(np.float64),
+                          d[i].astype(np.float64)) for i in range(n)])
+    assert np.all(np.isfinite(out))
+    assert np.abs(out[:, 1:] - ref[:, 1:]).max() <= 2e-2
+    assert np.all(np.abs(out[:, 0] - ref[:, 0]) <= 5e-2 * np.maximum(1.0, ref[:, 0]))
+    # BF16 is a rounding of the same function: it tracks FP32 far better than
+    # a wrong layout would (which gives O(1) differences)
+    assert np.abs(out[:, 1:] - out32[:, 1:]).mean() <= 3e-3
+    r.close()
+
+
+def test_mlp_eval_bf16_one_field_many_tiles(roam, room32):
+    """A long run of one field (many consecutive tiles in one CTA, weights
+    loaded once) next to single-sample fields (one partial tile each)."""
+    W, H = 64, 3
+    w = F.xavier_weights(1, F.ROLE_STUDENT, room32.part.n_fields, W, H, bias_scale=0.2)
+    r = roam.Roam(0)
+    r.load_grid(room32.scene.bits, room32.scene.dims, room32.scene.origin, room32.scene.vox)
+    r.load_fields(room32.part.field_of_rank, room32.affine)
+    r.load_weights(w, W, H, room32.sigma_scale)
+    rng = np.random.default_rng(1)
+    fields = np.concatenate([np.full(20000, 3), [0, 1, 2, 4, 5, 6, 7]])
+    p, d, f = _points_in_fields(room32, fields.size, rng, fields)
+    out = r.mlp_eval(torch.from_numpy(p).cuda(), torch.from_numpy(d).cuda(),
+                     torch.from_numpy(f.astype(np.int16)).cuda(), roam.ROAM_BF16)
+    torch.cuda.synchronize()
+    out = out.cpu().numpy().astype(np.float64)
+    pick = np.concatenate([rng.choice(20000, 300, replace=False), np.arange(20000, fields.size)])
+    for i in pick:
+        ref = O.mlp(w[f[i]], W, H, room32.sigma_scale, room32.affine[f[i]], p[i].astype(np.float64),
+                    d[i].astype(np.float64))
+        assert np.abs(out[i, 1:] - ref[1:]).max() <= 2e-2
+        assert abs(out[i, 0] - ref[0]) <= 5e-2 * max(1.0, ref[0])
+    r.close()
+
+
+def test_render_room32_bf16(roam, room32, room32_grid):
+    r = roam.Roam(0)
+    r.load_workload(room32)
+    opts = roam.render_opts(room32.delta, room32.n_max, precision=roam.ROAM_BF16)
+    rgb, depth, op = r.render(room32.cams, opts)
+    torch.cuda.synchronize()
+    r.check()
+    ref = O.render(room32_grid, room32.weights, room32.affine, room32.W, room32.H, room32.sigma_scale,
+                   F.camera_array(room32.cams), None, room32.delta, room32.n_max)
+    rgb = rgb.cpu().numpy().astype(np.float64)
+    assert _psnr(rgb, ref["rgb"]) >= 40.0
+    assert np.abs(rgb - ref["rgb"]).max() <= 2e-2
+    r.close()
+
+
+def test_render_floor256_bf16_sampled(roam):
+    """Full-size render of both views in the benchmark's configuration;
+    sampled pixels against the oracle."""
+    wl = F.floor256()
+    g = O.Grid(wl.scene, wl.part)
+    r = roam.Roam(0)
+    r.load_workload(wl)
+    opts = roam.render_opts(wl.delta, wl.n_max, precision=roam.ROAM_BF16)
+    rgb, depth, op = r.render(wl.cams, opts)
+    torch.cuda.synchronize()
+    r.check()
+    rng = np.random.default_rng(23)
+    sizes = [c.n_pixels for c in wl.cams]
+    starts = np.concatenate([[0], np.cumsum(sizes)])
+    n = 6000
+    view = rng.integers(0, 2, n)
+    pix = np.array([rng.integers(0, sizes[v]) for v in view])
+    rays = np.stack([view, pix], 1).astype(np.uint32)
+    ref = O.render(g, wl.weights, wl.affine, wl.W, wl.H, wl.sigma_scale, F.camera_array(wl.cams), rays,
+                   wl.delta, wl.n_max)
+    got = rgb.cpu().numpy()[starts[view] + pix].astype(np.float64)
+    assert _psnr(got, ref["rgb"]) >= 40.0
+    assert np.abs(got - ref["rgb"]).max() <= 2e-2
+    r.close()
+
+
+def test_bf16_round_schedule_is_invisible(roam, room32):
+    r = roam.Roam(0)
+    r.load_workload(room32)
+    outs = []
+    for R in (3, 16, 64):
+        rgb, depth, op = r.render(room32.cams, roam.render_opts(room32.delta, room32.n_max,
+                                                                precision=roam.ROAM_BF16, round_size=R))
+        outs.append(rgb.clone())
+    torch.cuda.synchronize()
+    assert torch.equal(outs[0], outs[1]) and torch.equal(outs[0], outs[2])
+    r.close()
+
+
+def test_width128_bf16_reports_unsupported(roam, room32):
+    r = roam.Roam(0)
+    r.load_grid(room32.scene.bits, room32.scene.dims, room32.scene.origin, room32.scene.vox)
+    r.load_fields(room32.part.field_of_rank, room32.affine)
+    r.load_weights(F.xavier_weights(1, 2, room32.part.n_fields, 128, 2), 128, 2, room32.sigma_scale)
+    with pytest.raises(roam.RoamError) as e:
+        r.render(room32.cams, roam.render_opts(room32.delta, room32.n_max, precision=roam.ROAM_BF16))
+    assert e.value.status == -7
+    # the FP32 path serves every width
+    rgb, _, _ = r.render(room32.cams, roam.render_opts(room32.delta, room32.n_max))
+    torch.cuda.synchronize()
+    assert torch.isfinite(rgb).all()
+    r.close()

@@ -170,8 +170,10 @@ def test_mlp_eval_f32_matches_oracle(roam, room32):
     for i in range(n):
         ref = O.mlp(w[f[i]], W, H, room32.sigma_scale, room32.affine[f[i]], p[i].astype(np.float64),
                     d[i].astype(np.float64))
-        scale = np.array([max(1.0, ref[0]), 1, 1, 1])
-        assert np.all(np.abs(out[i] - ref) <= 2e-5 * scale), (i, out[i], ref)
+        # FP32 rounding of x_loc (6e-8) is amplified by the 2^9 pi encoding
+        # frequency to ~1e-4 in the features; sigma carries sigma_scale on top
+        assert abs(out[i, 0] - ref[0]) <= 1e-4 * max(1.0, ref[0]), (i, out[i], ref)
+        assert np.all(np.abs(out[i, 1:] - ref[1:]) <= 2e-5), (i, out[i], ref)
     r.close()
 
 
