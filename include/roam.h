@@ -215,6 +215,29 @@ roam_status roam_bucket(roam_ctx *ctx, const uint16_t *keys, int64_t n, uint32_t
 roam_status roam_mlp_eval(roam_ctx *ctx, const float *p, const float *d, const uint16_t *field,
                           int64_t n, int precision, float *out, void *stream);
 
+/* Allocation-free variant of roam_bucket, for callers that may not allocate
+ * device memory: hosts whose own pool allocator owns every device byte, or
+ * frame loops that cannot afford the device-wide synchronisation cudaFree
+ * brings.  (The paper has no counterpart: this is a service of the library.)
+ * Needs no context and never calls cudaMalloc, cudaFree or an allocating
+ * library routine: its scratch is a fixed array of about 96 KiB in device
+ * memory, created when the library is loaded and held by every GPU that
+ * loads it until the process exits.
+ *   keys    device uint16[n], field ids < n_fields (larger ids are dropped)
+ *   n       0 .. 2^31 - 1
+ *   n_fields 1 .. 4096; more gives ROAM_ERR_ARG (the scratch is sized for 4096)
+ *   perm    device uint32[n]: sample indices grouped by field, fields in
+ *           increasing order (order within a field unspecified)
+ *   offsets device uint32[n_fields + 1]: group boundaries
+ * Works on the calling thread's current device and is asynchronous on
+ * `stream`.  The first call on each device looks up the scratch array's
+ * device address (cudaGetSymbolAddress); make that first call before any
+ * stream capture.  All calls share the one array and it keeps the previous
+ * call's contents (each call clears what must start at zero), so calls whose
+ * work overlaps on the GPU -- e.g. on two streams -- race: serialise them. */
+roam_status roam_bucket_static(const uint16_t *keys, int64_t n, int n_fields, uint32_t *perm,
+                               uint32_t *offsets, void *stream);
+
 /* Compositing with early termination (Eq. 4-5) of n_rays rays holding
  * count[r] <= n_max samples: sigma_rgb device float[n_rays][n_max][4]
  * (sigma, r, g, b), t device float[n_rays][n_max] sample depths; outputs as

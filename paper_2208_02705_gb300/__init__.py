@@ -28,7 +28,8 @@ STATUS = {0: "ROAM_OK", -1: "ROAM_ERR_ARG", -2: "ROAM_ERR_OOM", -3: "ROAM_ERR_CU
 ENTRY_POINTS = ("roam_create", "roam_destroy", "roam_last_error", "roam_check", "roam_load_grid",
                 "roam_load_fields", "roam_load_weights", "roam_get_weights", "roam_render", "roam_get_stats",
                 "roam_march", "roam_bucket", "roam_mlp_eval", "roam_composite", "roam_train_forward",
-                "roam_train_backward", "roam_adam_step", "roam_profile", "roam_profile_read")
+                "roam_train_backward", "roam_adam_step", "roam_profile", "roam_profile_read",
+                "roam_bucket_static")
 
 
 class RoamError(RuntimeError):
@@ -101,6 +102,7 @@ def load_library(path: str = LIB_PATH):
     L.roam_train_forward.argtypes = [vp, P(roam_camera), i32, vp, i64, P(roam_render_opts), vp, vp]
     L.roam_train_backward.argtypes = [vp, vp, vp, vp]
     L.roam_adam_step.argtypes = [vp, vp, P(roam_adam_cfg), vp]
+    L.roam_bucket_static.argtypes = [vp, i64, i32, vp, vp, vp]
     L.roam_profile.argtypes = [vp, i32]
     L.roam_profile_read.argtypes = [vp, P(roam_kernel_time), i32, P(ctypes.c_int)]
     for name in ENTRY_POINTS:
@@ -340,6 +342,21 @@ class Roam:
         c = roam_adam_cfg()
         c.lr, c.beta1, c.beta2, c.eps, c.step = float(lr), float(beta1), float(beta2), float(eps), int(step)
         _check(self.L.roam_adam_step(self.h, _ptr(grad), ctypes.byref(c), _stream(stream)))
+
+
+def bucket_static(keys, n_fields: int, stream=None):
+    """roam_bucket_static: bucketing without a context and without any device
+    allocation by the library (its scratch is a fixed device array).  keys is
+    a device int16/uint16 tensor; returns (perm, offsets) tensors, which this
+    Python helper allocates through torch -- a caller that must not allocate
+    passes its own buffers to the C entry point instead."""
+    import torch
+    L = load_library()
+    n = int(keys.shape[0])
+    perm = torch.empty(n, dtype=torch.int32, device=keys.device)
+    offsets = torch.empty(n_fields + 1, dtype=torch.int32, device=keys.device)
+    _check(L.roam_bucket_static(_ptr(keys), n, int(n_fields), _ptr(perm), _ptr(offsets), _stream(stream)))
+    return perm, offsets
 
 
 def render_function():

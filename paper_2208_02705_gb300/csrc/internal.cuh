@@ -153,6 +153,9 @@ void launch_composite_flat(int64_t n_rays, int n_max, const uint32_t *count, con
                            const float *t, float delta, float t_stop, const float *bg, float *rgb,
                            float *depth, float *opacity, uint32_t *n_used, cudaStream_t s);
 
+// sets the calling thread's roam_last_error() message
+void set_error_message(const char *msg);
+
 // tcgen05 BF16 path
 bool tc_supported(int W, int H);
 int64_t tc_image_bytes(int W, int H);

@@ -445,6 +445,10 @@ int round_size(const roam_render_opts *o, int64_t n_rays)
 
 }  // namespace
 
+namespace roam {
+void set_error_message(const char *msg) { snprintf(g_err, sizeof(g_err), "%s", msg); }
+}  // namespace roam
+
 extern "C" {
 
 const char *roam_last_error(void) { return g_err; }
