@@ -194,6 +194,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="roam", choices=["roam", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--quick", action="store_true",
+                    help="headline loop only (no FP32 comparison, accuracy, e2e or CPU baseline): for profilers")
+    ap.add_argument("--views", default="both", choices=["both", "equirect", "perspective"])
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
@@ -210,12 +213,13 @@ def main():
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
-    wl = F.floor256()
+    wl = F.floor256(views=args.views)
     r = roam.Roam(local)
     r.load_workload(wl)
     stream = torch.cuda.current_stream()
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")   # 256 MiB > L2
-    views = ["equirect 1024x512", "perspective 1920x1080 fov 90"]
+    views = [{"equirect": "equirect 1024x512", "perspective": "perspective 1920x1080 fov 90"}[m]
+             for m in (["equirect", "perspective"] if args.views == "both" else [args.views])]
 
     try:
         r.render(wl.cams, roam.render_opts(wl.delta, wl.n_max, precision=roam.ROAM_BF16))
@@ -248,6 +252,13 @@ def main():
     evaluated_per_step = st.n_samples
     value = world * used_per_step * args.steps / (total_ms / 1000.0)
     ms_per_step = total_ms / args.steps
+    if args.quick:
+        if rank == 0:
+            print(json.dumps({"quick": True, "metric": METRIC, "value": value, "unit": UNIT, "dtype": dtype,
+                              "ms_per_step": ms_per_step, "views": views, "kernels": prof, "clocks": clocks}),
+                  flush=True)
+        r.close()
+        return 0
 
     # ---- per-view frame times and the FP32 SIMT form ----
     frame = {}

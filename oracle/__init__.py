@@ -18,6 +18,7 @@ Parity status of each function (what pins it; see tests/test_oracle_pins.py):
   composite       pinned: two-sample closed form, constant slab exp(-sigma l),
                   sum of weights = 1 - T_end, empty ray = background
   loss / grad     pinned: central finite differences (h = 1e-4)
+  adam            pinned: first-step update lr * sign(g), constant-gradient steps
 """
 from __future__ import annotations
 
@@ -73,6 +74,7 @@ def lib():
         L.orc_loss_grad.restype = D
         L.orc_rays_touching.argtypes = [i32p, f64p, D, i32p, f64p, I, u32p, I64, D, I, I, u8p]
         L.orc_rays_touching.restype = I
+        L.orc_adam.argtypes = [I64, f64p, f64p, f64p, f64p, D, D, D, D, I]
         _lib = L
     return _lib
 
@@ -249,3 +251,14 @@ def rays_touching(grid: Grid, cams16, rays, delta: float, n_max: int, field: int
     lib().orc_rays_touching(*grid.args(), _p(cams, ctypes.c_double), int(cams.shape[0]), _p(r, ctypes.c_uint32),
                             int(r.shape[0]), f32(delta), n_max, field, _p(mask, ctypes.c_uint8))
     return mask.astype(bool)
+
+
+def adam(w, m, v, g, lr: float, step: int, b1: float = 0.9, b2: float = 0.99, eps: float = 1e-8):
+    """One Adam step in FP64 on copies; returns (w, m, v)."""
+    w = np.array(w, dtype=np.float64).ravel().copy()
+    m = np.array(m, dtype=np.float64).ravel().copy()
+    v = np.array(v, dtype=np.float64).ravel().copy()
+    g = np.ascontiguousarray(np.array(g, dtype=np.float64).ravel())
+    lib().orc_adam(int(w.size), _p(w, ctypes.c_double), _p(m, ctypes.c_double), _p(v, ctypes.c_double),
+                   _p(g, ctypes.c_double), lr, b1, b2, eps, int(step))
+    return w, m, v

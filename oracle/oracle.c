@@ -775,3 +775,22 @@ int orc_rays_touching(const int32_t *dims, const double *origin, double vox, con
     (void)n_views;
     return 0;
 }
+
+/* ------------------------------------------------------------------ */
+/* Adam (Sec. "Training Details and Parameters": beta1 = 0.9,           */
+/* beta2 = 0.99, exponentially decaying learning rate)                  */
+/* ------------------------------------------------------------------ */
+
+/* One Adam step of the (FP32-stored) weights w with gradient g, moments m
+ * and v updated in place, everything computed in FP64: m <- b1 m + (1-b1) g,
+ * v <- b2 v + (1-b2) g^2, w <- w - lr (m / (1 - b1^t)) / (sqrt(v / (1 - b2^t)) + eps). */
+void orc_adam(int64_t n, double *w, double *m, double *v, const double *g, double lr, double b1, double b2,
+              double eps, int t)
+{
+    const double c1 = 1.0 - pow(b1, t), c2 = 1.0 - pow(b2, t);
+    for (int64_t i = 0; i < n; ++i) {
+        m[i] = b1 * m[i] + (1.0 - b1) * g[i];
+        v[i] = b2 * v[i] + (1.0 - b2) * g[i] * g[i];
+        w[i] -= lr * (m[i] / c1) / (sqrt(v[i] / c2) + eps);
+    }
+}

@@ -60,9 +60,17 @@ __global__ void __launch_bounds__(512) k_hist(const uint32_t *cnt, const uint32_
         if (sh[f]) atomicAdd(&hist[f], sh[f]);
 }
 
+__device__ __forceinline__ uint32_t ntiles_of(uint32_t h, int tile, int group)
+{
+    const uint32_t t = (h + (uint32_t)tile - 1u) / (uint32_t)tile;
+    return (t + (uint32_t)group - 1u) / (uint32_t)group * (uint32_t)group;
+}
+
 // One block: offsets = exclusive scan of hist; tiles of `tile` samples per
-// field; resets hist for the next use.
-__global__ void __launch_bounds__(1024) k_scan(uint32_t *hist, int n_fields, int tile, uint32_t *offsets,
+// field, the tile count of every non-empty field rounded up to a multiple of
+// `group` (trailing tiles empty) so that groups of tiles never mix fields;
+// resets hist for the next use.
+__global__ void __launch_bounds__(1024) k_scan(uint32_t *hist, int n_fields, int tile, int group, uint32_t *offsets,
                                                uint32_t *cursor, Tile *tiles, Counters *ctr)
 {
     __shared__ uint32_t warp_a[32], warp_b[32];
@@ -75,7 +83,7 @@ __global__ void __launch_bounds__(1024) k_scan(uint32_t *hist, int n_fields, int
         if (f < n_fields) {
             const uint32_t h = hist[f];
             cs += h;
-            ts += (h + tile - 1) / tile;
+            ts += ntiles_of(h, tile, group);
             hit += h > 0;
         }
     }
@@ -113,7 +121,7 @@ __global__ void __launch_bounds__(1024) k_scan(uint32_t *hist, int n_fields, int
             cursor[f] = ea;
             tile_off[f] = eb;
             ea += h;
-            eb += (h + tile - 1) / tile;
+            eb += ntiles_of(h, tile, group);
         }
     }
     if (threadIdx.x == 0) {
@@ -138,7 +146,7 @@ __global__ void __launch_bounds__(1024) k_scan(uint32_t *hist, int n_fields, int
         Tile tl;
         tl.field = (uint32_t)lo;
         tl.start = offsets[lo] + k * (uint32_t)tile;
-        tl.count = min((uint32_t)tile, h - k * (uint32_t)tile);
+        tl.count = h > k * (uint32_t)tile ? min((uint32_t)tile, h - k * (uint32_t)tile) : 0u;
         tl.pad = 0;
         tiles[t] = tl;
     }
@@ -194,13 +202,13 @@ __global__ void __launch_bounds__(512) k_scatter(const uint32_t *cnt, const uint
 }  // namespace
 
 void launch_bucket(const uint32_t *cnt, const uint32_t *recs, const uint32_t *live_count, uint32_t n_fixed,
-                   int R, int /*flat_keys16*/, const uint16_t *keys16, int n_fields, int tile,
+                   int R, int group, const uint16_t *keys16, int n_fields, int tile,
                    const BucketBufs &b, Counters *ctr, int grid, cudaStream_t s)
 {
     const size_t sh = (size_t)n_fields * sizeof(uint32_t);
     k_hist<<<grid, 512, sh, s>>>(cnt, recs, live_count, n_fixed, R, keys16, n_fields, b.hist, ctr);
-    k_scan<<<1, 1024, (size_t)(n_fields + 1) * sizeof(uint32_t), s>>>(b.hist, n_fields, tile, b.offsets,
-                                                                       b.cursor, b.tiles, ctr);
+    k_scan<<<1, 1024, (size_t)(n_fields + 1) * sizeof(uint32_t), s>>>(b.hist, n_fields, tile, group < 1 ? 1 : group,
+                                                                       b.offsets, b.cursor, b.tiles, ctr);
     k_scatter<<<grid, 512, 0, s>>>(cnt, recs, live_count, n_fixed, R, keys16, n_fields, b.cursor, b.sorted);
 }
 

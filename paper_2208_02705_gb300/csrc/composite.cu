@@ -116,7 +116,67 @@ __global__ void k_composite_flat(int64_t n_rays, int n_max, const uint32_t *coun
     }
 }
 
+// Adjoint of the compositing for one ray (rays of a single round holding all
+// their samples, slot layout with R = n_max).  With I the last composited
+// sample, w_i = T_i alpha_i and C = sum_{i<=I} w_i c_i + T_end bg:
+//   dC/dc_i     = w_i
+//   dC/dsigma_i = delta (T_{i+1} c_i - sum_{i<j<=I} w_j c_j - T_end bg).
+// Pass 1 repeats the forward arithmetic to find I, T_end and the composited
+// colour; pass 2 emits per slot (dL/dsigma, dL/dc) and the used count.
+__global__ void __launch_bounds__(256) k_composite_bwd(int64_t n_rays, int R, const uint32_t *cnt,
+                                                       const uint32_t *recs, const float4 *sr, float delta,
+                                                       float t_stop, float bg0, float bg1, float bg2,
+                                                       const float *dl_drgb, float4 *gsr, uint32_t *cnt_used)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_rays; i += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t c = cnt[i];
+        float T = 1.f, sw = 0.f;
+        float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+        uint32_t used = 0;
+        for (uint32_t k = 0; k < c; ++k) {
+            const uint32_t s = slot_of((uint32_t)i, k, (uint32_t)R);
+            const float4 v = sr[s];
+            const uint32_t j = recs[s] & 0xffffu;
+            step(v, ((float)j + 0.5f) * delta, delta, T, sw, acc);
+            used = k + 1;
+            if (T < t_stop) break;
+        }
+        const float T_end = T;
+        const float g0 = dl_drgb[3 * i], g1 = dl_drgb[3 * i + 1], g2 = dl_drgb[3 * i + 2];
+        const float bgterm = T_end * (bg0 * g0 + bg1 * g1 + bg2 * g2);
+        float Tk = 1.f;
+        float S0 = 0.f, S1 = 0.f, S2 = 0.f;
+        for (uint32_t k = 0; k < used; ++k) {
+            const uint32_t s = slot_of((uint32_t)i, k, (uint32_t)R);
+            const float4 v = sr[s];
+            const float a = -expm1f(-v.x * delta);
+            const float wgt = Tk * a;
+            const float Tn = Tk * expf(-v.x * delta);
+            S0 = fmaf(wgt, v.y, S0);
+            S1 = fmaf(wgt, v.z, S1);
+            S2 = fmaf(wgt, v.w, S2);
+            const float d0 = fmaf(Tn, v.y, -(acc.x - S0)), d1 = fmaf(Tn, v.z, -(acc.y - S1)),
+                        d2 = fmaf(Tn, v.w, -(acc.z - S2));
+            const float dsig = delta * (d0 * g0 + d1 * g1 + d2 * g2 - bgterm);
+            gsr[s] = make_float4(dsig, wgt * g0, wgt * g1, wgt * g2);
+            Tk = Tn;
+        }
+        cnt_used[i] = used;
+    }
+}
+
 }  // namespace
+
+void launch_composite_bwd(int64_t n_rays, int R, const uint32_t *cnt, const uint32_t *recs, const float4 *sr,
+                          float delta, float t_stop, const float *bg, const float *dl_drgb, float4 *gsr,
+                          uint32_t *cnt_used, cudaStream_t s)
+{
+    int64_t blocks = (n_rays + 255) / 256;
+    if (blocks > 8192) blocks = 8192;
+    if (blocks < 1) blocks = 1;
+    k_composite_bwd<<<(unsigned)blocks, 256, 0, s>>>(n_rays, R, cnt, recs, sr, delta, t_stop, bg[0], bg[1], bg[2],
+                                                     dl_drgb, gsr, cnt_used);
+}
 
 void launch_composite_round(const MarchParams &mp, const float4 *sr, uint32_t *next_live, uint32_t *next_count,
                             float t_stop, const float *bg, float *rgb, float *depth, float *opacity, int grid,

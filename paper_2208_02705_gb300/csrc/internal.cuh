@@ -124,6 +124,8 @@ struct MlpWeights {
     const float *w32;          // FP32 masters [F][P]
     const float *wt;           // FP32 transposed/padded copy for SIMT [F][Pt]
     int64_t Pt;
+    const float *wr;           // FP32 row-padded copy ([out][round4(in)]) for the SIMT adjoint [F][Pr]
+    int64_t Pr;
     const void *wimg;          // BF16 tensor-core images [F][img_bytes]
     int64_t img_bytes;
     const float *bias;         // FP32 biases for the TC epilogue [F][nb]
@@ -137,8 +139,10 @@ void launch_grid_prefix(const uint32_t *bits, uint32_t *prefix, uint32_t *block_
                         int64_t n_words, cudaStream_t s);
 void launch_brick_map(GridDev g, uint32_t *brick, cudaStream_t s);
 void launch_march(const GridDev &g, const MarchParams &p, int grid, cudaStream_t s);
+// tiles of `tile` samples, every non-empty field's tile count rounded up to a
+// multiple of `group`
 void launch_bucket(const uint32_t *cnt, const uint32_t *recs, const uint32_t *live_count,
-                   uint32_t n_fixed, int R, int flat_keys16, const uint16_t *keys16,
+                   uint32_t n_fixed, int R, int group, const uint16_t *keys16,
                    int n_fields, int tile, const BucketBufs &b, Counters *ctr, int grid,
                    cudaStream_t s);
 void launch_mlp_simt(const MlpWeights &w, const SampleSrc &src, const BucketBufs &b,
@@ -153,6 +157,18 @@ void launch_composite_flat(int64_t n_rays, int n_max, const uint32_t *count, con
                            const float *t, float delta, float t_stop, const float *bg, float *rgb,
                            float *depth, float *opacity, uint32_t *n_used, cudaStream_t s);
 
+void launch_composite_bwd(int64_t n_rays, int R, const uint32_t *cnt, const uint32_t *recs, const float4 *sr,
+                          float delta, float t_stop, const float *bg, const float *dl_drgb, float4 *gsr,
+                          uint32_t *cnt_used, cudaStream_t s);
+void launch_mlp_bwd_simt(const MlpWeights &w, const SampleSrc &src, const BucketBufs &b, Counters *ctr,
+                         const float4 *gsr, float *grad, int grid, cudaStream_t s);
+bool mlp_bwd_supported(int W, int H);
+void launch_pack_rows(const float *w32, int n_fields, int W, int H, int64_t P, float *wr, int64_t Pr,
+                      cudaStream_t s);
+int64_t rows_padded_size(int W, int H);
+void launch_adam(float *w32, float *m, float *v, const float *g, int64_t n, float lr, float b1, float b2,
+                 float eps, float bc1, float bc2, cudaStream_t s);
+
 // sets the calling thread's roam_last_error() message
 void set_error_message(const char *msg);
 
@@ -161,6 +177,7 @@ bool tc_supported(int W, int H);
 int64_t tc_image_bytes(int W, int H);
 int tc_bias_count(int W, int H);
 int tc_tile_samples();
+int tc_tile_group();
 void launch_pack_tc(const float *w32, int n_fields, int W, int H, int64_t P, void *wimg,
                     int64_t img_bytes, float *bias, int nb, cudaStream_t s);
 void launch_mlp_tc(const MlpWeights &w, const SampleSrc &src, const BucketBufs &b, Counters *ctr,

@@ -23,9 +23,6 @@ namespace roam {
 
 namespace {
 
-constexpr int kEpiWarps = 4;
-constexpr int kThreads = (kEpiWarps + 1) * 32;    // 4 epilogue warps + 1 MMA warp
-constexpr int kMmaWarp = kEpiWarps;
 constexpr unsigned long long kWaitNs = 2000000000ull;   // 2 s per wait
 
 __host__ __device__ constexpr int cdiv(int a, int b) { return (a + b - 1) / b; }
@@ -238,34 +235,74 @@ __device__ __forceinline__ void encode1(float v, float (&s)[L], float (&c)[L])
 __device__ __forceinline__ float softplus_f(float s) { return s > 20.f ? s : log1pf(__expf(s)); }
 __device__ __forceinline__ float sigmoid_f(float s) { return 1.f / (1.f + __expf(-s)); }
 
-template <int W, int H>
-__global__ void __launch_bounds__(kThreads, 1) k_mlp_tc(MlpWeights w, SampleSrc src, BucketBufs b, Counters *ctr,
-                                                        float4 *out)
+__device__ __forceinline__ bool mbar_test(uint64_t *bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ void tmem_ld16_nowait(uint32_t taddr, uint32_t (&r)[16])
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+}
+
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// Persistent kernel, one CTA per SM.  kSlots tiles are in flight at once:
+// slot s owns warpgroup s (encoding + epilogues of its tile, one row per
+// thread), an X buffer and kColsPerSlot TMEM columns; warp kSlots*4 issues
+// the MMAs of whichever slot has its next layer's input ready and reloads the
+// shared weight image at field changes.  Tiles come in field-uniform groups
+// of kSlots (bucket padding), so all slots of a group use the same image.
+template <int W, int H, int kSlots>
+__global__ void __launch_bounds__((kSlots * 4 + 1) * 32, 1)
+    k_mlp_tc(MlpWeights w, SampleSrc src, BucketBufs b, Counters *ctr, float4 *out)
 {
     using S = TcShape<W, H>;
+    constexpr int kLayers = S::kLayers;
+    constexpr int kMma = kSlots * 4;                   // MMA warp index
+    constexpr int kColsPerSlot = S::kTmemCols;
+    constexpr int kTmemAlloc = kSlots * kColsPerSlot <= 32 ? 32 : (kSlots * kColsPerSlot <= 64 ? 64 :
+                               (kSlots * kColsPerSlot <= 128 ? 128 : (kSlots * kColsPerSlot <= 256 ? 256 : 512)));
+    static_assert(kSlots * kColsPerSlot <= 512, "TMEM holds every slot's accumulator");
     extern __shared__ uint8_t smem_raw[];
-    __shared__ uint64_t bar_x, bar_d, bar_w, bar_fin;
+    __shared__ uint64_t bar_x[kSlots], bar_d[kSlots];
+    __shared__ uint64_t bar_w, bar_drain;
     __shared__ uint32_t tmem_slot;
     __shared__ int abort_flag;
 
     const uint32_t base = (smem_u32(smem_raw) + 1023u) & ~1023u;
-    uint8_t *X = smem_raw + (base - smem_u32(smem_raw));
-    uint8_t *IMG = X + S::kXBytes;
+    uint8_t *IMG = smem_raw + (base - smem_u32(smem_raw));
+    uint8_t *X0 = IMG + S::kImageBytes;                // slot s: X0 + s * kXBytes (1024-aligned)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     volatile int *abortp = &abort_flag;
     uint32_t *status = &ctr->status;
 
     if (threadIdx.x == 0) {
-        mbar_init(&bar_x, kEpiWarps * 32);
-        mbar_init(&bar_d, 1);
+        for (int q = 0; q < kSlots; ++q) {
+            mbar_init(&bar_x[q], 128);
+            mbar_init(&bar_d[q], 1);
+        }
         mbar_init(&bar_w, 1);
-        mbar_init(&bar_fin, 1);
+        mbar_init(&bar_drain, 1);
         abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (warp == kMmaWarp) {
+    if (warp == kMma) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
-                     "r"(S::kTmemCols)
+                     "r"(kTmemAlloc)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -274,68 +311,108 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_tc(MlpWeights w, SampleSrc 
     tc_fence_after();
     const uint32_t tmem = tmem_slot;
 
-    const uint32_t n_tiles = ctr->n_tiles;
-    const uint32_t t0 = (uint32_t)((uint64_t)n_tiles * blockIdx.x / gridDim.x);
-    const uint32_t t1 = (uint32_t)((uint64_t)n_tiles * (blockIdx.x + 1) / gridDim.x);
+    const uint32_t n_groups = ctr->n_tiles / kSlots;
+    const uint32_t g0 = (uint32_t)((uint64_t)n_groups * blockIdx.x / gridDim.x);
+    const uint32_t g1 = (uint32_t)((uint64_t)n_groups * (blockIdx.x + 1) / gridDim.x);
 
-    if (warp == kMmaWarp) {
+    if (warp == kMma) {
         // ------------------------------------------------------------ MMA
         if (lane == 0) {
-            uint32_t x_waits = 0, d_issued = 0, w_loads = 0;
+            uint32_t xph = 0;                          // bit q: parity of slot q's next bar_x phase
+            uint32_t n_drain = 0, n_loads = 0;
             uint32_t cur_field = 0xffffffffu;
-            bool w_pending = false;
-            for (uint32_t t = t0; t < t1 && !*abortp; ++t) {
-                const uint32_t f = b.tiles[t].field;
+            bool w_pending = false, issued_any = false;
+            for (uint32_t g = g0; g < g1 && !*abortp; ++g) {
+                const uint32_t f = b.tiles[g * kSlots].field;
                 if (f != cur_field) {
-                    // the previous tile's last MMA must be done before the image is overwritten
-                    if (d_issued && !mbar_wait(&bar_d, (d_issued - 1) & 1u, abortp, status)) break;
+                    if (issued_any) {
+                        // every MMA reading the old image must finish first
+                        umma_commit(&bar_drain);
+                        if (!mbar_wait(&bar_drain, n_drain & 1u, abortp, status)) break;
+                        ++n_drain;
+                    }
                     mbar_expect_tx(&bar_w, (uint32_t)S::kImageBytes);
-                    const uint8_t *g = reinterpret_cast<const uint8_t *>(w.wimg) + (int64_t)f * w.img_bytes;
+                    const uint8_t *gsrc = reinterpret_cast<const uint8_t *>(w.wimg) + (int64_t)f * w.img_bytes;
                     for (int off = 0; off < S::kImageBytes; off += 16384) {
-                        const int n = S::kImageBytes - off < 16384 ? S::kImageBytes - off : 16384;
-                        bulk_g2s(IMG + off, g + off, (uint32_t)n, &bar_w);
+                        const int nb = S::kImageBytes - off < 16384 ? S::kImageBytes - off : 16384;
+                        bulk_g2s(IMG + off, gsrc + off, (uint32_t)nb, &bar_w);
                     }
                     w_pending = true;
                     cur_field = f;
                 }
-#pragma unroll 1
-                for (int l = 0; l < S::kLayers; ++l) {
-                    if (!mbar_wait(&bar_x, x_waits & 1u, abortp, status)) break;
-                    ++x_waits;
-                    if (w_pending) {
-                        if (!mbar_wait(&bar_w, w_loads & 1u, abortp, status)) break;
-                        ++w_loads;
-                        w_pending = false;
-                    }
-                    tc_fence_after();
-                    const int K = S::K(l), N = S::N(l);
-                    const uint32_t idesc = idesc_bf16(N);
-                    const uint32_t xa = smem_u32(X), ba = smem_u32(IMG + S::offset(l));
-#pragma unroll 1
-                    for (int ks = 0; ks < K / 16; ++ks) {
-                        const int ch = ks >> 2, kin = ks & 3;
-                        const uint64_t ad = sdesc(xa + ch * 16384 + kin * 32);
-                        const uint64_t bd = sdesc(ba + ch * N * 128 + kin * 32);
-                        umma(tmem, ad, bd, idesc, ks > 0 ? 1u : 0u);
-                    }
-                    umma_commit(&bar_d);
-                    ++d_issued;
+                int layer[kSlots];
+                int remaining = 0;
+#pragma unroll
+                for (int q = 0; q < kSlots; ++q) {
+                    const bool live = b.tiles[g * kSlots + q].count > 0;
+                    layer[q] = live ? 0 : kLayers;
+                    remaining += live ? kLayers : 0;
                 }
+                const unsigned long long t_start = now_ns();
+                unsigned long long t_prog = t_start;
+                uint32_t spins = 0;
+                while (remaining > 0) {
+                    bool progressed = false;
+#pragma unroll
+                    for (int q = 0; q < kSlots; ++q) {
+                        if (layer[q] >= kLayers) continue;
+                        if (!mbar_test(&bar_x[q], (xph >> q) & 1u)) continue;
+                        xph ^= 1u << q;
+                        if (w_pending) {
+                            if (!mbar_wait(&bar_w, n_loads & 1u, abortp, status)) { remaining = -1; break; }
+                            ++n_loads;
+                            w_pending = false;
+                        }
+                        tc_fence_after();
+                        const int l = layer[q];
+                        const int K = S::K(l), N = S::N(l);
+                        const uint32_t idesc = idesc_bf16(N);
+                        const uint32_t xa = smem_u32(X0 + q * S::kXBytes), ba = smem_u32(IMG + S::offset(l));
+                        const uint32_t dt = tmem + (uint32_t)(q * kColsPerSlot);
+#pragma unroll 1
+                        for (int ks = 0; ks < K / 16; ++ks) {
+                            const int ch = ks >> 2, kin = ks & 3;
+                            umma(dt, sdesc(xa + ch * 16384 + kin * 32), sdesc(ba + ch * N * 128 + kin * 32), idesc,
+                                 ks > 0 ? 1u : 0u);
+                        }
+                        umma_commit(&bar_d[q]);
+                        issued_any = true;
+                        ++layer[q];
+                        --remaining;
+                        progressed = true;
+                    }
+                    if (remaining < 0) break;
+                    if (!progressed && ((++spins & 255u) == 0u)) {
+                        if (*abortp) { remaining = -1; break; }
+                        if (now_ns() - t_prog > kWaitNs) {
+                            *abortp = 1;
+                            atomicOr(status, kStatusTimeout);
+                            remaining = -1;
+                            break;
+                        }
+                    } else if (progressed) {
+                        t_prog = now_ns();
+                    }
+                }
+                if (remaining < 0) break;
             }
             // drain: every issued MMA and bulk copy completes before TMEM is freed
-            umma_commit(&bar_fin);
-            mbar_wait(&bar_fin, 0, abortp, status, true);
-            if (w_pending) mbar_wait(&bar_w, w_loads & 1u, abortp, status, true);
+            umma_commit(&bar_drain);
+            mbar_wait(&bar_drain, n_drain & 1u, abortp, status, true);
+            if (w_pending) mbar_wait(&bar_w, n_loads & 1u, abortp, status, true);
         }
         __syncwarp();
     } else {
         // ------------------------------------------------------- epilogue
-        const int row = warp * 32 + lane;                 // TMEM lane == tile row
-        const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
-        uint32_t d_waits = 0;
+        const int slot = warp >> 2, wq = warp & 3;
+        const int row = wq * 32 + lane;                       // TMEM lane == tile row
+        const uint32_t trow = tmem + ((uint32_t)(wq * 32) << 16) + (uint32_t)(slot * kColsPerSlot);
+        uint8_t *X = X0 + slot * S::kXBytes;
+        uint32_t d_ph = 0;
         const float sig_scale = w.sigma_scale;
-        for (uint32_t t = t0; t < t1 && !*abortp; ++t) {
-            const Tile tl = b.tiles[t];
+        for (uint32_t g = g0; g < g1 && !*abortp; ++g) {
+            const Tile tl = b.tiles[g * kSlots + slot];
+            if (tl.count == 0) continue;
             const bool valid = (uint32_t)row < tl.count;
             uint32_t idx = 0;
             float px = 0.f, py = 0.f, pz = 0.f, dx = 0.f, dy = 0.f, dz = 1.f;
@@ -365,12 +442,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_tc(MlpWeights w, SampleSrc 
                 e[0] = xl[0]; e[1] = xl[1]; e[2] = xl[2];
 #pragma unroll
                 for (int a = 0; a < 3; ++a) {
-                    float s[10], c[10];
-                    encode1<10>(xl[a], s, c);
+                    float sn[10], cs[10];
+                    encode1<10>(xl[a], sn, cs);
 #pragma unroll
                     for (int k = 0; k < 10; ++k) {
-                        e[3 + 6 * k + a] = s[k];
-                        e[6 + 6 * k + a] = c[k];
+                        e[3 + 6 * k + a] = sn[k];
+                        e[6 + 6 * k + a] = cs[k];
                     }
                 }
                 e[63] = 1.0f;
@@ -387,38 +464,46 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_tc(MlpWeights w, SampleSrc 
                 }
             }
             fence_proxy_async();
-            mbar_arrive(&bar_x);
+            mbar_arrive(&bar_x[slot]);
             float sigma = 0.f;
 #pragma unroll 1
-            for (int l = 0; l < S::kLayers; ++l) {
+            for (int l = 0; l < kLayers; ++l) {
                 // all lanes of the warp leave together (tcgen05.ld is warp-collective)
-                if (!__all_sync(0xffffffffu, mbar_wait(&bar_d, d_waits & 1u, abortp, status))) break;
-                ++d_waits;
+                if (!__all_sync(0xffffffffu, mbar_wait(&bar_d[slot], d_ph, abortp, status))) break;
+                d_ph ^= 1u;
                 tc_fence_after();
                 if (l < H + 2) {
-                    // layers writing the next X: L1, hidden, head, colour
                     const float *bl = nullptr;
                     if (l >= 1 && l < H) bl = bias + (l - 1) * W;          // hidden
                     else if (l == H) bl = bias + (H - 1) * W;              // head features, then density
+                    uint32_t r[W / 16][16];
 #pragma unroll
-                    for (int c0 = 0; c0 < W; c0 += 16) {
+                    for (int c = 0; c < W / 16; ++c) tmem_ld16_nowait(trow + 16 * c, r[c]);
+                    uint32_t rs[16];
+                    if (l == H) tmem_ld16_nowait(trow + W, rs);
+                    tmem_wait_ld();
+#pragma unroll
+                    for (int c = 0; c < W / 16; ++c) {
                         float v[16];
-                        tmem_ld16(trow + c0, v);
-                        if (bl) {
 #pragma unroll
-                            for (int q = 0; q < 16; ++q) v[q] += __ldg(bl + c0 + q);
+                        for (int q = 0; q < 16; ++q) v[q] = __uint_as_float(r[c][q]);
+                        if (bl) {
+                            const float4 *b4 = reinterpret_cast<const float4 *>(bl + 16 * c);
+#pragma unroll
+                            for (int q4 = 0; q4 < 4; ++q4) {
+                                const float4 bb = __ldg(b4 + q4);
+                                v[4 * q4 + 0] += bb.x; v[4 * q4 + 1] += bb.y; v[4 * q4 + 2] += bb.z; v[4 * q4 + 3] += bb.w;
+                            }
                         }
                         if (l != H) {
 #pragma unroll
                             for (int q = 0; q < 16; ++q) v[q] = fmaxf(v[q], 0.f);
                         }
-                        st_x16(X, row, c0, v);
+                        st_x16(X, row, 16 * c, v);
                     }
                     if (l == H) {
-                        float v[16];
-                        tmem_ld16(trow + W, v);
-                        const float s = v[0] + __ldg(bl + W);
-                        sigma = sig_scale * (w.act == ROAM_RELU ? fmaxf(s, 0.f) : softplus_f(s));
+                        const float sl = __uint_as_float(rs[0]) + __ldg(bl + W);
+                        sigma = sig_scale * (w.act == ROAM_RELU ? fmaxf(sl, 0.f) : softplus_f(sl));
                     }
                     if (l == 0) {
                         // colour-layer tail of X: [F(d) | 1 | 0 0 0 0] at columns W .. W+31
@@ -427,12 +512,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_tc(MlpWeights w, SampleSrc 
                         const float dv[3] = {dx, dy, dz};
 #pragma unroll
                         for (int a = 0; a < 3; ++a) {
-                            float s[4], c[4];
-                            encode1<4>(dv[a], s, c);
+                            float sn[4], cs[4];
+                            encode1<4>(dv[a], sn, cs);
 #pragma unroll
                             for (int k = 0; k < 4; ++k) {
-                                e[3 + 6 * k + a] = s[k];
-                                e[6 + 6 * k + a] = c[k];
+                                e[3 + 6 * k + a] = sn[k];
+                                e[6 + 6 * k + a] = cs[k];
                             }
                         }
                         e[27] = valid ? 1.0f : 0.0f;
@@ -447,25 +532,27 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_tc(MlpWeights w, SampleSrc 
                     }
                     tc_fence_before();
                     fence_proxy_async();
-                    mbar_arrive(&bar_x);
+                    mbar_arrive(&bar_x[slot]);
                 } else {
                     // output layer: rgb = sigmoid(z + b)
-                    float v[16];
-                    tmem_ld16(trow, v);
+                    uint32_t r[16];
+                    tmem_ld16_nowait(trow, r);
+                    tmem_wait_ld();
                     tc_fence_before();
                     const float *bo = bias + (H - 1) * W + W + 1;
                     if (valid)
-                        out[idx] = make_float4(sigma, sigmoid_f(v[0] + __ldg(bo + 0)), sigmoid_f(v[1] + __ldg(bo + 1)),
-                                               sigmoid_f(v[2] + __ldg(bo + 2)));
+                        out[idx] = make_float4(sigma, sigmoid_f(__uint_as_float(r[0]) + __ldg(bo + 0)),
+                                               sigmoid_f(__uint_as_float(r[1]) + __ldg(bo + 1)),
+                                               sigmoid_f(__uint_as_float(r[2]) + __ldg(bo + 2)));
                 }
             }
         }
     }
     tc_fence_before();
     __syncthreads();
-    if (warp == kMmaWarp) {
+    if (warp == kMma) {
         tc_fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(S::kTmemCols)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemAlloc)
                      : "memory");
     }
 }
@@ -543,18 +630,20 @@ __global__ void k_pack_tc(const float *__restrict__ w32, int n_fields, int64_t P
     }
 }
 
+constexpr int kSlotsTc = 4;
+
 template <int W, int H>
 void launch_t(const MlpWeights &w, const SampleSrc &src, const BucketBufs &b, Counters *ctr, float4 *out, int n_sm,
               cudaStream_t s)
 {
     using S = TcShape<W, H>;
+    const int smem = 1024 + S::kImageBytes + kSlotsTc * S::kXBytes;
     static bool attr = false;
     if (!attr) {
-        cudaFuncSetAttribute(k_mlp_tc<W, H>, cudaFuncAttributeMaxDynamicSharedMemorySize, S::kSmem);
+        cudaFuncSetAttribute(k_mlp_tc<W, H, kSlotsTc>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         attr = true;
     }
-    const int per_sm = (2 * (S::kSmem + 1024) <= 227 * 1024 && 2 * S::kTmemCols <= 512) ? 2 : 1;
-    k_mlp_tc<W, H><<<n_sm * per_sm, kThreads, S::kSmem, s>>>(w, src, b, ctr, out);
+    k_mlp_tc<W, H, kSlotsTc><<<n_sm, (kSlotsTc * 4 + 1) * 32, smem, s>>>(w, src, b, ctr, out);
 }
 
 }  // namespace
@@ -562,8 +651,8 @@ void launch_t(const MlpWeights &w, const SampleSrc &src, const BucketBufs &b, Co
 bool tc_supported(int W, int H)
 {
     if (H < 1 || H > 4) return false;
-    if (W == 32) return TcShape<32, 4>::kSmem <= 227 * 1024;
-    if (W == 64) return TcShape<64, 4>::kSmem <= 227 * 1024;
+    if (W == 32) return 1024 + TcShape<32, 4>::kImageBytes + kSlotsTc * TcShape<32, 4>::kXBytes <= 227 * 1024;
+    if (W == 64) return 1024 + TcShape<64, 4>::kImageBytes + kSlotsTc * TcShape<64, 4>::kXBytes <= 227 * 1024;
     return false;   // W = 128: the full image does not fit next to the activations
 }
 
@@ -580,6 +669,8 @@ int64_t tc_image_bytes(int W, int H)
 int tc_bias_count(int W, int H) { return ((H - 1) * W + W + 1 + 3 + 3) & ~3; }
 
 int tc_tile_samples() { return 128; }
+
+int tc_tile_group() { return kSlotsTc; }
 
 void launch_pack_tc(const float *w32, int n_fields, int W, int H, int64_t P, void *wimg, int64_t img_bytes,
                     float *bias, int nb, cudaStream_t s)

@@ -108,10 +108,12 @@ struct roam_ctx {
     int64_t P = 0, Pt = 0, img_bytes = 0;
     int nb = 0;
     bool tc_ok = false;
-    DBuf<float> w32, wt, bias, adam_m, adam_v;
+    DBuf<float> w32, wt, wr, bias, adam_m, adam_v;
+    int64_t Pr = 0;
+    bool adam_fresh = true;
     DBuf<uint8_t> wimg;
     // per-call workspace
-    DBuf<float4> orig, dir, dir_lo, acc, sr;
+    DBuf<float4> orig, dir, dir_lo, acc, sr, gsr;
     DBuf<float2> tw;
     DBuf<uint32_t> j_next, j_end, n_kept, live0, live1, cnt, recs, sorted, hist, offsets, cursor, scratch_u32;
     DBuf<Tile> tiles;
@@ -132,9 +134,10 @@ struct roam_ctx {
     std::vector<cudaEvent_t> ev_pool;
     std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> prof_pending;
     std::vector<std::pair<int64_t, double>> prof_acc;
-    // training
+    // training: state kept from roam_train_forward for roam_train_backward
     int64_t train_rays = 0;
     int train_R = 0;
+    roam_render_opts train_opts{};
 };
 
 namespace {
@@ -214,6 +217,8 @@ MlpWeights weights_of(const roam_ctx *c)
     w.w32 = c->w32.p;
     w.wt = c->wt.p;
     w.Pt = c->Pt;
+    w.wr = c->wr.p;
+    w.Pr = c->Pr;
     w.wimg = c->wimg.p;
     w.img_bytes = c->img_bytes;
     w.bias = c->bias.p;
@@ -301,6 +306,10 @@ roam_status upload_cams(roam_ctx *c, const roam_camera *cams, int n_views, float
     return ROAM_OK;
 }
 
+// tile records needed for `samples` samples: one per 128 plus padding of
+// each field's run to a whole group
+size_t tile_capacity(size_t samples, int n_fields) { return samples / 128 + (size_t)n_fields * 8 + 1; }
+
 roam_status ensure_rays(roam_ctx *c, int64_t n_rays, int R)
 {
     const size_t n = (size_t)n_rays;
@@ -319,7 +328,7 @@ roam_status ensure_rays(roam_ctx *c, int64_t n_rays, int R)
     ROAM_TRY(ensure(c->recs, slots));
     ROAM_TRY(ensure(c->sr, slots));
     ROAM_TRY(ensure(c->sorted, slots));
-    ROAM_TRY(ensure(c->tiles, slots / 64 + (size_t)c->n_fields + 1));
+    ROAM_TRY(ensure(c->tiles, tile_capacity(slots, c->n_fields)));
     return ROAM_OK;
 }
 
@@ -360,6 +369,7 @@ BucketBufs bucket_of(roam_ctx *c)
 }
 
 int tile_of(int precision) { return precision == ROAM_BF16 ? tc_tile_samples() : 128; }
+int group_of(int precision) { return precision == ROAM_BF16 ? tc_tile_group() : 1; }
 
 roam_status run_mlp(roam_ctx *c, int precision, const SampleSrc &src, const BucketBufs &b, float4 *out,
                     cudaStream_t s)
@@ -407,8 +417,8 @@ roam_status run_rounds(roam_ctx *c, const uint32_t *rays, int64_t n_rays, const 
         ROAM_TRY(launched("march"));
         {
             ProfScope ps(c, P_BUCKET, s);
-            launch_bucket(mp.cnt, mp.recs, mp.live_count, mp.n_rays, R, 0, nullptr, c->n_fields,
-                          tile_of(o->precision), b, c->ctr, grid, s);
+            launch_bucket(mp.cnt, mp.recs, mp.live_count, mp.n_rays, R, group_of(o->precision), nullptr,
+                          c->n_fields, tile_of(o->precision), b, c->ctr, grid, s);
         }
         ROAM_TRY(launched("bucket"));
         SampleSrc src{};
@@ -489,7 +499,7 @@ roam_status roam_destroy(roam_ctx *c)
     cudaDeviceSynchronize();
     release(c->bits); release(c->prefix); release(c->brick); release(c->block_sums);
     release(c->labels); release(c->affine);
-    release(c->w32); release(c->wt); release(c->bias); release(c->adam_m); release(c->adam_v); release(c->wimg);
+    release(c->w32); release(c->wt); release(c->wr); release(c->gsr); release(c->bias); release(c->adam_m); release(c->adam_v); release(c->wimg);
     release(c->orig); release(c->dir); release(c->dir_lo); release(c->acc); release(c->sr); release(c->tw);
     release(c->j_next); release(c->j_end); release(c->n_kept); release(c->live0); release(c->live1);
     release(c->cnt); release(c->recs); release(c->sorted); release(c->hist); release(c->offsets);
@@ -632,6 +642,12 @@ roam_status roam_load_weights(roam_ctx *c, const roam_mlp_desc *desc, const floa
     ROAM_TRY(ensure(c->wt, (size_t)(c->Pt * c->n_fields)));
     launch_pack_simt(c->w32.p, c->n_fields, W, H, P, c->wt.p, c->Pt, 0);
     ROAM_TRY(launched("pack simt"));
+    c->Pr = rows_padded_size(W, H);
+    ROAM_TRY(ensure(c->wr, (size_t)(c->Pr * c->n_fields)));
+    launch_pack_rows(c->w32.p, c->n_fields, W, H, P, c->wr.p, c->Pr, 0);
+    ROAM_TRY(launched("pack rows"));
+    c->adam_fresh = true;
+    c->train_rays = 0;
     c->tc_ok = tc_supported(W, H);
     if (c->tc_ok) {
         c->img_bytes = tc_image_bytes(W, H);
@@ -789,7 +805,7 @@ roam_status roam_bucket(roam_ctx *c, const uint16_t *keys, int64_t n, uint32_t *
     if (n < 0 || n > 0x7fffffff) return fail(ROAM_ERR_ARG, "bad sample count");
     if (!offsets || (n > 0 && (!keys || !perm))) return fail(ROAM_ERR_ARG, "null pointer");
     cudaStream_t s = (cudaStream_t)stream;
-    ROAM_TRY(ensure(c->tiles, (size_t)n / 64 + c->n_fields + 1));
+    ROAM_TRY(ensure(c->tiles, tile_capacity((size_t)n, c->n_fields)));
     BucketBufs b = bucket_of(c);
     b.offsets = offsets;
     b.sorted = perm;
@@ -811,11 +827,11 @@ roam_status roam_mlp_eval(roam_ctx *c, const float *p, const float *d, const uin
     if (precision == ROAM_BF16 && !c->tc_ok) return fail(ROAM_ERR_UNSUPPORTED, "BF16 path not available");
     cudaStream_t s = (cudaStream_t)stream;
     ROAM_TRY(ensure(c->sorted, (size_t)n));
-    ROAM_TRY(ensure(c->tiles, (size_t)n / 64 + c->n_fields + 1));
+    ROAM_TRY(ensure(c->tiles, tile_capacity((size_t)n, c->n_fields)));
     const BucketBufs b = bucket_of(c);
     ROAM_CUDA(cudaMemsetAsync(c->ctr, 0, sizeof(Counters), s));
-    launch_bucket(nullptr, nullptr, nullptr, (uint32_t)n, 1, 1, field, c->n_fields, tile_of(precision), b, c->ctr,
-                  grid_blocks(c, 2), s);
+    launch_bucket(nullptr, nullptr, nullptr, (uint32_t)n, 1, group_of(precision), field, c->n_fields,
+                  tile_of(precision), b, c->ctr, grid_blocks(c, 2), s);
     ROAM_TRY(launched("bucket"));
     SampleSrc src{};
     src.mode = 1;
@@ -843,23 +859,110 @@ roam_status roam_composite(roam_ctx *c, int64_t n_rays, int n_max, const uint32_
     return launched("composite");
 }
 
-roam_status roam_train_forward(roam_ctx *c, const roam_camera *, int, const uint32_t *, int64_t,
-                               const roam_render_opts *, float *, void *)
+roam_status roam_train_forward(roam_ctx *c, const roam_camera *cams, int n_views, const uint32_t *rays, int64_t n_rays,
+                               const roam_render_opts *opts, float *rgb, void *stream)
 {
     ROAM_TRY(set_dev(c));
-    return fail(ROAM_ERR_UNSUPPORTED, "training forward not built yet");
+    ROAM_TRY(check_ready(c));
+    ROAM_TRY(check_opts(c, opts));
+    if (!rays || !rgb) return fail(ROAM_ERR_ARG, "null rays or rgb");
+    if (n_rays < 1 || n_rays > 0x7fffffff) return fail(ROAM_ERR_ARG, "bad ray count");
+    if (!mlp_bwd_supported(c->md.width, c->md.n_hidden))
+        return fail(ROAM_ERR_UNSUPPORTED, "training supports W = 32 or 64");
+    cudaStream_t s = (cudaStream_t)stream;
+    int64_t n_pix = 0;
+    ROAM_TRY(upload_cams(c, cams, n_views, opts->delta, &n_pix, s));
+    // one round holding every kept sample of every ray, so the backward pass
+    // finds each ray's samples in one place
+    const int R = opts->n_max;
+    if ((double)((n_rays + 31) & ~31LL) * R >= 4294967295.0) return fail(ROAM_ERR_ARG, "too many rays x samples");
+    ROAM_TRY(ensure_rays(c, n_rays, R));
+    ROAM_CUDA(cudaMemsetAsync(c->ctr, 0, sizeof(Counters), s));
+    ROAM_TRY(run_rounds(c, rays, n_rays, opts, rgb, nullptr, nullptr, R, s));
+    c->last = s;
+    c->last_rays = n_rays;
+    c->last_rounds = 1;
+    c->train_rays = n_rays;
+    c->train_R = R;
+    c->train_opts = *opts;
+    return ROAM_OK;
 }
 
-roam_status roam_train_backward(roam_ctx *c, const float *, float *, void *)
+roam_status roam_train_backward(roam_ctx *c, const float *dl_drgb, float *grad, void *stream)
 {
     ROAM_TRY(set_dev(c));
-    return fail(ROAM_ERR_UNSUPPORTED, "training backward not built yet");
+    ROAM_TRY(check_ready(c));
+    if (c->train_rays <= 0) return fail(ROAM_ERR_STATE, "call roam_train_forward first");
+    if (!dl_drgb || !grad) return fail(ROAM_ERR_ARG, "null pointer");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t n = c->train_rays;
+    const int R = c->train_R;
+    const roam_render_opts &o = c->train_opts;
+    const size_t slots = ((size_t)(n + 31) & ~(size_t)31) * (size_t)R;
+    ROAM_TRY(ensure(c->gsr, slots));
+    {
+        ProfScope ps(c, P_COMPOSITE_BWD, s);
+        launch_composite_bwd(n, R, c->cnt.p, c->recs.p, c->sr.p, o.delta, o.t_stop, o.bg, dl_drgb, c->gsr.p,
+                             c->live1.p, s);
+    }
+    ROAM_TRY(launched("composite_bwd"));
+    ROAM_CUDA(cudaMemsetAsync(c->ctr, 0, sizeof(Counters), s));
+    const BucketBufs b = bucket_of(c);
+    {
+        ProfScope ps(c, P_BUCKET, s);
+        launch_bucket(c->live1.p, c->recs.p, nullptr, (uint32_t)n, R, 1, nullptr, c->n_fields, 128, b, c->ctr,
+                      grid_blocks(c, 4), s);
+    }
+    ROAM_TRY(launched("bucket"));
+    ROAM_CUDA(cudaMemsetAsync(grad, 0, (size_t)(c->P * c->n_fields) * sizeof(float), s));
+    SampleSrc src{};
+    src.mode = 0;
+    src.recs = c->recs.p;
+    src.live = nullptr;
+    src.live_count = nullptr;
+    src.R = R;
+    src.st = state_of(c);
+    src.delta = o.delta;
+    src.accurate = o.precision == ROAM_F32;
+    {
+        ProfScope ps(c, P_MLP_BWD, s);
+        launch_mlp_bwd_simt(weights_of(c), src, b, c->ctr, c->gsr.p, grad, c->n_sm, s);
+    }
+    c->last = s;
+    return launched("mlp_bwd");
 }
 
-roam_status roam_adam_step(roam_ctx *c, const float *, const roam_adam_cfg *, void *)
+roam_status roam_adam_step(roam_ctx *c, const float *grad, const roam_adam_cfg *cfg, void *stream)
 {
     ROAM_TRY(set_dev(c));
-    return fail(ROAM_ERR_UNSUPPORTED, "adam not built yet");
+    if (!c->has_weights) return fail(ROAM_ERR_STATE, "no weights loaded");
+    if (!grad || !cfg) return fail(ROAM_ERR_ARG, "null pointer");
+    if (!(cfg->lr >= 0.f) || !finite(cfg->lr) || !(cfg->beta1 >= 0.f && cfg->beta1 < 1.f) ||
+        !(cfg->beta2 >= 0.f && cfg->beta2 < 1.f) || !(cfg->eps > 0.f) || cfg->step < 1)
+        return fail(ROAM_ERR_ARG, "bad Adam configuration");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t n = c->P * c->n_fields;
+    ROAM_TRY(ensure(c->adam_m, (size_t)n));
+    ROAM_TRY(ensure(c->adam_v, (size_t)n));
+    if (c->adam_fresh) {
+        ROAM_CUDA(cudaMemsetAsync(c->adam_m.p, 0, n * sizeof(float), s));
+        ROAM_CUDA(cudaMemsetAsync(c->adam_v.p, 0, n * sizeof(float), s));
+        c->adam_fresh = false;
+    }
+    const float bc1 = (float)(1.0 - std::pow((double)cfg->beta1, (double)cfg->step));
+    const float bc2 = (float)(1.0 - std::pow((double)cfg->beta2, (double)cfg->step));
+    {
+        ProfScope ps(c, P_ADAM, s);
+        launch_adam(c->w32.p, c->adam_m.p, c->adam_v.p, grad, n, cfg->lr, cfg->beta1, cfg->beta2, cfg->eps, bc1, bc2,
+                    s);
+        // refresh every derived copy of the masters
+        const int W = c->md.width, H = c->md.n_hidden;
+        launch_pack_simt(c->w32.p, c->n_fields, W, H, c->P, c->wt.p, c->Pt, s);
+        launch_pack_rows(c->w32.p, c->n_fields, W, H, c->P, c->wr.p, c->Pr, s);
+        if (c->tc_ok) launch_pack_tc(c->w32.p, c->n_fields, W, H, c->P, c->wimg.p, c->img_bytes, c->bias.p, c->nb, s);
+    }
+    c->last = s;
+    return launched("adam");
 }
 
 }  // extern "C"

@@ -489,3 +489,26 @@ def test_loss_gradient_matches_central_differences(room32, room32_grid):
         assert abs(fd - grad[f, k]) <= 1e-6 * gmax + 1e-7 * abs(grad[f, k]) + 1e-10, (f, k, fd, grad[f, k])
         checked += 1
     assert checked >= 40
+
+
+# ----------------------------------------------------------------------------
+# Adam
+# ----------------------------------------------------------------------------
+
+def test_adam_first_steps_closed_form():
+    """With zero moments, bias correction makes the first update exactly
+    lr * g / (|g| + eps) (= lr * sign(g) for |g| >> eps), and a constant
+    gradient keeps that update on later steps."""
+    rng = np.random.default_rng(0)
+    g = rng.normal(size=1000) * 10.0 ** rng.uniform(-3, 2, 1000)
+    w0 = rng.normal(size=1000)
+    lr, eps = 1e-3, 1e-8
+    w, m, v = O.adam(w0, np.zeros(1000), np.zeros(1000), g, lr, 1, eps=eps)
+    assert np.allclose(w0 - w, lr * g / (np.abs(g) + eps), rtol=1e-12, atol=0)
+    for t in range(2, 11):
+        w_prev = w
+        w, m, v = O.adam(w, m, v, g, lr, t, eps=eps)
+        assert np.allclose(w_prev - w, lr * g / (np.abs(g) + eps), rtol=1e-9, atol=0)
+    # the moments are the exponential averages
+    assert np.allclose(m, g * (1 - 0.9 ** 10), rtol=1e-12)
+    assert np.allclose(v, g * g * (1 - 0.99 ** 10), rtol=1e-12)
