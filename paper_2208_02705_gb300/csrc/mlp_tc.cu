@@ -3,20 +3,20 @@
 // the 5th-generation tensor cores).  One tile = 128 samples of one field =
 // one M=128 MMA row block; every layer of the chain is
 //   D[128 x N] (TMEM, FP32) = X[128 x K] (SMEM, BF16) * B[K x N] (SMEM, BF16)
-// issued by one thread with tcgen05.mma kind::f16.  The epilogue warps read
-// D back with tcgen05.ld (one row per thread), add bias, apply the
-// activation, round to BF16 and write the next layer's X in the 128-byte
-// swizzled K-major layout.  The field's weight image (all layers, already in
-// the swizzled layout, built once by launch_pack_tc) is copied to shared
-// memory by the bulk-copy (TMA) engine whenever the field changes; a CTA
-// walks a contiguous range of the field-sorted tiles so weights are reused.
+// with tcgen05.mma kind::f16.  Every bias rides in the MMA: X carries a
+// constant-1 column and B the bias in the matching row, so the epilogue only
+// converts (cvt.rn.relu.bf16x2 fuses the ReLU) and writes the next layer's X
+// in the 128-byte swizzled K-major layout.  The field's weight image (all
+// layers, pre-swizzled by launch_pack_tc) is copied to shared memory by the
+// bulk-copy (TMA) engine when the field changes.
 //
-// Layer shapes (K padded to the MMA's 16, N to a multiple of 16):
-//   L1      X = [F(x_loc) (63) | 1]            K = 64      N = W      (bias folded)
-//   hidden  X = h                              K = W       N = W
-//   head    X = h_H                            K = W       N = W + 16 (W features, then density)
-//   colour  X = [feat (W) | F(d) (27) | 1 | 0] K = W + 32  N = W      (bias folded)
-//   output  X = g                              K = W       N = 16     (3 used)
+// X columns (row = sample):
+//   L1 input        [F(x_loc) (63) | 1]                          K = 64
+//   after L1        [h (W) | 1 | F(d) (27) | 0 0 0 0]             (the tail stays)
+//   hidden / head   [h (W) | 1 | ...]     B zero past the bias    K = W + 16
+//   colour          [feat (W) | 1 | F(d) (27) | 0 0 0 0]          K = W + 32
+//   output          [g (W) | 1 | ...]                             K = W + 16
+// Head N = W + 16 (W features, then the density logit), output N = 16.
 #include "internal.cuh"
 
 namespace roam {
@@ -34,7 +34,7 @@ struct TcShape {
     static constexpr int K_COL = W + 32;
     static constexpr int N_OUT = 16;
     static constexpr int kLayers = H + 3;
-    __host__ __device__ static constexpr int K(int l) { return l == 0 ? 64 : (l == H + 1 ? K_COL : W); }
+    __host__ __device__ static constexpr int K(int l) { return l == 0 ? 64 : (l == H + 1 ? K_COL : W + 16); }
     __host__ __device__ static constexpr int N(int l) { return l == H ? N_HEAD : (l == H + 2 ? N_OUT : W); }
     __host__ __device__ static constexpr int chunks(int l) { return cdiv(K(l), 64); }
     __host__ __device__ static constexpr int bytes(int l) { return chunks(l) * N(l) * 128; }
@@ -260,47 +260,125 @@ __device__ __forceinline__ void tmem_ld16_nowait(uint32_t taddr, uint32_t (&r)[1
 
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
-// Persistent kernel, one CTA per SM.  kSlots tiles are in flight at once:
-// slot s owns warpgroup s (encoding + epilogues of its tile, one row per
-// thread), an X buffer and kColsPerSlot TMEM columns; warp kSlots*4 issues
-// the MMAs of whichever slot has its next layer's input ready and reloads the
-// shared weight image at field changes.  Tiles come in field-uniform groups
-// of kSlots (bucket padding), so all slots of a group use the same image.
+__device__ __forceinline__ uint32_t pack_bf16_relu(float a, float b)
+{
+    uint32_t r;
+    asm("cvt.rn.relu.bf16x2.f32 %0, %2, %1;" : "=r"(r) : "f"(a), "f"(b));
+    return r;
+}
+
+// Named barrier over n threads that also ORs a flag across them: every
+// participant gets the same answer, so an abort leaves all of them together.
+__device__ __forceinline__ bool named_sync_or(int id, int n, bool flag)
+{
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\t"
+        "setp.ne.u32 p, %3, 0;\n\t"
+        "bar.red.or.pred q, %1, %2, p;\n\t"
+        "selp.u32 %0, 1, 0, q;\n\t}"
+        : "=r"(r)
+        : "r"(id), "r"(n), "r"((uint32_t)flag)
+        : "memory");
+    return r != 0;
+}
+
+// 16 accumulator columns -> 16 BF16 X columns (two 16-byte chunks)
+template <bool kRelu>
+__device__ __forceinline__ void st_x16_bits(uint8_t *X, int row, int col, const uint32_t (&r)[16])
+{
+    uint4 a, b;
+    if (kRelu) {
+        a.x = pack_bf16_relu(__uint_as_float(r[0]), __uint_as_float(r[1]));
+        a.y = pack_bf16_relu(__uint_as_float(r[2]), __uint_as_float(r[3]));
+        a.z = pack_bf16_relu(__uint_as_float(r[4]), __uint_as_float(r[5]));
+        a.w = pack_bf16_relu(__uint_as_float(r[6]), __uint_as_float(r[7]));
+        b.x = pack_bf16_relu(__uint_as_float(r[8]), __uint_as_float(r[9]));
+        b.y = pack_bf16_relu(__uint_as_float(r[10]), __uint_as_float(r[11]));
+        b.z = pack_bf16_relu(__uint_as_float(r[12]), __uint_as_float(r[13]));
+        b.w = pack_bf16_relu(__uint_as_float(r[14]), __uint_as_float(r[15]));
+    } else {
+        a.x = pack_bf16(__uint_as_float(r[0]), __uint_as_float(r[1]));
+        a.y = pack_bf16(__uint_as_float(r[2]), __uint_as_float(r[3]));
+        a.z = pack_bf16(__uint_as_float(r[4]), __uint_as_float(r[5]));
+        a.w = pack_bf16(__uint_as_float(r[6]), __uint_as_float(r[7]));
+        b.x = pack_bf16(__uint_as_float(r[8]), __uint_as_float(r[9]));
+        b.y = pack_bf16(__uint_as_float(r[10]), __uint_as_float(r[11]));
+        b.z = pack_bf16(__uint_as_float(r[12]), __uint_as_float(r[13]));
+        b.w = pack_bf16(__uint_as_float(r[14]), __uint_as_float(r[15]));
+    }
+    st_x8(X, row, col >> 3, a);
+    st_x8(X, row, (col >> 3) + 1, b);
+}
+
+// Everything the encoding of one sample needs, fetched a tile ahead.
+struct SampleIn {
+    uint32_t idx;
+    float px, py, pz, dx, dy, dz;
+};
+
+__device__ __forceinline__ SampleIn fetch_sample(const SampleSrc &src, const BucketBufs &b, const Tile &tl, int row)
+{
+    SampleIn r{0u, 0.f, 0.f, 0.f, 0.f, 0.f, 1.f};
+    if ((uint32_t)row >= tl.count) return r;
+    r.idx = b.sorted[tl.start + row];
+    if (src.mode == 0) {
+        const uint32_t col = r.idx >> 5;
+        const uint32_t i = (col / (uint32_t)src.R) * 32u + (r.idx & 31u);
+        const uint32_t ray = src.live ? src.live[i] : i;
+        const uint32_t j = src.recs[r.idx] & 0xffffu;
+        const float tt = ((float)j + 0.5f) * src.delta;
+        const float4 o = src.st.orig[ray], d = src.st.dir[ray];
+        r.px = fmaf(tt, d.x, o.x); r.py = fmaf(tt, d.y, o.y); r.pz = fmaf(tt, d.z, o.z);
+        r.dx = d.x; r.dy = d.y; r.dz = d.z;
+    } else {
+        r.px = src.p[3 * (int64_t)r.idx]; r.py = src.p[3 * (int64_t)r.idx + 1]; r.pz = src.p[3 * (int64_t)r.idx + 2];
+        r.dx = src.d[3 * (int64_t)r.idx]; r.dy = src.d[3 * (int64_t)r.idx + 1]; r.dz = src.d[3 * (int64_t)r.idx + 2];
+    }
+    return r;
+}
+
+// Persistent kernel, one CTA per SM, kSlots tiles in flight.  Slot s is
+// warpgroup s: its 128 threads encode and run the epilogues of their tile
+// (one row each), and its first thread issues the tile's MMAs itself --
+// tcgen05.mma and tcgen05.commit occupy the issuing thread for tens to
+// hundreds of cycles each, so one issuer per slot lets the slots' chains
+// overlap.  Tiles come in field-uniform groups of kSlots (bucket padding);
+// at a field change all slots meet at a CTA barrier, thread 0 reloads the
+// shared weight image, and each issuer waits for it before its next MMA.
 template <int W, int H, int kSlots>
-__global__ void __launch_bounds__((kSlots * 4 + 1) * 32, 1)
+__global__ void __launch_bounds__(kSlots * 128, 1)
     k_mlp_tc(MlpWeights w, SampleSrc src, BucketBufs b, Counters *ctr, float4 *out)
 {
     using S = TcShape<W, H>;
     constexpr int kLayers = S::kLayers;
-    constexpr int kMma = kSlots * 4;                   // MMA warp index
-    constexpr int kColsPerSlot = S::kTmemCols;
-    constexpr int kTmemAlloc = kSlots * kColsPerSlot <= 32 ? 32 : (kSlots * kColsPerSlot <= 64 ? 64 :
-                               (kSlots * kColsPerSlot <= 128 ? 128 : (kSlots * kColsPerSlot <= 256 ? 256 : 512)));
-    static_assert(kSlots * kColsPerSlot <= 512, "TMEM holds every slot's accumulator");
+    constexpr int kCols = S::kTmemCols;
+    constexpr int kTmemAlloc = kSlots * kCols <= 32 ? 32 : (kSlots * kCols <= 64 ? 64 :
+                               (kSlots * kCols <= 128 ? 128 : (kSlots * kCols <= 256 ? 256 : 512)));
+    static_assert(kSlots * kCols <= 512, "TMEM holds every slot's accumulator");
     extern __shared__ uint8_t smem_raw[];
-    __shared__ uint64_t bar_x[kSlots], bar_d[kSlots];
-    __shared__ uint64_t bar_w, bar_drain;
+    __shared__ uint64_t bar_d[kSlots];
+    __shared__ uint64_t bar_w;
     __shared__ uint32_t tmem_slot;
     __shared__ int abort_flag;
 
     const uint32_t base = (smem_u32(smem_raw) + 1023u) & ~1023u;
     uint8_t *IMG = smem_raw + (base - smem_u32(smem_raw));
-    uint8_t *X0 = IMG + S::kImageBytes;                // slot s: X0 + s * kXBytes (1024-aligned)
+    uint8_t *X0 = IMG + S::kImageBytes;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int slot = warp >> 2, wq = warp & 3;
+    const int row = wq * 32 + lane;                           // TMEM lane == tile row
+    const bool issuer = (threadIdx.x & 127) == 0;
     volatile int *abortp = &abort_flag;
     uint32_t *status = &ctr->status;
 
     if (threadIdx.x == 0) {
-        for (int q = 0; q < kSlots; ++q) {
-            mbar_init(&bar_x[q], 128);
-            mbar_init(&bar_d[q], 1);
-        }
+        for (int q = 0; q < kSlots; ++q) mbar_init(&bar_d[q], 1);
         mbar_init(&bar_w, 1);
-        mbar_init(&bar_drain, 1);
         abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (warp == kMma) {
+    if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
                      "r"(kTmemAlloc)
                      : "memory");
@@ -310,247 +388,185 @@ __global__ void __launch_bounds__((kSlots * 4 + 1) * 32, 1)
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = tmem_slot;
+    const uint32_t tslot = tmem + (uint32_t)(slot * kCols);
+    const uint32_t trow = tslot + ((uint32_t)(wq * 32) << 16);
+    uint8_t *X = X0 + slot * S::kXBytes;
+    const uint32_t xa = smem_u32(X), imga = smem_u32(IMG);
 
     const uint32_t n_groups = ctr->n_tiles / kSlots;
     const uint32_t g0 = (uint32_t)((uint64_t)n_groups * blockIdx.x / gridDim.x);
     const uint32_t g1 = (uint32_t)((uint64_t)n_groups * (blockIdx.x + 1) / gridDim.x);
 
-    if (warp == kMma) {
-        // ------------------------------------------------------------ MMA
-        if (lane == 0) {
-            uint32_t xph = 0;                          // bit q: parity of slot q's next bar_x phase
-            uint32_t n_drain = 0, n_loads = 0;
-            uint32_t cur_field = 0xffffffffu;
-            bool w_pending = false, issued_any = false;
-            for (uint32_t g = g0; g < g1 && !*abortp; ++g) {
-                const uint32_t f = b.tiles[g * kSlots].field;
-                if (f != cur_field) {
-                    if (issued_any) {
-                        // every MMA reading the old image must finish first
-                        umma_commit(&bar_drain);
-                        if (!mbar_wait(&bar_drain, n_drain & 1u, abortp, status)) break;
-                        ++n_drain;
-                    }
-                    mbar_expect_tx(&bar_w, (uint32_t)S::kImageBytes);
-                    const uint8_t *gsrc = reinterpret_cast<const uint8_t *>(w.wimg) + (int64_t)f * w.img_bytes;
-                    for (int off = 0; off < S::kImageBytes; off += 16384) {
-                        const int nb = S::kImageBytes - off < 16384 ? S::kImageBytes - off : 16384;
-                        bulk_g2s(IMG + off, gsrc + off, (uint32_t)nb, &bar_w);
-                    }
-                    w_pending = true;
-                    cur_field = f;
+    uint32_t d_ph = 0, n_changes = 0, n_commits = 0, n_waits = 0;
+    uint32_t cur_field = 0xffffffffu;
+    bool w_ready = false, w_waited_last = true;
+    bool aborted = false;
+    const float sig_scale = w.sigma_scale;
+    Tile tl{0u, 0u, 0u, 0u};
+    SampleIn nxt{0u, 0.f, 0.f, 0.f, 0.f, 0.f, 1.f};
+    uint32_t g = g0;
+    if (g < g1) {
+        tl = b.tiles[g * kSlots + slot];
+        nxt = fetch_sample(src, b, tl, row);
+    }
+    for (; g < g1; ++g) {
+        const uint32_t f = tl.field;           // identical for every slot (field-uniform groups)
+        if (f != cur_field) {
+            // every slot has waited on its last layer, so no MMA reads the old
+            // image; meet (and agree on any abort), reload, issuers wait below
+            if (named_sync_or(15, kSlots * 128, aborted || *abortp)) break;
+            if (threadIdx.x == 0) {
+                mbar_expect_tx(&bar_w, (uint32_t)S::kImageBytes);
+                const uint8_t *gsrc = reinterpret_cast<const uint8_t *>(w.wimg) + (int64_t)f * w.img_bytes;
+                for (int off = 0; off < S::kImageBytes; off += 16384) {
+                    const int nb = S::kImageBytes - off < 16384 ? S::kImageBytes - off : 16384;
+                    bulk_g2s(IMG + off, gsrc + off, (uint32_t)nb, &bar_w);
                 }
-                int layer[kSlots];
-                int remaining = 0;
-#pragma unroll
-                for (int q = 0; q < kSlots; ++q) {
-                    const bool live = b.tiles[g * kSlots + q].count > 0;
-                    layer[q] = live ? 0 : kLayers;
-                    remaining += live ? kLayers : 0;
-                }
-                const unsigned long long t_start = now_ns();
-                unsigned long long t_prog = t_start;
-                uint32_t spins = 0;
-                while (remaining > 0) {
-                    bool progressed = false;
-#pragma unroll
-                    for (int q = 0; q < kSlots; ++q) {
-                        if (layer[q] >= kLayers) continue;
-                        if (!mbar_test(&bar_x[q], (xph >> q) & 1u)) continue;
-                        xph ^= 1u << q;
-                        if (w_pending) {
-                            if (!mbar_wait(&bar_w, n_loads & 1u, abortp, status)) { remaining = -1; break; }
-                            ++n_loads;
-                            w_pending = false;
-                        }
-                        tc_fence_after();
-                        const int l = layer[q];
-                        const int K = S::K(l), N = S::N(l);
-                        const uint32_t idesc = idesc_bf16(N);
-                        const uint32_t xa = smem_u32(X0 + q * S::kXBytes), ba = smem_u32(IMG + S::offset(l));
-                        const uint32_t dt = tmem + (uint32_t)(q * kColsPerSlot);
-#pragma unroll 1
-                        for (int ks = 0; ks < K / 16; ++ks) {
-                            const int ch = ks >> 2, kin = ks & 3;
-                            umma(dt, sdesc(xa + ch * 16384 + kin * 32), sdesc(ba + ch * N * 128 + kin * 32), idesc,
-                                 ks > 0 ? 1u : 0u);
-                        }
-                        umma_commit(&bar_d[q]);
-                        issued_any = true;
-                        ++layer[q];
-                        --remaining;
-                        progressed = true;
-                    }
-                    if (remaining < 0) break;
-                    if (!progressed && ((++spins & 255u) == 0u)) {
-                        if (*abortp) { remaining = -1; break; }
-                        if (now_ns() - t_prog > kWaitNs) {
-                            *abortp = 1;
-                            atomicOr(status, kStatusTimeout);
-                            remaining = -1;
-                            break;
-                        }
-                    } else if (progressed) {
-                        t_prog = now_ns();
-                    }
-                }
-                if (remaining < 0) break;
+                w_waited_last = false;
             }
-            // drain: every issued MMA and bulk copy completes before TMEM is freed
-            umma_commit(&bar_drain);
-            mbar_wait(&bar_drain, n_drain & 1u, abortp, status, true);
-            if (w_pending) mbar_wait(&bar_w, n_loads & 1u, abortp, status, true);
+            ++n_changes;
+            cur_field = f;
+            w_ready = false;
         }
-        __syncwarp();
-    } else {
-        // ------------------------------------------------------- epilogue
-        const int slot = warp >> 2, wq = warp & 3;
-        const int row = wq * 32 + lane;                       // TMEM lane == tile row
-        const uint32_t trow = tmem + ((uint32_t)(wq * 32) << 16) + (uint32_t)(slot * kColsPerSlot);
-        uint8_t *X = X0 + slot * S::kXBytes;
-        uint32_t d_ph = 0;
-        const float sig_scale = w.sigma_scale;
-        for (uint32_t g = g0; g < g1 && !*abortp; ++g) {
-            const Tile tl = b.tiles[g * kSlots + slot];
-            if (tl.count == 0) continue;
-            const bool valid = (uint32_t)row < tl.count;
-            uint32_t idx = 0;
-            float px = 0.f, py = 0.f, pz = 0.f, dx = 0.f, dy = 0.f, dz = 1.f;
-            if (valid) {
-                idx = b.sorted[tl.start + row];
-                if (src.mode == 0) {
-                    const uint32_t col = idx >> 5;
-                    const uint32_t i = (col / (uint32_t)src.R) * 32u + (idx & 31u);
-                    const uint32_t ray = src.live ? src.live[i] : i;
-                    const uint32_t j = src.recs[idx] & 0xffffu;
-                    const float tt = ((float)j + 0.5f) * src.delta;
-                    const float4 o = src.st.orig[ray], d = src.st.dir[ray];
-                    px = fmaf(tt, d.x, o.x); py = fmaf(tt, d.y, o.y); pz = fmaf(tt, d.z, o.z);
-                    dx = d.x; dy = d.y; dz = d.z;
-                } else {
-                    px = src.p[3 * (int64_t)idx]; py = src.p[3 * (int64_t)idx + 1]; pz = src.p[3 * (int64_t)idx + 2];
-                    dx = src.d[3 * (int64_t)idx]; dy = src.d[3 * (int64_t)idx + 1]; dz = src.d[3 * (int64_t)idx + 2];
+        const Tile cur = tl;
+        const SampleIn sm = nxt;
+        if (g + 1 < g1) tl = b.tiles[(g + 1) * kSlots + slot];
+        if (cur.count == 0 || aborted) {
+            if (g + 1 < g1) nxt = fetch_sample(src, b, tl, row);
+            continue;
+        }
+        const bool valid = (uint32_t)row < cur.count;
+        const float *aff = w.affine + 6 * (int64_t)cur.field;
+        // ---- L1 input: [F(x_loc) | 1] ----
+        {
+            const float xl[3] = {fmaf(__ldg(aff + 0), sm.px, __ldg(aff + 3)), fmaf(__ldg(aff + 1), sm.py, __ldg(aff + 4)),
+                                 fmaf(__ldg(aff + 2), sm.pz, __ldg(aff + 5))};
+            float e[64];
+            e[0] = xl[0]; e[1] = xl[1]; e[2] = xl[2];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                float sn[10], cs[10];
+                encode1<10>(xl[a], sn, cs);
+#pragma unroll
+                for (int k = 0; k < 10; ++k) {
+                    e[3 + 6 * k + a] = sn[k];
+                    e[6 + 6 * k + a] = cs[k];
                 }
             }
-            const float *aff = w.affine + 6 * (int64_t)tl.field;
-            const float *bias = w.bias + (int64_t)tl.field * w.nb;
-            // ---- L1 input: [F(x_loc) | 1] ----
-            {
-                const float xl[3] = {fmaf(__ldg(aff + 0), px, __ldg(aff + 3)), fmaf(__ldg(aff + 1), py, __ldg(aff + 4)),
-                                     fmaf(__ldg(aff + 2), pz, __ldg(aff + 5))};
-                float e[64];
-                e[0] = xl[0]; e[1] = xl[1]; e[2] = xl[2];
+            e[63] = 1.0f;
 #pragma unroll
-                for (int a = 0; a < 3; ++a) {
-                    float sn[10], cs[10];
-                    encode1<10>(xl[a], sn, cs);
+            for (int c16 = 0; c16 < 4; ++c16) {
+                float v[16];
 #pragma unroll
-                    for (int k = 0; k < 10; ++k) {
-                        e[3 + 6 * k + a] = sn[k];
-                        e[6 + 6 * k + a] = cs[k];
+                for (int q = 0; q < 16; ++q) v[q] = valid ? e[16 * c16 + q] : 0.f;
+                st_x16(X, row, 16 * c16, v);
+            }
+        }
+        // the next tile's gathers overlap this tile's layers
+        if (g + 1 < g1) nxt = fetch_sample(src, b, tl, row);
+        float sigma = 0.f;
+#pragma unroll 1
+        for (int l = 0; l < kLayers; ++l) {
+            // X for layer l is complete once all 128 threads of the slot arrive
+            fence_proxy_async();
+            if (named_sync_or(1 + slot, 128, aborted || *abortp)) {
+                aborted = true;
+                break;
+            }
+            if (issuer) {
+                bool ok = true;
+                if (!w_ready) {
+                    ok = mbar_wait(&bar_w, (n_changes - 1) & 1u, abortp, status);
+                    w_ready = ok;
+                    if (threadIdx.x == 0) w_waited_last = ok;
+                }
+                if (ok) {
+                    tc_fence_after();
+                    const int K = S::K(l), N = S::N(l);
+                    const uint32_t idesc = idesc_bf16(N);
+                    const uint32_t ba = imga + S::offset(l);
+#pragma unroll 1
+                    for (int ks = 0; ks < K / 16; ++ks) {
+                        const int ch = ks >> 2, kin = ks & 3;
+                        umma(tslot, sdesc(xa + ch * 16384 + kin * 32), sdesc(ba + ch * N * 128 + kin * 32), idesc,
+                             ks > 0 ? 1u : 0u);
                     }
                 }
-                e[63] = 1.0f;
-                if (!valid) {
+                umma_commit(&bar_d[slot]);
+                ++n_commits;
+            }
+            const bool got = mbar_wait(&bar_d[slot], d_ph, abortp, status);
+            if (issuer && got) ++n_waits;
+            d_ph ^= 1u;
+            // tcgen05.ld is warp-collective: the warp decides together; the
+            // slot decides together at the next barrier
+            if (!__all_sync(0xffffffffu, got)) {
+                aborted = true;
+                continue;
+            }
+            tc_fence_after();
+            if (l < H + 2) {
+                uint32_t r[W / 16][16];
 #pragma unroll
-                    for (int q = 0; q < 64; ++q) e[q] = 0.f;
+                for (int c = 0; c < W / 16; ++c) tmem_ld16_nowait(trow + 16 * c, r[c]);
+                uint32_t rs[16];
+                if (l == H) tmem_ld16_nowait(trow + W, rs);
+                tmem_wait_ld();
+                if (l == H) {
+                    // head: features stay linear; density from column W
+#pragma unroll
+                    for (int c = 0; c < W / 16; ++c) st_x16_bits<false>(X, row, 16 * c, r[c]);
+                    const float sl = __uint_as_float(rs[0]);
+                    sigma = sig_scale * (w.act == ROAM_RELU ? fmaxf(sl, 0.f) : softplus_f(sl));
+                } else {
+#pragma unroll
+                    for (int c = 0; c < W / 16; ++c) st_x16_bits<true>(X, row, 16 * c, r[c]);
                 }
+                if (l == 0) {
+                    // tail of X from here on: [1 | F(d) | 0 0 0 0] at columns W .. W+31
+                    float e[32];
+                    e[0] = valid ? 1.0f : 0.0f;
+                    const float dv[3] = {sm.dx, sm.dy, sm.dz};
+                    e[1] = dv[0]; e[2] = dv[1]; e[3] = dv[2];
 #pragma unroll
-                for (int c16 = 0; c16 < 4; ++c16) {
+                    for (int a = 0; a < 3; ++a) {
+                        float sn[4], cs[4];
+                        encode1<4>(dv[a], sn, cs);
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) {
+                            e[4 + 6 * k + a] = sn[k];
+                            e[7 + 6 * k + a] = cs[k];
+                        }
+                    }
+                    e[28] = e[29] = e[30] = e[31] = 0.f;
                     float v[16];
 #pragma unroll
-                    for (int q = 0; q < 16; ++q) v[q] = e[16 * c16 + q];
-                    st_x16(X, row, 16 * c16, v);
+                    for (int q = 0; q < 16; ++q) v[q] = e[q];
+                    st_x16(X, row, W, v);
+#pragma unroll
+                    for (int q = 0; q < 16; ++q) v[q] = e[16 + q];
+                    st_x16(X, row, W + 16, v);
                 }
-            }
-            fence_proxy_async();
-            mbar_arrive(&bar_x[slot]);
-            float sigma = 0.f;
-#pragma unroll 1
-            for (int l = 0; l < kLayers; ++l) {
-                // all lanes of the warp leave together (tcgen05.ld is warp-collective)
-                if (!__all_sync(0xffffffffu, mbar_wait(&bar_d[slot], d_ph, abortp, status))) break;
-                d_ph ^= 1u;
-                tc_fence_after();
-                if (l < H + 2) {
-                    const float *bl = nullptr;
-                    if (l >= 1 && l < H) bl = bias + (l - 1) * W;          // hidden
-                    else if (l == H) bl = bias + (H - 1) * W;              // head features, then density
-                    uint32_t r[W / 16][16];
-#pragma unroll
-                    for (int c = 0; c < W / 16; ++c) tmem_ld16_nowait(trow + 16 * c, r[c]);
-                    uint32_t rs[16];
-                    if (l == H) tmem_ld16_nowait(trow + W, rs);
-                    tmem_wait_ld();
-#pragma unroll
-                    for (int c = 0; c < W / 16; ++c) {
-                        float v[16];
-#pragma unroll
-                        for (int q = 0; q < 16; ++q) v[q] = __uint_as_float(r[c][q]);
-                        if (bl) {
-                            const float4 *b4 = reinterpret_cast<const float4 *>(bl + 16 * c);
-#pragma unroll
-                            for (int q4 = 0; q4 < 4; ++q4) {
-                                const float4 bb = __ldg(b4 + q4);
-                                v[4 * q4 + 0] += bb.x; v[4 * q4 + 1] += bb.y; v[4 * q4 + 2] += bb.z; v[4 * q4 + 3] += bb.w;
-                            }
-                        }
-                        if (l != H) {
-#pragma unroll
-                            for (int q = 0; q < 16; ++q) v[q] = fmaxf(v[q], 0.f);
-                        }
-                        st_x16(X, row, 16 * c, v);
-                    }
-                    if (l == H) {
-                        const float sl = __uint_as_float(rs[0]) + __ldg(bl + W);
-                        sigma = sig_scale * (w.act == ROAM_RELU ? fmaxf(sl, 0.f) : softplus_f(sl));
-                    }
-                    if (l == 0) {
-                        // colour-layer tail of X: [F(d) | 1 | 0 0 0 0] at columns W .. W+31
-                        float e[32];
-                        e[0] = dx; e[1] = dy; e[2] = dz;
-                        const float dv[3] = {dx, dy, dz};
-#pragma unroll
-                        for (int a = 0; a < 3; ++a) {
-                            float sn[4], cs[4];
-                            encode1<4>(dv[a], sn, cs);
-#pragma unroll
-                            for (int k = 0; k < 4; ++k) {
-                                e[3 + 6 * k + a] = sn[k];
-                                e[6 + 6 * k + a] = cs[k];
-                            }
-                        }
-                        e[27] = valid ? 1.0f : 0.0f;
-                        e[28] = e[29] = e[30] = e[31] = 0.f;
-                        float v[16];
-#pragma unroll
-                        for (int q = 0; q < 16; ++q) v[q] = e[q];
-                        st_x16(X, row, W, v);
-#pragma unroll
-                        for (int q = 0; q < 16; ++q) v[q] = e[16 + q];
-                        st_x16(X, row, W + 16, v);
-                    }
-                    tc_fence_before();
-                    fence_proxy_async();
-                    mbar_arrive(&bar_x[slot]);
-                } else {
-                    // output layer: rgb = sigmoid(z + b)
-                    uint32_t r[16];
-                    tmem_ld16_nowait(trow, r);
-                    tmem_wait_ld();
-                    tc_fence_before();
-                    const float *bo = bias + (H - 1) * W + W + 1;
-                    if (valid)
-                        out[idx] = make_float4(sigma, sigmoid_f(__uint_as_float(r[0]) + __ldg(bo + 0)),
-                                               sigmoid_f(__uint_as_float(r[1]) + __ldg(bo + 1)),
-                                               sigmoid_f(__uint_as_float(r[2]) + __ldg(bo + 2)));
-                }
+                tc_fence_before();
+            } else {
+                // output layer: rgb = sigmoid(z)
+                uint32_t r[16];
+                tmem_ld16_nowait(trow, r);
+                tmem_wait_ld();
+                tc_fence_before();
+                if (valid)
+                    out[sm.idx] = make_float4(sigma, sigmoid_f(__uint_as_float(r[0])), sigmoid_f(__uint_as_float(r[1])),
+                                              sigmoid_f(__uint_as_float(r[2])));
             }
         }
     }
+    // drain before TMEM is freed and the CTA exits: a commit whose wait gave
+    // up, and an image load nobody waited for
+    if (issuer && n_commits > n_waits) mbar_wait(&bar_d[slot], (n_commits - 1) & 1u, abortp, status, true);
+    if (threadIdx.x == 0 && !w_waited_last) mbar_wait(&bar_w, (n_changes - 1) & 1u, abortp, status, true);
     tc_fence_before();
     __syncthreads();
-    if (warp == kMma) {
+    if (warp == 0) {
         tc_fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemAlloc)
                      : "memory");
@@ -592,16 +608,25 @@ __global__ void k_pack_tc(const float *__restrict__ w32, int n_fields, int64_t P
                 else if (k == kPeX) v = wf[o_l1 + (int64_t)W * kPeX + nrow];
             } else if (l < H) {
                 const int64_t ob = o_hid + (int64_t)(l - 1) * (W * W + W);
-                v = wf[ob + (int64_t)nrow * W + k];
+                if (k < W) v = wf[ob + (int64_t)nrow * W + k];
+                else if (k == W) v = wf[ob + (int64_t)W * W + nrow];
             } else if (l == H) {
-                if (nrow < W) v = wf[o_head + (int64_t)(1 + nrow) * W + k];
-                else if (nrow == W) v = wf[o_head + k];
+                // rows: W features (API rows 1..W), then the density logit (API row 0)
+                const int ar = nrow < W ? 1 + nrow : (nrow == W ? 0 : -1);
+                if (ar >= 0) {
+                    if (k < W) v = wf[o_head + (int64_t)ar * W + k];
+                    else if (k == W) v = wf[o_head + (int64_t)(1 + W) * W + ar];
+                }
             } else if (l == H + 1) {
                 const int kc = W + kPeD;
-                if (k < kc) v = wf[o_col + (int64_t)nrow * kc + k];
-                else if (k == kc) v = wf[o_col + (int64_t)W * kc + nrow];
+                if (k < W) v = wf[o_col + (int64_t)nrow * kc + k];
+                else if (k == W) v = wf[o_col + (int64_t)W * kc + nrow];
+                else if (k <= W + kPeD) v = wf[o_col + (int64_t)nrow * kc + (k - 1)];
             } else {
-                if (nrow < 3) v = wf[o_out + (int64_t)nrow * W + k];
+                if (nrow < 3) {
+                    if (k < W) v = wf[o_out + (int64_t)nrow * W + k];
+                    else if (k == W) v = wf[o_out + 3 * W + nrow];
+                }
             }
         }
         const uint32_t bits = __float_as_uint(v);
@@ -633,17 +658,19 @@ __global__ void k_pack_tc(const float *__restrict__ w32, int n_fields, int64_t P
 constexpr int kSlotsTc = 4;
 
 template <int W, int H>
+int tc_smem_bytes() { return 1024 + TcShape<W, H>::kImageBytes + kSlotsTc * TcShape<W, H>::kXBytes; }
+
+template <int W, int H>
 void launch_t(const MlpWeights &w, const SampleSrc &src, const BucketBufs &b, Counters *ctr, float4 *out, int n_sm,
               cudaStream_t s)
 {
-    using S = TcShape<W, H>;
-    const int smem = 1024 + S::kImageBytes + kSlotsTc * S::kXBytes;
+    const int smem = tc_smem_bytes<W, H>();
     static bool attr = false;
     if (!attr) {
         cudaFuncSetAttribute(k_mlp_tc<W, H, kSlotsTc>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         attr = true;
     }
-    k_mlp_tc<W, H, kSlotsTc><<<n_sm, (kSlotsTc * 4 + 1) * 32, smem, s>>>(w, src, b, ctr, out);
+    k_mlp_tc<W, H, kSlotsTc><<<n_sm, kSlotsTc * 128, smem, s>>>(w, src, b, ctr, out);
 }
 
 }  // namespace
@@ -651,8 +678,8 @@ void launch_t(const MlpWeights &w, const SampleSrc &src, const BucketBufs &b, Co
 bool tc_supported(int W, int H)
 {
     if (H < 1 || H > 4) return false;
-    if (W == 32) return 1024 + TcShape<32, 4>::kImageBytes + kSlotsTc * TcShape<32, 4>::kXBytes <= 227 * 1024;
-    if (W == 64) return 1024 + TcShape<64, 4>::kImageBytes + kSlotsTc * TcShape<64, 4>::kXBytes <= 227 * 1024;
+    if (W == 32) return tc_smem_bytes<32, 4>() <= 227 * 1024;
+    if (W == 64) return tc_smem_bytes<64, 4>() <= 227 * 1024;
     return false;   // W = 128: the full image does not fit next to the activations
 }
 
