@@ -15,8 +15,8 @@
 //   after L1        [h (W) | 1 | F(d) (27) | 0 0 0 0]             (the tail stays)
 //   hidden / head   [h (W) | 1 | ...]     B zero past the bias    K = W + 16
 //   colour          [feat (W) | 1 | F(d) (27) | 0 0 0 0]          K = W + 32
-//   output          [g (W) | 1 | ...]                             K = W + 16
-// Head N = W + 16 (W features, then the density logit), output N = 16.
+// Head N = W + 16 (W features, then the density logit).  The 3-output colour
+// layer is a dot product per thread in the colour layer's epilogue.
 #include "internal.cuh"
 
 namespace roam {
@@ -33,9 +33,9 @@ struct TcShape {
     static constexpr int N_HEAD = W + 16;
     static constexpr int K_COL = W + 32;
     static constexpr int N_OUT = 16;
-    static constexpr int kLayers = H + 3;
+    static constexpr int kLayers = H + 2;      // L1, hidden, head, colour (the 3-output layer runs on CUDA cores)
     __host__ __device__ static constexpr int K(int l) { return l == 0 ? 64 : (l == H + 1 ? K_COL : W + 16); }
-    __host__ __device__ static constexpr int N(int l) { return l == H ? N_HEAD : (l == H + 2 ? N_OUT : W); }
+    __host__ __device__ static constexpr int N(int l) { return l == H ? N_HEAD : W; }
     __host__ __device__ static constexpr int chunks(int l) { return cdiv(K(l), 64); }
     __host__ __device__ static constexpr int bytes(int l) { return chunks(l) * N(l) * 128; }
     __host__ __device__ static constexpr int offset(int l)
@@ -44,7 +44,11 @@ struct TcShape {
         for (int i = 0; i < l; ++i) o += bytes(i);
         return o;
     }
-    static constexpr int kImageBytes = offset(H + 3);
+    static constexpr int kMatBytes = offset(H + 2);
+    // after the MMA operands: FP32 output layer, [W][4] (3 outputs + pad) then bias[4]
+    static constexpr int kOutBytes = (4 * W + 4) * 4;
+    static constexpr int kImageBytes = kMatBytes + kOutBytes;
+    static constexpr int kImageAlloc = (kImageBytes + 1023) & ~1023;
     static constexpr int kXChunks = cdiv(K_COL, 64) > 1 ? cdiv(K_COL, 64) : 1;
     static constexpr int kXBytes = kXChunks * 128 * 128;
     static constexpr int kNBias = ((H - 1) * W + W + 1 + 3 + 3) & ~3;
@@ -78,15 +82,18 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes)
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
 }
 
+// try_wait with a suspend-time hint: the warp sleeps in hardware until the
+// phase completes (or ~20 us pass) instead of spinning on issue slots that
+// the other slots' warps need
 __device__ __forceinline__ bool mbar_try(uint64_t *bar, uint32_t parity)
 {
     uint32_t ok;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
         "selp.u32 %0, 1, 0, p;\n\t}"
         : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
+        : "r"(smem_u32(bar)), "r"(parity), "r"(20000u)
         : "memory");
     return ok != 0;
 }
@@ -107,7 +114,7 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volati
     const unsigned long long t0 = now_ns();
     for (uint32_t it = 0;; ++it) {
         if (mbar_try(bar, parity)) return true;
-        if ((it & 63u) == 63u) {
+        {
             if (*abort_flag && !drain) return false;
             if (now_ns() - t0 > kWaitNs) {
                 *abort_flag = 1;
@@ -364,7 +371,7 @@ __global__ void __launch_bounds__(kSlots * 128, 1)
 
     const uint32_t base = (smem_u32(smem_raw) + 1023u) & ~1023u;
     uint8_t *IMG = smem_raw + (base - smem_u32(smem_raw));
-    uint8_t *X0 = IMG + S::kImageBytes;
+    uint8_t *X0 = IMG + S::kImageAlloc;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int slot = warp >> 2, wq = warp & 3;
     const int row = wq * 32 + lane;                           // TMEM lane == tile row
@@ -505,13 +512,14 @@ __global__ void __launch_bounds__(kSlots * 128, 1)
                 continue;
             }
             tc_fence_after();
-            if (l < H + 2) {
-                uint32_t r[W / 16][16];
+            uint32_t r[W / 16][16];
 #pragma unroll
-                for (int c = 0; c < W / 16; ++c) tmem_ld16_nowait(trow + 16 * c, r[c]);
-                uint32_t rs[16];
-                if (l == H) tmem_ld16_nowait(trow + W, rs);
-                tmem_wait_ld();
+            for (int c = 0; c < W / 16; ++c) tmem_ld16_nowait(trow + 16 * c, r[c]);
+            uint32_t rs[16];
+            if (l == H) tmem_ld16_nowait(trow + W, rs);
+            tmem_wait_ld();
+            tc_fence_before();
+            if (l < H + 1) {
                 if (l == H) {
                     // head: features stay linear; density from column W
 #pragma unroll
@@ -547,16 +555,25 @@ __global__ void __launch_bounds__(kSlots * 128, 1)
                     for (int q = 0; q < 16; ++q) v[q] = e[16 + q];
                     st_x16(X, row, W + 16, v);
                 }
-                tc_fence_before();
             } else {
-                // output layer: rgb = sigmoid(z)
-                uint32_t r[16];
-                tmem_ld16_nowait(trow, r);
-                tmem_wait_ld();
-                tc_fence_before();
-                if (valid)
-                    out[sm.idx] = make_float4(sigma, sigmoid_f(__uint_as_float(r[0])), sigmoid_f(__uint_as_float(r[1])),
-                                              sigmoid_f(__uint_as_float(r[2])));
+                // colour layer: g = relu(z) in FP32, then rgb = sigmoid(Wo g + bo) with
+                // the FP32 output table at the end of the shared image (this thread
+                // waits for the image itself before reading it with generic loads)
+                mbar_wait(&bar_w, (n_changes - 1) & 1u, abortp, status);
+                const float4 *wo = reinterpret_cast<const float4 *>(IMG + S::kMatBytes);
+                float4 acc = wo[W];
+#pragma unroll
+                for (int c = 0; c < W / 16; ++c) {
+#pragma unroll
+                    for (int q = 0; q < 16; ++q) {
+                        const float gk = fmaxf(__uint_as_float(r[c][q]), 0.f);
+                        const float4 wk = wo[16 * c + q];
+                        acc.x = fmaf(wk.x, gk, acc.x);
+                        acc.y = fmaf(wk.y, gk, acc.y);
+                        acc.z = fmaf(wk.z, gk, acc.z);
+                    }
+                }
+                if (valid) out[sm.idx] = make_float4(sigma, sigmoid_f(acc.x), sigmoid_f(acc.y), sigmoid_f(acc.z));
             }
         }
     }
@@ -584,7 +601,7 @@ __global__ void k_pack_tc(const float *__restrict__ w32, int n_fields, int64_t P
     const int64_t o_head = o_hid + (int64_t)(H - 1) * (W * W + W);
     const int64_t o_col = o_head + (int64_t)(1 + W) * W + (1 + W);
     const int64_t o_out = o_col + (int64_t)W * (W + kPeD) + W;
-    const int64_t per = img_bytes / 2;           // BF16 elements per field image
+    const int64_t per = S::kMatBytes / 2;        // BF16 elements of the MMA operands per field
     const int64_t n = (int64_t)n_fields * per;
     for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x) {
         const int64_t f = g / per;
@@ -622,17 +639,28 @@ __global__ void k_pack_tc(const float *__restrict__ w32, int n_fields, int64_t P
                 if (k < W) v = wf[o_col + (int64_t)nrow * kc + k];
                 else if (k == W) v = wf[o_col + (int64_t)W * kc + nrow];
                 else if (k <= W + kPeD) v = wf[o_col + (int64_t)nrow * kc + (k - 1)];
-            } else {
-                if (nrow < 3) {
-                    if (k < W) v = wf[o_out + (int64_t)nrow * W + k];
-                    else if (k == W) v = wf[o_out + 3 * W + nrow];
-                }
             }
         }
         const uint32_t bits = __float_as_uint(v);
         // round to nearest even
         const uint32_t r = bits + 0x7fffu + ((bits >> 16) & 1u);
-        reinterpret_cast<uint16_t *>(img)[g] = (uint16_t)(r >> 16);
+        reinterpret_cast<uint16_t *>(img + f * img_bytes)[g % per] = (uint16_t)(r >> 16);
+    }
+    // FP32 output layer after the operands: [W][4] (weights of the 3 colours, pad 0), then bias[4]
+    const int nout = 4 * W + 4;
+    for (int64_t gi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; gi < (int64_t)n_fields * nout;
+         gi += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t f = gi / nout;
+        const int q = (int)(gi % nout);
+        const float *wf = w32 + f * P;
+        float v = 0.f;
+        if (q < 4 * W) {
+            const int k = q / 4, c = q % 4;
+            if (c < 3) v = wf[o_out + (int64_t)c * W + k];
+        } else if (q - 4 * W < 3) {
+            v = wf[o_out + 3 * W + (q - 4 * W)];
+        }
+        reinterpret_cast<float *>(img + f * img_bytes + S::kMatBytes)[q] = v;
     }
     // bias table: hidden (H-1)*W, head features W, head density 1, output 3
     const int64_t nbt = (int64_t)n_fields * nb;
@@ -658,7 +686,7 @@ __global__ void k_pack_tc(const float *__restrict__ w32, int n_fields, int64_t P
 constexpr int kSlotsTc = 4;
 
 template <int W, int H>
-int tc_smem_bytes() { return 1024 + TcShape<W, H>::kImageBytes + kSlotsTc * TcShape<W, H>::kXBytes; }
+int tc_smem_bytes() { return 1024 + TcShape<W, H>::kImageAlloc + kSlotsTc * TcShape<W, H>::kXBytes; }
 
 template <int W, int H>
 void launch_t(const MlpWeights &w, const SampleSrc &src, const BucketBufs &b, Counters *ctr, float4 *out, int n_sm,
