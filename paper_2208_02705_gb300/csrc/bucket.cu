@@ -212,4 +212,13 @@ void launch_bucket(const uint32_t *cnt, const uint32_t *recs, const uint32_t *li
     k_scatter<<<grid, 512, 0, s>>>(cnt, recs, live_count, n_fixed, R, keys16, n_fields, b.cursor, b.sorted);
 }
 
+void launch_bucket_ready(const uint32_t *cnt, const uint32_t *recs, const uint32_t *live_count, uint32_t n_fixed,
+                         int R, int group, int n_fields, int tile, const BucketBufs &b, Counters *ctr, int grid,
+                         cudaStream_t s)
+{
+    k_scan<<<1, 1024, (size_t)(n_fields + 1) * sizeof(uint32_t), s>>>(b.hist, n_fields, tile, group < 1 ? 1 : group,
+                                                                       b.offsets, b.cursor, b.tiles, ctr);
+    k_scatter<<<grid, 512, 0, s>>>(cnt, recs, live_count, n_fixed, R, nullptr, n_fields, b.cursor, b.sorted);
+}
+
 }  // namespace roam

@@ -30,12 +30,12 @@ struct DevCamera {
 
 struct GridDev {
     int gx, gy, gz, wpr;          // wpr = gx / 32
-    int bx, by, bz, bwpr;         // brick grid, bwpr = ceil(bx / 32)
+    int bx, by, bz;               // brick grid (8^3 voxels per brick)
     float origin[3];
     float vox, inv_vox;
     const uint32_t *bits;         // [gz][gy][wpr]
     const uint32_t *prefix;       // exclusive popcount before each word
-    const uint32_t *brick;        // [bz][by][bwpr] non-empty brick bits
+    const uint8_t *brick_dist;    // [bz][by][bx] Chebyshev distance (bricks) to an occupied brick, 0 = occupied
     const uint16_t *labels;       // field of each occupied voxel, rank order
     int n_fields;
 };
@@ -87,6 +87,7 @@ struct MarchParams {
     uint32_t *cnt;              // per live index: samples emitted
     uint32_t *recs;             // j | field << 16
     Counters *ctr;
+    uint32_t *hist;             // if set: field histogram of the emitted samples (added to)
 };
 
 // Sample source of the MLP kernels.
@@ -137,10 +138,13 @@ struct MlpWeights {
 
 void launch_grid_prefix(const uint32_t *bits, uint32_t *prefix, uint32_t *block_sums,
                         int64_t n_words, cudaStream_t s);
-void launch_brick_map(GridDev g, uint32_t *brick, cudaStream_t s);
+void launch_brick_dist(GridDev g, uint8_t *occ, uint16_t *t0, uint16_t *t1, uint8_t *dist, cudaStream_t s);
 void launch_march(const GridDev &g, const MarchParams &p, int grid, cudaStream_t s);
 // tiles of `tile` samples, every non-empty field's tile count rounded up to a
-// multiple of `group`
+// multiple of `group`; with hist_ready the histogram is already in b.hist
+void launch_bucket_ready(const uint32_t *cnt, const uint32_t *recs, const uint32_t *live_count,
+                         uint32_t n_fixed, int R, int group, int n_fields, int tile, const BucketBufs &b,
+                         Counters *ctr, int grid, cudaStream_t s);
 void launch_bucket(const uint32_t *cnt, const uint32_t *recs, const uint32_t *live_count,
                    uint32_t n_fixed, int R, int group, const uint16_t *keys16,
                    int n_fields, int tile, const BucketBufs &b, Counters *ctr, int grid,

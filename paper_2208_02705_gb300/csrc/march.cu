@@ -2,7 +2,7 @@
 // grid and field lookup (Sec. "Real-time Rendering Speedup": rays are cast
 // through a GPU-resident voxel structure to find occupied voxels, one ray
 // per thread, each occupied voxel carrying the id of its tiny MLP), plus the
-// load-time kernels that build the rank prefix and the brick occupancy map.
+// load-time kernels that build the rank prefix and the brick distance map.
 #include "internal.cuh"
 
 namespace roam {
@@ -80,8 +80,8 @@ __global__ void k_prefix_add(uint32_t *prefix, const uint32_t *block_sums, int64
     if (i < n_words) prefix[i] += block_sums[i / 4096];
 }
 
-// one thread per 8^3 brick: OR of its 512 voxel bits
-__global__ void k_brick_map(GridDev g, uint32_t *brick)
+// one thread per 8^3 brick: 1 if any of its 512 voxels is occupied
+__global__ void k_brick_occ(GridDev g, uint8_t *occ)
 {
     const int64_t n = (int64_t)g.bx * g.by * g.bz;
     for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < n; b += (int64_t)gridDim.x * blockDim.x) {
@@ -93,8 +93,40 @@ __global__ void k_brick_map(GridDev g, uint32_t *brick)
                 const uint32_t w = g.bits[((int64_t)z * g.gy + y) * g.wpr + (x0 >> 5)];
                 any |= (w >> (x0 & 31)) & 0xffu;
             }
-        if (any) atomicOr(&brick[((int64_t)bz * g.by + by) * g.bwpr + (bx >> 5)], 1u << (bx & 31));
+        occ[b] = any ? 1 : 0;
     }
+}
+
+// Chebyshev (L-infinity) distance, in bricks, from every brick to the nearest
+// occupied brick, separably: along x from the occupancy, then along y and z
+// taking max(|offset|, previous distance).  0 marks an occupied brick.
+__global__ void k_brick_dist(GridDev g, int axis, const uint8_t *occ, const uint16_t *src, uint16_t *dst)
+{
+    const int ext[3] = {g.bx, g.by, g.bz};
+    const int64_t n = (int64_t)g.bx * g.by * g.bz;
+    for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < n; b += (int64_t)gridDim.x * blockDim.x) {
+        int c[3] = {(int)(b % g.bx), (int)((b / g.bx) % g.by), (int)(b / ((int64_t)g.bx * g.by))};
+        const int64_t stride = axis == 0 ? 1 : (axis == 1 ? g.bx : (int64_t)g.bx * g.by);
+        const int64_t b0 = b - (int64_t)c[axis] * stride;
+        int best = 0xffff;
+        for (int u = 0; u < ext[axis]; ++u) {
+            const int off = u > c[axis] ? u - c[axis] : c[axis] - u;
+            int v;
+            if (axis == 0) v = occ[b0 + u * stride] ? off : 0xffff;
+            else {
+                const int prev = src[b0 + u * stride];
+                v = prev == 0xffff ? 0xffff : (off > prev ? off : prev);
+            }
+            best = v < best ? v : best;
+        }
+        dst[b] = (uint16_t)best;
+    }
+}
+
+__global__ void k_brick_final(int64_t n, const uint16_t *d16, uint8_t *dist)
+{
+    for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < n; b += (int64_t)gridDim.x * blockDim.x)
+        dist[b] = (uint8_t)(d16[b] > 255 ? 255 : d16[b]);
 }
 
 // Pixel -> world ray.  Equirectangular: Eq. 2 gives longitude
@@ -168,11 +200,19 @@ __device__ __forceinline__ int view_of(const DevCamera *cams, int n_views, uint3
 
 // Sample j of a ray sits at t_j = (j + 1/2) delta and is kept iff its voxel
 // floor((o + t_j d - origin) / vox) is inside the grid and occupied.  The
-// walk tests samples one by one inside non-empty 8^3 bricks and jumps over
-// empty bricks to the first sample past the brick's exit (minus one, so that
-// a sample rounded onto the exit face is still tested).
+// walk tests samples in occupied voxels one by one and jumps over empty
+// space: out of an empty voxel to the first sample past its exit face, and
+// out of an empty brick to the first sample past the exit of the largest
+// empty cube of bricks around it (from the brick distance map), minus one
+// sample so that a sample rounded onto that face is still tested.  Emitted
+// records also feed a per-block field histogram for the bucketing.
 __global__ void __launch_bounds__(256) k_march(GridDev g, MarchParams p)
 {
+    extern __shared__ uint32_t s_hist[];      // per-block field histogram (when p.hist)
+    if (p.hist) {
+        for (int f = threadIdx.x; f < g.n_fields; f += blockDim.x) s_hist[f] = 0;
+        __syncthreads();
+    }
     if (blockIdx.x == 0 && threadIdx.x == 0 && p.live_count != nullptr) {
         // the count slot the composite of this round fills is the one the
         // previous round read: clear it for reuse
@@ -272,12 +312,14 @@ __global__ void __launch_bounds__(256) k_march(GridDev g, MarchParams p)
                 continue;
             }
             const int bxi = ix >> kBrickShift, byi = iy >> kBrickShift, bzi = iz >> kBrickShift;
-            const uint32_t bw = __ldg(&g.brick[((int64_t)bzi * g.by + byi) * g.bwpr + (bxi >> 5)]);
-            if (!((bw >> (bxi & 31)) & 1u)) {
-                // exit of the empty brick along the ray (voxel units)
-                const float ex = dgx > 0.f ? (float)((bxi + 1) << kBrickShift) : (float)(bxi << kBrickShift);
-                const float ey = dgy > 0.f ? (float)((byi + 1) << kBrickShift) : (float)(byi << kBrickShift);
-                const float ez = dgz > 0.f ? (float)((bzi + 1) << kBrickShift) : (float)(bzi << kBrickShift);
+            const int dd = __ldg(&g.brick_dist[((int64_t)bzi * g.by + byi) * g.bx + bxi]);
+            if (dd > 0) {
+                // every brick within Chebyshev distance dd - 1 is empty: leave that
+                // cube of bricks in one step (voxel units, clamped to the grid)
+                const int r = dd - 1;
+                const float ex = dgx > 0.f ? (float)(min(bxi + r + 1, g.bx) << kBrickShift) : (float)(max(bxi - r, 0) << kBrickShift);
+                const float ey = dgy > 0.f ? (float)(min(byi + r + 1, g.by) << kBrickShift) : (float)(max(byi - r, 0) << kBrickShift);
+                const float ez = dgz > 0.f ? (float)(min(bzi + r + 1, g.bz) << kBrickShift) : (float)(max(bzi - r, 0) << kBrickShift);
                 float te = 3.0e38f;
                 if (dgx != 0.f) te = fminf(te, (ex - ogx) * idx);
                 if (dgy != 0.f) te = fminf(te, (ey - ogy) * idy);
@@ -290,7 +332,21 @@ __global__ void __launch_bounds__(256) k_march(GridDev g, MarchParams p)
             const int64_t wi = ((int64_t)iz * g.gy + iy) * g.wpr + (ix >> 5);
             const uint32_t w = __ldg(&g.bits[wi]);
             const uint32_t b = (uint32_t)(ix & 31);
-            if ((w >> b) & 1u) {
+            if (!((w >> b) & 1u)) {
+                // empty voxel: jump to the first sample past its exit face
+                const float ex = dgx > 0.f ? (float)(ix + 1) : (float)ix;
+                const float ey = dgy > 0.f ? (float)(iy + 1) : (float)iy;
+                const float ez = dgz > 0.f ? (float)(iz + 1) : (float)iz;
+                float te = 3.0e38f;
+                if (dgx != 0.f) te = fminf(te, (ex - ogx) * idx);
+                if (dgy != 0.f) te = fminf(te, (ey - ogy) * idy);
+                if (dgz != 0.f) te = fminf(te, (ez - ogz) * idz);
+                const float jf = ceilf(te / delta - 0.5f);
+                const uint32_t jj = jf > (float)je ? je : (jf > 0.f ? (uint32_t)jf : 0u);
+                jn = jj > jn + 1 ? jj : jn + 1;
+                continue;
+            }
+            {
                 const uint32_t rank = __ldg(&g.prefix[wi]) + (uint32_t)__popc(w & ((1u << b) - 1u));
                 uint32_t f = __ldg(&g.labels[rank]);
                 if (f >= (uint32_t)g.n_fields) {
@@ -299,6 +355,7 @@ __global__ void __launch_bounds__(256) k_march(GridDev g, MarchParams p)
                 }
                 const uint32_t s = p.flat ? i * R + em : slot_of(i, em, R);
                 p.recs[s] = jn | (f << 16);
+                if (p.hist) atomicAdd(&s_hist[f], 1u);
                 ++em;
                 ++nk;
             }
@@ -307,6 +364,11 @@ __global__ void __launch_bounds__(256) k_march(GridDev g, MarchParams p)
         p.cnt[i] = em;
         p.st.j_next[ray] = jn;
         p.st.n_kept[ray] = nk;
+    }
+    if (p.hist) {
+        __syncthreads();
+        for (int f = threadIdx.x; f < g.n_fields; f += blockDim.x)
+            if (s_hist[f]) atomicAdd(&p.hist[f], s_hist[f]);
     }
 }
 
@@ -321,16 +383,20 @@ void launch_grid_prefix(const uint32_t *bits, uint32_t *prefix, uint32_t *block_
     k_prefix_add<<<(unsigned)((n_words + 255) / 256), 256, 0, s>>>(prefix, block_sums, n_words);
 }
 
-void launch_brick_map(GridDev g, uint32_t *brick, cudaStream_t s)
+void launch_brick_dist(GridDev g, uint8_t *occ, uint16_t *t0, uint16_t *t1, uint8_t *dist, cudaStream_t s)
 {
     const int64_t n = (int64_t)g.bx * g.by * g.bz;
     const int blocks = (int)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096);
-    k_brick_map<<<blocks, 256, 0, s>>>(g, brick);
+    k_brick_occ<<<blocks, 256, 0, s>>>(g, occ);
+    k_brick_dist<<<blocks, 256, 0, s>>>(g, 0, occ, nullptr, t0);
+    k_brick_dist<<<blocks, 256, 0, s>>>(g, 1, occ, t0, t1);
+    k_brick_dist<<<blocks, 256, 0, s>>>(g, 2, occ, t1, t0);
+    k_brick_final<<<blocks, 256, 0, s>>>(n, t0, dist);
 }
 
 void launch_march(const GridDev &g, const MarchParams &p, int grid, cudaStream_t s)
 {
-    k_march<<<grid, 256, 0, s>>>(g, p);
+    k_march<<<grid, 256, p.hist ? (size_t)g.n_fields * sizeof(uint32_t) : 0, s>>>(g, p);
 }
 
 }  // namespace roam

@@ -96,7 +96,9 @@ struct roam_ctx {
     roam_grid_desc gd{};
     GridDev g{};
     int64_t n_words = 0, n_occ = 0;
-    DBuf<uint32_t> bits, prefix, brick, block_sums;
+    DBuf<uint32_t> bits, prefix, block_sums;
+    DBuf<uint8_t> brick_occ, brick_dist;
+    DBuf<uint16_t> brick_t0, brick_t1;
     // fields
     bool has_fields = false;
     int n_fields = 0;
@@ -403,6 +405,7 @@ roam_status run_rounds(roam_ctx *c, const uint32_t *rays, int64_t n_rays, const 
     mp.cnt = c->cnt.p;
     mp.recs = c->recs.p;
     mp.ctr = c->ctr;
+    mp.hist = c->hist.p;             // the march counts samples per field as it emits them
     const BucketBufs b = bucket_of(c);
     const int grid = grid_blocks(c, 4);
     uint32_t *lives[2] = {c->live0.p, c->live1.p};
@@ -417,8 +420,8 @@ roam_status run_rounds(roam_ctx *c, const uint32_t *rays, int64_t n_rays, const 
         ROAM_TRY(launched("march"));
         {
             ProfScope ps(c, P_BUCKET, s);
-            launch_bucket(mp.cnt, mp.recs, mp.live_count, mp.n_rays, R, group_of(o->precision), nullptr,
-                          c->n_fields, tile_of(o->precision), b, c->ctr, grid, s);
+            launch_bucket_ready(mp.cnt, mp.recs, mp.live_count, mp.n_rays, R, group_of(o->precision), c->n_fields,
+                                tile_of(o->precision), b, c->ctr, grid, s);
         }
         ROAM_TRY(launched("bucket"));
         SampleSrc src{};
@@ -497,7 +500,8 @@ roam_status roam_destroy(roam_ctx *c)
     if (!c) return ROAM_OK;
     cudaSetDevice(c->device);
     cudaDeviceSynchronize();
-    release(c->bits); release(c->prefix); release(c->brick); release(c->block_sums);
+    release(c->bits); release(c->prefix); release(c->block_sums);
+    release(c->brick_occ); release(c->brick_dist); release(c->brick_t0); release(c->brick_t1);
     release(c->labels); release(c->affine);
     release(c->w32); release(c->wt); release(c->wr); release(c->gsr); release(c->bias); release(c->adam_m); release(c->adam_v); release(c->wimg);
     release(c->orig); release(c->dir); release(c->dir_lo); release(c->acc); release(c->sr); release(c->tw);
@@ -549,22 +553,23 @@ roam_status roam_load_grid(roam_ctx *c, const roam_grid_desc *desc, const uint32
     g.gx = desc->dims[0]; g.gy = desc->dims[1]; g.gz = desc->dims[2];
     g.wpr = g.gx / 32;
     g.bx = g.gx >> kBrickShift; g.by = g.gy >> kBrickShift; g.bz = g.gz >> kBrickShift;
-    g.bwpr = (g.bx + 31) / 32;
     for (int a = 0; a < 3; ++a) g.origin[a] = desc->origin[a];
     g.vox = desc->vox;
     g.inv_vox = 1.0f / desc->vox;
-    const int64_t n_brick_words = (int64_t)g.bwpr * g.by * g.bz;
-    ROAM_TRY(ensure(c->brick, (size_t)n_brick_words));
-    ROAM_CUDA(cudaMemset(c->brick.p, 0, n_brick_words * sizeof(uint32_t)));
+    const size_t n_bricks = (size_t)g.bx * g.by * g.bz;
+    ROAM_TRY(ensure(c->brick_occ, n_bricks));
+    ROAM_TRY(ensure(c->brick_dist, n_bricks));
+    ROAM_TRY(ensure(c->brick_t0, n_bricks));
+    ROAM_TRY(ensure(c->brick_t1, n_bricks));
     g.bits = c->bits.p;
     g.prefix = c->prefix.p;
-    g.brick = c->brick.p;
+    g.brick_dist = c->brick_dist.p;
     g.labels = nullptr;
     g.n_fields = 0;
     launch_grid_prefix(c->bits.p, c->prefix.p, c->block_sums.p, n_words, 0);
     ROAM_TRY(launched("grid prefix"));
-    launch_brick_map(g, c->brick.p, 0);
-    ROAM_TRY(launched("brick map"));
+    launch_brick_dist(g, c->brick_occ.p, c->brick_t0.p, c->brick_t1.p, c->brick_dist.p, 0);
+    ROAM_TRY(launched("brick distance map"));
     uint32_t last_pre = 0, last_word = 0;
     ROAM_CUDA(cudaMemcpy(&last_pre, c->prefix.p + n_words - 1, 4, cudaMemcpyDeviceToHost));
     ROAM_CUDA(cudaMemcpy(&last_word, c->bits.p + n_words - 1, 4, cudaMemcpyDeviceToHost));
@@ -691,6 +696,7 @@ roam_status roam_render(roam_ctx *c, const roam_camera *cams, int n_views, const
         if (opacity) { ROAM_TRY(ensure(c->o_op, (size_t)n_pix)); d_op = c->o_op.p; }
     }
     ROAM_CUDA(cudaMemsetAsync(c->ctr, 0, sizeof(Counters), s));
+    ROAM_CUDA(cudaMemsetAsync(c->hist.p, 0, (size_t)c->n_fields * sizeof(uint32_t), s));
     ROAM_TRY(run_rounds(c, nullptr, n_pix, opts, d_rgb, d_depth, d_op, R, s));
     c->last = s;
     c->last_rays = n_pix;
@@ -878,6 +884,7 @@ roam_status roam_train_forward(roam_ctx *c, const roam_camera *cams, int n_views
     if ((double)((n_rays + 31) & ~31LL) * R >= 4294967295.0) return fail(ROAM_ERR_ARG, "too many rays x samples");
     ROAM_TRY(ensure_rays(c, n_rays, R));
     ROAM_CUDA(cudaMemsetAsync(c->ctr, 0, sizeof(Counters), s));
+    ROAM_CUDA(cudaMemsetAsync(c->hist.p, 0, (size_t)c->n_fields * sizeof(uint32_t), s));
     ROAM_TRY(run_rounds(c, rays, n_rays, opts, rgb, nullptr, nullptr, R, s));
     c->last = s;
     c->last_rays = n_rays;
