@@ -2,21 +2,22 @@
 // queries of Sec. "Real-time Rendering Speedup" as a grouped GEMM chain on
 // the 5th-generation tensor cores).  One tile = 128 samples of one field =
 // one M=128 MMA row block; every layer of the chain is
-//   D[128 x N] (TMEM, FP32) = X[128 x K] (SMEM, BF16) * B[K x N] (SMEM, BF16)
-// with tcgen05.mma kind::f16.  Every bias rides in the MMA: X carries a
-// constant-1 column and B the bias in the matching row, so the epilogue only
-// converts (cvt.rn.relu.bf16x2 fuses the ReLU) and writes the next layer's X
-// in the 128-byte swizzled K-major layout.  The field's weight image (all
-// layers, pre-swizzled by launch_pack_tc) is copied to shared memory by the
-// bulk-copy (TMA) engine when the field changes.
+//   D[128 x N] (TMEM, FP32) = A[128 x K] (TMEM, BF16) * B[K x N] (SMEM, BF16)
+// with tcgen05.mma kind::f16.  The activations A never touch shared memory:
+// the epilogue reads D with tcgen05.ld (one row per thread), converts
+// (cvt.rn.relu.bf16x2 fuses the ReLU) and writes the next layer's A with
+// tcgen05.st, so the MMA streams only the weights from shared memory.  Every
+// bias rides in the MMA: A carries a constant-1 column and B the bias in the
+// matching row.  The field's weight image (all layers' B operands in the
+// 128-byte-swizzled K-major layout, then an FP32 table of the 3-output
+// layer) is copied to shared memory by the bulk-copy (TMA) engine when the
+// field changes.
 //
-// X columns (row = sample):
+// A columns (row = sample):
 //   L1 input        [F(x_loc) (63) | 1]                          K = 64
 //   after L1        [h (W) | 1 | F(d) (27) | 0 0 0 0]             (the tail stays)
 //   hidden / head   [h (W) | 1 | ...]     B zero past the bias    K = W + 16
 //   colour          [feat (W) | 1 | F(d) (27) | 0 0 0 0]          K = W + 32
-// Head N = W + 16 (W features, then the density logit).  The 3-output colour
-// layer is a dot product per thread in the colour layer's epilogue.
 #include "internal.cuh"
 
 namespace roam {
@@ -53,6 +54,11 @@ struct TcShape {
     static constexpr int kXBytes = kXChunks * 128 * 128;
     static constexpr int kNBias = ((H - 1) * W + W + 1 + 3 + 3) & ~3;
     static constexpr int kTmemCols = N_HEAD <= 32 ? 32 : (N_HEAD <= 64 ? 64 : (N_HEAD <= 128 ? 128 : 256));
+    // TMEM of one slot: accumulator D (N_HEAD columns), then the activations A
+    // of the next MMA (K_COL BF16 per row, two per 32-bit column)
+    static constexpr int kDCols = N_HEAD;
+    static constexpr int kACols = K_COL / 2;
+    static constexpr int kSlotCols = kDCols + kACols;
     static constexpr int kSmem = 1024 + kXBytes + kImageBytes + 64;
 };
 
@@ -267,6 +273,37 @@ __device__ __forceinline__ void tmem_ld16_nowait(uint32_t taddr, uint32_t (&r)[1
 
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
+// 16 consecutive 32-bit TMEM columns of this thread's lane
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&v)[16])
+{
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], "
+        "{%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(taddr),
+        "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]), "r"(v[8]), "r"(v[9]),
+        "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15])
+        : "memory");
+}
+
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
+// D (TMEM) [+]= A (TMEM, 128 lanes x K/2 columns of BF16 pairs) * B (SMEM descriptor)
+__device__ __forceinline__ void umma_ta(uint32_t d_tmem, uint32_t a_tmem, uint64_t b, uint32_t idesc, uint32_t acc)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "r"(a_tmem), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+}
+
+// 32 floats -> 16 BF16 pairs (element 2c in the low half of column c)
+__device__ __forceinline__ void pack16(const float *v, uint32_t (&o)[16])
+{
+#pragma unroll
+    for (int q = 0; q < 16; ++q) o[q] = pack_bf16(v[2 * q], v[2 * q + 1]);
+}
+
 __device__ __forceinline__ uint32_t pack_bf16_relu(float a, float b)
 {
     uint32_t r;
@@ -359,10 +396,10 @@ __global__ void __launch_bounds__(kSlots * 128, 1)
 {
     using S = TcShape<W, H>;
     constexpr int kLayers = S::kLayers;
-    constexpr int kCols = S::kTmemCols;
+    constexpr int kCols = S::kSlotCols;
     constexpr int kTmemAlloc = kSlots * kCols <= 32 ? 32 : (kSlots * kCols <= 64 ? 64 :
                                (kSlots * kCols <= 128 ? 128 : (kSlots * kCols <= 256 ? 256 : 512)));
-    static_assert(kSlots * kCols <= 512, "TMEM holds every slot's accumulator");
+    static_assert(kSlots * kCols <= 512, "TMEM holds every slot's accumulator and activations");
     extern __shared__ uint8_t smem_raw[];
     __shared__ uint64_t bar_d[kSlots];
     __shared__ uint64_t bar_w;
@@ -371,7 +408,6 @@ __global__ void __launch_bounds__(kSlots * 128, 1)
 
     const uint32_t base = (smem_u32(smem_raw) + 1023u) & ~1023u;
     uint8_t *IMG = smem_raw + (base - smem_u32(smem_raw));
-    uint8_t *X0 = IMG + S::kImageAlloc;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int slot = warp >> 2, wq = warp & 3;
     const int row = wq * 32 + lane;                           // TMEM lane == tile row
@@ -395,10 +431,11 @@ __global__ void __launch_bounds__(kSlots * 128, 1)
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = tmem_slot;
-    const uint32_t tslot = tmem + (uint32_t)(slot * kCols);
+    const uint32_t tslot = tmem + (uint32_t)(slot * kCols);        // accumulator D
+    const uint32_t tA = tslot + (uint32_t)S::kDCols;                  // activations A
     const uint32_t trow = tslot + ((uint32_t)(wq * 32) << 16);
-    uint8_t *X = X0 + slot * S::kXBytes;
-    const uint32_t xa = smem_u32(X), imga = smem_u32(IMG);
+    const uint32_t tArow = tA + ((uint32_t)(wq * 32) << 16);
+    const uint32_t imga = smem_u32(IMG);
 
     const uint32_t n_groups = ctr->n_tiles / kSlots;
     const uint32_t g0 = (uint32_t)((uint64_t)n_groups * blockIdx.x / gridDim.x);
@@ -461,21 +498,24 @@ __global__ void __launch_bounds__(kSlots * 128, 1)
                 }
             }
             e[63] = 1.0f;
+            if (!valid) {
 #pragma unroll
-            for (int c16 = 0; c16 < 4; ++c16) {
-                float v[16];
-#pragma unroll
-                for (int q = 0; q < 16; ++q) v[q] = valid ? e[16 * c16 + q] : 0.f;
-                st_x16(X, row, 16 * c16, v);
+                for (int q = 0; q < 64; ++q) e[q] = 0.f;
             }
+            uint32_t pk[16];
+            pack16(e, pk);
+            tmem_st16(tArow, pk);
+            pack16(e + 32, pk);
+            tmem_st16(tArow + 16, pk);
         }
         // the next tile's gathers overlap this tile's layers
         if (g + 1 < g1) nxt = fetch_sample(src, b, tl, row);
         float sigma = 0.f;
 #pragma unroll 1
         for (int l = 0; l < kLayers; ++l) {
-            // X for layer l is complete once all 128 threads of the slot arrive
-            fence_proxy_async();
+            // A for layer l is complete once all 128 threads of the slot arrive
+            tmem_wait_st();
+            tc_fence_before();
             if (named_sync_or(1 + slot, 128, aborted || *abortp)) {
                 aborted = true;
                 break;
@@ -495,8 +535,8 @@ __global__ void __launch_bounds__(kSlots * 128, 1)
 #pragma unroll 1
                     for (int ks = 0; ks < K / 16; ++ks) {
                         const int ch = ks >> 2, kin = ks & 3;
-                        umma(tslot, sdesc(xa + ch * 16384 + kin * 32), sdesc(ba + ch * N * 128 + kin * 32), idesc,
-                             ks > 0 ? 1u : 0u);
+                        umma_ta(tslot, tA + (uint32_t)(ks * 8), sdesc(ba + ch * N * 128 + kin * 32), idesc,
+                                ks > 0 ? 1u : 0u);
                     }
                 }
                 umma_commit(&bar_d[slot]);
@@ -520,15 +560,26 @@ __global__ void __launch_bounds__(kSlots * 128, 1)
             tmem_wait_ld();
             tc_fence_before();
             if (l < H + 1) {
-                if (l == H) {
-                    // head: features stay linear; density from column W
+                // next activations: head features stay linear, every other layer ReLU
+                uint32_t pk[W / 2];
 #pragma unroll
-                    for (int c = 0; c < W / 16; ++c) st_x16_bits<false>(X, row, 16 * c, r[c]);
+                for (int c = 0; c < W / 16; ++c)
+#pragma unroll
+                    for (int q = 0; q < 8; ++q)
+                        pk[8 * c + q] = l == H ? pack_bf16(__uint_as_float(r[c][2 * q]), __uint_as_float(r[c][2 * q + 1]))
+                                               : pack_bf16_relu(__uint_as_float(r[c][2 * q]),
+                                                                __uint_as_float(r[c][2 * q + 1]));
+#pragma unroll
+                for (int c = 0; c < W / 32; ++c) {
+                    uint32_t v16[16];
+#pragma unroll
+                    for (int q = 0; q < 16; ++q) v16[q] = pk[16 * c + q];
+                    tmem_st16(tArow + 16 * c, v16);
+                }
+                if (l == H) {
+                    // density from column W of the head
                     const float sl = __uint_as_float(rs[0]);
                     sigma = sig_scale * (w.act == ROAM_RELU ? fmaxf(sl, 0.f) : softplus_f(sl));
-                } else {
-#pragma unroll
-                    for (int c = 0; c < W / 16; ++c) st_x16_bits<true>(X, row, 16 * c, r[c]);
                 }
                 if (l == 0) {
                     // tail of X from here on: [1 | F(d) | 0 0 0 0] at columns W .. W+31
@@ -547,13 +598,9 @@ __global__ void __launch_bounds__(kSlots * 128, 1)
                         }
                     }
                     e[28] = e[29] = e[30] = e[31] = 0.f;
-                    float v[16];
-#pragma unroll
-                    for (int q = 0; q < 16; ++q) v[q] = e[q];
-                    st_x16(X, row, W, v);
-#pragma unroll
-                    for (int q = 0; q < 16; ++q) v[q] = e[16 + q];
-                    st_x16(X, row, W + 16, v);
+                    uint32_t pt[16];
+                    pack16(e, pt);
+                    tmem_st16(tArow + W / 2, pt);
                 }
             } else {
                 // colour layer: g = relu(z) in FP32, then rgb = sigmoid(Wo g + bo) with
@@ -686,7 +733,7 @@ __global__ void k_pack_tc(const float *__restrict__ w32, int n_fields, int64_t P
 constexpr int kSlotsTc = 4;
 
 template <int W, int H>
-int tc_smem_bytes() { return 1024 + TcShape<W, H>::kImageAlloc + kSlotsTc * TcShape<W, H>::kXBytes; }
+int tc_smem_bytes() { return 1024 + TcShape<W, H>::kImageAlloc; }
 
 template <int W, int H>
 void launch_t(const MlpWeights &w, const SampleSrc &src, const BucketBufs &b, Counters *ctr, float4 *out, int n_sm,
