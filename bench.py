@@ -187,6 +187,59 @@ def time_steps(r, cams, opts, steps, warmup, flush, stream):
     return total, per
 
 
+def train_step_bench(roam, F, torch, wl, args, stream):
+    """One fine-tuning step = forward (BF16 tensor cores) + L2 loss + adjoint
+    (composite + FP32 MLP adjoint) + Adam, on 65,536 rays of 16 1024x512
+    equirect views of the floor (targets rendered once, untimed)."""
+    import numpy as np
+    cams = F.make_cameras(wl.scene, 3, [(F.EQUIRECT, 1024, 512, 0.0)] * 16)
+    teacher = roam.Roam(torch.cuda.current_device())
+    teacher.load_workload(wl)
+    rgb_t, _, _ = teacher.render(cams, roam.render_opts(wl.delta, wl.n_max, precision=roam.ROAM_BF16))
+    n = 65536
+    rays_np = F.ray_batch(3, cams, n)
+    rays = torch.from_numpy(rays_np.astype(np.int32)).cuda()
+    gidx = torch.from_numpy((rays_np[:, 0].astype(np.int64) * 1024 * 512 + rays_np[:, 1]).astype(np.int64)).cuda()
+    noise = torch.from_numpy(F.rng_for(3, F.ROLE_NOISE).normal(0, 0.01, (n, 3)).astype(np.float32)).cuda()
+    target = (rgb_t[gidx] + noise).contiguous()
+    teacher.close()
+    student = F.xavier_weights(2, F.ROLE_STUDENT, wl.part.n_fields, wl.W, wl.H)
+    r = roam.Roam(torch.cuda.current_device())
+    r.load_grid(wl.scene.bits, wl.scene.dims, wl.scene.origin, wl.scene.vox)
+    r.load_fields(wl.part.field_of_rank, wl.affine)
+    r.load_weights(student, wl.W, wl.H, wl.sigma_scale)
+    opts = roam.render_opts(wl.delta, wl.n_max, precision=roam.ROAM_BF16)
+
+    def step(k):
+        loss, g = r.local_grad(cams, rays, target, opts, 3.0 * n, stream=stream)
+        r.adam_step(g, lr=1e-3, step=k, stream=stream)
+        return loss
+
+    for k in range(1, 4):
+        step(k)
+    torch.cuda.synchronize()
+    r.profile(True)
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    steps = max(3, args.steps)
+    losses = []
+    a.record(stream)
+    for k in range(4, 4 + steps):
+        losses.append(step(k))
+    b.record(stream)
+    b.synchronize()
+    prof = r.profile_read()
+    r.profile(False)
+    ms = a.elapsed_time(b) / steps
+    st = r.get_stats()
+    r.close()
+    return {"workload": "floor256_kd512_w64h3, 16 equirect 1024x512 views, 65536 random rays, teacher+N(0,0.01^2) targets",
+            "ms_per_step": ms, "rays_per_s": n / (ms / 1000.0), "samples_per_step": int(st.n_samples),
+            "loss_first_last": [float(losses[0]), float(losses[-1])],
+            "kernels": {k: {"launches": v[0], "ms": round(v[1], 3)} for k, v in prof.items()},
+            "precision": "forward BF16 tcgen05, adjoint FP32 SIMT, FP32 master weights"}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -335,6 +388,12 @@ def main():
     e2e = {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 64 * len(wl.cams),
            "d2h_bytes_per_step": 20 * n_pix, "ms_per_step": 1000 * sum(e2e_times) / args.steps}
 
+    # ---- training step: 65,536 random rays of 16 equirect views, targets
+    # from the teacher weights + N(0, 0.01^2), student weights trained ----
+    train = None
+    if rank == 0:
+        train = train_step_bench(roam, F, torch, wl, args, stream)
+
     cpu = None
     if rank == 0 and world == 1:
         v, cores, desc = cpu_oracle_rate(wl, args.cpu_seconds)
@@ -350,6 +409,7 @@ def main():
                 "frame_ms": frame,
                 "fp32_simt": {"value": f32_value, "unit": UNIT, "ms_per_step": t32 / max(3, args.steps // 2)},
                 "accuracy_vs_oracle": acc, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+                "train_step": train,
                 "gpu_launches": int(6 * st.n_rounds * args.steps), "clocks": clocks}
         print(json.dumps(line), flush=True)
     r.close()

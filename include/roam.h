@@ -266,6 +266,15 @@ roam_status roam_train_forward(roam_ctx *ctx, const roam_camera *cams, int n_vie
  * Asynchronous. */
 roam_status roam_train_backward(roam_ctx *ctx, const float *dl_drgb, float *grad, void *stream);
 
+/* L2 photometric loss of the fine-tuning stage on device arrays rgb and
+ * target (float[n_rays][3]): *loss (device float, may be NULL) receives
+ * sum (rgb - target)^2 / norm and dl_drgb (device float[n_rays][3])
+ * 2 (rgb - target) / norm.  norm = 3 n for the mean over a batch of n rays;
+ * with data parallelism, 3 n over the global batch so that summed per-rank
+ * gradients equal the global one.  Asynchronous. */
+roam_status roam_l2_loss(roam_ctx *ctx, const float *rgb, const float *target, int64_t n_rays, float norm,
+                         float *dl_drgb, float *loss, void *stream);
+
 /* Adam update of the FP32 master weights with grad (device, layout of
  * roam_load_weights); refreshes the BF16 images.  Asynchronous. */
 roam_status roam_adam_step(roam_ctx *ctx, const float *grad, const roam_adam_cfg *cfg, void *stream);

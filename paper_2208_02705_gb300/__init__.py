@@ -29,7 +29,7 @@ ENTRY_POINTS = ("roam_create", "roam_destroy", "roam_last_error", "roam_check", 
                 "roam_load_fields", "roam_load_weights", "roam_get_weights", "roam_render", "roam_get_stats",
                 "roam_march", "roam_bucket", "roam_mlp_eval", "roam_composite", "roam_train_forward",
                 "roam_train_backward", "roam_adam_step", "roam_profile", "roam_profile_read",
-                "roam_bucket_static")
+                "roam_bucket_static", "roam_l2_loss")
 
 
 class RoamError(RuntimeError):
@@ -103,6 +103,7 @@ def load_library(path: str = LIB_PATH):
     L.roam_train_backward.argtypes = [vp, vp, vp, vp]
     L.roam_adam_step.argtypes = [vp, vp, P(roam_adam_cfg), vp]
     L.roam_bucket_static.argtypes = [vp, i64, i32, vp, vp, vp]
+    L.roam_l2_loss.argtypes = [vp, vp, vp, i64, ctypes.c_float, vp, vp, vp]
     L.roam_profile.argtypes = [vp, i32]
     L.roam_profile_read.argtypes = [vp, P(roam_kernel_time), i32, P(ctypes.c_int)]
     for name in ENTRY_POINTS:
@@ -336,6 +337,24 @@ class Roam:
                                                          device=self._dev())
         _check(self.L.roam_train_backward(self.h, _ptr(dl_drgb), _ptr(grad), _stream(stream)))
         return grad
+
+    def l2_loss(self, rgb, target, norm: float, stream=None):
+        """(loss tensor [1], dl/drgb tensor [n, 3]) of sum (rgb - target)^2 / norm."""
+        import torch
+        n = int(rgb.shape[0])
+        dl = torch.empty_like(rgb)
+        loss = torch.zeros(1, dtype=torch.float32, device=rgb.device)
+        _check(self.L.roam_l2_loss(self.h, _ptr(rgb), _ptr(target), n, float(norm), _ptr(dl), _ptr(loss),
+                                   _stream(stream)))
+        return loss, dl
+
+    def local_grad(self, cams, rays, target, opts, norm: float, stream=None):
+        """Forward, L2 loss (normalised by `norm`) and backward on this
+        process's rays: returns (loss [1], gradient [F, P])."""
+        rgb = self.train_forward(cams, rays, opts, stream=stream)
+        loss, dl = self.l2_loss(rgb, target, norm, stream=stream)
+        grad = self.train_backward(dl, stream=stream)
+        return loss, grad
 
     def adam_step(self, grad, lr: float, step: int, beta1: float = 0.9, beta2: float = 0.99, eps: float = 1e-8,
                   stream=None):

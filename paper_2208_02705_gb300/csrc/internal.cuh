@@ -170,6 +170,8 @@ bool mlp_bwd_supported(int W, int H);
 void launch_pack_rows(const float *w32, int n_fields, int W, int H, int64_t P, float *wr, int64_t Pr,
                       cudaStream_t s);
 int64_t rows_padded_size(int W, int H);
+void launch_l2_loss(int64_t n_rays, const float *rgb, const float *target, float norm, float *dl, float *loss,
+                    cudaStream_t s);
 void launch_adam(float *w32, float *m, float *v, const float *g, int64_t n, float lr, float b1, float b2,
                  float eps, float bc1, float bc2, cudaStream_t s);
 

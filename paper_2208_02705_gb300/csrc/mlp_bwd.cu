@@ -418,6 +418,22 @@ __global__ void k_adam(float *__restrict__ w, float *__restrict__ m, float *__re
     }
 }
 
+// L2 photometric loss of the fine-tuning stage: loss += sum (rgb - target)^2
+// / norm over the rays, and dl/drgb = 2 (rgb - target) / norm.
+__global__ void k_l2_loss(int64_t n3, const float *__restrict__ rgb, const float *__restrict__ target, float inv_norm,
+                          float *__restrict__ dl, float *__restrict__ loss)
+{
+    float acc = 0.f;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n3; i += (int64_t)gridDim.x * blockDim.x) {
+        const float e = rgb[i] - target[i];
+        dl[i] = 2.f * e * inv_norm;
+        acc = fmaf(e * inv_norm, e, acc);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0 && loss) atomicAdd(loss, acc);
+}
+
 template <int W, int H>
 void launch_bwd_t(const MlpWeights &w, const SampleSrc &src, const BucketBufs &b, Counters *ctr, const float4 *gsr,
                   float *grad, int grid, cudaStream_t s)
@@ -454,6 +470,16 @@ void launch_mlp_bwd_simt(const MlpWeights &w, const SampleSrc &src, const Bucket
     ROAM_CASE(32, 1) ROAM_CASE(32, 2) ROAM_CASE(32, 3) ROAM_CASE(32, 4)
     ROAM_CASE(64, 1) ROAM_CASE(64, 2) ROAM_CASE(64, 3) ROAM_CASE(64, 4)
 #undef ROAM_CASE
+}
+
+void launch_l2_loss(int64_t n_rays, const float *rgb, const float *target, float norm, float *dl, float *loss,
+                    cudaStream_t s)
+{
+    if (loss) cudaMemsetAsync(loss, 0, sizeof(float), s);
+    int64_t blocks = (3 * n_rays + 255) / 256;
+    if (blocks > 4096) blocks = 4096;
+    if (blocks < 1) blocks = 1;
+    k_l2_loss<<<(unsigned)blocks, 256, 0, s>>>(3 * n_rays, rgb, target, 1.0f / norm, dl, loss);
 }
 
 void launch_adam(float *w32, float *m, float *v, const float *g, int64_t n, float lr, float b1, float b2, float eps,

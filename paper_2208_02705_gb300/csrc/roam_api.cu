@@ -939,6 +939,20 @@ roam_status roam_train_backward(roam_ctx *c, const float *dl_drgb, float *grad, 
     return launched("mlp_bwd");
 }
 
+roam_status roam_l2_loss(roam_ctx *c, const float *rgb, const float *target, int64_t n_rays, float norm,
+                         float *dl_drgb, float *loss, void *stream)
+{
+    ROAM_TRY(set_dev(c));
+    if (n_rays < 0) return fail(ROAM_ERR_ARG, "bad ray count");
+    if (!(norm > 0.f) || !finite(norm)) return fail(ROAM_ERR_ARG, "norm must be positive");
+    if (n_rays == 0) return ROAM_OK;
+    if (!rgb || !target || !dl_drgb) return fail(ROAM_ERR_ARG, "null pointer");
+    cudaStream_t s = (cudaStream_t)stream;
+    launch_l2_loss(n_rays, rgb, target, norm, dl_drgb, loss, s);
+    c->last = s;
+    return launched("l2_loss");
+}
+
 roam_status roam_adam_step(roam_ctx *c, const float *grad, const roam_adam_cfg *cfg, void *stream)
 {
     ROAM_TRY(set_dev(c));
