@@ -96,6 +96,9 @@ typedef struct {
     float bg[3];
     int32_t precision;    /* ROAM_F32 (SIMT FP32) or ROAM_BF16 (tcgen05 BF16, FP32 accumulate) */
     int32_t round_size;   /* kept samples marched per ray per round, 0 = library default */
+    int32_t use_graph;    /* 1: roam_render captures its launch sequence into a CUDA graph
+                             (once per configuration: view sizes, options, output pointers)
+                             and replays it on later calls; 0: plain launches */
 } roam_render_opts;
 
 /* Counters of the last render / training forward (read with a sync). */

@@ -54,7 +54,8 @@ class roam_camera(ctypes.Structure):
 
 class roam_render_opts(ctypes.Structure):
     _fields_ = [("delta", ctypes.c_float), ("n_max", ctypes.c_int32), ("t_stop", ctypes.c_float),
-                ("bg", ctypes.c_float * 3), ("precision", ctypes.c_int32), ("round_size", ctypes.c_int32)]
+                ("bg", ctypes.c_float * 3), ("precision", ctypes.c_int32), ("round_size", ctypes.c_int32),
+                ("use_graph", ctypes.c_int32)]
 
 
 class roam_stats(ctypes.Structure):
@@ -156,7 +157,7 @@ def camera_array(cams: Sequence) -> ctypes.Array:
 
 
 def render_opts(delta: float, n_max: int, t_stop: float = 1e-4, bg=(0.0, 0.0, 0.0),
-                precision: int = ROAM_F32, round_size: int = 0) -> roam_render_opts:
+                precision: int = ROAM_F32, round_size: int = 0, use_graph: bool = False) -> roam_render_opts:
     o = roam_render_opts()
     o.delta = float(delta)
     o.n_max = int(n_max)
@@ -165,6 +166,7 @@ def render_opts(delta: float, n_max: int, t_stop: float = 1e-4, bg=(0.0, 0.0, 0.
         o.bg[i] = float(bg[i])
     o.precision = int(precision)
     o.round_size = int(round_size)
+    o.use_graph = int(bool(use_graph))
     return o
 
 

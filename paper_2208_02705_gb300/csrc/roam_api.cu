@@ -5,6 +5,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <atomic>
 #include <vector>
 
 #include "internal.cuh"
@@ -42,11 +43,16 @@ struct DBuf {
     size_t n = 0;
 };
 
+// bumped by every device (re)allocation: a captured render graph holds raw
+// pointers and is re-captured when this moves
+std::atomic<uint64_t> g_alloc_gen{0};
+
 template <class T>
 roam_status ensure(DBuf<T> &b, size_t n)
 {
     if (n == 0) n = 1;
     if (b.p && b.n >= n) return ROAM_OK;
+    ++g_alloc_gen;
     if (b.p) cudaFree(b.p);
     b.p = nullptr;
     b.n = 0;
@@ -136,6 +142,12 @@ struct roam_ctx {
     std::vector<cudaEvent_t> ev_pool;
     std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> prof_pending;
     std::vector<std::pair<int64_t, double>> prof_acc;
+    // CUDA-graph replay of roam_render
+    uint64_t gen = 0;                   // bumped whenever the grid, fields or weights are reloaded
+    cudaGraphExec_t gexec = nullptr;
+    std::vector<uint64_t> gkey;
+    cudaStream_t gstream = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     // training: state kept from roam_train_forward for roam_train_backward
     int64_t train_rays = 0;
     int train_R = 0;
@@ -249,6 +261,7 @@ roam_status check_opts(const roam_ctx *c, const roam_render_opts *o)
     if (o->precision == ROAM_BF16 && !c->tc_ok)
         return fail(ROAM_ERR_UNSUPPORTED, "BF16 tensor-core path not available for W=%d H=%d", c->md.width, c->md.n_hidden);
     if (o->round_size < 0) return fail(ROAM_ERR_ARG, "round_size must be >= 0");
+    if (o->use_graph != 0 && o->use_graph != 1) return fail(ROAM_ERR_ARG, "use_graph must be 0 or 1");
     return ROAM_OK;
 }
 
@@ -456,6 +469,60 @@ int round_size(const roam_render_opts *o, int64_t n_rays)
     return R;
 }
 
+// The launch sequence of one render (counter resets + every round) as a CUDA
+// graph on the context's own stream, captured for a configuration and
+// replayed while it holds; forked from and joined back to the caller's stream.
+roam_status render_graph(roam_ctx *c, int64_t n_pix, const roam_render_opts *o, float *rgb, float *depth,
+                         float *opacity, int R, cudaStream_t s)
+{
+    if (!c->gstream) {
+        ROAM_CUDA(cudaStreamCreateWithFlags(&c->gstream, cudaStreamNonBlocking));
+        ROAM_CUDA(cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming));
+        ROAM_CUDA(cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming));
+    }
+    uint32_t f[5];
+    memcpy(&f[0], &o->delta, 4);
+    memcpy(&f[1], &o->t_stop, 4);
+    memcpy(&f[2], &o->bg[0], 4);
+    memcpy(&f[3], &o->bg[1], 4);
+    memcpy(&f[4], &o->bg[2], 4);
+    const std::vector<uint64_t> key = {c->gen, g_alloc_gen.load(), (uint64_t)n_pix, (uint64_t)c->n_views, (uint64_t)R,
+                                       (uint64_t)o->n_max, (uint64_t)o->precision, f[0], f[1], f[2], f[3], f[4],
+                                       (uint64_t)(uintptr_t)rgb, (uint64_t)(uintptr_t)depth,
+                                       (uint64_t)(uintptr_t)opacity};
+    if (!c->gexec || key != c->gkey) {
+        if (c->gexec) {
+            cudaGraphExecDestroy(c->gexec);
+            c->gexec = nullptr;
+        }
+        cudaStream_t g = c->gstream;
+        ROAM_CUDA(cudaStreamBeginCapture(g, cudaStreamCaptureModeThreadLocal));
+        cudaMemsetAsync(c->ctr, 0, sizeof(Counters), g);
+        cudaMemsetAsync(c->hist.p, 0, (size_t)c->n_fields * sizeof(uint32_t), g);
+        const roam_status st = run_rounds(c, nullptr, n_pix, o, rgb, depth, opacity, R, g);
+        cudaGraph_t graph = nullptr;
+        const cudaError_t e = cudaStreamEndCapture(g, &graph);
+        if (st != ROAM_OK) {
+            if (graph) cudaGraphDestroy(graph);
+            return st;
+        }
+        if (e != cudaSuccess) return fail(ROAM_ERR_CUDA, "graph capture failed: %s", cudaGetErrorString(e));
+        const cudaError_t ei = cudaGraphInstantiate(&c->gexec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (ei != cudaSuccess) {
+            c->gexec = nullptr;
+            return fail(ROAM_ERR_CUDA, "graph instantiation failed: %s", cudaGetErrorString(ei));
+        }
+        c->gkey = key;
+    }
+    ROAM_CUDA(cudaEventRecord(c->ev_fork, s));
+    ROAM_CUDA(cudaStreamWaitEvent(c->gstream, c->ev_fork, 0));
+    ROAM_CUDA(cudaGraphLaunch(c->gexec, c->gstream));
+    ROAM_CUDA(cudaEventRecord(c->ev_join, c->gstream));
+    ROAM_CUDA(cudaStreamWaitEvent(s, c->ev_join, 0));
+    return ROAM_OK;
+}
+
 }  // namespace
 
 namespace roam {
@@ -514,6 +581,10 @@ roam_status roam_destroy(roam_ctx *c)
     if (c->ctr) cudaFree(c->ctr);
     if (c->d_flag) cudaFree(c->d_flag);
     if (c->cam_ev) cudaEventDestroy(c->cam_ev);
+    if (c->gexec) cudaGraphExecDestroy(c->gexec);
+    if (c->gstream) cudaStreamDestroy(c->gstream);
+    if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+    if (c->ev_join) cudaEventDestroy(c->ev_join);
     for (auto e : c->ev_pool) cudaEventDestroy(e);
     for (auto &p : c->prof_pending) {
         cudaEventDestroy(p.second.first);
@@ -543,6 +614,7 @@ roam_status roam_load_grid(roam_ctx *c, const roam_grid_desc *desc, const uint32
     for (int a = 0; a < 3; ++a)
         if (!finite(desc->origin[a])) return fail(ROAM_ERR_ARG, "grid origin must be finite");
     c->has_grid = c->has_fields = c->has_weights = false;
+    ++c->gen;
     const int64_t n_words = (int64_t)desc->dims[0] / 32 * desc->dims[1] * desc->dims[2];
     ROAM_TRY(ensure(c->bits, (size_t)n_words));
     ROAM_TRY(ensure(c->prefix, (size_t)n_words));
@@ -597,6 +669,7 @@ roam_status roam_load_fields(roam_ctx *c, int n_fields, const uint16_t *labels, 
     for (float v : aff_h)
         if (!finite(v)) return fail(ROAM_ERR_ARG, "non-finite field affine");
     c->has_fields = c->has_weights = false;
+    ++c->gen;
     ROAM_TRY(ensure(c->labels, (size_t)std::max<int64_t>(n_occupied, 1)));
     ROAM_TRY(ensure(c->affine, 6 * (size_t)n_fields));
     if (n_occupied > 0) ROAM_CUDA(cudaMemcpy(c->labels.p, labels, n_occupied * sizeof(uint16_t), kind));
@@ -629,6 +702,7 @@ roam_status roam_load_weights(roam_ctx *c, const roam_mlp_desc *desc, const floa
     if (desc->density_act != ROAM_SOFTPLUS && desc->density_act != ROAM_RELU)
         return fail(ROAM_ERR_ARG, "unknown density activation");
     c->has_weights = false;
+    ++c->gen;
     const int W = desc->width, H = desc->n_hidden;
     const int64_t P = param_count(W, H);
     const int64_t total = P * c->n_fields;
@@ -695,9 +769,13 @@ roam_status roam_render(roam_ctx *c, const roam_camera *cams, int n_views, const
         if (depth) { ROAM_TRY(ensure(c->o_depth, (size_t)n_pix)); d_depth = c->o_depth.p; }
         if (opacity) { ROAM_TRY(ensure(c->o_op, (size_t)n_pix)); d_op = c->o_op.p; }
     }
-    ROAM_CUDA(cudaMemsetAsync(c->ctr, 0, sizeof(Counters), s));
-    ROAM_CUDA(cudaMemsetAsync(c->hist.p, 0, (size_t)c->n_fields * sizeof(uint32_t), s));
-    ROAM_TRY(run_rounds(c, nullptr, n_pix, opts, d_rgb, d_depth, d_op, R, s));
+    if (opts->use_graph && !c->prof) {
+        ROAM_TRY(render_graph(c, n_pix, opts, d_rgb, d_depth, d_op, R, s));
+    } else {
+        ROAM_CUDA(cudaMemsetAsync(c->ctr, 0, sizeof(Counters), s));
+        ROAM_CUDA(cudaMemsetAsync(c->hist.p, 0, (size_t)c->n_fields * sizeof(uint32_t), s));
+        ROAM_TRY(run_rounds(c, nullptr, n_pix, opts, d_rgb, d_depth, d_op, R, s));
+    }
     c->last = s;
     c->last_rays = n_pix;
     c->last_rounds = (opts->n_max + R - 1) / R;

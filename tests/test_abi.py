@@ -44,7 +44,7 @@ def test_binding_lists_every_declared_symbol():
 def test_binding_structs_match_header_sizes():
     import paper_2208_02705_gb300 as roam
     assert ctypes.sizeof(roam.roam_camera) == 64
-    assert ctypes.sizeof(roam.roam_render_opts) == 32
+    assert ctypes.sizeof(roam.roam_render_opts) == 36
     assert ctypes.sizeof(roam.roam_grid_desc) == 28
     assert ctypes.sizeof(roam.roam_mlp_desc) == 16
 

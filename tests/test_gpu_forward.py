@@ -241,6 +241,30 @@ def test_render_round_schedule_is_invisible(roam, room, room32):
             assert torch.equal(a, b)
 
 
+@pytest.mark.parametrize("precision", ["f32", "bf16"])
+def test_render_graph_replay_is_bit_identical(roam, room, room32, precision):
+    """CUDA-graph replay (captured once per configuration) gives the same bits
+    as plain launches; a new camera set of another size, new output buffers
+    and host outputs each re-capture."""
+    prec = roam.ROAM_F32 if precision == "f32" else roam.ROAM_BF16
+    plain = roam.render_opts(room32.delta, room32.n_max, precision=prec)
+    graph = roam.render_opts(room32.delta, room32.n_max, precision=prec, use_graph=True)
+    persp = [F.Camera(F.PERSPECTIVE, 40, 24, math.pi / 2, F.yaw_pitch(0.3, 0.1), room32.cams[0].o)]
+    for cams in (room32.cams, persp, room32.cams):
+        ref = [t.clone() for t in room.render(cams, plain)]
+        outs = [room.render(cams, graph) for _ in range(3)]        # capture, then two replays
+        torch.cuda.synchronize()
+        for o in outs:
+            for a, b in zip(ref, o):
+                assert torch.equal(a, b)
+        n = ref[0].shape[0]
+        rgb_h = np.zeros((n, 3), np.float32)
+        room.render_host(cams, graph, rgb_h)
+        assert np.array_equal(rgb_h, ref[0].cpu().numpy())
+    st = room.get_stats()
+    assert st.n_rays == 128 * 64
+
+
 def test_render_host_outputs_match_device(roam, room, room32):
     opts = roam.render_opts(room32.delta, room32.n_max)
     rgb_d, depth_d, op_d = room.render(room32.cams, opts)
