@@ -183,7 +183,7 @@ bool tc_supported(int W, int H);
 int64_t tc_image_bytes(int W, int H);
 int tc_bias_count(int W, int H);
 int tc_tile_samples();
-int tc_tile_group();
+int tc_tile_group(int W);
 void launch_pack_tc(const float *w32, int n_fields, int W, int H, int64_t P, void *wimg,
                     int64_t img_bytes, float *bias, int nb, cudaStream_t s);
 void launch_mlp_tc(const MlpWeights &w, const SampleSrc &src, const BucketBufs &b, Counters *ctr,

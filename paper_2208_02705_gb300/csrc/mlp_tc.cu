@@ -18,6 +18,11 @@
 //   after L1        [h (W) | 1 | F(d) (27) | 0 0 0 0]             (the tail stays)
 //   hidden / head   [h (W) | 1 | ...]     B zero past the bias    K = W + 16
 //   colour          [feat (W) | 1 | F(d) (27) | 0 0 0 0]          K = W + 32
+// At W = 128 the folded hidden/head biases would cost a third 64-column
+// K-chunk per layer and the image would not fit in shared memory, so there
+// the hidden and head layers run at K = W and their biases are added in
+// FP32 by the epilogue from a table at the end of the image; the image then
+// fits (about 200 KB at H = 4) and two slots fill the 512 TMEM columns.
 #include "internal.cuh"
 
 namespace roam {
@@ -31,11 +36,14 @@ __host__ __device__ constexpr int cdiv(int a, int b) { return (a + b - 1) / b; }
 // ---- shapes of the weight image ----
 template <int W, int H>
 struct TcShape {
+    static constexpr bool kFold = W <= 64;     // hidden/head biases ride in the MMA
     static constexpr int N_HEAD = W + 16;
     static constexpr int K_COL = W + 32;
+    static constexpr int K_HID = kFold ? W + 16 : W;
     static constexpr int N_OUT = 16;
+    static constexpr int kSlots = W <= 64 ? 4 : 2;
     static constexpr int kLayers = H + 2;      // L1, hidden, head, colour (the 3-output layer runs on CUDA cores)
-    __host__ __device__ static constexpr int K(int l) { return l == 0 ? 64 : (l == H + 1 ? K_COL : W + 16); }
+    __host__ __device__ static constexpr int K(int l) { return l == 0 ? 64 : (l == H + 1 ? K_COL : K_HID); }
     __host__ __device__ static constexpr int N(int l) { return l == H ? N_HEAD : W; }
     __host__ __device__ static constexpr int chunks(int l) { return cdiv(K(l), 64); }
     __host__ __device__ static constexpr int bytes(int l) { return chunks(l) * N(l) * 128; }
@@ -48,7 +56,11 @@ struct TcShape {
     static constexpr int kMatBytes = offset(H + 2);
     // after the MMA operands: FP32 output layer, [W][4] (3 outputs + pad) then bias[4]
     static constexpr int kOutBytes = (4 * W + 4) * 4;
-    static constexpr int kImageBytes = kMatBytes + kOutBytes;
+    // unfolded widths: FP32 biases of the hidden layers ((H-1) x W), then the
+    // head's W features and its density logit, padded to 16 bytes
+    static constexpr int kNTab = kFold ? 0 : (((H - 1) * W + W + 1 + 3) & ~3);
+    static constexpr int kTabBytes = kNTab * 4;
+    static constexpr int kImageBytes = kMatBytes + kOutBytes + kTabBytes;
     static constexpr int kImageAlloc = (kImageBytes + 1023) & ~1023;
     static constexpr int kXChunks = cdiv(K_COL, 64) > 1 ? cdiv(K_COL, 64) : 1;
     static constexpr int kXBytes = kXChunks * 128 * 128;
@@ -444,6 +456,7 @@ __global__ void __launch_bounds__(kSlots * 128, 1)
     uint32_t d_ph = 0, n_changes = 0, n_commits = 0, n_waits = 0;
     uint32_t cur_field = 0xffffffffu;
     bool w_ready = false, w_waited_last = true;
+    bool img_seen = false;     // this thread has waited for the current image (before generic loads of it)
     bool aborted = false;
     const float sig_scale = w.sigma_scale;
     Tile tl{0u, 0u, 0u, 0u};
@@ -471,6 +484,7 @@ __global__ void __launch_bounds__(kSlots * 128, 1)
             ++n_changes;
             cur_field = f;
             w_ready = false;
+            img_seen = false;
         }
         const Tile cur = tl;
         const SampleIn sm = nxt;
@@ -559,26 +573,43 @@ __global__ void __launch_bounds__(kSlots * 128, 1)
             if (l == H) tmem_ld16_nowait(trow + W, rs);
             tmem_wait_ld();
             tc_fence_before();
+            const float *btab = reinterpret_cast<const float *>(IMG + S::kMatBytes + S::kOutBytes) + (l >= 1 ? l - 1 : 0) * W;
+            if constexpr (!S::kFold) {
+                if (l >= 1 && !img_seen) {
+                    mbar_wait(&bar_w, (n_changes - 1) & 1u, abortp, status);
+                    img_seen = true;
+                }
+            }
             if (l < H + 1) {
                 // next activations: head features stay linear, every other layer ReLU
-                uint32_t pk[W / 2];
-#pragma unroll
-                for (int c = 0; c < W / 16; ++c)
-#pragma unroll
-                    for (int q = 0; q < 8; ++q)
-                        pk[8 * c + q] = l == H ? pack_bf16(__uint_as_float(r[c][2 * q]), __uint_as_float(r[c][2 * q + 1]))
-                                               : pack_bf16_relu(__uint_as_float(r[c][2 * q]),
-                                                                __uint_as_float(r[c][2 * q + 1]));
 #pragma unroll
                 for (int c = 0; c < W / 32; ++c) {
+                    float bv[32];
+#pragma unroll
+                    for (int q = 0; q < 32; ++q) bv[q] = 0.f;
+                    if constexpr (!S::kFold) {
+                        if (l >= 1) {
+#pragma unroll
+                            for (int q = 0; q < 8; ++q) {
+                                const float4 t = reinterpret_cast<const float4 *>(btab + 32 * c)[q];
+                                bv[4 * q] = t.x; bv[4 * q + 1] = t.y; bv[4 * q + 2] = t.z; bv[4 * q + 3] = t.w;
+                            }
+                        }
+                    }
                     uint32_t v16[16];
 #pragma unroll
-                    for (int q = 0; q < 16; ++q) v16[q] = pk[16 * c + q];
+                    for (int q = 0; q < 16; ++q) {
+                        const int e0 = 32 * c + 2 * q;
+                        const float a0 = __uint_as_float(r[e0 >> 4][e0 & 15]) + bv[2 * q];
+                        const float a1 = __uint_as_float(r[(e0 + 1) >> 4][(e0 + 1) & 15]) + bv[2 * q + 1];
+                        v16[q] = l == H ? pack_bf16(a0, a1) : pack_bf16_relu(a0, a1);
+                    }
                     tmem_st16(tArow + 16 * c, v16);
                 }
                 if (l == H) {
                     // density from column W of the head
-                    const float sl = __uint_as_float(rs[0]);
+                    float sl = __uint_as_float(rs[0]);
+                    if constexpr (!S::kFold) sl += btab[W];
                     sigma = sig_scale * (w.act == ROAM_RELU ? fmaxf(sl, 0.f) : softplus_f(sl));
                 }
                 if (l == 0) {
@@ -606,7 +637,10 @@ __global__ void __launch_bounds__(kSlots * 128, 1)
                 // colour layer: g = relu(z) in FP32, then rgb = sigmoid(Wo g + bo) with
                 // the FP32 output table at the end of the shared image (this thread
                 // waits for the image itself before reading it with generic loads)
-                mbar_wait(&bar_w, (n_changes - 1) & 1u, abortp, status);
+                if (!img_seen) {
+                    mbar_wait(&bar_w, (n_changes - 1) & 1u, abortp, status);
+                    img_seen = true;
+                }
                 const float4 *wo = reinterpret_cast<const float4 *>(IMG + S::kMatBytes);
                 float4 acc = wo[W];
 #pragma unroll
@@ -709,6 +743,20 @@ __global__ void k_pack_tc(const float *__restrict__ w32, int n_fields, int64_t P
         }
         reinterpret_cast<float *>(img + f * img_bytes + S::kMatBytes)[q] = v;
     }
+    // unfolded widths: the FP32 bias table of the hidden and head layers
+    if (S::kNTab > 0) {
+        for (int64_t gi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; gi < (int64_t)n_fields * S::kNTab;
+             gi += (int64_t)gridDim.x * blockDim.x) {
+            const int64_t f = gi / S::kNTab;
+            const int q = (int)(gi % S::kNTab);
+            const float *wf = w32 + f * P;
+            float v = 0.f;
+            if (q < (H - 1) * W) v = wf[o_hid + (int64_t)(q / W) * (W * W + W) + (int64_t)W * W + q % W];
+            else if (q < H * W) v = wf[o_head + (int64_t)(1 + W) * W + 1 + (q - (H - 1) * W)];
+            else if (q == H * W) v = wf[o_head + (int64_t)(1 + W) * W];
+            reinterpret_cast<float *>(img + f * img_bytes + S::kMatBytes + S::kOutBytes)[q] = v;
+        }
+    }
     // bias table: hidden (H-1)*W, head features W, head density 1, output 3
     const int64_t nbt = (int64_t)n_fields * nb;
     for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < nbt; g += (int64_t)gridDim.x * blockDim.x) {
@@ -730,8 +778,6 @@ __global__ void k_pack_tc(const float *__restrict__ w32, int n_fields, int64_t P
     }
 }
 
-constexpr int kSlotsTc = 4;
-
 template <int W, int H>
 int tc_smem_bytes() { return 1024 + TcShape<W, H>::kImageAlloc; }
 
@@ -739,31 +785,37 @@ template <int W, int H>
 void launch_t(const MlpWeights &w, const SampleSrc &src, const BucketBufs &b, Counters *ctr, float4 *out, int n_sm,
               cudaStream_t s)
 {
+    constexpr int kSlots = TcShape<W, H>::kSlots;
     const int smem = tc_smem_bytes<W, H>();
     static bool attr = false;
     if (!attr) {
-        cudaFuncSetAttribute(k_mlp_tc<W, H, kSlotsTc>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        cudaFuncSetAttribute(k_mlp_tc<W, H, kSlots>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         attr = true;
     }
-    k_mlp_tc<W, H, kSlotsTc><<<n_sm, kSlotsTc * 128, smem, s>>>(w, src, b, ctr, out);
+    k_mlp_tc<W, H, kSlots><<<n_sm, kSlots * 128, smem, s>>>(w, src, b, ctr, out);
 }
+
+#define ROAM_TC_CASES                                                                                   \
+    ROAM_CASE(32, 1) ROAM_CASE(32, 2) ROAM_CASE(32, 3) ROAM_CASE(32, 4) ROAM_CASE(64, 1) ROAM_CASE(64, 2) \
+    ROAM_CASE(64, 3) ROAM_CASE(64, 4) ROAM_CASE(128, 1) ROAM_CASE(128, 2) ROAM_CASE(128, 3) ROAM_CASE(128, 4)
 
 }  // namespace
 
 bool tc_supported(int W, int H)
 {
     if (H < 1 || H > 4) return false;
-    if (W == 32) return tc_smem_bytes<32, 4>() <= 227 * 1024;
-    if (W == 64) return tc_smem_bytes<64, 4>() <= 227 * 1024;
-    return false;   // W = 128: the full image does not fit next to the activations
+#define ROAM_CASE(WW, HH) \
+    if (W == WW && H == HH) return tc_smem_bytes<WW, HH>() <= 227 * 1024;
+    ROAM_TC_CASES
+#undef ROAM_CASE
+    return false;
 }
 
 int64_t tc_image_bytes(int W, int H)
 {
 #define ROAM_CASE(WW, HH) \
     if (W == WW && H == HH) return TcShape<WW, HH>::kImageBytes;
-    ROAM_CASE(32, 1) ROAM_CASE(32, 2) ROAM_CASE(32, 3) ROAM_CASE(32, 4)
-    ROAM_CASE(64, 1) ROAM_CASE(64, 2) ROAM_CASE(64, 3) ROAM_CASE(64, 4)
+    ROAM_TC_CASES
 #undef ROAM_CASE
     return 0;
 }
@@ -772,15 +824,14 @@ int tc_bias_count(int W, int H) { return ((H - 1) * W + W + 1 + 3 + 3) & ~3; }
 
 int tc_tile_samples() { return 128; }
 
-int tc_tile_group() { return kSlotsTc; }
+int tc_tile_group(int W) { return W <= 64 ? TcShape<64, 1>::kSlots : TcShape<128, 1>::kSlots; }
 
 void launch_pack_tc(const float *w32, int n_fields, int W, int H, int64_t P, void *wimg, int64_t img_bytes,
                     float *bias, int nb, cudaStream_t s)
 {
 #define ROAM_CASE(WW, HH) \
     if (W == WW && H == HH) { k_pack_tc<WW, HH><<<2048, 256, 0, s>>>(w32, n_fields, P, (uint8_t *)wimg, img_bytes, bias, nb); return; }
-    ROAM_CASE(32, 1) ROAM_CASE(32, 2) ROAM_CASE(32, 3) ROAM_CASE(32, 4)
-    ROAM_CASE(64, 1) ROAM_CASE(64, 2) ROAM_CASE(64, 3) ROAM_CASE(64, 4)
+    ROAM_TC_CASES
 #undef ROAM_CASE
 }
 
@@ -789,8 +840,7 @@ void launch_mlp_tc(const MlpWeights &w, const SampleSrc &src, const BucketBufs &
 {
 #define ROAM_CASE(WW, HH) \
     if (w.W == WW && w.H == HH) { launch_t<WW, HH>(w, src, b, ctr, out, n_sm, s); return; }
-    ROAM_CASE(32, 1) ROAM_CASE(32, 2) ROAM_CASE(32, 3) ROAM_CASE(32, 4)
-    ROAM_CASE(64, 1) ROAM_CASE(64, 2) ROAM_CASE(64, 3) ROAM_CASE(64, 4)
+    ROAM_TC_CASES
 #undef ROAM_CASE
 }
 

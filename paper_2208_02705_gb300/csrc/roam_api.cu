@@ -384,7 +384,7 @@ BucketBufs bucket_of(roam_ctx *c)
 }
 
 int tile_of(int precision) { return precision == ROAM_BF16 ? tc_tile_samples() : 128; }
-int group_of(int precision) { return precision == ROAM_BF16 ? tc_tile_group() : 1; }
+int group_of(const roam_ctx *c, int precision) { return precision == ROAM_BF16 ? tc_tile_group(c->md.width) : 1; }
 
 roam_status run_mlp(roam_ctx *c, int precision, const SampleSrc &src, const BucketBufs &b, float4 *out,
                     cudaStream_t s)
@@ -433,7 +433,7 @@ roam_status run_rounds(roam_ctx *c, const uint32_t *rays, int64_t n_rays, const 
         ROAM_TRY(launched("march"));
         {
             ProfScope ps(c, P_BUCKET, s);
-            launch_bucket_ready(mp.cnt, mp.recs, mp.live_count, mp.n_rays, R, group_of(o->precision), c->n_fields,
+            launch_bucket_ready(mp.cnt, mp.recs, mp.live_count, mp.n_rays, R, group_of(c, o->precision), c->n_fields,
                                 tile_of(o->precision), b, c->ctr, grid, s);
         }
         ROAM_TRY(launched("bucket"));
@@ -914,7 +914,7 @@ roam_status roam_mlp_eval(roam_ctx *c, const float *p, const float *d, const uin
     ROAM_TRY(ensure(c->tiles, tile_capacity((size_t)n, c->n_fields)));
     const BucketBufs b = bucket_of(c);
     ROAM_CUDA(cudaMemsetAsync(c->ctr, 0, sizeof(Counters), s));
-    launch_bucket(nullptr, nullptr, nullptr, (uint32_t)n, 1, group_of(precision), field, c->n_fields,
+    launch_bucket(nullptr, nullptr, nullptr, (uint32_t)n, 1, group_of(c, precision), field, c->n_fields,
                   tile_of(precision), b, c->ctr, grid_blocks(c, 2), s);
     ROAM_TRY(launched("bucket"));
     SampleSrc src{};
