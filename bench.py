@@ -240,6 +240,66 @@ def train_step_bench(roam, F, torch, wl, args, stream):
             "precision": "forward BF16 tcgen05, adjoint FP32 SIMT, FP32 master weights"}
 
 
+def large_scene_bench(roam, F, torch, args, stream, flush, peaks):
+    """The 512^3 twenty-room floor: 4096 kd fields of W=128/H=4 MLPs, one
+    2048x1024 equirectangular view, <= 192 samples per ray; BF16 and FP8
+    E4M3 tensor-core paths and the FP32 SIMT form, each with its frame time,
+    MLP-kernel roofline and accuracy on sampled pixels against the FP64
+    oracle (FP8 also against the oracle's FP8 reading)."""
+    import numpy as np
+    import oracle as O
+    wl = F.floor512()
+    r = roam.Roam(torch.cuda.current_device())
+    r.load_workload(wl)
+    flops_per = 2.0 * macs_per_sample(wl.W, wl.H)
+    bf16_peak = peaks.get("bf16_tflops", 1900.0)
+    out = {"workload": f"floor512_kd4096_w128h4_equirect2048x1024 ({100.0 * wl.scene.n_occupied / 512 ** 3:.1f}% "
+                       f"occupied, n_max {wl.n_max})", "paths": {}}
+    g = O.Grid(wl.scene, wl.part)
+    rays = oracle_sample_rays(wl, 2000, 17)
+    cams = F.camera_array(wl.cams)
+    ref = O.render(g, wl.weights, wl.affine, wl.W, wl.H, wl.sigma_scale, cams, rays, wl.delta, wl.n_max)
+    ref8 = O.render(g, wl.weights, wl.affine, wl.W, wl.H, wl.sigma_scale, cams, rays, wl.delta, wl.n_max, quant=1)
+    gi = rays[:, 1].astype(np.int64)
+    steps = max(3, args.steps // 2)
+    for prec, tag, key, peak in ((roam.ROAM_BF16, "bf16", "mlp_bf16_tcgen05", bf16_peak),
+                                 (roam.ROAM_FP8, "fp8_e4m3", "mlp_fp8_tcgen05", 2.0 * bf16_peak),
+                                 (roam.ROAM_F32, "f32", "mlp_f32_simt", None)):
+        opts = roam.render_opts(wl.delta, wl.n_max, precision=prec)
+        for _ in range(3):
+            r.render(wl.cams, opts, stream=stream)
+        torch.cuda.synchronize()
+        r.profile(True)
+        tot, per = time_steps(r, wl.cams, opts, steps, 0, flush, stream)
+        prof = r.profile_read()
+        r.profile(False)
+        st = r.get_stats()
+        rgb, _, _ = r.render(wl.cams, opts, stream=stream)
+        torch.cuda.synchronize()
+        got = rgb.cpu().numpy()[gi].astype(np.float64)
+        acc = {}
+        for name, rr in (("vs_fp64_oracle", ref), ("vs_oracle_fp8_reading", ref8)):
+            if name == "vs_oracle_fp8_reading" and prec != roam.ROAM_FP8:
+                continue
+            e = got - rr["rgb"]
+            mse = float((e ** 2).mean())
+            acc[name] = {"psnr_db": 10 * math.log10(1.0 / mse) if mse > 0 else float("inf"),
+                         "max_abs": float(np.abs(e).max())}
+        launches, mlp_ms = prof.get(key, (0, float("nan")))
+        tflops = flops_per * st.n_samples * steps / (mlp_ms / 1000.0) / 1e12
+        path = {"frame_ms": statistics.median(per), "samples_per_s": st.n_used * steps / (tot / 1000.0),
+                "mlp_ms_per_frame": mlp_ms / steps, "mlp_tflops": tflops,
+                "kernels": {k: round(v[1] / steps, 4) for k, v in prof.items() if v[0]}, "accuracy": acc,
+                "samples_per_frame": {"composited": int(st.n_used), "evaluated": int(st.n_samples)}}
+        if peak:
+            path["mlp_frac_of_peak"] = tflops / peak
+            path["peak"] = ("measured bf16 burst" if prec == roam.ROAM_BF16 else
+                            "2 x measured bf16 burst (nominal fp8:bf16 ratio)") if peaks else "fallback"
+        out["paths"][tag] = path
+    r.close()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -394,6 +454,10 @@ def main():
     if rank == 0:
         train = train_step_bench(roam, F, torch, wl, args, stream)
 
+    large = None
+    if rank == 0:
+        large = large_scene_bench(roam, F, torch, args, stream, flush, peaks)
+
     cpu = None
     if rank == 0 and world == 1:
         v, cores, desc = cpu_oracle_rate(wl, args.cpu_seconds)
@@ -409,7 +473,7 @@ def main():
                 "frame_ms": frame,
                 "fp32_simt": {"value": f32_value, "unit": UNIT, "ms_per_step": t32 / max(3, args.steps // 2)},
                 "accuracy_vs_oracle": acc, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
-                "train_step": train,
+                "train_step": train, "large_scene": large,
                 "gpu_launches": int(6 * st.n_rounds * args.steps), "clocks": clocks}
         print(json.dumps(line), flush=True)
     r.close()

@@ -257,7 +257,7 @@ def kd_partition(scene: Scene, n_fields: int) -> Partition:
 
     def rec(idx, lo, hi, d):
         if d == 0:
-            leaves.append((lo.copy(), hi.copy()))
+            leaves.append((lo.copy(), hi.copy(), idx))
             return
         ext = hi - lo
         # longest axis first; fall back to another axis when occupied voxels
@@ -291,8 +291,15 @@ def kd_partition(scene: Scene, n_fields: int) -> Partition:
         rec(right, lr, hi, d - 1)
 
     rec(np.arange(xyz.shape[0]), np.zeros(3, dtype=np.int64), np.array(scene.dims, dtype=np.int64), depth)
-    boxes = np.array(leaves, dtype=np.int32)
-    return Partition(boxes, _labels_from_boxes(xyz, boxes))
+    boxes = np.array([(lo, hi) for (lo, hi, _) in leaves], dtype=np.int32)
+    # each occupied voxel lies in the leaf whose subset it reached (the boxes
+    # tile the grid, so this is also the containing box)
+    lab = np.full(xyz.shape[0], -1, dtype=np.int64)
+    for f, (_, _, idx) in enumerate(leaves):
+        lab[idx] = f
+    if (lab < 0).any():
+        raise RuntimeError("kd leaves do not cover every occupied voxel")
+    return Partition(boxes, lab.astype(np.uint16))
 
 
 def field_affine(scene: Scene, part: Partition) -> np.ndarray:
@@ -471,3 +478,16 @@ def floor256(views: str = "both", n_fields: int = 512, W: int = 64, H: int = 3, 
     cams = make_cameras(scene, 2, specs)
     return Workload(f"floor256_kd{n_fields}_w{W}h{H}", scene, part, field_affine(scene, part), W, H, w,
                     density_scale(delta), delta, 128, cams)
+
+
+def floor512(n_fields: int = 4096, W: int = 128, H: int = 4, role: int = ROLE_TEACHER) -> Workload:
+    """512^3 twenty-room floor (5 x 4 rooms, about 2% of voxels occupied),
+    4096 kd fields, W=128/H=4 MLPs (94,724 parameters each), one 2048x1024
+    equirectangular view, <=192 samples per ray."""
+    scene = floor_scene(5, 512, 5, 4, 0.03, height_frac=0.25, boxes_per_room=3)
+    part = kd_partition(scene, n_fields)
+    delta = scene.vox / 4
+    w = xavier_weights(5, role, part.n_fields, W, H)
+    cams = make_cameras(scene, 5, [(EQUIRECT, 2048, 1024, 0.0)])
+    return Workload(f"floor512_kd{n_fields}_w{W}h{H}", scene, part, field_affine(scene, part), W, H, w,
+                    density_scale(delta), delta, 192, cams)

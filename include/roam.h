@@ -43,7 +43,7 @@ typedef enum {
     ROAM_ERR_UNSUPPORTED = -7  /* valid request this build does not provide */
 } roam_status;
 
-enum { ROAM_F32 = 0, ROAM_BF16 = 1 };                 /* MLP arithmetic */
+enum { ROAM_F32 = 0, ROAM_BF16 = 1, ROAM_FP8 = 2 };   /* MLP arithmetic */
 enum { ROAM_EQUIRECT = 0, ROAM_PERSPECTIVE = 1 };     /* camera models */
 enum { ROAM_SOFTPLUS = 0, ROAM_RELU = 1 };            /* density activation */
 
@@ -94,7 +94,10 @@ typedef struct {
     int32_t n_max;        /* 1..1024 */
     float t_stop;         /* e.g. 1e-4; 0 disables early termination */
     float bg[3];
-    int32_t precision;    /* ROAM_F32 (SIMT FP32) or ROAM_BF16 (tcgen05 BF16, FP32 accumulate) */
+    int32_t precision;    /* ROAM_F32 (SIMT FP32), ROAM_BF16 (tcgen05 BF16, FP32 accumulate) or
+                             ROAM_FP8 (tcgen05 E4M3 weights with one FP32 scale per output
+                             channel, E4M3 activations, FP32 accumulate, FP32 biases; render
+                             and roam_mlp_eval only) */
     int32_t round_size;   /* kept samples marched per ray per round, 0 = library default */
     int32_t use_graph;    /* 1: roam_render captures its launch sequence into a CUDA graph
                              (once per configuration: view sizes, options, output pointers)
@@ -213,7 +216,7 @@ roam_status roam_bucket(roam_ctx *ctx, const uint16_t *keys, int64_t n, uint32_t
 
 /* Positional encoding + per-field MLP at n world points: p, d device
  * float[n][3] (d the world view direction), field device uint16[n];
- * out device float[n][4] = (sigma, r, g, b).  precision ROAM_F32 or
+ * out device float[n][4] = (sigma, r, g, b).  precision ROAM_F32, ROAM_FP8 or
  * ROAM_BF16.  Asynchronous. */
 roam_status roam_mlp_eval(roam_ctx *ctx, const float *p, const float *d, const uint16_t *field,
                           int64_t n, int precision, float *out, void *stream);

@@ -61,10 +61,11 @@ def lib():
         L.orc_march.argtypes = [i32p, f64p, D, i32p, f64p, f64p, D, I, i32p, i32p, i32p]
         L.orc_march.restype = I
         L.orc_encode.argtypes = [f64p, I, f64p]
-        L.orc_mlp.argtypes = [f32p, I, I, I, D, f64p, f64p, f64p, f64p]
+        L.orc_mlp.argtypes = [f32p, I, I, I, D, I, f64p, f64p, f64p, f64p]
+        L.orc_e4m3.argtypes = [D]; L.orc_e4m3.restype = D
         L.orc_composite.argtypes = [I, f64p, f64p, f64p, D, D, f64p, f64p, f64p]
         L.orc_composite.restype = I
-        L.orc_render.argtypes = [i32p, f64p, D, i32p, f32p, f32p, I, I, I, D, f64p, I, u32p, I64,
+        L.orc_render.argtypes = [i32p, f64p, D, i32p, f32p, f32p, I, I, I, D, I, f64p, I, u32p, I64,
                                  D, I, D, f64p, f64p, f64p, f64p, i32p, i32p, i32p, f64p]
         L.orc_render.restype = I
         L.orc_march_rays.argtypes = [i32p, f64p, D, i32p, f64p, I, u32p, I64, D, I, i32p, i32p, i32p, i32p]
@@ -110,13 +111,23 @@ def encode(x, L: int) -> np.ndarray:
     return out
 
 
-def mlp(w_field: np.ndarray, W: int, H: int, sigma_scale: float, aff: np.ndarray, p, d, act: int = 0):
+def e4m3(x) -> np.ndarray:
+    """Nearest FP8 E4M3 value of each element (ties to even, saturating at 448)."""
+    x = np.asarray(x, dtype=np.float64)
+    f = lib().orc_e4m3
+    return np.vectorize(lambda v: f(float(v)), otypes=[np.float64])(x)
+
+
+def mlp(w_field: np.ndarray, W: int, H: int, sigma_scale: float, aff: np.ndarray, p, d, act: int = 0,
+        quant: int = 0):
+    """One sample through one field's MLP: (sigma, r, g, b).  quant=1 takes the
+    FP8 E4M3 reading of the matrix layers."""
     w = np.ascontiguousarray(w_field, dtype=np.float32)
     a = np.ascontiguousarray(np.asarray(aff, dtype=np.float32), dtype=np.float64)
     p = np.ascontiguousarray(p, dtype=np.float64)
     d = np.ascontiguousarray(d, dtype=np.float64)
     out = np.zeros(4)
-    lib().orc_mlp(_p(w, ctypes.c_float), W, H, act, f32(sigma_scale), _p(a, ctypes.c_double),
+    lib().orc_mlp(_p(w, ctypes.c_float), W, H, act, f32(sigma_scale), int(quant), _p(a, ctypes.c_double),
                   _p(p, ctypes.c_double), _p(d, ctypes.c_double), _p(out, ctypes.c_double))
     return out
 
@@ -192,9 +203,10 @@ def march_rays(grid: Grid, cams16, rays: Optional[np.ndarray], delta: float, n_m
 
 def render(grid: Grid, weights, affine, W: int, H: int, sigma_scale: float, cams16,
            rays: Optional[np.ndarray], delta: float, n_max: int, t_stop: float = 1e-4,
-           bg=(0.0, 0.0, 0.0), act: int = 0):
+           bg=(0.0, 0.0, 0.0), act: int = 0, quant: int = 0):
     """Renders (view, pixel) rays, or every pixel of every view (rays=None).
-    Returns a dict of per-ray arrays."""
+    Returns a dict of per-ray arrays.  quant=1 takes the FP8 E4M3 reading of
+    the matrix layers."""
     cams = cams_f32(cams16)
     w = np.ascontiguousarray(weights, dtype=np.float32)
     aff = np.ascontiguousarray(affine, dtype=np.float32)
@@ -205,7 +217,7 @@ def render(grid: Grid, weights, affine, W: int, H: int, sigma_scale: float, cams
                n_kept=np.zeros(n_rays, np.int32), n_used=np.zeros(n_rays, np.int32),
                ties=np.zeros(n_rays, np.int32), margin=np.zeros(n_rays))
     rc = lib().orc_render(*grid.args(), _p(w, ctypes.c_float), _p(aff, ctypes.c_float), W, H, act,
-                          f32(sigma_scale), _p(cams, ctypes.c_double), int(cams.shape[0]),
+                          f32(sigma_scale), int(quant), _p(cams, ctypes.c_double), int(cams.shape[0]),
                           _p(r, ctypes.c_uint32), n_rays, f32(delta), n_max, f32(t_stop),
                           _p(bgv, ctypes.c_double), _p(out["rgb"], ctypes.c_double),
                           _p(out["depth"], ctypes.c_double), _p(out["opacity"], ctypes.c_double),

@@ -41,6 +41,13 @@
  *     which reproduce the paper's 6,212 parameters per tiny network);
  *   - density = sigma_scale * softplus(s) (or ReLU(s) when act == 1);
  *     the feature branch of the head has no activation; colour = sigmoid.
+ *
+ * The reduced-precision reading (quant == 1, the library's FP8 path; the
+ * paper fixes no arithmetic format): every matrix layer but the 3-output
+ * one takes its inputs rounded to FP8 E4M3 and its weights rounded to E4M3
+ * after division by a per-output-row scale s = max |row| / 448 (s and the
+ * division in FP32), then y = bias + s * sum(products), everything else in
+ * FP64 as above.
  */
 #define _GNU_SOURCE
 #include <math.h>
@@ -259,6 +266,7 @@ static void encode(const double *x, int L, double *out)
 typedef struct {
     int W, H, act;
     double sigma_scale;
+    int quant;                  /* 1: the FP8 E4M3 reading of the matrix layers */
 } orc_arch;
 
 /* y[o] = b[o] + sum_i Wm[o][i] x[i] */
@@ -268,6 +276,42 @@ static void dense(const float *Wm, const float *b, int n_out, int n_in, const do
         double acc = (double)b[r];
         for (int c = 0; c < n_in; ++c) acc += (double)Wm[(int64_t)r * n_in + c] * x[c];
         y[r] = acc;
+    }
+}
+
+/* Nearest value of the 8-bit E4M3 floating-point format (1 sign bit, 4
+ * exponent bits with bias 7, 3 mantissa bits; normal numbers from 2^-6,
+ * subnormal spacing 2^-9, largest finite value 448, no infinities), ties to
+ * even; magnitudes beyond 448 saturate to 448. */
+static double e4m3(double x)
+{
+    double a = fabs(x);
+    if (a == 0.0) return x;
+    int e;
+    frexp(a, &e);                 /* a = m 2^e, m in [0.5, 1): leading bit 2^(e-1) */
+    int lead = e - 1;
+    if (lead < -6) lead = -6;     /* subnormal range keeps the spacing of 2^-6 * 2^-3 */
+    double q = ldexp(1.0, lead - 3);
+    double r = nearbyint(a / q) * q;   /* default rounding mode: to nearest, ties to even */
+    if (r > 448.0) r = 448.0;
+    return copysign(r, x);
+}
+
+double orc_e4m3(double x) { return e4m3(x); }
+
+/* dense() in the FP8 reading: inputs and per-row-scaled weights rounded to E4M3 */
+static void dense_e4m3(const float *Wm, const float *b, int n_out, int n_in, const double *x, double *y)
+{
+    double xq[512];
+    for (int c = 0; c < n_in; ++c) xq[c] = e4m3((double)(float)x[c]);
+    for (int r = 0; r < n_out; ++r) {
+        const float *row = Wm + (int64_t)r * n_in;
+        float amax = 0.0f;
+        for (int c = 0; c < n_in; ++c) amax = fmaxf(amax, fabsf(row[c]));
+        const float s = amax > 0.0f ? amax / 448.0f : 1.0f;
+        double acc = 0.0;
+        for (int c = 0; c < n_in; ++c) acc += e4m3((double)(row[c] / s)) * xq[c];
+        y[r] = (double)b[r] + (double)s * acc;
     }
 }
 
@@ -296,21 +340,22 @@ static void mlp_forward(const float *w, const orc_arch *A, const double *aff, co
     encode(xl, 10, c->pe_x);
     const float *q = w;
     double h[256];
-    dense(q, q + W * ORC_PE_POS, W, ORC_PE_POS, c->pe_x, c->z[0]);
+    void (*mat)(const float *, const float *, int, int, const double *, double *) = A->quant ? dense_e4m3 : dense;
+    mat(q, q + W * ORC_PE_POS, W, ORC_PE_POS, c->pe_x, c->z[0]);
     q += W * ORC_PE_POS + W;
     for (int r = 0; r < W; ++r) h[r] = c->z[0][r] > 0.0 ? c->z[0][r] : 0.0;
     for (int k = 1; k < H; ++k) {
-        dense(q, q + W * W, W, W, h, c->z[k]);
+        mat(q, q + W * W, W, W, h, c->z[k]);
         q += W * W + W;
         for (int r = 0; r < W; ++r) h[r] = c->z[k][r] > 0.0 ? c->z[k][r] : 0.0;
     }
-    dense(q, q + (1 + W) * W, 1 + W, W, h, c->zh);
+    mat(q, q + (1 + W) * W, 1 + W, W, h, c->zh);
     q += (1 + W) * W + (1 + W);
     double s = c->zh[0];
     c->sigma = A->sigma_scale * (A->act == 1 ? (s > 0.0 ? s : 0.0) : softplus(s));
     for (int r = 0; r < W; ++r) c->in_c[r] = c->zh[1 + r];
     encode(d, 4, c->in_c + W);
-    dense(q, q + W * (W + ORC_PE_DIR), W, W + ORC_PE_DIR, c->in_c, c->zc);
+    mat(q, q + W * (W + ORC_PE_DIR), W, W + ORC_PE_DIR, c->in_c, c->zc);
     q += W * (W + ORC_PE_DIR) + W;
     double g[256];
     for (int r = 0; r < W; ++r) g[r] = c->zc[r] > 0.0 ? c->zc[r] : 0.0;
@@ -320,10 +365,10 @@ static void mlp_forward(const float *w, const orc_arch *A, const double *aff, co
 
 /* Public single-sample evaluation.  w: FP32 weights of one field in storage
  * order; aff = (scale[3], offset[3]); out = (sigma, r, g, b). */
-void orc_mlp(const float *w, int W, int H, int act, double sigma_scale, const double *aff,
+void orc_mlp(const float *w, int W, int H, int act, double sigma_scale, int quant, const double *aff,
              const double *p, const double *d, double *out)
 {
-    orc_arch A = {W, H, act, sigma_scale};
+    orc_arch A = {W, H, act, sigma_scale, quant};
     orc_cache c;
     mlp_forward(w, &A, aff, p, d, &c);
     out[0] = c.sigma;
@@ -531,12 +576,12 @@ static int render_ray(const orc_scene *S, const double *o, const double *d, doub
 
 static int setup_scene(orc_scene *S, const int32_t *dims, const double *origin, double vox,
                        const int32_t *label, const float *weights, const float *affine, int W, int H,
-                       int act, double sigma_scale, const double *cams, int n_views, double delta,
-                       int n_max, double t_stop, const double *bg)
+                       int act, double sigma_scale, int quant, const double *cams, int n_views,
+                       double delta, int n_max, double t_stop, const double *bg)
 {
     if (n_max > 1024 || W > 256 || H > 8 || H < 1) return -1;
     S->g = (orc_grid){{dims[0], dims[1], dims[2]}, {origin[0], origin[1], origin[2]}, vox, label};
-    S->A = (orc_arch){W, H, act, sigma_scale};
+    S->A = (orc_arch){W, H, act, sigma_scale, quant};
     S->P = orc_param_count(W, H);
     S->weights = weights;
     S->affine = affine;
@@ -555,12 +600,12 @@ static int setup_scene(orc_scene *S, const int32_t *dims, const double *origin, 
  * march, termination margin.  Returns 0, or -1 on bad sizes. */
 int orc_render(const int32_t *dims, const double *origin, double vox, const int32_t *label,
                const float *weights, const float *affine, int W, int H, int act, double sigma_scale,
-               const double *cams, int n_views, const uint32_t *rays, int64_t n_rays, double delta,
-               int n_max, double t_stop, const double *bg, double *rgb, double *depth,
+               int quant, const double *cams, int n_views, const uint32_t *rays, int64_t n_rays,
+               double delta, int n_max, double t_stop, const double *bg, double *rgb, double *depth,
                double *opacity, int32_t *n_kept, int32_t *n_used, int32_t *ties, double *margin)
 {
     orc_scene S;
-    if (setup_scene(&S, dims, origin, vox, label, weights, affine, W, H, act, sigma_scale, cams,
+    if (setup_scene(&S, dims, origin, vox, label, weights, affine, W, H, act, sigma_scale, quant, cams,
                     n_views, delta, n_max, t_stop, bg))
         return -1;
     int64_t starts[257];
@@ -595,7 +640,7 @@ int orc_march_rays(const int32_t *dims, const double *origin, double vox, const 
     orc_scene S;
     static const float dummy_w[1] = {0};
     static const double zero_bg[3] = {0, 0, 0};
-    if (setup_scene(&S, dims, origin, vox, label, dummy_w, dummy_w, 1, 1, 0, 1.0, cams, n_views,
+    if (setup_scene(&S, dims, origin, vox, label, dummy_w, dummy_w, 1, 1, 0, 1.0, 0, cams, n_views,
                     delta, n_max, 1e-4, zero_bg))
         return -1;
     int64_t starts[257];
@@ -636,7 +681,7 @@ double orc_loss_grad(const int32_t *dims, const double *origin, double vox, cons
                      double *rgb_out)
 {
     orc_scene S;
-    if (setup_scene(&S, dims, origin, vox, label, weights, affine, W, H, act, sigma_scale, cams,
+    if (setup_scene(&S, dims, origin, vox, label, weights, affine, W, H, act, sigma_scale, 0, cams,
                     n_views, delta, n_max, t_stop, bg))
         return NAN;
     int64_t starts[257];

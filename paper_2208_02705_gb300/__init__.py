@@ -17,7 +17,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libroam.so")
 
-ROAM_F32, ROAM_BF16 = 0, 1
+ROAM_F32, ROAM_BF16, ROAM_FP8 = 0, 1, 2
 ROAM_EQUIRECT, ROAM_PERSPECTIVE = 0, 1
 ROAM_SOFTPLUS, ROAM_RELU = 0, 1
 

@@ -129,8 +129,8 @@ struct MlpWeights {
     int64_t Pr;
     const void *wimg;          // BF16 tensor-core images [F][img_bytes]
     int64_t img_bytes;
-    const float *bias;         // FP32 biases for the TC epilogue [F][nb]
-    int nb;
+    const void *wimg8;         // FP8 E4M3 tensor-core images [F][img8_bytes]
+    int64_t img8_bytes;
     const float *affine;       // [F][6]
 };
 
@@ -179,14 +179,13 @@ void launch_adam(float *w32, float *m, float *v, const float *g, int64_t n, floa
 void set_error_message(const char *msg);
 
 // tcgen05 BF16 path
-bool tc_supported(int W, int H);
-int64_t tc_image_bytes(int W, int H);
-int tc_bias_count(int W, int H);
+bool tc_supported(int W, int H, bool f8);
+int64_t tc_image_bytes(int W, int H, bool f8);
 int tc_tile_samples();
-int tc_tile_group(int W);
-void launch_pack_tc(const float *w32, int n_fields, int W, int H, int64_t P, void *wimg,
-                    int64_t img_bytes, float *bias, int nb, cudaStream_t s);
-void launch_mlp_tc(const MlpWeights &w, const SampleSrc &src, const BucketBufs &b, Counters *ctr,
-                   float4 *out, int grid, cudaStream_t s);
+int tc_tile_group(int W, bool f8);
+void launch_pack_tc(const float *w32, int n_fields, int W, int H, int64_t P, void *wimg, int64_t img_bytes, bool f8,
+                    cudaStream_t s);
+void launch_mlp_tc(const MlpWeights &w, bool f8, const SampleSrc &src, const BucketBufs &b, Counters *ctr,
+                   float4 *out, int n_sm, cudaStream_t s);
 
 }  // namespace roam

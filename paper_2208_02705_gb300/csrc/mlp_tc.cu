@@ -1,28 +1,35 @@
-// tcgen05 BF16 evaluation of the per-field tiny MLPs (the concurrent MLP
-// queries of Sec. "Real-time Rendering Speedup" as a grouped GEMM chain on
-// the 5th-generation tensor cores).  One tile = 128 samples of one field =
-// one M=128 MMA row block; every layer of the chain is
-//   D[128 x N] (TMEM, FP32) = A[128 x K] (TMEM, BF16) * B[K x N] (SMEM, BF16)
-// with tcgen05.mma kind::f16.  The activations A never touch shared memory:
-// the epilogue reads D with tcgen05.ld (one row per thread), converts
-// (cvt.rn.relu.bf16x2 fuses the ReLU) and writes the next layer's A with
-// tcgen05.st, so the MMA streams only the weights from shared memory.  Every
-// bias rides in the MMA: A carries a constant-1 column and B the bias in the
-// matching row.  The field's weight image (all layers' B operands in the
-// 128-byte-swizzled K-major layout, then an FP32 table of the 3-output
-// layer) is copied to shared memory by the bulk-copy (TMA) engine when the
-// field changes.
+// tcgen05 evaluation of the per-field tiny MLPs (the concurrent MLP queries
+// of Sec. "Real-time Rendering Speedup" as a grouped GEMM chain on the
+// 5th-generation tensor cores), with BF16 or FP8 E4M3 operands and FP32
+// accumulation.  One tile = 128 samples of one field = one M=128 MMA row
+// block; every layer of the chain is
+//   D[128 x N] (TMEM, FP32) = A[128 x K] (TMEM) * B[K x N] (SMEM)
+// with tcgen05.mma kind::f16 (BF16) or kind::f8f6f4 (E4M3).  The activations
+// A never touch shared memory: the epilogue reads D with tcgen05.ld (one row
+// per thread), converts and writes the next layer's A with tcgen05.st, so
+// the MMA streams only the weights from shared memory.  The field's weight
+// image (all layers' B operands in the 128-byte-swizzled K-major layout,
+// then FP32 tables) is copied to shared memory by the bulk-copy (TMA) engine
+// when the field changes.
 //
 // A columns (row = sample):
 //   L1 input        [F(x_loc) (63) | 1]                          K = 64
 //   after L1        [h (W) | 1 | F(d) (27) | 0 0 0 0]             (the tail stays)
-//   hidden / head   [h (W) | 1 | ...]     B zero past the bias    K = W + 16
+//   hidden / head   [h (W) | 1 | ...]                            K = W + 16 or W
 //   colour          [feat (W) | 1 | F(d) (27) | 0 0 0 0]          K = W + 32
-// At W = 128 the folded hidden/head biases would cost a third 64-column
-// K-chunk per layer and the image would not fit in shared memory, so there
-// the hidden and head layers run at K = W and their biases are added in
-// FP32 by the epilogue from a table at the end of the image; the image then
-// fits (about 200 KB at H = 4) and two slots fill the 512 TMEM columns.
+//
+// Biases.  BF16 at W <= 64 folds every bias into the MMA: the constant-1
+// column of A meets the bias row of B.  BF16 at W = 128 folds only the L1
+// and colour biases (their K has the spare column anyway): a folded bias in
+// the hidden and head layers would cost a third 64-column K-chunk per layer
+// and the image would not fit in shared memory.  E4M3 folds none (a bias
+// rounded to 3 mantissa bits loses too much).  Unfolded biases are added in
+// FP32 by the epilogue from a per-layer table at the end of the image.
+//
+// E4M3 weights carry one FP32 scale per output channel (row n of layer l):
+// s = max_k |W[n][k]| / 448, B[k][n] = e4m3(W[n][k] / s), and the epilogue
+// forms y = s * D + b.  Activations are rounded to E4M3 unscaled (the
+// ReLU/PE values of these networks sit well inside the format's range).
 #include "internal.cuh"
 
 namespace roam {
@@ -34,18 +41,20 @@ constexpr unsigned long long kWaitNs = 2000000000ull;   // 2 s per wait
 __host__ __device__ constexpr int cdiv(int a, int b) { return (a + b - 1) / b; }
 
 // ---- shapes of the weight image ----
-template <int W, int H>
+template <int W, int H, bool F8>
 struct TcShape {
-    static constexpr bool kFold = W <= 64;     // hidden/head biases ride in the MMA
+    static constexpr bool kFold = !F8 && W <= 64;    // hidden/head biases ride in the MMA
+    static constexpr bool kTab = !kFold;             // FP32 per-layer scale/bias table in the image
+    static constexpr int kEB = F8 ? 1 : 2;           // bytes per operand element
+    static constexpr int kCE = 128 / kEB;            // K elements per 128-byte swizzle row (one chunk)
+    static constexpr int kKS = 32 / kEB;             // K of one MMA instruction (32 bytes)
     static constexpr int N_HEAD = W + 16;
     static constexpr int K_COL = W + 32;
     static constexpr int K_HID = kFold ? W + 16 : W;
-    static constexpr int N_OUT = 16;
-    static constexpr int kSlots = W <= 64 ? 4 : 2;
     static constexpr int kLayers = H + 2;      // L1, hidden, head, colour (the 3-output layer runs on CUDA cores)
     __host__ __device__ static constexpr int K(int l) { return l == 0 ? 64 : (l == H + 1 ? K_COL : K_HID); }
     __host__ __device__ static constexpr int N(int l) { return l == H ? N_HEAD : W; }
-    __host__ __device__ static constexpr int chunks(int l) { return cdiv(K(l), 64); }
+    __host__ __device__ static constexpr int chunks(int l) { return cdiv(K(l), kCE); }
     __host__ __device__ static constexpr int bytes(int l) { return chunks(l) * N(l) * 128; }
     __host__ __device__ static constexpr int offset(int l)
     {
@@ -56,31 +65,19 @@ struct TcShape {
     static constexpr int kMatBytes = offset(H + 2);
     // after the MMA operands: FP32 output layer, [W][4] (3 outputs + pad) then bias[4]
     static constexpr int kOutBytes = (4 * W + 4) * 4;
-    // unfolded widths: FP32 biases of the hidden layers ((H-1) x W), then the
-    // head's W features and its density logit, padded to 16 bytes
-    static constexpr int kNTab = kFold ? 0 : (((H - 1) * W + W + 1 + 3) & ~3);
-    static constexpr int kTabBytes = kNTab * 4;
-    static constexpr int kImageBytes = kMatBytes + kOutBytes + kTabBytes;
+    // then (kTab) per layer l: scale[kTabStride] and bias[kTabStride]; the
+    // head's entry W is its density logit
+    static constexpr int kTabStride = W + 4;
+    static constexpr int kNTab = kTab ? kLayers * 2 * kTabStride : 0;
+    static constexpr int kImageBytes = kMatBytes + kOutBytes + kNTab * 4;
     static constexpr int kImageAlloc = (kImageBytes + 1023) & ~1023;
-    static constexpr int kXChunks = cdiv(K_COL, 64) > 1 ? cdiv(K_COL, 64) : 1;
-    static constexpr int kXBytes = kXChunks * 128 * 128;
-    static constexpr int kNBias = ((H - 1) * W + W + 1 + 3 + 3) & ~3;
-    static constexpr int kTmemCols = N_HEAD <= 32 ? 32 : (N_HEAD <= 64 ? 64 : (N_HEAD <= 128 ? 128 : 256));
     // TMEM of one slot: accumulator D (N_HEAD columns), then the activations A
-    // of the next MMA (K_COL BF16 per row, two per 32-bit column)
+    // of the next MMA (K_COL elements per row, 4 / kEB per 32-bit column)
     static constexpr int kDCols = N_HEAD;
-    static constexpr int kACols = K_COL / 2;
+    static constexpr int kACols = K_COL * kEB / 4;
     static constexpr int kSlotCols = kDCols + kACols;
-    static constexpr int kSmem = 1024 + kXBytes + kImageBytes + 64;
+    static constexpr int kSlots = 512 / kSlotCols >= 4 ? 4 : (512 / kSlotCols >= 2 ? 2 : 1);
 };
-
-// byte offset of element (n, k) in a K-major, 128B-swizzled operand whose
-// K-chunks of 64 elements are stored as consecutive [rows][128 B] regions
-__host__ __device__ inline int swz_offset(int n, int k, int rows)
-{
-    const int chunk = k >> 6, kk = k & 63;
-    return chunk * rows * 128 + (n >> 3) * 1024 + (n & 7) * 128 + ((((kk >> 3) ^ (n & 7)) & 7) << 4) + (kk & 7) * 2;
-}
 
 // ---- PTX wrappers ----
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -88,11 +85,6 @@ __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)_
 __device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
 {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
-{
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
 __device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes)
@@ -130,20 +122,17 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volati
 {
     if (mbar_try(bar, parity)) return true;
     const unsigned long long t0 = now_ns();
-    for (uint32_t it = 0;; ++it) {
+    for (;;) {
         if (mbar_try(bar, parity)) return true;
-        {
-            if (*abort_flag && !drain) return false;
-            if (now_ns() - t0 > kWaitNs) {
-                *abort_flag = 1;
-                atomicOr(status, kStatusTimeout);
-                return false;
-            }
+        if (*abort_flag && !drain) return false;
+        if (now_ns() - t0 > kWaitNs) {
+            *abort_flag = 1;
+            atomicOr(status, kStatusTimeout);
+            return false;
         }
     }
 }
 
-__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
@@ -168,20 +157,16 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t saddr)
     return d;
 }
 
-// instruction descriptor: kind::f16, A = B = BF16, D = F32, both K-major, M = 128
+// instruction descriptors, D = F32, A and B K-major, M = 128:
+// kind::f16 with A = B = BF16 (format 1); kind::f8f6f4 with A = B = E4M3 (format 0)
 __host__ __device__ constexpr uint32_t idesc_bf16(int N)
 {
     return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
 }
 
-__device__ __forceinline__ void umma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc)
+__host__ __device__ constexpr uint32_t idesc_e4m3(int N)
 {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "setp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
-        "l"(a), "l"(b), "r"(idesc), "r"(acc)
-        : "memory");
+    return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
 }
 
 __device__ __forceinline__ void umma_commit(uint64_t *bar)
@@ -190,20 +175,60 @@ __device__ __forceinline__ void umma_commit(uint64_t *bar)
                  : "memory");
 }
 
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16])
+// D (TMEM) [+]= A (TMEM, 128 lanes, packed operand elements) * B (SMEM descriptor)
+template <bool F8>
+__device__ __forceinline__ void umma_ta(uint32_t d_tmem, uint32_t a_tmem, uint64_t b, uint32_t idesc, uint32_t acc)
 {
-    uint32_t r[16];
+    if constexpr (F8) {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "setp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d_tmem),
+            "r"(a_tmem), "l"(b), "r"(idesc), "r"(acc)
+            : "memory");
+    } else {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "setp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d_tmem),
+            "r"(a_tmem), "l"(b), "r"(idesc), "r"(acc)
+            : "memory");
+    }
+}
+
+__device__ __forceinline__ void tmem_ld16_nowait(uint32_t taddr, uint32_t (&r)[16])
+{
     asm volatile(
         "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
         "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
           "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
         : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// 16 (8) consecutive 32-bit TMEM columns of this thread's lane
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&v)[16])
+{
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], "
+        "{%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(taddr),
+        "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]), "r"(v[8]), "r"(v[9]),
+        "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15])
+        : "memory");
+}
+
+__device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t (&v)[8])
+{
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(taddr), "r"(v[0]),
+                 "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7])
+                 : "memory");
+}
+
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
+// element 2c in the low half of 32-bit column c
 __device__ __forceinline__ uint32_t pack_bf16(float a, float b)
 {
     uint32_t r;
@@ -211,22 +236,31 @@ __device__ __forceinline__ uint32_t pack_bf16(float a, float b)
     return r;
 }
 
-// 8 consecutive BF16 columns [c8*8, c8*8+8) of row `row` of a swizzled X
-__device__ __forceinline__ void st_x8(uint8_t *X, int row, int c8, uint4 v)
+// element 4c + i in byte i of 32-bit column c; round to nearest even,
+// magnitudes beyond 448 saturate
+__device__ __forceinline__ uint32_t pack_e4m3x4(float a, float b, float c, float d)
 {
-    const int chunk = c8 >> 3, cc = c8 & 7;
-    uint8_t *p = X + chunk * 16384 + (row >> 3) * 1024 + (row & 7) * 128 + (((cc ^ (row & 7)) & 7) << 4);
-    *reinterpret_cast<uint4 *>(p) = v;
+    uint16_t lo, hi;
+    asm("cvt.rn.satfinite.e4m3x2.f32 %0, %2, %1;" : "=h"(lo) : "f"(a), "f"(b));
+    asm("cvt.rn.satfinite.e4m3x2.f32 %0, %2, %1;" : "=h"(hi) : "f"(c), "f"(d));
+    return (uint32_t)lo | ((uint32_t)hi << 16);
 }
 
-__device__ __forceinline__ void st_x16(uint8_t *X, int row, int col, const float (&v)[16])
+// Writes 32 activation values (elements [32c, 32c + 32) of A) to TMEM.
+template <bool F8>
+__device__ __forceinline__ void st_act32(uint32_t tArow, int c, const float (&v)[32])
 {
-    uint4 a, b;
-    a.x = pack_bf16(v[0], v[1]); a.y = pack_bf16(v[2], v[3]); a.z = pack_bf16(v[4], v[5]); a.w = pack_bf16(v[6], v[7]);
-    b.x = pack_bf16(v[8], v[9]); b.y = pack_bf16(v[10], v[11]); b.z = pack_bf16(v[12], v[13]);
-    b.w = pack_bf16(v[14], v[15]);
-    st_x8(X, row, col >> 3, a);
-    st_x8(X, row, (col >> 3) + 1, b);
+    if constexpr (F8) {
+        uint32_t o[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) o[q] = pack_e4m3x4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+        tmem_st8(tArow + 8 * c, o);
+    } else {
+        uint32_t o[16];
+#pragma unroll
+        for (int q = 0; q < 16; ++q) o[q] = pack_bf16(v[2 * q], v[2 * q + 1]);
+        tmem_st16(tArow + 16 * c, o);
+    }
 }
 
 // sin(pi y), cos(pi y) for |y| up to 2^9: exact reduction of y to
@@ -260,69 +294,6 @@ __device__ __forceinline__ void encode1(float v, float (&s)[L], float (&c)[L])
 __device__ __forceinline__ float softplus_f(float s) { return s > 20.f ? s : log1pf(__expf(s)); }
 __device__ __forceinline__ float sigmoid_f(float s) { return 1.f / (1.f + __expf(-s)); }
 
-__device__ __forceinline__ bool mbar_test(uint64_t *bar, uint32_t parity)
-{
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-__device__ __forceinline__ void tmem_ld16_nowait(uint32_t taddr, uint32_t (&r)[16])
-{
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
-        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-        : "r"(taddr));
-}
-
-__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
-
-// 16 consecutive 32-bit TMEM columns of this thread's lane
-__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&v)[16])
-{
-    asm volatile(
-        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], "
-        "{%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(taddr),
-        "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]), "r"(v[8]), "r"(v[9]),
-        "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15])
-        : "memory");
-}
-
-__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
-
-// D (TMEM) [+]= A (TMEM, 128 lanes x K/2 columns of BF16 pairs) * B (SMEM descriptor)
-__device__ __forceinline__ void umma_ta(uint32_t d_tmem, uint32_t a_tmem, uint64_t b, uint32_t idesc, uint32_t acc)
-{
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "setp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d_tmem),
-        "r"(a_tmem), "l"(b), "r"(idesc), "r"(acc)
-        : "memory");
-}
-
-// 32 floats -> 16 BF16 pairs (element 2c in the low half of column c)
-__device__ __forceinline__ void pack16(const float *v, uint32_t (&o)[16])
-{
-#pragma unroll
-    for (int q = 0; q < 16; ++q) o[q] = pack_bf16(v[2 * q], v[2 * q + 1]);
-}
-
-__device__ __forceinline__ uint32_t pack_bf16_relu(float a, float b)
-{
-    uint32_t r;
-    asm("cvt.rn.relu.bf16x2.f32 %0, %2, %1;" : "=r"(r) : "f"(a), "f"(b));
-    return r;
-}
-
 // Named barrier over n threads that also ORs a flag across them: every
 // participant gets the same answer, so an abort leaves all of them together.
 __device__ __forceinline__ bool named_sync_or(int id, int n, bool flag)
@@ -337,34 +308,6 @@ __device__ __forceinline__ bool named_sync_or(int id, int n, bool flag)
         : "r"(id), "r"(n), "r"((uint32_t)flag)
         : "memory");
     return r != 0;
-}
-
-// 16 accumulator columns -> 16 BF16 X columns (two 16-byte chunks)
-template <bool kRelu>
-__device__ __forceinline__ void st_x16_bits(uint8_t *X, int row, int col, const uint32_t (&r)[16])
-{
-    uint4 a, b;
-    if (kRelu) {
-        a.x = pack_bf16_relu(__uint_as_float(r[0]), __uint_as_float(r[1]));
-        a.y = pack_bf16_relu(__uint_as_float(r[2]), __uint_as_float(r[3]));
-        a.z = pack_bf16_relu(__uint_as_float(r[4]), __uint_as_float(r[5]));
-        a.w = pack_bf16_relu(__uint_as_float(r[6]), __uint_as_float(r[7]));
-        b.x = pack_bf16_relu(__uint_as_float(r[8]), __uint_as_float(r[9]));
-        b.y = pack_bf16_relu(__uint_as_float(r[10]), __uint_as_float(r[11]));
-        b.z = pack_bf16_relu(__uint_as_float(r[12]), __uint_as_float(r[13]));
-        b.w = pack_bf16_relu(__uint_as_float(r[14]), __uint_as_float(r[15]));
-    } else {
-        a.x = pack_bf16(__uint_as_float(r[0]), __uint_as_float(r[1]));
-        a.y = pack_bf16(__uint_as_float(r[2]), __uint_as_float(r[3]));
-        a.z = pack_bf16(__uint_as_float(r[4]), __uint_as_float(r[5]));
-        a.w = pack_bf16(__uint_as_float(r[6]), __uint_as_float(r[7]));
-        b.x = pack_bf16(__uint_as_float(r[8]), __uint_as_float(r[9]));
-        b.y = pack_bf16(__uint_as_float(r[10]), __uint_as_float(r[11]));
-        b.z = pack_bf16(__uint_as_float(r[12]), __uint_as_float(r[13]));
-        b.w = pack_bf16(__uint_as_float(r[14]), __uint_as_float(r[15]));
-    }
-    st_x8(X, row, col >> 3, a);
-    st_x8(X, row, (col >> 3) + 1, b);
 }
 
 // Everything the encoding of one sample needs, fetched a tile ahead.
@@ -402,11 +345,13 @@ __device__ __forceinline__ SampleIn fetch_sample(const SampleSrc &src, const Buc
 // overlap.  Tiles come in field-uniform groups of kSlots (bucket padding);
 // at a field change all slots meet at a CTA barrier, thread 0 reloads the
 // shared weight image, and each issuer waits for it before its next MMA.
-template <int W, int H, int kSlots>
-__global__ void __launch_bounds__(kSlots * 128, 1)
-    k_mlp_tc(MlpWeights w, SampleSrc src, BucketBufs b, Counters *ctr, float4 *out)
+template <int W, int H, bool F8>
+__global__ void __launch_bounds__(TcShape<W, H, F8>::kSlots * 128, 1)
+    k_mlp_tc(const void *wimg, int64_t img_bytes, const float *affine, float sig_scale, int act, SampleSrc src,
+             BucketBufs b, Counters *ctr, float4 *out)
 {
-    using S = TcShape<W, H>;
+    using S = TcShape<W, H, F8>;
+    constexpr int kSlots = S::kSlots;
     constexpr int kLayers = S::kLayers;
     constexpr int kCols = S::kSlotCols;
     constexpr int kTmemAlloc = kSlots * kCols <= 32 ? 32 : (kSlots * kCols <= 64 ? 64 :
@@ -448,6 +393,7 @@ __global__ void __launch_bounds__(kSlots * 128, 1)
     const uint32_t trow = tslot + ((uint32_t)(wq * 32) << 16);
     const uint32_t tArow = tA + ((uint32_t)(wq * 32) << 16);
     const uint32_t imga = smem_u32(IMG);
+    const float *tab = reinterpret_cast<const float *>(IMG + S::kMatBytes + S::kOutBytes);
 
     const uint32_t n_groups = ctr->n_tiles / kSlots;
     const uint32_t g0 = (uint32_t)((uint64_t)n_groups * blockIdx.x / gridDim.x);
@@ -458,7 +404,6 @@ __global__ void __launch_bounds__(kSlots * 128, 1)
     bool w_ready = false, w_waited_last = true;
     bool img_seen = false;     // this thread has waited for the current image (before generic loads of it)
     bool aborted = false;
-    const float sig_scale = w.sigma_scale;
     Tile tl{0u, 0u, 0u, 0u};
     SampleIn nxt{0u, 0.f, 0.f, 0.f, 0.f, 0.f, 1.f};
     uint32_t g = g0;
@@ -474,7 +419,7 @@ __global__ void __launch_bounds__(kSlots * 128, 1)
             if (named_sync_or(15, kSlots * 128, aborted || *abortp)) break;
             if (threadIdx.x == 0) {
                 mbar_expect_tx(&bar_w, (uint32_t)S::kImageBytes);
-                const uint8_t *gsrc = reinterpret_cast<const uint8_t *>(w.wimg) + (int64_t)f * w.img_bytes;
+                const uint8_t *gsrc = reinterpret_cast<const uint8_t *>(wimg) + (int64_t)f * img_bytes;
                 for (int off = 0; off < S::kImageBytes; off += 16384) {
                     const int nb = S::kImageBytes - off < 16384 ? S::kImageBytes - off : 16384;
                     bulk_g2s(IMG + off, gsrc + off, (uint32_t)nb, &bar_w);
@@ -494,7 +439,7 @@ __global__ void __launch_bounds__(kSlots * 128, 1)
             continue;
         }
         const bool valid = (uint32_t)row < cur.count;
-        const float *aff = w.affine + 6 * (int64_t)cur.field;
+        const float *aff = affine + 6 * (int64_t)cur.field;
         // ---- L1 input: [F(x_loc) | 1] ----
         {
             const float xl[3] = {fmaf(__ldg(aff + 0), sm.px, __ldg(aff + 3)), fmaf(__ldg(aff + 1), sm.py, __ldg(aff + 4)),
@@ -516,11 +461,13 @@ __global__ void __launch_bounds__(kSlots * 128, 1)
 #pragma unroll
                 for (int q = 0; q < 64; ++q) e[q] = 0.f;
             }
-            uint32_t pk[16];
-            pack16(e, pk);
-            tmem_st16(tArow, pk);
-            pack16(e + 32, pk);
-            tmem_st16(tArow + 16, pk);
+#pragma unroll
+            for (int c = 0; c < 2; ++c) {
+                float v[32];
+#pragma unroll
+                for (int q = 0; q < 32; ++q) v[q] = e[32 * c + q];
+                st_act32<F8>(tArow, c, v);
+            }
         }
         // the next tile's gathers overlap this tile's layers
         if (g + 1 < g1) nxt = fetch_sample(src, b, tl, row);
@@ -544,13 +491,14 @@ __global__ void __launch_bounds__(kSlots * 128, 1)
                 if (ok) {
                     tc_fence_after();
                     const int K = S::K(l), N = S::N(l);
-                    const uint32_t idesc = idesc_bf16(N);
+                    const uint32_t idesc = F8 ? idesc_e4m3(N) : idesc_bf16(N);
                     const uint32_t ba = imga + S::offset(l);
+                    // one MMA per 32 bytes of K: 4 per 128-byte chunk, 8 TMEM columns of A each
 #pragma unroll 1
-                    for (int ks = 0; ks < K / 16; ++ks) {
+                    for (int ks = 0; ks < K / S::kKS; ++ks) {
                         const int ch = ks >> 2, kin = ks & 3;
-                        umma_ta(tslot, tA + (uint32_t)(ks * 8), sdesc(ba + ch * N * 128 + kin * 32), idesc,
-                                ks > 0 ? 1u : 0u);
+                        umma_ta<F8>(tslot, tA + (uint32_t)(ks * 8), sdesc(ba + ch * N * 128 + kin * 32), idesc,
+                                    ks > 0 ? 1u : 0u);
                     }
                 }
                 umma_commit(&bar_d[slot]);
@@ -573,47 +521,51 @@ __global__ void __launch_bounds__(kSlots * 128, 1)
             if (l == H) tmem_ld16_nowait(trow + W, rs);
             tmem_wait_ld();
             tc_fence_before();
-            const float *btab = reinterpret_cast<const float *>(IMG + S::kMatBytes + S::kOutBytes) + (l >= 1 ? l - 1 : 0) * W;
-            if constexpr (!S::kFold) {
-                if (l >= 1 && !img_seen) {
-                    mbar_wait(&bar_w, (n_changes - 1) & 1u, abortp, status);
-                    img_seen = true;
-                }
+            // the FP32 per-layer table, where this layer's epilogue uses it
+            const bool use_tab = S::kTab && (F8 || (l >= 1 && l <= H));
+            const float *tsc = tab + l * 2 * S::kTabStride, *tbi = tsc + S::kTabStride;
+            if (use_tab && !img_seen) {
+                mbar_wait(&bar_w, (n_changes - 1) & 1u, abortp, status);
+                img_seen = true;
             }
             if (l < H + 1) {
                 // next activations: head features stay linear, every other layer ReLU
 #pragma unroll
                 for (int c = 0; c < W / 32; ++c) {
-                    float bv[32];
+                    float v[32];
 #pragma unroll
-                    for (int q = 0; q < 32; ++q) bv[q] = 0.f;
-                    if constexpr (!S::kFold) {
-                        if (l >= 1) {
+                    for (int q = 0; q < 32; ++q) v[q] = __uint_as_float(r[(32 * c + q) >> 4][(32 * c + q) & 15]);
+                    if constexpr (S::kTab) {
+                        if (use_tab) {
 #pragma unroll
                             for (int q = 0; q < 8; ++q) {
-                                const float4 t = reinterpret_cast<const float4 *>(btab + 32 * c)[q];
-                                bv[4 * q] = t.x; bv[4 * q + 1] = t.y; bv[4 * q + 2] = t.z; bv[4 * q + 3] = t.w;
+                                const float4 bb = reinterpret_cast<const float4 *>(tbi + 32 * c)[q];
+                                if constexpr (F8) {
+                                    const float4 ss = reinterpret_cast<const float4 *>(tsc + 32 * c)[q];
+                                    v[4 * q] = fmaf(v[4 * q], ss.x, bb.x);
+                                    v[4 * q + 1] = fmaf(v[4 * q + 1], ss.y, bb.y);
+                                    v[4 * q + 2] = fmaf(v[4 * q + 2], ss.z, bb.z);
+                                    v[4 * q + 3] = fmaf(v[4 * q + 3], ss.w, bb.w);
+                                } else {
+                                    v[4 * q] += bb.x; v[4 * q + 1] += bb.y; v[4 * q + 2] += bb.z; v[4 * q + 3] += bb.w;
+                                }
                             }
                         }
                     }
-                    uint32_t v16[16];
+                    if (l != H) {
 #pragma unroll
-                    for (int q = 0; q < 16; ++q) {
-                        const int e0 = 32 * c + 2 * q;
-                        const float a0 = __uint_as_float(r[e0 >> 4][e0 & 15]) + bv[2 * q];
-                        const float a1 = __uint_as_float(r[(e0 + 1) >> 4][(e0 + 1) & 15]) + bv[2 * q + 1];
-                        v16[q] = l == H ? pack_bf16(a0, a1) : pack_bf16_relu(a0, a1);
+                        for (int q = 0; q < 32; ++q) v[q] = fmaxf(v[q], 0.f);
                     }
-                    tmem_st16(tArow + 16 * c, v16);
+                    st_act32<F8>(tArow, c, v);
                 }
                 if (l == H) {
                     // density from column W of the head
                     float sl = __uint_as_float(rs[0]);
-                    if constexpr (!S::kFold) sl += btab[W];
-                    sigma = sig_scale * (w.act == ROAM_RELU ? fmaxf(sl, 0.f) : softplus_f(sl));
+                    if (use_tab) sl = F8 ? fmaf(sl, tsc[W], tbi[W]) : sl + tbi[W];
+                    sigma = sig_scale * (act == ROAM_RELU ? fmaxf(sl, 0.f) : softplus_f(sl));
                 }
                 if (l == 0) {
-                    // tail of X from here on: [1 | F(d) | 0 0 0 0] at columns W .. W+31
+                    // tail of A from here on: [1 | F(d) | 0 0 0 0] at columns W .. W+31
                     float e[32];
                     e[0] = valid ? 1.0f : 0.0f;
                     const float dv[3] = {sm.dx, sm.dy, sm.dz};
@@ -629,9 +581,7 @@ __global__ void __launch_bounds__(kSlots * 128, 1)
                         }
                     }
                     e[28] = e[29] = e[30] = e[31] = 0.f;
-                    uint32_t pt[16];
-                    pack16(e, pt);
-                    tmem_st16(tArow + W / 2, pt);
+                    st_act32<F8>(tArow, W / 32, e);
                 }
             } else {
                 // colour layer: g = relu(z) in FP32, then rgb = sigmoid(Wo g + bo) with
@@ -645,9 +595,21 @@ __global__ void __launch_bounds__(kSlots * 128, 1)
                 float4 acc = wo[W];
 #pragma unroll
                 for (int c = 0; c < W / 16; ++c) {
+                    float sc[16], bi[16];
+#pragma unroll
+                    for (int q = 0; q < 16; ++q) { sc[q] = 1.f; bi[q] = 0.f; }
+                    if constexpr (F8) {
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            const float4 ss = reinterpret_cast<const float4 *>(tsc + 16 * c)[q];
+                            const float4 bb = reinterpret_cast<const float4 *>(tbi + 16 * c)[q];
+                            sc[4 * q] = ss.x; sc[4 * q + 1] = ss.y; sc[4 * q + 2] = ss.z; sc[4 * q + 3] = ss.w;
+                            bi[4 * q] = bb.x; bi[4 * q + 1] = bb.y; bi[4 * q + 2] = bb.z; bi[4 * q + 3] = bb.w;
+                        }
+                    }
 #pragma unroll
                     for (int q = 0; q < 16; ++q) {
-                        const float gk = fmaxf(__uint_as_float(r[c][q]), 0.f);
+                        const float gk = fmaxf(fmaf(__uint_as_float(r[c][q]), sc[q], bi[q]), 0.f);
                         const float4 wk = wo[16 * c + q];
                         acc.x = fmaf(wk.x, gk, acc.x);
                         acc.y = fmaf(wk.y, gk, acc.y);
@@ -671,61 +633,125 @@ __global__ void __launch_bounds__(kSlots * 128, 1)
     }
 }
 
-// API layout -> BF16 image of every layer + FP32 bias table.
-template <int W, int H>
-__global__ void k_pack_tc(const float *__restrict__ w32, int n_fields, int64_t P, uint8_t *__restrict__ img,
-                          int64_t img_bytes, float *__restrict__ bias, int nb)
+// ---- packing: API layout -> tensor-core image ----
+
+// offsets of one field's layers in the API layout (row-major [out][in], then bias[out])
+struct ApiLayout {
+    int64_t l1, hid, head, col, out;
+    __host__ __device__ ApiLayout(int W, int H)
+    {
+        l1 = 0;
+        hid = (int64_t)W * kPeX + W;
+        head = hid + (int64_t)(H - 1) * (W * W + W);
+        col = head + (int64_t)(1 + W) * W + (1 + W);
+        out = col + (int64_t)W * (W + kPeD) + W;
+    }
+};
+
+// Weight at (n, k) of the B operand of layer l, as the MMA sees it (folded
+// bias entries included where the layout folds them).
+template <int W, int H, bool F8>
+__device__ float operand_value(const float *wf, const ApiLayout &o, int l, int n, int k)
 {
-    using S = TcShape<W, H>;
-    // offsets of the API layout
-    const int64_t o_l1 = 0, o_hid = (int64_t)W * kPeX + W;
-    const int64_t o_head = o_hid + (int64_t)(H - 1) * (W * W + W);
-    const int64_t o_col = o_head + (int64_t)(1 + W) * W + (1 + W);
-    const int64_t o_out = o_col + (int64_t)W * (W + kPeD) + W;
-    const int64_t per = S::kMatBytes / 2;        // BF16 elements of the MMA operands per field
+    using S = TcShape<W, H, F8>;
+    if (k >= S::K(l)) return 0.f;
+    if (l == 0) {
+        if (n >= W) return 0.f;
+        if (k < kPeX) return wf[o.l1 + (int64_t)n * kPeX + k];
+        return (k == kPeX && !F8) ? wf[o.l1 + (int64_t)W * kPeX + n] : 0.f;
+    }
+    if (l < H) {
+        const int64_t ob = o.hid + (int64_t)(l - 1) * (W * W + W);
+        if (k < W) return wf[ob + (int64_t)n * W + k];
+        return (k == W && S::kFold) ? wf[ob + (int64_t)W * W + n] : 0.f;
+    }
+    if (l == H) {
+        // rows: W features (API rows 1..W), then the density logit (API row 0)
+        const int ar = n < W ? 1 + n : (n == W ? 0 : -1);
+        if (ar < 0) return 0.f;
+        if (k < W) return wf[o.head + (int64_t)ar * W + k];
+        return (k == W && S::kFold) ? wf[o.head + (int64_t)(1 + W) * W + ar] : 0.f;
+    }
+    const int kc = W + kPeD;
+    if (k < W) return wf[o.col + (int64_t)n * kc + k];
+    if (k == W) return F8 ? 0.f : wf[o.col + (int64_t)W * kc + n];
+    if (k <= W + kPeD) return wf[o.col + (int64_t)n * kc + (k - 1)];
+    return 0.f;
+}
+
+// bias of output n of layer l (the head's n = W is the density logit)
+template <int W, int H>
+__device__ float layer_bias(const float *wf, const ApiLayout &o, int l, int n)
+{
+    if (l == 0) return n < W ? wf[o.l1 + (int64_t)W * kPeX + n] : 0.f;
+    if (l < H) return n < W ? wf[o.hid + (int64_t)(l - 1) * (W * W + W) + (int64_t)W * W + n] : 0.f;
+    if (l == H)
+        return n < W ? wf[o.head + (int64_t)(1 + W) * W + 1 + n] : (n == W ? wf[o.head + (int64_t)(1 + W) * W] : 0.f);
+    return n < W ? wf[o.col + (int64_t)W * (W + kPeD) + n] : 0.f;
+}
+
+// per-layer FP32 table: E4M3 channel scales (max |row| / 448, 1 for an
+// all-zero row; 1 for BF16) and the biases
+template <int W, int H, bool F8>
+__global__ void k_pack_tab(const float *__restrict__ w32, int n_fields, int64_t P, uint8_t *__restrict__ img,
+                           int64_t img_bytes)
+{
+    using S = TcShape<W, H, F8>;
+    const ApiLayout o(W, H);
+    const int64_t per = (int64_t)S::kLayers * S::kTabStride;
+    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < (int64_t)n_fields * per;
+         g += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t f = g / per;
+        const int l = (int)((g % per) / S::kTabStride), n = (int)(g % S::kTabStride);
+        const float *wf = w32 + f * P;
+        float s = 1.f;
+        if (F8 && n < S::N(l)) {
+            float amax = 0.f;
+            for (int k = 0; k < S::K(l); ++k) amax = fmaxf(amax, fabsf(operand_value<W, H, F8>(wf, o, l, n, k)));
+            if (amax > 0.f) s = amax / 448.0f;
+        }
+        float *t = reinterpret_cast<float *>(img + f * img_bytes + S::kMatBytes + S::kOutBytes) + l * 2 * S::kTabStride;
+        t[n] = s;
+        t[S::kTabStride + n] = layer_bias<W, H>(wf, o, l, n);
+    }
+}
+
+template <int W, int H, bool F8>
+__global__ void k_pack_tc(const float *__restrict__ w32, int n_fields, int64_t P, uint8_t *__restrict__ img,
+                          int64_t img_bytes)
+{
+    using S = TcShape<W, H, F8>;
+    const ApiLayout o(W, H);
+    const int64_t per = S::kMatBytes / S::kEB;        // operand elements per field
     const int64_t n = (int64_t)n_fields * per;
     for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x) {
         const int64_t f = g / per;
-        const int byte = (int)((g % per) * 2);
-        // find the layer and (n, k) of this byte
+        const int byte = (int)((g % per) * S::kEB);
+        // find the layer and (n, k) of this element
         int l = 0;
         while (l + 1 < S::kLayers && byte >= S::offset(l + 1)) ++l;
         const int lb = byte - S::offset(l);
-        const int N = S::N(l), K = S::K(l);
+        const int N = S::N(l);
         const int chunk = lb / (N * 128);
         const int in_chunk = lb % (N * 128);
         const int nrow = (in_chunk / 1024) * 8 + (in_chunk % 1024) / 128;
         const int sw16 = (in_chunk % 128) / 16;
-        const int k8 = (sw16 ^ (nrow & 7)) & 7;
-        const int k = chunk * 64 + k8 * 8 + (in_chunk % 16) / 2;
+        const int u = (sw16 ^ (nrow & 7)) & 7;               // 16-byte unit before the swizzle
+        const int k = chunk * S::kCE + u * (16 / S::kEB) + (in_chunk % 16) / S::kEB;
         const float *wf = w32 + f * P;
-        float v = 0.f;
-        if (k < K) {
-            if (l == 0) {
-                if (k < kPeX) v = wf[o_l1 + (int64_t)nrow * kPeX + k];
-                else if (k == kPeX) v = wf[o_l1 + (int64_t)W * kPeX + nrow];
-            } else if (l < H) {
-                const int64_t ob = o_hid + (int64_t)(l - 1) * (W * W + W);
-                if (k < W) v = wf[ob + (int64_t)nrow * W + k];
-                else if (k == W) v = wf[ob + (int64_t)W * W + nrow];
-            } else if (l == H) {
-                // rows: W features (API rows 1..W), then the density logit (API row 0)
-                const int ar = nrow < W ? 1 + nrow : (nrow == W ? 0 : -1);
-                if (ar >= 0) {
-                    if (k < W) v = wf[o_head + (int64_t)ar * W + k];
-                    else if (k == W) v = wf[o_head + (int64_t)(1 + W) * W + ar];
-                }
-            } else if (l == H + 1) {
-                const int kc = W + kPeD;
-                if (k < W) v = wf[o_col + (int64_t)nrow * kc + k];
-                else if (k == W) v = wf[o_col + (int64_t)W * kc + nrow];
-                else if (k <= W + kPeD) v = wf[o_col + (int64_t)nrow * kc + (k - 1)];
-            }
+        const float v = operand_value<W, H, F8>(wf, o, l, nrow, k);
+        uint8_t *dst = img + f * img_bytes;
+        if constexpr (F8) {
+            const float s =
+                reinterpret_cast<const float *>(dst + S::kMatBytes + S::kOutBytes)[l * 2 * S::kTabStride + nrow];
+            uint16_t q;
+            asm("cvt.rn.satfinite.e4m3x2.f32 %0, %2, %1;" : "=h"(q) : "f"(v / s), "f"(0.f));
+            dst[g % per] = (uint8_t)(q & 0xffu);
+        } else {
+            const uint32_t bits = __float_as_uint(v);
+            const uint32_t r = bits + 0x7fffu + ((bits >> 16) & 1u);     // round to nearest even
+            reinterpret_cast<uint16_t *>(dst)[g % per] = (uint16_t)(r >> 16);
         }
-        const uint32_t bits = __float_as_uint(v);
-        // round to nearest even
-        const uint32_t r = bits + 0x7fffu + ((bits >> 16) & 1u);
-        reinterpret_cast<uint16_t *>(img + f * img_bytes)[g % per] = (uint16_t)(r >> 16);
     }
     // FP32 output layer after the operands: [W][4] (weights of the 3 colours, pad 0), then bias[4]
     const int nout = 4 * W + 4;
@@ -737,62 +763,31 @@ __global__ void k_pack_tc(const float *__restrict__ w32, int n_fields, int64_t P
         float v = 0.f;
         if (q < 4 * W) {
             const int k = q / 4, c = q % 4;
-            if (c < 3) v = wf[o_out + (int64_t)c * W + k];
+            if (c < 3) v = wf[o.out + (int64_t)c * W + k];
         } else if (q - 4 * W < 3) {
-            v = wf[o_out + 3 * W + (q - 4 * W)];
+            v = wf[o.out + 3 * W + (q - 4 * W)];
         }
         reinterpret_cast<float *>(img + f * img_bytes + S::kMatBytes)[q] = v;
     }
-    // unfolded widths: the FP32 bias table of the hidden and head layers
-    if (S::kNTab > 0) {
-        for (int64_t gi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; gi < (int64_t)n_fields * S::kNTab;
-             gi += (int64_t)gridDim.x * blockDim.x) {
-            const int64_t f = gi / S::kNTab;
-            const int q = (int)(gi % S::kNTab);
-            const float *wf = w32 + f * P;
-            float v = 0.f;
-            if (q < (H - 1) * W) v = wf[o_hid + (int64_t)(q / W) * (W * W + W) + (int64_t)W * W + q % W];
-            else if (q < H * W) v = wf[o_head + (int64_t)(1 + W) * W + 1 + (q - (H - 1) * W)];
-            else if (q == H * W) v = wf[o_head + (int64_t)(1 + W) * W];
-            reinterpret_cast<float *>(img + f * img_bytes + S::kMatBytes + S::kOutBytes)[q] = v;
-        }
-    }
-    // bias table: hidden (H-1)*W, head features W, head density 1, output 3
-    const int64_t nbt = (int64_t)n_fields * nb;
-    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < nbt; g += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t f = g / nb;
-        const int q = (int)(g % nb);
-        const float *wf = w32 + f * P;
-        float v = 0.f;
-        if (q < (H - 1) * W) {
-            const int l = q / W, o = q % W;
-            v = wf[o_hid + (int64_t)l * (W * W + W) + (int64_t)W * W + o];
-        } else if (q < (H - 1) * W + W) {
-            v = wf[o_head + (int64_t)(1 + W) * W + 1 + (q - (H - 1) * W)];
-        } else if (q == (H - 1) * W + W) {
-            v = wf[o_head + (int64_t)(1 + W) * W];
-        } else if (q < (H - 1) * W + W + 4) {
-            v = wf[o_out + 3 * W + (q - (H - 1) * W - W - 1)];
-        }
-        bias[g] = v;
-    }
 }
 
-template <int W, int H>
-int tc_smem_bytes() { return 1024 + TcShape<W, H>::kImageAlloc; }
+template <int W, int H, bool F8>
+int tc_smem_bytes() { return 1024 + TcShape<W, H, F8>::kImageAlloc; }
 
-template <int W, int H>
+template <int W, int H, bool F8>
 void launch_t(const MlpWeights &w, const SampleSrc &src, const BucketBufs &b, Counters *ctr, float4 *out, int n_sm,
               cudaStream_t s)
 {
-    constexpr int kSlots = TcShape<W, H>::kSlots;
-    const int smem = tc_smem_bytes<W, H>();
+    constexpr int kSlots = TcShape<W, H, F8>::kSlots;
+    const int smem = tc_smem_bytes<W, H, F8>();
     static bool attr = false;
     if (!attr) {
-        cudaFuncSetAttribute(k_mlp_tc<W, H, kSlots>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        cudaFuncSetAttribute(k_mlp_tc<W, H, F8>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         attr = true;
     }
-    k_mlp_tc<W, H, kSlots><<<n_sm, kSlots * 128, smem, s>>>(w, src, b, ctr, out);
+    const void *img = F8 ? w.wimg8 : w.wimg;
+    const int64_t ib = F8 ? w.img8_bytes : w.img_bytes;
+    k_mlp_tc<W, H, F8><<<n_sm, kSlots * 128, smem, s>>>(img, ib, w.affine, w.sigma_scale, w.act, src, b, ctr, out);
 }
 
 #define ROAM_TC_CASES                                                                                   \
@@ -801,45 +796,62 @@ void launch_t(const MlpWeights &w, const SampleSrc &src, const BucketBufs &b, Co
 
 }  // namespace
 
-bool tc_supported(int W, int H)
+bool tc_supported(int W, int H, bool f8)
 {
     if (H < 1 || H > 4) return false;
 #define ROAM_CASE(WW, HH) \
-    if (W == WW && H == HH) return tc_smem_bytes<WW, HH>() <= 227 * 1024;
+    if (W == WW && H == HH) return (f8 ? tc_smem_bytes<WW, HH, true>() : tc_smem_bytes<WW, HH, false>()) <= 227 * 1024;
     ROAM_TC_CASES
 #undef ROAM_CASE
     return false;
 }
 
-int64_t tc_image_bytes(int W, int H)
+int64_t tc_image_bytes(int W, int H, bool f8)
 {
 #define ROAM_CASE(WW, HH) \
-    if (W == WW && H == HH) return TcShape<WW, HH>::kImageBytes;
+    if (W == WW && H == HH) return f8 ? TcShape<WW, HH, true>::kImageBytes : TcShape<WW, HH, false>::kImageBytes;
     ROAM_TC_CASES
 #undef ROAM_CASE
     return 0;
 }
 
-int tc_bias_count(int W, int H) { return ((H - 1) * W + W + 1 + 3 + 3) & ~3; }
-
 int tc_tile_samples() { return 128; }
 
-int tc_tile_group(int W) { return W <= 64 ? TcShape<64, 1>::kSlots : TcShape<128, 1>::kSlots; }
-
-void launch_pack_tc(const float *w32, int n_fields, int W, int H, int64_t P, void *wimg, int64_t img_bytes,
-                    float *bias, int nb, cudaStream_t s)
+int tc_tile_group(int W, bool f8)
 {
-#define ROAM_CASE(WW, HH) \
-    if (W == WW && H == HH) { k_pack_tc<WW, HH><<<2048, 256, 0, s>>>(w32, n_fields, P, (uint8_t *)wimg, img_bytes, bias, nb); return; }
+    if (W <= 32) return f8 ? TcShape<32, 1, true>::kSlots : TcShape<32, 1, false>::kSlots;
+    if (W <= 64) return f8 ? TcShape<64, 1, true>::kSlots : TcShape<64, 1, false>::kSlots;
+    return f8 ? TcShape<128, 1, true>::kSlots : TcShape<128, 1, false>::kSlots;
+}
+
+void launch_pack_tc(const float *w32, int n_fields, int W, int H, int64_t P, void *wimg, int64_t img_bytes, bool f8,
+                    cudaStream_t s)
+{
+#define ROAM_CASE(WW, HH)                                                                                      \
+    if (W == WW && H == HH) {                                                                                  \
+        if (f8) {                                                                                              \
+            k_pack_tab<WW, HH, true><<<1024, 256, 0, s>>>(w32, n_fields, P, (uint8_t *)wimg, img_bytes);      \
+            k_pack_tc<WW, HH, true><<<2048, 256, 0, s>>>(w32, n_fields, P, (uint8_t *)wimg, img_bytes);       \
+        } else {                                                                                               \
+            if (TcShape<WW, HH, false>::kTab)                                                                  \
+                k_pack_tab<WW, HH, false><<<1024, 256, 0, s>>>(w32, n_fields, P, (uint8_t *)wimg, img_bytes); \
+            k_pack_tc<WW, HH, false><<<2048, 256, 0, s>>>(w32, n_fields, P, (uint8_t *)wimg, img_bytes);      \
+        }                                                                                                      \
+        return;                                                                                                \
+    }
     ROAM_TC_CASES
 #undef ROAM_CASE
 }
 
-void launch_mlp_tc(const MlpWeights &w, const SampleSrc &src, const BucketBufs &b, Counters *ctr, float4 *out,
-                   int n_sm, cudaStream_t s)
+void launch_mlp_tc(const MlpWeights &w, bool f8, const SampleSrc &src, const BucketBufs &b, Counters *ctr,
+                   float4 *out, int n_sm, cudaStream_t s)
 {
-#define ROAM_CASE(WW, HH) \
-    if (w.W == WW && w.H == HH) { launch_t<WW, HH>(w, src, b, ctr, out, n_sm, s); return; }
+#define ROAM_CASE(WW, HH)                                             \
+    if (w.W == WW && w.H == HH) {                                     \
+        if (f8) launch_t<WW, HH, true>(w, src, b, ctr, out, n_sm, s); \
+        else launch_t<WW, HH, false>(w, src, b, ctr, out, n_sm, s);   \
+        return;                                                       \
+    }
     ROAM_TC_CASES
 #undef ROAM_CASE
 }

@@ -113,13 +113,12 @@ struct roam_ctx {
     // weights
     bool has_weights = false;
     roam_mlp_desc md{};
-    int64_t P = 0, Pt = 0, img_bytes = 0;
-    int nb = 0;
-    bool tc_ok = false;
-    DBuf<float> w32, wt, wr, bias, adam_m, adam_v;
+    int64_t P = 0, Pt = 0, img_bytes = 0, img8_bytes = 0;
+    bool tc_ok = false, tc8_ok = false;
+    DBuf<float> w32, wt, wr, adam_m, adam_v;
     int64_t Pr = 0;
     bool adam_fresh = true;
-    DBuf<uint8_t> wimg;
+    DBuf<uint8_t> wimg, wimg8;
     // per-call workspace
     DBuf<float4> orig, dir, dir_lo, acc, sr, gsr;
     DBuf<float2> tw;
@@ -157,9 +156,9 @@ struct roam_ctx {
 namespace {
 
 const char *const kProfNames[] = {"march", "bucket", "mlp_f32_simt", "mlp_bf16_tcgen05", "composite",
-                                  "composite_bwd", "mlp_bwd", "adam"};
-constexpr int kProfKinds = 8;
-enum { P_MARCH, P_BUCKET, P_MLP_F32, P_MLP_BF16, P_COMPOSITE, P_COMPOSITE_BWD, P_MLP_BWD, P_ADAM };
+                                  "composite_bwd", "mlp_bwd", "adam", "mlp_fp8_tcgen05"};
+constexpr int kProfKinds = 9;
+enum { P_MARCH, P_BUCKET, P_MLP_F32, P_MLP_BF16, P_COMPOSITE, P_COMPOSITE_BWD, P_MLP_BWD, P_ADAM, P_MLP_FP8 };
 
 cudaEvent_t pool_event(roam_ctx *c)
 {
@@ -235,8 +234,8 @@ MlpWeights weights_of(const roam_ctx *c)
     w.Pr = c->Pr;
     w.wimg = c->wimg.p;
     w.img_bytes = c->img_bytes;
-    w.bias = c->bias.p;
-    w.nb = c->nb;
+    w.wimg8 = c->wimg8.p;
+    w.img8_bytes = c->img8_bytes;
     w.affine = c->affine.p;
     return w;
 }
@@ -257,9 +256,10 @@ roam_status check_opts(const roam_ctx *c, const roam_render_opts *o)
     if (!(o->t_stop >= 0.f && o->t_stop < 1.f)) return fail(ROAM_ERR_ARG, "t_stop must be in [0, 1)");
     for (int i = 0; i < 3; ++i)
         if (!finite(o->bg[i])) return fail(ROAM_ERR_ARG, "background must be finite");
-    if (o->precision != ROAM_F32 && o->precision != ROAM_BF16) return fail(ROAM_ERR_ARG, "unknown precision");
-    if (o->precision == ROAM_BF16 && !c->tc_ok)
-        return fail(ROAM_ERR_UNSUPPORTED, "BF16 tensor-core path not available for W=%d H=%d", c->md.width, c->md.n_hidden);
+    if (o->precision != ROAM_F32 && o->precision != ROAM_BF16 && o->precision != ROAM_FP8)
+        return fail(ROAM_ERR_ARG, "unknown precision");
+    if ((o->precision == ROAM_BF16 && !c->tc_ok) || (o->precision == ROAM_FP8 && !c->tc8_ok))
+        return fail(ROAM_ERR_UNSUPPORTED, "tensor-core path not available for W=%d H=%d", c->md.width, c->md.n_hidden);
     if (o->round_size < 0) return fail(ROAM_ERR_ARG, "round_size must be >= 0");
     if (o->use_graph != 0 && o->use_graph != 1) return fail(ROAM_ERR_ARG, "use_graph must be 0 or 1");
     return ROAM_OK;
@@ -383,15 +383,18 @@ BucketBufs bucket_of(roam_ctx *c)
     return b;
 }
 
-int tile_of(int precision) { return precision == ROAM_BF16 ? tc_tile_samples() : 128; }
-int group_of(const roam_ctx *c, int precision) { return precision == ROAM_BF16 ? tc_tile_group(c->md.width) : 1; }
+int tile_of(int precision) { return precision != ROAM_F32 ? tc_tile_samples() : 128; }
+int group_of(const roam_ctx *c, int precision)
+{
+    return precision != ROAM_F32 ? tc_tile_group(c->md.width, precision == ROAM_FP8) : 1;
+}
 
 roam_status run_mlp(roam_ctx *c, int precision, const SampleSrc &src, const BucketBufs &b, float4 *out,
                     cudaStream_t s)
 {
     const MlpWeights w = weights_of(c);
-    if (precision == ROAM_BF16) {
-        launch_mlp_tc(w, src, b, c->ctr, out, c->n_sm, s);
+    if (precision != ROAM_F32) {
+        launch_mlp_tc(w, precision == ROAM_FP8, src, b, c->ctr, out, c->n_sm, s);
         return launched("mlp_tc");
     }
     launch_mlp_simt(w, src, b, c->ctr, out, grid_blocks(c, 4), s);
@@ -447,7 +450,7 @@ roam_status run_rounds(roam_ctx *c, const uint32_t *rays, int64_t n_rays, const 
         src.delta = o->delta;
         src.accurate = mp.accurate;
         {
-            ProfScope ps(c, o->precision == ROAM_BF16 ? P_MLP_BF16 : P_MLP_F32, s);
+            ProfScope ps(c, o->precision == ROAM_BF16 ? P_MLP_BF16 : (o->precision == ROAM_FP8 ? P_MLP_FP8 : P_MLP_F32), s);
             ROAM_TRY(run_mlp(c, o->precision, src, b, c->sr.p, s));
         }
         {
@@ -570,7 +573,7 @@ roam_status roam_destroy(roam_ctx *c)
     release(c->bits); release(c->prefix); release(c->block_sums);
     release(c->brick_occ); release(c->brick_dist); release(c->brick_t0); release(c->brick_t1);
     release(c->labels); release(c->affine);
-    release(c->w32); release(c->wt); release(c->wr); release(c->gsr); release(c->bias); release(c->adam_m); release(c->adam_v); release(c->wimg);
+    release(c->w32); release(c->wt); release(c->wr); release(c->gsr); release(c->adam_m); release(c->adam_v); release(c->wimg); release(c->wimg8);
     release(c->orig); release(c->dir); release(c->dir_lo); release(c->acc); release(c->sr); release(c->tw);
     release(c->j_next); release(c->j_end); release(c->n_kept); release(c->live0); release(c->live1);
     release(c->cnt); release(c->recs); release(c->sorted); release(c->hist); release(c->offsets);
@@ -727,14 +730,19 @@ roam_status roam_load_weights(roam_ctx *c, const roam_mlp_desc *desc, const floa
     ROAM_TRY(launched("pack rows"));
     c->adam_fresh = true;
     c->train_rays = 0;
-    c->tc_ok = tc_supported(W, H);
+    c->tc_ok = tc_supported(W, H, false);
     if (c->tc_ok) {
-        c->img_bytes = tc_image_bytes(W, H);
-        c->nb = tc_bias_count(W, H);
+        c->img_bytes = tc_image_bytes(W, H, false);
         ROAM_TRY(ensure(c->wimg, (size_t)(c->img_bytes * c->n_fields)));
-        ROAM_TRY(ensure(c->bias, (size_t)c->nb * c->n_fields));
-        launch_pack_tc(c->w32.p, c->n_fields, W, H, P, c->wimg.p, c->img_bytes, c->bias.p, c->nb, 0);
+        launch_pack_tc(c->w32.p, c->n_fields, W, H, P, c->wimg.p, c->img_bytes, false, 0);
         ROAM_TRY(launched("pack tc"));
+    }
+    c->tc8_ok = tc_supported(W, H, true);
+    if (c->tc8_ok) {
+        c->img8_bytes = tc_image_bytes(W, H, true);
+        ROAM_TRY(ensure(c->wimg8, (size_t)(c->img8_bytes * c->n_fields)));
+        launch_pack_tc(c->w32.p, c->n_fields, W, H, P, c->wimg8.p, c->img8_bytes, true, 0);
+        ROAM_TRY(launched("pack tc fp8"));
     }
     ROAM_CUDA(cudaDeviceSynchronize());
     c->has_weights = true;
@@ -907,8 +915,10 @@ roam_status roam_mlp_eval(roam_ctx *c, const float *p, const float *d, const uin
     if (n < 0 || n > 0x7fffffff) return fail(ROAM_ERR_ARG, "bad sample count");
     if (n == 0) return ROAM_OK;
     if (!p || !d || !field || !out) return fail(ROAM_ERR_ARG, "null pointer");
-    if (precision != ROAM_F32 && precision != ROAM_BF16) return fail(ROAM_ERR_ARG, "unknown precision");
-    if (precision == ROAM_BF16 && !c->tc_ok) return fail(ROAM_ERR_UNSUPPORTED, "BF16 path not available");
+    if (precision != ROAM_F32 && precision != ROAM_BF16 && precision != ROAM_FP8)
+        return fail(ROAM_ERR_ARG, "unknown precision");
+    if ((precision == ROAM_BF16 && !c->tc_ok) || (precision == ROAM_FP8 && !c->tc8_ok))
+        return fail(ROAM_ERR_UNSUPPORTED, "tensor-core path not available");
     cudaStream_t s = (cudaStream_t)stream;
     ROAM_TRY(ensure(c->sorted, (size_t)n));
     ROAM_TRY(ensure(c->tiles, tile_capacity((size_t)n, c->n_fields)));
@@ -949,6 +959,7 @@ roam_status roam_train_forward(roam_ctx *c, const roam_camera *cams, int n_views
     ROAM_TRY(set_dev(c));
     ROAM_TRY(check_ready(c));
     ROAM_TRY(check_opts(c, opts));
+    if (opts->precision == ROAM_FP8) return fail(ROAM_ERR_UNSUPPORTED, "training runs in FP32 or BF16");
     if (!rays || !rgb) return fail(ROAM_ERR_ARG, "null rays or rgb");
     if (n_rays < 1 || n_rays > 0x7fffffff) return fail(ROAM_ERR_ARG, "bad ray count");
     if (!mlp_bwd_supported(c->md.width, c->md.n_hidden))
@@ -1058,7 +1069,8 @@ roam_status roam_adam_step(roam_ctx *c, const float *grad, const roam_adam_cfg *
         const int W = c->md.width, H = c->md.n_hidden;
         launch_pack_simt(c->w32.p, c->n_fields, W, H, c->P, c->wt.p, c->Pt, s);
         launch_pack_rows(c->w32.p, c->n_fields, W, H, c->P, c->wr.p, c->Pr, s);
-        if (c->tc_ok) launch_pack_tc(c->w32.p, c->n_fields, W, H, c->P, c->wimg.p, c->img_bytes, c->bias.p, c->nb, s);
+        if (c->tc_ok) launch_pack_tc(c->w32.p, c->n_fields, W, H, c->P, c->wimg.p, c->img_bytes, false, s);
+        if (c->tc8_ok) launch_pack_tc(c->w32.p, c->n_fields, W, H, c->P, c->wimg8.p, c->img8_bytes, true, s);
     }
     c->last = s;
     return launched("adam");

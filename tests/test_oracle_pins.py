@@ -339,6 +339,104 @@ def test_mlp_affine_maps_field_box():
 
 
 # ----------------------------------------------------------------------------
+# the FP8 E4M3 reading of the matrix layers (a precision choice of the
+# library; the paper fixes no arithmetic format)
+# ----------------------------------------------------------------------------
+
+def test_e4m3_hand_values():
+    cases = [(1.0625, 1.0), (1.1875, 1.25), (2.0 ** -10, 0.0), (3 * 2.0 ** -11, 2.0 ** -9), (470.0, 448.0),
+             (448.0, 448.0), (-0.3, -0.3125), (0.0, 0.0), (2.0 ** -6, 2.0 ** -6), (1.96875, 2.0), (-1e9, -448.0)]
+    for x, want in cases:
+        assert float(O.e4m3(x)) == want, (x, want)
+
+
+def test_e4m3_rounding_matches_torch_float8():
+    """Every finite E4M3 value, every midpoint between neighbours (ties) and
+    random values over the whole range against torch's own conversion."""
+    torch = pytest.importorskip("torch")
+    if not hasattr(torch, "float8_e4m3fn"):
+        pytest.skip("torch without float8")
+    codes = torch.arange(0, 127, dtype=torch.uint8).view(torch.float8_e4m3fn).to(torch.float64).numpy()
+    mids = 0.5 * (codes[1:] + codes[:-1])
+    rng = np.random.default_rng(8)
+    logu = np.exp2(rng.uniform(-12, 8.8, 20000)) * rng.choice([-1.0, 1.0], 20000)
+    x = np.concatenate([codes, -codes, mids, -mids, logu, rng.uniform(-1, 1, 5000)])
+    x = x[np.abs(x) < 464].astype(np.float32)
+    ref = torch.from_numpy(x).to(torch.float8_e4m3fn).to(torch.float64).numpy()
+    got = O.e4m3(x.astype(np.float64))
+    assert np.array_equal(got, ref)
+
+
+def _np_encode(v, L):
+    out = [v]
+    for k in range(L):
+        out += [np.sin(2.0 ** k * math.pi * v), np.cos(2.0 ** k * math.pi * v)]
+    return np.concatenate(out)
+
+
+def _np_mlp_fp8(w, W, H, sig, aff, p, d, quant):
+    """The FP8 reading written independently: NumPy matrices, torch's float8
+    conversion as the rounding."""
+    torch = pytest.importorskip("torch")
+    q8 = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).to(torch.float8_e4m3fn) \
+        .to(torch.float64).numpy()
+    offs, _ = _offsets(W, H)
+
+    def dense(i, x, quantised=True):
+        wo, bo, n_out, n_in = offs[i]
+        Wm = w[wo:wo + n_out * n_in].reshape(n_out, n_in)
+        b = w[bo:bo + n_out].astype(np.float64)
+        if not (quant and quantised):
+            return b + Wm.astype(np.float64) @ x
+        amax = np.abs(Wm).max(axis=1)
+        s = np.where(amax > 0, amax / np.float32(448.0), np.float32(1.0)).astype(np.float32)
+        Wq = q8((Wm / s[:, None]).astype(np.float32))
+        return b + s.astype(np.float64) * (Wq @ q8(x.astype(np.float32)))
+
+    xl = aff[:3].astype(np.float64) * p + aff[3:].astype(np.float64)
+    h = np.maximum(dense(0, _np_encode(xl, 10)), 0)
+    for k in range(1, H):
+        h = np.maximum(dense(k, h), 0)
+    z = dense(H, h)
+    sigma = O.f32(sig) * np.log1p(np.exp(z[0]))
+    g = np.maximum(dense(H + 1, np.concatenate([z[1:], _np_encode(d, 4)])), 0)
+    rgb = 1 / (1 + np.exp(-dense(H + 2, g, quantised=False)))
+    return np.concatenate([[sigma], rgb])
+
+
+@pytest.mark.parametrize("W,H", [(16, 2), (32, 3)])
+def test_mlp_fp8_reading_matches_independent_chain(W, H):
+    rng = np.random.default_rng(W + H)
+    w = F.xavier_weights(9, 2, 1, W, H, bias_scale=0.3)[0]
+    aff = np.array([1.5, 0.8, 1.1, -0.2, 0.1, 0.05], dtype=np.float32)
+    for _ in range(20):
+        p = rng.uniform(-0.6, 0.6, 3)
+        d = rng.normal(size=3)
+        d /= np.linalg.norm(d)
+        got = O.mlp(w, W, H, 2.0, aff, p, d, quant=1)
+        want = _np_mlp_fp8(w, W, H, 2.0, aff, p, d, True)
+        assert np.abs(got - want).max() <= 1e-9
+        full = O.mlp(w, W, H, 2.0, aff, p, d)
+        assert np.abs(full - _np_mlp_fp8(w, W, H, 2.0, aff, p, d, False)).max() <= 1e-9
+        # the rounding is really applied, and stays within a few E4M3 steps
+        assert 1e-6 < np.abs(got[1:] - full[1:]).max() < 0.1
+
+
+def test_mlp_fp8_biases_are_not_rounded():
+    """Zero matrices: only the (unrounded) biases reach the outputs, so the
+    FP8 reading equals the FP64 one exactly."""
+    W, H = 16, 3
+    offs, P = _offsets(W, H)
+    rng = np.random.default_rng(3)
+    w = np.zeros(P, dtype=np.float32)
+    for (wo, bo, n_out, _) in offs:
+        w[bo:bo + n_out] = rng.uniform(-1, 1, n_out)
+    aff = np.array([1, 1, 1, 0, 0, 0], dtype=np.float32)
+    p, d = rng.uniform(-1, 1, 3), np.array([0.0, 0.6, 0.8])
+    assert np.array_equal(O.mlp(w, W, H, 2.5, aff, p, d, quant=1), O.mlp(w, W, H, 2.5, aff, p, d))
+
+
+# ----------------------------------------------------------------------------
 # compositing (Eq. 4, Eq. 5) with early termination
 # ----------------------------------------------------------------------------
 
