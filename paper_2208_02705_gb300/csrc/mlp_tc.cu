@@ -316,6 +316,15 @@ struct SampleIn {
     float px, py, pz, dx, dy, dz;
 };
 
+// The next tile's sample, gathered in stages spread over this tile's layers
+// (sorted index -> record and ray -> ray origin and direction), so that no
+// stage waits on the previous one's load.
+struct Pending {
+    bool on;
+    uint32_t idx, rec, ray;
+    float4 o, d;
+};
+
 __device__ __forceinline__ SampleIn fetch_sample(const SampleSrc &src, const BucketBufs &b, const Tile &tl, int row)
 {
     SampleIn r{0u, 0.f, 0.f, 0.f, 0.f, 0.f, 1.f};
@@ -334,6 +343,49 @@ __device__ __forceinline__ SampleIn fetch_sample(const SampleSrc &src, const Buc
         r.px = src.p[3 * (int64_t)r.idx]; r.py = src.p[3 * (int64_t)r.idx + 1]; r.pz = src.p[3 * (int64_t)r.idx + 2];
         r.dx = src.d[3 * (int64_t)r.idx]; r.dy = src.d[3 * (int64_t)r.idx + 1]; r.dz = src.d[3 * (int64_t)r.idx + 2];
     }
+    return r;
+}
+
+__device__ __forceinline__ void stage_index(Pending &q, const BucketBufs &b, const Tile &tl, int row, bool more)
+{
+    q.on = more && (uint32_t)row < tl.count;
+    if (q.on) q.idx = b.sorted[tl.start + row];
+}
+
+__device__ __forceinline__ void stage_record(Pending &q, const SampleSrc &src)
+{
+    if (!q.on || src.mode != 0) return;
+    const uint32_t col = q.idx >> 5;
+    const uint32_t i = (col / (uint32_t)src.R) * 32u + (q.idx & 31u);
+    q.rec = src.recs[q.idx];
+    q.ray = src.live ? src.live[i] : i;
+}
+
+__device__ __forceinline__ void stage_ray(Pending &q, const SampleSrc &src)
+{
+    if (!q.on) return;
+    if (src.mode == 0) {
+        q.o = src.st.orig[q.ray];
+        q.d = src.st.dir[q.ray];
+    } else {
+        const int64_t k = 3 * (int64_t)q.idx;
+        q.o = make_float4(src.p[k], src.p[k + 1], src.p[k + 2], 0.f);
+        q.d = make_float4(src.d[k], src.d[k + 1], src.d[k + 2], 0.f);
+    }
+}
+
+__device__ __forceinline__ SampleIn stage_finish(const Pending &q, const SampleSrc &src)
+{
+    SampleIn r{0u, 0.f, 0.f, 0.f, 0.f, 0.f, 1.f};
+    if (!q.on) return r;
+    r.idx = q.idx;
+    if (src.mode == 0) {
+        const float tt = ((float)(q.rec & 0xffffu) + 0.5f) * src.delta;
+        r.px = fmaf(tt, q.d.x, q.o.x); r.py = fmaf(tt, q.d.y, q.o.y); r.pz = fmaf(tt, q.d.z, q.o.z);
+    } else {
+        r.px = q.o.x; r.py = q.o.y; r.pz = q.o.z;
+    }
+    r.dx = q.d.x; r.dy = q.d.y; r.dz = q.d.z;
     return r;
 }
 
@@ -368,7 +420,9 @@ __global__ void __launch_bounds__(TcShape<W, H, F8>::kSlots * 128, 1)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int slot = warp >> 2, wq = warp & 3;
     const int row = wq * 32 + lane;                           // TMEM lane == tile row
-    const bool issuer = (threadIdx.x & 127) == 0;
+    // the slot's issuing thread sits in the slot's warp with index = slot mod 4,
+    // so the slots' issuers run on different SM sub-partitions
+    const bool issuer = wq == (slot & 3) && lane == 0;
     volatile int *abortp = &abort_flag;
     uint32_t *status = &ctr->status;
 
@@ -406,6 +460,7 @@ __global__ void __launch_bounds__(TcShape<W, H, F8>::kSlots * 128, 1)
     bool aborted = false;
     Tile tl{0u, 0u, 0u, 0u};
     SampleIn nxt{0u, 0.f, 0.f, 0.f, 0.f, 0.f, 1.f};
+    Pending pend{};
     uint32_t g = g0;
     if (g < g1) {
         tl = b.tiles[g * kSlots + slot];
@@ -470,7 +525,7 @@ __global__ void __launch_bounds__(TcShape<W, H, F8>::kSlots * 128, 1)
             }
         }
         // the next tile's gathers overlap this tile's layers
-        if (g + 1 < g1) nxt = fetch_sample(src, b, tl, row);
+        stage_index(pend, b, tl, row, g + 1 < g1);
         float sigma = 0.f;
 #pragma unroll 1
         for (int l = 0; l < kLayers; ++l) {
@@ -618,7 +673,10 @@ __global__ void __launch_bounds__(TcShape<W, H, F8>::kSlots * 128, 1)
                 }
                 if (valid) out[sm.idx] = make_float4(sigma, sigmoid_f(acc.x), sigmoid_f(acc.y), sigmoid_f(acc.z));
             }
+            if (l == 0) stage_record(pend, src);
+            if (l == 1) stage_ray(pend, src);
         }
+        if (!aborted) nxt = stage_finish(pend, src);
     }
     // drain before TMEM is freed and the CTA exits: a commit whose wait gave
     // up, and an image load nobody waited for
