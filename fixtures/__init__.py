@@ -36,7 +36,7 @@ from typing import List, Optional, Tuple
 
 import numpy as np
 
-ROLE_SCENE, ROLE_TEACHER, ROLE_STUDENT, ROLE_CAMERAS, ROLE_RAYS, ROLE_NOISE = range(6)
+ROLE_SCENE, ROLE_TEACHER, ROLE_STUDENT, ROLE_CAMERAS, ROLE_RAYS, ROLE_NOISE, ROLE_WIDTHS = range(7)
 
 PE_POS_DIM = 63   # 3 + 2*3*10
 PE_DIR_DIM = 27   # 3 + 2*3*4
@@ -346,6 +346,25 @@ def xavier_weights(workload: int, role: int, n_fields: int, W: int, H: int,
     return out
 
 
+def mixed_widths(workload: int, n_fields: int, choices=(32, 64, 128)) -> np.ndarray:
+    """int32 [F]: an MLP width per field, drawn uniformly from `choices`."""
+    rng = rng_for(workload, ROLE_WIDTHS)
+    return np.asarray(choices, dtype=np.int32)[rng.integers(0, len(choices), n_fields)]
+
+
+def xavier_weights_mixed(workload: int, role: int, widths: np.ndarray, H: int, bias_scale: float = 0.0) -> np.ndarray:
+    """float32 1-D: the fields' parameters one after another, field f in the
+    layout of width widths[f] (Xavier-uniform matrices as xavier_weights)."""
+    rng = rng_for(workload, role)
+    parts = []
+    for W in widths:
+        for (o, i) in layer_shapes(int(W), H):
+            a = math.sqrt(6.0 / (o + i))
+            parts.append(rng.uniform(-a, a, size=o * i))
+            parts.append(rng.uniform(-bias_scale, bias_scale, size=o) if bias_scale else np.zeros(o))
+    return np.concatenate(parts).astype(np.float32)
+
+
 def density_scale(delta: float, median_alpha: float = 0.3) -> float:
     """Density multiplier so that a sample with density logit 0 (the median
     for symmetric random weights: softplus(0) = ln 2) has opacity
@@ -448,6 +467,7 @@ class Workload:
     n_max: int
     cams: List[Camera]
     t_stop: float = 1e-4
+    widths: Optional[np.ndarray] = None     # per-field MLP widths (W == 0, weights 1-D) when mixed
 
 
 def room32(W: int = 32, H: int = 2) -> Workload:
@@ -491,3 +511,32 @@ def floor512(n_fields: int = 4096, W: int = 128, H: int = 4, role: int = ROLE_TE
     cams = make_cameras(scene, 5, [(EQUIRECT, 2048, 1024, 0.0)])
     return Workload(f"floor512_kd{n_fields}_w{W}h{H}", scene, part, field_affine(scene, part), W, H, w,
                     density_scale(delta), delta, 192, cams)
+
+
+def multiview_specs():
+    """32 views: 24 equirectangular panoramas in four sizes from 512x256 to
+    2048x1024, and 8 perspective 1280x720 views at 90 degrees horizontal FOV,
+    interleaved."""
+    eq = [(512, 256), (1024, 512), (1536, 768), (2048, 1024)]
+    specs = []
+    for i in range(32):
+        if i % 4 == 3:
+            specs.append((PERSPECTIVE, 1280, 720, math.pi / 2))
+        else:
+            w, h = eq[(i - i // 4) % 4]
+            specs.append((EQUIRECT, w, h, 0.0))
+    return specs
+
+
+def floor384(n_fields: int = 2048, H: int = 3, role: int = ROLE_TEACHER, specs=None) -> Workload:
+    """384^3 twelve-room floor (4 x 3 rooms), 2048 kd fields whose MLP widths
+    are drawn from 32/64/128 per field, H=3, the 32 mixed views of
+    multiview_specs, <=128 samples per ray."""
+    scene = floor_scene(4, 384, 4, 3, 0.03, height_frac=0.28, boxes_per_room=4)
+    part = kd_partition(scene, n_fields)
+    delta = scene.vox / 4
+    widths = mixed_widths(4, part.n_fields)
+    w = xavier_weights_mixed(4, role, widths, H)
+    cams = make_cameras(scene, 4, specs if specs is not None else multiview_specs())
+    return Workload(f"floor384_kd{n_fields}_mixedw_h{H}", scene, part, field_affine(scene, part), 0, H, w,
+                    density_scale(delta), delta, 128, cams, widths=widths)

@@ -168,8 +168,22 @@ roam_status roam_load_fields(roam_ctx *ctx, int n_fields, const uint16_t *field_
 roam_status roam_load_weights(roam_ctx *ctx, const roam_mlp_desc *desc, const float *weights,
                               int on_device);
 
-/* Copies the FP32 master weights (same layout as roam_load_weights) to `out`
- * (device memory iff on_device).  Synchronises. */
+/* Loads per-field MLPs of mixed widths (each field 32, 64 or 128 wide, all
+ * with desc->n_hidden hidden layers; desc->width is ignored).  field_width:
+ * host int32[n_fields]; weights: host or device (on_device) float32, field
+ * after field in the caller's field order, each field in the layout of
+ * roam_load_weights for its own width.
+ * Internally the fields are grouped by width and each group runs its own
+ * kernel over its own tiles; field ids seen through the ABI (roam_march
+ * records, roam_mlp_eval keys, roam_get_weights order) stay the caller's.
+ * Rendering and roam_mlp_eval accept every precision; training
+ * (roam_train_forward, roam_adam_step) needs a single width.  Synchronous. */
+roam_status roam_load_weights_mixed(roam_ctx *ctx, const roam_mlp_desc *desc, const int32_t *field_width,
+                                    const float *weights, int on_device);
+
+/* Copies the FP32 master weights (same layout as roam_load_weights, or as
+ * roam_load_weights_mixed when the widths are mixed) to `out` (device memory
+ * iff on_device).  Synchronises. */
 roam_status roam_get_weights(roam_ctx *ctx, float *out, int on_device);
 
 /* ---- rendering (Sec. "Real-time Rendering Speedup", Eq. 2-5) ---------- */
@@ -277,7 +291,8 @@ roam_status roam_train_backward(roam_ctx *ctx, const float *dl_drgb, float *grad
  * sum (rgb - target)^2 / norm and dl_drgb (device float[n_rays][3])
  * 2 (rgb - target) / norm.  norm = 3 n for the mean over a batch of n rays;
  * with data parallelism, 3 n over the global batch so that summed per-rank
- * gradients equal the global one.  Asynchronous. */
+ * gradients equal the global one.  The sum runs in a fixed order: the same
+ * inputs give the same bits.  Asynchronous. */
 roam_status roam_l2_loss(roam_ctx *ctx, const float *rgb, const float *target, int64_t n_rays, float norm,
                          float *dl_drgb, float *loss, void *stream);
 

@@ -65,7 +65,7 @@ def lib():
         L.orc_e4m3.argtypes = [D]; L.orc_e4m3.restype = D
         L.orc_composite.argtypes = [I, f64p, f64p, f64p, D, D, f64p, f64p, f64p]
         L.orc_composite.restype = I
-        L.orc_render.argtypes = [i32p, f64p, D, i32p, f32p, f32p, I, I, I, D, I, f64p, I, u32p, I64,
+        L.orc_render.argtypes = [i32p, f64p, D, i32p, f32p, f32p, I, I, I, D, I, i32p, I, f64p, I, u32p, I64,
                                  D, I, D, f64p, f64p, f64p, f64p, i32p, i32p, i32p, f64p]
         L.orc_render.restype = I
         L.orc_march_rays.argtypes = [i32p, f64p, D, i32p, f64p, I, u32p, I64, D, I, i32p, i32p, i32p, i32p]
@@ -203,13 +203,16 @@ def march_rays(grid: Grid, cams16, rays: Optional[np.ndarray], delta: float, n_m
 
 def render(grid: Grid, weights, affine, W: int, H: int, sigma_scale: float, cams16,
            rays: Optional[np.ndarray], delta: float, n_max: int, t_stop: float = 1e-4,
-           bg=(0.0, 0.0, 0.0), act: int = 0, quant: int = 0):
+           bg=(0.0, 0.0, 0.0), act: int = 0, quant: int = 0, widths=None):
     """Renders (view, pixel) rays, or every pixel of every view (rays=None).
     Returns a dict of per-ray arrays.  quant=1 takes the FP8 E4M3 reading of
-    the matrix layers."""
+    the matrix layers.  widths (int per field) gives every field its own MLP
+    width; weights is then the fields' parameters one after another."""
     cams = cams_f32(cams16)
     w = np.ascontiguousarray(weights, dtype=np.float32)
     aff = np.ascontiguousarray(affine, dtype=np.float32)
+    wd = np.ascontiguousarray(widths, dtype=np.int32) if widths is not None else None
+    n_fields = int(aff.shape[0])
     n_rays = int(rays.shape[0]) if rays is not None else int(sum(c[1] * c[2] for c in cams))
     r = np.ascontiguousarray(rays, dtype=np.uint32) if rays is not None else None
     bgv = np.array([f32(b) for b in bg], dtype=np.float64)
@@ -217,7 +220,8 @@ def render(grid: Grid, weights, affine, W: int, H: int, sigma_scale: float, cams
                n_kept=np.zeros(n_rays, np.int32), n_used=np.zeros(n_rays, np.int32),
                ties=np.zeros(n_rays, np.int32), margin=np.zeros(n_rays))
     rc = lib().orc_render(*grid.args(), _p(w, ctypes.c_float), _p(aff, ctypes.c_float), W, H, act,
-                          f32(sigma_scale), int(quant), _p(cams, ctypes.c_double), int(cams.shape[0]),
+                          f32(sigma_scale), int(quant), _p(wd, ctypes.c_int32), n_fields,
+                          _p(cams, ctypes.c_double), int(cams.shape[0]),
                           _p(r, ctypes.c_uint32), n_rays, f32(delta), n_max, f32(t_stop),
                           _p(bgv, ctypes.c_double), _p(out["rgb"], ctypes.c_double),
                           _p(out["depth"], ctypes.c_double), _p(out["opacity"], ctypes.c_double),

@@ -520,7 +520,9 @@ typedef struct {
     orc_grid g;
     orc_arch A;
     int64_t P;
-    const float *weights;   /* [F][P] */
+    const float *weights;   /* [F][P], or field after field at woff[f] when widths vary */
+    const int32_t *widths;  /* NULL: every field has width A.W */
+    int64_t *woff;          /* start of field f's weights (widths != NULL) */
     const float *affine;    /* [F][6] */
     const double *cams;     /* [n_views][16] */
     int n_views;
@@ -560,7 +562,9 @@ static int render_ray(const orc_scene *S, const double *o, const double *d, doub
         double p[3] = {o[0] + t * d[0], o[1] + t * d[1], o[2] + t * d[2]};
         int f = fields[k];
         orc_cache *c = caches ? &caches[k] : &local;
-        mlp_forward(S->weights + (int64_t)f * S->P, &S->A, (const double[6]){
+        orc_arch A = S->A;
+        if (S->widths) A.W = S->widths[f];
+        mlp_forward(S->weights + (S->widths ? S->woff[f] : (int64_t)f * S->P), &A, (const double[6]){
                         S->affine[6 * f + 0], S->affine[6 * f + 1], S->affine[6 * f + 2],
                         S->affine[6 * f + 3], S->affine[6 * f + 4], S->affine[6 * f + 5]},
                     p, d, c);
@@ -584,6 +588,8 @@ static int setup_scene(orc_scene *S, const int32_t *dims, const double *origin, 
     S->A = (orc_arch){W, H, act, sigma_scale, quant};
     S->P = orc_param_count(W, H);
     S->weights = weights;
+    S->widths = NULL;
+    S->woff = NULL;
     S->affine = affine;
     S->cams = cams;
     S->n_views = n_views;
@@ -597,17 +603,33 @@ static int setup_scene(orc_scene *S, const int32_t *dims, const double *origin, 
 /* Renders rays (view, pixel) pairs, or every pixel of every view in order
  * when rays == NULL.  Per ray: rgb[3], depth, opacity, number of kept
  * samples, number composited before termination, near-tie count of the
- * march, termination margin.  Returns 0, or -1 on bad sizes. */
+ * march, termination margin.  widths (NULL: every field has width W) gives
+ * each of the n_fields fields its own width, the weights then lying field
+ * after field.  Returns 0, or -1 on bad sizes. */
 int orc_render(const int32_t *dims, const double *origin, double vox, const int32_t *label,
                const float *weights, const float *affine, int W, int H, int act, double sigma_scale,
-               int quant, const double *cams, int n_views, const uint32_t *rays, int64_t n_rays,
-               double delta, int n_max, double t_stop, const double *bg, double *rgb, double *depth,
-               double *opacity, int32_t *n_kept, int32_t *n_used, int32_t *ties, double *margin)
+               int quant, const int32_t *widths, int n_fields, const double *cams, int n_views,
+               const uint32_t *rays, int64_t n_rays, double delta, int n_max, double t_stop,
+               const double *bg, double *rgb, double *depth, double *opacity, int32_t *n_kept,
+               int32_t *n_used, int32_t *ties, double *margin)
 {
     orc_scene S;
     if (setup_scene(&S, dims, origin, vox, label, weights, affine, W, H, act, sigma_scale, quant, cams,
                     n_views, delta, n_max, t_stop, bg))
         return -1;
+    int64_t *woff = NULL;
+    if (widths) {
+        woff = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n_fields > 0 ? n_fields : 1));
+        if (!woff) return -1;
+        int64_t o = 0;
+        for (int f = 0; f < n_fields; ++f) {
+            if (widths[f] < 1 || widths[f] > 256) { free(woff); return -1; }
+            woff[f] = o;
+            o += orc_param_count(widths[f], H);
+        }
+        S.widths = widths;
+        S.woff = woff;
+    }
     int64_t starts[257];
     if (n_views > 256) return -1;
     starts[0] = 0;
@@ -627,6 +649,7 @@ int orc_render(const int32_t *dims, const double *origin, double vox, const int3
         if (ties) ties[r] = nt;
         if (margin) margin[r] = mg;
     }
+    free(woff);
     return 0;
 }
 

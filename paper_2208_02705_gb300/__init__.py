@@ -26,7 +26,7 @@ STATUS = {0: "ROAM_OK", -1: "ROAM_ERR_ARG", -2: "ROAM_ERR_OOM", -3: "ROAM_ERR_CU
 
 # every entry point declared in include/roam.h
 ENTRY_POINTS = ("roam_create", "roam_destroy", "roam_last_error", "roam_check", "roam_load_grid",
-                "roam_load_fields", "roam_load_weights", "roam_get_weights", "roam_render", "roam_get_stats",
+                "roam_load_fields", "roam_load_weights", "roam_load_weights_mixed", "roam_get_weights", "roam_render", "roam_get_stats",
                 "roam_march", "roam_bucket", "roam_mlp_eval", "roam_composite", "roam_train_forward",
                 "roam_train_backward", "roam_adam_step", "roam_profile", "roam_profile_read",
                 "roam_bucket_static", "roam_l2_loss")
@@ -93,6 +93,7 @@ def load_library(path: str = LIB_PATH):
     L.roam_load_grid.argtypes = [vp, P(roam_grid_desc), vp, i32]
     L.roam_load_fields.argtypes = [vp, i32, vp, i64, vp, i32]
     L.roam_load_weights.argtypes = [vp, P(roam_mlp_desc), vp, i32]
+    L.roam_load_weights_mixed.argtypes = [vp, P(roam_mlp_desc), vp, vp, i32]
     L.roam_get_weights.argtypes = [vp, vp, i32]
     L.roam_render.argtypes = [vp, P(roam_camera), i32, P(roam_render_opts), vp, vp, vp, i32, vp]
     L.roam_get_stats.argtypes = [vp, P(roam_stats)]
@@ -228,18 +229,37 @@ class Roam:
         _check(self.L.roam_load_weights(self.h, ctypes.byref(d), _ptr(weights), int(on_dev)))
         self.W, self.H = W, H
         self.P = int(weights.shape[-1])
+        self.n_params = self.P * self.n_fields
+
+    def load_weights_mixed(self, weights, widths, H: int, sigma_scale: float, act: int = ROAM_SOFTPLUS):
+        """weights: the fields' parameters one after another (1-D), field f in
+        the layout of width widths[f]."""
+        d = roam_mlp_desc()
+        d.width, d.n_hidden, d.sigma_scale, d.density_act = 0, int(H), float(sigma_scale), int(act)
+        wd = np.ascontiguousarray(widths, dtype=np.int32)
+        on_dev = not isinstance(weights, np.ndarray)
+        if not on_dev:
+            weights = np.ascontiguousarray(weights, dtype=np.float32).reshape(-1)
+        _check(self.L.roam_load_weights_mixed(self.h, ctypes.byref(d), _ptr(wd), _ptr(weights), int(on_dev)))
+        self.W, self.H = 0, H
+        self.P = None
+        self.n_params = int(weights.numel() if on_dev else weights.size)
 
     def get_weights(self):
+        """FP32 masters: [n_fields, P] for one width, 1-D (field after field) when mixed."""
         import torch
-        out = torch.empty((self.n_fields, self.P), dtype=torch.float32, device=self._dev())
+        out = torch.empty(self.n_params, dtype=torch.float32, device=self._dev())
         _check(self.L.roam_get_weights(self.h, _ptr(out), 1))
-        return out
+        return out.view(self.n_fields, self.P) if self.P else out
 
     def load_workload(self, wl):
         """Loads grid, fields and weights of a fixtures.Workload."""
         self.load_grid(wl.scene.bits, wl.scene.dims, wl.scene.origin, wl.scene.vox)
         self.load_fields(wl.part.field_of_rank, wl.affine)
-        self.load_weights(wl.weights, wl.W, wl.H, wl.sigma_scale)
+        if getattr(wl, "widths", None) is not None:
+            self.load_weights_mixed(wl.weights, wl.widths, wl.H, wl.sigma_scale)
+        else:
+            self.load_weights(wl.weights, wl.W, wl.H, wl.sigma_scale)
 
     # ---- rendering ----
     def render(self, cams, opts: roam_render_opts, rgb=None, depth=None, opacity=None, stream=None):

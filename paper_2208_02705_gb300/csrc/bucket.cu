@@ -71,7 +71,7 @@ __device__ __forceinline__ uint32_t ntiles_of(uint32_t h, int tile, int group)
 // `group` (trailing tiles empty) so that groups of tiles never mix fields;
 // resets hist for the next use.
 __global__ void __launch_bounds__(1024) k_scan(uint32_t *hist, int n_fields, int tile, int group, uint32_t *offsets,
-                                               uint32_t *cursor, Tile *tiles, Counters *ctr)
+                                               uint32_t *cursor, Tile *tiles, Counters *ctr, ClassBounds cb)
 {
     __shared__ uint32_t warp_a[32], warp_b[32];
     extern __shared__ uint32_t tile_off[];   // [n_fields + 1]
@@ -128,6 +128,9 @@ __global__ void __launch_bounds__(1024) k_scan(uint32_t *hist, int n_fields, int
         offsets[n_fields] = total;
         tile_off[n_fields] = total_tiles;
     }
+    __syncthreads();
+    if (threadIdx.x == 0)
+        for (int c = 0; c < 4; ++c) ctr->class_tiles[c] = tile_off[min(max(cb.first[c], 0), n_fields)];
     // field hit counts (warp reduce then atomics)
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) hit += __shfl_down_sync(kFull, hit, o);
@@ -203,21 +206,21 @@ __global__ void __launch_bounds__(512) k_scatter(const uint32_t *cnt, const uint
 
 void launch_bucket(const uint32_t *cnt, const uint32_t *recs, const uint32_t *live_count, uint32_t n_fixed,
                    int R, int group, const uint16_t *keys16, int n_fields, int tile,
-                   const BucketBufs &b, Counters *ctr, int grid, cudaStream_t s)
+                   const BucketBufs &b, Counters *ctr, int grid, cudaStream_t s, ClassBounds cb)
 {
     const size_t sh = (size_t)n_fields * sizeof(uint32_t);
     k_hist<<<grid, 512, sh, s>>>(cnt, recs, live_count, n_fixed, R, keys16, n_fields, b.hist, ctr);
     k_scan<<<1, 1024, (size_t)(n_fields + 1) * sizeof(uint32_t), s>>>(b.hist, n_fields, tile, group < 1 ? 1 : group,
-                                                                       b.offsets, b.cursor, b.tiles, ctr);
+                                                                       b.offsets, b.cursor, b.tiles, ctr, cb);
     k_scatter<<<grid, 512, 0, s>>>(cnt, recs, live_count, n_fixed, R, keys16, n_fields, b.cursor, b.sorted);
 }
 
 void launch_bucket_ready(const uint32_t *cnt, const uint32_t *recs, const uint32_t *live_count, uint32_t n_fixed,
                          int R, int group, int n_fields, int tile, const BucketBufs &b, Counters *ctr, int grid,
-                         cudaStream_t s)
+                         cudaStream_t s, ClassBounds cb)
 {
     k_scan<<<1, 1024, (size_t)(n_fields + 1) * sizeof(uint32_t), s>>>(b.hist, n_fields, tile, group < 1 ? 1 : group,
-                                                                       b.offsets, b.cursor, b.tiles, ctr);
+                                                                       b.offsets, b.cursor, b.tiles, ctr, cb);
     k_scatter<<<grid, 512, 0, s>>>(cnt, recs, live_count, n_fixed, R, nullptr, n_fields, b.cursor, b.sorted);
 }
 

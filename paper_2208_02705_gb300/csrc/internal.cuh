@@ -49,6 +49,14 @@ struct Counters {
     unsigned long long n_used;      // samples composited (up to termination)
     uint32_t fields_hit;
     uint32_t pad;
+    uint32_t class_tiles[4];        // first tile of width class c; entry n_classes = n_tiles
+};
+
+// Width classes of a mixed-width field set: internal field ids are grouped by
+// class; first[c] = first internal field of class c (n_fields past the last
+// class).  A single width is one class: {0, F, F, F}.
+struct ClassBounds {
+    int first[4];
 };
 
 // Ray state, structure of arrays, indexed by ray id.
@@ -131,6 +139,8 @@ struct MlpWeights {
     int64_t img_bytes;
     const void *wimg8;         // FP8 E4M3 tensor-core images [F][img8_bytes]
     int64_t img8_bytes;
+    int cls;                   // width class: the kernels take tiles [class_tiles[cls], class_tiles[cls + 1])
+    int field_base;            // first internal field id of the class (row 0 of the per-class arrays)
     const float *affine;       // [F][6]
 };
 
@@ -144,11 +154,11 @@ void launch_march(const GridDev &g, const MarchParams &p, int grid, cudaStream_t
 // multiple of `group`; with hist_ready the histogram is already in b.hist
 void launch_bucket_ready(const uint32_t *cnt, const uint32_t *recs, const uint32_t *live_count,
                          uint32_t n_fixed, int R, int group, int n_fields, int tile, const BucketBufs &b,
-                         Counters *ctr, int grid, cudaStream_t s);
+                         Counters *ctr, int grid, cudaStream_t s, ClassBounds cb);
 void launch_bucket(const uint32_t *cnt, const uint32_t *recs, const uint32_t *live_count,
                    uint32_t n_fixed, int R, int group, const uint16_t *keys16,
                    int n_fields, int tile, const BucketBufs &b, Counters *ctr, int grid,
-                   cudaStream_t s);
+                   cudaStream_t s, ClassBounds cb);
 void launch_mlp_simt(const MlpWeights &w, const SampleSrc &src, const BucketBufs &b,
                      Counters *ctr, float4 *out, int grid, cudaStream_t s);
 void launch_pack_simt(const float *w32, int n_fields, int W, int H, int64_t P, float *wt,

@@ -420,18 +420,29 @@ __global__ void k_adam(float *__restrict__ w, float *__restrict__ m, float *__re
 
 // L2 photometric loss of the fine-tuning stage: loss += sum (rgb - target)^2
 // / norm over the rays, and dl/drgb = 2 (rgb - target) / norm.
-__global__ void k_l2_loss(int64_t n3, const float *__restrict__ rgb, const float *__restrict__ target, float inv_norm,
-                          float *__restrict__ dl, float *__restrict__ loss)
+// One block: the loss is summed in a fixed order (per-thread strided sums,
+// then a fixed tree), so the same inputs give the same bits on every run.
+__global__ void __launch_bounds__(1024) k_l2_loss(int64_t n3, const float *__restrict__ rgb,
+                                                  const float *__restrict__ target, float inv_norm,
+                                                  float *__restrict__ dl, float *__restrict__ loss)
 {
+    __shared__ float part[32];
     float acc = 0.f;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n3; i += (int64_t)gridDim.x * blockDim.x) {
+    for (int64_t i = threadIdx.x; i < n3; i += blockDim.x) {
         const float e = rgb[i] - target[i];
         dl[i] = 2.f * e * inv_norm;
         acc = fmaf(e * inv_norm, e, acc);
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
-    if ((threadIdx.x & 31) == 0 && loss) atomicAdd(loss, acc);
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        float v = threadIdx.x < (blockDim.x >> 5) ? part[threadIdx.x] : 0.f;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if (threadIdx.x == 0 && loss) *loss = v;
+    }
 }
 
 template <int W, int H>
@@ -475,11 +486,7 @@ void launch_mlp_bwd_simt(const MlpWeights &w, const SampleSrc &src, const Bucket
 void launch_l2_loss(int64_t n_rays, const float *rgb, const float *target, float norm, float *dl, float *loss,
                     cudaStream_t s)
 {
-    if (loss) cudaMemsetAsync(loss, 0, sizeof(float), s);
-    int64_t blocks = (3 * n_rays + 255) / 256;
-    if (blocks > 4096) blocks = 4096;
-    if (blocks < 1) blocks = 1;
-    k_l2_loss<<<(unsigned)blocks, 256, 0, s>>>(3 * n_rays, rgb, target, 1.0f / norm, dl, loss);
+    k_l2_loss<<<1, 1024, 0, s>>>(3 * n_rays, rgb, target, 1.0f / norm, dl, loss);
 }
 
 void launch_adam(float *w32, float *m, float *v, const float *g, int64_t n, float lr, float b1, float b2, float eps,

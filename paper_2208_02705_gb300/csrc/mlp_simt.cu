@@ -115,9 +115,10 @@ __global__ void __launch_bounds__(kThreads) k_mlp_simt(MlpWeights w, SampleSrc s
 {
     extern __shared__ float sx[];   // [(W + kPeD) or kPeX][kThreads]
     const int tid = threadIdx.x;
-    const uint32_t n_tiles = ctr->n_tiles;
-    const uint32_t t0 = (uint32_t)((uint64_t)n_tiles * blockIdx.x / gridDim.x);
-    const uint32_t t1 = (uint32_t)((uint64_t)n_tiles * (blockIdx.x + 1) / gridDim.x);
+    // this width class's tiles
+    const uint32_t c0 = ctr->class_tiles[w.cls], n_tiles = ctr->class_tiles[w.cls + 1] - c0;
+    const uint32_t t0 = c0 + (uint32_t)((uint64_t)n_tiles * blockIdx.x / gridDim.x);
+    const uint32_t t1 = c0 + (uint32_t)((uint64_t)n_tiles * (blockIdx.x + 1) / gridDim.x);
     const TLayout L(W, H);
     constexpr int NH = round4(1 + W);
     for (uint32_t t = t0; t < t1; ++t) {
@@ -155,7 +156,7 @@ __global__ void __launch_bounds__(kThreads) k_mlp_simt(MlpWeights w, SampleSrc s
                 xl2 = fmaf(aff[2], pz, aff[5]);
             }
         }
-        const float *wf = w.wt + (int64_t)tl.field * w.Pt;
+        const float *wf = w.wt + (int64_t)((int)tl.field - w.field_base) * w.Pt;
 
         encode<10>(xl0, xl1, xl2, sx, 0, tid);
         float h[W];

@@ -399,8 +399,8 @@ __device__ __forceinline__ SampleIn stage_finish(const Pending &q, const SampleS
 // shared weight image, and each issuer waits for it before its next MMA.
 template <int W, int H, bool F8>
 __global__ void __launch_bounds__(TcShape<W, H, F8>::kSlots * 128, 1)
-    k_mlp_tc(const void *wimg, int64_t img_bytes, const float *affine, float sig_scale, int act, SampleSrc src,
-             BucketBufs b, Counters *ctr, float4 *out)
+    k_mlp_tc(const void *wimg, int64_t img_bytes, int field_base, int cls, const float *affine, float sig_scale,
+             int act, SampleSrc src, BucketBufs b, Counters *ctr, float4 *out)
 {
     using S = TcShape<W, H, F8>;
     constexpr int kSlots = S::kSlots;
@@ -449,7 +449,9 @@ __global__ void __launch_bounds__(TcShape<W, H, F8>::kSlots * 128, 1)
     const uint32_t imga = smem_u32(IMG);
     const float *tab = reinterpret_cast<const float *>(IMG + S::kMatBytes + S::kOutBytes);
 
-    const uint32_t n_groups = ctr->n_tiles / kSlots;
+    // this width class's tiles (a multiple of kSlots apart: bucket padding)
+    const Tile *tiles = b.tiles + ctr->class_tiles[cls];
+    const uint32_t n_groups = (ctr->class_tiles[cls + 1] - ctr->class_tiles[cls]) / kSlots;
     const uint32_t g0 = (uint32_t)((uint64_t)n_groups * blockIdx.x / gridDim.x);
     const uint32_t g1 = (uint32_t)((uint64_t)n_groups * (blockIdx.x + 1) / gridDim.x);
 
@@ -463,7 +465,7 @@ __global__ void __launch_bounds__(TcShape<W, H, F8>::kSlots * 128, 1)
     Pending pend{};
     uint32_t g = g0;
     if (g < g1) {
-        tl = b.tiles[g * kSlots + slot];
+        tl = tiles[g * kSlots + slot];
         nxt = fetch_sample(src, b, tl, row);
     }
     for (; g < g1; ++g) {
@@ -473,13 +475,22 @@ __global__ void __launch_bounds__(TcShape<W, H, F8>::kSlots * 128, 1)
             // image; meet (and agree on any abort), reload, issuers wait below
             if (named_sync_or(15, kSlots * 128, aborted || *abortp)) break;
             if (threadIdx.x == 0) {
-                mbar_expect_tx(&bar_w, (uint32_t)S::kImageBytes);
-                const uint8_t *gsrc = reinterpret_cast<const uint8_t *>(wimg) + (int64_t)f * img_bytes;
-                for (int off = 0; off < S::kImageBytes; off += 16384) {
-                    const int nb = S::kImageBytes - off < 16384 ? S::kImageBytes - off : 16384;
-                    bulk_g2s(IMG + off, gsrc + off, (uint32_t)nb, &bar_w);
+                // a load whose groups held only empty tiles was never waited
+                // for: retire it first, so each phase of bar_w carries
+                // exactly one arrival and one image
+                if (!w_waited_last) w_waited_last = mbar_wait(&bar_w, (n_changes - 1) & 1u, abortp, status, true);
+                if (w_waited_last) {
+                    mbar_expect_tx(&bar_w, (uint32_t)S::kImageBytes);
+                    const uint8_t *gsrc =
+                        reinterpret_cast<const uint8_t *>(wimg) + (int64_t)(f - field_base) * img_bytes;
+                    for (int off = 0; off < S::kImageBytes; off += 16384) {
+                        const int nb = S::kImageBytes - off < 16384 ? S::kImageBytes - off : 16384;
+                        bulk_g2s(IMG + off, gsrc + off, (uint32_t)nb, &bar_w);
+                    }
+                    w_waited_last = false;
+                } else {
+                    *abortp = 1;           // the old load never landed: give up (status already flagged)
                 }
-                w_waited_last = false;
             }
             ++n_changes;
             cur_field = f;
@@ -488,7 +499,7 @@ __global__ void __launch_bounds__(TcShape<W, H, F8>::kSlots * 128, 1)
         }
         const Tile cur = tl;
         const SampleIn sm = nxt;
-        if (g + 1 < g1) tl = b.tiles[(g + 1) * kSlots + slot];
+        if (g + 1 < g1) tl = tiles[(g + 1) * kSlots + slot];
         if (cur.count == 0 || aborted) {
             if (g + 1 < g1) nxt = fetch_sample(src, b, tl, row);
             continue;
@@ -845,7 +856,8 @@ void launch_t(const MlpWeights &w, const SampleSrc &src, const BucketBufs &b, Co
     }
     const void *img = F8 ? w.wimg8 : w.wimg;
     const int64_t ib = F8 ? w.img8_bytes : w.img_bytes;
-    k_mlp_tc<W, H, F8><<<n_sm, kSlots * 128, smem, s>>>(img, ib, w.affine, w.sigma_scale, w.act, src, b, ctr, out);
+    k_mlp_tc<W, H, F8><<<n_sm, kSlots * 128, smem, s>>>(img, ib, w.field_base, w.cls, w.affine, w.sigma_scale, w.act,
+                                                        src, b, ctr, out);
 }
 
 #define ROAM_TC_CASES                                                                                   \

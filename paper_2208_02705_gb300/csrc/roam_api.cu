@@ -93,6 +93,15 @@ int64_t param_count(int W, int H)
            (int64_t)W * (W + kPeD) + W + 3 * (int64_t)W + 3;
 }
 
+// Weights of the fields of one width: FP32 masters and the derived copies.
+struct WSet {
+    int W = 0, first = 0, n = 0;        // width; internal field ids [first, first + n)
+    int64_t P = 0, Pt = 0, Pr = 0, img_bytes = 0, img8_bytes = 0;
+    bool tc_ok = false, tc8_ok = false;
+    DBuf<float> w32, wt, wr;
+    DBuf<uint8_t> wimg, wimg8;
+};
+
 }  // namespace
 
 struct roam_ctx {
@@ -113,12 +122,17 @@ struct roam_ctx {
     // weights
     bool has_weights = false;
     roam_mlp_desc md{};
-    int64_t P = 0, Pt = 0, img_bytes = 0, img8_bytes = 0;
-    bool tc_ok = false, tc8_ok = false;
-    DBuf<float> w32, wt, wr, adam_m, adam_v;
-    int64_t Pr = 0;
+    // one weight set per width class; internal field ids are grouped by class
+    // (a permutation of the caller's ids when the widths are mixed)
+    WSet ws[3];
+    int n_ws = 0;
+    ClassBounds cb{{0, 0, 0, 0}};
+    bool permuted = false;
+    DBuf<uint16_t> perm, inv, labels_orig, keys_tmp;
+    std::vector<float> affine_orig;
+    std::vector<int32_t> widths;            // caller's field order
+    DBuf<float> adam_m, adam_v;
     bool adam_fresh = true;
-    DBuf<uint8_t> wimg, wimg8;
     // per-call workspace
     DBuf<float4> orig, dir, dir_lo, acc, sr, gsr;
     DBuf<float2> tw;
@@ -218,26 +232,36 @@ roam_status status_of(uint32_t st)
 
 int grid_blocks(const roam_ctx *c, int per_sm) { return c->n_sm * per_sm; }
 
-MlpWeights weights_of(const roam_ctx *c)
+MlpWeights weights_of(const roam_ctx *c, int k = 0)
 {
+    const WSet &q = c->ws[k];
     MlpWeights w{};
-    w.W = c->md.width;
+    w.W = q.W;
     w.H = c->md.n_hidden;
     w.act = c->md.density_act;
-    w.n_fields = c->n_fields;
-    w.P = c->P;
+    w.n_fields = q.n;
+    w.P = q.P;
     w.sigma_scale = c->md.sigma_scale;
-    w.w32 = c->w32.p;
-    w.wt = c->wt.p;
-    w.Pt = c->Pt;
-    w.wr = c->wr.p;
-    w.Pr = c->Pr;
-    w.wimg = c->wimg.p;
-    w.img_bytes = c->img_bytes;
-    w.wimg8 = c->wimg8.p;
-    w.img8_bytes = c->img8_bytes;
+    w.w32 = q.w32.p;
+    w.wt = q.wt.p;
+    w.Pt = q.Pt;
+    w.wr = q.wr.p;
+    w.Pr = q.Pr;
+    w.wimg = q.wimg.p;
+    w.img_bytes = q.img_bytes;
+    w.wimg8 = q.wimg8.p;
+    w.img8_bytes = q.img8_bytes;
+    w.cls = k;
+    w.field_base = q.first;
     w.affine = c->affine.p;
     return w;
+}
+
+bool all_tc(const roam_ctx *c, bool f8)
+{
+    for (int k = 0; k < c->n_ws; ++k)
+        if (!(f8 ? c->ws[k].tc8_ok : c->ws[k].tc_ok)) return false;
+    return c->n_ws > 0;
 }
 
 roam_status check_ready(const roam_ctx *c)
@@ -258,7 +282,7 @@ roam_status check_opts(const roam_ctx *c, const roam_render_opts *o)
         if (!finite(o->bg[i])) return fail(ROAM_ERR_ARG, "background must be finite");
     if (o->precision != ROAM_F32 && o->precision != ROAM_BF16 && o->precision != ROAM_FP8)
         return fail(ROAM_ERR_ARG, "unknown precision");
-    if ((o->precision == ROAM_BF16 && !c->tc_ok) || (o->precision == ROAM_FP8 && !c->tc8_ok))
+    if ((o->precision == ROAM_BF16 && !all_tc(c, false)) || (o->precision == ROAM_FP8 && !all_tc(c, true)))
         return fail(ROAM_ERR_UNSUPPORTED, "tensor-core path not available for W=%d H=%d", c->md.width, c->md.n_hidden);
     if (o->round_size < 0) return fail(ROAM_ERR_ARG, "round_size must be >= 0");
     if (o->use_graph != 0 && o->use_graph != 1) return fail(ROAM_ERR_ARG, "use_graph must be 0 or 1");
@@ -384,21 +408,32 @@ BucketBufs bucket_of(roam_ctx *c)
 }
 
 int tile_of(int precision) { return precision != ROAM_F32 ? tc_tile_samples() : 128; }
+// tiles per field are padded to a multiple of the largest slot count of the
+// classes present (every class's count divides it: 4, 2 or 1), so each
+// class's tile range starts on a group boundary of its own kernel
 int group_of(const roam_ctx *c, int precision)
 {
-    return precision != ROAM_F32 ? tc_tile_group(c->md.width, precision == ROAM_FP8) : 1;
+    int g = 1;
+    if (precision != ROAM_F32)
+        for (int k = 0; k < c->n_ws; ++k) g = std::max(g, tc_tile_group(c->ws[k].W, precision == ROAM_FP8));
+    return g;
 }
 
 roam_status run_mlp(roam_ctx *c, int precision, const SampleSrc &src, const BucketBufs &b, float4 *out,
                     cudaStream_t s)
 {
-    const MlpWeights w = weights_of(c);
-    if (precision != ROAM_F32) {
-        launch_mlp_tc(w, precision == ROAM_FP8, src, b, c->ctr, out, c->n_sm, s);
-        return launched("mlp_tc");
+    // one launch per width class over its own tile range
+    for (int k = 0; k < c->n_ws; ++k) {
+        const MlpWeights w = weights_of(c, k);
+        if (precision != ROAM_F32) {
+            launch_mlp_tc(w, precision == ROAM_FP8, src, b, c->ctr, out, c->n_sm, s);
+            ROAM_TRY(launched("mlp_tc"));
+        } else {
+            launch_mlp_simt(w, src, b, c->ctr, out, grid_blocks(c, 4), s);
+            ROAM_TRY(launched("mlp_simt"));
+        }
     }
-    launch_mlp_simt(w, src, b, c->ctr, out, grid_blocks(c, 4), s);
-    return launched("mlp_simt");
+    return ROAM_OK;
 }
 
 // The render / training-forward pipeline: rounds of march -> bucket -> MLP ->
@@ -437,7 +472,7 @@ roam_status run_rounds(roam_ctx *c, const uint32_t *rays, int64_t n_rays, const 
         {
             ProfScope ps(c, P_BUCKET, s);
             launch_bucket_ready(mp.cnt, mp.recs, mp.live_count, mp.n_rays, R, group_of(c, o->precision), c->n_fields,
-                                tile_of(o->precision), b, c->ctr, grid, s);
+                                tile_of(o->precision), b, c->ctr, grid, s, c->cb);
         }
         ROAM_TRY(launched("bucket"));
         SampleSrc src{};
@@ -526,6 +561,112 @@ roam_status render_graph(roam_ctx *c, int64_t n_pix, const roam_render_opts *o, 
     return ROAM_OK;
 }
 
+roam_status check_desc(const roam_mlp_desc *desc)
+{
+    if (desc->n_hidden < 1 || desc->n_hidden > 4) return fail(ROAM_ERR_ARG, "n_hidden must be in [1, 4]");
+    if (!(desc->sigma_scale > 0.f) || !finite(desc->sigma_scale)) return fail(ROAM_ERR_ARG, "sigma_scale must be positive");
+    if (desc->density_act != ROAM_SOFTPLUS && desc->density_act != ROAM_RELU)
+        return fail(ROAM_ERR_ARG, "unknown density activation");
+    return ROAM_OK;
+}
+
+__global__ void k_relabel(const uint16_t *src, const uint16_t *perm, int64_t n, uint16_t *dst)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        dst[i] = perm[src[i]];
+}
+
+// Internal field ids: perm[f] for the caller's field f (nullptr = identity).
+// The device labels and the field affines follow; the caller's labels are
+// kept aside while a permutation is in force.
+roam_status set_field_order(roam_ctx *c, const uint16_t *perm)
+{
+    const int F = c->n_fields;
+    if (!perm && !c->permuted) return ROAM_OK;
+    if (!c->permuted && c->n_occ > 0) {
+        ROAM_TRY(ensure(c->labels_orig, (size_t)c->n_occ));
+        ROAM_CUDA(cudaMemcpy(c->labels_orig.p, c->labels.p, c->n_occ * sizeof(uint16_t), cudaMemcpyDeviceToDevice));
+    }
+    std::vector<float> aff(6 * (size_t)F);
+    if (perm) {
+        for (int f = 0; f < F; ++f) memcpy(&aff[6 * (size_t)perm[f]], &c->affine_orig[6 * (size_t)f], 6 * sizeof(float));
+        ROAM_TRY(ensure(c->perm, (size_t)F));
+        ROAM_CUDA(cudaMemcpy(c->perm.p, perm, F * sizeof(uint16_t), cudaMemcpyHostToDevice));
+        if (c->n_occ > 0) {
+            k_relabel<<<1024, 256>>>(c->labels_orig.p, c->perm.p, c->n_occ, c->labels.p);
+            ROAM_TRY(launched("relabel"));
+        }
+    } else {
+        aff = c->affine_orig;
+        if (c->n_occ > 0)
+            ROAM_CUDA(cudaMemcpy(c->labels.p, c->labels_orig.p, c->n_occ * sizeof(uint16_t), cudaMemcpyDeviceToDevice));
+    }
+    ROAM_CUDA(cudaMemcpy(c->affine.p, aff.data(), aff.size() * sizeof(float), cudaMemcpyHostToDevice));
+    ROAM_CUDA(cudaDeviceSynchronize());
+    c->permuted = perm != nullptr;
+    return ROAM_OK;
+}
+
+// Loads weight set k: n fields of width W (internal ids first .. first + n - 1),
+// FP32 masters in the API layout, and packs the SIMT and tensor-core copies.
+roam_status load_set(roam_ctx *c, int k, int W, int H, int first, int n, const float *weights, bool on_device)
+{
+    WSet &q = c->ws[k];
+    const int64_t P = param_count(W, H);
+    const int64_t total = P * n;
+    ROAM_TRY(ensure(q.w32, (size_t)total));
+    ROAM_CUDA(cudaMemcpy(q.w32.p, weights, total * sizeof(float),
+                         on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice));
+    ROAM_CUDA(cudaMemset(c->d_flag, 0, 4));
+    k_check_finite<<<1024, 256>>>(q.w32.p, total, c->d_flag);
+    ROAM_TRY(launched("weight check"));
+    uint32_t bad = 0;
+    ROAM_CUDA(cudaMemcpy(&bad, c->d_flag, 4, cudaMemcpyDeviceToHost));
+    if (bad) return fail(ROAM_ERR_ARG, "weights contain NaN or Inf");
+    q.W = W;
+    q.first = first;
+    q.n = n;
+    q.P = P;
+    q.Pt = simt_transposed_size(W, H);
+    ROAM_TRY(ensure(q.wt, (size_t)(q.Pt * n)));
+    launch_pack_simt(q.w32.p, n, W, H, P, q.wt.p, q.Pt, 0);
+    ROAM_TRY(launched("pack simt"));
+    q.Pr = rows_padded_size(W, H);
+    ROAM_TRY(ensure(q.wr, (size_t)(q.Pr * n)));
+    launch_pack_rows(q.w32.p, n, W, H, P, q.wr.p, q.Pr, 0);
+    ROAM_TRY(launched("pack rows"));
+    q.tc_ok = tc_supported(W, H, false);
+    if (q.tc_ok) {
+        q.img_bytes = tc_image_bytes(W, H, false);
+        ROAM_TRY(ensure(q.wimg, (size_t)(q.img_bytes * n)));
+        launch_pack_tc(q.w32.p, n, W, H, P, q.wimg.p, q.img_bytes, false, 0);
+        ROAM_TRY(launched("pack tc"));
+    }
+    q.tc8_ok = tc_supported(W, H, true);
+    if (q.tc8_ok) {
+        q.img8_bytes = tc_image_bytes(W, H, true);
+        ROAM_TRY(ensure(q.wimg8, (size_t)(q.img8_bytes * n)));
+        launch_pack_tc(q.w32.p, n, W, H, P, q.wimg8.p, q.img8_bytes, true, 0);
+        ROAM_TRY(launched("pack tc fp8"));
+    }
+    return ROAM_OK;
+}
+
+__global__ void k_unpermute_recs(const uint32_t *count, uint32_t *recs, int64_t n_rays, int n_max, const uint16_t *inv)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_rays * n_max;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = i / n_max;
+        if ((uint32_t)(i % n_max) < count[r]) recs[i] = (recs[i] & 0xffffu) | ((uint32_t)inv[recs[i] >> 16] << 16);
+    }
+}
+
+__global__ void k_map_keys(const uint16_t *keys, int64_t n, const uint16_t *perm, int n_fields, uint16_t *out)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = keys[i] < n_fields ? perm[keys[i]] : keys[i];   // out-of-range ids stay invalid
+}
+
 }  // namespace
 
 namespace roam {
@@ -573,7 +714,11 @@ roam_status roam_destroy(roam_ctx *c)
     release(c->bits); release(c->prefix); release(c->block_sums);
     release(c->brick_occ); release(c->brick_dist); release(c->brick_t0); release(c->brick_t1);
     release(c->labels); release(c->affine);
-    release(c->w32); release(c->wt); release(c->wr); release(c->gsr); release(c->adam_m); release(c->adam_v); release(c->wimg); release(c->wimg8);
+    for (WSet &q : c->ws) {
+        release(q.w32); release(q.wt); release(q.wr); release(q.wimg); release(q.wimg8);
+    }
+    release(c->perm); release(c->inv); release(c->labels_orig); release(c->keys_tmp);
+    release(c->gsr); release(c->adam_m); release(c->adam_v);
     release(c->orig); release(c->dir); release(c->dir_lo); release(c->acc); release(c->sr); release(c->tw);
     release(c->j_next); release(c->j_end); release(c->n_kept); release(c->live0); release(c->live1);
     release(c->cnt); release(c->recs); release(c->sorted); release(c->hist); release(c->offsets);
@@ -688,6 +833,9 @@ roam_status roam_load_fields(roam_ctx *c, int n_fields, const uint16_t *labels, 
     c->n_fields = n_fields;
     c->g.labels = c->labels.p;
     c->g.n_fields = n_fields;
+    c->permuted = false;
+    release(c->labels_orig);
+    c->affine_orig = aff_h;
     ROAM_TRY(ensure_fields_ws(c));
     c->has_fields = true;
     return ROAM_OK;
@@ -700,50 +848,87 @@ roam_status roam_load_weights(roam_ctx *c, const roam_mlp_desc *desc, const floa
     if (!desc || !weights) return fail(ROAM_ERR_ARG, "null MLP descriptor or weights");
     if (desc->width != 32 && desc->width != 64 && desc->width != 128)
         return fail(ROAM_ERR_ARG, "width must be 32, 64 or 128");
-    if (desc->n_hidden < 1 || desc->n_hidden > 4) return fail(ROAM_ERR_ARG, "n_hidden must be in [1, 4]");
-    if (!(desc->sigma_scale > 0.f) || !finite(desc->sigma_scale)) return fail(ROAM_ERR_ARG, "sigma_scale must be positive");
-    if (desc->density_act != ROAM_SOFTPLUS && desc->density_act != ROAM_RELU)
-        return fail(ROAM_ERR_ARG, "unknown density activation");
+    ROAM_TRY(check_desc(desc));
     c->has_weights = false;
     ++c->gen;
-    const int W = desc->width, H = desc->n_hidden;
-    const int64_t P = param_count(W, H);
-    const int64_t total = P * c->n_fields;
-    ROAM_TRY(ensure(c->w32, (size_t)total));
-    ROAM_CUDA(cudaMemcpy(c->w32.p, weights, total * sizeof(float),
-                         on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice));
-    ROAM_CUDA(cudaMemset(c->d_flag, 0, 4));
-    k_check_finite<<<1024, 256>>>(c->w32.p, total, c->d_flag);
-    ROAM_TRY(launched("weight check"));
-    uint32_t bad = 0;
-    ROAM_CUDA(cudaMemcpy(&bad, c->d_flag, 4, cudaMemcpyDeviceToHost));
-    if (bad) return fail(ROAM_ERR_ARG, "weights contain NaN or Inf");
+    ROAM_TRY(set_field_order(c, nullptr));
+    c->n_ws = 1;
+    c->cb = ClassBounds{{0, c->n_fields, c->n_fields, c->n_fields}};
+    c->widths.assign(c->n_fields, desc->width);
+    ROAM_TRY(load_set(c, 0, desc->width, desc->n_hidden, 0, c->n_fields, weights, on_device != 0));
     c->md = *desc;
-    c->P = P;
-    c->Pt = simt_transposed_size(W, H);
-    ROAM_TRY(ensure(c->wt, (size_t)(c->Pt * c->n_fields)));
-    launch_pack_simt(c->w32.p, c->n_fields, W, H, P, c->wt.p, c->Pt, 0);
-    ROAM_TRY(launched("pack simt"));
-    c->Pr = rows_padded_size(W, H);
-    ROAM_TRY(ensure(c->wr, (size_t)(c->Pr * c->n_fields)));
-    launch_pack_rows(c->w32.p, c->n_fields, W, H, P, c->wr.p, c->Pr, 0);
-    ROAM_TRY(launched("pack rows"));
     c->adam_fresh = true;
     c->train_rays = 0;
-    c->tc_ok = tc_supported(W, H, false);
-    if (c->tc_ok) {
-        c->img_bytes = tc_image_bytes(W, H, false);
-        ROAM_TRY(ensure(c->wimg, (size_t)(c->img_bytes * c->n_fields)));
-        launch_pack_tc(c->w32.p, c->n_fields, W, H, P, c->wimg.p, c->img_bytes, false, 0);
-        ROAM_TRY(launched("pack tc"));
+    ROAM_CUDA(cudaDeviceSynchronize());
+    c->has_weights = true;
+    return ROAM_OK;
+}
+
+roam_status roam_load_weights_mixed(roam_ctx *c, const roam_mlp_desc *desc, const int32_t *field_width,
+                                    const float *weights, int on_device)
+{
+    ROAM_TRY(set_dev(c));
+    if (!c->has_fields) return fail(ROAM_ERR_STATE, "load the field labels first");
+    if (!desc || !weights || !field_width) return fail(ROAM_ERR_ARG, "null descriptor, widths or weights");
+    ROAM_TRY(check_desc(desc));
+    const int F = c->n_fields, H = desc->n_hidden;
+    const int kW[3] = {32, 64, 128};
+    std::vector<int> cls(F);
+    int count[3] = {0, 0, 0};
+    int64_t total = 0;
+    for (int f = 0; f < F; ++f) {
+        const int w = field_width[f];
+        cls[f] = w == 32 ? 0 : (w == 64 ? 1 : (w == 128 ? 2 : -1));
+        if (cls[f] < 0) return fail(ROAM_ERR_ARG, "field %d: width must be 32, 64 or 128", f);
+        ++count[cls[f]];
+        total += param_count(w, H);
     }
-    c->tc8_ok = tc_supported(W, H, true);
-    if (c->tc8_ok) {
-        c->img8_bytes = tc_image_bytes(W, H, true);
-        ROAM_TRY(ensure(c->wimg8, (size_t)(c->img8_bytes * c->n_fields)));
-        launch_pack_tc(c->w32.p, c->n_fields, W, H, P, c->wimg8.p, c->img8_bytes, true, 0);
-        ROAM_TRY(launched("pack tc fp8"));
+    c->has_weights = false;
+    ++c->gen;
+    // the caller's weights, field after field (each in its own width's layout)
+    std::vector<float> hw((size_t)total);
+    ROAM_CUDA(cudaMemcpy(hw.data(), weights, (size_t)total * sizeof(float),
+                         on_device ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost));
+    std::vector<int64_t> off(F + 1, 0);
+    for (int f = 0; f < F; ++f) off[f + 1] = off[f] + param_count(field_width[f], H);
+    // internal ids: classes in width order, the caller's order inside a class
+    std::vector<uint16_t> perm(F), inv(F);
+    int n_ws = 0, next = 0, first[3] = {0, 0, 0}, wcls[3] = {0, 0, 0};
+    for (int k = 0; k < 3; ++k) {
+        if (!count[k]) continue;
+        first[n_ws] = next;
+        wcls[n_ws] = kW[k];
+        for (int f = 0; f < F; ++f)
+            if (cls[f] == k) {
+                perm[f] = (uint16_t)next;
+                inv[next] = (uint16_t)f;
+                ++next;
+            }
+        ++n_ws;
     }
+    ROAM_TRY(set_field_order(c, n_ws > 1 ? perm.data() : nullptr));
+    if (n_ws > 1) {
+        ROAM_TRY(ensure(c->inv, (size_t)F));
+        ROAM_CUDA(cudaMemcpy(c->inv.p, inv.data(), F * sizeof(uint16_t), cudaMemcpyHostToDevice));
+    }
+    c->n_ws = n_ws;
+    c->cb = ClassBounds{{0, F, F, F}};
+    for (int k = 0; k < n_ws; ++k) {
+        c->cb.first[k] = first[k];
+        const int n_k = (k + 1 < n_ws ? first[k + 1] : F) - first[k];
+        const int64_t P = param_count(wcls[k], H);
+        std::vector<float> part((size_t)(P * n_k));
+        for (int q = 0; q < n_k; ++q) {
+            const int f = n_ws > 1 ? inv[first[k] + q] : first[k] + q;
+            memcpy(part.data() + (size_t)q * P, hw.data() + off[f], (size_t)P * sizeof(float));
+        }
+        ROAM_TRY(load_set(c, k, wcls[k], H, first[k], n_k, part.data(), false));
+    }
+    c->widths.assign(field_width, field_width + F);
+    c->md = *desc;
+    c->md.width = n_ws == 1 ? wcls[0] : 0;
+    c->adam_fresh = true;
+    c->train_rays = 0;
     ROAM_CUDA(cudaDeviceSynchronize());
     c->has_weights = true;
     return ROAM_OK;
@@ -755,8 +940,23 @@ roam_status roam_get_weights(roam_ctx *c, float *out, int on_device)
     if (!c->has_weights) return fail(ROAM_ERR_STATE, "no weights loaded");
     if (!out) return fail(ROAM_ERR_ARG, "null output");
     ROAM_CUDA(cudaDeviceSynchronize());
-    ROAM_CUDA(cudaMemcpy(out, c->w32.p, (size_t)(c->P * c->n_fields) * sizeof(float),
-                         on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost));
+    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    if (c->n_ws == 1) {
+        ROAM_CUDA(cudaMemcpy(out, c->ws[0].w32.p, (size_t)(c->ws[0].P * c->n_fields) * sizeof(float), kind));
+        return ROAM_OK;
+    }
+    // mixed widths: field after field in the caller's order
+    std::vector<uint16_t> perm(c->n_fields);
+    ROAM_CUDA(cudaMemcpy(perm.data(), c->perm.p, c->n_fields * sizeof(uint16_t), cudaMemcpyDeviceToHost));
+    int64_t off = 0;
+    for (int f = 0; f < c->n_fields; ++f) {
+        const int i = perm[f];
+        int k = 0;
+        while (k + 1 < c->n_ws && i >= c->ws[k + 1].first) ++k;
+        const WSet &q = c->ws[k];
+        ROAM_CUDA(cudaMemcpy(out + off, q.w32.p + (int64_t)(i - q.first) * q.P, (size_t)q.P * sizeof(float), kind));
+        off += q.P;
+    }
     return ROAM_OK;
 }
 
@@ -886,8 +1086,14 @@ roam_status roam_march(roam_ctx *c, const roam_camera *cams, int n_views, const 
     mp.ctr = c->ctr;
     ROAM_CUDA(cudaMemsetAsync(c->ctr, 0, sizeof(Counters), s));
     launch_march(c->g, mp, grid_blocks(c, 4), s);
+    ROAM_TRY(launched("march"));
+    if (c->permuted) {
+        // records carry the caller's field ids
+        k_unpermute_recs<<<grid_blocks(c, 4), 256, 0, s>>>(count, recs, n_rays, opts->n_max, c->inv.p);
+        ROAM_TRY(launched("march field ids"));
+    }
     c->last = s;
-    return launched("march");
+    return ROAM_OK;
 }
 
 roam_status roam_bucket(roam_ctx *c, const uint16_t *keys, int64_t n, uint32_t *perm, uint32_t *offsets, void *stream)
@@ -902,7 +1108,8 @@ roam_status roam_bucket(roam_ctx *c, const uint16_t *keys, int64_t n, uint32_t *
     b.offsets = offsets;
     b.sorted = perm;
     ROAM_CUDA(cudaMemsetAsync(c->ctr, 0, sizeof(Counters), s));
-    launch_bucket(nullptr, nullptr, nullptr, (uint32_t)n, 1, 1, keys, c->n_fields, 128, b, c->ctr, grid_blocks(c, 2), s);
+    launch_bucket(nullptr, nullptr, nullptr, (uint32_t)n, 1, 1, keys, c->n_fields, 128, b, c->ctr, grid_blocks(c, 2), s,
+                  ClassBounds{{0, c->n_fields, c->n_fields, c->n_fields}});
     c->last = s;
     return launched("bucket");
 }
@@ -917,15 +1124,22 @@ roam_status roam_mlp_eval(roam_ctx *c, const float *p, const float *d, const uin
     if (!p || !d || !field || !out) return fail(ROAM_ERR_ARG, "null pointer");
     if (precision != ROAM_F32 && precision != ROAM_BF16 && precision != ROAM_FP8)
         return fail(ROAM_ERR_ARG, "unknown precision");
-    if ((precision == ROAM_BF16 && !c->tc_ok) || (precision == ROAM_FP8 && !c->tc8_ok))
+    if ((precision == ROAM_BF16 && !all_tc(c, false)) || (precision == ROAM_FP8 && !all_tc(c, true)))
         return fail(ROAM_ERR_UNSUPPORTED, "tensor-core path not available");
     cudaStream_t s = (cudaStream_t)stream;
     ROAM_TRY(ensure(c->sorted, (size_t)n));
     ROAM_TRY(ensure(c->tiles, tile_capacity((size_t)n, c->n_fields)));
     const BucketBufs b = bucket_of(c);
     ROAM_CUDA(cudaMemsetAsync(c->ctr, 0, sizeof(Counters), s));
-    launch_bucket(nullptr, nullptr, nullptr, (uint32_t)n, 1, group_of(c, precision), field, c->n_fields,
-                  tile_of(precision), b, c->ctr, grid_blocks(c, 2), s);
+    const uint16_t *keys = field;
+    if (c->permuted) {
+        ROAM_TRY(ensure(c->keys_tmp, (size_t)n));
+        k_map_keys<<<grid_blocks(c, 2), 256, 0, s>>>(field, n, c->perm.p, c->n_fields, c->keys_tmp.p);
+        ROAM_TRY(launched("field ids"));
+        keys = c->keys_tmp.p;
+    }
+    launch_bucket(nullptr, nullptr, nullptr, (uint32_t)n, 1, group_of(c, precision), keys, c->n_fields,
+                  tile_of(precision), b, c->ctr, grid_blocks(c, 2), s, c->cb);
     ROAM_TRY(launched("bucket"));
     SampleSrc src{};
     src.mode = 1;
@@ -962,6 +1176,7 @@ roam_status roam_train_forward(roam_ctx *c, const roam_camera *cams, int n_views
     if (opts->precision == ROAM_FP8) return fail(ROAM_ERR_UNSUPPORTED, "training runs in FP32 or BF16");
     if (!rays || !rgb) return fail(ROAM_ERR_ARG, "null rays or rgb");
     if (n_rays < 1 || n_rays > 0x7fffffff) return fail(ROAM_ERR_ARG, "bad ray count");
+    if (c->n_ws != 1) return fail(ROAM_ERR_UNSUPPORTED, "training needs one MLP width for every field");
     if (!mlp_bwd_supported(c->md.width, c->md.n_hidden))
         return fail(ROAM_ERR_UNSUPPORTED, "training supports W = 32 or 64");
     cudaStream_t s = (cudaStream_t)stream;
@@ -1007,10 +1222,10 @@ roam_status roam_train_backward(roam_ctx *c, const float *dl_drgb, float *grad, 
     {
         ProfScope ps(c, P_BUCKET, s);
         launch_bucket(c->live1.p, c->recs.p, nullptr, (uint32_t)n, R, 1, nullptr, c->n_fields, 128, b, c->ctr,
-                      grid_blocks(c, 4), s);
+                      grid_blocks(c, 4), s, c->cb);
     }
     ROAM_TRY(launched("bucket"));
-    ROAM_CUDA(cudaMemsetAsync(grad, 0, (size_t)(c->P * c->n_fields) * sizeof(float), s));
+    ROAM_CUDA(cudaMemsetAsync(grad, 0, (size_t)(c->ws[0].P * c->n_fields) * sizeof(float), s));
     SampleSrc src{};
     src.mode = 0;
     src.recs = c->recs.p;
@@ -1051,7 +1266,9 @@ roam_status roam_adam_step(roam_ctx *c, const float *grad, const roam_adam_cfg *
         !(cfg->beta2 >= 0.f && cfg->beta2 < 1.f) || !(cfg->eps > 0.f) || cfg->step < 1)
         return fail(ROAM_ERR_ARG, "bad Adam configuration");
     cudaStream_t s = (cudaStream_t)stream;
-    const int64_t n = c->P * c->n_fields;
+    if (c->n_ws != 1) return fail(ROAM_ERR_UNSUPPORTED, "training needs one MLP width for every field");
+    WSet &q = c->ws[0];
+    const int64_t n = q.P * c->n_fields;
     ROAM_TRY(ensure(c->adam_m, (size_t)n));
     ROAM_TRY(ensure(c->adam_v, (size_t)n));
     if (c->adam_fresh) {
@@ -1063,14 +1280,14 @@ roam_status roam_adam_step(roam_ctx *c, const float *grad, const roam_adam_cfg *
     const float bc2 = (float)(1.0 - std::pow((double)cfg->beta2, (double)cfg->step));
     {
         ProfScope ps(c, P_ADAM, s);
-        launch_adam(c->w32.p, c->adam_m.p, c->adam_v.p, grad, n, cfg->lr, cfg->beta1, cfg->beta2, cfg->eps, bc1, bc2,
+        launch_adam(q.w32.p, c->adam_m.p, c->adam_v.p, grad, n, cfg->lr, cfg->beta1, cfg->beta2, cfg->eps, bc1, bc2,
                     s);
         // refresh every derived copy of the masters
         const int W = c->md.width, H = c->md.n_hidden;
-        launch_pack_simt(c->w32.p, c->n_fields, W, H, c->P, c->wt.p, c->Pt, s);
-        launch_pack_rows(c->w32.p, c->n_fields, W, H, c->P, c->wr.p, c->Pr, s);
-        if (c->tc_ok) launch_pack_tc(c->w32.p, c->n_fields, W, H, c->P, c->wimg.p, c->img_bytes, false, s);
-        if (c->tc8_ok) launch_pack_tc(c->w32.p, c->n_fields, W, H, c->P, c->wimg8.p, c->img8_bytes, true, s);
+        launch_pack_simt(q.w32.p, c->n_fields, W, H, q.P, q.wt.p, q.Pt, s);
+        launch_pack_rows(q.w32.p, c->n_fields, W, H, q.P, q.wr.p, q.Pr, s);
+        if (q.tc_ok) launch_pack_tc(q.w32.p, c->n_fields, W, H, q.P, q.wimg.p, q.img_bytes, false, s);
+        if (q.tc8_ok) launch_pack_tc(q.w32.p, c->n_fields, W, H, q.P, q.wimg8.p, q.img8_bytes, true, s);
     }
     c->last = s;
     return launched("adam");

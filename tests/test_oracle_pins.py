@@ -556,6 +556,46 @@ def test_render_slab_transmittance_matches_exp_sigma_l():
 # gradient: analytic reverse mode versus central finite differences
 # ----------------------------------------------------------------------------
 
+def test_render_mixed_widths_assembles_per_field_mlps(room32, room32_grid):
+    """A render whose fields have different MLP widths equals the composite of
+    each sample's own field MLP (its own width, its own slice of the weights)
+    along the marched samples; uniform widths passed per field equal the
+    single-width render."""
+    H = 2
+    widths = F.mixed_widths(1, room32.part.n_fields)
+    assert len(set(widths.tolist())) > 1
+    w = F.xavier_weights_mixed(1, F.ROLE_STUDENT, widths, H, bias_scale=0.2)
+    offs = np.concatenate([[0], np.cumsum([F.n_params(int(W), H) for W in widths])])
+    cams = F.camera_array(room32.cams)
+    cf = O.cams_f32(cams)
+    rng = np.random.default_rng(5)
+    pix = rng.choice(room32.cams[0].n_pixels, 60, replace=False)
+    rays = np.stack([np.zeros_like(pix), pix], 1).astype(np.uint32)
+    ref = O.render(room32_grid, w, room32.affine, 0, H, room32.sigma_scale, cams, rays, room32.delta,
+                   room32.n_max, widths=widths)
+    cnt, js, fs, _ = O.march_rays(room32_grid, cams, rays, room32.delta, room32.n_max)
+    delta = O.f32(room32.delta)
+    width_px = room32.cams[0].width
+    checked = 0
+    for r in range(len(pix)):
+        o, d = O.ray(cf[0], pix[r] % width_px + 0.5, pix[r] // width_px + 0.5)
+        sig, rgb, t = [], [], []
+        for k in range(cnt[r]):
+            f = fs[r, k]
+            tt = (js[r, k] + 0.5) * delta
+            out = O.mlp(w[offs[f]:offs[f + 1]], int(widths[f]), H, room32.sigma_scale, room32.affine[f], o + tt * d, d)
+            sig.append(out[0]); rgb.append(out[1:]); t.append(tt)
+        got, _, _ = O.composite(np.array(sig), np.array(rgb).reshape(-1, 3), np.array(t), delta)
+        assert np.abs(got[:3] - ref["rgb"][r]).max() <= 1e-12
+        checked += cnt[r] > 0
+    assert checked > 10
+    wu = F.xavier_weights(1, F.ROLE_STUDENT, room32.part.n_fields, 32, H)
+    a = O.render(room32_grid, wu, room32.affine, 32, H, room32.sigma_scale, cams, rays, room32.delta, room32.n_max)
+    b = O.render(room32_grid, wu.reshape(-1), room32.affine, 0, H, room32.sigma_scale, cams, rays, room32.delta,
+                 room32.n_max, widths=np.full(room32.part.n_fields, 32))
+    assert np.array_equal(a["rgb"], b["rgb"])
+
+
 def test_loss_gradient_matches_central_differences(room32, room32_grid):
     W, H = 16, 2
     n_fields = room32.part.n_fields
