@@ -312,6 +312,62 @@ def large_scene_bench(roam, F, torch, args, stream, flush, peaks):
     return out
 
 
+def multiview_bench(roam, F, torch, args, stream, flush):
+    """The 384^3 twelve-room floor: 2048 kd fields with per-field widths drawn
+    from 32/64/128, H=3, and 32 views (24 equirectangular from 512x256 to
+    2048x1024, 8 perspective 1280x720), BF16 tensor cores.  One batched call
+    over all views (round size from roam_tune_round_size), CUDA-graph
+    replayed and plain, against one render call per view; sampled pixels
+    against the FP64 oracle."""
+    import numpy as np
+    import oracle as O
+    wl = F.floor384()
+    r = roam.Roam(torch.cuda.current_device())
+    r.load_workload(wl)
+    base = roam.render_opts(wl.delta, wl.n_max, precision=roam.ROAM_BF16)
+    R, tune_ms = r.tune_round_size(wl.cams, base, stream=stream)
+    opts = roam.render_opts(wl.delta, wl.n_max, precision=roam.ROAM_BF16, round_size=R)
+    gopts = roam.render_opts(wl.delta, wl.n_max, precision=roam.ROAM_BF16, round_size=R, use_graph=True)
+    steps = max(3, args.steps // 2)
+    out = {"workload": "floor384_kd2048_mixed_w32_64_128_h3, 32 views (24 equirect 512x256..2048x1024, "
+                       "8 perspective 1280x720)", "rays_per_batch": int(sum(c.n_pixels for c in wl.cams)),
+           "round_size_tuned": R, "tuned_render_ms": tune_ms}
+    for _ in range(2):
+        r.render(wl.cams, gopts, stream=stream)
+    tot_g, per_g = time_steps(r, wl.cams, gopts, steps, 0, flush, stream)
+    st = r.get_stats()
+    tot_b, per_b = time_steps(r, wl.cams, opts, steps, 1, flush, stream)
+    # one call per view, the same options
+    per_v = []
+    for k in range(steps + 1):
+        flush.zero_()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for cam in wl.cams:
+            r.render([cam], opts, stream=stream)
+        b.record(stream)
+        b.synchronize()
+        if k:
+            per_v.append(a.elapsed_time(b))
+    out.update({"batched_graph_ms": statistics.median(per_g), "batched_plain_ms": statistics.median(per_b),
+                "per_view_calls_ms": statistics.median(per_v),
+                "speedup_batched_graph_vs_per_view": statistics.median(per_v) / statistics.median(per_g),
+                "samples_per_s": st.n_used * steps / (tot_g / 1000.0),
+                "samples_per_batch": {"composited": int(st.n_used), "evaluated": int(st.n_samples)}})
+    rgb, _, _ = r.render(wl.cams, gopts, stream=stream)
+    torch.cuda.synchronize()
+    g = O.Grid(wl.scene, wl.part)
+    rays = oracle_sample_rays(wl, 2000, 31)
+    ref = O.render(g, wl.weights, wl.affine, 0, wl.H, wl.sigma_scale, F.camera_array(wl.cams), rays, wl.delta,
+                   wl.n_max, widths=wl.widths)
+    starts = np.concatenate([[0], np.cumsum([c.n_pixels for c in wl.cams])])
+    gi = starts[rays[:, 0].astype(np.int64)] + rays[:, 1].astype(np.int64)
+    out["accuracy_vs_oracle"] = accuracy(rgb.cpu().numpy()[gi].astype(np.float64), ref)
+    r.close()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -463,9 +519,10 @@ def main():
     if rank == 0:
         train = train_step_bench(roam, F, torch, wl, args, stream)
 
-    large = None
+    large = multiview = None
     if rank == 0:
         large = large_scene_bench(roam, F, torch, args, stream, flush, peaks)
+        multiview = multiview_bench(roam, F, torch, args, stream, flush)
 
     cpu = None
     if rank == 0 and world == 1:
@@ -482,7 +539,7 @@ def main():
                 "frame_ms": frame,
                 "fp32_simt": {"value": f32_value, "unit": UNIT, "ms_per_step": t32 / max(3, args.steps // 2)},
                 "accuracy_vs_oracle": acc, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
-                "train_step": train, "large_scene": large,
+                "train_step": train, "large_scene": large, "multi_view": multiview,
                 "gpu_launches": int(6 * st.n_rounds * args.steps), "clocks": clocks}
         print(json.dumps(line), flush=True)
     r.close()

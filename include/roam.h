@@ -198,6 +198,16 @@ roam_status roam_render(roam_ctx *ctx, const roam_camera *cams, int n_views,
                         const roam_render_opts *opts, float *rgb, float *depth, float *opacity,
                         int out_on_device, void *stream);
 
+/* Chooses the round size (kept samples marched per live ray per round) for
+ * this camera batch and these options: renders the batch once per candidate
+ * (4, 8, 16, ... up to n_max, while the workspace fits in half the free
+ * device memory and slot ids in 32 bits) after one warm-up render each,
+ * timing with CUDA events on `stream`, and returns the fastest in
+ * *best_round_size (its time in *best_ms, may be NULL).  Pass it back as
+ * roam_render_opts.round_size.  Synchronous. */
+roam_status roam_tune_round_size(roam_ctx *ctx, const roam_camera *cams, int n_views, const roam_render_opts *opts,
+                                 int32_t *best_round_size, float *best_ms, void *stream);
+
 /* Counters of the last roam_render / roam_train_forward (synchronises). */
 roam_status roam_get_stats(roam_ctx *ctx, roam_stats *stats);
 

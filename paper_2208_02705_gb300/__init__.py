@@ -26,8 +26,8 @@ STATUS = {0: "ROAM_OK", -1: "ROAM_ERR_ARG", -2: "ROAM_ERR_OOM", -3: "ROAM_ERR_CU
 
 # every entry point declared in include/roam.h
 ENTRY_POINTS = ("roam_create", "roam_destroy", "roam_last_error", "roam_check", "roam_load_grid",
-                "roam_load_fields", "roam_load_weights", "roam_load_weights_mixed", "roam_get_weights", "roam_render", "roam_get_stats",
-                "roam_march", "roam_bucket", "roam_mlp_eval", "roam_composite", "roam_train_forward",
+                "roam_load_fields", "roam_load_weights", "roam_load_weights_mixed", "roam_get_weights", "roam_render",
+                "roam_get_stats", "roam_tune_round_size", "roam_march", "roam_bucket", "roam_mlp_eval", "roam_composite", "roam_train_forward",
                 "roam_train_backward", "roam_adam_step", "roam_profile", "roam_profile_read",
                 "roam_bucket_static", "roam_l2_loss")
 
@@ -94,6 +94,7 @@ def load_library(path: str = LIB_PATH):
     L.roam_load_fields.argtypes = [vp, i32, vp, i64, vp, i32]
     L.roam_load_weights.argtypes = [vp, P(roam_mlp_desc), vp, i32]
     L.roam_load_weights_mixed.argtypes = [vp, P(roam_mlp_desc), vp, vp, i32]
+    L.roam_tune_round_size.argtypes = [vp, vp, i32, P(roam_render_opts), vp, vp, vp]
     L.roam_get_weights.argtypes = [vp, vp, i32]
     L.roam_render.argtypes = [vp, P(roam_camera), i32, P(roam_render_opts), vp, vp, vp, i32, vp]
     L.roam_get_stats.argtypes = [vp, P(roam_stats)]
@@ -285,6 +286,15 @@ class Roam:
     def render_host_ptrs(self, cams_arr, n_views, opts, rgb_ptr, depth_ptr, op_ptr, stream_handle):
         _check(self.L.roam_render(self.h, cams_arr, n_views, ctypes.byref(opts), rgb_ptr, depth_ptr, op_ptr, 0,
                                   stream_handle))
+
+    def tune_round_size(self, cams, opts: roam_render_opts, stream=None):
+        """roam_tune_round_size: (best round size, its render time in ms)."""
+        arr = camera_array(cams)
+        best = ctypes.c_int32()
+        ms = ctypes.c_float()
+        _check(self.L.roam_tune_round_size(self.h, arr, len(cams), ctypes.byref(opts), ctypes.byref(best),
+                                           ctypes.byref(ms), _stream(stream)))
+        return int(best.value), float(ms.value)
 
     def get_stats(self) -> roam_stats:
         s = roam_stats()

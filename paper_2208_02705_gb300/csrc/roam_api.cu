@@ -140,9 +140,14 @@ struct roam_ctx {
     DBuf<Tile> tiles;
     DBuf<float> o_rgb, o_depth, o_op;
     DBuf<DevCamera> cams;
-    DevCamera *h_cams = nullptr;
-    cudaEvent_t cam_ev = nullptr;
-    bool cam_pending = false;
+    // pinned staging of the camera uploads: a ring, so that consecutive calls
+    // (e.g. one per view) do not wait for each other's copies
+    static constexpr int kCamRing = 8;
+    DevCamera *h_cams_ring = nullptr;        // [kCamRing][kMaxViews]
+    DevCamera *h_cams = nullptr;             // the slot filled by the current call
+    cudaEvent_t cam_ev[kCamRing] = {};
+    bool cam_pending[kCamRing] = {};
+    int cam_slot = 0;
     Counters *ctr = nullptr;
     Counters *h_ctr = nullptr;
     uint32_t *d_flag = nullptr;
@@ -295,10 +300,13 @@ roam_status upload_cams(roam_ctx *c, const roam_camera *cams, int n_views, float
 {
     if (!cams) return fail(ROAM_ERR_ARG, "null cameras");
     if (n_views < 1 || n_views > kMaxViews) return fail(ROAM_ERR_ARG, "n_views must be in [1, %d]", kMaxViews);
-    if (c->cam_pending) {
-        cudaEventSynchronize(c->cam_ev);
-        c->cam_pending = false;
+    const int slot = c->cam_slot;
+    c->cam_slot = (slot + 1) % roam_ctx::kCamRing;
+    if (c->cam_pending[slot]) {
+        cudaEventSynchronize(c->cam_ev[slot]);   // the copy that last used this staging slot
+        c->cam_pending[slot] = false;
     }
+    c->h_cams = c->h_cams_ring + (size_t)slot * kMaxViews;
     int64_t total = 0;
     const float ext[3] = {c->gd.dims[0] * c->gd.vox, c->gd.dims[1] * c->gd.vox, c->gd.dims[2] * c->gd.vox};
     for (int v = 0; v < n_views; ++v) {
@@ -338,8 +346,8 @@ roam_status upload_cams(roam_ctx *c, const roam_camera *cams, int n_views, float
     }
     ROAM_TRY(ensure(c->cams, (size_t)n_views));
     ROAM_CUDA(cudaMemcpyAsync(c->cams.p, c->h_cams, sizeof(DevCamera) * n_views, cudaMemcpyHostToDevice, s));
-    ROAM_CUDA(cudaEventRecord(c->cam_ev, s));
-    c->cam_pending = true;
+    ROAM_CUDA(cudaEventRecord(c->cam_ev[slot], s));
+    c->cam_pending[slot] = true;
     *n_pix = total;
     c->n_views = n_views;
     return ROAM_OK;
@@ -693,10 +701,14 @@ roam_status roam_create(roam_ctx **out, int device)
     roam_ctx *c = new roam_ctx();
     c->device = device;
     c->n_sm = prop.multiProcessorCount;
-    if (cudaMalloc(&c->ctr, sizeof(Counters)) != cudaSuccess || cudaMallocHost(&c->h_ctr, sizeof(Counters)) != cudaSuccess ||
-        cudaMallocHost(&c->h_cams, sizeof(DevCamera) * kMaxViews) != cudaSuccess ||
-        cudaMalloc(&c->d_flag, sizeof(uint32_t)) != cudaSuccess ||
-        cudaEventCreateWithFlags(&c->cam_ev, cudaEventDisableTiming) != cudaSuccess) {
+    bool ok = cudaMalloc(&c->ctr, sizeof(Counters)) == cudaSuccess &&
+              cudaMallocHost(&c->h_ctr, sizeof(Counters)) == cudaSuccess &&
+              cudaMallocHost(&c->h_cams_ring, sizeof(DevCamera) * kMaxViews * roam_ctx::kCamRing) == cudaSuccess &&
+              cudaMalloc(&c->d_flag, sizeof(uint32_t)) == cudaSuccess;
+    for (int i = 0; i < roam_ctx::kCamRing && ok; ++i)
+        ok = cudaEventCreateWithFlags(&c->cam_ev[i], cudaEventDisableTiming) == cudaSuccess;
+    c->h_cams = c->h_cams_ring;
+    if (!ok) {
         cudaGetLastError();
         roam_destroy(c);
         return fail(ROAM_ERR_OOM, "context allocation failed");
@@ -724,11 +736,12 @@ roam_status roam_destroy(roam_ctx *c)
     release(c->cnt); release(c->recs); release(c->sorted); release(c->hist); release(c->offsets);
     release(c->cursor); release(c->scratch_u32); release(c->tiles);
     release(c->o_rgb); release(c->o_depth); release(c->o_op); release(c->cams);
-    if (c->h_cams) cudaFreeHost(c->h_cams);
+    if (c->h_cams_ring) cudaFreeHost(c->h_cams_ring);
     if (c->h_ctr) cudaFreeHost(c->h_ctr);
     if (c->ctr) cudaFree(c->ctr);
     if (c->d_flag) cudaFree(c->d_flag);
-    if (c->cam_ev) cudaEventDestroy(c->cam_ev);
+    for (cudaEvent_t e : c->cam_ev)
+        if (e) cudaEventDestroy(e);
     if (c->gexec) cudaGraphExecDestroy(c->gexec);
     if (c->gstream) cudaStreamDestroy(c->gstream);
     if (c->ev_fork) cudaEventDestroy(c->ev_fork);
@@ -997,6 +1010,61 @@ roam_status roam_render(roam_ctx *c, const roam_camera *cams, int n_views, const
         return status_of(c->h_ctr->status);
     }
     return ROAM_OK;
+}
+
+roam_status roam_tune_round_size(roam_ctx *c, const roam_camera *cams, int n_views, const roam_render_opts *opts,
+                                 int32_t *best_round_size, float *best_ms, void *stream)
+{
+    ROAM_TRY(set_dev(c));
+    ROAM_TRY(check_ready(c));
+    ROAM_TRY(check_opts(c, opts));
+    if (!best_round_size) return fail(ROAM_ERR_ARG, "null output");
+    cudaStream_t s = (cudaStream_t)stream;
+    int64_t n_pix = 0;
+    ROAM_TRY(upload_cams(c, cams, n_views, opts->delta, &n_pix, s));
+    size_t free_b = 0, total_b = 0;
+    ROAM_CUDA(cudaMemGetInfo(&free_b, &total_b));
+    const size_t have = c->recs.n + free_b / 24;          // slots the workspace can reach (24 B per slot)
+    ROAM_TRY(ensure(c->o_rgb, 3 * (size_t)n_pix));
+    cudaEvent_t e0, e1;
+    ROAM_CUDA(cudaEventCreate(&e0));
+    ROAM_CUDA(cudaEventCreate(&e1));
+    int best = 0;
+    float best_t = 0.f;
+    roam_status st = ROAM_OK;
+    for (int R = 4; R <= opts->n_max && R <= 256 && st == ROAM_OK; R *= 2) {
+        roam_render_opts o = *opts;
+        o.round_size = R;
+        o.use_graph = 0;
+        const int Ruse = round_size(&o, n_pix);
+        if (Ruse != R) break;                                  // 32-bit slot ids
+        if ((size_t)((n_pix + 31) & ~31LL) * (size_t)R > have / 2) break;   // leave half the memory free
+        float t = 0.f;
+        for (int rep = 0; rep < 2 && st == ROAM_OK; ++rep) {    // warm-up, then timed
+            if ((st = ensure_rays(c, n_pix, R)) != ROAM_OK) break;
+            cudaEventRecord(e0, s);
+            cudaMemsetAsync(c->ctr, 0, sizeof(Counters), s);
+            cudaMemsetAsync(c->hist.p, 0, (size_t)c->n_fields * sizeof(uint32_t), s);
+            st = run_rounds(c, nullptr, n_pix, &o, c->o_rgb.p, nullptr, nullptr, R, s);
+            cudaEventRecord(e1, s);
+            if (cudaEventSynchronize(e1) != cudaSuccess) st = fail(ROAM_ERR_CUDA, "tuning render failed");
+            cudaEventElapsedTime(&t, e0, e1);
+        }
+        if (st == ROAM_OK && (best == 0 || t < best_t)) {
+            best = R;
+            best_t = t;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    ROAM_TRY(st);
+    if (best == 0) return fail(ROAM_ERR_OOM, "no round size fits the device");
+    c->last = s;
+    c->last_rays = n_pix;
+    *best_round_size = best;
+    if (best_ms) *best_ms = best_t;
+    ROAM_CUDA(cudaMemcpy(c->h_ctr, c->ctr, sizeof(Counters), cudaMemcpyDeviceToHost));
+    return status_of(c->h_ctr->status);
 }
 
 roam_status roam_get_stats(roam_ctx *c, roam_stats *st)
