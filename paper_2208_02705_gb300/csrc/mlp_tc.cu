@@ -246,19 +246,34 @@ __device__ __forceinline__ uint32_t pack_e4m3x4(float a, float b, float c, float
     return (uint32_t)lo | ((uint32_t)hi << 16);
 }
 
-// Writes 32 activation values (elements [32c, 32c + 32) of A) to TMEM.
-template <bool F8>
+__device__ __forceinline__ uint32_t pack_bf16_relu(float a, float b)
+{
+    uint32_t r;
+    asm("cvt.rn.relu.bf16x2.f32 %0, %2, %1;" : "=r"(r) : "f"(a), "f"(b));
+    return r;
+}
+
+// Writes 32 activation values (elements [32c, 32c + 32) of A) to TMEM,
+// through a ReLU when kRelu (fused into the BF16 conversion).
+template <bool F8, bool kRelu>
 __device__ __forceinline__ void st_act32(uint32_t tArow, int c, const float (&v)[32])
 {
     if constexpr (F8) {
         uint32_t o[8];
 #pragma unroll
-        for (int q = 0; q < 8; ++q) o[q] = pack_e4m3x4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+        for (int q = 0; q < 8; ++q) {
+            const float a0 = kRelu ? fmaxf(v[4 * q], 0.f) : v[4 * q];
+            const float a1 = kRelu ? fmaxf(v[4 * q + 1], 0.f) : v[4 * q + 1];
+            const float a2 = kRelu ? fmaxf(v[4 * q + 2], 0.f) : v[4 * q + 2];
+            const float a3 = kRelu ? fmaxf(v[4 * q + 3], 0.f) : v[4 * q + 3];
+            o[q] = pack_e4m3x4(a0, a1, a2, a3);
+        }
         tmem_st8(tArow + 8 * c, o);
     } else {
         uint32_t o[16];
 #pragma unroll
-        for (int q = 0; q < 16; ++q) o[q] = pack_bf16(v[2 * q], v[2 * q + 1]);
+        for (int q = 0; q < 16; ++q)
+            o[q] = kRelu ? pack_bf16_relu(v[2 * q], v[2 * q + 1]) : pack_bf16(v[2 * q], v[2 * q + 1]);
         tmem_st16(tArow + 16 * c, o);
     }
 }
@@ -282,7 +297,7 @@ __device__ __forceinline__ void encode1(float v, float (&s)[L], float (&c)[L])
 #pragma unroll
     for (int k = 0; k < L; ++k) {
         if (k == 0 || k == 5) {
-            sincospi_fast(ldexpf(v, k), s[k], c[k]);
+            sincospi_fast(v * (float)(1 << k), s[k], c[k]);     // exact scaling by 2^k
         } else {
             const float sp = s[k - 1], cp = c[k - 1];
             s[k] = 2.0f * sp * cp;
@@ -522,17 +537,13 @@ __global__ void __launch_bounds__(TcShape<W, H, F8>::kSlots * 128, 1)
                     e[6 + 6 * k + a] = cs[k];
                 }
             }
-            e[63] = 1.0f;
-            if (!valid) {
-#pragma unroll
-                for (int q = 0; q < 64; ++q) e[q] = 0.f;
-            }
+            e[63] = 1.0f;        // rows past the tile's count compute garbage that is never stored
 #pragma unroll
             for (int c = 0; c < 2; ++c) {
                 float v[32];
 #pragma unroll
                 for (int q = 0; q < 32; ++q) v[q] = e[32 * c + q];
-                st_act32<F8>(tArow, c, v);
+                st_act32<F8, false>(tArow, c, v);
             }
         }
         // the next tile's gathers overlap this tile's layers
@@ -618,11 +629,8 @@ __global__ void __launch_bounds__(TcShape<W, H, F8>::kSlots * 128, 1)
                             }
                         }
                     }
-                    if (l != H) {
-#pragma unroll
-                        for (int q = 0; q < 32; ++q) v[q] = fmaxf(v[q], 0.f);
-                    }
-                    st_act32<F8>(tArow, c, v);
+                    if (l == H) st_act32<F8, false>(tArow, c, v);
+                    else st_act32<F8, true>(tArow, c, v);
                 }
                 if (l == H) {
                     // density from column W of the head
@@ -633,7 +641,7 @@ __global__ void __launch_bounds__(TcShape<W, H, F8>::kSlots * 128, 1)
                 if (l == 0) {
                     // tail of A from here on: [1 | F(d) | 0 0 0 0] at columns W .. W+31
                     float e[32];
-                    e[0] = valid ? 1.0f : 0.0f;
+                    e[0] = 1.0f;
                     const float dv[3] = {sm.dx, sm.dy, sm.dz};
                     e[1] = dv[0]; e[2] = dv[1]; e[3] = dv[2];
 #pragma unroll
@@ -647,7 +655,7 @@ __global__ void __launch_bounds__(TcShape<W, H, F8>::kSlots * 128, 1)
                         }
                     }
                     e[28] = e[29] = e[30] = e[31] = 0.f;
-                    st_act32<F8>(tArow, W / 32, e);
+                    st_act32<F8, false>(tArow, W / 32, e);
                 }
             } else {
                 // colour layer: g = relu(z) in FP32, then rgb = sigmoid(Wo g + bo) with
@@ -675,7 +683,8 @@ __global__ void __launch_bounds__(TcShape<W, H, F8>::kSlots * 128, 1)
                     }
 #pragma unroll
                     for (int q = 0; q < 16; ++q) {
-                        const float gk = fmaxf(fmaf(__uint_as_float(r[c][q]), sc[q], bi[q]), 0.f);
+                        const float z = __uint_as_float(r[c][q]);
+                        const float gk = fmaxf(F8 ? fmaf(z, sc[q], bi[q]) : z, 0.f);
                         const float4 wk = wo[16 * c + q];
                         acc.x = fmaf(wk.x, gk, acc.x);
                         acc.y = fmaf(wk.y, gk, acc.y);
