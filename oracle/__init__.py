@@ -76,6 +76,11 @@ def lib():
         L.orc_rays_touching.argtypes = [i32p, f64p, D, i32p, f64p, I, u32p, I64, D, I, I, u8p]
         L.orc_rays_touching.restype = I
         L.orc_adam.argtypes = [I64, f64p, f64p, f64p, f64p, D, D, D, D, I]
+        L.orc_occupancy_update.argtypes = [i32p, f64p, D, f64p, f64p, I, f32p, f32p, f64p, u32p,
+                                           ctypes.POINTER(ctypes.c_int64)]
+        L.orc_occupancy_update.restype = I
+        L.orc_segment_voxels.argtypes = [i32p, f64p, D, f64p, f64p, D, ctypes.POINTER(ctypes.c_int64), I64]
+        L.orc_segment_voxels.restype = I64
         _lib = L
     return _lib
 
@@ -278,3 +283,46 @@ def adam(w, m, v, g, lr: float, step: int, b1: float = 0.9, b2: float = 0.99, ep
     lib().orc_adam(int(w.size), _p(w, ctypes.c_double), _p(m, ctypes.c_double), _p(v, ctypes.c_double),
                    _p(g, ctypes.c_double), lr, b1, b2, eps, int(step))
     return w, m, v
+
+
+# occupancy parameters: p_hit, p_miss, l_min, l_max, p_occ, a_min
+OCC_DEFAULT = (0.7, 0.4, -2.0, 3.5, 0.97, 0.5)
+
+
+def segment_voxels(dims, origin, vox: float, o, d, t_end: float) -> np.ndarray:
+    """Linear indices (x fastest) of the voxels whose interior o + t d,
+    0 < t < t_end, crosses, in traversal order."""
+    dims = np.ascontiguousarray(dims, dtype=np.int32)
+    org = np.ascontiguousarray(origin, dtype=np.float64)
+    o = np.ascontiguousarray(o, dtype=np.float64)
+    d = np.ascontiguousarray(d, dtype=np.float64)
+    cap = 4 * int(dims.sum()) + 16
+    out = np.zeros(cap, dtype=np.int64)
+    n = lib().orc_segment_voxels(_p(dims, ctypes.c_int32), _p(org, ctypes.c_double), float(vox),
+                                 _p(o, ctypes.c_double), _p(d, ctypes.c_double), float(t_end),
+                                 out.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), cap)
+    if n < 0:
+        raise ValueError("segment crosses too many voxels")
+    return out[:n].copy()
+
+
+def occupancy_update(dims, origin, vox: float, logit: np.ndarray, cams16, depth, opacity, params=OCC_DEFAULT):
+    """Eq. 6 over one scan per camera (in order).  logit: float64 [n_voxels],
+    updated in place.  Returns (occupancy bits u32 [n_voxels / 32],
+    near-tie count)."""
+    dims = np.ascontiguousarray(dims, dtype=np.int32)
+    org = np.ascontiguousarray([f32(v) for v in origin], dtype=np.float64)
+    cams = cams_f32(cams16)
+    dep = np.ascontiguousarray(depth, dtype=np.float32)
+    opa = np.ascontiguousarray(opacity, dtype=np.float32)
+    prm = np.ascontiguousarray(params, dtype=np.float64)
+    assert logit.dtype == np.float64 and logit.flags.c_contiguous
+    bits = np.zeros(int(np.prod(dims)) // 32, dtype=np.uint32)
+    ties = ctypes.c_int64(0)
+    rc = lib().orc_occupancy_update(_p(dims, ctypes.c_int32), _p(org, ctypes.c_double), f32(vox),
+                                    _p(logit, ctypes.c_double), _p(cams, ctypes.c_double), int(cams.shape[0]),
+                                    _p(dep, ctypes.c_float), _p(opa, ctypes.c_float), _p(prm, ctypes.c_double),
+                                    _p(bits, ctypes.c_uint32), ctypes.byref(ties))
+    if rc:
+        raise ValueError("orc_occupancy_update rejected its arguments")
+    return bits, int(ties.value)

@@ -25,6 +25,8 @@
  *   orc_render       all of the above per ray
  *   orc_loss_grad    L2 photometric loss of the fine-tuning stage and its
  *                    analytic reverse-mode gradient w.r.t. every MLP weight
+ *   orc_occupancy_update  the log-odds occupancy recursion of Eq. 6 over
+ *                    scans of rendered depth and opacity (Alg. 1 stage I)
  *
  * Readings of the paper taken here (the paper is silent or garbled on these):
  *   - pixel centres at (u + 1/2, v + 1/2);
@@ -861,4 +863,171 @@ void orc_adam(int64_t n, double *w, double *m, double *v, const double *g, doubl
         v[i] = b2 * v[i] + (1.0 - b2) * g[i] * g[i];
         w[i] -= lr * (m[i] / c1) / (sqrt(v[i] / c2) + eps);
     }
+}
+
+/* ------------------------------------------------------------------ */
+/* Progressive probabilistic occupancy (Eq. 6, Alg. 1 stage I)          */
+/* ------------------------------------------------------------------ */
+/*
+ * Reading of Eq. 6 taken here (the paper gives the log-odds recursion, the
+ * clamp [-2, 3.5], the 0.97 threshold, and that the measurement comes from
+ * a rendered depth map and an uncertainty obtained by normalising the
+ * weights of Eq. 5; it builds on Octomap's ray insertion):
+ *   - a pixel with opacity A = sum w_i (the normaliser of the weights) and
+ *     depth D = sum w_i t_i measures its ray's end point at
+ *     e = o + (D / A) d; pixels with A < a_min carry no measurement;
+ *   - per scan (one camera), every voxel whose interior the segment [o, e)
+ *     crosses is observed free, the voxel holding e is observed occupied,
+ *     occupied wins over free, and each voxel takes at most one update per
+ *     scan: L += logit(p_hit(A)) with p_hit(A) = 1/2 + (p_hit - 1/2) A (the
+ *     largest A among the rays ending in it), or L += logit(p_miss);
+ *   - L is clamped to [l_min, l_max] after every update; a voxel is occupied
+ *     iff L > logit(p_occ).
+ * The segment's voxels are found by their definition: every parameter at
+ * which the segment crosses a voxel plane is listed and sorted, and the
+ * voxel of each interval's midpoint is taken (intervals shorter than 1e-9
+ * voxel are reported as near-ties, where an incremental traversal may
+ * legitimately differ).
+ */
+
+static double logit_of(double p) { return log(p / (1.0 - p)); }
+
+static int dcmp(const void *a, const void *b)
+{
+    const double x = *(const double *)a, y = *(const double *)b;
+    return (x > y) - (x < y);
+}
+
+/* Voxels (linear indices x-fastest) crossed by the open segment between
+ * parameters 0 and t_end of o + t d, inside the grid.  Returns the count
+ * written to out (at most cap), or -1 on overflow; *ties counts intervals
+ * shorter than 1e-9 voxel. */
+static int64_t segment_voxels(const int32_t *dims, const double *origin, double vox, const double *o,
+                              const double *d, double t_end, int64_t *out, int64_t cap, int *ties)
+{
+    /* crossing parameters of every voxel plane between the two ends */
+    double len = 0.0;
+    for (int a = 0; a < 3; ++a) len += d[a] * d[a];
+    len = sqrt(len);
+    int64_t n_t = 0, cap_t = 4;
+    for (int a = 0; a < 3; ++a) cap_t += (int64_t)(fabs(d[a]) * t_end / vox) + 4;
+    double *ts = (double *)malloc(sizeof(double) * (size_t)cap_t);
+    if (!ts) return -1;
+    ts[n_t++] = 0.0;
+    ts[n_t++] = t_end;
+    for (int a = 0; a < 3; ++a) {
+        if (d[a] == 0.0) continue;
+        const double u0 = (o[a] - origin[a]) / vox, u1 = (o[a] + t_end * d[a] - origin[a]) / vox;
+        const double lo = fmin(u0, u1), hi = fmax(u0, u1);
+        for (double k = ceil(lo); k <= hi && n_t < cap_t; k += 1.0) {
+            const double t = (origin[a] + k * vox - o[a]) / d[a];
+            if (t > 0.0 && t < t_end) ts[n_t++] = t;
+        }
+    }
+    qsort(ts, (size_t)n_t, sizeof(double), dcmp);
+    int64_t n = 0;
+    for (int64_t i = 0; i + 1 < n_t; ++i) {
+        const double ta = ts[i], tb = ts[i + 1];
+        if (tb - ta <= 0.0) continue;
+        if ((tb - ta) * len < 1e-9 * vox) { if (ties) ++*ties; continue; }
+        const double tm = 0.5 * (ta + tb);
+        int64_t c[3];
+        int inside = 1;
+        for (int a = 0; a < 3; ++a) {
+            c[a] = (int64_t)floor((o[a] + tm * d[a] - origin[a]) / vox);
+            if (c[a] < 0 || c[a] >= dims[a]) inside = 0;
+        }
+        if (!inside) continue;
+        const int64_t v = (c[2] * dims[1] + c[1]) * dims[0] + c[0];
+        if (n > 0 && out[n - 1] == v) continue;
+        if (n >= cap) { free(ts); return -1; }
+        out[n++] = v;
+    }
+    free(ts);
+    return n;
+}
+
+/* One scan per camera, applied in camera order.  logit: double[n_voxels]
+ * (in/out); depth, opacity: per pixel of every view in order; params =
+ * (p_hit, p_miss, l_min, l_max, p_occ, a_min); bits (may be NULL): u32 words
+ * x-fastest, bit i of word w = voxel 32 w + i, set iff occupied.  ties
+ * (may be NULL) gets the number of near-tie intervals met.  Returns 0, or
+ * -1 on bad input. */
+int orc_occupancy_update(const int32_t *dims, const double *origin, double vox, double *logit,
+                         const double *cams, int n_views, const float *depth, const float *opacity,
+                         const double *params, uint32_t *bits, int64_t *ties_out)
+{
+    const double p_hit = params[0], p_miss = params[1], l_min = params[2], l_max = params[3];
+    const double p_occ = params[4], a_min = params[5];
+    const int64_t nv = (int64_t)dims[0] * dims[1] * dims[2];
+    double *conf = (double *)malloc(sizeof(double) * (size_t)nv);
+    uint8_t *miss = (uint8_t *)malloc((size_t)nv);
+    const int64_t cap = 4 * (int64_t)(dims[0] + dims[1] + dims[2]) + 16;
+    int64_t ties_total = 0;
+    if (!conf || !miss) { free(conf); free(miss); return -1; }
+    int64_t pix0 = 0;
+    for (int v = 0; v < n_views; ++v) {
+        const double *cam = cams + 16 * v;
+        const int64_t W = (int64_t)cam[1], H = (int64_t)cam[2];
+        for (int64_t i = 0; i < nv; ++i) { conf[i] = 0.0; miss[i] = 0; }
+        int64_t scan_ties = 0;
+#pragma omp parallel reduction(+ : scan_ties)
+        {
+            int64_t *vox_list = (int64_t *)malloc(sizeof(int64_t) * (size_t)cap);
+#pragma omp for schedule(dynamic, 256)
+            for (int64_t p = 0; p < W * H; ++p) {
+                const double A = (double)opacity[pix0 + p];
+                if (!(A >= a_min) || !vox_list) continue;
+                double o[3], d[3];
+                orc_ray(cam, (double)(p % W) + 0.5, (double)(p / W) + 0.5, o, d);
+                const double t_end = (double)depth[pix0 + p] / A;
+                int nt = 0;
+                const int64_t n = segment_voxels(dims, origin, vox, o, d, t_end, vox_list, cap, &nt);
+                scan_ties += nt;
+                for (int64_t k = 0; k < n; ++k) {
+#pragma omp atomic write
+                    miss[vox_list[k]] = 1;
+                }
+                int64_t c[3];
+                int inside = 1;
+                for (int a = 0; a < 3; ++a) {
+                    c[a] = (int64_t)floor((o[a] + t_end * d[a] - origin[a]) / vox);
+                    if (c[a] < 0 || c[a] >= dims[a]) inside = 0;
+                }
+                if (inside) {
+                    const int64_t e = (c[2] * dims[1] + c[1]) * dims[0] + c[0];
+#pragma omp critical(orc_occ_hit)
+                    if (A > conf[e]) conf[e] = A;
+                }
+            }
+            free(vox_list);
+        }
+        ties_total += scan_ties;
+        for (int64_t i = 0; i < nv; ++i) {
+            double upd = 0.0;
+            if (conf[i] > 0.0) upd = logit_of(0.5 + (p_hit - 0.5) * conf[i]);
+            else if (miss[i]) upd = logit_of(p_miss);
+            else continue;
+            double L = logit[i] + upd;
+            logit[i] = L < l_min ? l_min : (L > l_max ? l_max : L);
+        }
+        pix0 += W * H;
+    }
+    if (bits) {
+        const double thr = logit_of(p_occ);
+        for (int64_t w = 0; w < nv / 32; ++w) bits[w] = 0;
+        for (int64_t i = 0; i < nv; ++i)
+            if (logit[i] > thr) bits[i >> 5] |= 1u << (i & 31);
+    }
+    if (ties_out) *ties_out = ties_total;
+    free(conf);
+    free(miss);
+    return 0;
+}
+
+/* the segment traversal alone, for pins */
+int64_t orc_segment_voxels(const int32_t *dims, const double *origin, double vox, const double *o, const double *d,
+                           double t_end, int64_t *out, int64_t cap)
+{
+    return segment_voxels(dims, origin, vox, o, d, t_end, out, cap, NULL);
 }

@@ -650,3 +650,162 @@ def test_adam_first_steps_closed_form():
     # the moments are the exponential averages
     assert np.allclose(m, g * (1 - 0.9 ** 10), rtol=1e-12)
     assert np.allclose(v, g * g * (1 - 0.99 ** 10), rtol=1e-12)
+
+
+# ----------------------------------------------------------------------------
+# progressive probabilistic occupancy (Eq. 6, Alg. 1 stage I)
+# ----------------------------------------------------------------------------
+
+def _sigmoid(x):
+    return 1.0 / (1.0 + math.exp(-x))
+
+
+def test_occupancy_clamp_bounds_match_paper():
+    """The paper states the log-odds range [-2, 3.5] as occupancy
+    probabilities 0.12 and 0.97 (golden values)."""
+    import json, os
+    gold = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_values.json")))
+    occ = gold["occupancy"]
+    assert abs(_sigmoid(occ["logit_min"]) - occ["p_min"]) < 5e-3
+    assert abs(_sigmoid(occ["logit_max"]) - occ["p_max"]) < 5e-3
+    assert occ["logit_max"] > math.log(occ["p_occupied"] / (1 - occ["p_occupied"]))
+
+
+def test_segment_voxels_axis_aligned_closed_form():
+    dims, org, vox = (32, 32, 32), (0.0, 0.0, 0.0), 0.1
+    for axis in range(3):
+        for sgn in (1.0, -1.0):
+            o = np.array([1.55, 1.65, 1.75])
+            d = np.zeros(3)
+            d[axis] = sgn
+            got = O.segment_voxels(dims, org, vox, o, d, 0.93)
+            c0 = np.floor(o / vox).astype(int)
+            u_end = (o[axis] + sgn * 0.93) / vox
+            cells = np.arange(c0[axis], int(np.floor(u_end)) + sgn, int(sgn))
+            want = []
+            for k in cells:
+                c = c0.copy()
+                c[axis] = k
+                want.append((c[2] * 32 + c[1]) * 32 + c[0])
+            assert got.tolist() == want, (axis, sgn)
+
+
+def test_segment_voxels_match_dense_sampling():
+    """Random segments: the voxels met by points sampled every 1e-4 voxel
+    along the segment are exactly the traversal's voxels (no near-ties at
+    these random parameters)."""
+    rng = np.random.default_rng(6)
+    dims, org, vox = (32, 32, 32), (0.0, 0.0, 0.0), 0.1
+    for _ in range(20):
+        o = rng.uniform(0.2, 3.0, 3)
+        d = rng.normal(size=3)
+        d /= np.linalg.norm(d)
+        t_end = rng.uniform(0.05, 1.5)
+        got = O.segment_voxels(dims, org, vox, o, d, t_end)
+        ts = np.linspace(0, t_end, int(t_end / vox * 1e4) + 2)[1:-1]
+        pts = o[None, :] + ts[:, None] * d[None, :]
+        c = np.floor(pts / vox).astype(np.int64)
+        ok = np.all((c >= 0) & (c < 32), axis=1)
+        lin = (c[ok, 2] * 32 + c[ok, 1]) * 32 + c[ok, 0]
+        seq = lin[np.concatenate([[True], lin[1:] != lin[:-1]])]
+        assert got.tolist() == seq.tolist()
+
+
+def _cam_pixels(dirs, o):
+    """One 1x1 perspective view per direction, looking along it (its only
+    pixel's ray is the view axis)."""
+    cams = []
+    for d in dirs:
+        d = np.asarray(d, dtype=np.float64)
+        d = d / np.linalg.norm(d)
+        # camera z axis = d; any orthonormal completion
+        a = np.array([1.0, 0, 0]) if abs(d[0]) < 0.9 else np.array([0, 1.0, 0])
+        x = np.cross(a, d); x /= np.linalg.norm(x)
+        y = np.cross(d, x)
+        R = np.stack([x, y, d], axis=1)        # columns: camera axes in world
+        cams.append(F.Camera(F.PERSPECTIVE, 1, 1, 1.0, R, np.asarray(o, dtype=np.float64)))
+    return cams
+
+
+def test_occupancy_hits_clamp_and_threshold():
+    """One voxel hit by a confident ray in every scan: L grows by
+    logit(0.7) per scan, is clamped at 3.5, and the voxel becomes occupied
+    only once L > logit(0.97); the voxels before it go free, clamped at -2."""
+    dims, org, vox = (32, 32, 32), (0.0, 0.0, 0.0), 0.1
+    o = np.array([0.55, 1.65, 1.75])
+    cams = _cam_pixels([[1.0, 0, 0]] * 7, o)
+    cam16 = F.camera_array(cams)
+    o32 = O.cams_f32(cam16)[0, 13:16]
+    depth = np.full(7, 1.0, np.float32)        # end point 1.0 further along +x, A = 1
+    opac = np.ones(7, np.float32)
+    L = np.zeros(32 ** 3)
+    lh, lm = math.log(0.7 / 0.3), math.log(0.4 / 0.6)
+    for n in range(1, 8):
+        bits, _ = O.occupancy_update(dims, org, vox, L, cam16[n - 1:n], depth[:1], opac[:1])
+        e = np.floor((o32 + np.array([1.0, 0, 0])) / vox).astype(int)
+        ie = (e[2] * 32 + e[1]) * 32 + e[0]
+        assert abs(L[ie] - min(n * lh, 3.5)) < 1e-12
+        occupied = bool(bits[ie >> 5] >> (ie & 31) & 1)
+        assert occupied == (min(n * lh, 3.5) > math.log(0.97 / 0.03))
+        first = (np.floor(o32 / vox).astype(int))
+        i0 = (first[2] * 32 + first[1]) * 32 + first[0]
+        assert abs(L[i0] - max(n * lm, -2.0)) < 1e-12
+
+
+def test_occupancy_confidence_scaling_and_opacity_floor():
+    """A ray of opacity A ending in voxel v moves v by logit(1/2 + 0.2 A)
+    and every voxel it crosses by logit(0.4), nothing else; a ray below the
+    opacity floor (0.5) changes nothing."""
+    dims, org, vox = (32, 32, 32), (0.0, 0.0, 0.0), 0.1
+    o = np.array([0.55, 1.65, 1.75])
+    cam16 = F.camera_array(_cam_pixels([[1.0, 0, 0]], o))
+    L = np.zeros(32 ** 3)
+    a = float(np.float32(0.6))
+    O.occupancy_update(dims, org, vox, L, cam16, np.array([0.6], np.float32), np.array([0.6], np.float32))
+    o32 = O.cams_f32(cam16)[0, 13:16]
+    e = np.floor((o32 + np.array([1.0, 0, 0])) / vox).astype(int)
+    ie = (e[2] * 32 + e[1]) * 32 + e[0]
+    ph = 0.5 + 0.2 * a
+    assert abs(L[ie] - math.log(ph / (1 - ph))) < 1e-12
+    nz = np.nonzero(L)[0]
+    seg = O.segment_voxels(dims, org, vox, o32, np.array([1.0, 0, 0]), float(np.float32(0.6)) / a)
+    assert set(nz.tolist()) == set(seg.tolist()) | {ie}
+    assert np.allclose(L[seg[seg != ie]], math.log(0.4 / 0.6), atol=1e-12)
+    L2 = L.copy()
+    O.occupancy_update(dims, org, vox, L2, cam16, np.array([0.2], np.float32), np.array([0.45], np.float32))
+    assert np.array_equal(L, L2)
+
+
+def test_occupancy_scan_with_many_rays_matches_per_voxel_rules():
+    """A 16x8 equirect scan: every updated voxel took exactly one update --
+    a voxel where rays end takes the hit update of the largest opacity among
+    them (even if other rays cross it), a voxel only crossed takes one free
+    update however many rays cross it -- rebuilt here from the traversal
+    alone."""
+    dims, org, vox = (32, 32, 32), (0.0, 0.0, 0.0), 0.1
+    rng = np.random.default_rng(9)
+    cam = F.Camera(F.EQUIRECT, 16, 8, 0.0, F.yaw_pitch(0.4, 0.1), np.array([1.62, 1.57, 1.71]))
+    cam16 = F.camera_array([cam])
+    depth = rng.uniform(0.2, 1.2, 128).astype(np.float32)
+    opac = rng.uniform(0.3, 1.0, 128).astype(np.float32)
+    depth *= opac                               # D = A * (expected depth)
+    L = np.zeros(32 ** 3)
+    O.occupancy_update(dims, org, vox, L, cam16, depth, opac)
+    cf = O.cams_f32(cam16)[0]
+    conf, free = {}, set()
+    for p in range(128):
+        if opac[p] < 0.5:
+            continue
+        o, d = O.ray(cf, p % 16 + 0.5, p // 16 + 0.5)
+        t_end = float(depth[p]) / float(opac[p])
+        free |= set(O.segment_voxels(dims, org, vox, o, d, t_end).tolist())
+        e = np.floor((o + t_end * d) / vox).astype(int)
+        ie = int((e[2] * 32 + e[1]) * 32 + e[0])
+        conf[ie] = max(conf.get(ie, 0.0), float(opac[p]))
+    want = np.zeros(32 ** 3)
+    for i in free:
+        want[i] = math.log(0.4 / 0.6)
+    for i, a in conf.items():
+        ph = 0.5 + 0.2 * a
+        want[i] = math.log(ph / (1 - ph))
+    assert np.allclose(L, want, atol=1e-12)
