@@ -368,6 +368,42 @@ def multiview_bench(roam, F, torch, args, stream, flush):
     return out
 
 
+def occupancy_bench(roam, F, torch, args, stream):
+    """Progressive occupancy update (Eq. 6) on the floor256 lattice: depth
+    and opacity of 16 equirect 1024x512 views rendered once (BF16, untimed),
+    then 16 scans per step (ray traversal + per-voxel log-odds update)."""
+    import numpy as np
+    wl = F.floor256(views="equirect")
+    r = roam.Roam(torch.cuda.current_device())
+    r.load_workload(wl)
+    cams = F.make_cameras(wl.scene, 3, [(F.EQUIRECT, 1024, 512, 0.0)] * 16)
+    _, depth, op = r.render(cams, roam.render_opts(wl.delta, wl.n_max, precision=roam.ROAM_BF16))
+    n_vox = 256 ** 3
+    L = torch.zeros(n_vox, dtype=torch.float32, device="cuda")
+    bits = torch.zeros(n_vox // 32, dtype=torch.int32, device="cuda")
+    for _ in range(2):
+        r.occupancy_update(cams, depth, op, L, bits, stream=stream)
+    torch.cuda.synchronize()
+    steps = max(3, args.steps // 2)
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(steps):
+        r.occupancy_update(cams, depth, op, L, bits, stream=stream)
+    b.record(stream)
+    b.synchronize()
+    ms = a.elapsed_time(b) / steps
+    n_rays = 16 * 1024 * 512
+    occ = int(np.unpackbits(bits.cpu().numpy().view(np.uint8)).sum())
+    r.close()
+    # per scan the voxel pass reads the log-odds, hit word and free word and
+    # writes the occupancy word (the updated voxels' log-odds on top)
+    bytes_scan = n_vox * (4 + 4) + n_vox // 8 * 2
+    return {"workload": "floor256 lattice, 16 scans of 1024x512 equirect depth+opacity per step",
+            "ms_per_step": ms, "rays_per_s": n_rays / (ms / 1000.0),
+            "voxel_pass_min_bytes_per_scan": bytes_scan, "occupied_voxels_after": occ}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -519,10 +555,11 @@ def main():
     if rank == 0:
         train = train_step_bench(roam, F, torch, wl, args, stream)
 
-    large = multiview = None
+    large = multiview = occupancy = None
     if rank == 0:
         large = large_scene_bench(roam, F, torch, args, stream, flush, peaks)
         multiview = multiview_bench(roam, F, torch, args, stream, flush)
+        occupancy = occupancy_bench(roam, F, torch, args, stream)
 
     cpu = None
     if rank == 0 and world == 1:
@@ -540,6 +577,7 @@ def main():
                 "fp32_simt": {"value": f32_value, "unit": UNIT, "ms_per_step": t32 / max(3, args.steps // 2)},
                 "accuracy_vs_oracle": acc, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "train_step": train, "large_scene": large, "multi_view": multiview,
+                "occupancy_update": occupancy,
                 "gpu_launches": int(6 * st.n_rounds * args.steps), "clocks": clocks}
         print(json.dumps(line), flush=True)
     r.close()

@@ -198,6 +198,32 @@ roam_status roam_render(roam_ctx *ctx, const roam_camera *cams, int n_views,
                         const roam_render_opts *opts, float *rgb, float *depth, float *opacity,
                         int out_on_device, void *stream);
 
+/* Parameters of the occupancy update (Eq. 6): measurement probabilities of
+ * a confident end point (p_hit) and of a crossed voxel (p_miss), the
+ * log-odds clamp [l_min, l_max], the occupancy threshold p_occ, and the
+ * opacity below which a pixel carries no measurement (a_min).  The paper's
+ * values: l_min = -2, l_max = 3.5, p_occ = 0.97; the library's defaults
+ * p_hit = 0.7, p_miss = 0.4, a_min = 0.5 (24 bytes). */
+typedef struct {
+    float p_hit, p_miss, l_min, l_max, p_occ, a_min;
+} roam_occ_params;
+
+/* Progressive probabilistic occupancy update (Eq. 6; Alg. 1 stage I) on the
+ * loaded grid's voxel lattice, one scan per camera in order.  depth and
+ * opacity: device float per pixel of every view in order (roam_render's
+ * depth and opacity outputs: D = sum w t, A = sum w).  Each pixel with
+ * A >= a_min measures its ray's end point o + (D / A) d: the voxels whose
+ * interior the segment crosses are observed free, the end point's voxel
+ * occupied with confidence A (occupied wins; one update per voxel per scan:
+ * L += logit(1/2 + (p_hit - 1/2) A_max) or L += logit(p_miss)), then L is
+ * clamped to [l_min, l_max].  logit: device float[gz][gy][gx], in/out.
+ * bits (device, may be NULL): the occupancy bit grid (same layout as
+ * roam_load_grid; bit set iff L > logit(p_occ)) after the last scan.
+ * Asynchronous on `stream`. */
+roam_status roam_occupancy_update(roam_ctx *ctx, const roam_camera *cams, int n_views, const float *depth,
+                                  const float *opacity, const roam_occ_params *params, float *logit,
+                                  uint32_t *bits, void *stream);
+
 /* Chooses the round size (kept samples marched per live ray per round) for
  * this camera batch and these options: renders the batch once per candidate
  * (4, 8, 16, ... up to n_max, while the workspace fits in half the free

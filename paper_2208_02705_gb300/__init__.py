@@ -27,7 +27,7 @@ STATUS = {0: "ROAM_OK", -1: "ROAM_ERR_ARG", -2: "ROAM_ERR_OOM", -3: "ROAM_ERR_CU
 # every entry point declared in include/roam.h
 ENTRY_POINTS = ("roam_create", "roam_destroy", "roam_last_error", "roam_check", "roam_load_grid",
                 "roam_load_fields", "roam_load_weights", "roam_load_weights_mixed", "roam_get_weights", "roam_render",
-                "roam_get_stats", "roam_tune_round_size", "roam_march", "roam_bucket", "roam_mlp_eval", "roam_composite", "roam_train_forward",
+                "roam_get_stats", "roam_tune_round_size", "roam_occupancy_update", "roam_march", "roam_bucket", "roam_mlp_eval", "roam_composite", "roam_train_forward",
                 "roam_train_backward", "roam_adam_step", "roam_profile", "roam_profile_read",
                 "roam_bucket_static", "roam_l2_loss")
 
@@ -50,6 +50,18 @@ class roam_mlp_desc(ctypes.Structure):
 class roam_camera(ctypes.Structure):
     _fields_ = [("model", ctypes.c_int32), ("width", ctypes.c_int32), ("height", ctypes.c_int32),
                 ("fov_h", ctypes.c_float), ("R", ctypes.c_float * 9), ("o", ctypes.c_float * 3)]
+
+
+class roam_occ_params(ctypes.Structure):
+    _fields_ = [("p_hit", ctypes.c_float), ("p_miss", ctypes.c_float), ("l_min", ctypes.c_float),
+                ("l_max", ctypes.c_float), ("p_occ", ctypes.c_float), ("a_min", ctypes.c_float)]
+
+
+def occ_params(p_hit: float = 0.7, p_miss: float = 0.4, l_min: float = -2.0, l_max: float = 3.5,
+               p_occ: float = 0.97, a_min: float = 0.5) -> roam_occ_params:
+    q = roam_occ_params()
+    q.p_hit, q.p_miss, q.l_min, q.l_max, q.p_occ, q.a_min = p_hit, p_miss, l_min, l_max, p_occ, a_min
+    return q
 
 
 class roam_render_opts(ctypes.Structure):
@@ -95,6 +107,7 @@ def load_library(path: str = LIB_PATH):
     L.roam_load_weights.argtypes = [vp, P(roam_mlp_desc), vp, i32]
     L.roam_load_weights_mixed.argtypes = [vp, P(roam_mlp_desc), vp, vp, i32]
     L.roam_tune_round_size.argtypes = [vp, vp, i32, P(roam_render_opts), vp, vp, vp]
+    L.roam_occupancy_update.argtypes = [vp, vp, i32, vp, vp, P(roam_occ_params), vp, vp, vp]
     L.roam_get_weights.argtypes = [vp, vp, i32]
     L.roam_render.argtypes = [vp, P(roam_camera), i32, P(roam_render_opts), vp, vp, vp, i32, vp]
     L.roam_get_stats.argtypes = [vp, P(roam_stats)]
@@ -295,6 +308,16 @@ class Roam:
         _check(self.L.roam_tune_round_size(self.h, arr, len(cams), ctypes.byref(opts), ctypes.byref(best),
                                            ctypes.byref(ms), _stream(stream)))
         return int(best.value), float(ms.value)
+
+    def occupancy_update(self, cams, depth, opacity, logit, bits=None, params=None, stream=None):
+        """roam_occupancy_update: one scan per camera of (depth, opacity)
+        device tensors; logit (device float, one per voxel) is updated in
+        place; bits (device int32 words) receives the occupancy grid."""
+        arr = camera_array(cams)
+        q = params if params is not None else occ_params()
+        _check(self.L.roam_occupancy_update(self.h, arr, len(cams), _ptr(depth), _ptr(opacity), ctypes.byref(q),
+                                            _ptr(logit), _ptr(bits), _stream(stream)))
+        return logit, bits
 
     def get_stats(self) -> roam_stats:
         s = roam_stats()

@@ -40,6 +40,34 @@ struct GridDev {
     int n_fields;
 };
 
+// World direction of pixel `pix` of a view in FP64 (Eq. 2 and Eq. 3 for
+// equirectangular views, the pinhole model for perspective ones).
+__device__ __forceinline__ void make_ray64(const DevCamera &c, uint32_t pix, double3 &d)
+{
+    const uint32_t u = pix % (uint32_t)c.width, v = pix / (uint32_t)c.width;
+    double d0, d1, d2;
+    if (c.model == ROAM_EQUIRECT) {
+        const double pu = 2.0 * (((double)u + 0.5) / (double)c.width) - 1.0;
+        const double tv = 0.5 - ((double)v + 0.5) / (double)c.height;
+        double sp, cp, st, ct;
+        sincospi(pu, &sp, &cp);
+        sincospi(tv, &st, &ct);
+        d0 = ct * sp;
+        d1 = -st;
+        d2 = ct * cp;
+    } else {
+        const double x = ((double)u + 0.5 - 0.5 * (double)c.width) * c.inv_f64;
+        const double y = ((double)v + 0.5 - 0.5 * (double)c.height) * c.inv_f64;
+        const double n = 1.0 / sqrt(x * x + y * y + 1.0);
+        d0 = x * n;
+        d1 = y * n;
+        d2 = n;
+    }
+    d.x = (double)c.R[0] * d0 + (double)c.R[1] * d1 + (double)c.R[2] * d2;
+    d.y = (double)c.R[3] * d0 + (double)c.R[4] * d1 + (double)c.R[5] * d2;
+    d.z = (double)c.R[6] * d0 + (double)c.R[7] * d1 + (double)c.R[8] * d2;
+}
+
 // Device counters of one render / training pass.
 struct Counters {
     uint32_t live_count[2];
@@ -150,6 +178,9 @@ void launch_grid_prefix(const uint32_t *bits, uint32_t *prefix, uint32_t *block_
                         int64_t n_words, cudaStream_t s);
 void launch_brick_dist(GridDev g, uint8_t *occ, uint16_t *t0, uint16_t *t1, uint8_t *dist, cudaStream_t s);
 void launch_march(const GridDev &g, const MarchParams &p, int grid, cudaStream_t s);
+void launch_occupancy_scan(const GridDev &g, const DevCamera *cams, int view, int n_pix, const float *depth,
+                           const float *opacity, const roam_occ_params &q, uint32_t *hit, uint32_t *free_bits,
+                           float *logit, uint32_t *bits, int n_sm, cudaStream_t s);
 // tiles of `tile` samples, every non-empty field's tile count rounded up to a
 // multiple of `group`; with hist_ready the histogram is already in b.hist
 void launch_bucket_ready(const uint32_t *cnt, const uint32_t *recs, const uint32_t *live_count,

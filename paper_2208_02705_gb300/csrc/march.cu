@@ -162,32 +162,6 @@ __device__ __forceinline__ void make_ray(const DevCamera &c, uint32_t pix, float
 
 // The same ray direction in FP64, for the FP32 render path: its sample
 // positions feed 2^9 pi frequencies, so the direction carries a residual.
-__device__ __forceinline__ void make_ray64(const DevCamera &c, uint32_t pix, double3 &d)
-{
-    const uint32_t u = pix % (uint32_t)c.width, v = pix / (uint32_t)c.width;
-    double d0, d1, d2;
-    if (c.model == ROAM_EQUIRECT) {
-        const double pu = 2.0 * (((double)u + 0.5) / (double)c.width) - 1.0;
-        const double tv = 0.5 - ((double)v + 0.5) / (double)c.height;
-        double sp, cp, st, ct;
-        sincospi(pu, &sp, &cp);
-        sincospi(tv, &st, &ct);
-        d0 = ct * sp;
-        d1 = -st;
-        d2 = ct * cp;
-    } else {
-        const double x = ((double)u + 0.5 - 0.5 * (double)c.width) * c.inv_f64;
-        const double y = ((double)v + 0.5 - 0.5 * (double)c.height) * c.inv_f64;
-        const double n = 1.0 / sqrt(x * x + y * y + 1.0);
-        d0 = x * n;
-        d1 = y * n;
-        d2 = n;
-    }
-    d.x = (double)c.R[0] * d0 + (double)c.R[1] * d1 + (double)c.R[2] * d2;
-    d.y = (double)c.R[3] * d0 + (double)c.R[4] * d1 + (double)c.R[5] * d2;
-    d.z = (double)c.R[6] * d0 + (double)c.R[7] * d1 + (double)c.R[8] * d2;
-}
-
 __device__ __forceinline__ int view_of(const DevCamera *cams, int n_views, uint32_t gpix)
 {
     int lo = 0, hi = n_views - 1;

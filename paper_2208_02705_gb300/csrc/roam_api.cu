@@ -140,6 +140,7 @@ struct roam_ctx {
     DBuf<Tile> tiles;
     DBuf<float> o_rgb, o_depth, o_op;
     DBuf<DevCamera> cams;
+    DBuf<uint32_t> occ_hit, occ_free;        // occupancy update marks (per voxel, per 32 voxels)
     // pinned staging of the camera uploads: a ring, so that consecutive calls
     // (e.g. one per view) do not wait for each other's copies
     static constexpr int kCamRing = 8;
@@ -729,6 +730,7 @@ roam_status roam_destroy(roam_ctx *c)
     for (WSet &q : c->ws) {
         release(q.w32); release(q.wt); release(q.wr); release(q.wimg); release(q.wimg8);
     }
+    release(c->occ_hit); release(c->occ_free);
     release(c->perm); release(c->inv); release(c->labels_orig); release(c->keys_tmp);
     release(c->gsr); release(c->adam_m); release(c->adam_v);
     release(c->orig); release(c->dir); release(c->dir_lo); release(c->acc); release(c->sr); release(c->tw);
@@ -1065,6 +1067,34 @@ roam_status roam_tune_round_size(roam_ctx *c, const roam_camera *cams, int n_vie
     if (best_ms) *best_ms = best_t;
     ROAM_CUDA(cudaMemcpy(c->h_ctr, c->ctr, sizeof(Counters), cudaMemcpyDeviceToHost));
     return status_of(c->h_ctr->status);
+}
+
+roam_status roam_occupancy_update(roam_ctx *c, const roam_camera *cams, int n_views, const float *depth,
+                                  const float *opacity, const roam_occ_params *q, float *logit, uint32_t *bits,
+                                  void *stream)
+{
+    ROAM_TRY(set_dev(c));
+    if (!c->has_grid) return fail(ROAM_ERR_STATE, "load the occupancy grid first (it fixes the voxel lattice)");
+    if (!q || !depth || !opacity || !logit) return fail(ROAM_ERR_ARG, "null pointer");
+    if (!(q->p_hit > 0.5f && q->p_hit < 1.f) || !(q->p_miss > 0.f && q->p_miss < 0.5f) || !(q->l_min < 0.f) ||
+        !(q->l_max > 0.f) || !(q->p_occ > 0.f && q->p_occ < 1.f) || !(q->a_min > 0.f && q->a_min <= 1.f) ||
+        !finite(q->l_min) || !finite(q->l_max))
+        return fail(ROAM_ERR_ARG, "bad occupancy parameters");
+    cudaStream_t s = (cudaStream_t)stream;
+    int64_t n_pix = 0;
+    ROAM_TRY(upload_cams(c, cams, n_views, 0.25f * c->gd.vox, &n_pix, s));
+    const int64_t n_vox = (int64_t)c->g.gx * c->g.gy * c->g.gz;
+    ROAM_TRY(ensure(c->occ_hit, (size_t)n_vox));
+    ROAM_TRY(ensure(c->occ_free, (size_t)(n_vox / 32)));
+    ROAM_CUDA(cudaMemsetAsync(c->occ_hit.p, 0, (size_t)n_vox * 4, s));
+    ROAM_CUDA(cudaMemsetAsync(c->occ_free.p, 0, (size_t)(n_vox / 32) * 4, s));
+    for (int v = 0; v < n_views; ++v) {
+        launch_occupancy_scan(c->g, c->cams.p, v, cams[v].width * cams[v].height, depth, opacity, *q, c->occ_hit.p,
+                              c->occ_free.p, logit, bits, c->n_sm, s);
+        ROAM_TRY(launched("occupancy scan"));
+    }
+    c->last = s;
+    return ROAM_OK;
 }
 
 roam_status roam_get_stats(roam_ctx *c, roam_stats *st)
