@@ -404,6 +404,26 @@ def occupancy_bench(roam, F, torch, args, stream):
             "voxel_pass_min_bytes_per_scan": bytes_scan, "occupied_voxels_after": occ}
 
 
+def stereo_bench(roam, F, torch, stream):
+    """Stereoscopic roaming on the floor256 scene: a 120-frame walk, both
+    eyes (1280x720 perspective, 90 degree FOV, 64 mm apart) rendered in one
+    graph-replayed BF16 call per frame; per-frame device latency."""
+    import numpy as np
+    from paper_2208_02705_gb300.roaming import roam_frames
+    wl = F.floor256(views="equirect")
+    r = roam.Roam(torch.cuda.current_device())
+    r.load_workload(wl)
+    poses = F.roaming_path(wl.scene, 2, 128)
+    gopts = roam.render_opts(wl.delta, wl.n_max, precision=roam.ROAM_BF16, use_graph=True)
+    roam_frames(r, poses[:8], gopts, stream=stream)           # capture + warm-up
+    times, _ = roam_frames(r, poses[8:], gopts, stream=stream)
+    r.close()
+    t = np.array(times)
+    return {"workload": "floor256_kd512_w64h3, 120-frame walk, 2 x 1280x720 perspective eyes per frame",
+            "frame_ms_median": float(np.median(t)), "frame_ms_p95": float(np.percentile(t, 95)),
+            "fps_at_median": 1000.0 / float(np.median(t))}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -555,11 +575,12 @@ def main():
     if rank == 0:
         train = train_step_bench(roam, F, torch, wl, args, stream)
 
-    large = multiview = occupancy = None
+    large = multiview = occupancy = stereo = None
     if rank == 0:
         large = large_scene_bench(roam, F, torch, args, stream, flush, peaks)
         multiview = multiview_bench(roam, F, torch, args, stream, flush)
         occupancy = occupancy_bench(roam, F, torch, args, stream)
+        stereo = stereo_bench(roam, F, torch, stream)
 
     cpu = None
     if rank == 0 and world == 1:
@@ -577,7 +598,7 @@ def main():
                 "fp32_simt": {"value": f32_value, "unit": UNIT, "ms_per_step": t32 / max(3, args.steps // 2)},
                 "accuracy_vs_oracle": acc, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "train_step": train, "large_scene": large, "multi_view": multiview,
-                "occupancy_update": occupancy,
+                "occupancy_update": occupancy, "stereo_roaming": stereo,
                 "gpu_launches": int(6 * st.n_rounds * args.steps), "clocks": clocks}
         print(json.dumps(line), flush=True)
     r.close()

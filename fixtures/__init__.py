@@ -540,3 +540,27 @@ def floor384(n_fields: int = 2048, H: int = 3, role: int = ROLE_TEACHER, specs=N
     cams = make_cameras(scene, 4, specs if specs is not None else multiview_specs())
     return Workload(f"floor384_kd{n_fields}_mixedw_h{H}", scene, part, field_affine(scene, part), 0, H, w,
                     density_scale(delta), delta, 128, cams, widths=widths)
+
+
+def roaming_path(scene: Scene, workload: int, n_frames: int, width: int = 1280, height: int = 720,
+                 fov_h: float = math.pi / 2, step: float = 0.02) -> List[Camera]:
+    """A walk through one room: start at a seeded free voxel, move `step`
+    per frame along a seeded heading at eye height, turning slowly, and turn
+    back at occupied voxels; one perspective camera per frame."""
+    rng = rng_for(workload, ROLE_CAMERAS)
+    o = random_free_position(scene, rng)
+    yaw = float(rng.uniform(0, 2 * math.pi))
+    cams = []
+    for _ in range(n_frames):
+        R = yaw_pitch(yaw, 0.0)
+        fwd = R[:, 2]
+        nxt = o + step * fwd
+        c = np.floor((nxt - np.asarray(scene.origin)) / scene.vox).astype(int)
+        inside = np.all(c >= 0) and np.all(c < np.asarray(scene.dims))
+        if not inside or scene.occ[c[2], c[1], c[0]]:
+            yaw += math.pi * 0.75
+        else:
+            o = nxt
+        yaw += 0.01
+        cams.append(Camera(PERSPECTIVE, width, height, fov_h, yaw_pitch(yaw, 0.0), o.copy()))
+    return cams
