@@ -81,6 +81,8 @@ def lib():
         L.orc_occupancy_update.restype = I
         L.orc_segment_voxels.argtypes = [i32p, f64p, D, f64p, f64p, D, ctypes.POINTER(ctypes.c_int64), I64]
         L.orc_segment_voxels.restype = I64
+        L.orc_assign_fields.argtypes = [i32p, ctypes.POINTER(ctypes.c_int64), I64, I, i32p]
+        L.orc_assign_fields.restype = I
         _lib = L
     return _lib
 
@@ -326,3 +328,16 @@ def occupancy_update(dims, origin, vox: float, logit: np.ndarray, cams16, depth,
     if rc:
         raise ValueError("orc_occupancy_update rejected its arguments")
     return bits, int(ties.value)
+
+
+def assign_fields(dims, occ_linear: np.ndarray, n: int) -> np.ndarray:
+    """Alg. 1 stage II: network id (int32) of every occupied voxel, the
+    voxels given by their linear indices (x fastest) in increasing order."""
+    dims = np.ascontiguousarray(dims, dtype=np.int32)
+    idx = np.ascontiguousarray(occ_linear, dtype=np.int64)
+    out = np.zeros(idx.size, dtype=np.int32)
+    rc = lib().orc_assign_fields(_p(dims, ctypes.c_int32), idx.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                                 int(idx.size), int(n), _p(out, ctypes.c_int32))
+    if rc:
+        raise ValueError("orc_assign_fields rejected its arguments")
+    return out

@@ -27,6 +27,8 @@
  *                    analytic reverse-mode gradient w.r.t. every MLP weight
  *   orc_occupancy_update  the log-odds occupancy recursion of Eq. 6 over
  *                    scans of rendered depth and opacity (Alg. 1 stage I)
+ *   orc_assign_fields  the anchor + nearest-neighbour assignment of occupied
+ *                    voxels to networks (Alg. 1 stage II)
  *
  * Readings of the paper taken here (the paper is silent or garbled on these):
  *   - pixel centres at (u + 1/2, v + 1/2);
@@ -1030,4 +1032,80 @@ int64_t orc_segment_voxels(const int32_t *dims, const double *origin, double vox
                            double t_end, int64_t *out, int64_t cap)
 {
     return segment_voxels(dims, origin, vox, o, d, t_end, out, cap, NULL);
+}
+
+/* ------------------------------------------------------------------ */
+/* Adaptive assignment of occupied voxels to networks (Alg. 1 stage II) */
+/* ------------------------------------------------------------------ */
+/*
+ * Readings taken (the algorithm leaves them open): the "minimum coordinate"
+ * is the lexicographic (z, y, x) minimum, i.e. the smallest linear index
+ * (x fastest); the s - 1 "nearest neighbours" are the unassigned occupied
+ * voxels of smallest squared distance to the anchor (voxel units), ties
+ * broken by the smaller linear index; s = S / n (integer division) and the
+ * last network takes every voxel still unassigned.
+ */
+
+static void swap_u64(uint64_t *a, uint64_t *b) { uint64_t t = *a; *a = *b; *b = t; }
+
+/* rearranges a[0..n) so that a[k] is the k-th smallest (0-based), smaller
+ * ones before it */
+static void quickselect_u64(uint64_t *a, int64_t n, int64_t k)
+{
+    int64_t lo = 0, hi = n - 1;
+    uint64_t seed = 88172645463325252ull;
+    while (lo < hi) {
+        seed ^= seed << 13; seed ^= seed >> 7; seed ^= seed << 17;
+        const int64_t pi = lo + (int64_t)(seed % (uint64_t)(hi - lo + 1));
+        const uint64_t pivot = a[pi];
+        swap_u64(&a[pi], &a[hi]);
+        int64_t st = lo;
+        for (int64_t i = lo; i < hi; ++i)
+            if (a[i] < pivot) swap_u64(&a[i], &a[st++]);
+        swap_u64(&a[st], &a[hi]);
+        if (st == k) return;
+        if (st < k) lo = st + 1; else hi = st - 1;
+    }
+}
+
+/* occupied voxels given by their linear indices in increasing order
+ * (vox_idx[S], dims x-fastest); writes field[S].  Returns 0, or -1. */
+int orc_assign_fields(const int32_t *dims, const int64_t *vox_idx, int64_t S, int n, int32_t *field)
+{
+    if (n < 1 || S < n) return -1;
+    const int64_t s = S / n;
+    uint8_t *done = (uint8_t *)calloc((size_t)S, 1);
+    uint64_t *keys = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)S);
+    if (!done || !keys) { free(done); free(keys); return -1; }
+    int64_t cursor = 0;                      /* every position before it is assigned */
+    for (int k = 0; k < n; ++k) {
+        while (cursor < S && done[cursor]) ++cursor;
+        if (k == n - 1) {
+            for (int64_t i = cursor; i < S; ++i)
+                if (!done[i]) { field[i] = k; done[i] = 1; }
+            break;
+        }
+        const int64_t a = cursor;            /* anchor: smallest unassigned linear index */
+        const int64_t ax = vox_idx[a] % dims[0], ay = (vox_idx[a] / dims[0]) % dims[1],
+                      az = vox_idx[a] / ((int64_t)dims[0] * dims[1]);
+        int64_t m = 0;
+        for (int64_t i = a; i < S; ++i) {
+            if (done[i]) continue;
+            const int64_t x = vox_idx[i] % dims[0], y = (vox_idx[i] / dims[0]) % dims[1],
+                          z = vox_idx[i] / ((int64_t)dims[0] * dims[1]);
+            const uint64_t d2 = (uint64_t)((x - ax) * (x - ax) + (y - ay) * (y - ay) + (z - az) * (z - az));
+            keys[m++] = (d2 << 32) | (uint64_t)i;    /* position order = linear-index order */
+        }
+        /* the anchor (distance 0, smallest index) and its s - 1 nearest */
+        if (s < m) quickselect_u64(keys, m, s - 1);
+        const int64_t take = s < m ? s : m;
+        for (int64_t q = 0; q < take; ++q) {
+            const int64_t i = (int64_t)(keys[q] & 0xffffffffull);
+            field[i] = k;
+            done[i] = 1;
+        }
+    }
+    free(done);
+    free(keys);
+    return 0;
 }

@@ -809,3 +809,48 @@ def test_occupancy_scan_with_many_rays_matches_per_voxel_rules():
         ph = 0.5 + 0.2 * a
         want[i] = math.log(ph / (1 - ph))
     assert np.allclose(L, want, atol=1e-12)
+
+
+# ----------------------------------------------------------------------------
+# adaptive assignment of occupied voxels to networks (Alg. 1 stage II)
+# ----------------------------------------------------------------------------
+
+def test_assign_fields_line_is_contiguous_runs():
+    """Occupied voxels on one row: every anchor is the leftmost unassigned
+    voxel and its nearest unassigned neighbours are the next ones to the
+    right, so networks are runs of s = S // n (the last takes the rest)."""
+    dims = (64, 4, 4)
+    S, n = 61, 6
+    lin = np.arange(S, dtype=np.int64)          # x = 0..60, y = z = 0
+    f = O.assign_fields(dims, lin, n)
+    s = S // n
+    assert np.array_equal(f, np.minimum(np.arange(S) // s, n - 1))
+
+
+def _assign_brute(dims, lin, n):
+    gx, gy = dims[0], dims[1]
+    xyz = np.stack([lin % gx, (lin // gx) % gy, lin // (gx * gy)], axis=1)
+    S = lin.size
+    s = S // n
+    field = np.full(S, -1)
+    for k in range(n):
+        free = np.nonzero(field < 0)[0]
+        if k == n - 1:
+            field[free] = k
+            break
+        a = free[np.argmin(lin[free])]
+        d2 = ((xyz[free] - xyz[a]) ** 2).sum(axis=1)
+        order = np.lexsort((lin[free], d2))      # by distance, then by linear index
+        field[free[order[:s]]] = k
+    return field
+
+
+def test_assign_fields_matches_full_sort():
+    rng = np.random.default_rng(12)
+    for dims, S, n in [((32, 8, 8), 300, 7), ((16, 16, 16), 500, 13), ((32, 32, 32), 1000, 10)]:
+        total = dims[0] * dims[1] * dims[2]
+        lin = np.sort(rng.choice(total, S, replace=False)).astype(np.int64)
+        f = O.assign_fields(dims, lin, n)
+        assert np.array_equal(f, _assign_brute(dims, lin, n))
+        counts = np.bincount(f, minlength=n)
+        assert np.all(counts[:-1] == S // n) and counts[-1] == S - (n - 1) * (S // n)
