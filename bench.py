@@ -424,6 +424,55 @@ def stereo_bench(roam, F, torch, stream):
             "fps_at_median": 1000.0 / float(np.median(t))}
 
 
+def partition_bench(roam, F, torch, args, stream, flush):
+    """Partitions of the floor256 scene into 512 fields compared on the
+    1024x512 equirect view (W=64/H=3, BF16): kd (median splits), Alg. 1
+    stage II (anchor + nearest neighbours, computed on the GPU) and the
+    uniform 8x8x8 split -- samples per field, tile padding and MLP time."""
+    import numpy as np
+    wl = F.floor256(views="equirect")
+    out = {"workload": "floor256, 512 fields, W=64 H=3, 1024x512 equirect, BF16", "partitions": {}}
+    r = roam.Roam(torch.cuda.current_device())
+    r.load_grid(wl.scene.bits, wl.scene.dims, wl.scene.origin, wl.scene.vox)
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    labels, boxes = r.assign_fields(512, stream=stream)
+    b.record(stream)
+    b.synchronize()
+    alg1 = F.Partition(boxes.cpu().numpy().reshape(512, 2, 3).astype(np.int32),
+                       labels.cpu().numpy().view(np.uint16).copy())
+    out["alg1_assign_ms"] = a.elapsed_time(b)
+    parts = {"kd_median": wl.part, "alg1_nearest": alg1, "uniform_8x8x8": F.uniform_partition(wl.scene, (8, 8, 8))}
+    w = F.xavier_weights(2, F.ROLE_TEACHER, 512, 64, 3)
+    for name, part in parts.items():
+        r.load_fields(part.field_of_rank, F.field_affine(wl.scene, part))
+        r.load_weights(w, 64, 3, wl.sigma_scale)
+        opts = roam.render_opts(wl.delta, wl.n_max, precision=roam.ROAM_BF16)
+        cnt, recs = r.march(wl.cams, roam.render_opts(wl.delta, wl.n_max))
+        k = torch.arange(wl.n_max, device=cnt.device)[None, :] < cnt[:, None].long()
+        per = torch.bincount((recs[k].long() >> 16) & 0xffff, minlength=512).cpu().numpy()
+        used = per[per > 0]
+        tiles = int(np.sum(np.ceil(used / 128 / 4) * 4))
+        for _ in range(3):
+            r.render(wl.cams, opts, stream=stream)
+        torch.cuda.synchronize()
+        r.profile(True)
+        tot, frame = time_steps(r, wl.cams, opts, max(3, args.steps // 2), 0, flush, stream)
+        prof = r.profile_read()
+        r.profile(False)
+        st = r.get_stats()
+        steps = max(3, args.steps // 2)
+        out["partitions"][name] = {
+            "fields_with_samples": int(used.size), "marched_samples_max_per_field": int(per.max()),
+            "marched_samples_mean_per_field": float(used.mean()), "cv": float(used.std() / used.mean()),
+            "tiles_all_marched": tiles, "tile_fill": float(per.sum() / (tiles * 128)),
+            "frame_ms": statistics.median(frame), "mlp_ms": prof["mlp_bf16_tcgen05"][1] / steps,
+            "evaluated_per_frame": int(st.n_samples)}
+    r.close()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -575,12 +624,13 @@ def main():
     if rank == 0:
         train = train_step_bench(roam, F, torch, wl, args, stream)
 
-    large = multiview = occupancy = stereo = None
+    large = multiview = occupancy = stereo = partition = None
     if rank == 0:
         large = large_scene_bench(roam, F, torch, args, stream, flush, peaks)
         multiview = multiview_bench(roam, F, torch, args, stream, flush)
         occupancy = occupancy_bench(roam, F, torch, args, stream)
         stereo = stereo_bench(roam, F, torch, stream)
+        partition = partition_bench(roam, F, torch, args, stream, flush)
 
     cpu = None
     if rank == 0 and world == 1:
@@ -599,6 +649,7 @@ def main():
                 "accuracy_vs_oracle": acc, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "train_step": train, "large_scene": large, "multi_view": multiview,
                 "occupancy_update": occupancy, "stereo_roaming": stereo,
+                "partitions": partition,
                 "gpu_launches": int(6 * st.n_rounds * args.steps), "clocks": clocks}
         print(json.dumps(line), flush=True)
     r.close()

@@ -224,6 +224,17 @@ roam_status roam_occupancy_update(roam_ctx *ctx, const roam_camera *cams, int n_
                                   const float *opacity, const roam_occ_params *params, float *logit,
                                   uint32_t *bits, void *stream);
 
+/* Adaptive assignment of the loaded grid's occupied voxels to n_fields
+ * networks (Alg. 1 stage II): network k takes the smallest unassigned voxel
+ * (lexicographic (z, y, x): the smallest linear index) as its anchor and
+ * the s - 1 unassigned voxels nearest to it (squared distance in voxel
+ * units, ties to the smaller linear index), s = S / n_fields; the last
+ * network takes every voxel left.  labels: device uint16[S], the network of
+ * every occupied voxel in rank order (the layout roam_load_fields takes);
+ * boxes (device int32[n_fields][6], may be NULL): each network's voxel
+ * bounding box (min x, y, z, max x, y, z exclusive).  Synchronises. */
+roam_status roam_assign_fields(roam_ctx *ctx, int n_fields, uint16_t *labels, int32_t *boxes, void *stream);
+
 /* Chooses the round size (kept samples marched per live ray per round) for
  * this camera batch and these options: renders the batch once per candidate
  * (4, 8, 16, ... up to n_max, while the workspace fits in half the free

@@ -27,7 +27,7 @@ STATUS = {0: "ROAM_OK", -1: "ROAM_ERR_ARG", -2: "ROAM_ERR_OOM", -3: "ROAM_ERR_CU
 # every entry point declared in include/roam.h
 ENTRY_POINTS = ("roam_create", "roam_destroy", "roam_last_error", "roam_check", "roam_load_grid",
                 "roam_load_fields", "roam_load_weights", "roam_load_weights_mixed", "roam_get_weights", "roam_render",
-                "roam_get_stats", "roam_tune_round_size", "roam_occupancy_update", "roam_march", "roam_bucket", "roam_mlp_eval", "roam_composite", "roam_train_forward",
+                "roam_get_stats", "roam_tune_round_size", "roam_occupancy_update", "roam_assign_fields", "roam_march", "roam_bucket", "roam_mlp_eval", "roam_composite", "roam_train_forward",
                 "roam_train_backward", "roam_adam_step", "roam_profile", "roam_profile_read",
                 "roam_bucket_static", "roam_l2_loss")
 
@@ -108,6 +108,7 @@ def load_library(path: str = LIB_PATH):
     L.roam_load_weights_mixed.argtypes = [vp, P(roam_mlp_desc), vp, vp, i32]
     L.roam_tune_round_size.argtypes = [vp, vp, i32, P(roam_render_opts), vp, vp, vp]
     L.roam_occupancy_update.argtypes = [vp, vp, i32, vp, vp, P(roam_occ_params), vp, vp, vp]
+    L.roam_assign_fields.argtypes = [vp, i32, vp, vp, vp]
     L.roam_get_weights.argtypes = [vp, vp, i32]
     L.roam_render.argtypes = [vp, P(roam_camera), i32, P(roam_render_opts), vp, vp, vp, i32, vp]
     L.roam_get_stats.argtypes = [vp, P(roam_stats)]
@@ -223,6 +224,9 @@ class Roam:
         if not on_dev:
             bits = np.ascontiguousarray(bits, dtype=np.uint32)
         _check(self.L.roam_load_grid(self.h, ctypes.byref(d), _ptr(bits), int(on_dev)))
+        host_bits = bits if not on_dev else bits.cpu().numpy()
+        self.n_occupied = int(np.unpackbits(np.ascontiguousarray(host_bits).view(np.uint8)).sum())
+        self.dims = tuple(int(x) for x in dims)
 
     def load_fields(self, field_of_rank, affine):
         on_dev = not isinstance(field_of_rank, np.ndarray)
@@ -318,6 +322,16 @@ class Roam:
         _check(self.L.roam_occupancy_update(self.h, arr, len(cams), _ptr(depth), _ptr(opacity), ctypes.byref(q),
                                             _ptr(logit), _ptr(bits), _stream(stream)))
         return logit, bits
+
+    def assign_fields(self, n_fields: int, stream=None):
+        """roam_assign_fields (Alg. 1 stage II) on the loaded grid: returns
+        (labels int16 [S] device, boxes int32 [n_fields, 6] device)."""
+        import torch
+        n_occ = self.n_occupied
+        labels = torch.empty(n_occ, dtype=torch.int16, device=self._dev())
+        boxes = torch.empty((n_fields, 6), dtype=torch.int32, device=self._dev())
+        _check(self.L.roam_assign_fields(self.h, int(n_fields), _ptr(labels), _ptr(boxes), _stream(stream)))
+        return labels, boxes
 
     def get_stats(self) -> roam_stats:
         s = roam_stats()

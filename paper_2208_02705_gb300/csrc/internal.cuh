@@ -178,6 +178,10 @@ void launch_grid_prefix(const uint32_t *bits, uint32_t *prefix, uint32_t *block_
                         int64_t n_words, cudaStream_t s);
 void launch_brick_dist(GridDev g, uint8_t *occ, uint16_t *t0, uint16_t *t1, uint8_t *dist, cudaStream_t s);
 void launch_march(const GridDev &g, const MarchParams &p, int grid, cudaStream_t s);
+size_t assign_scratch_bytes();
+void launch_assign(const uint32_t *bits, const uint32_t *prefix, int64_t n_words, int gx, int gy, uint32_t S, int n,
+                   uint32_t *vox, uint16_t *field, int32_t *boxes, void *scratch, int n_sm, cudaStream_t s);
+uint32_t assign_status(const void *scratch);
 void launch_occupancy_scan(const GridDev &g, const DevCamera *cams, int view, int n_pix, const float *depth,
                            const float *opacity, const roam_occ_params &q, uint32_t *hit, uint32_t *free_bits,
                            float *logit, uint32_t *bits, int n_sm, cudaStream_t s);

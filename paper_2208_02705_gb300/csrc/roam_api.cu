@@ -141,6 +141,8 @@ struct roam_ctx {
     DBuf<float> o_rgb, o_depth, o_op;
     DBuf<DevCamera> cams;
     DBuf<uint32_t> occ_hit, occ_free;        // occupancy update marks (per voxel, per 32 voxels)
+    DBuf<uint32_t> assign_vox;               // occupied voxels' linear indices (field assignment)
+    DBuf<uint8_t> assign_scratch;
     // pinned staging of the camera uploads: a ring, so that consecutive calls
     // (e.g. one per view) do not wait for each other's copies
     static constexpr int kCamRing = 8;
@@ -730,7 +732,7 @@ roam_status roam_destroy(roam_ctx *c)
     for (WSet &q : c->ws) {
         release(q.w32); release(q.wt); release(q.wr); release(q.wimg); release(q.wimg8);
     }
-    release(c->occ_hit); release(c->occ_free);
+    release(c->occ_hit); release(c->occ_free); release(c->assign_vox); release(c->assign_scratch);
     release(c->perm); release(c->inv); release(c->labels_orig); release(c->keys_tmp);
     release(c->gsr); release(c->adam_m); release(c->adam_v);
     release(c->orig); release(c->dir); release(c->dir_lo); release(c->acc); release(c->sr); release(c->tw);
@@ -1094,6 +1096,26 @@ roam_status roam_occupancy_update(roam_ctx *c, const roam_camera *cams, int n_vi
         ROAM_TRY(launched("occupancy scan"));
     }
     c->last = s;
+    return ROAM_OK;
+}
+
+roam_status roam_assign_fields(roam_ctx *c, int n_fields, uint16_t *labels, int32_t *boxes, void *stream)
+{
+    ROAM_TRY(set_dev(c));
+    if (!c->has_grid) return fail(ROAM_ERR_STATE, "load the occupancy grid first");
+    if (!labels) return fail(ROAM_ERR_ARG, "null labels");
+    const int64_t S = c->n_occ;
+    if (n_fields < 1 || n_fields > 8192 || n_fields > S)
+        return fail(ROAM_ERR_ARG, "n_fields must be in [1, min(8192, occupied voxels = %lld)]", (long long)S);
+    if (S >= (int64_t)1 << 27) return fail(ROAM_ERR_ARG, "at most 2^27 - 1 occupied voxels");
+    cudaStream_t s = (cudaStream_t)stream;
+    ROAM_TRY(ensure(c->assign_vox, (size_t)S));
+    ROAM_TRY(ensure(c->assign_scratch, assign_scratch_bytes()));
+    launch_assign(c->bits.p, c->prefix.p, c->n_words, c->g.gx, c->g.gy, (uint32_t)S, n_fields, c->assign_vox.p,
+                  labels, boxes, c->assign_scratch.p, c->n_sm, s);
+    ROAM_TRY(launched("field assignment"));
+    ROAM_CUDA(cudaStreamSynchronize(s));
+    if (assign_status(c->assign_scratch.p)) return fail(ROAM_ERR_DATA, "field assignment ran out of voxels");
     return ROAM_OK;
 }
 
