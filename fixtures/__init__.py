@@ -564,3 +564,53 @@ def roaming_path(scene: Scene, workload: int, n_frames: int, width: int = 1280, 
         yaw += 0.01
         cams.append(Camera(PERSPECTIVE, width, height, fov_h, yaw_pitch(yaw, 0.0), o.copy()))
     return cams
+
+
+def teacher_layer_shapes(W: int = 256, C: int = 128, pos_dim: int = PE_POS_DIM, dir_dim: int = PE_DIR_DIM):
+    """(out, in) of every layer of the global 360NeRF, in storage order:
+    layers 1-4, layer 5 on [layer 4; F(x)], layers 6-8, density head,
+    feature head, layer 10 on [feature; F(d)], layer 11."""
+    return ([(W, pos_dim)] + [(W, W)] * 3 + [(W, W + pos_dim)] + [(W, W)] * 3 + [(1, W), (W, W),
+            (C, W + dir_dim), (3, C)])
+
+
+def teacher_weights(workload: int, role: int = ROLE_TEACHER, bias_scale: float = 0.0) -> np.ndarray:
+    """float32 [P] Xavier-uniform weights of the global 360NeRF (seeded)."""
+    rng = rng_for(workload, role)
+    parts = []
+    for (o, i) in teacher_layer_shapes():
+        a = math.sqrt(6.0 / (o + i))
+        parts.append(rng.uniform(-a, a, size=o * i))
+        parts.append(rng.uniform(-bias_scale, bias_scale, size=o) if bias_scale else np.zeros(o))
+    return np.concatenate(parts).astype(np.float32)
+
+
+def scene_affine(scene: Scene) -> np.ndarray:
+    """float32 [6]: the whole grid box onto [-1, 1]^3 (scale xyz, offset xyz)."""
+    o = np.array(scene.origin, dtype=np.float64)
+    ext = np.array(scene.dims, dtype=np.float64) * scene.vox
+    scale = 2.0 / ext
+    return np.concatenate([scale, -1.0 - o * scale]).astype(np.float32)
+
+
+def distill_points(scene: Scene, part: Partition, workload: int, per_field: int, step: int = 0):
+    """Distillation samples: per field, `per_field` points uniform in
+    uniformly drawn occupied voxels of the field, with uniform directions.
+    Returns (p float32 [n, 3], d float32 [n, 3], field int32 [n])."""
+    rng = rng_for(workload * 1000 + step, ROLE_RAYS)
+    xyz = _occupied_xyz(scene.occ)
+    lab = part.field_of_rank.astype(np.int64)
+    order = np.argsort(lab, kind="stable")
+    starts = np.searchsorted(lab[order], np.arange(part.n_fields + 1))
+    ps, ds, fs = [], [], []
+    for f in range(part.n_fields):
+        cand = order[starts[f]:starts[f + 1]]
+        if cand.size == 0:
+            continue
+        pick = cand[rng.integers(0, cand.size, per_field)]
+        pts = (xyz[pick] + rng.uniform(0, 1, (per_field, 3))) * scene.vox + np.asarray(scene.origin)
+        dd = rng.normal(size=(per_field, 3))
+        dd /= np.linalg.norm(dd, axis=1, keepdims=True)
+        ps.append(pts); ds.append(dd); fs.append(np.full(per_field, f))
+    return (np.concatenate(ps).astype(np.float32), np.concatenate(ds).astype(np.float32),
+            np.concatenate(fs).astype(np.int32))

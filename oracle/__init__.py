@@ -83,6 +83,10 @@ def lib():
         L.orc_segment_voxels.restype = I64
         L.orc_assign_fields.argtypes = [i32p, ctypes.POINTER(ctypes.c_int64), I64, I, i32p]
         L.orc_assign_fields.restype = I
+        L.orc_teacher_param_count.restype = I64
+        L.orc_teacher_eval.argtypes = [f32p, f64p, I64, f64p, f64p, f64p]
+        L.orc_distill_loss_grad.argtypes = [f32p, f32p, I, I, I, I, D, I64, f64p, f64p, i32p, f64p, D, f64p]
+        L.orc_distill_loss_grad.restype = D
         _lib = L
     return _lib
 
@@ -341,3 +345,39 @@ def assign_fields(dims, occ_linear: np.ndarray, n: int) -> np.ndarray:
     if rc:
         raise ValueError("orc_assign_fields rejected its arguments")
     return out
+
+
+def teacher_param_count() -> int:
+    return int(lib().orc_teacher_param_count())
+
+
+def teacher_eval(weights, aff_global, p, d) -> np.ndarray:
+    """The global 360NeRF at points p [n, 3] with directions d [n, 3]:
+    (sigma, r, g, b) per point."""
+    w = np.ascontiguousarray(weights, dtype=np.float32)
+    a = np.ascontiguousarray(np.asarray(aff_global, dtype=np.float32), dtype=np.float64)
+    p = np.ascontiguousarray(p, dtype=np.float64).reshape(-1, 3)
+    d = np.ascontiguousarray(d, dtype=np.float64).reshape(-1, 3)
+    out = np.zeros((p.shape[0], 4))
+    lib().orc_teacher_eval(_p(w, ctypes.c_float), _p(a, ctypes.c_double), int(p.shape[0]), _p(p, ctypes.c_double),
+                           _p(d, ctypes.c_double), _p(out, ctypes.c_double))
+    return out
+
+
+def distill_loss_grad(weights, affine, W: int, H: int, sigma_scale: float, p, d, field, target, I: float,
+                      act: int = 0):
+    """Eq. 7 summed over fields: (loss, gradient [F, P]) of the students."""
+    w = np.ascontiguousarray(weights, dtype=np.float32)
+    aff = np.ascontiguousarray(affine, dtype=np.float32)
+    F_ = int(aff.shape[0])
+    p = np.ascontiguousarray(p, dtype=np.float64).reshape(-1, 3)
+    d = np.ascontiguousarray(d, dtype=np.float64).reshape(-1, 3)
+    fl = np.ascontiguousarray(field, dtype=np.int32)
+    t = np.ascontiguousarray(target, dtype=np.float64).reshape(-1, 4)
+    P = param_count(W, H)
+    g = np.zeros((F_, P))
+    loss = lib().orc_distill_loss_grad(_p(w, ctypes.c_float), _p(aff, ctypes.c_float), F_, W, H, act,
+                                       f32(sigma_scale), int(p.shape[0]), _p(p, ctypes.c_double),
+                                       _p(d, ctypes.c_double), _p(fl, ctypes.c_int32), _p(t, ctypes.c_double),
+                                       float(I), _p(g, ctypes.c_double))
+    return float(loss), g

@@ -29,6 +29,9 @@
  *                    scans of rendered depth and opacity (Alg. 1 stage I)
  *   orc_assign_fields  the anchor + nearest-neighbour assignment of occupied
  *                    voxels to networks (Alg. 1 stage II)
+ *   orc_teacher_eval   the global 360NeRF of the implementation details (the
+ *                    distillation teacher)
+ *   orc_distill_loss_grad  the distillation loss of Eq. 7 and its gradient
  *
  * Readings of the paper taken here (the paper is silent or garbled on these):
  *   - pixel centres at (u + 1/2, v + 1/2);
@@ -1108,4 +1111,105 @@ int orc_assign_fields(const int32_t *dims, const int64_t *vox_idx, int64_t S, in
     free(done);
     free(keys);
     return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* The global 360NeRF as a distillation teacher (network table of the   */
+/* implementation details) and the distillation loss (Eq. 7)            */
+/* ------------------------------------------------------------------ */
+/*
+ * Readings: the global position is the world point mapped by a global
+ * affine (scene box onto [-1, 1]^3) and encoded with L = 10 (63 features),
+ * the view direction with L = 4 (27) as in the tiny networks (this makes
+ * the parameter count 595,844, the paper's "about 0.596M"); layers 1-7 are
+ * ReLU, layer 8 has no activation, the density head is ReLU, the feature
+ * head ReLU, layer 10 ReLU, layer 11 sigmoid; the skip connection feeds
+ * [layer-4 output; F(x)] into layer 5.  Eq. 7 sums over a field's I samples
+ * (sigma_k - sigma)^2 + |c_k - c|^2 and divides by I.
+ */
+
+#define ORC_T_W 256
+#define ORC_T_C 128
+
+int64_t orc_teacher_param_count(void)
+{
+    const int64_t W = ORC_T_W;
+    return (W * ORC_PE_POS + W) + 3 * (W * W + W) + (W * (W + ORC_PE_POS) + W) + 3 * (W * W + W) + (W + 1) +
+           (W * W + W) + (ORC_T_C * (W + ORC_PE_DIR) + ORC_T_C) + (3 * ORC_T_C + 3);
+}
+
+static void teacher_forward(const float *w, const double *aff, const double *p, const double *d, double *out)
+{
+    const int W = ORC_T_W;
+    double xg[3], pe[ORC_PE_POS], h[ORC_T_W + ORC_PE_POS], z[ORC_T_W], ped[ORC_PE_DIR];
+    for (int a = 0; a < 3; ++a) xg[a] = aff[a] * p[a] + aff[3 + a];
+    encode(xg, 10, pe);
+    encode(d, 4, ped);
+    const float *q = w;
+    dense(q, q + W * ORC_PE_POS, W, ORC_PE_POS, pe, z);                 /* layer 1 */
+    q += W * ORC_PE_POS + W;
+    for (int r = 0; r < W; ++r) h[r] = z[r] > 0.0 ? z[r] : 0.0;
+    for (int l = 2; l <= 4; ++l) {                                       /* layers 2-4 */
+        dense(q, q + W * W, W, W, h, z);
+        q += W * W + W;
+        for (int r = 0; r < W; ++r) h[r] = z[r] > 0.0 ? z[r] : 0.0;
+    }
+    for (int k = 0; k < ORC_PE_POS; ++k) h[W + k] = pe[k];               /* skip: [h4; F(x)] */
+    dense(q, q + W * (W + ORC_PE_POS), W, W + ORC_PE_POS, h, z);         /* layer 5 */
+    q += W * (W + ORC_PE_POS) + W;
+    for (int r = 0; r < W; ++r) h[r] = z[r] > 0.0 ? z[r] : 0.0;
+    for (int l = 6; l <= 8; ++l) {                                       /* layers 6-8 (8: linear) */
+        dense(q, q + W * W, W, W, h, z);
+        q += W * W + W;
+        for (int r = 0; r < W; ++r) h[r] = (l < 8) ? (z[r] > 0.0 ? z[r] : 0.0) : z[r];
+    }
+    double s;
+    dense(q, q + W, 1, W, h, &s);                                        /* layer 9, density */
+    q += W + 1;
+    out[0] = s > 0.0 ? s : 0.0;
+    double f[ORC_T_W + ORC_PE_DIR];
+    dense(q, q + W * W, W, W, h, z);                                     /* layer 9, feature */
+    q += W * W + W;
+    for (int r = 0; r < W; ++r) f[r] = z[r] > 0.0 ? z[r] : 0.0;
+    for (int k = 0; k < ORC_PE_DIR; ++k) f[W + k] = ped[k];
+    double g[ORC_T_C], zo[3];
+    dense(q, q + ORC_T_C * (W + ORC_PE_DIR), ORC_T_C, W + ORC_PE_DIR, f, g);   /* layer 10 */
+    q += ORC_T_C * (W + ORC_PE_DIR) + ORC_T_C;
+    for (int r = 0; r < ORC_T_C; ++r) g[r] = g[r] > 0.0 ? g[r] : 0.0;
+    dense(q, q + 3 * ORC_T_C, 3, ORC_T_C, g, zo);                        /* layer 11 */
+    for (int c = 0; c < 3; ++c) out[1 + c] = sigm(zo[c]);
+}
+
+/* out[n][4] = (sigma, r, g, b) of the teacher at points p[n][3], directions d[n][3] */
+void orc_teacher_eval(const float *w, const double *aff, int64_t n, const double *p, const double *d, double *out)
+{
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t i = 0; i < n; ++i) teacher_forward(w, aff, p + 3 * i, d + 3 * i, out + 4 * i);
+}
+
+/* Eq. 7 summed over the fields: loss = sum_i [(sigma_s - sigma_t)^2 +
+ * |c_s - c_t|^2] / I over the n samples (field[i] = the sample's field,
+ * target[i] = the teacher's (sigma, r, g, b)); grad[F][P] (zeroed here)
+ * receives d loss / d student weights.  Returns the loss. */
+double orc_distill_loss_grad(const float *weights, const float *affine, int n_fields, int W, int H, int act,
+                             double sigma_scale, int64_t n, const double *p, const double *d, const int32_t *field,
+                             const double *target, double I, double *grad)
+{
+    orc_arch A = {W, H, act, sigma_scale, 0};
+    const int64_t P = orc_param_count(W, H);
+    for (int64_t i = 0; i < P * n_fields; ++i) grad[i] = 0.0;
+    double loss = 0.0;
+    for (int64_t i = 0; i < n; ++i) {
+        const int f = field[i];
+        const double aff[6] = {affine[6 * f], affine[6 * f + 1], affine[6 * f + 2],
+                               affine[6 * f + 3], affine[6 * f + 4], affine[6 * f + 5]};
+        orc_cache c;
+        mlp_forward(weights + (int64_t)f * P, &A, aff, p + 3 * i, d + 3 * i, &c);
+        const double ds = c.sigma - target[4 * i];
+        const double dc[3] = {c.rgb[0] - target[4 * i + 1], c.rgb[1] - target[4 * i + 2], c.rgb[2] - target[4 * i + 3]};
+        loss += (ds * ds + dc[0] * dc[0] + dc[1] * dc[1] + dc[2] * dc[2]) / I;
+        const double drgb[3] = {2.0 * dc[0] / I, 2.0 * dc[1] / I, 2.0 * dc[2] / I};
+        mlp_backward(weights + (int64_t)f * P, &A, &c, 2.0 * ds / I, drgb, grad + (int64_t)f * P);
+    }
+    return loss;
 }

@@ -854,3 +854,105 @@ def test_assign_fields_matches_full_sort():
         assert np.array_equal(f, _assign_brute(dims, lin, n))
         counts = np.bincount(f, minlength=n)
         assert np.all(counts[:-1] == S // n) and counts[-1] == S - (n - 1) * (S // n)
+
+
+# ----------------------------------------------------------------------------
+# the global 360NeRF teacher and the distillation loss (Eq. 7)
+# ----------------------------------------------------------------------------
+
+def test_teacher_param_count_matches_paper():
+    import json, os
+    gold = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_values.json")))
+    t = gold["teacher_360nerf"]
+    assert O.teacher_param_count() == sum(o * i + o for o, i in F.teacher_layer_shapes())
+    assert abs(O.teacher_param_count() - t["params"]) <= t["tolerance"]
+
+
+def _np_teacher(w, aff, p, d):
+    """The teacher written independently with NumPy matrices."""
+    shapes = F.teacher_layer_shapes()
+    mats, o = [], 0
+    for (n_out, n_in) in shapes:
+        Wm = w[o:o + n_out * n_in].reshape(n_out, n_in).astype(np.float64)
+        b = w[o + n_out * n_in:o + n_out * n_in + n_out].astype(np.float64)
+        mats.append((Wm, b))
+        o += n_out * n_in + n_out
+    relu = lambda v: np.maximum(v, 0)
+    xg = aff[:3].astype(np.float64) * p + aff[3:].astype(np.float64)
+    pe, ped = _np_encode(xg, 10), _np_encode(d, 4)
+    h = relu(mats[0][0] @ pe + mats[0][1])
+    for k in (1, 2, 3):
+        h = relu(mats[k][0] @ h + mats[k][1])
+    h = relu(mats[4][0] @ np.concatenate([h, pe]) + mats[4][1])
+    for k in (5, 6):
+        h = relu(mats[k][0] @ h + mats[k][1])
+    h = mats[7][0] @ h + mats[7][1]
+    sigma = relu(mats[8][0] @ h + mats[8][1])[0]
+    f = relu(mats[9][0] @ h + mats[9][1])
+    g = relu(mats[10][0] @ np.concatenate([f, ped]) + mats[10][1])
+    rgb = 1 / (1 + np.exp(-(mats[11][0] @ g + mats[11][1])))
+    return np.concatenate([[sigma], rgb])
+
+
+def test_teacher_matches_independent_chain():
+    w = F.teacher_weights(3, bias_scale=0.2)
+    aff = np.array([0.3, 0.25, 0.2, -1.0, -0.9, -0.8], dtype=np.float32)
+    rng = np.random.default_rng(31)
+    p = rng.uniform(0, 6, (8, 3))
+    d = rng.normal(size=(8, 3))
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    got = O.teacher_eval(w, aff, p, d)
+    for i in range(8):
+        assert np.abs(got[i] - _np_teacher(w, aff, p[i], d[i])).max() <= 1e-10
+
+
+def test_teacher_skip_and_concat_routing():
+    """Only the skip path carries F(x)[m] (layers 1-4 are zero); the colour
+    sees [feature; F(d)] in that order: sigma = relu(F(x)[m]) and
+    green = sigmoid(relu(relu(F(x)[m]) + F(d)[m']))."""
+    shapes = F.teacher_layer_shapes()
+    offs, o = [], 0
+    for (n_out, n_in) in shapes:
+        offs.append((o, n_in))
+        o += n_out * n_in + n_out
+    w = np.zeros(o, dtype=np.float32)
+    m, mp = 8, 13                       # cos(pi x2) and cos(2 pi d1), values known below
+    w[offs[4][0] + 0 * offs[4][1] + 256 + m] = 1.0          # layer 5 unit 0 <- F(x)[m]
+    for k in (5, 6, 7):
+        w[offs[k][0] + 0] = 1.0                            # identity on unit 0
+    w[offs[8][0] + 0] = 1.0                                 # density <- unit 0
+    w[offs[9][0] + 2 * 256 + 0] = 1.0                       # feature 2 <- unit 0
+    w[offs[10][0] + 5 * offs[10][1] + 2] = 1.0              # g5 <- feature 2
+    w[offs[10][0] + 5 * offs[10][1] + 256 + mp] = 1.0       #     + F(d)[m']
+    w[offs[11][0] + 1 * 128 + 5] = 1.0                      # green <- g5
+    aff = np.array([1, 1, 1, 0, 0, 0], dtype=np.float32)
+    p = np.array([0.2, 0.4, -1.0 / 3.0])                    # cos(pi x2) = 1/2
+    d = np.array([0.3, 1.0 / 6.0, 0.2])                     # cos(2 pi d1) = 1/2
+    got = O.teacher_eval(w, aff, p[None], d[None])[0]
+    assert abs(got[0] - 0.5) < 1e-12
+    assert abs(got[2] - 1 / (1 + math.exp(-1.0))) < 1e-12
+    assert abs(got[1] - 0.5) < 1e-15 and abs(got[3] - 0.5) < 1e-15
+
+
+def test_distill_gradient_matches_central_differences(room32):
+    W, H = 16, 2
+    w = F.xavier_weights(1, F.ROLE_STUDENT, room32.part.n_fields, W, H, bias_scale=0.2)
+    p, d, f = F.distill_points(room32.scene, room32.part, 1, 6)
+    target = np.random.default_rng(4).uniform(0.1, 0.9, (p.shape[0], 4))
+    loss, g = O.distill_loss_grad(w, room32.affine, W, H, 1.5, p, d, f, target, 6.0)
+    rng = np.random.default_rng(8)
+    checked = 0
+    for _ in range(40):
+        fi, k = int(rng.integers(0, w.shape[0])), int(rng.integers(0, w.shape[1]))
+        if not np.any(f == fi):
+            continue
+        h = 1e-3 * max(1.0, abs(float(w[fi, k])))
+        wp, wm = w.copy(), w.copy()
+        wp[fi, k] += h
+        wm[fi, k] -= h
+        lp, _ = O.distill_loss_grad(wp, room32.affine, W, H, 1.5, p, d, f, target, 6.0)
+        lm, _ = O.distill_loss_grad(wm, room32.affine, W, H, 1.5, p, d, f, target, 6.0)
+        fd = (lp - lm) / (float(wp[fi, k]) - float(wm[fi, k]))
+        assert abs(fd - g[fi, k]) <= 1e-5 * max(1.0, abs(fd)), (fi, k, fd, g[fi, k])
+        checked += 1
+    assert checked >= 10
