@@ -235,6 +235,39 @@ roam_status roam_occupancy_update(roam_ctx *ctx, const roam_camera *cams, int n_
  * bounding box (min x, y, z, max x, y, z exclusive).  Synchronises. */
 roam_status roam_assign_fields(roam_ctx *ctx, int n_fields, uint16_t *labels, int32_t *boxes, void *stream);
 
+/* Distillation of the local fields from the global 360NeRF (Eq. 7).
+ *
+ * roam_teacher_load: the teacher's FP32 parameters (host, or device when
+ * on_device) in its layer order -- layers 1-4 (63 -> 256, 256 -> 256 x 3),
+ * layer 5 on [layer 4 (256); F(x) (63)], layers 6-8, the density head
+ * (256 -> 1), the feature head (256 -> 256), layer 10 on [feature (256);
+ * F(d) (27)] -> 128, layer 11 (128 -> 3); each layer row-major [out][in]
+ * then its bias -- 595,844 floats; affine (host float[6]): the global
+ * position's map onto [-1, 1]^3 (scale xyz, offset xyz).  Synchronous. */
+roam_status roam_teacher_load(roam_ctx *ctx, const float *weights, const float *affine, int on_device);
+
+/* The teacher at n points: p, d device float[n][3] (world position, view
+ * direction); out device float[n][4] = (sigma, r, g, b), 16-byte aligned.
+ * Asynchronous. */
+roam_status roam_teacher_eval(roam_ctx *ctx, const float *p, const float *d, int64_t n, float *out, void *stream);
+
+/* Eq. 7 over n samples: *loss (device, may be NULL) = sum over samples of
+ * [(sigma_s - sigma_t)^2 + |c_s - c_t|^2] / I, and dl_dout = 2 (student -
+ * teacher) / I per component; student, teacher, dl_dout device
+ * float[n][4], 16-byte aligned.  The sum runs in a fixed order.
+ * Asynchronous. */
+roam_status roam_distill_loss(roam_ctx *ctx, const float *student, const float *teacher, int64_t n, float I,
+                              float *dl_dout, float *loss, void *stream);
+
+/* Gradient of the loaded fields' weights at n points given the loss
+ * gradient of every sample's output: p, d device float[n][3], field device
+ * uint16[n], dl_dout device float[n][4] (d loss / d (sigma, r, g, b));
+ * grad device float[n_fields][P] (overwritten), the layout of
+ * roam_load_weights.  FP32 adjoint; one MLP width (32 or 64) for every
+ * field.  Asynchronous. */
+roam_status roam_mlp_backward(roam_ctx *ctx, const float *p, const float *d, const uint16_t *field, int64_t n,
+                              const float *dl_dout, float *grad, void *stream);
+
 /* Chooses the round size (kept samples marched per live ray per round) for
  * this camera batch and these options: renders the batch once per candidate
  * (4, 8, 16, ... up to n_max, while the workspace fits in half the free

@@ -1213,3 +1213,33 @@ double orc_distill_loss_grad(const float *weights, const float *affine, int n_fi
     }
     return loss;
 }
+
+/* The adjoint of the fields' MLPs at n points for given per-sample output
+ * gradients dl[n][4] = d loss / d (sigma, r, g, b): grad[F][P] (zeroed here)
+ * = sum_i J_i^T dl_i.  margin[i] (may be NULL) receives the smallest
+ * |pre-activation| over the sample's ReLU units: below ~1e-4 an FP32
+ * evaluation may take the other branch (a near-kink). */
+void orc_mlp_grad_points(const float *weights, const float *affine, int n_fields, int W, int H, int act,
+                         double sigma_scale, int64_t n, const double *p, const double *d, const int32_t *field,
+                         const double *dl, double *grad, double *margin)
+{
+    orc_arch A = {W, H, act, sigma_scale, 0};
+    const int64_t P = orc_param_count(W, H);
+    for (int64_t i = 0; i < P * n_fields; ++i) grad[i] = 0.0;
+    for (int64_t i = 0; i < n; ++i) {
+        const int f = field[i];
+        const double aff[6] = {affine[6 * f], affine[6 * f + 1], affine[6 * f + 2],
+                               affine[6 * f + 3], affine[6 * f + 4], affine[6 * f + 5]};
+        orc_cache c;
+        mlp_forward(weights + (int64_t)f * P, &A, aff, p + 3 * i, d + 3 * i, &c);
+        mlp_backward(weights + (int64_t)f * P, &A, &c, dl[4 * i], dl + 4 * i + 1, grad + (int64_t)f * P);
+        if (margin) {
+            double m = INFINITY;
+            for (int k = 0; k < H; ++k)
+                for (int r = 0; r < W; ++r) m = fmin(m, fabs(c.z[k][r]));
+            for (int r = 0; r < W; ++r) m = fmin(m, fabs(c.zc[r]));
+            if (act == 1) m = fmin(m, fabs(c.zh[0]));
+            margin[i] = m;
+        }
+    }
+}

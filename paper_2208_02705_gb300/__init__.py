@@ -27,7 +27,8 @@ STATUS = {0: "ROAM_OK", -1: "ROAM_ERR_ARG", -2: "ROAM_ERR_OOM", -3: "ROAM_ERR_CU
 # every entry point declared in include/roam.h
 ENTRY_POINTS = ("roam_create", "roam_destroy", "roam_last_error", "roam_check", "roam_load_grid",
                 "roam_load_fields", "roam_load_weights", "roam_load_weights_mixed", "roam_get_weights", "roam_render",
-                "roam_get_stats", "roam_tune_round_size", "roam_occupancy_update", "roam_assign_fields", "roam_march", "roam_bucket", "roam_mlp_eval", "roam_composite", "roam_train_forward",
+                "roam_get_stats", "roam_tune_round_size", "roam_occupancy_update", "roam_assign_fields", "roam_teacher_load", "roam_teacher_eval",
+                "roam_distill_loss", "roam_mlp_backward", "roam_march", "roam_bucket", "roam_mlp_eval", "roam_composite", "roam_train_forward",
                 "roam_train_backward", "roam_adam_step", "roam_profile", "roam_profile_read",
                 "roam_bucket_static", "roam_l2_loss")
 
@@ -109,6 +110,10 @@ def load_library(path: str = LIB_PATH):
     L.roam_tune_round_size.argtypes = [vp, vp, i32, P(roam_render_opts), vp, vp, vp]
     L.roam_occupancy_update.argtypes = [vp, vp, i32, vp, vp, P(roam_occ_params), vp, vp, vp]
     L.roam_assign_fields.argtypes = [vp, i32, vp, vp, vp]
+    L.roam_teacher_load.argtypes = [vp, vp, vp, i32]
+    L.roam_teacher_eval.argtypes = [vp, vp, vp, i64, vp, vp]
+    L.roam_distill_loss.argtypes = [vp, vp, vp, i64, ctypes.c_float, vp, vp, vp]
+    L.roam_mlp_backward.argtypes = [vp, vp, vp, vp, i64, vp, vp, vp]
     L.roam_get_weights.argtypes = [vp, vp, i32]
     L.roam_render.argtypes = [vp, P(roam_camera), i32, P(roam_render_opts), vp, vp, vp, i32, vp]
     L.roam_get_stats.argtypes = [vp, P(roam_stats)]
@@ -332,6 +337,49 @@ class Roam:
         boxes = torch.empty((n_fields, 6), dtype=torch.int32, device=self._dev())
         _check(self.L.roam_assign_fields(self.h, int(n_fields), _ptr(labels), _ptr(boxes), _stream(stream)))
         return labels, boxes
+
+    # ---- distillation from the global 360NeRF (Eq. 7) ----
+    def teacher_load(self, weights, affine):
+        on_dev = not isinstance(weights, np.ndarray)
+        if not on_dev:
+            weights = np.ascontiguousarray(weights, dtype=np.float32)
+        aff = np.ascontiguousarray(affine, dtype=np.float32)
+        _check(self.L.roam_teacher_load(self.h, _ptr(weights), _ptr(aff), int(on_dev)))
+
+    def teacher_eval(self, p, d, stream=None):
+        import torch
+        n = int(p.shape[0])
+        out = torch.empty((n, 4), dtype=torch.float32, device=self._dev())
+        _check(self.L.roam_teacher_eval(self.h, _ptr(p), _ptr(d), n, _ptr(out), _stream(stream)))
+        return out
+
+    def distill_loss(self, student, teacher, I: float, stream=None):
+        import torch
+        n = int(student.shape[0])
+        dl = torch.empty_like(student)
+        loss = torch.empty(1, dtype=torch.float32, device=self._dev())
+        _check(self.L.roam_distill_loss(self.h, _ptr(student), _ptr(teacher), n, float(I), _ptr(dl), _ptr(loss),
+                                        _stream(stream)))
+        return loss, dl
+
+    def mlp_backward(self, p, d, field, dl_dout, stream=None):
+        import torch
+        grad = torch.empty((self.n_fields, self.P), dtype=torch.float32, device=self._dev())
+        _check(self.L.roam_mlp_backward(self.h, _ptr(p), _ptr(d), _ptr(field), int(p.shape[0]), _ptr(dl_dout),
+                                        _ptr(grad), _stream(stream)))
+        return grad
+
+    def distill_step(self, p, d, field, I: float, lr: float, step: int, teacher_out=None, precision=None,
+                     stream=None):
+        """One distillation step (Eq. 7): teacher targets (computed unless
+        given), student outputs (FP32 by default), loss and its gradient,
+        the FP32 adjoint and Adam.  Returns the loss (device tensor)."""
+        t = teacher_out if teacher_out is not None else self.teacher_eval(p, d, stream=stream)
+        sdt = self.mlp_eval(p, d, field, ROAM_F32 if precision is None else precision, stream=stream)
+        loss, dl = self.distill_loss(sdt, t, I, stream=stream)
+        g = self.mlp_backward(p, d, field, dl, stream=stream)
+        self.adam_step(g, lr=lr, step=step, stream=stream)
+        return loss
 
     def get_stats(self) -> roam_stats:
         s = roam_stats()

@@ -178,6 +178,15 @@ void launch_grid_prefix(const uint32_t *bits, uint32_t *prefix, uint32_t *block_
                         int64_t n_words, cudaStream_t s);
 void launch_brick_dist(GridDev g, uint8_t *occ, uint16_t *t0, uint16_t *t1, uint8_t *dist, cudaStream_t s);
 void launch_march(const GridDev &g, const MarchParams &p, int grid, cudaStream_t s);
+struct TeacherAffine {
+    float v[6];      // global position -> [-1, 1]^3: scale xyz, offset xyz
+};
+int64_t teacher_param_count();
+size_t teacher_workspace_floats(int64_t n);
+int teacher_eval(void *cublas_handle, const float *w, TeacherAffine aff, int64_t n, const float *p, const float *d,
+                 float4 *out, float *ws, cudaStream_t s);
+void launch_distill_loss(int64_t n, const float4 *student, const float4 *teacher, float I, float4 *dl, float *loss,
+                         cudaStream_t s);
 size_t assign_scratch_bytes();
 void launch_assign(const uint32_t *bits, const uint32_t *prefix, int64_t n_words, int gx, int gy, uint32_t S, int n,
                    uint32_t *vox, uint16_t *field, int32_t *boxes, void *scratch, int n_sm, cudaStream_t s);

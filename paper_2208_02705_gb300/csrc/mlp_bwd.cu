@@ -222,7 +222,15 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_bwd_simt(MlpWeights w, Samp
         const float *aff = w.affine + 6 * (int64_t)tl.field;
         float xl0 = 0.f, xl1 = 0.f, xl2 = 0.f, dx = 0.f, dy = 0.f, dz = 1.f;
         float4 g = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (valid) {
+        if (valid && src.mode == 1) {
+            // direct points (distillation): world position and direction per sample
+            const float px = src.p[3 * (int64_t)idx], py = src.p[3 * (int64_t)idx + 1], pz = src.p[3 * (int64_t)idx + 2];
+            dx = src.d[3 * (int64_t)idx]; dy = src.d[3 * (int64_t)idx + 1]; dz = src.d[3 * (int64_t)idx + 2];
+            xl0 = fmaf(aff[0], px, aff[3]);
+            xl1 = fmaf(aff[1], py, aff[4]);
+            xl2 = fmaf(aff[2], pz, aff[5]);
+            g = gsr[idx];
+        } else if (valid) {
             const uint32_t col = idx >> 5;
             const uint32_t i = (col / (uint32_t)src.R) * 32u + (idx & 31u);
             const uint32_t ray = src.live ? src.live[i] : i;
@@ -481,6 +489,41 @@ void launch_mlp_bwd_simt(const MlpWeights &w, const SampleSrc &src, const Bucket
     ROAM_CASE(32, 1) ROAM_CASE(32, 2) ROAM_CASE(32, 3) ROAM_CASE(32, 4)
     ROAM_CASE(64, 1) ROAM_CASE(64, 2) ROAM_CASE(64, 3) ROAM_CASE(64, 4)
 #undef ROAM_CASE
+}
+
+// Eq. 7 over samples: sum [(sigma_s - sigma_t)^2 + |c_s - c_t|^2] / I, its
+// gradient 2 (student - teacher) / I per component; one block, fixed order.
+__global__ void __launch_bounds__(1024) k_distill_loss(int64_t n, const float4 *__restrict__ st,
+                                                       const float4 *__restrict__ te, float inv_I,
+                                                       float4 *__restrict__ dl, float *__restrict__ loss)
+{
+    __shared__ float part[32];
+    float acc = 0.f;
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+        const float4 a = st[i], b = te[i];
+        const float e0 = a.x - b.x, e1 = a.y - b.y, e2 = a.z - b.z, e3 = a.w - b.w;
+        dl[i] = make_float4(2.f * e0 * inv_I, 2.f * e1 * inv_I, 2.f * e2 * inv_I, 2.f * e3 * inv_I);
+        acc = fmaf(e0 * inv_I, e0, acc);
+        acc = fmaf(e1 * inv_I, e1, acc);
+        acc = fmaf(e2 * inv_I, e2, acc);
+        acc = fmaf(e3 * inv_I, e3, acc);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        float v = threadIdx.x < (blockDim.x >> 5) ? part[threadIdx.x] : 0.f;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if (threadIdx.x == 0 && loss) *loss = v;
+    }
+}
+
+void launch_distill_loss(int64_t n, const float4 *student, const float4 *teacher, float I, float4 *dl, float *loss,
+                         cudaStream_t s)
+{
+    k_distill_loss<<<1, 1024, 0, s>>>(n, student, teacher, 1.0f / I, dl, loss);
 }
 
 void launch_l2_loss(int64_t n_rays, const float *rgb, const float *target, float norm, float *dl, float *loss,

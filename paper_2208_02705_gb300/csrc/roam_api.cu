@@ -8,6 +8,8 @@
 #include <atomic>
 #include <vector>
 
+#include <cublas_v2.h>
+
 #include "internal.cuh"
 
 using namespace roam;
@@ -142,6 +144,11 @@ struct roam_ctx {
     DBuf<DevCamera> cams;
     DBuf<uint32_t> occ_hit, occ_free;        // occupancy update marks (per voxel, per 32 voxels)
     DBuf<uint32_t> assign_vox;               // occupied voxels' linear indices (field assignment)
+    // distillation teacher (global 360NeRF)
+    bool has_teacher = false;
+    DBuf<float> teacher_w, teacher_ws;
+    TeacherAffine teacher_aff{};
+    cublasHandle_t cublas = nullptr;
     DBuf<uint8_t> assign_scratch;
     // pinned staging of the camera uploads: a ring, so that consecutive calls
     // (e.g. one per view) do not wait for each other's copies
@@ -733,6 +740,8 @@ roam_status roam_destroy(roam_ctx *c)
         release(q.w32); release(q.wt); release(q.wr); release(q.wimg); release(q.wimg8);
     }
     release(c->occ_hit); release(c->occ_free); release(c->assign_vox); release(c->assign_scratch);
+    release(c->teacher_w); release(c->teacher_ws);
+    if (c->cublas) cublasDestroy(c->cublas);
     release(c->perm); release(c->inv); release(c->labels_orig); release(c->keys_tmp);
     release(c->gsr); release(c->adam_m); release(c->adam_v);
     release(c->orig); release(c->dir); release(c->dir_lo); release(c->acc); release(c->sr); release(c->tw);
@@ -1117,6 +1126,100 @@ roam_status roam_assign_fields(roam_ctx *c, int n_fields, uint16_t *labels, int3
     ROAM_CUDA(cudaStreamSynchronize(s));
     if (assign_status(c->assign_scratch.p)) return fail(ROAM_ERR_DATA, "field assignment ran out of voxels");
     return ROAM_OK;
+}
+
+roam_status roam_teacher_load(roam_ctx *c, const float *weights, const float *affine, int on_device)
+{
+    ROAM_TRY(set_dev(c));
+    if (!weights || !affine) return fail(ROAM_ERR_ARG, "null weights or affine");
+    const int64_t P = teacher_param_count();
+    c->has_teacher = false;
+    ROAM_TRY(ensure(c->teacher_w, (size_t)P));
+    ROAM_CUDA(cudaMemcpy(c->teacher_w.p, weights, (size_t)P * sizeof(float),
+                         on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice));
+    ROAM_CUDA(cudaMemset(c->d_flag, 0, 4));
+    k_check_finite<<<1024, 256>>>(c->teacher_w.p, P, c->d_flag);
+    ROAM_TRY(launched("teacher weight check"));
+    uint32_t bad = 0;
+    ROAM_CUDA(cudaMemcpy(&bad, c->d_flag, 4, cudaMemcpyDeviceToHost));
+    if (bad) return fail(ROAM_ERR_ARG, "teacher weights contain NaN or Inf");
+    for (int i = 0; i < 6; ++i) {
+        if (!finite(affine[i])) return fail(ROAM_ERR_ARG, "non-finite teacher affine");
+        c->teacher_aff.v[i] = affine[i];
+    }
+    if (!c->cublas && cublasCreate(&c->cublas) != CUBLAS_STATUS_SUCCESS) {
+        c->cublas = nullptr;
+        return fail(ROAM_ERR_CUDA, "cublasCreate failed");
+    }
+    c->has_teacher = true;
+    return ROAM_OK;
+}
+
+roam_status roam_teacher_eval(roam_ctx *c, const float *p, const float *d, int64_t n, float *out, void *stream)
+{
+    ROAM_TRY(set_dev(c));
+    if (!c->has_teacher) return fail(ROAM_ERR_STATE, "no teacher loaded");
+    if (n < 0 || n > 0x7fffffff) return fail(ROAM_ERR_ARG, "bad sample count");
+    if (n == 0) return ROAM_OK;
+    if (!p || !d || !out) return fail(ROAM_ERR_ARG, "null pointer");
+    if (((uintptr_t)out) & 15) return fail(ROAM_ERR_ARG, "out must be 16-byte aligned");
+    cudaStream_t s = (cudaStream_t)stream;
+    ROAM_TRY(ensure(c->teacher_ws, teacher_workspace_floats(n)));
+    if (teacher_eval(c->cublas, c->teacher_w.p, c->teacher_aff, n, p, d, reinterpret_cast<float4 *>(out),
+                     c->teacher_ws.p, s))
+        return fail(ROAM_ERR_CUDA, "cuBLAS GEMM failed in the teacher");
+    c->last = s;
+    return launched("teacher");
+}
+
+roam_status roam_distill_loss(roam_ctx *c, const float *student, const float *teacher, int64_t n, float I,
+                              float *dl_dout, float *loss, void *stream)
+{
+    ROAM_TRY(set_dev(c));
+    if (n < 0 || !(I > 0.f)) return fail(ROAM_ERR_ARG, "bad sizes");
+    if (!student || !teacher || !dl_dout) return fail(ROAM_ERR_ARG, "null pointer");
+    if ((((uintptr_t)student) | ((uintptr_t)teacher) | ((uintptr_t)dl_dout)) & 15)
+        return fail(ROAM_ERR_ARG, "arrays must be 16-byte aligned");
+    cudaStream_t s = (cudaStream_t)stream;
+    launch_distill_loss(n, reinterpret_cast<const float4 *>(student), reinterpret_cast<const float4 *>(teacher), I,
+                        reinterpret_cast<float4 *>(dl_dout), loss, s);
+    c->last = s;
+    return launched("distill loss");
+}
+
+roam_status roam_mlp_backward(roam_ctx *c, const float *p, const float *d, const uint16_t *field, int64_t n,
+                              const float *dl_dout, float *grad, void *stream)
+{
+    ROAM_TRY(set_dev(c));
+    ROAM_TRY(check_ready(c));
+    if (c->n_ws != 1) return fail(ROAM_ERR_UNSUPPORTED, "training needs one MLP width for every field");
+    if (!mlp_bwd_supported(c->md.width, c->md.n_hidden))
+        return fail(ROAM_ERR_UNSUPPORTED, "training supports W = 32 or 64");
+    if (n < 0 || n > 0x7fffffff) return fail(ROAM_ERR_ARG, "bad sample count");
+    if (!grad) return fail(ROAM_ERR_ARG, "null gradient");
+    cudaStream_t s = (cudaStream_t)stream;
+    ROAM_CUDA(cudaMemsetAsync(grad, 0, (size_t)(c->ws[0].P * c->n_fields) * sizeof(float), s));
+    if (n == 0) return ROAM_OK;
+    if (!p || !d || !field || !dl_dout) return fail(ROAM_ERR_ARG, "null pointer");
+    if (((uintptr_t)dl_dout) & 15) return fail(ROAM_ERR_ARG, "dl_dout must be 16-byte aligned");
+    ROAM_TRY(ensure(c->sorted, (size_t)n));
+    ROAM_TRY(ensure(c->tiles, tile_capacity((size_t)n, c->n_fields)));
+    const BucketBufs b = bucket_of(c);
+    ROAM_CUDA(cudaMemsetAsync(c->ctr, 0, sizeof(Counters), s));
+    launch_bucket(nullptr, nullptr, nullptr, (uint32_t)n, 1, 1, field, c->n_fields, 128, b, c->ctr, grid_blocks(c, 2),
+                  s, c->cb);
+    ROAM_TRY(launched("bucket"));
+    SampleSrc src{};
+    src.mode = 1;
+    src.p = p;
+    src.d = d;
+    {
+        ProfScope ps(c, P_MLP_BWD, s);
+        launch_mlp_bwd_simt(weights_of(c), src, b, c->ctr, reinterpret_cast<const float4 *>(dl_dout), grad, c->n_sm,
+                            s);
+    }
+    c->last = s;
+    return launched("mlp_bwd");
 }
 
 roam_status roam_get_stats(roam_ctx *c, roam_stats *st)

@@ -1,0 +1,136 @@
+// The global 360NeRF (network table of the implementation details) as the
+// distillation teacher of the local fields (Eq. 7): 8 fully connected layers
+// of width 256 with a skip of F(x) into layer 5, a density head, a feature
+// head, and a 128-wide colour layer on [feature; F(d)].  Its layers are
+// plain dense GEMMs over the sample batch (K up to 319, N = 256), run as
+// FP32 cuBLAS GEMMs; the encodings, bias + activation epilogues and the
+// output heads are this file's kernels.
+//
+// Activations live row-major per sample in two ping-pong buffers whose
+// trailing columns hold the encodings the skip and the colour layer read:
+//   A: [n][320]  columns 0..255 activations, 256..318 F(x), 319 zero
+//   B: [n][288]  columns 0..255 activations, 256..282 F(d), 283..287 zero
+#include <cublas_v2.h>
+
+#include "internal.cuh"
+
+namespace roam {
+
+namespace {
+
+constexpr int kTW = 256, kTC = 128;
+constexpr int kLdA = 320, kLdB = 288;
+
+__global__ void k_teacher_encode(int64_t n, const float *__restrict__ p, const float *__restrict__ d, TeacherAffine aff,
+                                 float *__restrict__ A, float *__restrict__ B)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        float x[3], dv[3];
+        for (int a = 0; a < 3; ++a) {
+            x[a] = fmaf(aff.v[a], p[3 * i + a], aff.v[3 + a]);
+            dv[a] = d[3 * i + a];
+        }
+        float *pa = A + i * kLdA + kTW;
+        float *pb = B + i * kLdB + kTW;
+        for (int a = 0; a < 3; ++a) { pa[a] = x[a]; pb[a] = dv[a]; }
+        for (int k = 0; k < 10; ++k)
+            for (int a = 0; a < 3; ++a) {
+                float s, c;
+                sincospif(x[a] * (float)(1 << k), &s, &c);
+                pa[3 + 6 * k + a] = s;
+                pa[6 + 6 * k + a] = c;
+            }
+        pa[63] = 0.f;
+        for (int k = 0; k < 4; ++k)
+            for (int a = 0; a < 3; ++a) {
+                float s, c;
+                sincospif(dv[a] * (float)(1 << k), &s, &c);
+                pb[3 + 6 * k + a] = s;
+                pb[6 + 6 * k + a] = c;
+            }
+        for (int q = 27; q < 32; ++q) pb[q] = 0.f;
+    }
+}
+
+// Y[i][0..N) += b, then ReLU when relu
+__global__ void k_bias_act(int64_t n, int N, int ld, float *__restrict__ Y, const float *__restrict__ b, int relu)
+{
+    const int64_t total = n * N;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = e / N;
+        const int c = (int)(e % N);
+        float v = Y[i * ld + c] + b[c];
+        Y[i * ld + c] = relu ? fmaxf(v, 0.f) : v;
+    }
+}
+
+// out[i] = (relu(s + b_s), sigmoid(z + b_o))
+__global__ void k_teacher_out(int64_t n, const float *__restrict__ s, const float *__restrict__ bs,
+                              const float *__restrict__ z, const float *__restrict__ bo, float4 *__restrict__ out)
+{
+    const float b0 = bs[0];
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float sg = fmaxf(s[i] + b0, 0.f);
+        float c[3];
+        for (int k = 0; k < 3; ++k) c[k] = 1.f / (1.f + expf(-(z[3 * i + k] + bo[k])));
+        out[i] = make_float4(sg, c[0], c[1], c[2]);
+    }
+}
+
+// C[n][N] (ldc) = X[n][K] (ldx) W^T, W row-major [N][K]: column-major
+// C^T = W X^T with W read transposed
+cublasStatus_t dense(cublasHandle_t h, int64_t n, int N, int K, const float *W, const float *X, int ldx, float *C,
+                     int ldc)
+{
+    const float one = 1.f, zero = 0.f;
+    return cublasSgemm(h, CUBLAS_OP_T, CUBLAS_OP_N, N, (int)n, K, &one, W, K, X, ldx, &zero, C, ldc);
+}
+
+}  // namespace
+
+int64_t teacher_param_count()
+{
+    return ((int64_t)kTW * kPeX + kTW) + 3 * ((int64_t)kTW * kTW + kTW) + ((int64_t)kTW * (kTW + kPeX) + kTW) +
+           3 * ((int64_t)kTW * kTW + kTW) + (kTW + 1) + ((int64_t)kTW * kTW + kTW) +
+           ((int64_t)kTC * (kTW + kPeD) + kTC) + (3 * kTC + 3);
+}
+
+size_t teacher_workspace_floats(int64_t n) { return (size_t)n * (kLdA + kLdB + 1 + 3); }
+
+// w: device FP32 parameters in the API layout (row-major [out][in] then bias, layer after layer)
+int teacher_eval(void *handle, const float *w, TeacherAffine aff, int64_t n, const float *p, const float *d,
+                 float4 *out, float *ws, cudaStream_t s)
+{
+    cublasHandle_t h = static_cast<cublasHandle_t>(handle);
+    if (cublasSetStream(h, s) != CUBLAS_STATUS_SUCCESS) return 1;
+    float *A = ws, *B = A + (size_t)n * kLdA, *sig = B + (size_t)n * kLdB, *z = sig + n;
+    const int grid = 1024;
+    k_teacher_encode<<<grid, 256, 0, s>>>(n, p, d, aff, A, B);
+    const float *q = w;
+    int st = 0;
+    auto layer = [&](int N, int K, const float *X, int ldx, float *Y, int ldy, int relu) {
+        st |= dense(h, n, N, K, q, X, ldx, Y, ldy) != CUBLAS_STATUS_SUCCESS;
+        k_bias_act<<<grid, 256, 0, s>>>(n, N, ldy, Y, q + (int64_t)N * K, relu);
+        q += (int64_t)N * K + N;
+    };
+    layer(kTW, kPeX, A + kTW, kLdA, B, kLdB, 1);          // layer 1 on F(x)
+    layer(kTW, kTW, B, kLdB, A, kLdA, 1);                 // layer 2
+    layer(kTW, kTW, A, kLdA, B, kLdB, 1);                 // layer 3
+    layer(kTW, kTW, B, kLdB, A, kLdA, 1);                 // layer 4 (A keeps F(x) after it)
+    layer(kTW, kTW + kPeX, A, kLdA, B, kLdB, 1);          // layer 5 on [layer 4; F(x)]
+    layer(kTW, kTW, B, kLdB, A, kLdA, 1);                 // layer 6
+    layer(kTW, kTW, A, kLdA, B, kLdB, 1);                 // layer 7
+    layer(kTW, kTW, B, kLdB, A, kLdA, 0);                 // layer 8, linear
+    // density head: N = 1
+    st |= dense(h, n, 1, kTW, q, A, kLdA, sig, 1) != CUBLAS_STATUS_SUCCESS;
+    const float *b_sig = q + kTW;
+    q += kTW + 1;
+    layer(kTW, kTW, A, kLdA, B, kLdB, 1);                 // feature head (B keeps F(d) after it)
+    layer(kTC, kTW + kPeD, B, kLdB, A, kLdA, 1);          // layer 10 on [feature; F(d)]
+    st |= dense(h, n, 3, kTC, q, A, kLdA, z, 3) != CUBLAS_STATUS_SUCCESS;   // layer 11
+    const float *b_out = q + 3 * kTC;
+    k_teacher_out<<<grid, 256, 0, s>>>(n, sig, b_sig, z, b_out, out);
+    return st;
+}
+
+}  // namespace roam

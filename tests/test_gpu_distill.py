@@ -1,0 +1,106 @@
+"""Distillation of the local fields from the global 360NeRF (Eq. 7) against
+the oracle: the teacher (FP32 cuBLAS GEMMs and the library's encodings and
+epilogues) within 1e-4 of the FP64 teacher; the Eq. 7 loss and the
+students' gradient through the C ABI: the loss within 1e-5 relative; the
+FP32 adjoint within 1e-4 of max |g| once the samples the oracle finds at a
+ReLU kink are left out of both sides (an FP32 pre-activation that close to
+zero may take the other branch -- the gradient's near-tie), and the full
+gradient within 1e-2 in norm; a few steps lower the loss."""
+import numpy as np
+import pytest
+
+import fixtures as F
+import oracle as O
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def roam():
+    import paper_2208_02705_gb300 as roam
+    from paper_2208_02705_gb300 import build
+    build.build()
+    return roam
+
+
+TEACHER_SEED = 7
+
+
+SIGMA_SCALE = 2.0     # student density on the teacher's scale (its ReLU head gives O(1) densities)
+
+
+def _ctx(roam, wl, W, H, w):
+    r = roam.Roam(0)
+    r.load_grid(wl.scene.bits, wl.scene.dims, wl.scene.origin, wl.scene.vox)
+    r.load_fields(wl.part.field_of_rank, wl.affine)
+    r.load_weights(w, W, H, SIGMA_SCALE)
+    r.teacher_load(F.teacher_weights(TEACHER_SEED, bias_scale=0.1), F.scene_affine(wl.scene))
+    return r
+
+
+def test_teacher_matches_oracle(roam, room32):
+    r = _ctx(roam, room32, 32, 2, room32.weights)
+    p, d, f = F.distill_points(room32.scene, room32.part, 1, 64)
+    out = r.teacher_eval(torch.from_numpy(p).cuda(), torch.from_numpy(d).cuda())
+    torch.cuda.synchronize()
+    ref = O.teacher_eval(F.teacher_weights(TEACHER_SEED, bias_scale=0.1), F.scene_affine(room32.scene), p.astype(np.float64),
+                         d.astype(np.float64))
+    got = out.cpu().numpy().astype(np.float64)
+    assert np.abs(got[:, 1:] - ref[:, 1:]).max() <= 1e-4
+    assert np.all(np.abs(got[:, 0] - ref[:, 0]) <= 1e-4 * np.maximum(1.0, ref[:, 0]))
+    r.close()
+
+
+@pytest.mark.parametrize("W,H", [(32, 2), (64, 3)])
+def test_distill_loss_and_gradient_match_oracle(roam, room32, W, H):
+    w = F.xavier_weights(1, F.ROLE_STUDENT, room32.part.n_fields, W, H, bias_scale=0.1)
+    r = _ctx(roam, room32, W, H, w)
+    I = 48
+    p, d, f = F.distill_points(room32.scene, room32.part, 1, I)
+    pt, dt, ft = torch.from_numpy(p).cuda(), torch.from_numpy(d).cuda(), torch.from_numpy(f.astype(np.int16)).cuda()
+    t = r.teacher_eval(pt, dt)
+    s = r.mlp_eval(pt, dt, ft)
+    loss, dl = r.distill_loss(s, t, I)
+    g = r.mlp_backward(pt, dt, ft, dl)
+    torch.cuda.synchronize()
+    r.check()
+    loss_o, g_full = O.distill_loss_grad(w, room32.affine, W, H, SIGMA_SCALE, p, d, f,
+                                         t.cpu().numpy().astype(np.float64), float(I))
+    assert abs(float(loss) - loss_o) <= 1e-5 * abs(loss_o)
+    # the same output gradients on both sides, with the samples the oracle
+    # finds at a ReLU kink (|pre-activation| < 1e-4, where FP32 may take the
+    # other branch) zeroed: then the adjoints agree to FP32 rounding
+    dl_np = dl.cpu().numpy().astype(np.float64)
+    _, margin = O.mlp_grad_points(w, room32.affine, W, H, SIGMA_SCALE, p, d, f, dl_np)
+    kink = margin < 1e-4
+    assert kink.mean() < 0.05
+    dl_np[kink] = 0.0
+    dl_c = torch.from_numpy(dl_np.astype(np.float32)).cuda()
+    g = r.mlp_backward(pt, dt, ft, dl_c)
+    torch.cuda.synchronize()
+    g_o, _ = O.mlp_grad_points(w, room32.affine, W, H, SIGMA_SCALE, p, d, f, dl_np.astype(np.float32))
+    gm = np.abs(g_o).max()
+    assert np.abs(g.cpu().numpy() - g_o).max() <= 1e-4 * gm
+    # the loss gradient itself (every sample) matches the oracle's Eq. 7
+    # gradient in norm
+    g_all = r.mlp_backward(pt, dt, ft, dl)
+    torch.cuda.synchronize()
+    assert np.linalg.norm(g_all.cpu().numpy() - g_full) <= 1e-2 * np.linalg.norm(g_full)
+    r.close()
+
+
+def test_distillation_lowers_the_loss(roam, room32):
+    W, H = 32, 2
+    w = F.xavier_weights(1, F.ROLE_STUDENT, room32.part.n_fields, W, H)
+    r = _ctx(roam, room32, W, H, w)
+    I = 256
+    losses = []
+    for step in range(1, 41):
+        p, d, f = F.distill_points(room32.scene, room32.part, 1, I, step=step)
+        loss = r.distill_step(torch.from_numpy(p).cuda(), torch.from_numpy(d).cuda(),
+                              torch.from_numpy(f.astype(np.int16)).cuda(), I, lr=3e-3, step=step)
+        losses.append(float(loss))
+    assert np.mean(losses[-5:]) < 0.5 * np.mean(losses[:5]), losses
+    r.close()
