@@ -189,8 +189,8 @@ def time_steps(r, cams, opts, steps, warmup, flush, stream):
 
 def train_step_bench(roam, F, torch, wl, args, stream):
     """One fine-tuning step = forward (BF16 tensor cores) + L2 loss + adjoint
-    (composite + FP32 MLP adjoint) + Adam, on 65,536 rays of 16 1024x512
-    equirect views of the floor (targets rendered once, untimed)."""
+    (composite + BF16 tensor-core MLP adjoint) + Adam, on 65,536 rays of 16
+    1024x512 equirect views of the floor (targets rendered once, untimed)."""
     import numpy as np
     cams = F.make_cameras(wl.scene, 3, [(F.EQUIRECT, 1024, 512, 0.0)] * 16)
     teacher = roam.Roam(torch.cuda.current_device())
@@ -233,11 +233,22 @@ def train_step_bench(roam, F, torch, wl, args, stream):
     ms = a.elapsed_time(b) / steps
     st = r.get_stats()
     r.close()
-    return {"workload": "floor256_kd512_w64h3, 16 equirect 1024x512 views, 65536 random rays, teacher+N(0,0.01^2) targets",
-            "ms_per_step": ms, "rays_per_s": n / (ms / 1000.0), "samples_per_step": int(st.n_samples),
-            "loss_first_last": [float(losses[0]), float(losses[-1])],
-            "kernels": {k: {"launches": v[0], "ms": round(v[1], 3)} for k, v in prof.items()},
-            "precision": "forward BF16 tcgen05, adjoint FP32 SIMT, FP32 master weights"}
+    out = {"workload": "floor256_kd512_w64h3, 16 equirect 1024x512 views, 65536 random rays, teacher+N(0,0.01^2) targets",
+           "ms_per_step": ms, "rays_per_s": n / (ms / 1000.0), "samples_per_step": int(st.n_samples),
+           "loss_first_last": [float(losses[0]), float(losses[-1])],
+           "kernels": {k: {"launches": v[0], "ms": round(v[1], 3)} for k, v in prof.items()},
+           "precision": "forward BF16 tcgen05, adjoint BF16 tcgen05 (FP32 accumulation), FP32 master weights"}
+    bw = prof.get("mlp_bwd_bf16_tcgen05")
+    if bw and bw[1] > 0:
+        # adjoint work per sample: forward recompute + wgrad + dgrad (no dgrad into the encoding)
+        macs = macs_per_sample(wl.W, wl.H)
+        flops = 2.0 * (3 * macs - wl.W * 63)
+        per_launch_s = bw[1] / bw[0] / 1000.0
+        samples = st.n_samples
+        out["mlp_adjoint"] = {"flops_per_sample": flops, "tflops": flops * samples / per_launch_s / 1e12,
+                              "ms_per_launch": bw[1] / bw[0]}
+    return out
+
 
 
 def accuracy(got, ref):
@@ -424,6 +435,62 @@ def stereo_bench(roam, F, torch, stream):
             "fps_at_median": 1000.0 / float(np.median(t))}
 
 
+def distill_bench(roam, F, torch, args, stream):
+    """One distillation step (Eq. 7) on the floor256 partition: the global
+    360NeRF teacher (8x256, 595,844 parameters, FP32 cuBLAS layers) labels
+    256 points per field in each of the 512 fields; the W=64/H=3 students
+    are evaluated (BF16 tensor cores), the loss and its output gradient
+    formed, the adjoint run (BF16 tensor cores) and Adam applied."""
+    import numpy as np
+    wl = F.floor256(views="equirect")
+    I = 256
+    p, d, f = F.distill_points(wl.scene, wl.part, 2, I)
+    pt, dt = torch.from_numpy(p).cuda(), torch.from_numpy(d).cuda()
+    ft = torch.from_numpy(f.astype(np.int16)).cuda()
+    student = F.xavier_weights(2, F.ROLE_STUDENT, wl.part.n_fields, wl.W, wl.H, bias_scale=0.1)
+    r = roam.Roam(torch.cuda.current_device())
+    r.load_grid(wl.scene.bits, wl.scene.dims, wl.scene.origin, wl.scene.vox)
+    r.load_fields(wl.part.field_of_rank, wl.affine)
+    r.load_weights(student, wl.W, wl.H, 2.0)
+    r.teacher_load(F.teacher_weights(3, bias_scale=0.1), F.scene_affine(wl.scene))
+    losses = []
+
+    def step(k):
+        return r.distill_step(pt, dt, ft, float(I), lr=1e-3, step=k, precision=roam.ROAM_BF16, stream=stream)
+
+    for k in range(1, 4):
+        step(k)
+    torch.cuda.synchronize()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    steps = max(5, args.steps)
+    r.profile(True)
+    a.record(stream)
+    for k in range(4, 4 + steps):
+        losses.append(step(k))
+    b.record(stream)
+    b.synchronize()
+    prof = r.profile_read()
+    r.profile(False)
+    ms = a.elapsed_time(b) / steps
+    # the teacher alone
+    with torch.cuda.stream(stream):
+        a.record(stream)
+        for _ in range(steps):
+            r.teacher_eval(pt, dt, stream=stream)
+        b.record(stream)
+    b.synchronize()
+    t_ms = a.elapsed_time(b) / steps
+    n = int(p.shape[0])
+    r.close()
+    return {"workload": f"floor256_kd512_w64h3 students, 360NeRF teacher, {I} points per field ({n} per step)",
+            "ms_per_step": ms, "points_per_s": n / (ms / 1000.0), "teacher_ms": t_ms,
+            "teacher_tflops": 2.0 * 595844 * n / (t_ms / 1000.0) / 1e12,
+            "loss_first_last": [float(losses[0]), float(losses[-1])],
+            "kernels": {k: {"launches": v[0], "ms": round(v[1], 3)} for k, v in prof.items()},
+            "precision": "teacher FP32 (cuBLAS), students BF16 tcgen05 forward and adjoint, FP32 master weights"}
+
+
 def partition_bench(roam, F, torch, args, stream, flush):
     """Partitions of the floor256 scene into 512 fields compared on the
     1024x512 equirect view (W=64/H=3, BF16): kd (median splits), Alg. 1
@@ -483,6 +550,8 @@ def main():
     ap.add_argument("--quick", action="store_true",
                     help="headline loop only (no FP32 comparison, accuracy, e2e or CPU baseline): for profilers")
     ap.add_argument("--views", default="both", choices=["both", "equirect", "perspective"])
+    ap.add_argument("--section", default=None, choices=["train", "distill"],
+                    help="run one secondary section alone and print its JSON (for profilers)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
@@ -493,6 +562,15 @@ def main():
 
     import fixtures as F
     import paper_2208_02705_gb300 as roam
+
+    if args.section is not None:
+        stream = torch.cuda.current_stream()
+        if args.section == "train":
+            res = train_step_bench(roam, F, torch, F.floor256(), args, stream)
+        else:
+            res = distill_bench(roam, F, torch, args, stream)
+        print(json.dumps({"section": args.section, **res}), flush=True)
+        return 0
 
     world, rank, local = dist_setup()
     torch.cuda.set_device(local)
@@ -624,8 +702,9 @@ def main():
     if rank == 0:
         train = train_step_bench(roam, F, torch, wl, args, stream)
 
-    large = multiview = occupancy = stereo = partition = None
+    large = multiview = occupancy = stereo = partition = distill = None
     if rank == 0:
+        distill = distill_bench(roam, F, torch, args, stream)
         large = large_scene_bench(roam, F, torch, args, stream, flush, peaks)
         multiview = multiview_bench(roam, F, torch, args, stream, flush)
         occupancy = occupancy_bench(roam, F, torch, args, stream)
@@ -649,7 +728,7 @@ def main():
                 "accuracy_vs_oracle": acc, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "train_step": train, "large_scene": large, "multi_view": multiview,
                 "occupancy_update": occupancy, "stereo_roaming": stereo,
-                "partitions": partition,
+                "partitions": partition, "distillation": distill,
                 "gpu_launches": int(6 * st.n_rounds * args.steps), "clocks": clocks}
         print(json.dumps(line), flush=True)
     r.close()

@@ -263,10 +263,13 @@ roam_status roam_distill_loss(roam_ctx *ctx, const float *student, const float *
  * gradient of every sample's output: p, d device float[n][3], field device
  * uint16[n], dl_dout device float[n][4] (d loss / d (sigma, r, g, b));
  * grad device float[n_fields][P] (overwritten), the layout of
- * roam_load_weights.  FP32 adjoint; one MLP width (32 or 64) for every
- * field.  Asynchronous. */
+ * roam_load_weights.  One MLP width (32 or 64) for every field.
+ * precision ROAM_F32: FP32 SIMT adjoint (recomputes the forward pass in
+ * FP32); ROAM_BF16: tcgen05 adjoint of the BF16 forward pass (BF16
+ * operands, FP32 accumulation; W = 32 with H <= 4 or W = 64 with H <= 3,
+ * else ROAM_ERR_UNSUPPORTED).  Asynchronous. */
 roam_status roam_mlp_backward(roam_ctx *ctx, const float *p, const float *d, const uint16_t *field, int64_t n,
-                              const float *dl_dout, float *grad, void *stream);
+                              int precision, const float *dl_dout, float *grad, void *stream);
 
 /* Chooses the round size (kept samples marched per live ray per round) for
  * this camera batch and these options: renders the batch once per candidate
@@ -362,8 +365,10 @@ roam_status roam_train_forward(roam_ctx *ctx, const roam_camera *cams, int n_vie
 /* Backward pass of the last roam_train_forward: dl_drgb device
  * float[n_rays][3]; grad device float[n_fields][P] receives d(loss)/d(weights)
  * (overwritten), in the layout of roam_load_weights.  Recomputes the
- * positional encodings and MLP activations instead of storing them.
- * Asynchronous. */
+ * positional encodings and MLP activations instead of storing them.  The
+ * MLP adjoint follows the forward's precision: FP32 SIMT after a ROAM_F32
+ * forward, tcgen05 BF16 after a ROAM_BF16 one (FP32 SIMT where the shape is
+ * outside the tensor-core adjoint's, see roam_mlp_backward).  Asynchronous. */
 roam_status roam_train_backward(roam_ctx *ctx, const float *dl_drgb, float *grad, void *stream);
 
 /* L2 photometric loss of the fine-tuning stage on device arrays rgb and

@@ -87,7 +87,9 @@ def lib():
         L.orc_teacher_eval.argtypes = [f32p, f64p, I64, f64p, f64p, f64p]
         L.orc_distill_loss_grad.argtypes = [f32p, f32p, I, I, I, I, D, I64, f64p, f64p, i32p, f64p, D, f64p]
         L.orc_distill_loss_grad.restype = D
-        L.orc_mlp_grad_points.argtypes = [f32p, f32p, I, I, I, I, D, I64, f64p, f64p, i32p, f64p, f64p, f64p]
+        L.orc_mlp_grad_points.argtypes = [f32p, f32p, I, I, I, I, D, I, I64, f64p, f64p, i32p, f64p, f64p, f64p]
+        L.orc_bf16.argtypes = [D]
+        L.orc_bf16.restype = D
         _lib = L
     return _lib
 
@@ -384,9 +386,16 @@ def distill_loss_grad(weights, affine, W: int, H: int, sigma_scale: float, p, d,
     return float(loss), g
 
 
-def mlp_grad_points(weights, affine, W: int, H: int, sigma_scale: float, p, d, field, dl, act: int = 0):
+def bf16(x: float) -> float:
+    """Nearest BF16 value (ties to even)."""
+    return lib().orc_bf16(float(x))
+
+
+def mlp_grad_points(weights, affine, W: int, H: int, sigma_scale: float, p, d, field, dl, act: int = 0,
+                    quant: int = 0):
     """The MLP adjoint at points for given output gradients dl [n, 4]:
-    (gradient [F, P], smallest |ReLU pre-activation| per sample)."""
+    (gradient [F, P], smallest |ReLU pre-activation| per sample).  quant=2
+    takes the BF16 reading of the forward pass and the adjoint."""
     w = np.ascontiguousarray(weights, dtype=np.float32)
     aff = np.ascontiguousarray(affine, dtype=np.float32)
     F_ = int(aff.shape[0])
@@ -397,7 +406,7 @@ def mlp_grad_points(weights, affine, W: int, H: int, sigma_scale: float, p, d, f
     g = np.zeros((F_, param_count(W, H)))
     margin = np.zeros(p.shape[0])
     lib().orc_mlp_grad_points(_p(w, ctypes.c_float), _p(aff, ctypes.c_float), F_, W, H, act, f32(sigma_scale),
-                              int(p.shape[0]), _p(p, ctypes.c_double), _p(d, ctypes.c_double),
+                              int(quant), int(p.shape[0]), _p(p, ctypes.c_double), _p(d, ctypes.c_double),
                               _p(fl, ctypes.c_int32), _p(g_out, ctypes.c_double), _p(g, ctypes.c_double),
                               _p(margin, ctypes.c_double))
     return g, margin

@@ -55,6 +55,16 @@
  * after division by a per-output-row scale s = max |row| / 448 (s and the
  * division in FP32), then y = bias + s * sum(products), everything else in
  * FP64 as above.
+ *
+ * The BF16 reading (quant == 2, the library's BF16 tensor-core path at
+ * W <= 64, where every bias rides in the matrix product): every matrix
+ * layer but the 3-output one takes its inputs, weights and bias rounded to
+ * BF16 (8 significant bits, nearest, ties to even) and sums in FP64; the
+ * 3-output layer stays FP64 on the FP32 weights.  Its adjoint rounds to BF16
+ * what that path keeps as BF16 operands: each layer's output gradient dz
+ * (after the ReLU mask), the layer inputs it multiplies, and the weights of
+ * the products that carry dz down; the 3-output layer's dz and its input g
+ * enter its weight gradient rounded too.
  */
 #define _GNU_SOURCE
 #include <math.h>
@@ -273,7 +283,7 @@ static void encode(const double *x, int L, double *out)
 typedef struct {
     int W, H, act;
     double sigma_scale;
-    int quant;                  /* 1: the FP8 E4M3 reading of the matrix layers */
+    int quant;                  /* 1: the FP8 E4M3 reading, 2: the BF16 reading */
 } orc_arch;
 
 /* y[o] = b[o] + sum_i Wm[o][i] x[i] */
@@ -322,6 +332,32 @@ static void dense_e4m3(const float *Wm, const float *b, int n_out, int n_in, con
     }
 }
 
+/* Nearest BF16 value (8 significant bits: a = m 2^e with m in [0.5, 1) is
+ * rounded to a multiple of 2^(e-8)), ties to even; the magnitudes here stay
+ * far inside the format's normal range. */
+static double bf16r(double x)
+{
+    if (x == 0.0 || !isfinite(x)) return x;
+    int e;
+    frexp(fabs(x), &e);
+    const double q = ldexp(1.0, e - 8);
+    return copysign(nearbyint(fabs(x) / q) * q, x);
+}
+
+double orc_bf16(double x) { return bf16r(x); }
+
+/* dense() in the BF16 reading: inputs, weights and bias rounded to BF16 */
+static void dense_bf16(const float *Wm, const float *b, int n_out, int n_in, const double *x, double *y)
+{
+    double xq[512];
+    for (int c = 0; c < n_in; ++c) xq[c] = bf16r(x[c]);
+    for (int r = 0; r < n_out; ++r) {
+        double acc = bf16r((double)b[r]);
+        for (int c = 0; c < n_in; ++c) acc += bf16r((double)Wm[(int64_t)r * n_in + c]) * xq[c];
+        y[r] = acc;
+    }
+}
+
 static double softplus(double s) { return s > 30.0 ? s : log1p(exp(s)); }
 static double sigm(double s) { return 1.0 / (1.0 + exp(-s)); }
 
@@ -347,7 +383,8 @@ static void mlp_forward(const float *w, const orc_arch *A, const double *aff, co
     encode(xl, 10, c->pe_x);
     const float *q = w;
     double h[256];
-    void (*mat)(const float *, const float *, int, int, const double *, double *) = A->quant ? dense_e4m3 : dense;
+    void (*mat)(const float *, const float *, int, int, const double *, double *) =
+        A->quant == 1 ? dense_e4m3 : (A->quant == 2 ? dense_bf16 : dense);
     mat(q, q + W * ORC_PE_POS, W, ORC_PE_POS, c->pe_x, c->z[0]);
     q += W * ORC_PE_POS + W;
     for (int r = 0; r < W; ++r) h[r] = c->z[0][r] > 0.0 ? c->z[0][r] : 0.0;
@@ -391,6 +428,9 @@ static void mlp_backward(const float *w, const orc_arch *A, const orc_cache *c, 
                          const double *drgb, double *gw)
 {
     int W = A->W, H = A->H;
+    /* the BF16 reading rounds operands (see the header); otherwise identity */
+    const int rb = A->quant == 2;
+#define RQ(x) (rb ? bf16r(x) : (x))
     /* offsets of each layer in the flat parameter vector */
     int64_t off[16];
     int64_t o = 0;
@@ -400,9 +440,9 @@ static void mlp_backward(const float *w, const orc_arch *A, const orc_cache *c, 
     int64_t off_c = o; o += (int64_t)W * (W + ORC_PE_DIR) + W;
     int64_t off_o = o;
 
-    double h[8][256];               /* post-activation of layers 1..H */
+    double h[8][256];               /* post-activation of layers 1..H (as the next layer reads them) */
     for (int k = 0; k < H; ++k)
-        for (int r = 0; r < W; ++r) h[k][r] = c->z[k][r] > 0.0 ? c->z[k][r] : 0.0;
+        for (int r = 0; r < W; ++r) h[k][r] = RQ(c->z[k][r] > 0.0 ? c->z[k][r] : 0.0);
     double g[256];
     for (int r = 0; r < W; ++r) g[r] = c->zc[r] > 0.0 ? c->zc[r] : 0.0;
 
@@ -414,10 +454,10 @@ static void mlp_backward(const float *w, const orc_arch *A, const orc_cache *c, 
     for (int i = 0; i < W; ++i) dg[i] = 0.0;
     for (int r = 0; r < 3; ++r) {
         for (int i = 0; i < W; ++i) {
-            gw[off_o + (int64_t)r * W + i] += dzo[r] * g[i];
+            gw[off_o + (int64_t)r * W + i] += RQ(dzo[r]) * RQ(g[i]);
             dg[i] += (double)Wo[r * W + i] * dzo[r];
         }
-        gw[off_o + 3 * W + r] += dzo[r];
+        gw[off_o + 3 * W + r] += RQ(dzo[r]);
     }
     /* colour layer: g = relu(zc), zc = Wc [feat; F(d)] + bc */
     int Kc = W + ORC_PE_DIR;
@@ -425,17 +465,17 @@ static void mlp_backward(const float *w, const orc_arch *A, const orc_cache *c, 
     double dfeat[256];
     for (int i = 0; i < W; ++i) dfeat[i] = 0.0;
     for (int r = 0; r < W; ++r) {
-        double dz = c->zc[r] > 0.0 ? dg[r] : 0.0;
+        double dz = RQ(c->zc[r] > 0.0 ? dg[r] : 0.0);
         if (dz == 0.0) continue;
-        for (int i = 0; i < Kc; ++i) gw[off_c + (int64_t)r * Kc + i] += dz * c->in_c[i];
-        for (int i = 0; i < W; ++i) dfeat[i] += (double)Wc[(int64_t)r * Kc + i] * dz;
+        for (int i = 0; i < Kc; ++i) gw[off_c + (int64_t)r * Kc + i] += dz * RQ(c->in_c[i]);
+        for (int i = 0; i < W; ++i) dfeat[i] += RQ((double)Wc[(int64_t)r * Kc + i]) * dz;
         gw[off_c + (int64_t)W * Kc + r] += dz;
     }
     /* head: [s; feat] = Wh h_H + bh; sigma = scale * softplus(s) */
     double s = c->zh[0];
     double dz_h[257];
-    dz_h[0] = dsigma * A->sigma_scale * (A->act == 1 ? (s > 0.0 ? 1.0 : 0.0) : sigm(s));
-    for (int i = 0; i < W; ++i) dz_h[1 + i] = dfeat[i];
+    dz_h[0] = RQ(dsigma * A->sigma_scale * (A->act == 1 ? (s > 0.0 ? 1.0 : 0.0) : sigm(s)));
+    for (int i = 0; i < W; ++i) dz_h[1 + i] = RQ(dfeat[i]);
     const float *Wh = w + off_h;
     double dh[256];
     for (int i = 0; i < W; ++i) dh[i] = 0.0;
@@ -444,7 +484,7 @@ static void mlp_backward(const float *w, const orc_arch *A, const orc_cache *c, 
         if (dz == 0.0) continue;
         for (int i = 0; i < W; ++i) {
             gw[off_h + (int64_t)r * W + i] += dz * h[H - 1][i];
-            dh[i] += (double)Wh[(int64_t)r * W + i] * dz;
+            dh[i] += RQ((double)Wh[(int64_t)r * W + i]) * dz;
         }
         gw[off_h + (int64_t)(1 + W) * W + r] += dz;
     }
@@ -454,11 +494,11 @@ static void mlp_backward(const float *w, const orc_arch *A, const orc_cache *c, 
         double dprev[256];
         for (int i = 0; i < W; ++i) dprev[i] = 0.0;
         for (int r = 0; r < W; ++r) {
-            double dz = c->z[k][r] > 0.0 ? dh[r] : 0.0;
+            double dz = RQ(c->z[k][r] > 0.0 ? dh[r] : 0.0);
             if (dz == 0.0) continue;
             for (int i = 0; i < W; ++i) {
                 gw[off[k] + (int64_t)r * W + i] += dz * h[k - 1][i];
-                dprev[i] += (double)Wk[(int64_t)r * W + i] * dz;
+                dprev[i] += RQ((double)Wk[(int64_t)r * W + i]) * dz;
             }
             gw[off[k] + (int64_t)W * W + r] += dz;
         }
@@ -466,11 +506,12 @@ static void mlp_backward(const float *w, const orc_arch *A, const orc_cache *c, 
     }
     /* layer 1 */
     for (int r = 0; r < W; ++r) {
-        double dz = c->z[0][r] > 0.0 ? dh[r] : 0.0;
+        double dz = RQ(c->z[0][r] > 0.0 ? dh[r] : 0.0);
         if (dz == 0.0) continue;
-        for (int i = 0; i < ORC_PE_POS; ++i) gw[off[0] + (int64_t)r * ORC_PE_POS + i] += dz * c->pe_x[i];
+        for (int i = 0; i < ORC_PE_POS; ++i) gw[off[0] + (int64_t)r * ORC_PE_POS + i] += dz * RQ(c->pe_x[i]);
         gw[off[0] + (int64_t)W * ORC_PE_POS + r] += dz;
     }
+#undef RQ
 }
 
 /* ------------------------------------------------------------------ */
@@ -1218,12 +1259,13 @@ double orc_distill_loss_grad(const float *weights, const float *affine, int n_fi
  * gradients dl[n][4] = d loss / d (sigma, r, g, b): grad[F][P] (zeroed here)
  * = sum_i J_i^T dl_i.  margin[i] (may be NULL) receives the smallest
  * |pre-activation| over the sample's ReLU units: below ~1e-4 an FP32
- * evaluation may take the other branch (a near-kink). */
+ * evaluation may take the other branch (a near-kink).  quant 0: FP64;
+ * quant 2: the BF16 reading of the forward pass and its adjoint. */
 void orc_mlp_grad_points(const float *weights, const float *affine, int n_fields, int W, int H, int act,
-                         double sigma_scale, int64_t n, const double *p, const double *d, const int32_t *field,
-                         const double *dl, double *grad, double *margin)
+                         double sigma_scale, int quant, int64_t n, const double *p, const double *d,
+                         const int32_t *field, const double *dl, double *grad, double *margin)
 {
-    orc_arch A = {W, H, act, sigma_scale, 0};
+    orc_arch A = {W, H, act, sigma_scale, quant};
     const int64_t P = orc_param_count(W, H);
     for (int64_t i = 0; i < P * n_fields; ++i) grad[i] = 0.0;
     for (int64_t i = 0; i < n; ++i) {

@@ -113,7 +113,7 @@ def load_library(path: str = LIB_PATH):
     L.roam_teacher_load.argtypes = [vp, vp, vp, i32]
     L.roam_teacher_eval.argtypes = [vp, vp, vp, i64, vp, vp]
     L.roam_distill_loss.argtypes = [vp, vp, vp, i64, ctypes.c_float, vp, vp, vp]
-    L.roam_mlp_backward.argtypes = [vp, vp, vp, vp, i64, vp, vp, vp]
+    L.roam_mlp_backward.argtypes = [vp, vp, vp, vp, i64, i32, vp, vp, vp]
     L.roam_get_weights.argtypes = [vp, vp, i32]
     L.roam_render.argtypes = [vp, P(roam_camera), i32, P(roam_render_opts), vp, vp, vp, i32, vp]
     L.roam_get_stats.argtypes = [vp, P(roam_stats)]
@@ -362,22 +362,24 @@ class Roam:
                                         _stream(stream)))
         return loss, dl
 
-    def mlp_backward(self, p, d, field, dl_dout, stream=None):
+    def mlp_backward(self, p, d, field, dl_dout, precision=ROAM_F32, stream=None):
         import torch
         grad = torch.empty((self.n_fields, self.P), dtype=torch.float32, device=self._dev())
-        _check(self.L.roam_mlp_backward(self.h, _ptr(p), _ptr(d), _ptr(field), int(p.shape[0]), _ptr(dl_dout),
-                                        _ptr(grad), _stream(stream)))
+        _check(self.L.roam_mlp_backward(self.h, _ptr(p), _ptr(d), _ptr(field), int(p.shape[0]), int(precision),
+                                        _ptr(dl_dout), _ptr(grad), _stream(stream)))
         return grad
 
     def distill_step(self, p, d, field, I: float, lr: float, step: int, teacher_out=None, precision=None,
                      stream=None):
         """One distillation step (Eq. 7): teacher targets (computed unless
         given), student outputs (FP32 by default), loss and its gradient,
-        the FP32 adjoint and Adam.  Returns the loss (device tensor)."""
+        the adjoint in the same precision (FP32 SIMT or BF16 tcgen05) and
+        Adam.  Returns the loss (device tensor)."""
+        prec = ROAM_F32 if precision is None else precision
         t = teacher_out if teacher_out is not None else self.teacher_eval(p, d, stream=stream)
-        sdt = self.mlp_eval(p, d, field, ROAM_F32 if precision is None else precision, stream=stream)
+        sdt = self.mlp_eval(p, d, field, prec, stream=stream)
         loss, dl = self.distill_loss(sdt, t, I, stream=stream)
-        g = self.mlp_backward(p, d, field, dl, stream=stream)
+        g = self.mlp_backward(p, d, field, dl, precision=prec, stream=stream)
         self.adam_step(g, lr=lr, step=step, stream=stream)
         return loss
 

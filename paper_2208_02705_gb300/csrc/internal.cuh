@@ -221,6 +221,11 @@ void launch_composite_bwd(int64_t n_rays, int R, const uint32_t *cnt, const uint
 void launch_mlp_bwd_simt(const MlpWeights &w, const SampleSrc &src, const BucketBufs &b, Counters *ctr,
                          const float4 *gsr, float *grad, int grid, cudaStream_t s);
 bool mlp_bwd_supported(int W, int H);
+// tcgen05 BF16 adjoint (W <= 64 and the shared-memory budget: W = 32 with
+// H <= 4, W = 64 with H <= 3); needs the BF16 weight images
+bool mlp_bwd_tc_supported(int W, int H);
+void launch_mlp_bwd_tc(const MlpWeights &w, const SampleSrc &src, const BucketBufs &b, Counters *ctr,
+                       const float4 *gsr, float *grad, int n_sm, cudaStream_t s);
 void launch_pack_rows(const float *w32, int n_fields, int W, int H, int64_t P, float *wr, int64_t Pr,
                       cudaStream_t s);
 int64_t rows_padded_size(int W, int H);

@@ -185,9 +185,10 @@ struct roam_ctx {
 namespace {
 
 const char *const kProfNames[] = {"march", "bucket", "mlp_f32_simt", "mlp_bf16_tcgen05", "composite",
-                                  "composite_bwd", "mlp_bwd", "adam", "mlp_fp8_tcgen05"};
-constexpr int kProfKinds = 9;
-enum { P_MARCH, P_BUCKET, P_MLP_F32, P_MLP_BF16, P_COMPOSITE, P_COMPOSITE_BWD, P_MLP_BWD, P_ADAM, P_MLP_FP8 };
+                                  "composite_bwd", "mlp_bwd", "adam", "mlp_fp8_tcgen05", "mlp_bwd_bf16_tcgen05"};
+constexpr int kProfKinds = (int)(sizeof(kProfNames) / sizeof(kProfNames[0]));
+enum { P_MARCH, P_BUCKET, P_MLP_F32, P_MLP_BF16, P_COMPOSITE, P_COMPOSITE_BWD, P_MLP_BWD, P_ADAM, P_MLP_FP8,
+       P_MLP_BWD_TC };
 
 cudaEvent_t pool_event(roam_ctx *c)
 {
@@ -1188,13 +1189,17 @@ roam_status roam_distill_loss(roam_ctx *c, const float *student, const float *te
 }
 
 roam_status roam_mlp_backward(roam_ctx *c, const float *p, const float *d, const uint16_t *field, int64_t n,
-                              const float *dl_dout, float *grad, void *stream)
+                              int precision, const float *dl_dout, float *grad, void *stream)
 {
     ROAM_TRY(set_dev(c));
     ROAM_TRY(check_ready(c));
     if (c->n_ws != 1) return fail(ROAM_ERR_UNSUPPORTED, "training needs one MLP width for every field");
     if (!mlp_bwd_supported(c->md.width, c->md.n_hidden))
         return fail(ROAM_ERR_UNSUPPORTED, "training supports W = 32 or 64");
+    if (precision != ROAM_F32 && precision != ROAM_BF16) return fail(ROAM_ERR_ARG, "precision: ROAM_F32 or ROAM_BF16");
+    const bool tc = precision == ROAM_BF16;
+    if (tc && (!mlp_bwd_tc_supported(c->md.width, c->md.n_hidden) || !c->ws[0].tc_ok))
+        return fail(ROAM_ERR_UNSUPPORTED, "the BF16 adjoint supports W = 32 (H <= 4) and W = 64 (H <= 3)");
     if (n < 0 || n > 0x7fffffff) return fail(ROAM_ERR_ARG, "bad sample count");
     if (!grad) return fail(ROAM_ERR_ARG, "null gradient");
     cudaStream_t s = (cudaStream_t)stream;
@@ -1213,7 +1218,10 @@ roam_status roam_mlp_backward(roam_ctx *c, const float *p, const float *d, const
     src.mode = 1;
     src.p = p;
     src.d = d;
-    {
+    if (tc) {
+        ProfScope ps(c, P_MLP_BWD_TC, s);
+        launch_mlp_bwd_tc(weights_of(c), src, b, c->ctr, reinterpret_cast<const float4 *>(dl_dout), grad, c->n_sm, s);
+    } else {
         ProfScope ps(c, P_MLP_BWD, s);
         launch_mlp_bwd_simt(weights_of(c), src, b, c->ctr, reinterpret_cast<const float4 *>(dl_dout), grad, c->n_sm,
                             s);
@@ -1458,7 +1466,10 @@ roam_status roam_train_backward(roam_ctx *c, const float *dl_drgb, float *grad, 
     src.st = state_of(c);
     src.delta = o.delta;
     src.accurate = o.precision == ROAM_F32;
-    {
+    if (o.precision == ROAM_BF16 && mlp_bwd_tc_supported(c->md.width, c->md.n_hidden) && c->ws[0].tc_ok) {
+        ProfScope ps(c, P_MLP_BWD_TC, s);
+        launch_mlp_bwd_tc(weights_of(c), src, b, c->ctr, c->gsr.p, grad, c->n_sm, s);
+    } else {
         ProfScope ps(c, P_MLP_BWD, s);
         launch_mlp_bwd_simt(weights_of(c), src, b, c->ctr, c->gsr.p, grad, c->n_sm, s);
     }

@@ -987,3 +987,105 @@ def test_point_adjoint_matches_central_differences(room32):
         assert abs(fd - g[fi, k]) <= 1e-5 * max(1.0, abs(fd)), (fi, k, fd, g[fi, k])
         checked += 1
     assert checked >= 8
+
+
+# ---- the BF16 reading (the library's BF16 tensor-core path) ----
+
+def test_bf16_rounding_matches_library_conversion():
+    """Nearest-even rounding to 8 significant bits: closed-form cases, and
+    PyTorch's float32 -> bfloat16 conversion on FP32 inputs."""
+    torch = pytest.importorskip("torch")
+    assert O.bf16(1.0 + 2.0 ** -8) == 1.0                       # tie, to even
+    assert O.bf16(1.0 + 3 * 2.0 ** -8) == 1.0 + 2.0 ** -6       # tie, to even (upwards)
+    assert O.bf16(1.0 + 2.0 ** -8 + 2.0 ** -20) == 1.0 + 2.0 ** -7
+    assert O.bf16(-3.14159) == -3.140625
+    assert O.bf16(0.0) == 0.0
+    x = np.random.default_rng(3).normal(size=2000).astype(np.float32) * np.float32(10.0) ** \
+        np.random.default_rng(4).integers(-8, 8, 2000).astype(np.float32)
+    ref = torch.from_numpy(x).to(torch.bfloat16).to(torch.float64).numpy()
+    got = np.array([O.bf16(float(v)) for v in x])
+    assert np.array_equal(got, ref)
+
+
+def _bf16_np(x):
+    x = np.asarray(x, dtype=np.float64)
+    m, e = np.frexp(np.abs(x))
+    q = np.ldexp(1.0, e - 8)
+    return np.where(x == 0, 0.0, np.copysign(np.round(np.abs(x) / q) * q, x))
+
+
+def _pe_np(x, L):
+    cols = [x]
+    for k in range(L):
+        cols.append(np.sin(np.pi * 2.0 ** k * x))
+        cols.append(np.cos(np.pi * 2.0 ** k * x))
+    return np.concatenate(cols, axis=1)
+
+
+def _bf16_reading_np(wf, aff, W, H, sig, p, d, dl):
+    """An independent NumPy chain of the BF16 reading for one field: every
+    matrix layer but the 3-output one on BF16 inputs, weights and biases;
+    the adjoint on BF16 output gradients, inputs and weights."""
+    R = _bf16_np
+    layers, o = [], 0
+    for r, c in [(W, 63)] + [(W, W)] * (H - 1) + [(1 + W, W), (W, W + 27), (3, W)]:
+        layers.append((wf[o:o + r * c].reshape(r, c).astype(np.float64), wf[o + r * c:o + r * c + r].astype(np.float64)))
+        o += r * c + r
+    x = p * aff[:3] + aff[3:]
+    h, ins, zs = _pe_np(x, 10), [], []
+    for l in range(H):
+        M, b = layers[l]
+        ins.append(R(h))
+        z = R(h) @ R(M).T + R(b)
+        zs.append(z)
+        h = np.maximum(z, 0)
+    M, b = layers[H]
+    ins.append(R(h))
+    hd = R(h) @ R(M).T + R(b)
+    inc = np.concatenate([hd[:, 1:], _pe_np(d, 4)], axis=1)
+    Mc, bc = layers[H + 1]
+    zc = R(inc) @ R(Mc).T + R(bc)
+    g = np.maximum(zc, 0)
+    Mo, bo = layers[H + 2]
+    rgb = 1 / (1 + np.exp(-(g @ Mo.T + bo)))
+    out = np.concatenate([(sig * np.log1p(np.exp(hd[:, :1]))), rgb], axis=1)
+    grads = [None] * (H + 3)
+    dzo = dl[:, 1:] * rgb * (1 - rgb)
+    grads[H + 2] = (R(dzo).T @ R(g), R(dzo).sum(0))
+    dzc = R((dzo @ Mo) * (zc > 0))
+    grads[H + 1] = (dzc.T @ R(inc), dzc.sum(0))
+    dfeat = dzc @ R(Mc)[:, :W]
+    dsig = dl[:, 0] * sig / (1 + np.exp(-hd[:, 0]))
+    dzh = R(np.concatenate([dsig[:, None], dfeat], axis=1))
+    grads[H] = (dzh.T @ ins[H], dzh.sum(0))
+    dh = dzh @ R(M)
+    for l in range(H - 1, -1, -1):
+        dz = R(dh * (zs[l] > 0))
+        grads[l] = (dz.T @ ins[l], dz.sum(0))
+        if l > 0:
+            dh = dz @ R(layers[l][0])
+    return out, np.concatenate([np.concatenate([a.ravel(), b]) for a, b in grads])
+
+
+def test_bf16_reading_matches_independent_chain(room32):
+    W, H, sig = 16, 3, 1.5
+    w = F.xavier_weights(1, F.ROLE_STUDENT, room32.part.n_fields, W, H, bias_scale=0.2)
+    p, d, f = F.distill_points(room32.scene, room32.part, 2, 40)
+    dl = np.random.default_rng(6).normal(size=(p.shape[0], 4))
+    g, _ = O.mlp_grad_points(w, room32.affine, W, H, sig, p, d, f, dl, quant=2)
+    g64, _ = O.mlp_grad_points(w, room32.affine, W, H, sig, p, d, f, dl)
+    for fi in range(room32.part.n_fields):
+        m = f == fi
+        aff = room32.affine[fi].astype(np.float64)
+        out, gn = _bf16_reading_np(w[fi], aff, W, H, sig, p[m].astype(np.float64), d[m].astype(np.float64), dl[m])
+        assert np.allclose(g[fi], gn, rtol=1e-10, atol=1e-12 * np.abs(gn).max())
+        for i in np.nonzero(m)[0][:3]:
+            o = O.mlp(w[fi], W, H, sig, aff, p[i], d[i], quant=2)
+            j = int(np.count_nonzero(m[:i]))
+            assert np.allclose(o, out[j], rtol=1e-12, atol=1e-14)
+    # the rounding is applied: the reading moves away from FP64, and stays
+    # correlated with it (a few mask flips on 40 samples per field move
+    # single entries by up to ~15 % of max |g|)
+    rel = np.abs(g - g64).max() / np.abs(g64).max()
+    cos = float((g * g64).sum() / (np.linalg.norm(g) * np.linalg.norm(g64)))
+    assert 1e-5 < rel < 0.3 and cos > 0.99
