@@ -119,43 +119,49 @@ __device__ __forceinline__ void ld16f(uint32_t taddr, float (&v)[16])
     for (int q = 0; q < 16; ++q) v[q] = __uint_as_float(r[q]);
 }
 
-// Parameter index (API layout: per layer row-major [out][in] then bias[out])
-// of wgrad accumulator l at MMA output column n and feature row k, or -1.
+// Where feature row k of wgrad accumulator l lands in the API layout (per
+// layer row-major [out][in] then bias[out]): column n (n < n_rows) goes to
+// base + n * stride; the head's column W (its density logit, API row 0) to
+// base0.  base < 0: the row holds no parameter.
+struct RowMap {
+    int64_t base, stride, base0;
+    int n_rows;
+};
+
 template <int W, int H>
-__device__ __forceinline__ int64_t api_index(int l, int n, int k)
+__device__ __forceinline__ RowMap row_map(int l, int k)
 {
     const int64_t o_hid = (int64_t)W * kPeX + W;
     const int64_t o_head = o_hid + (int64_t)(H - 1) * (W * W + W);
     const int64_t o_col = o_head + (int64_t)(1 + W) * W + (1 + W);
     const int64_t o_out = o_col + (int64_t)W * (W + kPeD) + W;
+    RowMap m{-1, 0, -1, 0};
     if (l == 0) {
-        if (n >= W) return -1;
-        if (k < kPeX) return (int64_t)n * kPeX + k;
-        return k == kPeX ? (int64_t)W * kPeX + n : -1;
-    }
-    if (l < H) {
-        if (n >= W) return -1;
+        m.n_rows = W;
+        if (k < kPeX) { m.base = k; m.stride = kPeX; }
+        else if (k == kPeX) { m.base = (int64_t)W * kPeX; m.stride = 1; }
+    } else if (l < H) {
+        m.n_rows = W;
         const int64_t ob = o_hid + (int64_t)(l - 1) * (W * W + W);
-        if (k < W) return ob + (int64_t)n * W + k;
-        return k == W ? ob + (int64_t)W * W + n : -1;
-    }
-    if (l == H) {
+        if (k < W) { m.base = ob + k; m.stride = W; }
+        else if (k == W) { m.base = ob + (int64_t)W * W; m.stride = 1; }
+    } else if (l == H) {
         // MMA columns: W features (API rows 1..W), then the density logit (API row 0)
-        const int ar = n < W ? 1 + n : (n == W ? 0 : -1);
-        if (ar < 0) return -1;
-        if (k < W) return o_head + (int64_t)ar * W + k;
-        return k == W ? o_head + (int64_t)(1 + W) * W + ar : -1;
-    }
-    if (l == H + 1) {
-        if (n >= W) return -1;
+        m.n_rows = W;
+        if (k < W) { m.base = o_head + W + k; m.stride = W; m.base0 = o_head + k; }
+        else if (k == W) { m.base = o_head + (int64_t)(1 + W) * W + 1; m.stride = 1; m.base0 = o_head + (int64_t)(1 + W) * W; }
+    } else if (l == H + 1) {
+        m.n_rows = W;
         const int kc = W + kPeD;
-        if (k < W) return o_col + (int64_t)n * kc + k;
-        if (k == W) return o_col + (int64_t)W * kc + n;
-        return k <= W + kPeD ? o_col + (int64_t)n * kc + (k - 1) : -1;
+        if (k < W) { m.base = o_col + k; m.stride = kc; }
+        else if (k == W) { m.base = o_col + (int64_t)W * kc; m.stride = 1; }
+        else if (k <= W + kPeD) { m.base = o_col + (k - 1); m.stride = kc; }
+    } else {
+        m.n_rows = 3;
+        if (k < W) { m.base = o_out + k; m.stride = W; }
+        else if (k == W) { m.base = o_out + 3 * (int64_t)W; m.stride = 1; }
     }
-    if (n >= 3) return -1;
-    if (k < W) return o_out + (int64_t)n * W + k;
-    return k == W ? o_out + 3 * (int64_t)W + n : -1;
+    return m;
 }
 
 template <int W, int H>
@@ -240,23 +246,44 @@ __global__ void __launch_bounds__(128, 1)
         float *gf = grad + (int64_t)f * P;
 #pragma unroll 1
         for (int l = 0; l < H + 3; ++l) {
+            const RowMap m = row_map<W, H>(l, row);
 #pragma unroll 1
             for (int c = 0; c < B::wN(l); c += 16) {
                 float v[16];
                 ld16f(tmem + tlane + (uint32_t)(B::wcol(l) + c), v);
+                if (m.base < 0) continue;
 #pragma unroll
                 for (int q = 0; q < 16; ++q) {
-                    const int64_t ix = api_index<W, H>(l, c + q, row);
-                    if (ix >= 0 && v[q] != 0.f) atomicAdd(gf + ix, v[q]);
+                    const int n = c + q;
+                    if (v[q] == 0.f) continue;
+                    if (n < m.n_rows) atomicAdd(gf + m.base + (int64_t)n * m.stride, v[q]);
+                    else if (n == W && m.base0 >= 0) atomicAdd(gf + m.base0, v[q]);
                 }
             }
         }
         tc_fence_before();
     };
 
+    // the next tile's sample is gathered in stages during this tile's forward
+    // layers (index, then record and ray, then position), so no stage waits
+    // on its own load
+    Tile tl_cur{0u, 0u, 0u, 0u};
+    SampleIn nxt{0u, 0.f, 0.f, 0.f, 0.f, 0.f, 1.f};
+    Pending pend{};
+    if (t0 < t1) {
+        tl_cur = b.tiles[t0];
+        nxt = fetch_sample(src, b, tl_cur, row);
+    }
     for (uint32_t t = t0; t < t1 && !aborted; ++t) {
-        const Tile tl = b.tiles[t];
-        if (tl.count == 0) continue;
+        const Tile tl = tl_cur;
+        const bool more = t + 1 < t1;
+        const Tile tl_nx = more ? b.tiles[t + 1] : Tile{0u, 0u, 0u, 0u};
+        const SampleIn smp = nxt;
+        tl_cur = tl_nx;
+        if (tl.count == 0) {
+            if (more) nxt = fetch_sample(src, b, tl_nx, row);
+            continue;
+        }
         if (tl.field != cur) {
             if (cur != 0xffffffffu && !wnew) flush(cur);
             __syncthreads();
@@ -282,7 +309,6 @@ __global__ void __launch_bounds__(128, 1)
         }
 
         // ---- the sample ----
-        const SampleIn smp = fetch_sample(src, b, tl, row);
         const bool valid = (uint32_t)row < tl.count;
         const float4 dl = valid ? gsr[smp.idx] : make_float4(0.f, 0.f, 0.f, 0.f);
         const float *aff = affine + 6 * (int64_t)tl.field;
@@ -360,6 +386,9 @@ __global__ void __launch_bounds__(128, 1)
                     umma_ss(tD, sdesc(a), sdesc(ba + (uint32_t)(ch * N * 128 + kin * 32)), idesc, ks > 0 ? 1u : 0u);
                 }
             }
+            if (l == 0) stage_index(pend, b, tl_nx, row, more);
+            if (l == 1) stage_record(pend, src);
+            if (l == 2) stage_ray(pend, src);
             ok = mma_wait();
             if (!ok) break;
             if (l < H) {
@@ -559,6 +588,7 @@ __global__ void __launch_bounds__(128, 1)
         if (issuer) issue_wgrad(0, sX, sDZ, 1024u);
         if (!mma_wait()) { aborted = true; break; }
         wnew = false;
+        if (more) nxt = stage_finish(pend, src);
     }
     if (!aborted && cur != 0xffffffffu && !wnew) flush(cur);
     // drain before TMEM is freed: a commit whose wait gave up, an image load nobody waited for

@@ -100,6 +100,7 @@ struct WSet {
     int W = 0, first = 0, n = 0;        // width; internal field ids [first, first + n)
     int64_t P = 0, Pt = 0, Pr = 0, img_bytes = 0, img8_bytes = 0;
     bool tc_ok = false, tc8_ok = false;
+    uint32_t stale = 0;                 // derived copies older than w32 (kStale* bits)
     DBuf<float> w32, wt, wr;
     DBuf<uint8_t> wimg, wimg8;
 };
@@ -278,6 +279,35 @@ bool all_tc(const roam_ctx *c, bool f8)
     for (int k = 0; k < c->n_ws; ++k)
         if (!(f8 ? c->ws[k].tc8_ok : c->ws[k].tc_ok)) return false;
     return c->n_ws > 0;
+}
+
+// Derived weight copies that an Adam step left stale are rebuilt before the
+// first launch that reads them: the SIMT forward's transposed copy (FP32
+// forward or SIMT adjoint), the SIMT adjoint's row-padded copy, the FP8
+// images.  Adam rebuilds the BF16 images itself.
+constexpr uint32_t kStaleWt = 1u, kStaleWr = 2u, kStaleImg8 = 4u;
+
+roam_status refresh(roam_ctx *c, int precision, bool simt_adjoint, cudaStream_t s)
+{
+    for (int k = 0; k < c->n_ws; ++k) {
+        WSet &q = c->ws[k];
+        if (!q.stale) continue;
+        const int H = c->md.n_hidden;
+        if ((precision == ROAM_F32 || simt_adjoint) && (q.stale & kStaleWt)) {
+            launch_pack_simt(q.w32.p, q.n, q.W, H, q.P, q.wt.p, q.Pt, s);
+            q.stale &= ~kStaleWt;
+        }
+        if (simt_adjoint && (q.stale & kStaleWr)) {
+            launch_pack_rows(q.w32.p, q.n, q.W, H, q.P, q.wr.p, q.Pr, s);
+            q.stale &= ~kStaleWr;
+        }
+        if (precision == ROAM_FP8 && (q.stale & kStaleImg8)) {
+            launch_pack_tc(q.w32.p, q.n, q.W, H, q.P, q.wimg8.p, q.img8_bytes, true, s);
+            q.stale &= ~kStaleImg8;
+        }
+        ROAM_TRY(launched("weight refresh"));
+    }
+    return ROAM_OK;
 }
 
 roam_status check_ready(const roam_ctx *c)
@@ -646,6 +676,7 @@ roam_status load_set(roam_ctx *c, int k, int W, int H, int first, int n, const f
     q.first = first;
     q.n = n;
     q.P = P;
+    q.stale = 0;
     q.Pt = simt_transposed_size(W, H);
     ROAM_TRY(ensure(q.wt, (size_t)(q.Pt * n)));
     launch_pack_simt(q.w32.p, n, W, H, P, q.wt.p, q.Pt, 0);
@@ -994,6 +1025,7 @@ roam_status roam_render(roam_ctx *c, const roam_camera *cams, int n_views, const
     ROAM_TRY(check_ready(c));
     ROAM_TRY(check_opts(c, opts));
     cudaStream_t s = (cudaStream_t)stream;
+    ROAM_TRY(refresh(c, opts->precision, false, s));
     int64_t n_pix = 0;
     ROAM_TRY(upload_cams(c, cams, n_views, opts->delta, &n_pix, s));
     const int R = round_size(opts, n_pix);
@@ -1034,6 +1066,7 @@ roam_status roam_tune_round_size(roam_ctx *c, const roam_camera *cams, int n_vie
     ROAM_TRY(check_opts(c, opts));
     if (!best_round_size) return fail(ROAM_ERR_ARG, "null output");
     cudaStream_t s = (cudaStream_t)stream;
+    ROAM_TRY(refresh(c, opts->precision, false, s));
     int64_t n_pix = 0;
     ROAM_TRY(upload_cams(c, cams, n_views, opts->delta, &n_pix, s));
     size_t free_b = 0, total_b = 0;
@@ -1203,6 +1236,7 @@ roam_status roam_mlp_backward(roam_ctx *c, const float *p, const float *d, const
     if (n < 0 || n > 0x7fffffff) return fail(ROAM_ERR_ARG, "bad sample count");
     if (!grad) return fail(ROAM_ERR_ARG, "null gradient");
     cudaStream_t s = (cudaStream_t)stream;
+    ROAM_TRY(refresh(c, precision, !tc, s));
     ROAM_CUDA(cudaMemsetAsync(grad, 0, (size_t)(c->ws[0].P * c->n_fields) * sizeof(float), s));
     if (n == 0) return ROAM_OK;
     if (!p || !d || !field || !dl_dout) return fail(ROAM_ERR_ARG, "null pointer");
@@ -1358,6 +1392,7 @@ roam_status roam_mlp_eval(roam_ctx *c, const float *p, const float *d, const uin
     if ((precision == ROAM_BF16 && !all_tc(c, false)) || (precision == ROAM_FP8 && !all_tc(c, true)))
         return fail(ROAM_ERR_UNSUPPORTED, "tensor-core path not available");
     cudaStream_t s = (cudaStream_t)stream;
+    ROAM_TRY(refresh(c, precision, false, s));
     ROAM_TRY(ensure(c->sorted, (size_t)n));
     ROAM_TRY(ensure(c->tiles, tile_capacity((size_t)n, c->n_fields)));
     const BucketBufs b = bucket_of(c);
@@ -1411,6 +1446,7 @@ roam_status roam_train_forward(roam_ctx *c, const roam_camera *cams, int n_views
     if (!mlp_bwd_supported(c->md.width, c->md.n_hidden))
         return fail(ROAM_ERR_UNSUPPORTED, "training supports W = 32 or 64");
     cudaStream_t s = (cudaStream_t)stream;
+    ROAM_TRY(refresh(c, opts->precision, false, s));
     int64_t n_pix = 0;
     ROAM_TRY(upload_cams(c, cams, n_views, opts->delta, &n_pix, s));
     // one round holding every kept sample of every ray, so the backward pass
@@ -1466,7 +1502,9 @@ roam_status roam_train_backward(roam_ctx *c, const float *dl_drgb, float *grad, 
     src.st = state_of(c);
     src.delta = o.delta;
     src.accurate = o.precision == ROAM_F32;
-    if (o.precision == ROAM_BF16 && mlp_bwd_tc_supported(c->md.width, c->md.n_hidden) && c->ws[0].tc_ok) {
+    const bool tc = o.precision == ROAM_BF16 && mlp_bwd_tc_supported(c->md.width, c->md.n_hidden) && c->ws[0].tc_ok;
+    if (!tc) ROAM_TRY(refresh(c, o.precision, true, s));
+    if (tc) {
         ProfScope ps(c, P_MLP_BWD_TC, s);
         launch_mlp_bwd_tc(weights_of(c), src, b, c->ctr, c->gsr.p, grad, c->n_sm, s);
     } else {
@@ -1516,12 +1554,11 @@ roam_status roam_adam_step(roam_ctx *c, const float *grad, const roam_adam_cfg *
         ProfScope ps(c, P_ADAM, s);
         launch_adam(q.w32.p, c->adam_m.p, c->adam_v.p, grad, n, cfg->lr, cfg->beta1, cfg->beta2, cfg->eps, bc1, bc2,
                     s);
-        // refresh every derived copy of the masters
+        // the BF16 images now; the other derived copies when a launch needs them
         const int W = c->md.width, H = c->md.n_hidden;
-        launch_pack_simt(q.w32.p, c->n_fields, W, H, q.P, q.wt.p, q.Pt, s);
-        launch_pack_rows(q.w32.p, c->n_fields, W, H, q.P, q.wr.p, q.Pr, s);
         if (q.tc_ok) launch_pack_tc(q.w32.p, c->n_fields, W, H, q.P, q.wimg.p, q.img_bytes, false, s);
-        if (q.tc8_ok) launch_pack_tc(q.w32.p, c->n_fields, W, H, q.P, q.wimg8.p, q.img8_bytes, true, s);
+        q.stale |= kStaleWt | kStaleWr | (q.tc8_ok ? kStaleImg8 : 0u);
+        if (!q.tc_ok) ROAM_TRY(refresh(c, ROAM_F32, true, s));
     }
     c->last = s;
     return launched("adam");
