@@ -619,7 +619,8 @@ def main():
     if args.quick:
         if rank == 0:
             print(json.dumps({"quick": True, "metric": METRIC, "value": value, "unit": UNIT, "dtype": dtype,
-                              "ms_per_step": ms_per_step, "views": views, "kernels": prof, "clocks": clocks}),
+                              "ms_per_step": ms_per_step, "views": views, "kernels": prof, "clocks": clocks,
+                              "evaluated_per_step": int(evaluated_per_step), "rounds": int(st.n_rounds)}),
                   flush=True)
         r.close()
         return 0

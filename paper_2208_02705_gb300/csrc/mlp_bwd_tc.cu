@@ -10,7 +10,10 @@
 //        wgrad   dW^T += X^T dZ     D[K x N]    += X (MN-major) * dZ (MN-major)
 //      where the wgrad accumulators of all layers stay in TMEM across the
 //      tiles of one field and are added to the global FP32 gradient (one
-//      atomic per parameter) when the field changes.
+//      atomic per parameter) when the field changes.  The MMAs of one
+//      backward group write independent accumulators, so up to three warps
+//      issue them side by side; every warp's lane 0 commits to the group's
+//      barrier.
 //
 // Every activation tile exists once, in the 128-byte-swizzled layout with
 // samples as rows and 64 features per 128-byte row ("natural" layout).  Read
@@ -119,6 +122,20 @@ __device__ __forceinline__ void ld16f(uint32_t taddr, float (&v)[16])
     for (int q = 0; q < 16; ++q) v[q] = __uint_as_float(r[q]);
 }
 
+// N consecutive TMEM columns of this thread's lane as floats, one wait for all
+template <int N>
+__device__ __forceinline__ void ldNf(uint32_t taddr, float (&v)[N])
+{
+    uint32_t r[N / 16][16];
+#pragma unroll
+    for (int c = 0; c < N / 16; ++c) tmem_ld16_nowait(taddr + (uint32_t)(16 * c), r[c]);
+    tmem_wait_ld();
+#pragma unroll
+    for (int c = 0; c < N / 16; ++c)
+#pragma unroll
+        for (int q = 0; q < 16; ++q) v[16 * c + q] = __uint_as_float(r[c][q]);
+}
+
 // Where feature row k of wgrad accumulator l lands in the API layout (per
 // layer row-major [out][in] then bias[out]): column n (n < n_rows) goes to
 // base + n * stride; the head's column W (its density logit, API row 0) to
@@ -185,12 +202,13 @@ __global__ void __launch_bounds__(128, 1)
     const uint32_t sIMG = base, sX = base + B::kOffX, sT = base + B::kOffT, sDZ = base + B::kOffDZ;
     const int tid = threadIdx.x, warp = tid >> 5;
     const int row = tid;                               // TMEM lane == tile row == sample
-    const bool issuer = tid == 0;
+    const bool issuer = tid == 0;                     // forward chain
+    const bool lead = (tid & 31) == 0;                // every warp's lane 0 commits each MMA group
     volatile int *abortp = &abort_flag;
     uint32_t *status = &ctr->status;
 
     if (tid == 0) {
-        mbar_init(&bar_d, 1);
+        mbar_init(&bar_d, 4);                         // one commit per warp leader
         mbar_init(&bar_w, 1);
         abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -223,12 +241,12 @@ __global__ void __launch_bounds__(128, 1)
 
     // issue, commit and wait: true when the MMAs landed
     auto mma_wait = [&]() -> bool {
-        if (issuer) {
+        if (lead) {
             umma_commit(&bar_d);
             ++n_commits;
         }
         const bool got = mbar_wait(&bar_d, d_ph, abortp, status);
-        if (issuer && got) ++n_waits;
+        if (lead && got) ++n_waits;
         d_ph ^= 1u;
         const bool all = __syncthreads_and(got) != 0;
         tc_fence_after();
@@ -395,45 +413,52 @@ __global__ void __launch_bounds__(128, 1)
                 // next hidden input: ReLU
                 uint8_t *xc = sm + B::kOffX + (l + 1) * kChunk;
 #pragma unroll
-                for (int c = 0; c < W; c += 16) {
-                    float v[16];
-                    ld16f(tD + tlane + (uint32_t)c, v);
-                    uint32_t p[8];
+                for (int cb = 0; cb < W; cb += 32) {
+                    float va[32];
+                    ldNf<32>(tD + tlane + (uint32_t)cb, va);
 #pragma unroll
-                    for (int q = 0; q < 8; ++q) p[q] = pack_bf16_relu(v[2 * q], v[2 * q + 1]);
-                    st_units<2>(xc, row, c / 8, p);
+                    for (int c = 0; c < 32; c += 16) {
+                        uint32_t p[8];
+#pragma unroll
+                        for (int q = 0; q < 8; ++q) p[q] = pack_bf16_relu(va[c + 2 * q], va[c + 2 * q + 1]);
+                        st_units<2>(xc, row, (cb + c) / 8, p);
+                    }
                 }
                 store_tail(l + 1);
             } else if (l == H) {
                 // head: features (linear) -> colour input, column W = density logit
                 uint8_t *xc = sm + B::kOffX + (H + 1) * kChunk;
 #pragma unroll
-                for (int c = 0; c < W; c += 16) {
-                    float v[16];
-                    ld16f(tD + tlane + (uint32_t)c, v);
-                    uint32_t p[8];
+                for (int cb = 0; cb < W; cb += 32) {
+                    float va[32];
+                    ldNf<32>(tD + tlane + (uint32_t)cb, va);
 #pragma unroll
-                    for (int q = 0; q < 8; ++q) p[q] = pack_bf16(v[2 * q], v[2 * q + 1]);
-                    st_units<2>(xc, row, c / 8, p);
+                    for (int c = 0; c < 32; c += 16) {
+                        uint32_t p[8];
+#pragma unroll
+                        for (int q = 0; q < 8; ++q) p[q] = pack_bf16(va[c + 2 * q], va[c + 2 * q + 1]);
+                        st_units<2>(xc, row, (cb + c) / 8, p);
+                    }
                 }
-                float v[16];
-                ld16f(tD + tlane + (uint32_t)W, v);
-                s_logit = v[0];
+                {
+                    float v[16];
+                    ld16f(tD + tlane + (uint32_t)W, v);
+                    s_logit = v[0];
+                }
                 store_tail(H + 1);
             } else {
                 // colour: z -> g = relu(z) (X_g), rgb = sigmoid(Wo g + bo) in FP32, then
-                // the output layer's adjoint and dZ of the colour layer (z is read
-                // from TMEM twice rather than held in registers)
+                // the output layer's adjoint and dZ of the colour layer
                 const float4 *wo = reinterpret_cast<const float4 *>(IMG + S::kMatBytes);
                 float4 acc = wo[W];
 #pragma unroll
-                for (int c = 0; c < W; c += 16) {
-                    float v[16];
-                    ld16f(tD + tlane + (uint32_t)c, v);
+                for (int cb = 0; cb < W; cb += 32) {
+                    float va[32];
+                    ldNf<32>(tD + tlane + (uint32_t)cb, va);
 #pragma unroll
-                    for (int q = 0; q < 16; ++q) {
-                        const float gk = fmaxf(v[q], 0.f);
-                        const float4 wk = wo[c + q];
+                    for (int k = 0; k < 32; ++k) {
+                        const float gk = fmaxf(va[k], 0.f);
+                        const float4 wk = wo[cb + k];
                         acc.x = fmaf(wk.x, gk, acc.x);
                         acc.y = fmaf(wk.y, gk, acc.y);
                         acc.z = fmaf(wk.z, gk, acc.z);
@@ -446,15 +471,15 @@ __global__ void __launch_bounds__(128, 1)
                 uint8_t *xg = sm + B::kOffX + (H + 2) * kChunk;
 #pragma unroll
                 for (int c = 0; c < W; c += 16) {
-                    float v[16];
-                    ld16f(tD + tlane + (uint32_t)c, v);
+                    float va[16];
+                    ld16f(tD + tlane + (uint32_t)c, va);     // re-read: cheaper than holding all W in registers
                     uint32_t pg[8], pd[8];
 #pragma unroll
                     for (int q = 0; q < 8; ++q) {
                         float gg[2], dd[2];
 #pragma unroll
                         for (int h = 0; h < 2; ++h) {
-                            const float zk = v[2 * q + h];
+                            const float zk = va[2 * q + h];
                             const float4 wk = wo[c + 2 * q + h];
                             gg[h] = fmaxf(zk, 0.f);
                             dd[h] = zk > 0.f ? fmaf(wk.x, dz0, fmaf(wk.y, dz1, wk.z * dz2)) : 0.f;
@@ -515,26 +540,30 @@ __global__ void __launch_bounds__(128, 1)
         auto next_dz = [&](int i, bool relu, bool head) {
             const uint8_t *xc = sm + B::kOffX + i * kChunk;
 #pragma unroll
-            for (int c = 0; c < W; c += 16) {
-                float v[16];
-                ld16f(tD + tlane + (uint32_t)c, v);
-                uint4 m0 = make_uint4(0u, 0u, 0u, 0u), m1 = m0;
-                if (relu) {
-                    m0 = *reinterpret_cast<const uint4 *>(xc + sw_off(row, c / 8));
-                    m1 = *reinterpret_cast<const uint4 *>(xc + sw_off(row, c / 8 + 1));
-                }
-                const uint32_t mk[8] = {m0.x, m0.y, m0.z, m0.w, m1.x, m1.y, m1.z, m1.w};
-                uint32_t p[8];
+            for (int cb = 0; cb < W; cb += 32) {
+                float va[32];
+                ldNf<32>(tD + tlane + (uint32_t)cb, va);
 #pragma unroll
-                for (int q = 0; q < 8; ++q) {
-                    float a = v[2 * q], bb = v[2 * q + 1];
+                for (int c0 = 0; c0 < 32; c0 += 16) {
+                    const int c = cb + c0;
+                    uint4 m0 = make_uint4(0u, 0u, 0u, 0u), m1 = m0;
                     if (relu) {
-                        if ((mk[q] & 0xffffu) == 0u) a = 0.f;
-                        if ((mk[q] >> 16) == 0u) bb = 0.f;
+                        m0 = *reinterpret_cast<const uint4 *>(xc + sw_off(row, c / 8));
+                        m1 = *reinterpret_cast<const uint4 *>(xc + sw_off(row, c / 8 + 1));
                     }
-                    p[q] = pack_bf16(a, bb);
+                    const uint32_t mk[8] = {m0.x, m0.y, m0.z, m0.w, m1.x, m1.y, m1.z, m1.w};
+                    uint32_t p[8];
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) {
+                        float a = va[c0 + 2 * q], bb = va[c0 + 2 * q + 1];
+                        if (relu) {
+                            if ((mk[q] & 0xffffu) == 0u) a = 0.f;
+                            if ((mk[q] >> 16) == 0u) bb = 0.f;
+                        }
+                        p[q] = pack_bf16(a, bb);
+                    }
+                    st_units<2>(DZ, row, c / 8, p);
                 }
-                st_units<2>(DZ, row, c / 8, p);
             }
             if constexpr (W == 64) {
                 if (head) {
@@ -555,19 +584,16 @@ __global__ void __launch_bounds__(128, 1)
 
         // output and colour layers
         publish();
-        if (issuer) {
-            issue_wgrad(H + 2, sX + (uint32_t)((H + 2) * kChunk), sDZ + kChunk, 1024u);
-            issue_wgrad(H + 1, sX + (uint32_t)((H + 1) * kChunk), sDZ, 1024u);
-            issue_dgrad(H + 1, W);
-        }
+        // independent accumulators, so three warps issue them side by side
+        if (tid == 0) issue_wgrad(H + 2, sX + (uint32_t)((H + 2) * kChunk), sDZ + kChunk, 1024u);
+        if (tid == 32) issue_wgrad(H + 1, sX + (uint32_t)((H + 1) * kChunk), sDZ, 1024u);
+        if (tid == 64) issue_dgrad(H + 1, W);
         if (!mma_wait()) { aborted = true; break; }
         next_dz(H + 1, false, true);          // dZ of the head: [d feat | d logit | 0]
         // head
         publish();
-        if (issuer) {
-            issue_wgrad(H, sX + (uint32_t)(H * kChunk), sDZ, (uint32_t)kChunk);
-            issue_dgrad(H, S::N_HEAD);
-        }
+        if (tid == 0) issue_wgrad(H, sX + (uint32_t)(H * kChunk), sDZ, (uint32_t)kChunk);
+        if (tid == 32) issue_dgrad(H, S::N_HEAD);
         if (!mma_wait()) { aborted = true; break; }
         next_dz(H, true, false);
         // hidden layers H-1 .. 1
@@ -575,10 +601,8 @@ __global__ void __launch_bounds__(128, 1)
 #pragma unroll 1
         for (int l = H - 1; l >= 1; --l) {
             publish();
-            if (issuer) {
-                issue_wgrad(l, sX + (uint32_t)(l * kChunk), sDZ, 1024u);
-                issue_dgrad(l, W);
-            }
+            if (tid == 0) issue_wgrad(l, sX + (uint32_t)(l * kChunk), sDZ, 1024u);
+            if (tid == 32) issue_dgrad(l, W);
             if (!mma_wait()) { ok2 = false; break; }
             next_dz(l, true, false);
         }
@@ -592,7 +616,7 @@ __global__ void __launch_bounds__(128, 1)
     }
     if (!aborted && cur != 0xffffffffu && !wnew) flush(cur);
     // drain before TMEM is freed: a commit whose wait gave up, an image load nobody waited for
-    if (issuer && n_commits > n_waits) mbar_wait(&bar_d, (n_commits - 1) & 1u, abortp, status, true);
+    if (lead && n_commits > n_waits) mbar_wait(&bar_d, (n_commits - 1) & 1u, abortp, status, true);
     if (tid == 0 && w_pending) mbar_wait(&bar_w, w_ph ^ 1u, abortp, status, true);
     tc_fence_before();
     __syncthreads();
