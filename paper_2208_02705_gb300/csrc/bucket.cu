@@ -10,7 +10,6 @@ namespace roam {
 namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
-constexpr int kMaxFieldsSmem = 8192;
 
 // Iterates the valid samples of a round.  Slot layout: 32 consecutive live
 // rays share a 32-wide column per sample index k (see slot_of); a warp covers
@@ -71,7 +70,8 @@ __device__ __forceinline__ uint32_t ntiles_of(uint32_t h, int tile, int group)
 // `group` (trailing tiles empty) so that groups of tiles never mix fields;
 // resets hist for the next use.
 __global__ void __launch_bounds__(1024) k_scan(uint32_t *hist, int n_fields, int tile, int group, uint32_t *offsets,
-                                               uint32_t *cursor, Tile *tiles, Counters *ctr, ClassBounds cb)
+                                               uint32_t *cursor, Tile *tiles, uint32_t *tile_off_out, Counters *ctr,
+                                               ClassBounds cb)
 {
     __shared__ uint32_t warp_a[32], warp_b[32];
     extern __shared__ uint32_t tile_off[];   // [n_fields + 1]
@@ -137,7 +137,10 @@ __global__ void __launch_bounds__(1024) k_scan(uint32_t *hist, int n_fields, int
     if (lane == 0 && hit) atomicAdd(&ctr->fields_hit, hit);
     __syncthreads();
     // tile descriptors: tile t belongs to the last field whose first tile is <= t
-    for (uint32_t t = threadIdx.x; t < total_tiles; t += blockDim.x) {
+    // (written here, or by the scatter's whole grid when tile_off_out is set)
+    if (tile_off_out)
+        for (int f = threadIdx.x; f <= n_fields; f += blockDim.x) tile_off_out[f] = tile_off[f];
+    for (uint32_t t = threadIdx.x; t < (tile_off_out ? 0u : total_tiles); t += blockDim.x) {
         int lo = 0, hi = n_fields - 1;
         while (lo < hi) {
             const int mid = (lo + hi + 1) >> 1;
@@ -202,6 +205,99 @@ __global__ void __launch_bounds__(512) k_scatter(const uint32_t *cnt, const uint
     }
 }
 
+// tile t of the list: the last field whose first tile is <= t
+__device__ __forceinline__ Tile tile_record(uint32_t t, const uint32_t *tile_off, const uint32_t *offsets, int n_fields,
+                                            int tile)
+{
+    int lo = 0, hi = n_fields - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(tile_off + mid) <= t) lo = mid; else hi = mid - 1;
+    }
+    const uint32_t k = t - __ldg(tile_off + lo);
+    const uint32_t o0 = __ldg(offsets + lo), h = __ldg(offsets + lo + 1) - o0;
+    Tile tl;
+    tl.field = (uint32_t)lo;
+    tl.start = o0 + k * (uint32_t)tile;
+    tl.count = h > k * (uint32_t)tile ? min((uint32_t)tile, h - k * (uint32_t)tile) : 0u;
+    tl.pad = 0;
+    return tl;
+}
+
+// Scatter with block-level aggregation: a block takes kItems x blockDim
+// consecutive samples, ranks them within their field in shared memory,
+// reserves each touched field's range with one global atomic, then writes;
+// the whole grid also writes the tile records from the scan's tile offsets.
+constexpr int kItems = 8;
+constexpr int kMaxFieldsBlk = 6144;     // two shared counters per field within 48 KB
+
+__global__ void __launch_bounds__(512) k_scatter_blk(const uint32_t *cnt, const uint32_t *recs,
+                                                     const uint32_t *live_count, uint32_t n_fixed, int R,
+                                                     const uint16_t *keys16, int n_fields, uint32_t *cursor,
+                                                     uint32_t *sorted, const uint32_t *tile_off,
+                                                     const uint32_t *offsets, Tile *tiles, int tile, Counters *ctr)
+{
+    extern __shared__ uint32_t sh[];
+    uint32_t *cnt_s = sh, *base_s = sh + n_fields;
+    for (int f = threadIdx.x; f < n_fields; f += blockDim.x) cnt_s[f] = 0u;
+    __syncthreads();
+    SlotIter it{cnt, recs, live_count ? *live_count : n_fixed, (uint32_t)R};
+    const uint64_t tot = keys16 ? (uint64_t)n_fixed : it.total();
+    const uint64_t chunk = (uint64_t)blockDim.x * kItems;
+    for (uint64_t c0 = (uint64_t)blockIdx.x * chunk; c0 < tot; c0 += (uint64_t)gridDim.x * chunk) {
+        uint32_t key[kItems], loc[kItems];
+        bool v[kItems];
+#pragma unroll
+        for (int i = 0; i < kItems; ++i) {
+            const uint64_t s = c0 + (uint64_t)i * blockDim.x + threadIdx.x;
+            key[i] = 0u;
+            v[i] = false;
+            if (s < tot) {
+                if (keys16) {
+                    key[i] = keys16[s];
+                    v[i] = key[i] < (uint32_t)n_fields;
+                    if (!v[i]) atomicOr(&ctr->status, kStatusBadLabel);
+                } else {
+                    v[i] = it.valid(s, key[i]);
+                }
+            }
+            if (v[i]) loc[i] = atomicAdd(&cnt_s[key[i]], 1u);
+        }
+        __syncthreads();
+        for (int f = threadIdx.x; f < n_fields; f += blockDim.x) {
+            const uint32_t n = cnt_s[f];
+            if (n) {
+                base_s[f] = atomicAdd(&cursor[f], n);
+                cnt_s[f] = 0u;
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < kItems; ++i)
+            if (v[i]) sorted[base_s[key[i]] + loc[i]] = (uint32_t)(c0 + (uint64_t)i * blockDim.x + threadIdx.x);
+        __syncthreads();
+    }
+    const uint32_t n_tiles = ctr->n_tiles;
+    for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < n_tiles; t += gridDim.x * blockDim.x)
+        tiles[t] = tile_record(t, tile_off, offsets, n_fields, tile);
+}
+
+void scan_and_scatter(const uint32_t *cnt, const uint32_t *recs, const uint32_t *live_count, uint32_t n_fixed, int R,
+                      int group, const uint16_t *keys16, int n_fields, int tile, const BucketBufs &b, Counters *ctr,
+                      int grid, cudaStream_t s, ClassBounds cb)
+{
+    const bool blk = b.tile_off != nullptr && n_fields <= kMaxFieldsBlk;
+    k_scan<<<1, 1024, (size_t)(n_fields + 1) * sizeof(uint32_t), s>>>(b.hist, n_fields, tile, group < 1 ? 1 : group,
+                                                                       b.offsets, b.cursor, b.tiles,
+                                                                       blk ? b.tile_off : nullptr, ctr, cb);
+    if (blk)
+        k_scatter_blk<<<grid, 512, 2 * (size_t)n_fields * sizeof(uint32_t), s>>>(
+            cnt, recs, live_count, n_fixed, R, keys16, n_fields, b.cursor, b.sorted, b.tile_off, b.offsets, b.tiles,
+            tile, ctr);
+    else
+        k_scatter<<<grid, 512, 0, s>>>(cnt, recs, live_count, n_fixed, R, keys16, n_fields, b.cursor, b.sorted);
+}
+
 }  // namespace
 
 void launch_bucket(const uint32_t *cnt, const uint32_t *recs, const uint32_t *live_count, uint32_t n_fixed,
@@ -210,18 +306,14 @@ void launch_bucket(const uint32_t *cnt, const uint32_t *recs, const uint32_t *li
 {
     const size_t sh = (size_t)n_fields * sizeof(uint32_t);
     k_hist<<<grid, 512, sh, s>>>(cnt, recs, live_count, n_fixed, R, keys16, n_fields, b.hist, ctr);
-    k_scan<<<1, 1024, (size_t)(n_fields + 1) * sizeof(uint32_t), s>>>(b.hist, n_fields, tile, group < 1 ? 1 : group,
-                                                                       b.offsets, b.cursor, b.tiles, ctr, cb);
-    k_scatter<<<grid, 512, 0, s>>>(cnt, recs, live_count, n_fixed, R, keys16, n_fields, b.cursor, b.sorted);
+    scan_and_scatter(cnt, recs, live_count, n_fixed, R, group, keys16, n_fields, tile, b, ctr, grid, s, cb);
 }
 
 void launch_bucket_ready(const uint32_t *cnt, const uint32_t *recs, const uint32_t *live_count, uint32_t n_fixed,
                          int R, int group, int n_fields, int tile, const BucketBufs &b, Counters *ctr, int grid,
                          cudaStream_t s, ClassBounds cb)
 {
-    k_scan<<<1, 1024, (size_t)(n_fields + 1) * sizeof(uint32_t), s>>>(b.hist, n_fields, tile, group < 1 ? 1 : group,
-                                                                       b.offsets, b.cursor, b.tiles, ctr, cb);
-    k_scatter<<<grid, 512, 0, s>>>(cnt, recs, live_count, n_fixed, R, nullptr, n_fields, b.cursor, b.sorted);
+    scan_and_scatter(cnt, recs, live_count, n_fixed, R, group, nullptr, n_fields, tile, b, ctr, grid, s, cb);
 }
 
 }  // namespace roam

@@ -87,6 +87,7 @@ extern "C" roam_status roam_bucket_static(const uint16_t *keys, int64_t n, int n
     b.cursor = cursor;
     b.tiles = tiles;
     b.sorted = perm;
+    b.tile_off = nullptr;
     // one tile record per field at most (tile length 2^31 - 1 >= n)
     launch_bucket(nullptr, nullptr, nullptr, (uint32_t)n, 1, 1, keys, n_fields, 0x7fffffff, b, ctr, ds.n_sm * 2, s,
                   ClassBounds{{0, n_fields, n_fields, n_fields}});

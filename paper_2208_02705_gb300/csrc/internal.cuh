@@ -152,6 +152,7 @@ struct BucketBufs {
     uint32_t *cursor;     // [F]
     Tile *tiles;          // [max tiles]
     uint32_t *sorted;     // [max samples]
+    uint32_t *tile_off;   // [F + 1] first tile of each field, or nullptr (tiles built by the scan)
 };
 
 struct MlpWeights {

@@ -139,7 +139,7 @@ struct roam_ctx {
     // per-call workspace
     DBuf<float4> orig, dir, dir_lo, acc, sr, gsr;
     DBuf<float2> tw;
-    DBuf<uint32_t> j_next, j_end, n_kept, live0, live1, cnt, recs, sorted, hist, offsets, cursor, scratch_u32;
+    DBuf<uint32_t> j_next, j_end, n_kept, live0, live1, cnt, recs, sorted, hist, offsets, cursor, scratch_u32, tile_off;
     DBuf<Tile> tiles;
     DBuf<float> o_rgb, o_depth, o_op;
     DBuf<DevCamera> cams;
@@ -427,6 +427,7 @@ roam_status ensure_fields_ws(roam_ctx *c)
     ROAM_TRY(ensure(c->hist, F));
     ROAM_TRY(ensure(c->offsets, F + 1));
     ROAM_TRY(ensure(c->cursor, F));
+    ROAM_TRY(ensure(c->tile_off, F + 1));
     if (fresh) ROAM_CUDA(cudaMemset(c->hist.p, 0, F * sizeof(uint32_t)));
     return ROAM_OK;
 }
@@ -453,6 +454,7 @@ BucketBufs bucket_of(roam_ctx *c)
     b.cursor = c->cursor.p;
     b.tiles = c->tiles.p;
     b.sorted = c->sorted.p;
+    b.tile_off = c->tile_off.p;
     return b;
 }
 
@@ -779,7 +781,7 @@ roam_status roam_destroy(roam_ctx *c)
     release(c->orig); release(c->dir); release(c->dir_lo); release(c->acc); release(c->sr); release(c->tw);
     release(c->j_next); release(c->j_end); release(c->n_kept); release(c->live0); release(c->live1);
     release(c->cnt); release(c->recs); release(c->sorted); release(c->hist); release(c->offsets);
-    release(c->cursor); release(c->scratch_u32); release(c->tiles);
+    release(c->cursor); release(c->scratch_u32); release(c->tiles); release(c->tile_off);
     release(c->o_rgb); release(c->o_depth); release(c->o_op); release(c->cams);
     if (c->h_cams_ring) cudaFreeHost(c->h_cams_ring);
     if (c->h_ctr) cudaFreeHost(c->h_ctr);
