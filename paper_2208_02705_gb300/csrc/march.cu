@@ -287,35 +287,34 @@ __global__ void __launch_bounds__(256) k_march(GridDev g, MarchParams p)
             }
             const int bxi = ix >> kBrickShift, byi = iy >> kBrickShift, bzi = iz >> kBrickShift;
             const int dd = __ldg(&g.brick_dist[((int64_t)bzi * g.by + byi) * g.bx + bxi]);
-            if (dd > 0) {
-                // every brick within Chebyshev distance dd - 1 is empty: leave that
-                // cube of bricks in one step (voxel units, clamped to the grid)
-                const int r = dd - 1;
-                const float ex = dgx > 0.f ? (float)(min(bxi + r + 1, g.bx) << kBrickShift) : (float)(max(bxi - r, 0) << kBrickShift);
-                const float ey = dgy > 0.f ? (float)(min(byi + r + 1, g.by) << kBrickShift) : (float)(max(byi - r, 0) << kBrickShift);
-                const float ez = dgz > 0.f ? (float)(min(bzi + r + 1, g.bz) << kBrickShift) : (float)(max(bzi - r, 0) << kBrickShift);
-                float te = 3.0e38f;
-                if (dgx != 0.f) te = fminf(te, (ex - ogx) * idx);
-                if (dgy != 0.f) te = fminf(te, (ey - ogy) * idy);
-                if (dgz != 0.f) te = fminf(te, (ez - ogz) * idz);
-                const float jf = ceilf(te / delta - 0.5f) - 1.0f;
-                const uint32_t jj = jf > (float)je ? je : (jf > 0.f ? (uint32_t)jf : 0u);
-                jn = jj > jn + 1 ? jj : jn + 1;
-                continue;
-            }
             const int64_t wi = ((int64_t)iz * g.gy + iy) * g.wpr + (ix >> 5);
-            const uint32_t w = __ldg(&g.bits[wi]);
             const uint32_t b = (uint32_t)(ix & 31);
+            const uint32_t w = dd > 0 ? 0u : __ldg(&g.bits[wi]);
             if (!((w >> b) & 1u)) {
-                // empty voxel: jump to the first sample past its exit face
-                const float ex = dgx > 0.f ? (float)(ix + 1) : (float)ix;
-                const float ey = dgy > 0.f ? (float)(iy + 1) : (float)iy;
-                const float ez = dgz > 0.f ? (float)(iz + 1) : (float)iz;
+                // empty space, one code path for both jumps (fewer divergent
+                // branches per step): out of an empty voxel to the first sample
+                // past its exit face; out of an empty brick to the first sample
+                // past the exit of the cube of bricks within Chebyshev distance
+                // dd - 1 (all empty; voxel units, clamped to the grid), minus one
+                // sample so that a sample rounded onto that face is still tested
+                float ex, ey, ez, back;
+                if (dd > 0) {
+                    const int r = dd - 1;
+                    ex = dgx > 0.f ? (float)(min(bxi + r + 1, g.bx) << kBrickShift) : (float)(max(bxi - r, 0) << kBrickShift);
+                    ey = dgy > 0.f ? (float)(min(byi + r + 1, g.by) << kBrickShift) : (float)(max(byi - r, 0) << kBrickShift);
+                    ez = dgz > 0.f ? (float)(min(bzi + r + 1, g.bz) << kBrickShift) : (float)(max(bzi - r, 0) << kBrickShift);
+                    back = 1.0f;
+                } else {
+                    ex = dgx > 0.f ? (float)(ix + 1) : (float)ix;
+                    ey = dgy > 0.f ? (float)(iy + 1) : (float)iy;
+                    ez = dgz > 0.f ? (float)(iz + 1) : (float)iz;
+                    back = 0.0f;
+                }
                 float te = 3.0e38f;
                 if (dgx != 0.f) te = fminf(te, (ex - ogx) * idx);
                 if (dgy != 0.f) te = fminf(te, (ey - ogy) * idy);
                 if (dgz != 0.f) te = fminf(te, (ez - ogz) * idz);
-                const float jf = ceilf(te / delta - 0.5f);
+                const float jf = ceilf(te / delta - 0.5f) - back;
                 const uint32_t jj = jf > (float)je ? je : (jf > 0.f ? (uint32_t)jf : 0u);
                 jn = jj > jn + 1 ? jj : jn + 1;
                 continue;
