@@ -456,7 +456,8 @@ def distill_bench(roam, F, torch, args, stream):
     losses = []
 
     def step(k):
-        return r.distill_step(pt, dt, ft, float(I), lr=1e-3, step=k, precision=roam.ROAM_BF16, stream=stream)
+        return r.distill_step(pt, dt, ft, float(I), lr=1e-3, step=k, precision=roam.ROAM_BF16,
+                              teacher_precision=roam.ROAM_TF32, stream=stream)
 
     for k in range(1, 4):
         step(k)
@@ -473,22 +474,24 @@ def distill_bench(roam, F, torch, args, stream):
     prof = r.profile_read()
     r.profile(False)
     ms = a.elapsed_time(b) / steps
-    # the teacher alone
-    with torch.cuda.stream(stream):
+    # the teacher alone, in both arithmetics
+    n = int(p.shape[0])
+    teacher = {}
+    for name, prec in (("tf32", roam.ROAM_TF32), ("f32", roam.ROAM_F32)):
         a.record(stream)
         for _ in range(steps):
-            r.teacher_eval(pt, dt, stream=stream)
+            r.teacher_eval(pt, dt, precision=prec, stream=stream)
         b.record(stream)
-    b.synchronize()
-    t_ms = a.elapsed_time(b) / steps
-    n = int(p.shape[0])
+        b.synchronize()
+        t_ms = a.elapsed_time(b) / steps
+        teacher[name] = {"ms": t_ms, "tflops": 2.0 * 595844 * n / (t_ms / 1000.0) / 1e12}
     r.close()
     return {"workload": f"floor256_kd512_w64h3 students, 360NeRF teacher, {I} points per field ({n} per step)",
-            "ms_per_step": ms, "points_per_s": n / (ms / 1000.0), "teacher_ms": t_ms,
-            "teacher_tflops": 2.0 * 595844 * n / (t_ms / 1000.0) / 1e12,
+            "ms_per_step": ms, "points_per_s": n / (ms / 1000.0), "teacher": teacher,
             "loss_first_last": [float(losses[0]), float(losses[-1])],
             "kernels": {k: {"launches": v[0], "ms": round(v[1], 3)} for k, v in prof.items()},
-            "precision": "teacher FP32 (cuBLAS), students BF16 tcgen05 forward and adjoint, FP32 master weights"}
+            "precision": "teacher TF32 tensor cores (cuBLAS, FP32 accumulation), students BF16 tcgen05 forward "
+                         "and adjoint, FP32 master weights"}
 
 
 def partition_bench(roam, F, torch, args, stream, flush):

@@ -43,7 +43,7 @@ typedef enum {
     ROAM_ERR_UNSUPPORTED = -7  /* valid request this build does not provide */
 } roam_status;
 
-enum { ROAM_F32 = 0, ROAM_BF16 = 1, ROAM_FP8 = 2 };   /* MLP arithmetic */
+enum { ROAM_F32 = 0, ROAM_BF16 = 1, ROAM_FP8 = 2, ROAM_TF32 = 3 };   /* arithmetic (TF32: the teacher only) */
 enum { ROAM_EQUIRECT = 0, ROAM_PERSPECTIVE = 1 };     /* camera models */
 enum { ROAM_SOFTPLUS = 0, ROAM_RELU = 1 };            /* density activation */
 
@@ -248,8 +248,11 @@ roam_status roam_teacher_load(roam_ctx *ctx, const float *weights, const float *
 
 /* The teacher at n points: p, d device float[n][3] (world position, view
  * direction); out device float[n][4] = (sigma, r, g, b), 16-byte aligned.
- * Asynchronous. */
-roam_status roam_teacher_eval(roam_ctx *ctx, const float *p, const float *d, int64_t n, float *out, void *stream);
+ * precision ROAM_F32: FP32 GEMMs; ROAM_TF32: the GEMMs on the tensor cores
+ * with TF32 operands (10-bit mantissas) and FP32 accumulation; the
+ * encodings, biases and activations stay FP32 either way.  Asynchronous. */
+roam_status roam_teacher_eval(roam_ctx *ctx, const float *p, const float *d, int64_t n, int precision, float *out,
+                              void *stream);
 
 /* Eq. 7 over n samples: *loss (device, may be NULL) = sum over samples of
  * [(sigma_s - sigma_t)^2 + |c_s - c_t|^2] / I, and dl_dout = 2 (student -

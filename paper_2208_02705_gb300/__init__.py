@@ -17,7 +17,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libroam.so")
 
-ROAM_F32, ROAM_BF16, ROAM_FP8 = 0, 1, 2
+ROAM_F32, ROAM_BF16, ROAM_FP8, ROAM_TF32 = 0, 1, 2, 3
 ROAM_EQUIRECT, ROAM_PERSPECTIVE = 0, 1
 ROAM_SOFTPLUS, ROAM_RELU = 0, 1
 
@@ -111,7 +111,7 @@ def load_library(path: str = LIB_PATH):
     L.roam_occupancy_update.argtypes = [vp, vp, i32, vp, vp, P(roam_occ_params), vp, vp, vp]
     L.roam_assign_fields.argtypes = [vp, i32, vp, vp, vp]
     L.roam_teacher_load.argtypes = [vp, vp, vp, i32]
-    L.roam_teacher_eval.argtypes = [vp, vp, vp, i64, vp, vp]
+    L.roam_teacher_eval.argtypes = [vp, vp, vp, i64, i32, vp, vp]
     L.roam_distill_loss.argtypes = [vp, vp, vp, i64, ctypes.c_float, vp, vp, vp]
     L.roam_mlp_backward.argtypes = [vp, vp, vp, vp, i64, i32, vp, vp, vp]
     L.roam_get_weights.argtypes = [vp, vp, i32]
@@ -346,11 +346,12 @@ class Roam:
         aff = np.ascontiguousarray(affine, dtype=np.float32)
         _check(self.L.roam_teacher_load(self.h, _ptr(weights), _ptr(aff), int(on_dev)))
 
-    def teacher_eval(self, p, d, stream=None):
+    def teacher_eval(self, p, d, precision=None, stream=None):
         import torch
         n = int(p.shape[0])
         out = torch.empty((n, 4), dtype=torch.float32, device=self._dev())
-        _check(self.L.roam_teacher_eval(self.h, _ptr(p), _ptr(d), n, _ptr(out), _stream(stream)))
+        _check(self.L.roam_teacher_eval(self.h, _ptr(p), _ptr(d), n, ROAM_F32 if precision is None else int(precision),
+                                        _ptr(out), _stream(stream)))
         return out
 
     def distill_loss(self, student, teacher, I: float, stream=None):
@@ -370,13 +371,13 @@ class Roam:
         return grad
 
     def distill_step(self, p, d, field, I: float, lr: float, step: int, teacher_out=None, precision=None,
-                     stream=None):
+                     teacher_precision=None, stream=None):
         """One distillation step (Eq. 7): teacher targets (computed unless
         given), student outputs (FP32 by default), loss and its gradient,
         the adjoint in the same precision (FP32 SIMT or BF16 tcgen05) and
         Adam.  Returns the loss (device tensor)."""
         prec = ROAM_F32 if precision is None else precision
-        t = teacher_out if teacher_out is not None else self.teacher_eval(p, d, stream=stream)
+        t = teacher_out if teacher_out is not None else self.teacher_eval(p, d, teacher_precision, stream=stream)
         sdt = self.mlp_eval(p, d, field, prec, stream=stream)
         loss, dl = self.distill_loss(sdt, t, I, stream=stream)
         g = self.mlp_backward(p, d, field, dl, precision=prec, stream=stream)

@@ -185,7 +185,7 @@ struct TeacherAffine {
 int64_t teacher_param_count();
 size_t teacher_workspace_floats(int64_t n);
 int teacher_eval(void *cublas_handle, const float *w, TeacherAffine aff, int64_t n, const float *p, const float *d,
-                 float4 *out, float *ws, cudaStream_t s);
+                 float4 *out, float *ws, bool tf32, cudaStream_t s);
 void launch_distill_loss(int64_t n, const float4 *student, const float4 *teacher, float I, float4 *dl, float *loss,
                          cudaStream_t s);
 size_t assign_scratch_bytes();

@@ -1191,10 +1191,12 @@ roam_status roam_teacher_load(roam_ctx *c, const float *weights, const float *af
     return ROAM_OK;
 }
 
-roam_status roam_teacher_eval(roam_ctx *c, const float *p, const float *d, int64_t n, float *out, void *stream)
+roam_status roam_teacher_eval(roam_ctx *c, const float *p, const float *d, int64_t n, int precision, float *out,
+                              void *stream)
 {
     ROAM_TRY(set_dev(c));
     if (!c->has_teacher) return fail(ROAM_ERR_STATE, "no teacher loaded");
+    if (precision != ROAM_F32 && precision != ROAM_TF32) return fail(ROAM_ERR_ARG, "precision: ROAM_F32 or ROAM_TF32");
     if (n < 0 || n > 0x7fffffff) return fail(ROAM_ERR_ARG, "bad sample count");
     if (n == 0) return ROAM_OK;
     if (!p || !d || !out) return fail(ROAM_ERR_ARG, "null pointer");
@@ -1202,7 +1204,7 @@ roam_status roam_teacher_eval(roam_ctx *c, const float *p, const float *d, int64
     cudaStream_t s = (cudaStream_t)stream;
     ROAM_TRY(ensure(c->teacher_ws, teacher_workspace_floats(n)));
     if (teacher_eval(c->cublas, c->teacher_w.p, c->teacher_aff, n, p, d, reinterpret_cast<float4 *>(out),
-                     c->teacher_ws.p, s))
+                     c->teacher_ws.p, precision == ROAM_TF32, s))
         return fail(ROAM_ERR_CUDA, "cuBLAS GEMM failed in the teacher");
     c->last = s;
     return launched("teacher");

@@ -3,8 +3,9 @@
 // of width 256 with a skip of F(x) into layer 5, a density head, a feature
 // head, and a 128-wide colour layer on [feature; F(d)].  Its layers are
 // plain dense GEMMs over the sample batch (K up to 319, N = 256), run as
-// FP32 cuBLAS GEMMs; the encodings, bias + activation epilogues and the
-// output heads are this file's kernels.
+// cuBLAS GEMMs in FP32 or, on request, on the tensor cores with TF32
+// operands and FP32 accumulation; the encodings, bias + activation
+// epilogues and the output heads are this file's kernels, in FP32.
 //
 // Activations live row-major per sample in two ping-pong buffers whose
 // trailing columns hold the encodings the skip and the colour layer read:
@@ -99,10 +100,12 @@ size_t teacher_workspace_floats(int64_t n) { return (size_t)n * (kLdA + kLdB + 1
 
 // w: device FP32 parameters in the API layout (row-major [out][in] then bias, layer after layer)
 int teacher_eval(void *handle, const float *w, TeacherAffine aff, int64_t n, const float *p, const float *d,
-                 float4 *out, float *ws, cudaStream_t s)
+                 float4 *out, float *ws, bool tf32, cudaStream_t s)
 {
     cublasHandle_t h = static_cast<cublasHandle_t>(handle);
     if (cublasSetStream(h, s) != CUBLAS_STATUS_SUCCESS) return 1;
+    if (cublasSetMathMode(h, tf32 ? CUBLAS_TF32_TENSOR_OP_MATH : CUBLAS_PEDANTIC_MATH) != CUBLAS_STATUS_SUCCESS)
+        return 1;
     float *A = ws, *B = A + (size_t)n * kLdA, *sig = B + (size_t)n * kLdB, *z = sig + n;
     const int grid = 1024;
     k_teacher_encode<<<grid, 256, 0, s>>>(n, p, d, aff, A, B);

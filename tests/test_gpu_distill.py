@@ -40,16 +40,30 @@ def _ctx(roam, wl, W, H, w):
     return r
 
 
-def test_teacher_matches_oracle(roam, room32):
+@pytest.mark.parametrize("tf32", [False, True])
+def test_teacher_matches_oracle(roam, room32, tf32):
+    """FP32 GEMMs: within 1e-4 (FP32 sums of up to 319 terms over 11
+    layers).  TF32 tensor-core GEMMs: both operands of every product are
+    rounded to 11 significant bits (2^-11 relative each); with independent
+    rounding signs a layer adds ~2^-11 sqrt(K)/K ~ 3e-5 of its |W||x| sum,
+    ~1e-4 relative after 11 layers (measured: 1e-4 on the colours, 4e-4 on
+    the density): bars 1e-3 (colours, sigmoid slope <= 1/4) and 5e-3
+    (density, relative to max(1, sigma))."""
     r = _ctx(roam, room32, 32, 2, room32.weights)
     p, d, f = F.distill_points(room32.scene, room32.part, 1, 64)
-    out = r.teacher_eval(torch.from_numpy(p).cuda(), torch.from_numpy(d).cuda())
+    out = r.teacher_eval(torch.from_numpy(p).cuda(), torch.from_numpy(d).cuda(),
+                         precision=roam.ROAM_TF32 if tf32 else roam.ROAM_F32)
     torch.cuda.synchronize()
     ref = O.teacher_eval(F.teacher_weights(TEACHER_SEED, bias_scale=0.1), F.scene_affine(room32.scene), p.astype(np.float64),
                          d.astype(np.float64))
     got = out.cpu().numpy().astype(np.float64)
-    assert np.abs(got[:, 1:] - ref[:, 1:]).max() <= 1e-4
-    assert np.all(np.abs(got[:, 0] - ref[:, 0]) <= 1e-4 * np.maximum(1.0, ref[:, 0]))
+    tol_c, tol_s = (1e-3, 5e-3) if tf32 else (1e-4, 1e-4)
+    ec = np.abs(got[:, 1:] - ref[:, 1:]).max()
+    es = (np.abs(got[:, 0] - ref[:, 0]) / np.maximum(1.0, ref[:, 0])).max()
+    print(f"teacher tf32={tf32}: colour max err {ec:.3e}, density rel err {es:.3e}")
+    assert ec <= tol_c and es <= tol_s
+    if tf32:
+        assert ec > 0 or es > 0          # the tensor-core path really rounds
     r.close()
 
 
