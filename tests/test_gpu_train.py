@@ -171,6 +171,19 @@ def test_adam_matches_oracle_and_refreshes_copies(roam, room32, room32_grid):
         torch.cuda.synchronize()
         err = np.abs(rgb.cpu().numpy() - ref["rgb"])[ok].max()
         assert err <= tol, (prec, err)
+    # the FP8 images, rebuilt lazily at the first FP8 launch after the steps
+    ref8 = O.render(room32_grid, new_w, room32.affine, W, H, room32.sigma_scale, F.camera_array(room32.cams), None,
+                    room32.delta, room32.n_max, quant=1)
+    rgb8, _, _ = r.render(room32.cams, roam.render_opts(room32.delta, room32.n_max, precision=roam.ROAM_FP8))
+    torch.cuda.synchronize()
+    assert np.abs(rgb8.cpu().numpy() - ref8["rgb"])[ok].max() <= 2e-2
+    # the row-padded copy of the FP32 adjoint, rebuilt at its first launch
+    rays_np = _rays(room32, 1024, 23)
+    target = np.random.default_rng(24).uniform(0, 1, (1024, 3)).astype(np.float32)
+    _, g = _grad_gpu(roam, r, room32, rays_np, target, roam.ROAM_F32)
+    _, go, _, _ = O.loss_grad(room32_grid, new_w, room32.affine, W, H, room32.sigma_scale, F.camera_array(room32.cams),
+                              rays_np, target, room32.delta, room32.n_max)
+    assert np.abs(g - go).max() <= 1e-3 * np.abs(go).max()
     r.close()
 
 
