@@ -179,7 +179,8 @@ __device__ __forceinline__ int view_of(const DevCamera *cams, int n_views, uint3
 // out of an empty brick to the first sample past the exit of the largest
 // empty cube of bricks around it (from the brick distance map), minus one
 // sample so that a sample rounded onto that face is still tested.  Emitted
-// records also feed a per-block field histogram for the bucketing.
+// records also feed a per-block field histogram for the bucketing.  Launched
+// with about one thread per ray (the stride loop covers larger requests).
 __global__ void __launch_bounds__(256) k_march(GridDev g, MarchParams p)
 {
     extern __shared__ uint32_t s_hist[];      // per-block field histogram (when p.hist)

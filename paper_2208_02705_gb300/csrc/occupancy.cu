@@ -148,8 +148,8 @@ void launch_occupancy_scan(const GridDev &g, const DevCamera *cams, int view, in
                            const float *opacity, const roam_occ_params &q, uint32_t *hit, uint32_t *free_bits,
                            float *logit, uint32_t *bits, int n_sm, cudaStream_t s)
 {
+    // one thread per pixel: the traversal lengths differ widely between rays
     int blocks_r = (n_pix + 255) / 256;
-    if (blocks_r > n_sm * 8) blocks_r = n_sm * 8;
     if (blocks_r < 1) blocks_r = 1;
     k_occ_rays<<<blocks_r, 256, 0, s>>>(g, cams, view, depth, opacity, q.a_min, hit, free_bits);
     const int64_t n_vox = (int64_t)g.gx * g.gy * g.gz;
