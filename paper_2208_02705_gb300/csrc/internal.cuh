@@ -245,6 +245,9 @@ int tc_tile_samples();
 int tc_tile_group(int W, bool f8);
 void launch_pack_tc(const float *w32, int n_fields, int W, int H, int64_t P, void *wimg, int64_t img_bytes, bool f8,
                     cudaStream_t s);
+// Adam fused with the BF16 image refresh (W <= 64); false: not available for this shape
+bool launch_adam_tc(float *w32, float *m, float *v, const float *g, int n_fields, int W, int H, int64_t P, void *wimg,
+                    int64_t img_bytes, float lr, float b1, float b2, float eps, float bc1, float bc2, cudaStream_t s);
 void launch_mlp_tc(const MlpWeights &w, bool f8, const SampleSrc &src, const BucketBufs &b, Counters *ctr,
                    float4 *out, int n_sm, cudaStream_t s);
 

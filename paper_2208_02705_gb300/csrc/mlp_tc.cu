@@ -481,6 +481,69 @@ __global__ void k_pack_tc(const float *__restrict__ w32, int n_fields, int64_t P
     }
 }
 
+// Adam on the FP32 masters fused with the refresh of the BF16 image (every
+// bias folded into the MMA: W <= 64): one thread per parameter updates it
+// and writes its one image element (or its FP32 output-table entry).
+template <int W, int H>
+__global__ void k_adam_tc(float *__restrict__ w, float *__restrict__ m, float *__restrict__ v,
+                          const float *__restrict__ g, int n_fields, int64_t P, uint8_t *__restrict__ img,
+                          int64_t img_bytes, float lr, float b1, float b2, float eps, float bc1, float bc2)
+{
+    using S = TcShape<W, H, false>;
+    static_assert(S::kFold, "fused refresh needs every bias in the image's MMA operands");
+    const ApiLayout o(W, H);
+    const int64_t n = (int64_t)n_fields * P;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float gi = g[i];
+        const float mi = fmaf(b1, m[i], (1.f - b1) * gi);
+        const float vi = fmaf(b2, v[i], (1.f - b2) * gi * gi);
+        m[i] = mi;
+        v[i] = vi;
+        const float wi = w[i] - lr * (mi / bc1) / (sqrtf(vi / bc2) + eps);
+        w[i] = wi;
+        // where this parameter sits in the field's image
+        const int64_t f = i / P, q = i % P;
+        uint8_t *dst = img + f * img_bytes;
+        int l, nr, k;
+        if (q < o.hid) {
+            const int r = (int)(q - o.l1);
+            l = 0;
+            if (r < W * kPeX) { nr = r / kPeX; k = r % kPeX; }
+            else { nr = r - W * kPeX; k = kPeX; }
+        } else if (q < o.head) {
+            const int64_t r0 = q - o.hid;
+            l = 1 + (int)(r0 / (W * W + W));
+            const int r = (int)(r0 % (W * W + W));
+            if (r < W * W) { nr = r / W; k = r % W; }
+            else { nr = r - W * W; k = W; }
+        } else if (q < o.col) {
+            const int r = (int)(q - o.head);
+            int ar;
+            l = H;
+            if (r < (1 + W) * W) { ar = r / W; k = r % W; }
+            else { ar = r - (1 + W) * W; k = W; }
+            nr = ar == 0 ? W : ar - 1;          // image rows: W features, then the density logit
+        } else if (q < o.out) {
+            const int r = (int)(q - o.col), kc = W + kPeD;
+            l = H + 1;
+            if (r < W * kc) { nr = r / kc; const int ka = r % kc; k = ka < W ? ka : ka + 1; }
+            else { nr = r - W * kc; k = W; }
+        } else {
+            // the FP32 3-output layer: [W][4] then bias[4]
+            const int r = (int)(q - o.out);
+            float *tab = reinterpret_cast<float *>(dst + S::kMatBytes);
+            if (r < 3 * W) tab[4 * (r % W) + r / W] = wi;
+            else tab[4 * W + (r - 3 * W)] = wi;
+            continue;
+        }
+        const int N = S::N(l);
+        const int off = S::offset(l) + (k / S::kCE) * N * 128 + (nr >> 3) * 1024 + (nr & 7) * 128 +
+                        ((((k % S::kCE) >> 3) ^ (nr & 7)) << 4) + (k & 7) * 2;
+        const uint32_t bits = __float_as_uint(wi);
+        *reinterpret_cast<uint16_t *>(dst + off) = (uint16_t)((bits + 0x7fffu + ((bits >> 16) & 1u)) >> 16);
+    }
+}
+
 template <int W, int H, bool F8>
 int tc_smem_bytes() { return 1024 + TcShape<W, H, F8>::kImageAlloc; }
 
@@ -552,6 +615,21 @@ void launch_pack_tc(const float *w32, int n_fields, int W, int H, int64_t P, voi
     }
     ROAM_TC_CASES
 #undef ROAM_CASE
+}
+
+bool launch_adam_tc(float *w32, float *m, float *v, const float *g, int n_fields, int W, int H, int64_t P, void *wimg,
+                    int64_t img_bytes, float lr, float b1, float b2, float eps, float bc1, float bc2, cudaStream_t s)
+{
+#define ROAM_ADAM_CASE(WW, HH)                                                                                   \
+    if (W == WW && H == HH) {                                                                                  \
+        k_adam_tc<WW, HH><<<2048, 256, 0, s>>>(w32, m, v, g, n_fields, P, (uint8_t *)wimg, img_bytes, lr, b1, b2, \
+                                               eps, bc1, bc2);                                                 \
+        return true;                                                                                           \
+    }
+    ROAM_ADAM_CASE(32, 1) ROAM_ADAM_CASE(32, 2) ROAM_ADAM_CASE(32, 3) ROAM_ADAM_CASE(32, 4)
+    ROAM_ADAM_CASE(64, 1) ROAM_ADAM_CASE(64, 2) ROAM_ADAM_CASE(64, 3) ROAM_ADAM_CASE(64, 4)
+#undef ROAM_ADAM_CASE
+    return false;
 }
 
 void launch_mlp_tc(const MlpWeights &w, bool f8, const SampleSrc &src, const BucketBufs &b, Counters *ctr,

@@ -1561,11 +1561,17 @@ roam_status roam_adam_step(roam_ctx *c, const float *grad, const roam_adam_cfg *
     const float bc2 = (float)(1.0 - std::pow((double)cfg->beta2, (double)cfg->step));
     {
         ProfScope ps(c, P_ADAM, s);
-        launch_adam(q.w32.p, c->adam_m.p, c->adam_v.p, grad, n, cfg->lr, cfg->beta1, cfg->beta2, cfg->eps, bc1, bc2,
-                    s);
-        // the BF16 images now; the other derived copies when a launch needs them
+        // the BF16 images now (in the same pass where they fold every bias);
+        // the other derived copies when a launch needs them
         const int W = c->md.width, H = c->md.n_hidden;
-        if (q.tc_ok) launch_pack_tc(q.w32.p, c->n_fields, W, H, q.P, q.wimg.p, q.img_bytes, false, s);
+        const bool fused = q.tc_ok && launch_adam_tc(q.w32.p, c->adam_m.p, c->adam_v.p, grad, c->n_fields, W, H, q.P,
+                                                     q.wimg.p, q.img_bytes, cfg->lr, cfg->beta1, cfg->beta2, cfg->eps,
+                                                     bc1, bc2, s);
+        if (!fused) {
+            launch_adam(q.w32.p, c->adam_m.p, c->adam_v.p, grad, n, cfg->lr, cfg->beta1, cfg->beta2, cfg->eps, bc1,
+                        bc2, s);
+            if (q.tc_ok) launch_pack_tc(q.w32.p, c->n_fields, W, H, q.P, q.wimg.p, q.img_bytes, false, s);
+        }
         q.stale |= kStaleWt | kStaleWr | (q.tc8_ok ? kStaleImg8 : 0u);
         if (!q.tc_ok) ROAM_TRY(refresh(c, ROAM_F32, true, s));
     }

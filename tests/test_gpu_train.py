@@ -171,6 +171,15 @@ def test_adam_matches_oracle_and_refreshes_copies(roam, room32, room32_grid):
         torch.cuda.synchronize()
         err = np.abs(rgb.cpu().numpy() - ref["rgb"])[ok].max()
         assert err <= tol, (prec, err)
+    # the BF16 images that Adam refreshes in place equal a fresh packing of
+    # the updated masters: bit-identical renders
+    r2 = _ctx(roam, room32, new_w, W, H)
+    o16 = roam.render_opts(room32.delta, room32.n_max, precision=roam.ROAM_BF16)
+    a16, _, _ = r.render(room32.cams, o16)
+    b16, _, _ = r2.render(room32.cams, o16)
+    torch.cuda.synchronize()
+    assert torch.equal(a16, b16)
+    r2.close()
     # the FP8 images, rebuilt lazily at the first FP8 launch after the steps
     ref8 = O.render(room32_grid, new_w, room32.affine, W, H, room32.sigma_scale, F.camera_array(room32.cams), None,
                     room32.delta, room32.n_max, quant=1)
