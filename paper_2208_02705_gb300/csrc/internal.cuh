@@ -183,6 +183,8 @@ struct TeacherAffine {
     float v[6];      // global position -> [-1, 1]^3: scale xyz, offset xyz
 };
 int64_t teacher_param_count();
+int64_t teacher_padded_floats();
+void launch_teacher_pad(const float *w, float *wp, cudaStream_t s);
 size_t teacher_workspace_floats(int64_t n);
 int teacher_eval(void *cublas_handle, const float *w, TeacherAffine aff, int64_t n, const float *p, const float *d,
                  float4 *out, float *ws, bool tf32, cudaStream_t s);

@@ -1175,15 +1175,21 @@ roam_status roam_teacher_load(roam_ctx *c, const float *weights, const float *af
     if (!weights || !affine) return fail(ROAM_ERR_ARG, "null weights or affine");
     const int64_t P = teacher_param_count();
     c->has_teacher = false;
-    ROAM_TRY(ensure(c->teacher_w, (size_t)P));
-    ROAM_CUDA(cudaMemcpy(c->teacher_w.p, weights, (size_t)P * sizeof(float),
+    // the caller's layout lands in the workspace, is checked, then padded
+    // into the GEMM layout the evaluation reads
+    ROAM_TRY(ensure(c->teacher_ws, (size_t)P));
+    ROAM_TRY(ensure(c->teacher_w, (size_t)teacher_padded_floats()));
+    ROAM_CUDA(cudaMemcpy(c->teacher_ws.p, weights, (size_t)P * sizeof(float),
                          on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice));
     ROAM_CUDA(cudaMemset(c->d_flag, 0, 4));
-    k_check_finite<<<1024, 256>>>(c->teacher_w.p, P, c->d_flag);
+    k_check_finite<<<1024, 256>>>(c->teacher_ws.p, P, c->d_flag);
     ROAM_TRY(launched("teacher weight check"));
     uint32_t bad = 0;
     ROAM_CUDA(cudaMemcpy(&bad, c->d_flag, 4, cudaMemcpyDeviceToHost));
     if (bad) return fail(ROAM_ERR_ARG, "teacher weights contain NaN or Inf");
+    launch_teacher_pad(c->teacher_ws.p, c->teacher_w.p, 0);
+    ROAM_TRY(launched("teacher pad"));
+    ROAM_CUDA(cudaDeviceSynchronize());
     for (int i = 0; i < 6; ++i) {
         if (!finite(affine[i])) return fail(ROAM_ERR_ARG, "non-finite teacher affine");
         c->teacher_aff.v[i] = affine[i];

@@ -53,15 +53,55 @@ __global__ void k_teacher_encode(int64_t n, const float *__restrict__ p, const f
     }
 }
 
-// Y[i][0..N) += b, then ReLU when relu
+// Y[i][0..N) += b, then ReLU when relu; N and ld multiples of 4: one float4
+// per thread, a block of rows per CTA (threadIdx.y)
 __global__ void k_bias_act(int64_t n, int N, int ld, float *__restrict__ Y, const float *__restrict__ b, int relu)
 {
-    const int64_t total = n * N;
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t i = e / N;
-        const int c = (int)(e % N);
-        float v = Y[i * ld + c] + b[c];
-        Y[i * ld + c] = relu ? fmaxf(v, 0.f) : v;
+    const int c4 = threadIdx.x;                       // float4 column, blockDim.x = N / 4
+    const float4 bb = reinterpret_cast<const float4 *>(b)[c4];
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.y + threadIdx.y; i < n; i += (int64_t)gridDim.x * blockDim.y) {
+        float4 *y = reinterpret_cast<float4 *>(Y + i * ld) + c4;
+        float4 v = *y;
+        v.x += bb.x; v.y += bb.y; v.z += bb.z; v.w += bb.w;
+        if (relu) {
+            v.x = fmaxf(v.x, 0.f); v.y = fmaxf(v.y, 0.f); v.z = fmaxf(v.z, 0.f); v.w = fmaxf(v.w, 0.f);
+        }
+        *y = v;
+    }
+}
+
+// the layers of the API layout: output width, input width
+constexpr int kTLayers = 12;
+__host__ __device__ constexpr int t_out(int l)
+{
+    return l == 8 ? 1 : (l == 10 ? kTC : (l == 11 ? 3 : kTW));
+}
+__host__ __device__ constexpr int t_in(int l)
+{
+    return l == 0 ? kPeX : (l == 4 ? kTW + kPeX : (l == 10 ? kTW + kPeD : (l == 11 ? kTC : kTW)));
+}
+__host__ __device__ constexpr int round4i(int x) { return (x + 3) & ~3; }
+
+// API layout -> every layer's matrix with its rows padded to a multiple of
+// 4 floats (zeros), bias after it (16-byte aligned operands for the GEMMs)
+__global__ void k_teacher_pad(const float *__restrict__ w, float *__restrict__ wp)
+{
+    int64_t src = 0, dst = 0;
+    for (int l = 0; l < kTLayers; ++l) {
+        const int N = t_out(l), K = t_in(l), Kp = round4i(K);
+        for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < (int64_t)N * Kp + N;
+             e += (int64_t)gridDim.x * blockDim.x) {
+            float v = 0.f;
+            if (e < (int64_t)N * Kp) {
+                const int r = (int)(e / Kp), k = (int)(e % Kp);
+                if (k < K) v = w[src + (int64_t)r * K + k];
+            } else {
+                v = w[src + (int64_t)N * K + (e - (int64_t)N * Kp)];
+            }
+            wp[dst + e] = v;
+        }
+        src += (int64_t)N * K + N;
+        dst += round4i((int)((int64_t)N * Kp + N));
     }
 }
 
@@ -89,6 +129,15 @@ cublasStatus_t dense(cublasHandle_t h, int64_t n, int N, int K, const float *W, 
 
 }  // namespace
 
+int64_t teacher_padded_floats()
+{
+    int64_t t = 0;
+    for (int l = 0; l < kTLayers; ++l) t += round4i(t_out(l) * round4i(t_in(l)) + t_out(l));
+    return t;
+}
+
+void launch_teacher_pad(const float *w, float *wp, cudaStream_t s) { k_teacher_pad<<<512, 256, 0, s>>>(w, wp); }
+
 int64_t teacher_param_count()
 {
     return ((int64_t)kTW * kPeX + kTW) + 3 * ((int64_t)kTW * kTW + kTW) + ((int64_t)kTW * (kTW + kPeX) + kTW) +
@@ -98,7 +147,8 @@ int64_t teacher_param_count()
 
 size_t teacher_workspace_floats(int64_t n) { return (size_t)n * (kLdA + kLdB + 1 + 3); }
 
-// w: device FP32 parameters in the API layout (row-major [out][in] then bias, layer after layer)
+// w: device FP32 parameters padded by launch_teacher_pad (each layer's rows
+// padded to a multiple of 4 floats with zeros, then its bias)
 int teacher_eval(void *handle, const float *w, TeacherAffine aff, int64_t n, const float *p, const float *d,
                  float4 *out, float *ws, bool tf32, cudaStream_t s)
 {
@@ -111,10 +161,14 @@ int teacher_eval(void *handle, const float *w, TeacherAffine aff, int64_t n, con
     k_teacher_encode<<<grid, 256, 0, s>>>(n, p, d, aff, A, B);
     const float *q = w;
     int st = 0;
+    // K: the layer's input width; the GEMM runs over it rounded up to 4 (the
+    // padded weight columns and the activation columns there are zero)
     auto layer = [&](int N, int K, const float *X, int ldx, float *Y, int ldy, int relu) {
-        st |= dense(h, n, N, K, q, X, ldx, Y, ldy) != CUBLAS_STATUS_SUCCESS;
-        k_bias_act<<<grid, 256, 0, s>>>(n, N, ldy, Y, q + (int64_t)N * K, relu);
-        q += (int64_t)N * K + N;
+        const int Kp = round4i(K);
+        st |= dense(h, n, N, Kp, q, X, ldx, Y, ldy) != CUBLAS_STATUS_SUCCESS;
+        const dim3 blk((unsigned)(N / 4), (unsigned)(256 / (N / 4)));
+        k_bias_act<<<grid, blk, 0, s>>>(n, N, ldy, Y, q + (int64_t)N * Kp, relu);
+        q += round4i(N * Kp + N);
     };
     layer(kTW, kPeX, A + kTW, kLdA, B, kLdB, 1);          // layer 1 on F(x)
     layer(kTW, kTW, B, kLdB, A, kLdA, 1);                 // layer 2
@@ -127,7 +181,7 @@ int teacher_eval(void *handle, const float *w, TeacherAffine aff, int64_t n, con
     // density head: N = 1
     st |= dense(h, n, 1, kTW, q, A, kLdA, sig, 1) != CUBLAS_STATUS_SUCCESS;
     const float *b_sig = q + kTW;
-    q += kTW + 1;
+    q += round4i(kTW + 1);
     layer(kTW, kTW, A, kLdA, B, kLdB, 1);                 // feature head (B keeps F(d) after it)
     layer(kTC, kTW + kPeD, B, kLdB, A, kLdA, 1);          // layer 10 on [feature; F(d)]
     st |= dense(h, n, 3, kTC, q, A, kLdA, z, 3) != CUBLAS_STATUS_SUCCESS;   // layer 11
