@@ -20,12 +20,15 @@ struct SlotIter {
     uint32_t n_live;
     uint32_t R;
     __device__ uint64_t total() const { return (uint64_t)((n_live + 31u) >> 5) * R * 32u; }
+    // slot ids fit in 32 bits (the round size is chosen so), so the column
+    // arithmetic stays 32-bit
     __device__ bool valid(uint64_t s, uint32_t &key) const
     {
         const uint32_t lane = (uint32_t)(s & 31u);
-        const uint64_t col = s >> 5;
-        const uint32_t k = (uint32_t)(col % R);
-        const uint32_t i = (uint32_t)(col / R) * 32u + lane;
+        const uint32_t col = (uint32_t)(s >> 5);
+        const uint32_t q = col / R;
+        const uint32_t k = col - q * R;
+        const uint32_t i = q * 32u + lane;
         if (i >= n_live || k >= cnt[i]) return false;
         key = recs[s] >> 16;
         return true;

@@ -492,8 +492,10 @@ __global__ void k_adam_tc(float *__restrict__ w, float *__restrict__ m, float *_
     using S = TcShape<W, H, false>;
     static_assert(S::kFold, "fused refresh needs every bias in the image's MMA operands");
     const ApiLayout o(W, H);
-    const int64_t n = (int64_t)n_fields * P;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t f = blockIdx.y;                      // one grid row per field: no 64-bit division
+    if (f >= n_fields) return;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < P; q += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = f * P + q;
         const float gi = g[i];
         const float mi = fmaf(b1, m[i], (1.f - b1) * gi);
         const float vi = fmaf(b2, v[i], (1.f - b2) * gi * gi);
@@ -502,7 +504,6 @@ __global__ void k_adam_tc(float *__restrict__ w, float *__restrict__ m, float *_
         const float wi = w[i] - lr * (mi / bc1) / (sqrtf(vi / bc2) + eps);
         w[i] = wi;
         // where this parameter sits in the field's image
-        const int64_t f = i / P, q = i % P;
         uint8_t *dst = img + f * img_bytes;
         int l, nr, k;
         if (q < o.hid) {
@@ -620,9 +621,11 @@ void launch_pack_tc(const float *w32, int n_fields, int W, int H, int64_t P, voi
 bool launch_adam_tc(float *w32, float *m, float *v, const float *g, int n_fields, int W, int H, int64_t P, void *wimg,
                     int64_t img_bytes, float lr, float b1, float b2, float eps, float bc1, float bc2, cudaStream_t s)
 {
+    if (n_fields > 65535) return false;           // one grid row per field
 #define ROAM_ADAM_CASE(WW, HH)                                                                                   \
     if (W == WW && H == HH) {                                                                                  \
-        k_adam_tc<WW, HH><<<2048, 256, 0, s>>>(w32, m, v, g, n_fields, P, (uint8_t *)wimg, img_bytes, lr, b1, b2, \
+        const dim3 grid((unsigned)((P + 255) / 256), (unsigned)n_fields);                                       \
+        k_adam_tc<WW, HH><<<grid, 256, 0, s>>>(w32, m, v, g, n_fields, P, (uint8_t *)wimg, img_bytes, lr, b1, b2, \
                                                eps, bc1, bc2);                                                 \
         return true;                                                                                           \
     }
