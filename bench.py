@@ -478,6 +478,8 @@ def distill_bench(roam, F, torch, args, stream):
     n = int(p.shape[0])
     teacher = {}
     for name, prec in (("tf32", roam.ROAM_TF32), ("f32", roam.ROAM_F32)):
+        for _ in range(2):                     # warm-up: library kernel selection and loading
+            r.teacher_eval(pt, dt, precision=prec, stream=stream)
         a.record(stream)
         for _ in range(steps):
             r.teacher_eval(pt, dt, precision=prec, stream=stream)

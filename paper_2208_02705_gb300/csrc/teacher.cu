@@ -154,7 +154,7 @@ int teacher_eval(void *handle, const float *w, TeacherAffine aff, int64_t n, con
 {
     cublasHandle_t h = static_cast<cublasHandle_t>(handle);
     if (cublasSetStream(h, s) != CUBLAS_STATUS_SUCCESS) return 1;
-    if (cublasSetMathMode(h, tf32 ? CUBLAS_TF32_TENSOR_OP_MATH : CUBLAS_PEDANTIC_MATH) != CUBLAS_STATUS_SUCCESS)
+    if (cublasSetMathMode(h, tf32 ? CUBLAS_TF32_TENSOR_OP_MATH : CUBLAS_DEFAULT_MATH) != CUBLAS_STATUS_SUCCESS)
         return 1;
     float *A = ws, *B = A + (size_t)n * kLdA, *sig = B + (size_t)n * kLdB, *z = sig + n;
     const int grid = 1024;
