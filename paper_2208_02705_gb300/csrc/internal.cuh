@@ -207,7 +207,7 @@ void launch_bucket(const uint32_t *cnt, const uint32_t *recs, const uint32_t *li
                    int n_fields, int tile, const BucketBufs &b, Counters *ctr, int grid,
                    cudaStream_t s, ClassBounds cb);
 void launch_mlp_simt(const MlpWeights &w, const SampleSrc &src, const BucketBufs &b,
-                     Counters *ctr, float4 *out, int grid, cudaStream_t s);
+                     Counters *ctr, float4 *out, int n_sm, cudaStream_t s);
 void launch_pack_simt(const float *w32, int n_fields, int W, int H, int64_t P, float *wt,
                       int64_t Pt, cudaStream_t s);
 int64_t simt_transposed_size(int W, int H);

@@ -50,7 +50,8 @@ struct RLayout {
     }
 };
 
-// offsets of the transposed copy used by the forward kernel (same as mlp_simt.cu)
+// offsets of the transposed copy used by the forward kernel (same as mlp_simt.cu;
+// the head's row: W features, then the density logit, then zeros)
 struct TLayout {
     int64_t l1, hid, head, col, out, total;
     __host__ __device__ TLayout(int W, int H)
@@ -277,9 +278,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_mlp_bwd_simt(MlpWeights w, Samp
         {
             float acc[NH];
             dense_arr<W, NH>(hs[H - 1], wtf + TL.head, acc);
-            s_logit = acc[0];
+            s_logit = acc[W];             // the transposed head: features, then the density logit
 #pragma unroll
-            for (int o = 0; o < W; ++o) inc[o] = acc[1 + o];
+            for (int o = 0; o < W; ++o) inc[o] = acc[o];
         }
         encode_arr<4>(dx, dy, dz, inc + W);
         float gg[W];

@@ -1,20 +1,42 @@
 // FP32 SIMT evaluation of the per-field tiny MLPs (the plain FP32 form of
-// querying many MLPs at once), one thread per sample, tiles of 128 samples
-// of one field.  Positional encoding (Eq. 1's F(.)) is recomputed in the
-// kernel.  Weights are read as a transposed FP32 copy ([in][out], padded to
-// multiples of 4 outputs) through the read-only path; the whole warp reads
-// the same weight, so every load is a broadcast.
+// querying many MLPs at once), tiles of 128 samples of one field, each layer
+// a register-tiled FP32 product: a thread owns 4 consecutive samples (a
+// sample group) and TN = W / OG of the layer's outputs, so every weight it
+// loads feeds 4 FMAs and every activation TN.  The layer's input sits in
+// shared memory, feature-major ([k][128 samples]); the weights are read as a
+// transposed FP32 copy ([in][out], output rows padded to 16 bytes) through
+// the read-only path, the OG threads of a sample group reading one
+// contiguous run of each row.  Positional encoding (Eq. 1's F(.)) is
+// recomputed in the kernel.  The density (the head's extra output) rides in
+// the head layer's loop; the 3-output colour layer is formed from the colour
+// features still in registers, summed over the sample group's threads with
+// warp shuffles.
 #include "internal.cuh"
 
 namespace roam {
 
 namespace {
 
-constexpr int kThreads = 128;
-
 __host__ __device__ constexpr int round4(int x) { return (x + 3) & ~3; }
 
-// Parameter offsets of the transposed copy.
+// Thread layout of one tile: 32 sample groups of 4 samples times OG output
+// groups; thread t has sample group t / OG and output group t % OG, and
+// owns outputs n = 4 (q OG + og) + i (q < TN / 4, i < 4): the float4 loads
+// of one weight row by a sample group's threads are contiguous.
+template <int W>
+struct SimtShape {
+    static constexpr int OG = W >= 128 ? 8 : 4;
+    static constexpr int TN = W / OG;
+    static constexpr int kThreads = 32 * OG;
+    static constexpr int kMinBlocks = W >= 128 ? 2 : 0;                   // W = 128: two blocks per SM
+    static constexpr int kRows = (W + kPeD) > kPeX ? (W + kPeD) : kPeX;   // activation rows in shared memory
+    static constexpr size_t kSmem = (size_t)kRows * 128 * sizeof(float) + 128 * sizeof(uint32_t);
+    static_assert(TN % 4 == 0, "whole float4 runs per thread");
+};
+
+// Parameter offsets of the transposed copy: per layer WT[in][n_pad] then
+// bias[n_pad]; the head's row holds the W features, then the density logit
+// (column W), then zeros.
 struct TLayout {
     int64_t l1, hid, head, col, out, total;
     __host__ __device__ TLayout(int W, int H)
@@ -29,42 +51,82 @@ struct TLayout {
     }
 };
 
-// acc[o] = b[o] + sum_i x[i] * WT[i][o]; x[i] lives in the thread's column
-// of the shared buffer (sx[i * kThreads + tid]).
-template <int K, int N>
-__device__ __forceinline__ void dense(const float *__restrict__ sx, const float *__restrict__ wt,
-                                      float (&acc)[N], int tid)
+// acc[s][4q + i] = b[n] + sum_k x[k][4 sg + s] WT[k][n] over rows [0, K) of
+// the shared activations, n = 4 (q OG + og) + i; with kDens also
+// dens[s] = b[W] + sum_k x[k][4 sg + s] WT[k][W] (every thread of the
+// sample group forms the same value).
+template <int K, int N, int OG, int TN, bool kDens>
+__device__ __forceinline__ void dense_tile(const float *__restrict__ sx, const float *__restrict__ wt, int og,
+                                           int sg, float (&acc)[4][TN], float (&dens)[4])
 {
-    static_assert(N % 4 == 0, "padded output count");
-    const float4 *b4 = reinterpret_cast<const float4 *>(wt + (int64_t)K * N);
+    const float4 *b4 = reinterpret_cast<const float4 *>(wt + (int64_t)K * N) + og;
 #pragma unroll
-    for (int q = 0; q < N / 4; ++q) {
-        const float4 b = __ldg(b4 + q);
-        acc[4 * q + 0] = b.x; acc[4 * q + 1] = b.y; acc[4 * q + 2] = b.z; acc[4 * q + 3] = b.w;
+    for (int q = 0; q < TN / 4; ++q) {
+        const float4 b = __ldg(b4 + q * OG);
+#pragma unroll
+        for (int s = 0; s < 4; ++s) {
+            acc[s][4 * q + 0] = b.x; acc[s][4 * q + 1] = b.y; acc[s][4 * q + 2] = b.z; acc[s][4 * q + 3] = b.w;
+        }
     }
-#pragma unroll 2
-    for (int i = 0; i < K; ++i) {
-        const float xi = sx[i * kThreads + tid];
-        const float4 *wr = reinterpret_cast<const float4 *>(wt + (int64_t)i * N);
+    if constexpr (kDens) {
+        const float bd = __ldg(wt + (int64_t)K * N + (N - 4));
 #pragma unroll
-        for (int q = 0; q < N / 4; ++q) {
-            const float4 w = __ldg(wr + q);
-            acc[4 * q + 0] = fmaf(w.x, xi, acc[4 * q + 0]);
-            acc[4 * q + 1] = fmaf(w.y, xi, acc[4 * q + 1]);
-            acc[4 * q + 2] = fmaf(w.z, xi, acc[4 * q + 2]);
-            acc[4 * q + 3] = fmaf(w.w, xi, acc[4 * q + 3]);
+        for (int s = 0; s < 4; ++s) dens[s] = bd;
+    }
+    const float4 *xs = reinterpret_cast<const float4 *>(sx) + sg;   // row k at xs[32 k]
+#pragma unroll 2
+    for (int k = 0; k < K; ++k) {
+        const float4 x = xs[32 * k];
+        const float xv[4] = {x.x, x.y, x.z, x.w};
+        const float4 *wr = reinterpret_cast<const float4 *>(wt + (int64_t)k * N) + og;
+#pragma unroll
+        for (int q = 0; q < TN / 4; ++q) {
+            const float4 w = __ldg(wr + q * OG);
+#pragma unroll
+            for (int s = 0; s < 4; ++s) {
+                acc[s][4 * q + 0] = fmaf(w.x, xv[s], acc[s][4 * q + 0]);
+                acc[s][4 * q + 1] = fmaf(w.y, xv[s], acc[s][4 * q + 1]);
+                acc[s][4 * q + 2] = fmaf(w.z, xv[s], acc[s][4 * q + 2]);
+                acc[s][4 * q + 3] = fmaf(w.w, xv[s], acc[s][4 * q + 3]);
+            }
+        }
+        if constexpr (kDens) {
+            const float wd = __ldg(wt + (int64_t)k * N + (N - 4));
+#pragma unroll
+            for (int s = 0; s < 4; ++s) dens[s] = fmaf(wd, xv[s], dens[s]);
+        }
+    }
+}
+
+// Writes this thread's outputs (through a ReLU when kRelu) as rows n of the
+// shared activations, its 4 samples at once.
+template <int OG, int TN, bool kRelu>
+__device__ __forceinline__ void store_tile(float *sx, const float (&acc)[4][TN], int og, int sg)
+{
+    float4 *xs = reinterpret_cast<float4 *>(sx) + sg;
+#pragma unroll
+    for (int q = 0; q < TN / 4; ++q) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int n = 4 * (q * OG + og) + i;
+            float4 v = make_float4(acc[0][4 * q + i], acc[1][4 * q + i], acc[2][4 * q + i], acc[3][4 * q + i]);
+            if (kRelu) {
+                v.x = fmaxf(v.x, 0.f); v.y = fmaxf(v.y, 0.f); v.z = fmaxf(v.z, 0.f); v.w = fmaxf(v.w, 0.f);
+            }
+            xs[32 * n] = v;
         }
     }
 }
 
 // F(x) = [x, sin(2^k pi x), cos(2^k pi x)]_k, three sines then three cosines
-// per frequency; 2^k x is exact in FP32, sincospif reduces it exactly.
+// per frequency, as rows base.. of column tid; 2^k x is exact in FP32,
+// sincospif reduces it exactly.
 template <int L>
 __device__ __forceinline__ void encode(float x0, float x1, float x2, float *sx, int base, int tid)
 {
-    sx[(base + 0) * kThreads + tid] = x0;
-    sx[(base + 1) * kThreads + tid] = x1;
-    sx[(base + 2) * kThreads + tid] = x2;
+    sx[(base + 0) * 128 + tid] = x0;
+    sx[(base + 1) * 128 + tid] = x1;
+    sx[(base + 2) * 128 + tid] = x2;
     const float xs[3] = {x0, x1, x2};
 #pragma unroll
     for (int k = 0; k < L; ++k) {
@@ -72,18 +134,10 @@ __device__ __forceinline__ void encode(float x0, float x1, float x2, float *sx, 
         for (int a = 0; a < 3; ++a) {
             float s, c;
             sincospif(ldexpf(xs[a], k), &s, &c);
-            sx[(base + 3 + 6 * k + a) * kThreads + tid] = s;
-            sx[(base + 6 + 6 * k + a) * kThreads + tid] = c;
+            sx[(base + 3 + 6 * k + a) * 128 + tid] = s;
+            sx[(base + 6 + 6 * k + a) * 128 + tid] = c;
         }
     }
-}
-
-template <int N>
-__device__ __forceinline__ void store_relu(const float (&acc)[N], int n, float *sx, int base, int tid)
-{
-#pragma unroll
-    for (int o = 0; o < N; ++o)
-        if (o < n) sx[(base + o) * kThreads + tid] = fmaxf(acc[o], 0.f);
 }
 
 // Field-local coordinate scale * (o + t d) + offset of sample j, with
@@ -110,76 +164,127 @@ __device__ __forceinline__ float softplus_f(float s) { return s > 20.f ? s : log
 __device__ __forceinline__ float sigmoid_f(float s) { return 1.f / (1.f + expf(-s)); }
 
 template <int W, int H>
-__global__ void __launch_bounds__(kThreads) k_mlp_simt(MlpWeights w, SampleSrc src, BucketBufs b, Counters *ctr,
-                                                       float4 *out)
+__global__ void __launch_bounds__(SimtShape<W>::kThreads, SimtShape<W>::kMinBlocks) k_mlp_simt(MlpWeights w, SampleSrc src, BucketBufs b,
+                                                                    Counters *ctr, float4 *out)
 {
-    extern __shared__ float sx[];   // [(W + kPeD) or kPeX][kThreads]
+    using S = SimtShape<W>;
+    constexpr int OG = S::OG, TN = S::TN;
+    constexpr int NH = round4(1 + W);
+    extern __shared__ float sx[];                       // [kRows][128 samples]
+    uint32_t *s_idx = reinterpret_cast<uint32_t *>(sx + S::kRows * 128);
     const int tid = threadIdx.x;
+    const int og = tid % OG, sg = tid / OG;
     // this width class's tiles
     const uint32_t c0 = ctr->class_tiles[w.cls], n_tiles = ctr->class_tiles[w.cls + 1] - c0;
     const uint32_t t0 = c0 + (uint32_t)((uint64_t)n_tiles * blockIdx.x / gridDim.x);
     const uint32_t t1 = c0 + (uint32_t)((uint64_t)n_tiles * (blockIdx.x + 1) / gridDim.x);
     const TLayout L(W, H);
-    constexpr int NH = round4(1 + W);
+    float acc[4][TN], dens[4];
     for (uint32_t t = t0; t < t1; ++t) {
         const Tile tl = b.tiles[t];
-        const bool valid = (uint32_t)tid < tl.count;
-        const uint32_t idx = valid ? b.sorted[tl.start + tid] : 0u;
-        const float *aff = w.affine + 6 * (int64_t)tl.field;
-        float xl0 = 0.f, xl1 = 0.f, xl2 = 0.f, dx = 0.f, dy = 0.f, dz = 1.f;
-        if (valid) {
-            if (src.mode == 0) {
-                const uint32_t col = idx >> 5;
-                const uint32_t i = (col / (uint32_t)src.R) * 32u + (idx & 31u);
-                const uint32_t ray = src.live ? src.live[i] : i;
-                const uint32_t j = src.recs[idx] & 0xffffu;
-                const float4 o = src.st.orig[ray], d = src.st.dir[ray];
-                dx = d.x; dy = d.y; dz = d.z;
-                if (src.accurate) {
-                    const float4 dl = src.st.dir_lo[ray];
-                    const float th0 = (float)j + 0.5f;
-                    xl0 = local_coord(th0, src.delta, o.x, d.x, dl.x, aff[0], aff[3]);
-                    xl1 = local_coord(th0, src.delta, o.y, d.y, dl.y, aff[1], aff[4]);
-                    xl2 = local_coord(th0, src.delta, o.z, d.z, dl.z, aff[2], aff[5]);
+        // ---- gather and encode: thread tid < 128 takes sample tid of the tile ----
+        float dx = 0.f, dy = 0.f, dz = 1.f;
+        __syncthreads();                                // the previous tile's reads of sx and s_idx are done
+        if (tid < 128) {
+            const bool valid = (uint32_t)tid < tl.count;
+            const uint32_t idx = valid ? b.sorted[tl.start + tid] : 0u;
+            const float *aff = w.affine + 6 * (int64_t)tl.field;
+            float xl0 = 0.f, xl1 = 0.f, xl2 = 0.f;
+            if (valid) {
+                if (src.mode == 0) {
+                    const uint32_t col = idx >> 5;
+                    const uint32_t i = (col / (uint32_t)src.R) * 32u + (idx & 31u);
+                    const uint32_t ray = src.live ? src.live[i] : i;
+                    const uint32_t j = src.recs[idx] & 0xffffu;
+                    const float4 o = src.st.orig[ray], d = src.st.dir[ray];
+                    dx = d.x; dy = d.y; dz = d.z;
+                    if (src.accurate) {
+                        const float4 dl = src.st.dir_lo[ray];
+                        const float th0 = (float)j + 0.5f;
+                        xl0 = local_coord(th0, src.delta, o.x, d.x, dl.x, aff[0], aff[3]);
+                        xl1 = local_coord(th0, src.delta, o.y, d.y, dl.y, aff[1], aff[4]);
+                        xl2 = local_coord(th0, src.delta, o.z, d.z, dl.z, aff[2], aff[5]);
+                    } else {
+                        const float tt = ((float)j + 0.5f) * src.delta;
+                        xl0 = fmaf(aff[0], fmaf(tt, d.x, o.x), aff[3]);
+                        xl1 = fmaf(aff[1], fmaf(tt, d.y, o.y), aff[4]);
+                        xl2 = fmaf(aff[2], fmaf(tt, d.z, o.z), aff[5]);
+                    }
                 } else {
-                    const float tt = ((float)j + 0.5f) * src.delta;
-                    xl0 = fmaf(aff[0], fmaf(tt, d.x, o.x), aff[3]);
-                    xl1 = fmaf(aff[1], fmaf(tt, d.y, o.y), aff[4]);
-                    xl2 = fmaf(aff[2], fmaf(tt, d.z, o.z), aff[5]);
+                    const float px = src.p[3 * (int64_t)idx], py = src.p[3 * (int64_t)idx + 1],
+                                pz = src.p[3 * (int64_t)idx + 2];
+                    dx = src.d[3 * (int64_t)idx]; dy = src.d[3 * (int64_t)idx + 1]; dz = src.d[3 * (int64_t)idx + 2];
+                    xl0 = fmaf(aff[0], px, aff[3]);
+                    xl1 = fmaf(aff[1], py, aff[4]);
+                    xl2 = fmaf(aff[2], pz, aff[5]);
                 }
-            } else {
-                const float px = src.p[3 * (int64_t)idx], py = src.p[3 * (int64_t)idx + 1],
-                            pz = src.p[3 * (int64_t)idx + 2];
-                dx = src.d[3 * (int64_t)idx]; dy = src.d[3 * (int64_t)idx + 1]; dz = src.d[3 * (int64_t)idx + 2];
-                xl0 = fmaf(aff[0], px, aff[3]);
-                xl1 = fmaf(aff[1], py, aff[4]);
-                xl2 = fmaf(aff[2], pz, aff[5]);
             }
+            s_idx[tid] = valid ? idx : 0xffffffffu;
+            encode<10>(xl0, xl1, xl2, sx, 0, tid);
         }
+        __syncthreads();
         const float *wf = w.wt + (int64_t)((int)tl.field - w.field_base) * w.Pt;
 
-        encode<10>(xl0, xl1, xl2, sx, 0, tid);
-        float h[W];
-        dense<kPeX, W>(sx, wf + L.l1, h, tid);
-        store_relu(h, W, sx, 0, tid);
+        // ---- L1, then F(d) beside the hidden features (rows W ..), which
+        // only the colour layer reads ----
+        dense_tile<kPeX, W, OG, TN, false>(sx, wf + L.l1, og, sg, acc, dens);
+        __syncthreads();
+        store_tile<OG, TN, true>(sx, acc, og, sg);
+        if (tid < 128) encode<4>(dx, dy, dz, sx, W, tid);
+        __syncthreads();
 #pragma unroll 1
         for (int k = 0; k < H - 1; ++k) {
-            dense<W, W>(sx, wf + L.hid + (int64_t)k * (W * W + W), h, tid);
-            store_relu(h, W, sx, 0, tid);
+            dense_tile<W, W, OG, TN, false>(sx, wf + L.hid + (int64_t)k * (W * W + W), og, sg, acc, dens);
+            __syncthreads();
+            store_tile<OG, TN, true>(sx, acc, og, sg);
+            __syncthreads();
         }
-        float hd[NH];
-        dense<W, NH>(sx, wf + L.head, hd, tid);
-        const float s = hd[0];
+        // ---- head: features (linear) and the density logit ----
+        dense_tile<W, NH, OG, TN, true>(sx, wf + L.head, og, sg, acc, dens);
+        __syncthreads();
+        store_tile<OG, TN, false>(sx, acc, og, sg);
+        __syncthreads();
+        // ---- colour features g = relu(Wc [feat; F(d)] + bc), in registers ----
+        dense_tile<W + kPeD, W, OG, TN, false>(sx, wf + L.col, og, sg, acc, dens);
+        // ---- rgb = sigmoid(Wo g + bo): this thread's share of the sums, then
+        // the sample group's OG threads (adjacent lanes) add theirs ----
+        const float4 *wo = reinterpret_cast<const float4 *>(wf + L.out);   // [W][4], then bias[4]
+        float z[4][3];
 #pragma unroll
-        for (int o = 0; o < W; ++o) sx[o * kThreads + tid] = hd[1 + o];   // features, no activation
-        encode<4>(dx, dy, dz, sx, W, tid);
-        dense<W + kPeD, W>(sx, wf + L.col, h, tid);
-        store_relu(h, W, sx, 0, tid);
-        float zo[4];
-        dense<W, 4>(sx, wf + L.out, zo, tid);
-        if (valid) {
-            const float sigma = w.sigma_scale * (w.act == ROAM_RELU ? fmaxf(s, 0.f) : softplus_f(s));
-            out[idx] = make_float4(sigma, sigmoid_f(zo[0]), sigmoid_f(zo[1]), sigmoid_f(zo[2]));
+        for (int s = 0; s < 4; ++s) z[s][0] = z[s][1] = z[s][2] = 0.f;
+#pragma unroll
+        for (int q = 0; q < TN / 4; ++q) {
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const float4 wk = __ldg(wo + 4 * (q * OG + og) + i);
+#pragma unroll
+                for (int s = 0; s < 4; ++s) {
+                    const float g = fmaxf(acc[s][4 * q + i], 0.f);
+                    z[s][0] = fmaf(wk.x, g, z[s][0]);
+                    z[s][1] = fmaf(wk.y, g, z[s][1]);
+                    z[s][2] = fmaf(wk.z, g, z[s][2]);
+                }
+            }
+        }
+#pragma unroll
+        for (int m = 1; m < OG; m <<= 1) {
+#pragma unroll
+            for (int s = 0; s < 4; ++s) {
+#pragma unroll
+                for (int c = 0; c < 3; ++c) z[s][c] += __shfl_xor_sync(0xffffffffu, z[s][c], m);
+            }
+        }
+        // thread og < 4 of the group writes sample 4 sg + og
+        const float4 bo = __ldg(wo + W);
+#pragma unroll
+        for (int s = 0; s < 4; ++s) {
+            if (og != s) continue;
+            const uint32_t idx = s_idx[4 * sg + s];
+            if (idx == 0xffffffffu) continue;
+            const float sl = dens[s];
+            const float sigma = w.sigma_scale * (w.act == ROAM_RELU ? fmaxf(sl, 0.f) : softplus_f(sl));
+            out[idx] = make_float4(sigma, sigmoid_f(z[s][0] + bo.x), sigmoid_f(z[s][1] + bo.y),
+                                   sigmoid_f(z[s][2] + bo.z));
         }
     }
 }
@@ -205,11 +310,13 @@ __global__ void k_pack_simt(const float *__restrict__ w32, int n_fields, int W, 
             else if (l == H + 1) { n_out = W; n_in = W + kPeD; base = L.col; n_pad = W; }
             else { n_out = 3; n_in = W; base = L.out; n_pad = 4; }
             const int64_t nw = (int64_t)n_out * n_in;
+            // the head's output 0 (density) goes to column W, its features to 0 .. W-1
+            auto column = [&](int64_t o) { return l == H ? (o == 0 ? (int64_t)W : o - 1) : o; };
             if (q < nw) {
                 const int64_t o = q / n_in, i = q % n_in;
-                dst = base + i * n_pad + o;
+                dst = base + i * n_pad + column(o);
             } else if (q < nw + n_out) {
-                dst = base + (int64_t)n_in * n_pad + (q - nw);
+                dst = base + (int64_t)n_in * n_pad + column(q - nw);
             } else {
                 q -= nw + n_out;
             }
@@ -231,23 +338,25 @@ void launch_pack_simt(const float *w32, int n_fields, int W, int H, int64_t P, f
 
 template <int W, int H>
 static void launch_t(const MlpWeights &w, const SampleSrc &src, const BucketBufs &b, Counters *ctr, float4 *out,
-                     int grid, cudaStream_t s)
+                     int n_sm, cudaStream_t s)
 {
-    const int kmax = (W + kPeD) > kPeX ? (W + kPeD) : kPeX;
-    const size_t sh = (size_t)kmax * kThreads * sizeof(float);
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(k_mlp_simt<W, H>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
-        attr = true;
+    using S = SimtShape<W>;
+    // one wave of resident blocks; each takes a contiguous run of tiles
+    static int per_sm = 0;
+    if (per_sm == 0) {
+        cudaFuncSetAttribute(k_mlp_simt<W, H>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::kSmem);
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_mlp_simt<W, H>, S::kThreads, S::kSmem) !=
+                cudaSuccess || per_sm < 1)
+            per_sm = 1;
     }
-    k_mlp_simt<W, H><<<grid, kThreads, sh, s>>>(w, src, b, ctr, out);
+    k_mlp_simt<W, H><<<n_sm * per_sm, S::kThreads, S::kSmem, s>>>(w, src, b, ctr, out);
 }
 
 void launch_mlp_simt(const MlpWeights &w, const SampleSrc &src, const BucketBufs &b, Counters *ctr, float4 *out,
-                     int grid, cudaStream_t s)
+                     int n_sm, cudaStream_t s)
 {
 #define ROAM_CASE(WW, HH) \
-    if (w.W == WW && w.H == HH) { launch_t<WW, HH>(w, src, b, ctr, out, grid, s); return; }
+    if (w.W == WW && w.H == HH) { launch_t<WW, HH>(w, src, b, ctr, out, n_sm, s); return; }
     ROAM_CASE(32, 1) ROAM_CASE(32, 2) ROAM_CASE(32, 3) ROAM_CASE(32, 4)
     ROAM_CASE(64, 1) ROAM_CASE(64, 2) ROAM_CASE(64, 3) ROAM_CASE(64, 4)
     ROAM_CASE(128, 1) ROAM_CASE(128, 2) ROAM_CASE(128, 3) ROAM_CASE(128, 4)

@@ -485,7 +485,7 @@ roam_status run_mlp(roam_ctx *c, int precision, const SampleSrc &src, const Buck
             launch_mlp_tc(w, precision == ROAM_FP8, src, b, c->ctr, out, c->n_sm, s);
             ROAM_TRY(launched("mlp_tc"));
         } else {
-            launch_mlp_simt(w, src, b, c->ctr, out, grid_blocks(c, 4), s);
+            launch_mlp_simt(w, src, b, c->ctr, out, c->n_sm, s);
             ROAM_TRY(launched("mlp_simt"));
         }
     }
