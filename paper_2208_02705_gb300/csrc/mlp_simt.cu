@@ -28,7 +28,7 @@ struct SimtShape {
     static constexpr int OG = W >= 128 ? 8 : 4;
     static constexpr int TN = W / OG;
     static constexpr int kThreads = 32 * OG;
-    static constexpr int kMinBlocks = W >= 128 ? 2 : 0;                   // W = 128: two blocks per SM
+    static constexpr int kMinBlocks = 2;          // blocks per SM of the read-only-path form (W = 128)
     static constexpr int kRows = (W + kPeD) > kPeX ? (W + kPeD) : kPeX;   // activation rows in shared memory
     static constexpr size_t kSmem = (size_t)kRows * 128 * sizeof(float) + 128 * sizeof(uint32_t);
     static_assert(TN % 4 == 0, "whole float4 runs per thread");
@@ -51,47 +51,76 @@ struct TLayout {
     }
 };
 
+// Weight loads: from the block's shared copy, or through the read-only path.
+template <bool kShared>
+__device__ __forceinline__ float4 ldw4(const float4 *p)
+{
+    if constexpr (kShared) return *p;
+    else return __ldg(p);
+}
+template <bool kShared>
+__device__ __forceinline__ float ldw1(const float *p)
+{
+    if constexpr (kShared) return *p;
+    else return __ldg(p);
+}
+
 // acc[s][4q + i] = b[n] + sum_k x[k][4 sg + s] WT[k][n] over rows [0, K) of
 // the shared activations, n = 4 (q OG + og) + i; with kDens also
 // dens[s] = b[W] + sum_k x[k][4 sg + s] WT[k][W] (every thread of the
 // sample group forms the same value).
-template <int K, int N, int OG, int TN, bool kDens>
+template <int K, int N, int OG, int TN, bool kDens, bool kShared>
 __device__ __forceinline__ void dense_tile(const float *__restrict__ sx, const float *__restrict__ wt, int og,
                                            int sg, float (&acc)[4][TN], float (&dens)[4])
 {
     const float4 *b4 = reinterpret_cast<const float4 *>(wt + (int64_t)K * N) + og;
 #pragma unroll
     for (int q = 0; q < TN / 4; ++q) {
-        const float4 b = __ldg(b4 + q * OG);
+        const float4 b = ldw4<kShared>(b4 + q * OG);
 #pragma unroll
         for (int s = 0; s < 4; ++s) {
             acc[s][4 * q + 0] = b.x; acc[s][4 * q + 1] = b.y; acc[s][4 * q + 2] = b.z; acc[s][4 * q + 3] = b.w;
         }
     }
     if constexpr (kDens) {
-        const float bd = __ldg(wt + (int64_t)K * N + (N - 4));
+        const float bd = ldw1<kShared>(wt + (int64_t)K * N + (N - 4));
 #pragma unroll
         for (int s = 0; s < 4; ++s) dens[s] = bd;
     }
+    // software-pipelined: row k + 1's weights and activations are in flight
+    // while row k's 16 TN FMAs issue
     const float4 *xs = reinterpret_cast<const float4 *>(sx) + sg;   // row k at xs[32 k]
-#pragma unroll 2
+    const float4 *wr = reinterpret_cast<const float4 *>(wt) + og;    // row k at wr[k N / 4]
+    float4 wn[TN / 4], xn = xs[0];
+    float wdn = 0.f;
+#pragma unroll
+    for (int q = 0; q < TN / 4; ++q) wn[q] = ldw4<kShared>(wr + q * OG);
+    if constexpr (kDens) wdn = ldw1<kShared>(wt + (N - 4));
+#pragma unroll 1
     for (int k = 0; k < K; ++k) {
-        const float4 x = xs[32 * k];
-        const float xv[4] = {x.x, x.y, x.z, x.w};
-        const float4 *wr = reinterpret_cast<const float4 *>(wt + (int64_t)k * N) + og;
+        float4 w[TN / 4];
+#pragma unroll
+        for (int q = 0; q < TN / 4; ++q) w[q] = wn[q];
+        const float xv[4] = {xn.x, xn.y, xn.z, xn.w};
+        const float wd = wdn;
+        if (k + 1 < K) {
+            const float4 *wr1 = wr + (int64_t)(k + 1) * (N / 4);
+#pragma unroll
+            for (int q = 0; q < TN / 4; ++q) wn[q] = ldw4<kShared>(wr1 + q * OG);
+            xn = xs[32 * (k + 1)];
+            if constexpr (kDens) wdn = ldw1<kShared>(wt + (int64_t)(k + 1) * N + (N - 4));
+        }
 #pragma unroll
         for (int q = 0; q < TN / 4; ++q) {
-            const float4 w = __ldg(wr + q * OG);
 #pragma unroll
             for (int s = 0; s < 4; ++s) {
-                acc[s][4 * q + 0] = fmaf(w.x, xv[s], acc[s][4 * q + 0]);
-                acc[s][4 * q + 1] = fmaf(w.y, xv[s], acc[s][4 * q + 1]);
-                acc[s][4 * q + 2] = fmaf(w.z, xv[s], acc[s][4 * q + 2]);
-                acc[s][4 * q + 3] = fmaf(w.w, xv[s], acc[s][4 * q + 3]);
+                acc[s][4 * q + 0] = fmaf(w[q].x, xv[s], acc[s][4 * q + 0]);
+                acc[s][4 * q + 1] = fmaf(w[q].y, xv[s], acc[s][4 * q + 1]);
+                acc[s][4 * q + 2] = fmaf(w[q].z, xv[s], acc[s][4 * q + 2]);
+                acc[s][4 * q + 3] = fmaf(w[q].w, xv[s], acc[s][4 * q + 3]);
             }
         }
         if constexpr (kDens) {
-            const float wd = __ldg(wt + (int64_t)k * N + (N - 4));
 #pragma unroll
             for (int s = 0; s < 4; ++s) dens[s] = fmaf(wd, xv[s], dens[s]);
         }
@@ -163,129 +192,206 @@ __device__ __forceinline__ float local_coord(float th0, float delta, float o, fl
 __device__ __forceinline__ float softplus_f(float s) { return s > 20.f ? s : log1pf(expf(s)); }
 __device__ __forceinline__ float sigmoid_f(float s) { return 1.f / (1.f + expf(-s)); }
 
-template <int W, int H>
-__global__ void __launch_bounds__(SimtShape<W>::kThreads, SimtShape<W>::kMinBlocks) k_mlp_simt(MlpWeights w, SampleSrc src, BucketBufs b,
-                                                                    Counters *ctr, float4 *out)
+__device__ __forceinline__ void group_sync(int id, int n) { asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory"); }
+
+// One tile of 128 samples through the whole network by one thread group of
+// SimtShape<W>::kThreads threads (barrier `bar`): sx / s_idx are the group's
+// activations and sample indices, wf the field's transposed weights (in
+// shared memory when kShared).
+template <int W, int H, bool kShared>
+__device__ __forceinline__ void run_tile(const Tile &tl, const MlpWeights &w, const SampleSrc &src,
+                                         const BucketBufs &b, const float *wf, float *sx, uint32_t *s_idx,
+                                         int tid, int bar, float4 *out)
 {
     using S = SimtShape<W>;
-    constexpr int OG = S::OG, TN = S::TN;
+    constexpr int OG = S::OG, TN = S::TN, NT = S::kThreads;
     constexpr int NH = round4(1 + W);
-    extern __shared__ float sx[];                       // [kRows][128 samples]
-    uint32_t *s_idx = reinterpret_cast<uint32_t *>(sx + S::kRows * 128);
-    const int tid = threadIdx.x;
     const int og = tid % OG, sg = tid / OG;
-    // this width class's tiles
-    const uint32_t c0 = ctr->class_tiles[w.cls], n_tiles = ctr->class_tiles[w.cls + 1] - c0;
-    const uint32_t t0 = c0 + (uint32_t)((uint64_t)n_tiles * blockIdx.x / gridDim.x);
-    const uint32_t t1 = c0 + (uint32_t)((uint64_t)n_tiles * (blockIdx.x + 1) / gridDim.x);
     const TLayout L(W, H);
     float acc[4][TN], dens[4];
-    for (uint32_t t = t0; t < t1; ++t) {
-        const Tile tl = b.tiles[t];
-        // ---- gather and encode: thread tid < 128 takes sample tid of the tile ----
-        float dx = 0.f, dy = 0.f, dz = 1.f;
-        __syncthreads();                                // the previous tile's reads of sx and s_idx are done
-        if (tid < 128) {
-            const bool valid = (uint32_t)tid < tl.count;
-            const uint32_t idx = valid ? b.sorted[tl.start + tid] : 0u;
-            const float *aff = w.affine + 6 * (int64_t)tl.field;
-            float xl0 = 0.f, xl1 = 0.f, xl2 = 0.f;
-            if (valid) {
-                if (src.mode == 0) {
-                    const uint32_t col = idx >> 5;
-                    const uint32_t i = (col / (uint32_t)src.R) * 32u + (idx & 31u);
-                    const uint32_t ray = src.live ? src.live[i] : i;
-                    const uint32_t j = src.recs[idx] & 0xffffu;
-                    const float4 o = src.st.orig[ray], d = src.st.dir[ray];
-                    dx = d.x; dy = d.y; dz = d.z;
-                    if (src.accurate) {
-                        const float4 dl = src.st.dir_lo[ray];
-                        const float th0 = (float)j + 0.5f;
-                        xl0 = local_coord(th0, src.delta, o.x, d.x, dl.x, aff[0], aff[3]);
-                        xl1 = local_coord(th0, src.delta, o.y, d.y, dl.y, aff[1], aff[4]);
-                        xl2 = local_coord(th0, src.delta, o.z, d.z, dl.z, aff[2], aff[5]);
-                    } else {
-                        const float tt = ((float)j + 0.5f) * src.delta;
-                        xl0 = fmaf(aff[0], fmaf(tt, d.x, o.x), aff[3]);
-                        xl1 = fmaf(aff[1], fmaf(tt, d.y, o.y), aff[4]);
-                        xl2 = fmaf(aff[2], fmaf(tt, d.z, o.z), aff[5]);
-                    }
+    // ---- gather and encode: thread tid < 128 takes sample tid of the tile ----
+    float dx = 0.f, dy = 0.f, dz = 1.f;
+    group_sync(bar, NT);                                 // the previous tile's reads of sx and s_idx are done
+    if (tid < 128) {
+        const bool valid = (uint32_t)tid < tl.count;
+        const uint32_t idx = valid ? b.sorted[tl.start + tid] : 0u;
+        const float *aff = w.affine + 6 * (int64_t)tl.field;
+        float xl0 = 0.f, xl1 = 0.f, xl2 = 0.f;
+        if (valid) {
+            if (src.mode == 0) {
+                const uint32_t col = idx >> 5;
+                const uint32_t i = (col / (uint32_t)src.R) * 32u + (idx & 31u);
+                const uint32_t ray = src.live ? src.live[i] : i;
+                const uint32_t j = src.recs[idx] & 0xffffu;
+                const float4 o = src.st.orig[ray], d = src.st.dir[ray];
+                dx = d.x; dy = d.y; dz = d.z;
+                if (src.accurate) {
+                    const float4 dl = src.st.dir_lo[ray];
+                    const float th0 = (float)j + 0.5f;
+                    xl0 = local_coord(th0, src.delta, o.x, d.x, dl.x, aff[0], aff[3]);
+                    xl1 = local_coord(th0, src.delta, o.y, d.y, dl.y, aff[1], aff[4]);
+                    xl2 = local_coord(th0, src.delta, o.z, d.z, dl.z, aff[2], aff[5]);
                 } else {
-                    const float px = src.p[3 * (int64_t)idx], py = src.p[3 * (int64_t)idx + 1],
-                                pz = src.p[3 * (int64_t)idx + 2];
-                    dx = src.d[3 * (int64_t)idx]; dy = src.d[3 * (int64_t)idx + 1]; dz = src.d[3 * (int64_t)idx + 2];
-                    xl0 = fmaf(aff[0], px, aff[3]);
-                    xl1 = fmaf(aff[1], py, aff[4]);
-                    xl2 = fmaf(aff[2], pz, aff[5]);
+                    const float tt = ((float)j + 0.5f) * src.delta;
+                    xl0 = fmaf(aff[0], fmaf(tt, d.x, o.x), aff[3]);
+                    xl1 = fmaf(aff[1], fmaf(tt, d.y, o.y), aff[4]);
+                    xl2 = fmaf(aff[2], fmaf(tt, d.z, o.z), aff[5]);
                 }
+            } else {
+                const float px = src.p[3 * (int64_t)idx], py = src.p[3 * (int64_t)idx + 1],
+                            pz = src.p[3 * (int64_t)idx + 2];
+                dx = src.d[3 * (int64_t)idx]; dy = src.d[3 * (int64_t)idx + 1]; dz = src.d[3 * (int64_t)idx + 2];
+                xl0 = fmaf(aff[0], px, aff[3]);
+                xl1 = fmaf(aff[1], py, aff[4]);
+                xl2 = fmaf(aff[2], pz, aff[5]);
             }
-            s_idx[tid] = valid ? idx : 0xffffffffu;
-            encode<10>(xl0, xl1, xl2, sx, 0, tid);
         }
-        __syncthreads();
-        const float *wf = w.wt + (int64_t)((int)tl.field - w.field_base) * w.Pt;
+        s_idx[tid] = valid ? idx : 0xffffffffu;
+        encode<10>(xl0, xl1, xl2, sx, 0, tid);
+    }
+    group_sync(bar, NT);
 
-        // ---- L1, then F(d) beside the hidden features (rows W ..), which
-        // only the colour layer reads ----
-        dense_tile<kPeX, W, OG, TN, false>(sx, wf + L.l1, og, sg, acc, dens);
-        __syncthreads();
-        store_tile<OG, TN, true>(sx, acc, og, sg);
-        if (tid < 128) encode<4>(dx, dy, dz, sx, W, tid);
-        __syncthreads();
+    // ---- L1, then F(d) beside the hidden features (rows W ..), which
+    // only the colour layer reads ----
+    dense_tile<kPeX, W, OG, TN, false, kShared>(sx, wf + L.l1, og, sg, acc, dens);
+    group_sync(bar, NT);
+    store_tile<OG, TN, true>(sx, acc, og, sg);
+    if (tid < 128) encode<4>(dx, dy, dz, sx, W, tid);
+    group_sync(bar, NT);
 #pragma unroll 1
-        for (int k = 0; k < H - 1; ++k) {
-            dense_tile<W, W, OG, TN, false>(sx, wf + L.hid + (int64_t)k * (W * W + W), og, sg, acc, dens);
-            __syncthreads();
-            store_tile<OG, TN, true>(sx, acc, og, sg);
-            __syncthreads();
-        }
-        // ---- head: features (linear) and the density logit ----
-        dense_tile<W, NH, OG, TN, true>(sx, wf + L.head, og, sg, acc, dens);
-        __syncthreads();
-        store_tile<OG, TN, false>(sx, acc, og, sg);
-        __syncthreads();
-        // ---- colour features g = relu(Wc [feat; F(d)] + bc), in registers ----
-        dense_tile<W + kPeD, W, OG, TN, false>(sx, wf + L.col, og, sg, acc, dens);
-        // ---- rgb = sigmoid(Wo g + bo): this thread's share of the sums, then
-        // the sample group's OG threads (adjacent lanes) add theirs ----
-        const float4 *wo = reinterpret_cast<const float4 *>(wf + L.out);   // [W][4], then bias[4]
-        float z[4][3];
+    for (int k = 0; k < H - 1; ++k) {
+        dense_tile<W, W, OG, TN, false, kShared>(sx, wf + L.hid + (int64_t)k * (W * W + W), og, sg, acc, dens);
+        group_sync(bar, NT);
+        store_tile<OG, TN, true>(sx, acc, og, sg);
+        group_sync(bar, NT);
+    }
+    // ---- head: features (linear) and the density logit ----
+    dense_tile<W, NH, OG, TN, true, kShared>(sx, wf + L.head, og, sg, acc, dens);
+    group_sync(bar, NT);
+    store_tile<OG, TN, false>(sx, acc, og, sg);
+    group_sync(bar, NT);
+    // ---- colour features g = relu(Wc [feat; F(d)] + bc), in registers ----
+    dense_tile<W + kPeD, W, OG, TN, false, kShared>(sx, wf + L.col, og, sg, acc, dens);
+    // ---- rgb = sigmoid(Wo g + bo): this thread's share of the sums, then
+    // the sample group's OG threads (adjacent lanes) add theirs ----
+    const float4 *wo = reinterpret_cast<const float4 *>(wf + L.out);   // [W][4], then bias[4]
+    float z[4][3];
 #pragma unroll
-        for (int s = 0; s < 4; ++s) z[s][0] = z[s][1] = z[s][2] = 0.f;
+    for (int s = 0; s < 4; ++s) z[s][0] = z[s][1] = z[s][2] = 0.f;
 #pragma unroll
-        for (int q = 0; q < TN / 4; ++q) {
+    for (int q = 0; q < TN / 4; ++q) {
 #pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                const float4 wk = __ldg(wo + 4 * (q * OG + og) + i);
-#pragma unroll
-                for (int s = 0; s < 4; ++s) {
-                    const float g = fmaxf(acc[s][4 * q + i], 0.f);
-                    z[s][0] = fmaf(wk.x, g, z[s][0]);
-                    z[s][1] = fmaf(wk.y, g, z[s][1]);
-                    z[s][2] = fmaf(wk.z, g, z[s][2]);
-                }
-            }
-        }
-#pragma unroll
-        for (int m = 1; m < OG; m <<= 1) {
+        for (int i = 0; i < 4; ++i) {
+            const float4 wk = ldw4<kShared>(wo + 4 * (q * OG + og) + i);
 #pragma unroll
             for (int s = 0; s < 4; ++s) {
-#pragma unroll
-                for (int c = 0; c < 3; ++c) z[s][c] += __shfl_xor_sync(0xffffffffu, z[s][c], m);
+                const float g = fmaxf(acc[s][4 * q + i], 0.f);
+                z[s][0] = fmaf(wk.x, g, z[s][0]);
+                z[s][1] = fmaf(wk.y, g, z[s][1]);
+                z[s][2] = fmaf(wk.z, g, z[s][2]);
             }
         }
-        // thread og < 4 of the group writes sample 4 sg + og
-        const float4 bo = __ldg(wo + W);
+    }
+#pragma unroll
+    for (int m = 1; m < OG; m <<= 1) {
 #pragma unroll
         for (int s = 0; s < 4; ++s) {
-            if (og != s) continue;
-            const uint32_t idx = s_idx[4 * sg + s];
-            if (idx == 0xffffffffu) continue;
-            const float sl = dens[s];
-            const float sigma = w.sigma_scale * (w.act == ROAM_RELU ? fmaxf(sl, 0.f) : softplus_f(sl));
-            out[idx] = make_float4(sigma, sigmoid_f(z[s][0] + bo.x), sigmoid_f(z[s][1] + bo.y),
-                                   sigmoid_f(z[s][2] + bo.z));
+#pragma unroll
+            for (int c = 0; c < 3; ++c) z[s][c] += __shfl_xor_sync(0xffffffffu, z[s][c], m);
         }
+    }
+    // thread og < 4 of the group writes sample 4 sg + og
+    const float4 bo = ldw4<kShared>(wo + W);
+#pragma unroll
+    for (int s = 0; s < 4; ++s) {
+        if (og != s) continue;
+        const uint32_t idx = s_idx[4 * sg + s];
+        if (idx == 0xffffffffu) continue;
+        const float sl = dens[s];
+        const float sigma = w.sigma_scale * (w.act == ROAM_RELU ? fmaxf(sl, 0.f) : softplus_f(sl));
+        out[idx] = make_float4(sigma, sigmoid_f(z[s][0] + bo.x), sigmoid_f(z[s][1] + bo.y),
+                               sigmoid_f(z[s][2] + bo.z));
+    }
+}
+
+// Tiles of one width class split evenly over the blocks, in order.
+__device__ __forceinline__ void tile_range(const Counters *ctr, int cls, uint32_t &t0, uint32_t &t1)
+{
+    const uint32_t c0 = ctr->class_tiles[cls], n_tiles = ctr->class_tiles[cls + 1] - c0;
+    t0 = c0 + (uint32_t)((uint64_t)n_tiles * blockIdx.x / gridDim.x);
+    t1 = c0 + (uint32_t)((uint64_t)n_tiles * (blockIdx.x + 1) / gridDim.x);
+}
+
+// Weights through the read-only path (W = 128: a field's 378 KB do not fit
+// in shared memory): one thread group per block, several blocks per SM.
+template <int W, int H>
+__global__ void __launch_bounds__(SimtShape<W>::kThreads, SimtShape<W>::kMinBlocks)
+    k_mlp_simt(MlpWeights w, SampleSrc src, BucketBufs b, Counters *ctr, float4 *out)
+{
+    using S = SimtShape<W>;
+    extern __shared__ float sx[];                       // [kRows][128 samples], then 128 sample indices
+    uint32_t *s_idx = reinterpret_cast<uint32_t *>(sx + S::kRows * 128);
+    uint32_t t0, t1;
+    tile_range(ctr, w.cls, t0, t1);
+    for (uint32_t t = t0; t < t1; ++t) {
+        const Tile tl = b.tiles[t];
+        const float *wf = w.wt + (int64_t)((int)tl.field - w.field_base) * w.Pt;
+        run_tile<W, H, false>(tl, w, src, b, wf, sx, s_idx, threadIdx.x, 1, out);
+    }
+}
+
+// Weights in shared memory (W <= 64): one block per SM holds the current
+// field's transposed copy and kGroups thread groups that take the field's
+// tiles in turn, each with its own activations and barrier.  Tiles come
+// sorted by field, so a block reloads the copy only where its run of tiles
+// crosses into the next field.
+template <int W>
+struct SimtSharedShape {
+    static constexpr int kGroups = 2;
+    static constexpr size_t kGroupFloats = (size_t)SimtShape<W>::kRows * 128 + 128;
+    static size_t smem(int64_t Pt) { return ((size_t)Pt + kGroups * kGroupFloats) * sizeof(float); }
+};
+
+template <int W, int H>
+__global__ void __launch_bounds__(SimtSharedShape<W>::kGroups * SimtShape<W>::kThreads, 1)
+    k_mlp_simt_sw(MlpWeights w, SampleSrc src, BucketBufs b, Counters *ctr, float4 *out)
+{
+    using S = SimtShape<W>;
+    using SS = SimtSharedShape<W>;
+    extern __shared__ float4 smem4[];
+    __shared__ uint32_t s_end;
+    float *wsm = reinterpret_cast<float *>(smem4);                      // Pt floats (a multiple of 4)
+    const int grp = threadIdx.x / S::kThreads, tid = threadIdx.x % S::kThreads;
+    float *sx = wsm + w.Pt + grp * SS::kGroupFloats;
+    uint32_t *s_idx = reinterpret_cast<uint32_t *>(sx + S::kRows * 128);
+    uint32_t t0, t1;
+    tile_range(ctr, w.cls, t0, t1);
+    uint32_t t = t0;
+    while (t < t1) {
+        // the run of tiles of field f starting at t: its end is the first
+        // tile of another field (tiles are sorted by field)
+        const uint32_t f = b.tiles[t].field;
+        __syncthreads();                                 // every group is done with the previous copy
+        if (threadIdx.x == 0) s_end = t1;
+        __syncthreads();
+        for (uint32_t base = t + 1; base < t1; base += blockDim.x) {
+            const uint32_t c = base + threadIdx.x;
+            if (c < t1 && b.tiles[c].field != f) atomicMin(&s_end, c);
+            __syncthreads();
+            const bool found = s_end < t1;
+            __syncthreads();
+            if (found) break;
+        }
+        const uint32_t e = s_end;
+        // the field's transposed copy into shared memory
+        const float4 *src4 = reinterpret_cast<const float4 *>(w.wt + (int64_t)((int)f - w.field_base) * w.Pt);
+        for (int64_t i = threadIdx.x; i < w.Pt / 4; i += blockDim.x) smem4[i] = __ldg(src4 + i);
+        __syncthreads();
+        for (uint32_t u = t + (uint32_t)grp; u < e; u += SS::kGroups) {
+            const Tile tl = b.tiles[u];
+            run_tile<W, H, true>(tl, w, src, b, wsm, sx, s_idx, tid, 1 + grp, out);
+        }
+        t = e;
     }
 }
 
@@ -341,15 +447,26 @@ static void launch_t(const MlpWeights &w, const SampleSrc &src, const BucketBufs
                      int n_sm, cudaStream_t s)
 {
     using S = SimtShape<W>;
-    // one wave of resident blocks; each takes a contiguous run of tiles
-    static int per_sm = 0;
-    if (per_sm == 0) {
-        cudaFuncSetAttribute(k_mlp_simt<W, H>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::kSmem);
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_mlp_simt<W, H>, S::kThreads, S::kSmem) !=
-                cudaSuccess || per_sm < 1)
-            per_sm = 1;
+    if constexpr (W <= 64) {
+        // one block per SM, the field's weights in shared memory
+        const size_t sh = SimtSharedShape<W>::smem(w.Pt);
+        static size_t attr = 0;
+        if (attr < sh) {
+            cudaFuncSetAttribute(k_mlp_simt_sw<W, H>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
+            attr = sh;
+        }
+        k_mlp_simt_sw<W, H><<<n_sm, SimtSharedShape<W>::kGroups * S::kThreads, sh, s>>>(w, src, b, ctr, out);
+    } else {
+        // one wave of resident blocks; each takes a contiguous run of tiles
+        static int per_sm = 0;
+        if (per_sm == 0) {
+            cudaFuncSetAttribute(k_mlp_simt<W, H>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::kSmem);
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_mlp_simt<W, H>, S::kThreads, S::kSmem) !=
+                    cudaSuccess || per_sm < 1)
+                per_sm = 1;
+        }
+        k_mlp_simt<W, H><<<n_sm * per_sm, S::kThreads, S::kSmem, s>>>(w, src, b, ctr, out);
     }
-    k_mlp_simt<W, H><<<n_sm * per_sm, S::kThreads, S::kSmem, s>>>(w, src, b, ctr, out);
 }
 
 void launch_mlp_simt(const MlpWeights &w, const SampleSrc &src, const BucketBufs &b, Counters *ctr, float4 *out,
