@@ -88,41 +88,54 @@ __device__ __forceinline__ void dense_tile(const float *__restrict__ sx, const f
         for (int s = 0; s < 4; ++s) dens[s] = bd;
     }
     // software-pipelined: row k + 1's weights and activations are in flight
-    // while row k's 16 TN FMAs issue
+    // while row k's 16 TN FMAs issue (two register sets used in turn, so no
+    // copies between rows)
     const float4 *xs = reinterpret_cast<const float4 *>(sx) + sg;   // row k at xs[32 k]
     const float4 *wr = reinterpret_cast<const float4 *>(wt) + og;    // row k at wr[k N / 4]
-    float4 wn[TN / 4], xn = xs[0];
-    float wdn = 0.f;
+    float4 wa[TN / 4], wb[TN / 4], xa, xb;
+    float da = 0.f, db = 0.f;
+    auto load = [&](int k, float4(&wv)[TN / 4], float4 &xv, float &dv) {
+        const float4 *wk = wr + (int64_t)k * (N / 4);
 #pragma unroll
-    for (int q = 0; q < TN / 4; ++q) wn[q] = ldw4<kShared>(wr + q * OG);
-    if constexpr (kDens) wdn = ldw1<kShared>(wt + (N - 4));
-#pragma unroll 1
-    for (int k = 0; k < K; ++k) {
-        float4 w[TN / 4];
-#pragma unroll
-        for (int q = 0; q < TN / 4; ++q) w[q] = wn[q];
-        const float xv[4] = {xn.x, xn.y, xn.z, xn.w};
-        const float wd = wdn;
-        if (k + 1 < K) {
-            const float4 *wr1 = wr + (int64_t)(k + 1) * (N / 4);
-#pragma unroll
-            for (int q = 0; q < TN / 4; ++q) wn[q] = ldw4<kShared>(wr1 + q * OG);
-            xn = xs[32 * (k + 1)];
-            if constexpr (kDens) wdn = ldw1<kShared>(wt + (int64_t)(k + 1) * N + (N - 4));
-        }
+        for (int q = 0; q < TN / 4; ++q) wv[q] = ldw4<kShared>(wk + q * OG);
+        xv = xs[32 * k];
+        if constexpr (kDens) dv = ldw1<kShared>(wt + (int64_t)k * N + (N - 4));
+    };
+    auto fma_row = [&](const float4(&wv)[TN / 4], const float4 &xv, float dv) {
+        const float x4[4] = {xv.x, xv.y, xv.z, xv.w};
 #pragma unroll
         for (int q = 0; q < TN / 4; ++q) {
 #pragma unroll
             for (int s = 0; s < 4; ++s) {
-                acc[s][4 * q + 0] = fmaf(w[q].x, xv[s], acc[s][4 * q + 0]);
-                acc[s][4 * q + 1] = fmaf(w[q].y, xv[s], acc[s][4 * q + 1]);
-                acc[s][4 * q + 2] = fmaf(w[q].z, xv[s], acc[s][4 * q + 2]);
-                acc[s][4 * q + 3] = fmaf(w[q].w, xv[s], acc[s][4 * q + 3]);
+                acc[s][4 * q + 0] = fmaf(wv[q].x, x4[s], acc[s][4 * q + 0]);
+                acc[s][4 * q + 1] = fmaf(wv[q].y, x4[s], acc[s][4 * q + 1]);
+                acc[s][4 * q + 2] = fmaf(wv[q].z, x4[s], acc[s][4 * q + 2]);
+                acc[s][4 * q + 3] = fmaf(wv[q].w, x4[s], acc[s][4 * q + 3]);
             }
         }
         if constexpr (kDens) {
 #pragma unroll
-            for (int s = 0; s < 4; ++s) dens[s] = fmaf(wd, xv[s], dens[s]);
+            for (int s = 0; s < 4; ++s) dens[s] = fmaf(dv, x4[s], dens[s]);
+        }
+    };
+    if constexpr (kShared) {
+        load(0, wa, xa, da);
+#pragma unroll 1
+        for (int k = 0; k < K; k += 2) {
+            if (k + 1 < K) load(k + 1, wb, xb, db);
+            fma_row(wa, xa, da);
+            if (k + 1 < K) {
+                if (k + 2 < K) load(k + 2, wa, xa, da);
+                fma_row(wb, xb, db);
+            }
+        }
+    } else {
+        // (the read-only-path form runs at 128 registers: no second set; the
+        // compiler schedules two rows at a time)
+#pragma unroll 2
+        for (int k = 0; k < K; ++k) {
+            load(k, wb, xb, db);
+            fma_row(wb, xb, db);
         }
     }
 }
