@@ -65,13 +65,22 @@ __device__ __forceinline__ float ldw1(const float *p)
     else return __ldg(p);
 }
 
+// Accumulators: this thread's output j of sample s is component j % 2 of
+// acc[s][j / 2], so that each packed FMA (__ffma2_rn: two independent
+// single-precision FMAs, each rounded as fmaf) updates two outputs.
+template <int TN>
+__device__ __forceinline__ float acc_get(const float2 (&acc)[4][TN / 2], int s, int j)
+{
+    return (j & 1) ? acc[s][j >> 1].y : acc[s][j >> 1].x;
+}
+
 // acc[s][4q + i] = b[n] + sum_k x[k][4 sg + s] WT[k][n] over rows [0, K) of
 // the shared activations, n = 4 (q OG + og) + i; with kDens also
 // dens[s] = b[W] + sum_k x[k][4 sg + s] WT[k][W] (every thread of the
 // sample group forms the same value).
 template <int K, int N, int OG, int TN, bool kDens, bool kShared>
 __device__ __forceinline__ void dense_tile(const float *__restrict__ sx, const float *__restrict__ wt, int og,
-                                           int sg, float (&acc)[4][TN], float (&dens)[4])
+                                           int sg, float2 (&acc)[4][TN / 2], float (&dens)[4])
 {
     const float4 *b4 = reinterpret_cast<const float4 *>(wt + (int64_t)K * N) + og;
 #pragma unroll
@@ -79,7 +88,8 @@ __device__ __forceinline__ void dense_tile(const float *__restrict__ sx, const f
         const float4 b = ldw4<kShared>(b4 + q * OG);
 #pragma unroll
         for (int s = 0; s < 4; ++s) {
-            acc[s][4 * q + 0] = b.x; acc[s][4 * q + 1] = b.y; acc[s][4 * q + 2] = b.z; acc[s][4 * q + 3] = b.w;
+            acc[s][2 * q] = make_float2(b.x, b.y);
+            acc[s][2 * q + 1] = make_float2(b.z, b.w);
         }
     }
     if constexpr (kDens) {
@@ -88,7 +98,7 @@ __device__ __forceinline__ void dense_tile(const float *__restrict__ sx, const f
         for (int s = 0; s < 4; ++s) dens[s] = bd;
     }
     // software-pipelined: row k + 1's weights and activations are in flight
-    // while row k's 16 TN FMAs issue (two register sets used in turn, so no
+    // while row k's 8 TN packed FMAs issue (two register sets used in turn, so no
     // copies between rows)
     const float4 *xs = reinterpret_cast<const float4 *>(sx) + sg;   // row k at xs[32 k]
     const float4 *wr = reinterpret_cast<const float4 *>(wt) + og;    // row k at wr[k N / 4]
@@ -103,14 +113,16 @@ __device__ __forceinline__ void dense_tile(const float *__restrict__ sx, const f
     };
     auto fma_row = [&](const float4(&wv)[TN / 4], const float4 &xv, float dv) {
         const float x4[4] = {xv.x, xv.y, xv.z, xv.w};
+        float2 xx[4];
+#pragma unroll
+        for (int s = 0; s < 4; ++s) xx[s] = make_float2(x4[s], x4[s]);
 #pragma unroll
         for (int q = 0; q < TN / 4; ++q) {
+            const float2 w01 = make_float2(wv[q].x, wv[q].y), w23 = make_float2(wv[q].z, wv[q].w);
 #pragma unroll
             for (int s = 0; s < 4; ++s) {
-                acc[s][4 * q + 0] = fmaf(wv[q].x, x4[s], acc[s][4 * q + 0]);
-                acc[s][4 * q + 1] = fmaf(wv[q].y, x4[s], acc[s][4 * q + 1]);
-                acc[s][4 * q + 2] = fmaf(wv[q].z, x4[s], acc[s][4 * q + 2]);
-                acc[s][4 * q + 3] = fmaf(wv[q].w, x4[s], acc[s][4 * q + 3]);
+                acc[s][2 * q] = __ffma2_rn(w01, xx[s], acc[s][2 * q]);
+                acc[s][2 * q + 1] = __ffma2_rn(w23, xx[s], acc[s][2 * q + 1]);
             }
         }
         if constexpr (kDens) {
@@ -143,7 +155,7 @@ __device__ __forceinline__ void dense_tile(const float *__restrict__ sx, const f
 // Writes this thread's outputs (through a ReLU when kRelu) as rows n of the
 // shared activations, its 4 samples at once.
 template <int OG, int TN, bool kRelu>
-__device__ __forceinline__ void store_tile(float *sx, const float (&acc)[4][TN], int og, int sg)
+__device__ __forceinline__ void store_tile(float *sx, const float2 (&acc)[4][TN / 2], int og, int sg)
 {
     float4 *xs = reinterpret_cast<float4 *>(sx) + sg;
 #pragma unroll
@@ -151,7 +163,9 @@ __device__ __forceinline__ void store_tile(float *sx, const float (&acc)[4][TN],
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
             const int n = 4 * (q * OG + og) + i;
-            float4 v = make_float4(acc[0][4 * q + i], acc[1][4 * q + i], acc[2][4 * q + i], acc[3][4 * q + i]);
+            const int j = 4 * q + i;
+            float4 v = make_float4(acc_get<TN>(acc, 0, j), acc_get<TN>(acc, 1, j), acc_get<TN>(acc, 2, j),
+                                   acc_get<TN>(acc, 3, j));
             if (kRelu) {
                 v.x = fmaxf(v.x, 0.f); v.y = fmaxf(v.y, 0.f); v.z = fmaxf(v.z, 0.f); v.w = fmaxf(v.w, 0.f);
             }
@@ -221,7 +235,8 @@ __device__ __forceinline__ void run_tile(const Tile &tl, const MlpWeights &w, co
     constexpr int NH = round4(1 + W);
     const int og = tid % OG, sg = tid / OG;
     const TLayout L(W, H);
-    float acc[4][TN], dens[4];
+    float2 acc[4][TN / 2];
+    float dens[4];
     // ---- gather and encode: thread tid < 128 takes sample tid of the tile ----
     float dx = 0.f, dy = 0.f, dz = 1.f;
     group_sync(bar, NT);                                 // the previous tile's reads of sx and s_idx are done
@@ -298,7 +313,7 @@ __device__ __forceinline__ void run_tile(const Tile &tl, const MlpWeights &w, co
             const float4 wk = ldw4<kShared>(wo + 4 * (q * OG + og) + i);
 #pragma unroll
             for (int s = 0; s < 4; ++s) {
-                const float g = fmaxf(acc[s][4 * q + i], 0.f);
+                const float g = fmaxf(acc_get<TN>(acc, s, 4 * q + i), 0.f);
                 z[s][0] = fmaf(wk.x, g, z[s][0]);
                 z[s][1] = fmaf(wk.y, g, z[s][1]);
                 z[s][2] = fmaf(wk.z, g, z[s][2]);
