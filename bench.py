@@ -555,6 +555,8 @@ def main():
     ap.add_argument("--quick", action="store_true",
                     help="headline loop only (no FP32 comparison, accuracy, e2e or CPU baseline): for profilers")
     ap.add_argument("--views", default="both", choices=["both", "equirect", "perspective"])
+    ap.add_argument("--precision", default=None, choices=["bf16", "f32"],
+                    help="with --quick: the arithmetic of the timed loop (default BF16 tensor cores)")
     ap.add_argument("--section", default=None, choices=["train", "distill"],
                     help="run one secondary section alone and print its JSON (for profilers)")
     args = ap.parse_args()
@@ -590,11 +592,14 @@ def main():
     views = [{"equirect": "equirect 1024x512", "perspective": "perspective 1920x1080 fov 90"}[m]
              for m in (["equirect", "perspective"] if args.views == "both" else [args.views])]
 
-    try:
-        r.render(wl.cams, roam.render_opts(wl.delta, wl.n_max, precision=roam.ROAM_BF16))
-        head_prec, dtype = roam.ROAM_BF16, "bf16"
-    except roam.RoamError:
+    if args.quick and args.precision == "f32":
         head_prec, dtype = roam.ROAM_F32, "f32"
+    else:
+        try:
+            r.render(wl.cams, roam.render_opts(wl.delta, wl.n_max, precision=roam.ROAM_BF16))
+            head_prec, dtype = roam.ROAM_BF16, "bf16"
+        except roam.RoamError:
+            head_prec, dtype = roam.ROAM_F32, "f32"
     opts = roam.render_opts(wl.delta, wl.n_max, precision=head_prec)
 
     # ---- headline: K timed steps, event-timed per-kernel record on ----
