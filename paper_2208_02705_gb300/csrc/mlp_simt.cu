@@ -3,14 +3,14 @@
 // a register-tiled FP32 product: a thread owns 4 consecutive samples (a
 // sample group) and TN = W / OG of the layer's outputs, so every weight it
 // loads feeds 4 FMAs and every activation TN.  The layer's input sits in
-// shared memory, feature-major ([k][128 samples]); the weights are read as a
-// transposed FP32 copy ([in][out], output rows padded to 16 bytes) through
-// the read-only path, the OG threads of a sample group reading one
-// contiguous run of each row.  Positional encoding (Eq. 1's F(.)) is
+// shared memory, feature-major ([k][128 samples]); the weights are a
+// transposed FP32 copy ([in][out], output rows padded to 16 bytes), in
+// shared memory (W <= 64) or read through the L1 cache (W = 128), each
+// warp's loads of them uniform.  Positional encoding (Eq. 1's F(.)) is
 // recomputed in the kernel.  The density (the head's extra output) rides in
 // the head layer's loop; the 3-output colour layer is formed from the colour
-// features still in registers, summed over the sample group's threads with
-// warp shuffles.
+// features still in registers, the output groups' shares summed through
+// shared memory.
 #include "internal.cuh"
 
 namespace roam {
@@ -19,10 +19,12 @@ namespace {
 
 __host__ __device__ constexpr int round4(int x) { return (x + 3) & ~3; }
 
-// Thread layout of one tile: 32 sample groups of 4 samples times OG output
-// groups; thread t has sample group t / OG and output group t % OG, and
-// owns outputs n = 4 (q OG + og) + i (q < TN / 4, i < 4): the float4 loads
-// of one weight row by a sample group's threads are contiguous.
+// Thread layout of one tile: OG warps, one per output group, each over the
+// tile's 32 sample groups of 4 samples; lane l of warp og owns samples
+// 4l .. 4l + 3 and outputs n = 4 (q OG + og) + i (q < TN / 4, i < 4).  A
+// warp's weight loads are uniform (one broadcast per float4) and its
+// activation loads one contiguous 512-byte row segment, so each row k costs
+// the shared memory 4 + TN / 4 wavefronts per warp.
 template <int W>
 struct SimtShape {
     static constexpr int OG = W >= 128 ? 8 : 4;
@@ -32,6 +34,7 @@ struct SimtShape {
     static constexpr int kRows = (W + kPeD) > kPeX ? (W + kPeD) : kPeX;   // activation rows in shared memory
     static constexpr size_t kSmem = (size_t)kRows * 128 * sizeof(float) + 128 * sizeof(uint32_t);
     static_assert(TN % 4 == 0, "whole float4 runs per thread");
+    static_assert(3 * OG + 1 <= kRows, "the colour sums fit in the activation buffer");
 };
 
 // Parameter offsets of the transposed copy: per layer WT[in][n_pad] then
@@ -233,7 +236,7 @@ __device__ __forceinline__ void run_tile(const Tile &tl, const MlpWeights &w, co
     using S = SimtShape<W>;
     constexpr int OG = S::OG, TN = S::TN, NT = S::kThreads;
     constexpr int NH = round4(1 + W);
-    const int og = tid % OG, sg = tid / OG;
+    const int og = tid >> 5, sg = tid & 31;
     const TLayout L(W, H);
     float2 acc[4][TN / 2];
     float dens[4];
@@ -300,8 +303,8 @@ __device__ __forceinline__ void run_tile(const Tile &tl, const MlpWeights &w, co
     group_sync(bar, NT);
     // ---- colour features g = relu(Wc [feat; F(d)] + bc), in registers ----
     dense_tile<W + kPeD, W, OG, TN, false, kShared>(sx, wf + L.col, og, sg, acc, dens);
-    // ---- rgb = sigmoid(Wo g + bo): this thread's share of the sums, then
-    // the sample group's OG threads (adjacent lanes) add theirs ----
+    // ---- rgb = sigmoid(Wo g + bo): each warp's share of the sums over its
+    // outputs, then thread t < 128 adds the OG shares of sample t ----
     const float4 *wo = reinterpret_cast<const float4 *>(wf + L.out);   // [W][4], then bias[4]
     float z[4][3];
 #pragma unroll
@@ -320,25 +323,28 @@ __device__ __forceinline__ void run_tile(const Tile &tl, const MlpWeights &w, co
             }
         }
     }
+    // shares and the density (every warp formed it) through the activation
+    // buffer, rows (3 og + c) and 3 OG
+    group_sync(bar, NT);                                 // every warp is done reading the colour input
+    float4 *red = reinterpret_cast<float4 *>(sx) + sg;
 #pragma unroll
-    for (int m = 1; m < OG; m <<= 1) {
+    for (int c = 0; c < 3; ++c) red[32 * (3 * og + c)] = make_float4(z[0][c], z[1][c], z[2][c], z[3][c]);
+    if (og == 0) red[32 * 3 * OG] = make_float4(dens[0], dens[1], dens[2], dens[3]);
+    group_sync(bar, NT);
+    if (tid < 128) {
+        const uint32_t idx = s_idx[tid];
+        if (idx != 0xffffffffu) {
+            const float4 bo = ldw4<kShared>(wo + W);
+            float zc[3] = {bo.x, bo.y, bo.z};
 #pragma unroll
-        for (int s = 0; s < 4; ++s) {
+            for (int g = 0; g < OG; ++g) {
 #pragma unroll
-            for (int c = 0; c < 3; ++c) z[s][c] += __shfl_xor_sync(0xffffffffu, z[s][c], m);
+                for (int c = 0; c < 3; ++c) zc[c] += sx[(3 * g + c) * 128 + tid];
+            }
+            const float sl = sx[3 * OG * 128 + tid];
+            const float sigma = w.sigma_scale * (w.act == ROAM_RELU ? fmaxf(sl, 0.f) : softplus_f(sl));
+            out[idx] = make_float4(sigma, sigmoid_f(zc[0]), sigmoid_f(zc[1]), sigmoid_f(zc[2]));
         }
-    }
-    // thread og < 4 of the group writes sample 4 sg + og
-    const float4 bo = ldw4<kShared>(wo + W);
-#pragma unroll
-    for (int s = 0; s < 4; ++s) {
-        if (og != s) continue;
-        const uint32_t idx = s_idx[4 * sg + s];
-        if (idx == 0xffffffffu) continue;
-        const float sl = dens[s];
-        const float sigma = w.sigma_scale * (w.act == ROAM_RELU ? fmaxf(sl, 0.f) : softplus_f(sl));
-        out[idx] = make_float4(sigma, sigmoid_f(z[s][0] + bo.x), sigmoid_f(z[s][1] + bo.y),
-                               sigmoid_f(z[s][2] + bo.z));
     }
 }
 
