@@ -68,10 +68,20 @@ __device__ __forceinline__ uint32_t ntiles_of(uint32_t h, int tile, int group)
     return (t + (uint32_t)group - 1u) / (uint32_t)group * (uint32_t)group;
 }
 
+// the padding group of field f: its class's own, else the call's
+__device__ __forceinline__ int group_of_field(const ClassBounds &cb, int f, int group)
+{
+    int c = 0;
+#pragma unroll
+    for (int k = 1; k < 4; ++k)
+        if (f >= cb.first[k]) c = k;
+    return cb.group[c] > 0 ? cb.group[c] : group;
+}
+
 // One block: offsets = exclusive scan of hist; tiles of `tile` samples per
 // field, the tile count of every non-empty field rounded up to a multiple of
-// `group` (trailing tiles empty) so that groups of tiles never mix fields;
-// resets hist for the next use.
+// its group (its class's, else `group`; trailing tiles empty) so that groups
+// of tiles never mix fields; resets hist for the next use.
 __global__ void __launch_bounds__(1024) k_scan(uint32_t *hist, int n_fields, int tile, int group, uint32_t *offsets,
                                                uint32_t *cursor, Tile *tiles, uint32_t *tile_off_out, Counters *ctr,
                                                ClassBounds cb)
@@ -86,7 +96,7 @@ __global__ void __launch_bounds__(1024) k_scan(uint32_t *hist, int n_fields, int
         if (f < n_fields) {
             const uint32_t h = hist[f];
             cs += h;
-            ts += ntiles_of(h, tile, group);
+            ts += ntiles_of(h, tile, group_of_field(cb, f, group));
             hit += h > 0;
         }
     }
@@ -124,7 +134,7 @@ __global__ void __launch_bounds__(1024) k_scan(uint32_t *hist, int n_fields, int
             cursor[f] = ea;
             tile_off[f] = eb;
             ea += h;
-            eb += ntiles_of(h, tile, group);
+            eb += ntiles_of(h, tile, group_of_field(cb, f, group));
         }
     }
     if (threadIdx.x == 0) {

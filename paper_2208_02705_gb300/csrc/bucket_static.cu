@@ -90,7 +90,7 @@ extern "C" roam_status roam_bucket_static(const uint16_t *keys, int64_t n, int n
     b.tile_off = nullptr;
     // one tile record per field at most (tile length 2^31 - 1 >= n)
     launch_bucket(nullptr, nullptr, nullptr, (uint32_t)n, 1, 1, keys, n_fields, 0x7fffffff, b, ctr, ds.n_sm * 2, s,
-                  ClassBounds{{0, n_fields, n_fields, n_fields}});
+                  ClassBounds{{0, n_fields, n_fields, n_fields}, {0, 0, 0, 0}});
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return static_fail(ROAM_ERR_CUDA, "roam_bucket_static: kernel launch failed");
     return ROAM_OK;

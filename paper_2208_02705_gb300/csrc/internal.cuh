@@ -82,9 +82,12 @@ struct Counters {
 
 // Width classes of a mixed-width field set: internal field ids are grouped by
 // class; first[c] = first internal field of class c (n_fields past the last
-// class).  A single width is one class: {0, F, F, F}.
+// class).  A single width is one class: {0, F, F, F}.  group[c] > 0: the tile
+// runs of class c's fields are padded to multiples of group[c] tiles (its
+// MLP kernel's tiles in flight) instead of the bucketing call's own group.
 struct ClassBounds {
     int first[4];
+    int group[4];
 };
 
 // Ray state, structure of arrays, indexed by ray id.

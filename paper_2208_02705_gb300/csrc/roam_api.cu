@@ -129,7 +129,7 @@ struct roam_ctx {
     // (a permutation of the caller's ids when the widths are mixed)
     WSet ws[3];
     int n_ws = 0;
-    ClassBounds cb{{0, 0, 0, 0}};
+    ClassBounds cb{{0, 0, 0, 0}, {0, 0, 0, 0}};
     bool permuted = false;
     DBuf<uint16_t> perm, inv, labels_orig, keys_tmp;
     std::vector<float> affine_orig;
@@ -464,15 +464,18 @@ BucketBufs bucket_of(roam_ctx *c)
 }
 
 int tile_of(int precision) { return precision != ROAM_F32 ? tc_tile_samples() : 128; }
-// tiles per field are padded to a multiple of the largest slot count of the
-// classes present (every class's count divides it: 4, 2 or 1), so each
-// class's tile range starts on a group boundary of its own kernel
-int group_of(const roam_ctx *c, int precision)
+// The classes with the tile padding of their MLP kernels: on the tensor cores
+// every field's tile run is a multiple of its own kernel's tiles in flight
+// (4, or 2 at W = 128), so that no group of tiles is empty throughout; the
+// classes come in increasing width and the counts do not grow with width,
+// so each class's range still starts on a group boundary of its kernel.
+// FP32 (SIMT, one tile at a time): no padding.
+ClassBounds classes_of(const roam_ctx *c, int precision)
 {
-    int g = 1;
-    if (precision != ROAM_F32)
-        for (int k = 0; k < c->n_ws; ++k) g = std::max(g, tc_tile_group(c->ws[k].W, precision == ROAM_FP8));
-    return g;
+    ClassBounds cb = c->cb;
+    for (int k = 0; k < 4; ++k)
+        cb.group[k] = (precision != ROAM_F32 && k < c->n_ws) ? tc_tile_group(c->ws[k].W, precision == ROAM_FP8) : 1;
+    return cb;
 }
 
 roam_status run_mlp(roam_ctx *c, int precision, const SampleSrc &src, const BucketBufs &b, float4 *out,
@@ -527,8 +530,8 @@ roam_status run_rounds(roam_ctx *c, const uint32_t *rays, int64_t n_rays, const 
         ROAM_TRY(launched("march"));
         {
             ProfScope ps(c, P_BUCKET, s);
-            launch_bucket_ready(mp.cnt, mp.recs, mp.live_count, mp.n_rays, R, group_of(c, o->precision), c->n_fields,
-                                tile_of(o->precision), b, c->ctr, grid, s, c->cb);
+            launch_bucket_ready(mp.cnt, mp.recs, mp.live_count, mp.n_rays, R, 1, c->n_fields, tile_of(o->precision), b,
+                                c->ctr, grid, s, classes_of(c, o->precision));
         }
         ROAM_TRY(launched("bucket"));
         SampleSrc src{};
@@ -918,7 +921,7 @@ roam_status roam_load_weights(roam_ctx *c, const roam_mlp_desc *desc, const floa
     ++c->gen;
     ROAM_TRY(set_field_order(c, nullptr));
     c->n_ws = 1;
-    c->cb = ClassBounds{{0, c->n_fields, c->n_fields, c->n_fields}};
+    c->cb = ClassBounds{{0, c->n_fields, c->n_fields, c->n_fields}, {0, 0, 0, 0}};
     c->widths.assign(c->n_fields, desc->width);
     ROAM_TRY(load_set(c, 0, desc->width, desc->n_hidden, 0, c->n_fields, weights, on_device != 0));
     c->md = *desc;
@@ -977,7 +980,7 @@ roam_status roam_load_weights_mixed(roam_ctx *c, const roam_mlp_desc *desc, cons
         ROAM_CUDA(cudaMemcpy(c->inv.p, inv.data(), F * sizeof(uint16_t), cudaMemcpyHostToDevice));
     }
     c->n_ws = n_ws;
-    c->cb = ClassBounds{{0, F, F, F}};
+    c->cb = ClassBounds{{0, F, F, F}, {0, 0, 0, 0}};
     for (int k = 0; k < n_ws; ++k) {
         c->cb.first[k] = first[k];
         const int n_k = (k + 1 < n_ws ? first[k + 1] : F) - first[k];
@@ -1389,7 +1392,7 @@ roam_status roam_bucket(roam_ctx *c, const uint16_t *keys, int64_t n, uint32_t *
     b.sorted = perm;
     ROAM_CUDA(cudaMemsetAsync(c->ctr, 0, sizeof(Counters), s));
     launch_bucket(nullptr, nullptr, nullptr, (uint32_t)n, 1, 1, keys, c->n_fields, 128, b, c->ctr, grid_blocks(c, 2), s,
-                  ClassBounds{{0, c->n_fields, c->n_fields, c->n_fields}});
+                  ClassBounds{{0, c->n_fields, c->n_fields, c->n_fields}, {0, 0, 0, 0}});
     c->last = s;
     return launched("bucket");
 }
@@ -1419,8 +1422,8 @@ roam_status roam_mlp_eval(roam_ctx *c, const float *p, const float *d, const uin
         ROAM_TRY(launched("field ids"));
         keys = c->keys_tmp.p;
     }
-    launch_bucket(nullptr, nullptr, nullptr, (uint32_t)n, 1, group_of(c, precision), keys, c->n_fields,
-                  tile_of(precision), b, c->ctr, grid_blocks(c, 2), s, c->cb);
+    launch_bucket(nullptr, nullptr, nullptr, (uint32_t)n, 1, 1, keys, c->n_fields, tile_of(precision), b, c->ctr,
+                  grid_blocks(c, 2), s, classes_of(c, precision));
     ROAM_TRY(launched("bucket"));
     SampleSrc src{};
     src.mode = 1;
