@@ -10,6 +10,21 @@ namespace roam {
 
 constexpr int kPeX = 63;          // 3 + 2*3*10 position features
 constexpr int kPeD = 27;          // 3 + 2*3*4 direction features
+
+// Kernel attributes are per device: a launcher raises a kernel's dynamic
+// shared-memory limit on the current device the first time it needs more
+// (`cached` holds the limit set so far per device ordinal; ordinals past
+// the table are set on every launch).
+constexpr int kMaxDevices = 64;
+inline void raise_smem_limit(const void *kernel, int bytes, int (&cached)[kMaxDevices])
+{
+    int dev = -1;
+    cudaGetDevice(&dev);
+    const bool tracked = dev >= 0 && dev < kMaxDevices;
+    if (tracked && cached[dev] >= bytes) return;
+    if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) == cudaSuccess && tracked)
+        cached[dev] = bytes;
+}
 constexpr int kBrickShift = 3;    // 8^3-voxel bricks for empty-space skipping
 constexpr int kMaxViews = 256;
 

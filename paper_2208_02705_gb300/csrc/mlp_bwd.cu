@@ -462,11 +462,8 @@ void launch_bwd_t(const MlpWeights &w, const SampleSrc &src, const BucketBufs &b
     constexpr int KMAX = KC > kPeX ? KC : kPeX;
     const size_t sh = ((size_t)round4((int)ALayout(W, H).total) + (size_t)kThreads * (KMAX + 1) +
                        (size_t)kThreads * (W + 2)) * sizeof(float);
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(k_mlp_bwd_simt<W, H>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
-        attr = true;
-    }
+    static int smem_set[kMaxDevices] = {};
+    raise_smem_limit((const void *)k_mlp_bwd_simt<W, H>, (int)sh, smem_set);
     k_mlp_bwd_simt<W, H><<<grid, kThreads, sh, s>>>(w, src, b, ctr, gsr, grad);
 }
 

@@ -597,11 +597,8 @@ void launch_bt(const MlpWeights &w, const SampleSrc &src, const BucketBufs &b, C
                float *grad, int n_sm, cudaStream_t s)
 {
     const int smem = 1024 + BwShape<W, H>::kSmem;
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(k_mlp_bwd_tc<W, H>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        attr = true;
-    }
+    static int smem_set[kMaxDevices] = {};
+    raise_smem_limit((const void *)k_mlp_bwd_tc<W, H>, smem, smem_set);
     k_mlp_bwd_tc<W, H><<<n_sm, 128, smem, s>>>(w.wimg, w.img_bytes, w.affine, w.sigma_scale, w.act, w.P, src, b, ctr,
                                                 gsr, grad);
 }

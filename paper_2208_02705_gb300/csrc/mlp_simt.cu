@@ -484,20 +484,22 @@ static void launch_t(const MlpWeights &w, const SampleSrc &src, const BucketBufs
     if constexpr (W <= 64) {
         // one block per SM, the field's weights in shared memory
         const size_t sh = SimtSharedShape<W>::smem(w.Pt);
-        static size_t attr = 0;
-        if (attr < sh) {
-            cudaFuncSetAttribute(k_mlp_simt_sw<W, H>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
-            attr = sh;
-        }
+        static int smem_set[kMaxDevices] = {};
+        raise_smem_limit((const void *)k_mlp_simt_sw<W, H>, (int)sh, smem_set);
         k_mlp_simt_sw<W, H><<<n_sm, SimtSharedShape<W>::kGroups * S::kThreads, sh, s>>>(w, src, b, ctr, out);
     } else {
         // one wave of resident blocks; each takes a contiguous run of tiles
-        static int per_sm = 0;
+        static int smem_set[kMaxDevices] = {};
+        raise_smem_limit((const void *)k_mlp_simt<W, H>, (int)S::kSmem, smem_set);
+        static int per_sm_dev[kMaxDevices] = {};
+        int dev = -1;
+        cudaGetDevice(&dev);
+        int per_sm = dev >= 0 && dev < kMaxDevices ? per_sm_dev[dev] : 0;
         if (per_sm == 0) {
-            cudaFuncSetAttribute(k_mlp_simt<W, H>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::kSmem);
             if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_mlp_simt<W, H>, S::kThreads, S::kSmem) !=
                     cudaSuccess || per_sm < 1)
                 per_sm = 1;
+            if (dev >= 0 && dev < kMaxDevices) per_sm_dev[dev] = per_sm;
         }
         k_mlp_simt<W, H><<<n_sm * per_sm, S::kThreads, S::kSmem, s>>>(w, src, b, ctr, out);
     }

@@ -554,11 +554,8 @@ void launch_t(const MlpWeights &w, const SampleSrc &src, const BucketBufs &b, Co
 {
     constexpr int kSlots = TcShape<W, H, F8>::kSlots;
     const int smem = tc_smem_bytes<W, H, F8>();
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(k_mlp_tc<W, H, F8>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        attr = true;
-    }
+    static int smem_set[kMaxDevices] = {};
+    raise_smem_limit((const void *)k_mlp_tc<W, H, F8>, smem, smem_set);
     const void *img = F8 ? w.wimg8 : w.wimg;
     const int64_t ib = F8 ? w.img8_bytes : w.img_bytes;
     k_mlp_tc<W, H, F8><<<n_sm, kSlots * 128, smem, s>>>(img, ib, w.field_base, w.cls, w.affine, w.sigma_scale, w.act,
