@@ -40,7 +40,7 @@ typedef enum {
     ROAM_ERR_STATE = -4,       /* call out of order (e.g. render before load) */
     ROAM_ERR_TIMEOUT = -5,     /* a device-side wait hit its iteration limit */
     ROAM_ERR_DATA = -6,        /* inconsistent data found on the device */
-    ROAM_ERR_UNSUPPORTED = -7  /* valid request this build does not provide */
+    ROAM_ERR_UNSUPPORTED = -7  /* valid request with no kernel for it (shape or precision) */
 } roam_status;
 
 enum { ROAM_F32 = 0, ROAM_BF16 = 1, ROAM_FP8 = 2, ROAM_TF32 = 3 };   /* arithmetic (TF32: the teacher only) */
