@@ -70,6 +70,12 @@ def lib():
         L.orc_render.restype = I
         L.orc_march_rays.argtypes = [i32p, f64p, D, i32p, f64p, I, u32p, I64, D, I, i32p, i32p, i32p, i32p]
         L.orc_march_rays.restype = I
+        L.orc_render_records.argtypes = [i32p, f64p, D, i32p, f32p, f32p, I, I, I, D, I, i32p, I, f64p, I, u32p,
+                                         I64, D, D, f64p, i32p, i32p, i32p, I, f64p, f64p, f64p, i32p, f64p]
+        L.orc_render_records.restype = I
+        L.orc_sample_tie_distance.argtypes = [i32p, f64p, D, i32p, f64p, I, u32p, I64, ctypes.POINTER(ctypes.c_int64),
+                                              i32p, D, f64p]
+        L.orc_sample_tie_distance.restype = I
         L.orc_loss_grad.argtypes = [i32p, f64p, D, i32p, f32p, f32p, I, I, I, I, D, f64p, I, u32p, I64,
                                     D, I, D, f64p, f32p, D, f64p, u64p, f64p]
         L.orc_loss_grad.restype = D
@@ -244,6 +250,59 @@ def render(grid: Grid, weights, affine, W: int, H: int, sigma_scale: float, cams
     if rc:
         raise ValueError("orc_render rejected its arguments")
     return out
+
+
+def render_records(grid: Grid, weights, affine, W: int, H: int, sigma_scale: float, cams16,
+                   rays: Optional[np.ndarray], counts, js, fields, delta: float, t_stop: float = 1e-4,
+                   bg=(0.0, 0.0, 0.0), act: int = 0, quant: int = 0, widths=None):
+    """Eq. 4-5 over a GIVEN kept-sample set per ray (counts [n], js and fields
+    [n, stride]) instead of the oracle's own march: the plain composite of
+    another march's records.  Returns a dict like render() (rgb, depth,
+    opacity, n_used, margin)."""
+    cams = cams_f32(cams16)
+    w = np.ascontiguousarray(weights, dtype=np.float32)
+    aff = np.ascontiguousarray(affine, dtype=np.float32)
+    wd = np.ascontiguousarray(widths, dtype=np.int32) if widths is not None else None
+    n_fields = int(aff.shape[0])
+    cnt = np.ascontiguousarray(counts, dtype=np.int32)
+    n_rays = int(cnt.shape[0])
+    jj = np.ascontiguousarray(js, dtype=np.int32).reshape(n_rays, -1)
+    ff = np.ascontiguousarray(fields, dtype=np.int32).reshape(n_rays, -1)
+    stride = int(jj.shape[1])
+    r = np.ascontiguousarray(rays, dtype=np.uint32) if rays is not None else None
+    bgv = np.array([f32(b) for b in bg], dtype=np.float64)
+    out = dict(rgb=np.zeros((n_rays, 3)), depth=np.zeros(n_rays), opacity=np.zeros(n_rays),
+               n_used=np.zeros(n_rays, np.int32), margin=np.zeros(n_rays))
+    if n_rays == 0:
+        return out
+    rc = lib().orc_render_records(*grid.args(), _p(w, ctypes.c_float), _p(aff, ctypes.c_float), W, H, act,
+                                  f32(sigma_scale), int(quant), _p(wd, ctypes.c_int32), n_fields,
+                                  _p(cams, ctypes.c_double), int(cams.shape[0]), _p(r, ctypes.c_uint32), n_rays,
+                                  f32(delta), f32(t_stop), _p(bgv, ctypes.c_double), _p(cnt, ctypes.c_int32),
+                                  _p(jj, ctypes.c_int32), _p(ff, ctypes.c_int32), stride,
+                                  _p(out["rgb"], ctypes.c_double), _p(out["depth"], ctypes.c_double),
+                                  _p(out["opacity"], ctypes.c_double), _p(out["n_used"], ctypes.c_int32),
+                                  _p(out["margin"], ctypes.c_double))
+    if rc:
+        raise ValueError("orc_render_records rejected its arguments")
+    return out
+
+
+def sample_tie_distance(grid: Grid, cams16, rays: Optional[np.ndarray], q_ray, q_j, delta: float) -> np.ndarray:
+    """Distance (voxel units) from sample q_j[k] of ray q_ray[k] to the nearest
+    face of its voxel whose two sides differ; inf if none does."""
+    cams = cams_f32(cams16)
+    qr = np.ascontiguousarray(q_ray, dtype=np.int64)
+    qj = np.ascontiguousarray(q_j, dtype=np.int32)
+    r = np.ascontiguousarray(rays, dtype=np.uint32) if rays is not None else None
+    dist = np.zeros(qr.size)
+    rc = lib().orc_sample_tie_distance(*grid.args(), _p(cams, ctypes.c_double), int(cams.shape[0]),
+                                       _p(r, ctypes.c_uint32), int(qr.size),
+                                       qr.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), _p(qj, ctypes.c_int32),
+                                       f32(delta), _p(dist, ctypes.c_double))
+    if rc:
+        raise ValueError("orc_sample_tie_distance rejected its arguments")
+    return dist
 
 
 def loss_grad(grid: Grid, weights, affine, W: int, H: int, sigma_scale: float, cams16, rays,

@@ -596,13 +596,13 @@ static void ray_of(const orc_scene *S, const uint32_t *rays, int64_t r, const in
     orc_ray(cam, u + 0.5, v + 0.5, o, d);
 }
 
-/* per-ray forward; fills per-sample caches if given (sized n_max) */
-static int render_ray(const orc_scene *S, const double *o, const double *d, double *out,
-                      int *n_kept, int *ties, double *margin, int32_t *js, int32_t *fields,
-                      orc_cache *caches, double *w_buf, double *T_end)
+/* The MLP at every given kept sample (j_k, field_k) of the ray o + t d,
+ * t_k = (j_k + 1/2) delta, then Eq. 4-5 over them in ray order; fills
+ * per-sample caches if given (sized n).  Returns the number composited. */
+static int shade_ray(const orc_scene *S, const double *o, const double *d, int n, const int32_t *js,
+                     const int32_t *fields, double *out, double *margin, orc_cache *caches, double *w_buf,
+                     double *T_end)
 {
-    int nt = 0;
-    int n = march_ray(&S->g, o, d, S->delta, S->n_max, js, fields, &nt);
     double sig[1024], rgb[3 * 1024], tt[1024];
     orc_cache local;
     for (int k = 0; k < n; ++k) {
@@ -620,7 +620,17 @@ static int render_ray(const orc_scene *S, const double *o, const double *d, doub
         rgb[3 * k + 0] = c->rgb[0]; rgb[3 * k + 1] = c->rgb[1]; rgb[3 * k + 2] = c->rgb[2];
         tt[k] = t;
     }
-    int used = composite(n, sig, rgb, tt, S->delta, S->t_stop, S->bg, out, margin, w_buf, T_end);
+    return composite(n, sig, rgb, tt, S->delta, S->t_stop, S->bg, out, margin, w_buf, T_end);
+}
+
+/* per-ray forward: the march, then shade_ray over its kept samples */
+static int render_ray(const orc_scene *S, const double *o, const double *d, double *out,
+                      int *n_kept, int *ties, double *margin, int32_t *js, int32_t *fields,
+                      orc_cache *caches, double *w_buf, double *T_end)
+{
+    int nt = 0;
+    int n = march_ray(&S->g, o, d, S->delta, S->n_max, js, fields, &nt);
+    int used = shade_ray(S, o, d, n, js, fields, out, margin, caches, w_buf, T_end);
     if (n_kept) *n_kept = n;
     if (ties) *ties = nt;
     return used;
@@ -648,6 +658,35 @@ static int setup_scene(orc_scene *S, const int32_t *dims, const double *origin, 
     return 0;
 }
 
+/* Per-field weight offsets when every field has its own width (widths !=
+ * NULL: field f's parameters follow field f-1's).  0, or -1 on a bad width
+ * or a failed allocation. */
+static int scene_widths(orc_scene *S, const int32_t *widths, int n_fields, int64_t **woff_out)
+{
+    *woff_out = NULL;
+    if (!widths) return 0;
+    int64_t *woff = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n_fields > 0 ? n_fields : 1));
+    if (!woff) return -1;
+    int64_t o = 0;
+    for (int f = 0; f < n_fields; ++f) {
+        if (widths[f] < 1 || widths[f] > 256) { free(woff); return -1; }
+        woff[f] = o;
+        o += orc_param_count(widths[f], S->A.H);
+    }
+    S->widths = widths;
+    S->woff = woff;
+    *woff_out = woff;
+    return 0;
+}
+
+static int view_starts(const double *cams, int n_views, int64_t *starts)
+{
+    if (n_views > 256) return -1;
+    starts[0] = 0;
+    for (int v = 0; v < n_views; ++v) starts[v + 1] = starts[v] + (int64_t)cams[16 * v + 1] * (int64_t)cams[16 * v + 2];
+    return 0;
+}
+
 /* Renders rays (view, pixel) pairs, or every pixel of every view in order
  * when rays == NULL.  Per ray: rgb[3], depth, opacity, number of kept
  * samples, number composited before termination, near-tie count of the
@@ -662,26 +701,11 @@ int orc_render(const int32_t *dims, const double *origin, double vox, const int3
                int32_t *n_used, int32_t *ties, double *margin)
 {
     orc_scene S;
+    int64_t *woff = NULL, starts[257];
     if (setup_scene(&S, dims, origin, vox, label, weights, affine, W, H, act, sigma_scale, quant, cams,
-                    n_views, delta, n_max, t_stop, bg))
+                    n_views, delta, n_max, t_stop, bg) ||
+        view_starts(cams, n_views, starts) || scene_widths(&S, widths, n_fields, &woff))
         return -1;
-    int64_t *woff = NULL;
-    if (widths) {
-        woff = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n_fields > 0 ? n_fields : 1));
-        if (!woff) return -1;
-        int64_t o = 0;
-        for (int f = 0; f < n_fields; ++f) {
-            if (widths[f] < 1 || widths[f] > 256) { free(woff); return -1; }
-            woff[f] = o;
-            o += orc_param_count(widths[f], H);
-        }
-        S.widths = widths;
-        S.woff = woff;
-    }
-    int64_t starts[257];
-    if (n_views > 256) return -1;
-    starts[0] = 0;
-    for (int v = 0; v < n_views; ++v) starts[v + 1] = starts[v] + (int64_t)cams[16 * v + 1] * (int64_t)cams[16 * v + 2];
 #pragma omp parallel for schedule(dynamic, 64)
     for (int64_t r = 0; r < n_rays; ++r) {
         double o[3], d[3], out[5], mg = INFINITY;
@@ -698,6 +722,97 @@ int orc_render(const int32_t *dims, const double *origin, double vox, const int3
         if (margin) margin[r] = mg;
     }
     free(woff);
+    return 0;
+}
+
+/* Eq. 4-5 over a GIVEN set of kept samples per ray instead of the oracle's
+ * own march: ray r composites samples (rec_j[r][k], rec_field[r][k]) for
+ * k < rec_count[r] (rows rec_stride apart), each through its field's MLP at
+ * t = (j + 1/2) delta, with early termination as orc_render.  This is the
+ * plain composite of another march's sample records (a renderer's, say),
+ * so that its colours can be checked on its own sample set where its march
+ * legitimately differs from the oracle's at near-ties.  Outputs as
+ * orc_render (no kept count or tie count).  Returns 0, or -1 on bad sizes,
+ * a negative sample index or a field id outside [0, n_fields). */
+int orc_render_records(const int32_t *dims, const double *origin, double vox, const int32_t *label,
+                       const float *weights, const float *affine, int W, int H, int act, double sigma_scale,
+                       int quant, const int32_t *widths, int n_fields, const double *cams, int n_views,
+                       const uint32_t *rays, int64_t n_rays, double delta, double t_stop, const double *bg,
+                       const int32_t *rec_count, const int32_t *rec_j, const int32_t *rec_field, int rec_stride,
+                       double *rgb, double *depth, double *opacity, int32_t *n_used, double *margin)
+{
+    orc_scene S;
+    int64_t *woff = NULL, starts[257];
+    if (rec_stride < 1 || rec_stride > 1024) return -1;
+    for (int64_t r = 0; r < n_rays; ++r) {
+        if (rec_count[r] < 0 || rec_count[r] > rec_stride) return -1;
+        for (int k = 0; k < rec_count[r]; ++k)
+            if (rec_j[r * rec_stride + k] < 0 || rec_field[r * rec_stride + k] < 0 ||
+                rec_field[r * rec_stride + k] >= n_fields)
+                return -1;
+    }
+    if (setup_scene(&S, dims, origin, vox, label, weights, affine, W, H, act, sigma_scale, quant, cams,
+                    n_views, delta, rec_stride, t_stop, bg) ||
+        view_starts(cams, n_views, starts) || scene_widths(&S, widths, n_fields, &woff))
+        return -1;
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t r = 0; r < n_rays; ++r) {
+        double o[3], d[3], out[5], mg = INFINITY;
+        ray_of(&S, rays, r, starts, o, d);
+        int used = shade_ray(&S, o, d, rec_count[r], rec_j + r * rec_stride, rec_field + r * rec_stride, out, &mg,
+                             NULL, NULL, NULL);
+        rgb[3 * r + 0] = out[0]; rgb[3 * r + 1] = out[1]; rgb[3 * r + 2] = out[2];
+        if (depth) depth[r] = out[3];
+        if (opacity) opacity[r] = out[4];
+        if (n_used) n_used[r] = used;
+        if (margin) margin[r] = mg;
+    }
+    free(woff);
+    return 0;
+}
+
+/* Near-tie certificate of single samples: for query q, sample q_j[q] of ray
+ * q_ray[q] (an index into rays, or a global pixel index when rays == NULL),
+ * the distance in voxel units from its point o + (j + 1/2) delta d to the
+ * nearest face of its voxel whose two sides differ in state (empty, outside
+ * the grid, or another field); INFINITY when no face of the voxel does.  A
+ * sample nearer such a face than the rounding error of another
+ * implementation's coordinates may legitimately land on either side.
+ * Returns 0, or -1 on bad sizes. */
+int orc_sample_tie_distance(const int32_t *dims, const double *origin, double vox, const int32_t *label,
+                            const double *cams, int n_views, const uint32_t *rays, int64_t n_queries,
+                            const int64_t *q_ray, const int32_t *q_j, double delta, double *dist)
+{
+    orc_scene S;
+    static const float dummy_w[1] = {0};
+    static const double zero_bg[3] = {0, 0, 0};
+    int64_t starts[257];
+    if (setup_scene(&S, dims, origin, vox, label, dummy_w, dummy_w, 1, 1, 0, 1.0, 0, cams, n_views,
+                    delta, 1, 1e-4, zero_bg) ||
+        view_starts(cams, n_views, starts))
+        return -1;
+    for (int64_t q = 0; q < n_queries; ++q) {
+        double o[3], d[3], gc[3];
+        int64_t iv[3];
+        ray_of(&S, rays, q_ray[q], starts, o, d);
+        double t = ((double)q_j[q] + 0.5) * delta;
+        for (int a = 0; a < 3; ++a) {
+            gc[a] = (o[a] + t * d[a] - S.g.origin[a]) / S.g.vox;
+            iv[a] = (int64_t)floor(gc[a]);
+        }
+        int32_t s = state_at(&S.g, iv);
+        double best = INFINITY;
+        for (int a = 0; a < 3; ++a)
+            for (int step = -1; step <= 1; step += 2) {
+                int64_t nb[3] = {iv[0], iv[1], iv[2]};
+                nb[a] += step;
+                if (state_at(&S.g, nb) == s) continue;
+                double fr = gc[a] - (double)iv[a];
+                double dd = step < 0 ? fr : 1.0 - fr;
+                if (dd < best) best = dd;
+            }
+        dist[q] = best;
+    }
     return 0;
 }
 

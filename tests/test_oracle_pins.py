@@ -552,6 +552,111 @@ def test_render_slab_transmittance_matches_exp_sigma_l():
     assert errs[-1] < 0.01 and errs[-1] < errs[0]
 
 
+def _axis_camera(o):
+    """A 3x3 perspective camera whose central pixel looks along world +x."""
+    R = np.array([[0.0, 0.0, 1.0], [0.0, 1.0, 0.0], [-1.0, 0.0, 0.0]])
+    return np.concatenate([[1, 3, 3, math.pi / 2], R.reshape(9), o])[None, :]
+
+
+def test_render_records_geometric_series_and_routing():
+    """Given kept-sample lists: with sigma * delta = ln 2 every sample halves
+    the transmittance, so the weights are 1/2, 1/4, 1/8, 1/16 whatever the
+    sample indices; colours route to each record's own field and depths to
+    its own t = (j + 1/2) delta."""
+    G = 32
+    occ = np.zeros((G, G, G), dtype=bool)
+    occ[:, :, 8:20] = True                         # any grid: the records are given
+    g = _grid(occ, 0.1)
+    W, H = 8, 2
+    b0, b1 = np.array([0.4, -0.2, 1.0]), np.array([-1.0, 0.5, 0.25])
+    w = np.stack([_const_weights(W, H, 0.0, b0), _const_weights(W, H, 0.0, b1)])
+    aff = np.tile(np.array([1, 1, 1, 0, 0, 0], dtype=np.float32), (2, 1))
+    delta, sigma_scale = 0.25, 4.0                 # 4 * softplus(0) * 0.25 = ln 2
+    cam = _axis_camera([0.35, 1.05, 1.05])
+    rays = np.array([[0, 4], [0, 4], [0, 4]], dtype=np.uint32)       # the central pixel, three record sets
+    js = np.array([[3, 10, 11, 40], [0, 1, 2, 3], [5, 0, 0, 0]])
+    fs = np.array([[0, 1, 1, 0], [1, 1, 1, 1], [1, 0, 0, 0]])
+    cnt = np.array([4, 4, 0])
+    bg = (0.1, 0.2, 0.3)
+    r = O.render_records(g, w, aff, W, H, sigma_scale, cam, rays, cnt, js, fs, delta, t_stop=1e-4, bg=bg)
+    c0, c1 = 1 / (1 + np.exp(-b0.astype(np.float32).astype(np.float64))), \
+        1 / (1 + np.exp(-b1.astype(np.float32).astype(np.float64)))
+    wts = np.array([1 / 2, 1 / 4, 1 / 8, 1 / 16])
+    bgv = np.array(bg, dtype=np.float32).astype(np.float64)
+    assert np.allclose(r["rgb"][0], (wts[0] + wts[3]) * c0 + (wts[1] + wts[2]) * c1 + bgv / 16, atol=1e-14)
+    assert np.allclose(r["rgb"][1], (15 / 16) * c1 + bgv / 16, atol=1e-14)
+    assert abs(r["depth"][0] - float((wts * (js[0] + 0.5) * delta).sum())) < 1e-13
+    assert abs(r["opacity"][0] - 15 / 16) < 1e-14 and r["n_used"][0] == 4
+    assert np.allclose(r["rgb"][2], bgv, atol=0) and r["opacity"][2] == 0 and r["depth"][2] == 0
+    # termination: t_stop = 0.1 stops after the fourth halving (T = 1/16 < 0.1)
+    js5 = np.array([[0, 1, 2, 3, 4, 5]])
+    r2 = O.render_records(g, w[:1], aff[:1], W, H, sigma_scale, cam, rays[:1], [6], js5, np.zeros((1, 6)), delta,
+                          t_stop=0.1)
+    assert r2["n_used"][0] == 4 and abs(r2["opacity"][0] - 15 / 16) < 1e-14
+    with pytest.raises(ValueError):        # a field id outside the partition
+        O.render_records(g, w, aff, W, H, sigma_scale, cam, rays[:1], [1], [[0]], [[2]], delta)
+
+
+def test_render_records_of_the_oracle_march_is_the_render(room32, room32_grid):
+    """Fed the oracle's own march, the records render is the render."""
+    cams = F.camera_array(room32.cams)
+    rng = np.random.default_rng(8)
+    rays = np.stack([np.zeros(300, np.int64), rng.integers(0, 128 * 64, 300)], 1).astype(np.uint32)
+    ref = O.render(room32_grid, room32.weights, room32.affine, room32.W, room32.H, room32.sigma_scale, cams, rays,
+                   room32.delta, room32.n_max)
+    cnt, js, fs, _ = O.march_rays(room32_grid, cams, rays, room32.delta, room32.n_max)
+    got = O.render_records(room32_grid, room32.weights, room32.affine, room32.W, room32.H, room32.sigma_scale, cams,
+                           rays, cnt, js, fs, room32.delta)
+    for k in ("rgb", "depth", "opacity", "n_used"):
+        assert np.array_equal(got[k], ref[k]), k
+    assert cnt.sum() > 1000
+
+
+def test_sample_tie_distance_closed_form():
+    """Distance to the nearest face whose two sides differ, along +x through
+    one occupied voxel x in [1.0, 1.1) (y, z at its centre), and a field
+    boundary between two occupied voxels."""
+    G, vox = 32, 0.1
+    occ = np.zeros((G, G, G), dtype=bool)
+    occ[10, 10, 10] = True
+    g = _grid(occ, vox)
+    x0 = 0.3125
+    cam = _axis_camera([x0, 1.05, 1.05])
+    delta = 0.0078125
+    vf = O.f32(vox)
+    y_fr = O.f32(1.05) / vf - 10                     # the y and z faces of the occupied voxel
+    js = np.arange(0, 130)
+    dist = O.sample_tie_distance(g, cam, np.array([[0, 4]], np.uint32), np.zeros(js.size, np.int64), js, delta)
+    for j, dd in zip(js, dist):
+        xv = (x0 + (j + 0.5) * delta) / vf
+        ix = math.floor(xv)
+        fr = xv - ix
+        if ix == 10:
+            expect = min(fr, 1 - fr, y_fr, 1 - y_fr)
+        elif ix == 9:
+            expect = 1 - fr
+        elif ix == 11:
+            expect = fr
+        else:
+            expect = math.inf
+        assert dd == expect or abs(dd - expect) < 1e-12, (j, dd, expect)
+    # two occupied voxels of different fields: their shared face counts
+    occ2 = np.zeros((G, G, G), dtype=bool)
+    occ2[10, 10, 10:12] = True
+    s = _Scene(occ2, vox)
+    part = _Part(2)
+    part.field_of_rank = np.array([0, 1], dtype=np.uint16)
+    g2 = O.Grid(s, part)
+    d2 = O.sample_tie_distance(g2, cam, np.array([[0, 4]], np.uint32), np.zeros(js.size, np.int64), js, delta)
+    for j, dd in zip(js, d2):
+        xv = (x0 + (j + 0.5) * delta) / vf
+        ix, fr = math.floor(xv), xv - math.floor(xv)
+        if ix == 10:
+            assert abs(dd - min(fr, 1 - fr, y_fr, 1 - y_fr)) < 1e-12
+        elif ix == 11:
+            assert abs(dd - min(fr, 1 - fr, y_fr, 1 - y_fr)) < 1e-12
+
+
 # ----------------------------------------------------------------------------
 # gradient: analytic reverse mode versus central finite differences
 # ----------------------------------------------------------------------------
