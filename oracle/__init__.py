@@ -56,6 +56,7 @@ def lib():
         I, D, I64 = ctypes.c_int, ctypes.c_double, ctypes.c_int64
         L.orc_param_count.argtypes = [I, I]; L.orc_param_count.restype = I64
         L.orc_threads.restype = I
+        L.orc_set_threads.argtypes = [I]
         L.orc_ray.argtypes = [f64p, D, D, f64p, f64p]
         L.orc_label_map.argtypes = [I, I, I, u32p, u16p, I64, i32p]; L.orc_label_map.restype = I64
         L.orc_march.argtypes = [i32p, f64p, D, i32p, f64p, f64p, D, I, i32p, i32p, i32p]
@@ -90,7 +91,7 @@ def lib():
         L.orc_assign_fields.argtypes = [i32p, ctypes.POINTER(ctypes.c_int64), I64, I, i32p]
         L.orc_assign_fields.restype = I
         L.orc_teacher_param_count.restype = I64
-        L.orc_teacher_eval.argtypes = [f32p, f64p, I64, f64p, f64p, f64p]
+        L.orc_teacher_eval.argtypes = [f32p, f64p, I64, f64p, f64p, f64p, I]
         L.orc_distill_loss_grad.argtypes = [f32p, f32p, I, I, I, I, D, I64, f64p, f64p, i32p, f64p, D, f64p]
         L.orc_distill_loss_grad.restype = D
         L.orc_mlp_grad_points.argtypes = [f32p, f32p, I, I, I, I, D, I, I64, f64p, f64p, i32p, f64p, f64p, f64p]
@@ -111,6 +112,11 @@ def f32(x) -> float:
 
 def threads() -> int:
     return int(lib().orc_threads())
+
+
+def set_threads(n: int) -> None:
+    """Host threads of the oracle's parallel loops from now on."""
+    lib().orc_set_threads(int(n))
 
 
 def param_count(W: int, H: int) -> int:
@@ -413,16 +419,18 @@ def teacher_param_count() -> int:
     return int(lib().orc_teacher_param_count())
 
 
-def teacher_eval(weights, aff_global, p, d) -> np.ndarray:
+def teacher_eval(weights, aff_global, p, d, quant: int = 0) -> np.ndarray:
     """The global 360NeRF at points p [n, 3] with directions d [n, 3]:
-    (sigma, r, g, b) per point."""
+    (sigma, r, g, b) per point.  quant=2 takes the BF16 reading (BF16
+    inputs and weights of the matrix layers but the density head and layer
+    11; the bias of layers 1, 5 and 10 rounded too)."""
     w = np.ascontiguousarray(weights, dtype=np.float32)
     a = np.ascontiguousarray(np.asarray(aff_global, dtype=np.float32), dtype=np.float64)
     p = np.ascontiguousarray(p, dtype=np.float64).reshape(-1, 3)
     d = np.ascontiguousarray(d, dtype=np.float64).reshape(-1, 3)
     out = np.zeros((p.shape[0], 4))
     lib().orc_teacher_eval(_p(w, ctypes.c_float), _p(a, ctypes.c_double), int(p.shape[0]), _p(p, ctypes.c_double),
-                           _p(d, ctypes.c_double), _p(out, ctypes.c_double))
+                           _p(d, ctypes.c_double), _p(out, ctypes.c_double), int(quant))
     return out
 
 

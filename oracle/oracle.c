@@ -106,6 +106,16 @@ int orc_threads(void)
 #endif
 }
 
+/* Number of host threads the parallel loops use from now on (timing only) */
+void orc_set_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
+
 /* ------------------------------------------------------------------ */
 /* ray generation: Eq. 2 (pixel <-> longitude/latitude) and Eq. 3       */
 /* ------------------------------------------------------------------ */
@@ -1294,28 +1304,51 @@ int64_t orc_teacher_param_count(void)
            (W * W + W) + (ORC_T_C * (W + ORC_PE_DIR) + ORC_T_C) + (3 * ORC_T_C + 3);
 }
 
-static void teacher_forward(const float *w, const double *aff, const double *p, const double *d, double *out)
+/* dense() with inputs and weights rounded to BF16 and the bias not (the
+ * teacher's BF16 reading of its layers whose bias is added in FP32) */
+static void dense_bf16_fb(const float *Wm, const float *b, int n_out, int n_in, const double *x, double *y)
+{
+    double xq[512];
+    for (int c = 0; c < n_in; ++c) xq[c] = bf16r(x[c]);
+    for (int r = 0; r < n_out; ++r) {
+        double acc = (double)b[r];
+        for (int c = 0; c < n_in; ++c) acc += bf16r((double)Wm[(int64_t)r * n_in + c]) * xq[c];
+        y[r] = acc;
+    }
+}
+
+/* The teacher at one point.  quant == 2 is the BF16 reading (the library's
+ * tensor-core teacher): every layer but the density head and layer 11 takes
+ * its inputs and weights rounded to BF16; layers 1, 5 and 10 (whose input
+ * has a spare column for it) their bias too, the others an unrounded bias;
+ * the density head (on layer 8's unrounded output) and layer 11 stay FP64
+ * on the FP32 weights; sums in FP64. */
+static void teacher_forward(const float *w, const double *aff, const double *p, const double *d, double *out,
+                            int quant)
 {
     const int W = ORC_T_W;
+    void (*mat_b)(const float *, const float *, int, int, const double *, double *) = quant == 2 ? dense_bf16 : dense;
+    void (*mat_f)(const float *, const float *, int, int, const double *, double *) =
+        quant == 2 ? dense_bf16_fb : dense;
     double xg[3], pe[ORC_PE_POS], h[ORC_T_W + ORC_PE_POS], z[ORC_T_W], ped[ORC_PE_DIR];
     for (int a = 0; a < 3; ++a) xg[a] = aff[a] * p[a] + aff[3 + a];
     encode(xg, 10, pe);
     encode(d, 4, ped);
     const float *q = w;
-    dense(q, q + W * ORC_PE_POS, W, ORC_PE_POS, pe, z);                 /* layer 1 */
+    mat_b(q, q + W * ORC_PE_POS, W, ORC_PE_POS, pe, z);                 /* layer 1 */
     q += W * ORC_PE_POS + W;
     for (int r = 0; r < W; ++r) h[r] = z[r] > 0.0 ? z[r] : 0.0;
     for (int l = 2; l <= 4; ++l) {                                       /* layers 2-4 */
-        dense(q, q + W * W, W, W, h, z);
+        mat_f(q, q + W * W, W, W, h, z);
         q += W * W + W;
         for (int r = 0; r < W; ++r) h[r] = z[r] > 0.0 ? z[r] : 0.0;
     }
     for (int k = 0; k < ORC_PE_POS; ++k) h[W + k] = pe[k];               /* skip: [h4; F(x)] */
-    dense(q, q + W * (W + ORC_PE_POS), W, W + ORC_PE_POS, h, z);         /* layer 5 */
+    mat_b(q, q + W * (W + ORC_PE_POS), W, W + ORC_PE_POS, h, z);         /* layer 5 */
     q += W * (W + ORC_PE_POS) + W;
     for (int r = 0; r < W; ++r) h[r] = z[r] > 0.0 ? z[r] : 0.0;
     for (int l = 6; l <= 8; ++l) {                                       /* layers 6-8 (8: linear) */
-        dense(q, q + W * W, W, W, h, z);
+        mat_f(q, q + W * W, W, W, h, z);
         q += W * W + W;
         for (int r = 0; r < W; ++r) h[r] = (l < 8) ? (z[r] > 0.0 ? z[r] : 0.0) : z[r];
     }
@@ -1324,23 +1357,25 @@ static void teacher_forward(const float *w, const double *aff, const double *p, 
     q += W + 1;
     out[0] = s > 0.0 ? s : 0.0;
     double f[ORC_T_W + ORC_PE_DIR];
-    dense(q, q + W * W, W, W, h, z);                                     /* layer 9, feature */
+    mat_f(q, q + W * W, W, W, h, z);                                     /* layer 9, feature */
     q += W * W + W;
     for (int r = 0; r < W; ++r) f[r] = z[r] > 0.0 ? z[r] : 0.0;
     for (int k = 0; k < ORC_PE_DIR; ++k) f[W + k] = ped[k];
     double g[ORC_T_C], zo[3];
-    dense(q, q + ORC_T_C * (W + ORC_PE_DIR), ORC_T_C, W + ORC_PE_DIR, f, g);   /* layer 10 */
+    mat_b(q, q + ORC_T_C * (W + ORC_PE_DIR), ORC_T_C, W + ORC_PE_DIR, f, g);   /* layer 10 */
     q += ORC_T_C * (W + ORC_PE_DIR) + ORC_T_C;
     for (int r = 0; r < ORC_T_C; ++r) g[r] = g[r] > 0.0 ? g[r] : 0.0;
     dense(q, q + 3 * ORC_T_C, 3, ORC_T_C, g, zo);                        /* layer 11 */
     for (int c = 0; c < 3; ++c) out[1 + c] = sigm(zo[c]);
 }
 
-/* out[n][4] = (sigma, r, g, b) of the teacher at points p[n][3], directions d[n][3] */
-void orc_teacher_eval(const float *w, const double *aff, int64_t n, const double *p, const double *d, double *out)
+/* out[n][4] = (sigma, r, g, b) of the teacher at points p[n][3], directions
+ * d[n][3]; quant 0: FP64, 2: the BF16 reading above */
+void orc_teacher_eval(const float *w, const double *aff, int64_t n, const double *p, const double *d, double *out,
+                      int quant)
 {
 #pragma omp parallel for schedule(dynamic, 64)
-    for (int64_t i = 0; i < n; ++i) teacher_forward(w, aff, p + 3 * i, d + 3 * i, out + 4 * i);
+    for (int64_t i = 0; i < n; ++i) teacher_forward(w, aff, p + 3 * i, d + 3 * i, out + 4 * i, quant);
 }
 
 /* Eq. 7 summed over the fields: loss = sum_i [(sigma_s - sigma_t)^2 +

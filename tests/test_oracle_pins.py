@@ -1194,3 +1194,45 @@ def test_bf16_reading_matches_independent_chain(room32):
     rel = np.abs(g - g64).max() / np.abs(g64).max()
     cos = float((g * g64).sum() / (np.linalg.norm(g) * np.linalg.norm(g64)))
     assert 1e-5 < rel < 0.3 and cos > 0.99
+
+
+def test_teacher_bf16_reading_matches_independent_chain():
+    """The teacher's BF16 reading against a NumPy chain that rounds the same
+    operands: inputs and weights of every matrix layer but the density head
+    and layer 11, and the biases of layers 1, 5 and 10 (the ones the
+    tensor-core kernel folds into its products)."""
+    w = F.teacher_weights(3, bias_scale=0.2)
+    aff = np.array([0.3, 0.25, 0.2, -1.0, -0.9, -0.8], dtype=np.float32)
+    rng = np.random.default_rng(32)
+    p = rng.uniform(0, 6, (6, 3))
+    d = rng.normal(size=(6, 3))
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    got = O.teacher_eval(w, aff, p, d, quant=2)
+    ref64 = O.teacher_eval(w, aff, p, d)
+    R = _bf16_np
+    mats, o = [], 0
+    for (n_out, n_in) in F.teacher_layer_shapes():
+        mats.append((w[o:o + n_out * n_in].reshape(n_out, n_in).astype(np.float64),
+                     w[o + n_out * n_in:o + n_out * n_in + n_out].astype(np.float64)))
+        o += n_out * n_in + n_out
+    relu = lambda v: np.maximum(v, 0)
+    for i in range(6):
+        xg = aff[:3].astype(np.float64) * p[i] + aff[3:].astype(np.float64)
+        pe, ped = _np_encode(xg, 10), _np_encode(d[i], 4)
+        folded = lambda k, x: R(mats[k][0]) @ R(x) + R(mats[k][1])
+        plain = lambda k, x: R(mats[k][0]) @ R(x) + mats[k][1]
+        h = relu(folded(0, pe))
+        for k in (1, 2, 3):
+            h = relu(plain(k, h))
+        h = relu(folded(4, np.concatenate([h, pe])))
+        for k in (5, 6):
+            h = relu(plain(k, h))
+        h = plain(7, h)
+        sigma = relu(mats[8][0] @ h + mats[8][1])[0]
+        f = relu(plain(9, h))
+        g = relu(folded(10, np.concatenate([f, ped])))
+        rgb = 1 / (1 + np.exp(-(mats[11][0] @ g + mats[11][1])))
+        assert np.abs(got[i] - np.concatenate([[sigma], rgb])).max() <= 1e-10 * max(1.0, abs(sigma))
+    # the rounding is applied and stays a small perturbation of FP64
+    diff = np.abs(got - ref64).max()
+    assert 1e-6 < diff < 0.2
