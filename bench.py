@@ -131,7 +131,45 @@ def cpu_oracle_rate(wl, target_s: float, seed: int = 1234):
     r = O.render(g, wl.weights, wl.affine, wl.W, wl.H, wl.sigma_scale, cams, rays, wl.delta, wl.n_max)
     dt = time.perf_counter() - t0
     used = int(r["n_used"].sum())
-    return used / dt, O.threads(), f"{n} random pixels of both views ({used} composited samples, {dt:.1f} s)"
+    return used / dt, O.threads(), f"{n} random pixels of both views ({used} composited samples, {dt:.1f} s)", n / dt
+
+
+def cpu_oracle_frames(wl, rate_rays_all, one_core_s: float = 4.0):
+    """The rest of the CPU baseline plan: the oracle on one core (samples/s
+    on a bounded sample), and per-frame times -- the 128x64 room rendered
+    whole on all cores, the 1024x512 floor view extrapolated from the
+    all-core ray rate measured on a sample (stated as such)."""
+    import fixtures as F
+    import oracle as O
+    g = O.Grid(wl.scene, wl.part)
+    cams = F.camera_array(wl.cams)
+    all_cores = O.threads()
+    O.set_threads(1)
+    try:
+        probe = oracle_sample_rays(wl, 300, 77)
+        t0 = time.perf_counter()
+        O.render(g, wl.weights, wl.affine, wl.W, wl.H, wl.sigma_scale, cams, probe, wl.delta, wl.n_max)
+        dt = time.perf_counter() - t0
+        n1 = int(max(300, min(200_000, 300 * one_core_s / max(dt, 1e-3))))
+        rays = oracle_sample_rays(wl, n1, 78)
+        t0 = time.perf_counter()
+        r = O.render(g, wl.weights, wl.affine, wl.W, wl.H, wl.sigma_scale, cams, rays, wl.delta, wl.n_max)
+        dt1 = time.perf_counter() - t0
+    finally:
+        O.set_threads(all_cores)
+    one = {"value": int(r["n_used"].sum()) / dt1, "unit": UNIT, "cores": 1,
+           "sample": f"{n1} random pixels of both views ({dt1:.1f} s)"}
+    room = F.room32()
+    gr = O.Grid(room.scene, room.part)
+    t0 = time.perf_counter()
+    O.render(gr, room.weights, room.affine, room.W, room.H, room.sigma_scale, F.camera_array(room.cams), None,
+             room.delta, room.n_max)
+    room_ms = 1000 * (time.perf_counter() - t0)
+    eq_pixels = wl.cams[0].n_pixels
+    frames = {"room32_128x64_ms": room_ms, "cores": all_cores,
+              "floor256_equirect_1024x512_ms_extrapolated": 1000.0 * eq_pixels / rate_rays_all,
+              "extrapolation": "all-core ray rate of the sampled pixels (both views) times the view's pixel count"}
+    return one, frames
 
 
 def reference_arm(args):
@@ -251,19 +289,29 @@ def train_step_bench(roam, F, torch, wl, args, stream):
 
 
 
-def accuracy(got, ref):
-    """PSNR and max abs error of sampled pixels against an oracle render; the
-    max is also given over the rays the oracle does not certify as near-ties
-    (a sample point within 1e-3 voxel of a voxel face whose sides differ, or
-    a transmittance within 1e-6 of the termination threshold)."""
+def accuracy(r, roam, F, g, wl, rays, prec, got, ref, quant=0, widths=None):
+    """Sampled pixels against the FP64 oracle under the render parity rule
+    (oracle.parity): every ray is held to the bar of its precision, against
+    the oracle's render where the library's kept-sample list equals the
+    oracle's, and against the oracle recomputed on the library's own list
+    where it differs (certified near-ties, counted).  Also gives the raw max
+    over all pixels against the oracle's own march."""
     import numpy as np
-    e = got - ref["rgb"]
-    mse = float((e ** 2).mean())
-    tie = (ref["ties"] > 0) | (ref["margin"] < 1e-6)
-    per = np.abs(e).max(axis=1)
-    return {"psnr_db": 10 * math.log10(1.0 / mse) if mse > 0 else float("inf"), "max_abs": float(per.max()),
-            "pixels": int(len(per)), "near_tie_rays": int(tie.sum()),
-            "max_abs_excl_near_ties": float(per[~tie].max()) if (~tie).any() else 0.0}
+    import torch
+    import oracle.parity as P
+    opts = roam.render_opts(wl.delta, wl.n_max, precision=prec)
+    cnt, recs = r.march(wl.cams, opts, rays=torch.from_numpy(rays.astype(np.int32)).cuda())
+    torch.cuda.synchronize()
+    tol = 1e-4 if prec == roam.ROAM_F32 else 2e-2
+    W = wl.W if widths is None else 0
+    rep = P.check_render(g, wl.weights, wl.affine, W, wl.H, wl.sigma_scale, F.camera_array(wl.cams), rays, wl.delta,
+                         wl.n_max, cnt.cpu().numpy(), recs.cpu().numpy(), got, tol=tol, quant=quant, widths=widths,
+                         ref=ref)
+    raw = np.abs(got - ref["rgb"]).max(axis=1)
+    return {"psnr_db": rep.psnr(got), "max_abs": rep.max_err, "bar": tol, "over_bar": int(rep.over.size),
+            "pixels": rep.n, "records_equal": rep.n_equal, "certified_mismatches": len(rep.certified),
+            "uncertified_mismatches": len(rep.uncertified), "termination_ties": rep.term_ties,
+            "max_abs_vs_oracle_own_march": float(raw.max()) if raw.size else 0.0}
 
 
 def large_scene_bench(roam, F, torch, args, stream, flush, peaks):
@@ -304,10 +352,10 @@ def large_scene_bench(roam, F, torch, args, stream, flush, peaks):
         torch.cuda.synchronize()
         got = rgb.cpu().numpy()[gi].astype(np.float64)
         acc = {}
-        for name, rr in (("vs_fp64_oracle", ref), ("vs_oracle_fp8_reading", ref8)):
+        for name, rr, quant in (("vs_fp64_oracle", ref, 0), ("vs_oracle_fp8_reading", ref8, 1)):
             if name == "vs_oracle_fp8_reading" and prec != roam.ROAM_FP8:
                 continue
-            acc[name] = accuracy(got, rr)
+            acc[name] = accuracy(r, roam, F, g, wl, rays, prec, got, rr, quant=quant)
         launches, mlp_ms = prof.get(key, (0, float("nan")))
         tflops = flops_per * st.n_samples * steps / (mlp_ms / 1000.0) / 1e12
         path = {"frame_ms": statistics.median(per), "samples_per_s": st.n_used * steps / (tot / 1000.0),
@@ -374,7 +422,8 @@ def multiview_bench(roam, F, torch, args, stream, flush):
                    wl.n_max, widths=wl.widths)
     starts = np.concatenate([[0], np.cumsum([c.n_pixels for c in wl.cams])])
     gi = starts[rays[:, 0].astype(np.int64)] + rays[:, 1].astype(np.int64)
-    out["accuracy_vs_oracle"] = accuracy(rgb.cpu().numpy()[gi].astype(np.float64), ref)
+    out["accuracy_vs_oracle"] = accuracy(r, roam, F, g, wl, rays, roam.ROAM_BF16, rgb.cpu().numpy()[gi].astype(np.float64),
+                                         ref, widths=wl.widths)
     r.close()
     return out
 
@@ -435,7 +484,7 @@ def stereo_bench(roam, F, torch, stream):
             "fps_at_median": 1000.0 / float(np.median(t))}
 
 
-def distill_bench(roam, F, torch, args, stream):
+def distill_bench(roam, F, torch, args, stream, peaks):
     """One distillation step (Eq. 7) on the floor256 partition: the global
     360NeRF teacher (8x256, 595,844 parameters, FP32 cuBLAS layers) labels
     256 points per field in each of the 512 fields; the W=64/H=3 students
@@ -457,7 +506,7 @@ def distill_bench(roam, F, torch, args, stream):
 
     def step(k):
         return r.distill_step(pt, dt, ft, float(I), lr=1e-3, step=k, precision=roam.ROAM_BF16,
-                              teacher_precision=roam.ROAM_TF32, stream=stream)
+                              teacher_precision=roam.ROAM_BF16, stream=stream)
 
     for k in range(1, 4):
         step(k)
@@ -477,8 +526,9 @@ def distill_bench(roam, F, torch, args, stream):
     # the teacher alone, in both arithmetics
     n = int(p.shape[0])
     teacher = {}
-    for name, prec in (("tf32", roam.ROAM_TF32), ("f32", roam.ROAM_F32)):
-        for _ in range(2):                     # warm-up: library kernel selection and loading
+    peak = peaks.get("bf16_tflops", 1900.0)
+    for name, prec in (("bf16_tcgen05", roam.ROAM_BF16), ("f32_simt", roam.ROAM_F32)):
+        for _ in range(2):
             r.teacher_eval(pt, dt, precision=prec, stream=stream)
         a.record(stream)
         for _ in range(steps):
@@ -486,13 +536,32 @@ def distill_bench(roam, F, torch, args, stream):
         b.record(stream)
         b.synchronize()
         t_ms = a.elapsed_time(b) / steps
-        teacher[name] = {"ms": t_ms, "tflops": 2.0 * 595844 * n / (t_ms / 1000.0) / 1e12}
+        tf = 2.0 * 595844 * n / (t_ms / 1000.0) / 1e12
+        teacher[name] = {"ms": t_ms, "tflops": tf}
+        if prec == roam.ROAM_BF16:
+            teacher[name]["frac_of_bf16_peak"] = tf / peak
+            teacher[name]["peak"] = "measured bf16 burst" if peaks else "fallback"
+    # a larger batch (the teacher's own roofline: many tiles per SM)
+    n_big = 1 << 20
+    rng = np.random.default_rng(5)
+    pb = torch.from_numpy(p[rng.integers(0, n, n_big)]).cuda()
+    db = torch.from_numpy(d[rng.integers(0, n, n_big)]).cuda()
+    for _ in range(2):
+        r.teacher_eval(pb, db, precision=roam.ROAM_BF16, stream=stream)
+    a.record(stream)
+    for _ in range(steps):
+        r.teacher_eval(pb, db, precision=roam.ROAM_BF16, stream=stream)
+    b.record(stream)
+    b.synchronize()
+    t_ms = a.elapsed_time(b) / steps
+    tf = 2.0 * 595844 * n_big / (t_ms / 1000.0) / 1e12
+    teacher["bf16_tcgen05_1M_points"] = {"ms": t_ms, "tflops": tf, "frac_of_bf16_peak": tf / peak}
     r.close()
     return {"workload": f"floor256_kd512_w64h3 students, 360NeRF teacher, {I} points per field ({n} per step)",
             "ms_per_step": ms, "points_per_s": n / (ms / 1000.0), "teacher": teacher,
             "loss_first_last": [float(losses[0]), float(losses[-1])],
             "kernels": {k: {"launches": v[0], "ms": round(v[1], 3)} for k, v in prof.items()},
-            "precision": "teacher TF32 tensor cores (cuBLAS, FP32 accumulation), students BF16 tcgen05 forward "
+            "precision": "teacher BF16 tcgen05 (FP32 accumulation), students BF16 tcgen05 forward "
                          "and adjoint, FP32 master weights"}
 
 
@@ -575,7 +644,10 @@ def main():
         if args.section == "train":
             res = train_step_bench(roam, F, torch, F.floor256(), args, stream)
         else:
-            res = distill_bench(roam, F, torch, args, stream)
+            pk = {}
+            if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")):
+                pk = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+            res = distill_bench(roam, F, torch, args, stream, pk)
         print(json.dumps({"section": args.section, **res}), flush=True)
         return 0
 
@@ -697,7 +769,7 @@ def main():
         for prec, tag in ((head_prec, dtype), (roam.ROAM_F32, "f32")):
             rgb, _, _ = r.render(wl.cams, roam.render_opts(wl.delta, wl.n_max, precision=prec))
             torch.cuda.synchronize()
-            acc[tag] = accuracy(rgb.cpu().numpy()[gi].astype(np.float64), ref)
+            acc[tag] = accuracy(r, roam, F, g, wl, rays, prec, rgb.cpu().numpy()[gi].astype(np.float64), ref)
 
     # ---- end to end through the C ABI with host buffers ----
     n_pix = sum(c.n_pixels for c in wl.cams)
@@ -725,7 +797,7 @@ def main():
 
     large = multiview = occupancy = stereo = partition = distill = None
     if rank == 0:
-        distill = distill_bench(roam, F, torch, args, stream)
+        distill = distill_bench(roam, F, torch, args, stream, peaks)
         large = large_scene_bench(roam, F, torch, args, stream, flush, peaks)
         multiview = multiview_bench(roam, F, torch, args, stream, flush)
         occupancy = occupancy_bench(roam, F, torch, args, stream)
@@ -734,8 +806,10 @@ def main():
 
     cpu = None
     if rank == 0 and world == 1:
-        v, cores, desc = cpu_oracle_rate(wl, args.cpu_seconds)
-        cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc}
+        v, cores, desc, rays_s = cpu_oracle_rate(wl, args.cpu_seconds)
+        one, frames = cpu_oracle_frames(wl, rays_s)
+        cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc,
+               "rays_per_s": rays_s, "one_core": one, "frames": frames}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

@@ -43,7 +43,7 @@ typedef enum {
     ROAM_ERR_UNSUPPORTED = -7  /* valid request with no kernel for it (shape or precision) */
 } roam_status;
 
-enum { ROAM_F32 = 0, ROAM_BF16 = 1, ROAM_FP8 = 2, ROAM_TF32 = 3 };   /* arithmetic (TF32: the teacher only) */
+enum { ROAM_F32 = 0, ROAM_BF16 = 1, ROAM_FP8 = 2 };   /* arithmetic */
 enum { ROAM_EQUIRECT = 0, ROAM_PERSPECTIVE = 1 };     /* camera models */
 enum { ROAM_SOFTPLUS = 0, ROAM_RELU = 1 };            /* density activation */
 
@@ -248,9 +248,11 @@ roam_status roam_teacher_load(roam_ctx *ctx, const float *weights, const float *
 
 /* The teacher at n points: p, d device float[n][3] (world position, view
  * direction); out device float[n][4] = (sigma, r, g, b), 16-byte aligned.
- * precision ROAM_F32: FP32 GEMMs; ROAM_TF32: the GEMMs on the tensor cores
- * with TF32 operands (10-bit mantissas) and FP32 accumulation; the
- * encodings, biases and activations stay FP32 either way.  Asynchronous. */
+ * precision ROAM_BF16: the matrix layers on the tensor cores (tcgen05, BF16
+ * inputs and weights, FP32 accumulation; layers 1, 5 and 10 take their bias
+ * as a BF16 product term, the others add it in FP32), the density head and
+ * layer 11 in FP32 on the CUDA cores; ROAM_F32: every layer in FP32 on the
+ * CUDA cores.  The encodings are FP32 in both.  Asynchronous. */
 roam_status roam_teacher_eval(roam_ctx *ctx, const float *p, const float *d, int64_t n, int precision, float *out,
                               void *stream);
 
@@ -284,8 +286,32 @@ roam_status roam_mlp_backward(roam_ctx *ctx, const float *p, const float *d, con
 roam_status roam_tune_round_size(roam_ctx *ctx, const roam_camera *cams, int n_views, const roam_render_opts *opts,
                                  int32_t *best_round_size, float *best_ms, void *stream);
 
-/* Counters of the last roam_render / roam_train_forward (synchronises). */
+/* Counters of the last roam_render / roam_train_forward (synchronises); the
+ * single-step entry points and the backward passes keep counters of their
+ * own and leave these as they are. */
 roam_status roam_get_stats(roam_ctx *ctx, roam_stats *stats);
+
+/* Pads every field's run of 128-sample tiles on the tensor-core paths to a
+ * multiple of `tiles` (a multiple of 4 in [4, 64]) instead of each MLP
+ * kernel's own tiles in flight (0, the default).  Results do not depend on
+ * it: the padding tiles hold no samples, and a kernel then meets groups of
+ * tiles in which no slot has work.  Meant for testing that every kernel
+ * handles such groups; it only adds work.  ROAM_ERR_ARG for other values. */
+roam_status roam_set_tile_padding(roam_ctx *ctx, int tiles);
+
+/* Self-test of the bounded device-side waits: runs the tensor-core MLP
+ * kernel of the loaded weights once over a tile of 128 points of one field
+ * with the copy of that field's weight image withheld, so that every wait
+ * for the image runs out after limit_ns (1e6 .. 1e10 ns) instead of the
+ * 2 s the kernels otherwise allow.  The kernel then flags the timeout in
+ * its status word, lets its other threads leave at their next barrier,
+ * finishes the commits it issued, frees its tensor memory and returns;
+ * nothing is copied or computed on the withheld image.  Synchronises.
+ * *observed receives the status a synchronising call reports for that
+ * launch (ROAM_ERR_TIMEOUT when the path works); the flag is then cleared,
+ * so the context stays usable.  ROAM_ERR_UNSUPPORTED without tensor-core
+ * weights. */
+roam_status roam_selftest_wait_timeout(roam_ctx *ctx, uint64_t limit_ns, int32_t *observed, void *stream);
 
 /* Turns per-kernel event timing on (clearing earlier records) or off.  While
  * on, every kernel launch of roam_render / roam_train_* is bracketed by two
@@ -302,7 +328,11 @@ roam_status roam_profile_read(roam_ctx *ctx, roam_kernel_time *out, int max_entr
  * pairs (device uint32[n_rays][2]; NULL = every pixel of every view in
  * order).  No compositing, no termination: per ray, the first n_max kept
  * samples.  count: device uint32[n_rays]; recs: device uint32[n_rays][n_max],
- * entry = j | field << 16.  Asynchronous. */
+ * entry = j | field << 16.  The rays are generated as roam_render generates
+ * them under the same options (opts->precision selects the FP32 render's
+ * directions, rounded from FP64, or the reduced-precision renders' FP32
+ * ones), so the records are exactly the samples roam_render composites, up
+ * to each ray's termination.  Asynchronous. */
 roam_status roam_march(roam_ctx *ctx, const roam_camera *cams, int n_views, const uint32_t *rays,
                        int64_t n_rays, const roam_render_opts *opts, uint32_t *count,
                        uint32_t *recs, void *stream);
@@ -329,18 +359,22 @@ roam_status roam_mlp_eval(roam_ctx *ctx, const float *p, const float *d, const u
  * library routine: its scratch is a fixed array of about 96 KiB in device
  * memory, created when the library is loaded and held by every GPU that
  * loads it until the process exits.
- *   keys    device uint16[n], field ids < n_fields (larger ids are dropped)
+ *   keys    device uint16[n], field ids; ids >= n_fields are dropped
  *   n       0 .. 2^31 - 1
  *   n_fields 1 .. 4096; more gives ROAM_ERR_ARG (the scratch is sized for 4096)
  *   perm    device uint32[n]: sample indices grouped by field, fields in
- *           increasing order (order within a field unspecified)
+ *           increasing order (order within a field unspecified); entries
+ *           from offsets[n_fields] (the number of samples kept) to n - 1
+ *           are left unwritten when ids were dropped
  *   offsets device uint32[n_fields + 1]: group boundaries
  * Works on the calling thread's current device and is asynchronous on
- * `stream`.  The first call on each device looks up the scratch array's
- * device address (cudaGetSymbolAddress); make that first call before any
- * stream capture.  All calls share the one array and it keeps the previous
- * call's contents (each call clears what must start at zero), so calls whose
- * work overlaps on the GPU -- e.g. on two streams -- race: serialise them. */
+ * `stream`.  The first successful call on each device looks up the scratch
+ * array's device address (cudaGetSymbolAddress) and keeps it; make that
+ * first call before any stream capture, and do not use this entry point
+ * after a cudaDeviceReset of the device (the kept address would be stale).
+ * All calls share the one array and it keeps the previous call's contents
+ * (each call clears what must start at zero), so calls whose work overlaps
+ * on the GPU -- e.g. on two streams -- race: serialise them. */
 roam_status roam_bucket_static(const uint16_t *keys, int64_t n, int n_fields, uint32_t *perm,
                                uint32_t *offsets, void *stream);
 

@@ -17,7 +17,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libroam.so")
 
-ROAM_F32, ROAM_BF16, ROAM_FP8, ROAM_TF32 = 0, 1, 2, 3
+ROAM_F32, ROAM_BF16, ROAM_FP8 = 0, 1, 2
 ROAM_EQUIRECT, ROAM_PERSPECTIVE = 0, 1
 ROAM_SOFTPLUS, ROAM_RELU = 0, 1
 
@@ -30,7 +30,7 @@ ENTRY_POINTS = ("roam_create", "roam_destroy", "roam_last_error", "roam_check", 
                 "roam_get_stats", "roam_tune_round_size", "roam_occupancy_update", "roam_assign_fields", "roam_teacher_load", "roam_teacher_eval",
                 "roam_distill_loss", "roam_mlp_backward", "roam_march", "roam_bucket", "roam_mlp_eval", "roam_composite", "roam_train_forward",
                 "roam_train_backward", "roam_adam_step", "roam_profile", "roam_profile_read",
-                "roam_bucket_static", "roam_l2_loss")
+                "roam_bucket_static", "roam_l2_loss", "roam_set_tile_padding", "roam_selftest_wait_timeout")
 
 
 class RoamError(RuntimeError):
@@ -126,6 +126,8 @@ def load_library(path: str = LIB_PATH):
     L.roam_adam_step.argtypes = [vp, vp, P(roam_adam_cfg), vp]
     L.roam_bucket_static.argtypes = [vp, i64, i32, vp, vp, vp]
     L.roam_l2_loss.argtypes = [vp, vp, vp, i64, ctypes.c_float, vp, vp, vp]
+    L.roam_set_tile_padding.argtypes = [vp, i32]
+    L.roam_selftest_wait_timeout.argtypes = [vp, ctypes.c_uint64, P(ctypes.c_int32), vp]
     L.roam_profile.argtypes = [vp, i32]
     L.roam_profile_read.argtypes = [vp, P(roam_kernel_time), i32, P(ctypes.c_int)]
     for name in ENTRY_POINTS:
@@ -202,6 +204,8 @@ class Roam:
         _check(self.L.roam_create(ctypes.byref(h), device))
         self.h = h
         self.n_pixels = 0
+        self.fwd_gen = 0            # counts train_forward calls (the state train_backward consumes)
+        self._wkey = None           # (pointer, version, shape) of the weight tensor last loaded, if any
 
     def close(self):
         if getattr(self, "h", None):
@@ -251,8 +255,24 @@ class Roam:
             weights = np.ascontiguousarray(weights, dtype=np.float32)
         _check(self.L.roam_load_weights(self.h, ctypes.byref(d), _ptr(weights), int(on_dev)))
         self.W, self.H = W, H
+        self.sigma_scale, self.act = float(sigma_scale), int(act)
         self.P = int(weights.shape[-1])
         self.n_params = self.P * self.n_fields
+        self._wkey = None
+
+    def sync_weights(self, weights):
+        """Loads a device float32 tensor [n_fields, P] (layout of
+        roam_load_weights) as the FP32 masters unless it is the tensor last
+        loaded this way and unchanged since: same storage, same version
+        counter (in-place updates under torch.no_grad(), as torch.optim makes
+        them, advance it)."""
+        import torch
+        key = (weights.data_ptr(), weights._version, tuple(weights.shape))
+        if key != self._wkey:
+            if tuple(weights.shape) != (self.n_fields, self.P) or weights.dtype != torch.float32:
+                raise RoamError(-1, f"weights must be float32 [{self.n_fields}, {self.P}]")
+            self.load_weights(weights.detach().contiguous(), self.W, self.H, self.sigma_scale, self.act)
+            self._wkey = key
 
     def load_weights_mixed(self, weights, widths, H: int, sigma_scale: float, act: int = ROAM_SOFTPLUS):
         """weights: the fields' parameters one after another (1-D), field f in
@@ -392,6 +412,19 @@ class Roam:
     def check(self):
         _check(self.L.roam_check(self.h))
 
+    def selftest_wait_timeout(self, limit_ns: int, stream=None) -> int:
+        """roam_selftest_wait_timeout: the status (ROAM_ERR_TIMEOUT = -5 when the
+        bounded-wait path works) of one MLP launch whose weight image is
+        withheld, every wait limited to limit_ns."""
+        obs = ctypes.c_int32(0)
+        _check(self.L.roam_selftest_wait_timeout(self.h, int(limit_ns), ctypes.byref(obs), _stream(stream)))
+        return int(obs.value)
+
+    def set_tile_padding(self, tiles: int):
+        """roam_set_tile_padding: pad every field's tile run to a multiple of
+        `tiles` (0: each kernel's own tiles in flight)."""
+        _check(self.L.roam_set_tile_padding(self.h, int(tiles)))
+
     def profile(self, enable: bool):
         _check(self.L.roam_profile(self.h, int(bool(enable))))
 
@@ -449,6 +482,7 @@ class Roam:
         rgb = rgb if rgb is not None else torch.empty((n, 3), dtype=torch.float32, device=self._dev())
         _check(self.L.roam_train_forward(self.h, arr, len(cams), _ptr(rays), n, ctypes.byref(opts), _ptr(rgb),
                                          _stream(stream)))
+        self.fwd_gen += 1
         return rgb
 
     def train_backward(self, dl_drgb, grad=None, stream=None):
@@ -490,28 +524,51 @@ def bucket_static(keys, n_fields: int, stream=None):
     Python helper allocates through torch -- a caller that must not allocate
     passes its own buffers to the C entry point instead."""
     import torch
+    if keys.dtype not in (torch.int16, getattr(torch, "uint16", torch.int16)) or not keys.is_contiguous():
+        raise RoamError(-1, "keys must be a contiguous int16 or uint16 tensor")
     L = load_library()
     n = int(keys.shape[0])
-    perm = torch.empty(n, dtype=torch.int32, device=keys.device)
-    offsets = torch.empty(n_fields + 1, dtype=torch.int32, device=keys.device)
-    _check(L.roam_bucket_static(_ptr(keys), n, int(n_fields), _ptr(perm), _ptr(offsets), _stream(stream)))
+    # the C entry point works on the current device: make it the keys' device
+    with torch.cuda.device(keys.device):
+        perm = torch.empty(n, dtype=torch.int32, device=keys.device)
+        offsets = torch.empty(n_fields + 1, dtype=torch.int32, device=keys.device)
+        s = stream if stream is not None else torch.cuda.current_stream(keys.device)
+        _check(L.roam_bucket_static(_ptr(keys), n, int(n_fields), _ptr(perm), _ptr(offsets), s.cuda_stream))
     return perm, offsets
 
 
 def render_function():
-    """torch.autograd.Function over the training forward/backward entry points."""
+    """torch.autograd.Function over the training forward/backward entry
+    points (the hand-written adjoint of compositing, MLPs and encodings).
+
+    ``RoamRender.apply(weights, roam, cams, rays, opts)`` returns rgb [n, 3]
+    for the rays (int32 [n, 2] (view, pixel), on the device).  ``weights`` is a
+    device float32 tensor [n_fields, P] in the layout of roam_load_weights;
+    the forward loads it into the context whenever it is not the tensor last
+    loaded or has changed since (Roam.sync_weights), so the render always
+    uses the tensor's current values, and the backward returns d(loss)/d
+    weights from roam_train_backward.  The context keeps the state of one
+    forward only: a backward whose forward has been followed by another
+    forward on the same context raises instead of returning that later
+    forward's gradient."""
     import torch
 
     class RoamRender(torch.autograd.Function):
         @staticmethod
-        def forward(ctx_, dummy_weights, roam: Roam, cams, rays, opts):
+        def forward(ctx_, weights, roam: Roam, cams, rays, opts):
+            roam.sync_weights(weights)
             rgb = roam.train_forward(cams, rays, opts)
             ctx_.roam = roam
+            ctx_.gen = roam.fwd_gen
+            ctx_.shape = tuple(weights.shape)
             return rgb
 
         @staticmethod
         def backward(ctx_, grad_rgb):
+            if ctx_.roam.fwd_gen != ctx_.gen:
+                raise RuntimeError("RoamRender.backward: another forward ran on this context since this "
+                                   "one; its saved state is gone (run backward before the next forward)")
             grad = ctx_.roam.train_backward(grad_rgb.contiguous())
-            return grad, None, None, None, None
+            return grad.view(ctx_.shape), None, None, None, None
 
     return RoamRender

@@ -24,13 +24,12 @@ static_assert(sizeof(Counters) <= 16 * sizeof(uint32_t), "counters fit their slo
 static __device__ __align__(256) uint32_t g_bucket_scratch[kScratchWords];
 
 struct DeviceSetup {
-    std::once_flag once;
-    uint32_t *scratch = nullptr;   // device address of g_bucket_scratch on this device
+    uint32_t *scratch = nullptr;   // device address of g_bucket_scratch on this device (set once found)
     int n_sm = 0;
-    cudaError_t err = cudaSuccess;
 };
 
 DeviceSetup g_setup[kStaticMaxDevices];
+std::mutex g_setup_mutex;
 
 // failures are reported through roam_last_error(), like every entry point
 roam_status static_fail(roam_status st, const char *msg)
@@ -58,17 +57,24 @@ extern "C" roam_status roam_bucket_static(const uint16_t *keys, int64_t n, int n
         return static_fail(ROAM_ERR_CUDA, "roam_bucket_static: no usable current device");
     }
     // once per device, with that device current: the host-side name of the
-    // array is not a device address, so look the address up
+    // array is not a device address, so look the address up (a failed lookup
+    // is not remembered: the next call tries again)
     DeviceSetup &ds = g_setup[dev];
-    std::call_once(ds.once, [&ds, dev]() {
-        void *p = nullptr;
-        ds.err = cudaGetSymbolAddress(&p, g_bucket_scratch);
-        if (ds.err == cudaSuccess) ds.err = cudaDeviceGetAttribute(&ds.n_sm, cudaDevAttrMultiProcessorCount, dev);
-        if (ds.err == cudaSuccess) ds.scratch = static_cast<uint32_t *>(p);
-        else cudaGetLastError();
-    });
-    if (ds.err != cudaSuccess || !ds.scratch)
-        return static_fail(ROAM_ERR_CUDA, "roam_bucket_static: cudaGetSymbolAddress of the scratch array failed");
+    {
+        std::lock_guard<std::mutex> lock(g_setup_mutex);
+        if (!ds.scratch) {
+            void *p = nullptr;
+            int n_sm = 0;
+            if (cudaGetSymbolAddress(&p, g_bucket_scratch) != cudaSuccess ||
+                cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || !p) {
+                cudaGetLastError();
+                return static_fail(ROAM_ERR_CUDA,
+                                   "roam_bucket_static: cudaGetSymbolAddress of the scratch array failed");
+            }
+            ds.n_sm = n_sm;
+            ds.scratch = static_cast<uint32_t *>(p);
+        }
+    }
 
     cudaStream_t s = (cudaStream_t)stream;
     uint32_t *hist = ds.scratch;

@@ -189,6 +189,11 @@ struct MlpWeights {
     int cls;                   // width class: the kernels take tiles [class_tiles[cls], class_tiles[cls + 1])
     int field_base;            // first internal field id of the class (row 0 of the per-class arrays)
     const float *affine;       // [F][6]
+    // self-test of the bounded waits (roam_selftest_wait_timeout): the limit of
+    // every wait of the tensor-core kernel in ns (0: the 2 s default), and
+    // whether the weight-image copies are withheld so that those waits run out
+    unsigned long long wait_ns;
+    int withhold_image;
 };
 
 // ---- kernels launched from the API layer -------------------------------
@@ -201,11 +206,13 @@ struct TeacherAffine {
     float v[6];      // global position -> [-1, 1]^3: scale xyz, offset xyz
 };
 int64_t teacher_param_count();
-int64_t teacher_padded_floats();
-void launch_teacher_pad(const float *w, float *wp, cudaStream_t s);
-size_t teacher_workspace_floats(int64_t n);
-int teacher_eval(void *cublas_handle, const float *w, TeacherAffine aff, int64_t n, const float *p, const float *d,
-                 float4 *out, float *ws, bool tf32, cudaStream_t s);
+int64_t teacher_image_bytes();
+// the caller's layout -> the tensor-core image and the transposed FP32 layers
+void launch_teacher_pack(const float *w, uint8_t *img, float *wt, cudaStream_t s);
+void launch_teacher_tc(const uint8_t *img, TeacherAffine aff, int64_t n, const float *p, const float *d, float4 *out,
+                       uint32_t *status, int n_sm, cudaStream_t s);
+void launch_teacher_simt(const float *wt, TeacherAffine aff, int64_t n, const float *p, const float *d, float4 *out,
+                         int n_sm, cudaStream_t s);
 void launch_distill_loss(int64_t n, const float4 *student, const float4 *teacher, float I, float4 *dl, float *loss,
                          cudaStream_t s);
 size_t assign_scratch_bytes();

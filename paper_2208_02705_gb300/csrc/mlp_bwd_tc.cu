@@ -270,6 +270,9 @@ __global__ void __launch_bounds__(128, 1)
         }
         if (tl.field != cur) {
             if (cur != 0xffffffffu && !wnew) flush(cur);
+            // generic reads of the old image (the epilogue tables) come before
+            // the bulk copy that overwrites it
+            fence_async_smem();
             __syncthreads();
             if (tid == 0) {
                 mbar_expect_tx(&bar_w, (uint32_t)S::kImageBytes);

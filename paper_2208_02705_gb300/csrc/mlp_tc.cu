@@ -47,7 +47,8 @@ namespace {
 template <int W, int H, bool F8>
 __global__ void __launch_bounds__(TcShape<W, H, F8>::kSlots * 128, 1)
     k_mlp_tc(const void *wimg, int64_t img_bytes, int field_base, int cls, const float *affine, float sig_scale,
-             int act, SampleSrc src, BucketBufs b, Counters *ctr, float4 *out)
+             int act, SampleSrc src, BucketBufs b, Counters *ctr, float4 *out, unsigned long long wait_ns,
+             int withhold_image)
 {
     using S = TcShape<W, H, F8>;
     constexpr int kSlots = S::kSlots;
@@ -118,27 +119,33 @@ __global__ void __launch_bounds__(TcShape<W, H, F8>::kSlots * 128, 1)
     for (; g < g1; ++g) {
         const uint32_t f = tl.field;           // identical for every slot (field-uniform groups)
         if (f != cur_field) {
+            // A load whose groups held only empty tiles was never waited for:
+            // thread 0 retires it BEFORE the barrier.  After the barrier any
+            // thread may wait for the next phase of bar_w by its parity, and
+            // a parity wait passes at once while the phase before it is still
+            // pending -- a slot would then read the image while it lands.
+            if (threadIdx.x == 0 && !w_waited_last) {
+                w_waited_last = mbar_wait(&bar_w, (n_changes - 1) & 1u, abortp, status, true, wait_ns);
+                if (!w_waited_last) *abortp = 1;   // the old load never landed: give up (status flagged)
+            }
+            // generic reads of the old image (the FP32 tables) come before the
+            // bulk copy that overwrites it
+            fence_async_smem();
             // every slot has waited on its last layer, so no MMA reads the old
             // image; meet (and agree on any abort), reload, issuers wait below
             if (named_sync_or(15, kSlots * 128, aborted || *abortp)) break;
-            if (threadIdx.x == 0) {
-                // a load whose groups held only empty tiles was never waited
-                // for: retire it first, so each phase of bar_w carries
-                // exactly one arrival and one image
-                if (!w_waited_last) w_waited_last = mbar_wait(&bar_w, (n_changes - 1) & 1u, abortp, status, true);
-                if (w_waited_last) {
-                    mbar_expect_tx(&bar_w, (uint32_t)S::kImageBytes);
-                    const uint8_t *gsrc =
-                        reinterpret_cast<const uint8_t *>(wimg) + (int64_t)(f - field_base) * img_bytes;
-                    for (int off = 0; off < S::kImageBytes; off += 16384) {
-                        const int nb = S::kImageBytes - off < 16384 ? S::kImageBytes - off : 16384;
-                        bulk_g2s(IMG + off, gsrc + off, (uint32_t)nb, &bar_w);
-                    }
-                    w_waited_last = false;
-                } else {
-                    *abortp = 1;           // the old load never landed: give up (status already flagged)
+            if (threadIdx.x == 0 && !withhold_image) {
+                // each phase of bar_w carries exactly one arrival and one image
+                mbar_expect_tx(&bar_w, (uint32_t)S::kImageBytes);
+                const uint8_t *gsrc = reinterpret_cast<const uint8_t *>(wimg) + (int64_t)(f - field_base) * img_bytes;
+                for (int off = 0; off < S::kImageBytes; off += 16384) {
+                    const int nb = S::kImageBytes - off < 16384 ? S::kImageBytes - off : 16384;
+                    bulk_g2s(IMG + off, gsrc + off, (uint32_t)nb, &bar_w);
                 }
+                w_waited_last = false;
             }
+            // (withheld, in the self-test: no copy and no arrival, so every
+            // wait on this phase runs out; nothing is in flight to drain)
             ++n_changes;
             cur_field = f;
             w_ready = false;
@@ -193,7 +200,7 @@ __global__ void __launch_bounds__(TcShape<W, H, F8>::kSlots * 128, 1)
             if (issuer) {
                 bool ok = true;
                 if (!w_ready) {
-                    ok = mbar_wait(&bar_w, (n_changes - 1) & 1u, abortp, status);
+                    ok = mbar_wait(&bar_w, (n_changes - 1) & 1u, abortp, status, false, wait_ns);
                     w_ready = ok;
                     if (threadIdx.x == 0) w_waited_last = ok;
                 }
@@ -213,7 +220,7 @@ __global__ void __launch_bounds__(TcShape<W, H, F8>::kSlots * 128, 1)
                 umma_commit(&bar_d[slot]);
                 ++n_commits;
             }
-            const bool got = mbar_wait(&bar_d[slot], d_ph, abortp, status);
+            const bool got = mbar_wait(&bar_d[slot], d_ph, abortp, status, false, wait_ns);
             if (issuer && got) ++n_waits;
             d_ph ^= 1u;
             // tcgen05.ld is warp-collective: the warp decides together; the
@@ -234,7 +241,7 @@ __global__ void __launch_bounds__(TcShape<W, H, F8>::kSlots * 128, 1)
             const bool use_tab = S::kTab && (F8 || (l >= 1 && l <= H));
             const float *tsc = tab + l * 2 * S::kTabStride, *tbi = tsc + S::kTabStride;
             if (use_tab && !img_seen) {
-                mbar_wait(&bar_w, (n_changes - 1) & 1u, abortp, status);
+                mbar_wait(&bar_w, (n_changes - 1) & 1u, abortp, status, false, wait_ns);
                 img_seen = true;
             }
             if (l < H + 1) {
@@ -294,7 +301,7 @@ __global__ void __launch_bounds__(TcShape<W, H, F8>::kSlots * 128, 1)
                 // the FP32 output table at the end of the shared image (this thread
                 // waits for the image itself before reading it with generic loads)
                 if (!img_seen) {
-                    mbar_wait(&bar_w, (n_changes - 1) & 1u, abortp, status);
+                    mbar_wait(&bar_w, (n_changes - 1) & 1u, abortp, status, false, wait_ns);
                     img_seen = true;
                 }
                 const float4 *wo = reinterpret_cast<const float4 *>(IMG + S::kMatBytes);
@@ -332,8 +339,8 @@ __global__ void __launch_bounds__(TcShape<W, H, F8>::kSlots * 128, 1)
     }
     // drain before TMEM is freed and the CTA exits: a commit whose wait gave
     // up, and an image load nobody waited for
-    if (issuer && n_commits > n_waits) mbar_wait(&bar_d[slot], (n_commits - 1) & 1u, abortp, status, true);
-    if (threadIdx.x == 0 && !w_waited_last) mbar_wait(&bar_w, (n_changes - 1) & 1u, abortp, status, true);
+    if (issuer && n_commits > n_waits) mbar_wait(&bar_d[slot], (n_commits - 1) & 1u, abortp, status, true, wait_ns);
+    if (threadIdx.x == 0 && !w_waited_last) mbar_wait(&bar_w, (n_changes - 1) & 1u, abortp, status, true, wait_ns);
     tc_fence_before();
     __syncthreads();
     if (warp == 0) {
@@ -559,7 +566,8 @@ void launch_t(const MlpWeights &w, const SampleSrc &src, const BucketBufs &b, Co
     const void *img = F8 ? w.wimg8 : w.wimg;
     const int64_t ib = F8 ? w.img8_bytes : w.img_bytes;
     k_mlp_tc<W, H, F8><<<n_sm, kSlots * 128, smem, s>>>(img, ib, w.field_base, w.cls, w.affine, w.sigma_scale, w.act,
-                                                        src, b, ctr, out);
+                                                        src, b, ctr, out, w.wait_ns ? w.wait_ns : kWaitNs,
+                                                        w.withhold_image);
 }
 
 #define ROAM_TC_CASES                                                                                   \

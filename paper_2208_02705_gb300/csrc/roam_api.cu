@@ -8,7 +8,6 @@
 #include <atomic>
 #include <vector>
 
-#include <cublas_v2.h>
 
 #include "internal.cuh"
 
@@ -147,9 +146,9 @@ struct roam_ctx {
     DBuf<uint32_t> assign_vox;               // occupied voxels' linear indices (field assignment)
     // distillation teacher (global 360NeRF)
     bool has_teacher = false;
-    DBuf<float> teacher_w, teacher_ws;
+    DBuf<uint8_t> teacher_img;              // BF16 tensor-core image (+ FP32 tables)
+    DBuf<float> teacher_wt, teacher_ws;      // FP32 transposed layers; the caller's layout while loading
     TeacherAffine teacher_aff{};
-    cublasHandle_t cublas = nullptr;
     DBuf<uint8_t> assign_scratch;
     // pinned staging of the camera uploads: a ring, so that consecutive calls
     // (e.g. one per view) do not wait for each other's copies
@@ -159,7 +158,8 @@ struct roam_ctx {
     cudaEvent_t cam_ev[kCamRing] = {};
     bool cam_pending[kCamRing] = {};
     int cam_slot = 0;
-    Counters *ctr = nullptr;
+    Counters *ctr = nullptr;        // the last render / training forward (roam_get_stats)
+    Counters *aux = nullptr;        // the other calls (single steps, backward passes): ctr + 1
     Counters *h_ctr = nullptr;
     uint32_t *d_flag = nullptr;
     cudaStream_t last = nullptr;
@@ -181,15 +181,18 @@ struct roam_ctx {
     int64_t train_rays = 0;
     int train_R = 0;
     roam_render_opts train_opts{};
+    int tile_pad = 0;                   // roam_set_tile_padding (0: each kernel's own tiles in flight)
+    DBuf<float> selftest;               // roam_selftest_wait_timeout: points, directions, outputs
 };
 
 namespace {
 
 const char *const kProfNames[] = {"march", "bucket", "mlp_f32_simt", "mlp_bf16_tcgen05", "composite",
-                                  "composite_bwd", "mlp_bwd", "adam", "mlp_fp8_tcgen05", "mlp_bwd_bf16_tcgen05"};
+                                  "composite_bwd", "mlp_bwd", "adam", "mlp_fp8_tcgen05", "mlp_bwd_bf16_tcgen05",
+                                  "teacher_bf16_tcgen05", "teacher_f32_simt"};
 constexpr int kProfKinds = (int)(sizeof(kProfNames) / sizeof(kProfNames[0]));
 enum { P_MARCH, P_BUCKET, P_MLP_F32, P_MLP_BF16, P_COMPOSITE, P_COMPOSITE_BWD, P_MLP_BWD, P_ADAM, P_MLP_FP8,
-       P_MLP_BWD_TC };
+       P_MLP_BWD_TC, P_TEACHER_TC, P_TEACHER_F32 };
 
 cudaEvent_t pool_event(roam_ctx *c)
 {
@@ -401,7 +404,12 @@ roam_status upload_cams(roam_ctx *c, const roam_camera *cams, int n_views, float
 
 // tile records needed for `samples` samples: one per 128 plus padding of
 // each field's run to a whole group
-size_t tile_capacity(size_t samples, int n_fields) { return samples / 128 + (size_t)n_fields * 8 + 1; }
+// tiles of 128 samples, each field's run rounded up to its padding (at most
+// the larger of 8 and the forced padding)
+size_t tile_capacity(const roam_ctx *c, size_t samples)
+{
+    return samples / 128 + (size_t)c->n_fields * (size_t)std::max(8, c->tile_pad) + 1;
+}
 
 roam_status ensure_rays(roam_ctx *c, int64_t n_rays, int R)
 {
@@ -421,7 +429,7 @@ roam_status ensure_rays(roam_ctx *c, int64_t n_rays, int R)
     ROAM_TRY(ensure(c->recs, slots));
     ROAM_TRY(ensure(c->sr, slots));
     ROAM_TRY(ensure(c->sorted, slots));
-    ROAM_TRY(ensure(c->tiles, tile_capacity(slots, c->n_fields)));
+    ROAM_TRY(ensure(c->tiles, tile_capacity(c, slots)));
     return ROAM_OK;
 }
 
@@ -474,21 +482,23 @@ ClassBounds classes_of(const roam_ctx *c, int precision)
 {
     ClassBounds cb = c->cb;
     for (int k = 0; k < 4; ++k)
-        cb.group[k] = (precision != ROAM_F32 && k < c->n_ws) ? tc_tile_group(c->ws[k].W, precision == ROAM_FP8) : 1;
+        cb.group[k] = (precision != ROAM_F32 && k < c->n_ws)
+                          ? (c->tile_pad > 0 ? c->tile_pad : tc_tile_group(c->ws[k].W, precision == ROAM_FP8))
+                          : 1;
     return cb;
 }
 
 roam_status run_mlp(roam_ctx *c, int precision, const SampleSrc &src, const BucketBufs &b, float4 *out,
-                    cudaStream_t s)
+                    Counters *ctr, cudaStream_t s)
 {
     // one launch per width class over its own tile range
     for (int k = 0; k < c->n_ws; ++k) {
         const MlpWeights w = weights_of(c, k);
         if (precision != ROAM_F32) {
-            launch_mlp_tc(w, precision == ROAM_FP8, src, b, c->ctr, out, c->n_sm, s);
+            launch_mlp_tc(w, precision == ROAM_FP8, src, b, ctr, out, c->n_sm, s);
             ROAM_TRY(launched("mlp_tc"));
         } else {
-            launch_mlp_simt(w, src, b, c->ctr, out, c->n_sm, s);
+            launch_mlp_simt(w, src, b, ctr, out, c->n_sm, s);
             ROAM_TRY(launched("mlp_simt"));
         }
     }
@@ -545,7 +555,7 @@ roam_status run_rounds(roam_ctx *c, const uint32_t *rays, int64_t n_rays, const 
         src.accurate = mp.accurate;
         {
             ProfScope ps(c, o->precision == ROAM_BF16 ? P_MLP_BF16 : (o->precision == ROAM_FP8 ? P_MLP_FP8 : P_MLP_F32), s);
-            ROAM_TRY(run_mlp(c, o->precision, src, b, c->sr.p, s));
+            ROAM_TRY(run_mlp(c, o->precision, src, b, c->sr.p, c->ctr, s));
         }
         {
             ProfScope ps(c, P_COMPOSITE, s);
@@ -753,8 +763,8 @@ roam_status roam_create(roam_ctx **out, int device)
     roam_ctx *c = new roam_ctx();
     c->device = device;
     c->n_sm = prop.multiProcessorCount;
-    bool ok = cudaMalloc(&c->ctr, sizeof(Counters)) == cudaSuccess &&
-              cudaMallocHost(&c->h_ctr, sizeof(Counters)) == cudaSuccess &&
+    bool ok = cudaMalloc(&c->ctr, 2 * sizeof(Counters)) == cudaSuccess &&
+              cudaMallocHost(&c->h_ctr, 2 * sizeof(Counters)) == cudaSuccess &&
               cudaMallocHost(&c->h_cams_ring, sizeof(DevCamera) * kMaxViews * roam_ctx::kCamRing) == cudaSuccess &&
               cudaMalloc(&c->d_flag, sizeof(uint32_t)) == cudaSuccess;
     for (int i = 0; i < roam_ctx::kCamRing && ok; ++i)
@@ -765,7 +775,8 @@ roam_status roam_create(roam_ctx **out, int device)
         roam_destroy(c);
         return fail(ROAM_ERR_OOM, "context allocation failed");
     }
-    cudaMemset(c->ctr, 0, sizeof(Counters));
+    c->aux = c->ctr + 1;
+    cudaMemset(c->ctr, 0, 2 * sizeof(Counters));
     *out = c;
     return ROAM_OK;
 }
@@ -782,8 +793,7 @@ roam_status roam_destroy(roam_ctx *c)
         release(q.w32); release(q.wt); release(q.wr); release(q.wimg); release(q.wimg8);
     }
     release(c->occ_hit); release(c->occ_free); release(c->assign_vox); release(c->assign_scratch);
-    release(c->teacher_w); release(c->teacher_ws);
-    if (c->cublas) cublasDestroy(c->cublas);
+    release(c->teacher_img); release(c->teacher_wt); release(c->teacher_ws); release(c->selftest);
     release(c->perm); release(c->inv); release(c->labels_orig); release(c->keys_tmp);
     release(c->gsr); release(c->adam_m); release(c->adam_v);
     release(c->orig); release(c->dir); release(c->dir_lo); release(c->acc); release(c->sr); release(c->tw);
@@ -814,8 +824,8 @@ roam_status roam_check(roam_ctx *c)
 {
     ROAM_TRY(set_dev(c));
     ROAM_CUDA(cudaStreamSynchronize(c->last));
-    ROAM_CUDA(cudaMemcpy(c->h_ctr, c->ctr, sizeof(Counters), cudaMemcpyDeviceToHost));
-    return status_of(c->h_ctr->status);
+    ROAM_CUDA(cudaMemcpy(c->h_ctr, c->ctr, 2 * sizeof(Counters), cudaMemcpyDeviceToHost));
+    return status_of(c->h_ctr[0].status | c->h_ctr[1].status);
 }
 
 roam_status roam_load_grid(roam_ctx *c, const roam_grid_desc *desc, const uint32_t *bits, int on_device)
@@ -1178,10 +1188,11 @@ roam_status roam_teacher_load(roam_ctx *c, const float *weights, const float *af
     if (!weights || !affine) return fail(ROAM_ERR_ARG, "null weights or affine");
     const int64_t P = teacher_param_count();
     c->has_teacher = false;
-    // the caller's layout lands in the workspace, is checked, then padded
-    // into the GEMM layout the evaluation reads
+    // the caller's layout lands in the workspace, is checked, then packed
+    // into the tensor-core image and the transposed FP32 layers
     ROAM_TRY(ensure(c->teacher_ws, (size_t)P));
-    ROAM_TRY(ensure(c->teacher_w, (size_t)teacher_padded_floats()));
+    ROAM_TRY(ensure(c->teacher_wt, (size_t)P));
+    ROAM_TRY(ensure(c->teacher_img, (size_t)teacher_image_bytes()));
     ROAM_CUDA(cudaMemcpy(c->teacher_ws.p, weights, (size_t)P * sizeof(float),
                          on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice));
     ROAM_CUDA(cudaMemset(c->d_flag, 0, 4));
@@ -1190,16 +1201,12 @@ roam_status roam_teacher_load(roam_ctx *c, const float *weights, const float *af
     uint32_t bad = 0;
     ROAM_CUDA(cudaMemcpy(&bad, c->d_flag, 4, cudaMemcpyDeviceToHost));
     if (bad) return fail(ROAM_ERR_ARG, "teacher weights contain NaN or Inf");
-    launch_teacher_pad(c->teacher_ws.p, c->teacher_w.p, 0);
-    ROAM_TRY(launched("teacher pad"));
+    launch_teacher_pack(c->teacher_ws.p, c->teacher_img.p, c->teacher_wt.p, 0);
+    ROAM_TRY(launched("teacher pack"));
     ROAM_CUDA(cudaDeviceSynchronize());
     for (int i = 0; i < 6; ++i) {
         if (!finite(affine[i])) return fail(ROAM_ERR_ARG, "non-finite teacher affine");
         c->teacher_aff.v[i] = affine[i];
-    }
-    if (!c->cublas && cublasCreate(&c->cublas) != CUBLAS_STATUS_SUCCESS) {
-        c->cublas = nullptr;
-        return fail(ROAM_ERR_CUDA, "cublasCreate failed");
     }
     c->has_teacher = true;
     return ROAM_OK;
@@ -1210,16 +1217,20 @@ roam_status roam_teacher_eval(roam_ctx *c, const float *p, const float *d, int64
 {
     ROAM_TRY(set_dev(c));
     if (!c->has_teacher) return fail(ROAM_ERR_STATE, "no teacher loaded");
-    if (precision != ROAM_F32 && precision != ROAM_TF32) return fail(ROAM_ERR_ARG, "precision: ROAM_F32 or ROAM_TF32");
+    if (precision != ROAM_F32 && precision != ROAM_BF16) return fail(ROAM_ERR_ARG, "precision: ROAM_F32 or ROAM_BF16");
     if (n < 0 || n > 0x7fffffff) return fail(ROAM_ERR_ARG, "bad sample count");
     if (n == 0) return ROAM_OK;
     if (!p || !d || !out) return fail(ROAM_ERR_ARG, "null pointer");
     if (((uintptr_t)out) & 15) return fail(ROAM_ERR_ARG, "out must be 16-byte aligned");
     cudaStream_t s = (cudaStream_t)stream;
-    ROAM_TRY(ensure(c->teacher_ws, teacher_workspace_floats(n)));
-    if (teacher_eval(c->cublas, c->teacher_w.p, c->teacher_aff, n, p, d, reinterpret_cast<float4 *>(out),
-                     c->teacher_ws.p, precision == ROAM_TF32, s))
-        return fail(ROAM_ERR_CUDA, "cuBLAS GEMM failed in the teacher");
+    if (precision == ROAM_BF16) {
+        ProfScope ps(c, P_TEACHER_TC, s);
+        launch_teacher_tc(c->teacher_img.p, c->teacher_aff, n, p, d, reinterpret_cast<float4 *>(out), &c->aux->status,
+                          c->n_sm, s);
+    } else {
+        ProfScope ps(c, P_TEACHER_F32, s);
+        launch_teacher_simt(c->teacher_wt.p, c->teacher_aff, n, p, d, reinterpret_cast<float4 *>(out), c->n_sm, s);
+    }
     c->last = s;
     return launched("teacher");
 }
@@ -1260,10 +1271,10 @@ roam_status roam_mlp_backward(roam_ctx *c, const float *p, const float *d, const
     if (!p || !d || !field || !dl_dout) return fail(ROAM_ERR_ARG, "null pointer");
     if (((uintptr_t)dl_dout) & 15) return fail(ROAM_ERR_ARG, "dl_dout must be 16-byte aligned");
     ROAM_TRY(ensure(c->sorted, (size_t)n));
-    ROAM_TRY(ensure(c->tiles, tile_capacity((size_t)n, c->n_fields)));
+    ROAM_TRY(ensure(c->tiles, tile_capacity(c, (size_t)n)));
     const BucketBufs b = bucket_of(c);
-    ROAM_CUDA(cudaMemsetAsync(c->ctr, 0, sizeof(Counters), s));
-    launch_bucket(nullptr, nullptr, nullptr, (uint32_t)n, 1, 1, field, c->n_fields, 128, b, c->ctr, grid_blocks(c, 2),
+    ROAM_CUDA(cudaMemsetAsync(c->aux, 0, sizeof(Counters), s));
+    launch_bucket(nullptr, nullptr, nullptr, (uint32_t)n, 1, 1, field, c->n_fields, 128, b, c->aux, grid_blocks(c, 2),
                   s, c->cb);
     ROAM_TRY(launched("bucket"));
     SampleSrc src{};
@@ -1272,10 +1283,10 @@ roam_status roam_mlp_backward(roam_ctx *c, const float *p, const float *d, const
     src.d = d;
     if (tc) {
         ProfScope ps(c, P_MLP_BWD_TC, s);
-        launch_mlp_bwd_tc(weights_of(c), src, b, c->ctr, reinterpret_cast<const float4 *>(dl_dout), grad, c->n_sm, s);
+        launch_mlp_bwd_tc(weights_of(c), src, b, c->aux, reinterpret_cast<const float4 *>(dl_dout), grad, c->n_sm, s);
     } else {
         ProfScope ps(c, P_MLP_BWD, s);
-        launch_mlp_bwd_simt(weights_of(c), src, b, c->ctr, reinterpret_cast<const float4 *>(dl_dout), grad, c->n_sm,
+        launch_mlp_bwd_simt(weights_of(c), src, b, c->aux, reinterpret_cast<const float4 *>(dl_dout), grad, c->n_sm,
                             s);
     }
     c->last = s;
@@ -1287,13 +1298,65 @@ roam_status roam_get_stats(roam_ctx *c, roam_stats *st)
     ROAM_TRY(set_dev(c));
     if (!st) return fail(ROAM_ERR_ARG, "null stats");
     ROAM_CUDA(cudaStreamSynchronize(c->last));
-    ROAM_CUDA(cudaMemcpy(c->h_ctr, c->ctr, sizeof(Counters), cudaMemcpyDeviceToHost));
+    ROAM_CUDA(cudaMemcpy(c->h_ctr, c->ctr, 2 * sizeof(Counters), cudaMemcpyDeviceToHost));
     st->n_samples = (int64_t)c->h_ctr->n_samples;
     st->n_used = (int64_t)c->h_ctr->n_used;
     st->n_fields_hit = (int32_t)c->h_ctr->fields_hit;
     st->n_rays = c->last_rays;
     st->n_rounds = c->last_rounds;
-    return status_of(c->h_ctr->status);
+    return status_of(c->h_ctr[0].status | c->h_ctr[1].status);
+}
+
+roam_status roam_set_tile_padding(roam_ctx *c, int tiles)
+{
+    ROAM_TRY(set_dev(c));
+    // a multiple of every tensor-core kernel's tiles in flight (4, 2 or 1),
+    // so that every width class's range still starts on a group boundary
+    if (tiles != 0 && (tiles < 4 || tiles > 64 || tiles % 4))
+        return fail(ROAM_ERR_ARG, "tile padding must be 0 or a multiple of 4 in [4, 64]");
+    c->tile_pad = tiles;
+    ++c->gen;                          // a captured render graph holds the old padding
+    return ROAM_OK;
+}
+
+roam_status roam_selftest_wait_timeout(roam_ctx *c, uint64_t limit_ns, int32_t *observed, void *stream)
+{
+    ROAM_TRY(set_dev(c));
+    ROAM_TRY(check_ready(c));
+    if (!observed) return fail(ROAM_ERR_ARG, "null output");
+    if (limit_ns < 1000000ull || limit_ns > 10000000000ull) return fail(ROAM_ERR_ARG, "limit_ns must be in [1e6, 1e10]");
+    if (!all_tc(c, false)) return fail(ROAM_ERR_UNSUPPORTED, "needs the tensor-core MLP of the loaded weights");
+    cudaStream_t s = (cudaStream_t)stream;
+    ROAM_TRY(refresh(c, ROAM_BF16, false, s));
+    // one tile of points of internal field 0 (the first field of width class 0)
+    const int64_t n = 128;
+    ROAM_TRY(ensure(c->selftest, (size_t)(10 * n + n / 2)));
+    ROAM_TRY(ensure(c->sorted, (size_t)n));
+    ROAM_TRY(ensure(c->tiles, tile_capacity(c, (size_t)n)));
+    float *p = c->selftest.p, *d = p + 3 * n, *out = d + 3 * n;
+    uint16_t *keys = reinterpret_cast<uint16_t *>(out + 4 * n);
+    ROAM_CUDA(cudaMemsetAsync(c->selftest.p, 0, (size_t)(10 * n + n / 2) * sizeof(float), s));
+    const BucketBufs b = bucket_of(c);
+    ROAM_CUDA(cudaMemsetAsync(c->aux, 0, sizeof(Counters), s));
+    launch_bucket(nullptr, nullptr, nullptr, (uint32_t)n, 1, 1, keys, c->n_fields, tile_of(ROAM_BF16), b, c->aux,
+                  grid_blocks(c, 2), s, classes_of(c, ROAM_BF16));
+    ROAM_TRY(launched("bucket"));
+    SampleSrc src{};
+    src.mode = 1;
+    src.p = p;
+    src.d = d;
+    MlpWeights w = weights_of(c, 0);
+    w.wait_ns = limit_ns;
+    w.withhold_image = 1;
+    launch_mlp_tc(w, false, src, b, c->aux, reinterpret_cast<float4 *>(out), c->n_sm, s);
+    ROAM_TRY(launched("mlp_tc"));
+    ROAM_CUDA(cudaStreamSynchronize(s));
+    ROAM_CUDA(cudaMemcpy(&c->h_ctr[1], c->aux, sizeof(Counters), cudaMemcpyDeviceToHost));
+    *observed = (int32_t)status_of(c->h_ctr[1].status);
+    // the context stays usable: the self-test's status does not outlive it
+    ROAM_CUDA(cudaMemset(c->aux, 0, sizeof(Counters)));
+    c->last = s;
+    return ROAM_OK;
 }
 
 roam_status roam_profile(roam_ctx *c, int enable)
@@ -1363,11 +1426,12 @@ roam_status roam_march(roam_ctx *c, const roam_camera *cams, int n_views, const 
     mp.delta = opts->delta;
     mp.init = 1;
     mp.flat = 1;
+    mp.accurate = opts->precision == ROAM_F32;      // the ray directions roam_render uses
     mp.st = state_of(c);
     mp.cnt = count;
     mp.recs = recs;
-    mp.ctr = c->ctr;
-    ROAM_CUDA(cudaMemsetAsync(c->ctr, 0, sizeof(Counters), s));
+    mp.ctr = c->aux;
+    ROAM_CUDA(cudaMemsetAsync(c->aux, 0, sizeof(Counters), s));
     launch_march(c->g, mp, march_grid(mp.n_rays), s);
     ROAM_TRY(launched("march"));
     if (c->permuted) {
@@ -1386,12 +1450,12 @@ roam_status roam_bucket(roam_ctx *c, const uint16_t *keys, int64_t n, uint32_t *
     if (n < 0 || n > 0x7fffffff) return fail(ROAM_ERR_ARG, "bad sample count");
     if (!offsets || (n > 0 && (!keys || !perm))) return fail(ROAM_ERR_ARG, "null pointer");
     cudaStream_t s = (cudaStream_t)stream;
-    ROAM_TRY(ensure(c->tiles, tile_capacity((size_t)n, c->n_fields)));
+    ROAM_TRY(ensure(c->tiles, tile_capacity(c, (size_t)n)));
     BucketBufs b = bucket_of(c);
     b.offsets = offsets;
     b.sorted = perm;
-    ROAM_CUDA(cudaMemsetAsync(c->ctr, 0, sizeof(Counters), s));
-    launch_bucket(nullptr, nullptr, nullptr, (uint32_t)n, 1, 1, keys, c->n_fields, 128, b, c->ctr, grid_blocks(c, 2), s,
+    ROAM_CUDA(cudaMemsetAsync(c->aux, 0, sizeof(Counters), s));
+    launch_bucket(nullptr, nullptr, nullptr, (uint32_t)n, 1, 1, keys, c->n_fields, 128, b, c->aux, grid_blocks(c, 2), s,
                   ClassBounds{{0, c->n_fields, c->n_fields, c->n_fields}, {0, 0, 0, 0}});
     c->last = s;
     return launched("bucket");
@@ -1412,9 +1476,9 @@ roam_status roam_mlp_eval(roam_ctx *c, const float *p, const float *d, const uin
     cudaStream_t s = (cudaStream_t)stream;
     ROAM_TRY(refresh(c, precision, false, s));
     ROAM_TRY(ensure(c->sorted, (size_t)n));
-    ROAM_TRY(ensure(c->tiles, tile_capacity((size_t)n, c->n_fields)));
+    ROAM_TRY(ensure(c->tiles, tile_capacity(c, (size_t)n)));
     const BucketBufs b = bucket_of(c);
-    ROAM_CUDA(cudaMemsetAsync(c->ctr, 0, sizeof(Counters), s));
+    ROAM_CUDA(cudaMemsetAsync(c->aux, 0, sizeof(Counters), s));
     const uint16_t *keys = field;
     if (c->permuted) {
         ROAM_TRY(ensure(c->keys_tmp, (size_t)n));
@@ -1422,7 +1486,7 @@ roam_status roam_mlp_eval(roam_ctx *c, const float *p, const float *d, const uin
         ROAM_TRY(launched("field ids"));
         keys = c->keys_tmp.p;
     }
-    launch_bucket(nullptr, nullptr, nullptr, (uint32_t)n, 1, 1, keys, c->n_fields, tile_of(precision), b, c->ctr,
+    launch_bucket(nullptr, nullptr, nullptr, (uint32_t)n, 1, 1, keys, c->n_fields, tile_of(precision), b, c->aux,
                   grid_blocks(c, 2), s, classes_of(c, precision));
     ROAM_TRY(launched("bucket"));
     SampleSrc src{};
@@ -1430,7 +1494,7 @@ roam_status roam_mlp_eval(roam_ctx *c, const float *p, const float *d, const uin
     src.p = p;
     src.d = d;
     c->last = s;
-    return run_mlp(c, precision, src, b, reinterpret_cast<float4 *>(out), s);
+    return run_mlp(c, precision, src, b, reinterpret_cast<float4 *>(out), c->aux, s);
 }
 
 roam_status roam_composite(roam_ctx *c, int64_t n_rays, int n_max, const uint32_t *count, const float *sigma_rgb,
@@ -1502,11 +1566,11 @@ roam_status roam_train_backward(roam_ctx *c, const float *dl_drgb, float *grad, 
                              c->live1.p, s);
     }
     ROAM_TRY(launched("composite_bwd"));
-    ROAM_CUDA(cudaMemsetAsync(c->ctr, 0, sizeof(Counters), s));
+    ROAM_CUDA(cudaMemsetAsync(c->aux, 0, sizeof(Counters), s));
     const BucketBufs b = bucket_of(c);
     {
         ProfScope ps(c, P_BUCKET, s);
-        launch_bucket(c->live1.p, c->recs.p, nullptr, (uint32_t)n, R, 1, nullptr, c->n_fields, 128, b, c->ctr,
+        launch_bucket(c->live1.p, c->recs.p, nullptr, (uint32_t)n, R, 1, nullptr, c->n_fields, 128, b, c->aux,
                       grid_blocks(c, 4), s, c->cb);
     }
     ROAM_TRY(launched("bucket"));
@@ -1524,10 +1588,10 @@ roam_status roam_train_backward(roam_ctx *c, const float *dl_drgb, float *grad, 
     if (!tc) ROAM_TRY(refresh(c, o.precision, true, s));
     if (tc) {
         ProfScope ps(c, P_MLP_BWD_TC, s);
-        launch_mlp_bwd_tc(weights_of(c), src, b, c->ctr, c->gsr.p, grad, c->n_sm, s);
+        launch_mlp_bwd_tc(weights_of(c), src, b, c->aux, c->gsr.p, grad, c->n_sm, s);
     } else {
         ProfScope ps(c, P_MLP_BWD, s);
-        launch_mlp_bwd_simt(weights_of(c), src, b, c->ctr, c->gsr.p, grad, c->n_sm, s);
+        launch_mlp_bwd_simt(weights_of(c), src, b, c->aux, c->gsr.p, grad, c->n_sm, s);
     }
     c->last = s;
     return launched("mlp_bwd");

@@ -90,17 +90,19 @@ __device__ __forceinline__ unsigned long long now_ns()
     return t;
 }
 
-// Waits for the phase of `parity` to complete; gives up after kWaitNs or as
-// soon as another thread has flagged an abort.  Returns false on give-up.
+// Waits for the phase of `parity` to complete; gives up after limit_ns or as
+// soon as another thread has flagged an abort (a drain wait ignores the
+// flag).  Returns false on give-up.
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *abort_flag,
-                                          uint32_t *status, bool drain = false)
+                                          uint32_t *status, bool drain = false,
+                                          unsigned long long limit_ns = kWaitNs)
 {
     if (mbar_try(bar, parity)) return true;
     const unsigned long long t0 = now_ns();
     for (;;) {
         if (mbar_try(bar, parity)) return true;
         if (*abort_flag && !drain) return false;
-        if (now_ns() - t0 > kWaitNs) {
+        if (now_ns() - t0 > limit_ns) {
             *abort_flag = 1;
             atomicOr(status, kStatusTimeout);
             return false;

@@ -7,6 +7,8 @@ import pytest
 
 import fixtures as F
 import oracle as O
+import oracle.parity as P
+from gpu_parity import assert_render, records
 
 pytestmark = pytest.mark.gpu
 
@@ -58,12 +60,12 @@ def test_render_with_assigned_fields(roam, room32, room32_grid):
     r.load_fields(part.field_of_rank, aff)
     w = F.xavier_weights(1, F.ROLE_TEACHER, n, 32, 2)
     r.load_weights(w, 32, 2, room32.sigma_scale)
-    rgb, _, _ = r.render(room32.cams, roam.render_opts(room32.delta, room32.n_max))
+    opts = roam.render_opts(room32.delta, room32.n_max)
+    rgb, _, _ = r.render(room32.cams, opts)
     torch.cuda.synchronize()
     grid = O.Grid(room32.scene, part)
-    ref = O.render(grid, w, aff, 32, 2, room32.sigma_scale, F.camera_array(room32.cams), None, room32.delta,
-                   room32.n_max)
-    tie = (ref["ties"] > 0) | (ref["margin"] < 1e-6)
-    err = np.abs(rgb.cpu().numpy() - ref["rgb"]).max(axis=1)
-    assert err[~tie].max() <= 1e-4
+    cnt, recs = records(r, room32.cams, opts)
+    rep = P.check_render(grid, w, aff, 32, 2, room32.sigma_scale, F.camera_array(room32.cams), None, room32.delta,
+                         room32.n_max, cnt, recs, rgb.cpu().numpy(), tol=1e-4)
+    assert_render(rep)
     r.close()

@@ -12,6 +12,8 @@ import pytest
 
 import fixtures as F
 import oracle as O
+import oracle.parity as P
+from gpu_parity import assert_render, records
 
 pytestmark = pytest.mark.gpu
 
@@ -102,11 +104,11 @@ def test_render_room32_bf16(roam, room32, room32_grid):
     rgb, depth, op = r.render(room32.cams, opts)
     torch.cuda.synchronize()
     r.check()
-    ref = O.render(room32_grid, room32.weights, room32.affine, room32.W, room32.H, room32.sigma_scale,
-                   F.camera_array(room32.cams), None, room32.delta, room32.n_max)
+    cnt, recs = records(r, room32.cams, opts)
     rgb = rgb.cpu().numpy().astype(np.float64)
-    assert _psnr(rgb, ref["rgb"]) >= 40.0
-    assert np.abs(rgb - ref["rgb"]).max() <= 2e-2
+    rep = P.check_render(room32_grid, room32.weights, room32.affine, room32.W, room32.H, room32.sigma_scale,
+                         F.camera_array(room32.cams), None, room32.delta, room32.n_max, cnt, recs, rgb, tol=2e-2)
+    assert_render(rep, psnr_min=40.0, got=rgb)
     r.close()
 
 
@@ -128,11 +130,11 @@ def test_render_floor256_bf16_sampled(roam):
     view = rng.integers(0, 2, n)
     pix = np.array([rng.integers(0, sizes[v]) for v in view])
     rays = np.stack([view, pix], 1).astype(np.uint32)
-    ref = O.render(g, wl.weights, wl.affine, wl.W, wl.H, wl.sigma_scale, F.camera_array(wl.cams), rays,
-                   wl.delta, wl.n_max)
+    cnt, recs = records(r, wl.cams, opts, rays)
     got = rgb.cpu().numpy()[starts[view] + pix].astype(np.float64)
-    assert _psnr(got, ref["rgb"]) >= 40.0
-    assert np.abs(got - ref["rgb"]).max() <= 2e-2
+    rep = P.check_render(g, wl.weights, wl.affine, wl.W, wl.H, wl.sigma_scale, F.camera_array(wl.cams), rays,
+                         wl.delta, wl.n_max, cnt, recs, got, tol=2e-2)
+    assert_render(rep, psnr_min=40.0, got=got)
     r.close()
 
 
@@ -165,12 +167,13 @@ def test_render_room32_width128_bf16(roam, room32, room32_grid):
     rng = np.random.default_rng(128)
     pix = rng.choice(room32.cams[0].n_pixels, 1500, replace=False)
     rays = np.stack([np.zeros_like(pix), pix], 1).astype(np.uint32)
-    ref = O.render(room32_grid, w, room32.affine, W, H, room32.sigma_scale, F.camera_array(room32.cams), rays,
-                   room32.delta, room32.n_max)
+    cams16 = F.camera_array(room32.cams)
+    ref = O.render(room32_grid, w, room32.affine, W, H, room32.sigma_scale, cams16, rays, room32.delta, room32.n_max)
     got = rgb.cpu().numpy()[pix].astype(np.float64)
-    assert _psnr(got, ref["rgb"]) >= 40.0
-    assert np.abs(got - ref["rgb"]).max() <= 2e-2
-    # FP32 SIMT at the same width: <= 1e-4 except the rare certified near-tie ray
-    e32 = np.abs(rgb32.cpu().numpy()[pix] - ref["rgb"]).max(axis=1)
-    assert (e32 > 1e-4).sum() <= 2
+    for prec, out, tol in ((roam.ROAM_BF16, got, 2e-2), (roam.ROAM_F32, rgb32.cpu().numpy()[pix], 1e-4)):
+        cnt, recs = records(r, room32.cams, roam.render_opts(room32.delta, room32.n_max, precision=prec), rays)
+        rep = P.check_render(room32_grid, w, room32.affine, W, H, room32.sigma_scale, cams16, rays, room32.delta,
+                             room32.n_max, cnt, recs, out, tol=tol, ref=ref)
+        # FP32 SIMT at the same width is held to 1e-4 like the W = 32 fields
+        assert_render(rep, psnr_min=40.0 if prec == roam.ROAM_BF16 else None, got=out)
     r.close()

@@ -135,3 +135,37 @@ def test_train_backward_bf16_tensor_cores_floor256(roam):
     assert "mlp_bwd_bf16_tcgen05" in names and "mlp_bwd" in names
     _close(grads[roam.ROAM_BF16], grads[roam.ROAM_F32], "floor256 BF16 vs FP32 adjoint", 8e-2, 0.995)
     r.close()
+
+
+def test_train_backward_bf16_floor256_against_oracle(roam):
+    """The fine-tuning step of the 256^3 floor as the training benchmark runs
+    it (512 W=64/H=3 student fields; targets rendered by the teacher weights
+    plus N(0, 0.01^2) noise; BF16 forward, tensor-core adjoint) on 8192
+    random rays, against the oracle's FP64 analytic gradient of the same
+    loss (no BF16 reading): within 3e-2 of max|g|, cosine >= 0.999."""
+    wl = F.floor256()
+    W, H = wl.W, wl.H
+    g_o = O.Grid(wl.scene, wl.part)
+    cams = F.camera_array(wl.cams)
+    student = F.xavier_weights(2, F.ROLE_STUDENT, wl.part.n_fields, W, H, bias_scale=0.05)
+    rng = np.random.default_rng(41)
+    n = 8192
+    view = rng.integers(0, len(wl.cams), n)
+    pix = np.array([rng.integers(0, wl.cams[v].n_pixels) for v in view])
+    rays_np = np.stack([view, pix], 1).astype(np.uint32)
+    teacher = O.render(g_o, wl.weights, wl.affine, W, H, wl.sigma_scale, cams, rays_np, wl.delta, wl.n_max)
+    target = (teacher["rgb"] + F.rng_for(3, F.ROLE_NOISE).normal(0, 0.01, (n, 3))).astype(np.float32)
+    r = roam.Roam(0)
+    r.load_grid(wl.scene.bits, wl.scene.dims, wl.scene.origin, wl.scene.vox)
+    r.load_fields(wl.part.field_of_rank, wl.affine)
+    r.load_weights(student, W, H, wl.sigma_scale)
+    rays = torch.from_numpy(rays_np.astype(np.int32)).cuda()
+    opts = roam.render_opts(wl.delta, wl.n_max, precision=roam.ROAM_BF16)
+    rgb = r.train_forward(wl.cams, rays, opts)
+    dl = ((2.0 / (3.0 * n)) * (rgb - torch.from_numpy(target).cuda())).contiguous()
+    g = r.train_backward(dl).cpu().numpy().astype(np.float64)
+    r.check()
+    _, go, _, _ = O.loss_grad(g_o, student, wl.affine, W, H, wl.sigma_scale, cams, rays_np, target, wl.delta,
+                              wl.n_max)
+    _close(g, go, "floor256 BF16 adjoint vs oracle FP64", 3e-2, 0.999)
+    r.close()

@@ -1,11 +1,14 @@
 """Parity of the CUDA render path (through the C ABI) with the FP64 oracle.
 
-Integer work (sample indices, field ids, bucketing) is compared bit-exactly;
-the only mismatches allowed are samples the oracle certifies as near-ties
-(a point within 1e-3 voxel of a face whose two sides differ: FP32 and FP64
-may legitimately floor such points differently), and those must stay below
-0.1% of rays.  FP32 colours: <= 1e-4 max abs.  BF16 colours: >= 40 dB PSNR
-and <= 2e-2 max abs."""
+Integer work (sample indices, field ids, bucketing) is compared bit-exactly.
+A ray whose kept-sample list differs from the oracle's must be certified by
+the oracle (every differing sample within 1e-3 voxel of a face whose two
+sides differ), and such rays stay below 0.1% of rays.  Colours are held to
+their bar on EVERY ray: against the oracle's render where the lists agree,
+against the oracle recomputed on the library's own list where they differ
+(oracle.parity).  FP32 colours: <= 1e-4 max abs (plus t_stop where the
+transmittance meets the stopping threshold within 1e-3 in log space).
+BF16 colours: >= 40 dB PSNR and <= 2e-2 max abs."""
 import math
 
 import numpy as np
@@ -13,6 +16,8 @@ import pytest
 
 import fixtures as F
 import oracle as O
+import oracle.parity as P
+from gpu_parity import assert_march, assert_render, records
 
 pytestmark = pytest.mark.gpu
 
@@ -53,67 +58,43 @@ def floor_ctx(roam, floor):
     r.close()
 
 
-def _compare_march(cnt_g, recs_g, cnt_o, js_o, fs_o, ties):
-    """Returns (n_mismatch, n_uncertified)."""
-    n = cnt_o.shape[0]
-    bad = 0
-    uncert = []
-    for r in range(n):
-        c = int(cnt_g[r])
-        same = c == cnt_o[r]
-        if same and c:
-            rg = recs_g[r, :c]
-            same = np.array_equal(rg & 0xFFFF, js_o[r, :c]) and np.array_equal(rg >> 16, fs_o[r, :c])
-        if not same:
-            bad += 1
-            if ties[r] == 0:
-                uncert.append(r)
-    return bad, uncert
-
-
 def test_march_room32_all_pixels(roam, room, room32, room32_grid):
     opts = roam.render_opts(room32.delta, room32.n_max)
-    cnt, recs = room.march(room32.cams, opts)
-    torch.cuda.synchronize()
-    cnt_o, js_o, fs_o, ties = O.march_rays(room32_grid, F.camera_array(room32.cams), None, room32.delta, room32.n_max)
-    bad, uncert = _compare_march(cnt.cpu().numpy(), recs.cpu().numpy(), cnt_o, js_o, fs_o, ties)
-    assert not uncert, f"uncertified mismatches at rays {uncert[:10]}"
-    assert bad <= 0.001 * cnt_o.shape[0]
-    assert cnt_o.sum() > 0
+    cnt, recs = records(room, room32.cams, opts)
+    _, rep, _ = P.check_march(room32_grid, F.camera_array(room32.cams), None, room32.delta, room32.n_max, cnt, recs)
+    assert_march(rep, rep.n)
+    assert cnt.sum() > 0
 
 
-def test_march_ragged_ray_list_and_perspective(roam, room, room32, room32_grid):
+@pytest.mark.parametrize("precision", ["f32", "bf16"])
+def test_march_ragged_ray_list_and_perspective(roam, room, room32, room32_grid, precision):
     cams = [room32.cams[0], F.Camera(F.PERSPECTIVE, 37, 23, 1.3, F.yaw_pitch(0.4, -0.2), room32.cams[0].o)]
     rng = np.random.default_rng(3)
     n = 1001
     view = rng.integers(0, 2, n)
     pix = np.where(view == 0, rng.integers(0, 128 * 64, n), rng.integers(0, 37 * 23, n))
     rays_np = np.stack([view, pix], 1).astype(np.uint32)
-    rays = torch.from_numpy(rays_np.astype(np.int32)).cuda()
-    opts = roam.render_opts(room32.delta, 17)
-    cnt, recs = room.march(cams, opts, rays=rays)
-    torch.cuda.synchronize()
-    cnt_o, js_o, fs_o, ties = O.march_rays(room32_grid, F.camera_array(cams), rays_np, room32.delta, 17)
-    bad, uncert = _compare_march(cnt.cpu().numpy(), recs.cpu().numpy(), cnt_o, js_o, fs_o, ties)
-    assert not uncert and bad <= 0.001 * n + 1
+    prec = roam.ROAM_F32 if precision == "f32" else roam.ROAM_BF16
+    opts = roam.render_opts(room32.delta, 17, precision=prec)
+    cnt, recs = records(room, cams, opts, rays_np)
+    (cnt_o, _, _), rep, _ = P.check_march(room32_grid, F.camera_array(cams), rays_np, room32.delta, 17, cnt, recs)
+    assert_march(rep, n)
     assert (cnt_o == 17).any()       # the cap is exercised
 
 
-def test_march_floor256_sampled(roam, floor_ctx, floor, floor_grid):
+@pytest.mark.parametrize("precision", ["f32", "bf16"])
+def test_march_floor256_sampled(roam, floor_ctx, floor, floor_grid, precision):
     rng = np.random.default_rng(5)
     n = 20000
     view = rng.integers(0, 2, n)
     sizes = [c.n_pixels for c in floor.cams]
     pix = np.array([rng.integers(0, sizes[v]) for v in view])
     rays_np = np.stack([view, pix], 1).astype(np.uint32)
-    rays = torch.from_numpy(rays_np.astype(np.int32)).cuda()
-    opts = roam.render_opts(floor.delta, floor.n_max)
-    cnt, recs = floor_ctx.march(floor.cams, opts, rays=rays)
-    torch.cuda.synchronize()
-    cnt_o, js_o, fs_o, ties = O.march_rays(floor_grid, F.camera_array(floor.cams), rays_np, floor.delta, floor.n_max)
-    bad, uncert = _compare_march(cnt.cpu().numpy(), recs.cpu().numpy(), cnt_o, js_o, fs_o, ties)
-    assert not uncert, f"uncertified mismatches at rays {uncert[:10]}"
-    assert bad <= 0.001 * n
+    prec = roam.ROAM_F32 if precision == "f32" else roam.ROAM_BF16
+    opts = roam.render_opts(floor.delta, floor.n_max, precision=prec)
+    cnt, recs = records(floor_ctx, floor.cams, opts, rays_np)
+    _, rep, _ = P.check_march(floor_grid, F.camera_array(floor.cams), rays_np, floor.delta, floor.n_max, cnt, recs)
+    assert_march(rep, n)
 
 
 @pytest.mark.parametrize("n,which,skew", [(0, "room", False), (1, "room", False), (4096, "room3", False),
@@ -196,19 +177,15 @@ def test_composite_matches_oracle(roam, room):
         c = int(cnt[r_])
         out, u, margin = O.composite(sr[r_, :c, 0], sr[r_, :c, 1:], t[r_, :c], df, O.f32(t_stop),
                                      [O.f32(b) for b in bg])
+        # a transmittance within 1e-4 (log space) of t_stop may stop one
+        # sample either side; that sample weighs at most t_stop
+        extra = 0.0
         if u != used[r_]:
-            assert margin < 1e-4
-            continue
-        assert np.abs(rgb[r_] - out[:3]).max() <= 2e-6
-        assert abs(op[r_] - out[4]) <= 2e-6
-        assert abs(depth[r_] - out[3]) <= 2e-6 * max(1.0, out[3])
-
-
-def _render_compare(rgb_g, ref, tol_rgb):
-    ok = ref["ties"] == 0
-    err = np.abs(rgb_g.astype(np.float64) - ref["rgb"]).max(axis=1)
-    assert (~ok).mean() < 0.1
-    return err, ok
+            assert margin < 1e-4 and abs(int(used[r_]) - u) == 1
+            extra = O.f32(t_stop)
+        assert np.abs(rgb[r_] - out[:3]).max() <= 2e-6 + extra
+        assert abs(op[r_] - out[4]) <= 2e-6 + extra
+        assert abs(depth[r_] - out[3]) <= 2e-6 * max(1.0, out[3]) + extra * float(t[r_, :c].max(initial=0.0))
 
 
 def test_render_room32_f32(roam, room, room32, room32_grid):
@@ -216,16 +193,11 @@ def test_render_room32_f32(roam, room, room32, room32_grid):
     rgb, depth, op = room.render(room32.cams, opts)
     torch.cuda.synchronize()
     room.check()
-    ref = O.render(room32_grid, room32.weights, room32.affine, room32.W, room32.H, room32.sigma_scale,
-                   F.camera_array(room32.cams), None, room32.delta, room32.n_max)
-    rgb = rgb.cpu().numpy()
-    err, ok = _render_compare(rgb, ref, 1e-4)
-    # rays whose march was certified exact must match to 1e-4
-    bad = np.nonzero((err > 1e-4) & ok)[0]
-    assert bad.size <= 0.001 * err.size, (bad[:10], err[bad[:10]])
-    assert np.abs(op.cpu().numpy() - ref["opacity"])[ok].max() <= 1e-4
-    d_err = np.abs(depth.cpu().numpy() - ref["depth"])[ok]
-    assert d_err.max() <= 1e-4 * max(1.0, np.abs(ref["depth"]).max())
+    cnt, recs = records(room, room32.cams, opts)
+    rep = P.check_render(room32_grid, room32.weights, room32.affine, room32.W, room32.H, room32.sigma_scale,
+                         F.camera_array(room32.cams), None, room32.delta, room32.n_max, cnt, recs,
+                         rgb.cpu().numpy(), depth.cpu().numpy(), op.cpu().numpy(), tol=1e-4)
+    assert_render(rep, depth_tol=1e-4 * max(1.0, float(np.abs(depth.cpu().numpy()).max())), opacity_tol=1e-4)
 
 
 def test_render_round_schedule_is_invisible(roam, room, room32):
@@ -310,13 +282,12 @@ def test_render_floor256_f32_sampled(roam, floor_ctx, floor, floor_grid):
     view = rng.integers(0, 2, n)
     pix = np.array([rng.integers(0, sizes[v]) for v in view])
     rays = np.stack([view, pix], 1).astype(np.uint32)
-    ref = O.render(floor_grid, floor.weights, floor.affine, floor.W, floor.H, floor.sigma_scale,
-                   F.camera_array(floor.cams), rays, floor.delta, floor.n_max)
+    cnt, recs = records(floor_ctx, floor.cams, opts, rays)
     gi = starts[view] + pix
-    rgb_g = rgb.cpu().numpy()[gi]
-    err, ok = _render_compare(rgb_g, ref, 1e-4)
-    bad = np.nonzero((err > 1e-4) & ok)[0]
-    assert bad.size <= 0.001 * n, (bad[:10], err[bad[:10]])
+    rep = P.check_render(floor_grid, floor.weights, floor.affine, floor.W, floor.H, floor.sigma_scale,
+                         F.camera_array(floor.cams), rays, floor.delta, floor.n_max, cnt, recs,
+                         rgb.cpu().numpy()[gi], depth.cpu().numpy()[gi], op.cpu().numpy()[gi], tol=1e-4)
+    assert_render(rep, depth_tol=1e-4 * max(1.0, float(np.abs(depth.cpu().numpy()[gi]).max())), opacity_tol=1e-4)
 
 
 def test_errors_are_reported(roam, room, room32):

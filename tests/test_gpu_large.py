@@ -3,13 +3,14 @@ configuration the benchmark times: 4096 kd fields of W=128/H=4 MLPs, one
 2048x1024 equirectangular view, <= 192 samples per ray.  Sampled pixels
 against the FP64 oracle: BF16 >= 40 dB PSNR and <= 2e-2 max abs; FP8
 against the oracle's FP8 reading by the same bars (and within 0.1 of the
-FP64 colours); the rays that the oracle certifies as near-ties are left
-out of the max."""
+FP64 colours), every ray under the render parity rule (oracle.parity)."""
 import numpy as np
 import pytest
 
 import fixtures as F
 import oracle as O
+import oracle.parity as P
+from gpu_parity import assert_render, records
 
 pytestmark = pytest.mark.gpu
 
@@ -40,18 +41,21 @@ def test_floor512_bf16_and_fp8_sampled(roam):
     cams = F.camera_array(wl.cams)
     ref = O.render(g, wl.weights, wl.affine, wl.W, wl.H, wl.sigma_scale, cams, rays, wl.delta, wl.n_max)
     ref8 = O.render(g, wl.weights, wl.affine, wl.W, wl.H, wl.sigma_scale, cams, rays, wl.delta, wl.n_max, quant=1)
-    ok = (ref["ties"] == 0) & (ref["margin"] >= 1e-6)
-    assert ok.mean() > 0.9
     gi = rays[:, 1].astype(np.int64)
-    for prec, rr in ((roam.ROAM_BF16, ref), (roam.ROAM_FP8, ref8)):
-        rgb, _, _ = r.render(wl.cams, roam.render_opts(wl.delta, wl.n_max, precision=prec))
+    for prec, rr, quant in ((roam.ROAM_BF16, ref, 0), (roam.ROAM_FP8, ref8, 1)):
+        opts = roam.render_opts(wl.delta, wl.n_max, precision=prec)
+        rgb, _, _ = r.render(wl.cams, opts)
         torch.cuda.synchronize()
         r.check()
         got = rgb.cpu().numpy()[gi].astype(np.float64)
-        assert _psnr(got, rr["rgb"]) >= 40.0, prec
-        assert np.abs(got - rr["rgb"])[ok].max() <= 2e-2, prec
+        cnt, recs = records(r, wl.cams, opts, rays)
+        rep = P.check_render(g, wl.weights, wl.affine, wl.W, wl.H, wl.sigma_scale, cams, rays, wl.delta, wl.n_max,
+                             cnt, recs, got, tol=2e-2, quant=quant, ref=rr)
+        assert_render(rep, psnr_min=40.0, got=got)
         if prec == roam.ROAM_FP8:
-            assert np.abs(got - ref["rgb"])[ok].max() <= 0.1
+            rep64 = P.check_render(g, wl.weights, wl.affine, wl.W, wl.H, wl.sigma_scale, cams, rays, wl.delta,
+                                   wl.n_max, cnt, recs, got, tol=0.1, ref=ref)
+            assert rep64.over.size == 0, rep64.summary()
     st = r.get_stats()
     assert st.n_rounds >= 1 and st.n_used > 0
     r.close()

@@ -10,6 +10,8 @@ import pytest
 
 import fixtures as F
 import oracle as O
+import oracle.parity as P
+from gpu_parity import assert_render, records
 
 pytestmark = pytest.mark.gpu
 
@@ -165,12 +167,18 @@ def test_adam_matches_oracle_and_refreshes_copies(roam, room32, room32_grid):
     new_w = wg.reshape(w.shape).astype(np.float32)
     ref = O.render(room32_grid, new_w, room32.affine, W, H, room32.sigma_scale, F.camera_array(room32.cams), None,
                    room32.delta, room32.n_max)
-    ok = ref["ties"] == 0
+    cams16 = F.camera_array(room32.cams)
+
+    def parity(prec, rgb, tol, rr, quant=0):
+        cnt, recs = records(r, room32.cams, roam.render_opts(room32.delta, room32.n_max, precision=prec))
+        rep = P.check_render(room32_grid, new_w, room32.affine, W, H, room32.sigma_scale, cams16, None, room32.delta,
+                             room32.n_max, cnt, recs, rgb, tol=tol, quant=quant, ref=rr)
+        assert_render(rep)
+
     for prec, tol in ((roam.ROAM_F32, 1e-4), (roam.ROAM_BF16, 2e-2)):
         rgb, _, _ = r.render(room32.cams, roam.render_opts(room32.delta, room32.n_max, precision=prec))
         torch.cuda.synchronize()
-        err = np.abs(rgb.cpu().numpy() - ref["rgb"])[ok].max()
-        assert err <= tol, (prec, err)
+        parity(prec, rgb.cpu().numpy(), tol, ref)
     # the BF16 images that Adam refreshes in place equal a fresh packing of
     # the updated masters: bit-identical renders
     r2 = _ctx(roam, room32, new_w, W, H)
@@ -185,7 +193,7 @@ def test_adam_matches_oracle_and_refreshes_copies(roam, room32, room32_grid):
                     room32.delta, room32.n_max, quant=1)
     rgb8, _, _ = r.render(room32.cams, roam.render_opts(room32.delta, room32.n_max, precision=roam.ROAM_FP8))
     torch.cuda.synchronize()
-    assert np.abs(rgb8.cpu().numpy() - ref8["rgb"])[ok].max() <= 2e-2
+    parity(roam.ROAM_FP8, rgb8.cpu().numpy(), 2e-2, ref8, quant=1)
     # the row-padded copy of the FP32 adjoint, rebuilt at its first launch
     rays_np = _rays(room32, 1024, 23)
     target = np.random.default_rng(24).uniform(0, 1, (1024, 3)).astype(np.float32)

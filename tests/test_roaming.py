@@ -45,3 +45,45 @@ def test_stereo_loop_graph_frames_match_plain_renders(room32):
     assert torch.equal(lt, l_ref) and torch.equal(rt, r_ref)
     assert not torch.equal(lt, rt)
     r.close()
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("which,prec", [("room32", "bf16"), ("room32", "f32"), ("floor256", "bf16")])
+def test_stereo_frame_matches_oracle(room32, which, prec):
+    """Both eyes of the last frame of a graph-replayed walk against the FP64
+    oracle under the render parity rule (oracle.parity): the room's 96x64
+    eye pair on every pixel, the eight-room floor's 1280x720 pair (the
+    benchmark's eyes) on 3000 sampled pixels."""
+    torch = pytest.importorskip("torch")
+    import oracle as O
+    import oracle.parity as P
+    from gpu_parity import assert_render, records
+    import paper_2208_02705_gb300 as roam
+    from paper_2208_02705_gb300 import build
+    build.build()
+    wl = room32 if which == "room32" else F.floor256(views="equirect")
+    size = (96, 64) if which == "room32" else (1280, 720)
+    r = roam.Roam(0)
+    r.load_workload(wl)
+    poses = F.roaming_path(wl.scene, 1 if which == "room32" else 2, 4, width=size[0], height=size[1])
+    p = roam.ROAM_BF16 if prec == "bf16" else roam.ROAM_F32
+    opts = roam.render_opts(wl.delta, wl.n_max, precision=p)
+    gopts = roam.render_opts(wl.delta, wl.n_max, precision=p, use_graph=True)
+    _, (lt, rt) = roam_frames(r, poses, gopts)
+    eyes = list(stereo_pair(poses[-1]))
+    got_all = torch.cat([lt, rt]).cpu().numpy().astype(np.float64)
+    n_eye = size[0] * size[1]
+    if which == "room32":
+        rays = None
+        got = got_all
+    else:
+        rng = np.random.default_rng(720)
+        view = rng.integers(0, 2, 3000)
+        rays = np.stack([view, rng.integers(0, n_eye, 3000)], 1).astype(np.uint32)
+        got = got_all[view * n_eye + rays[:, 1].astype(np.int64)]
+    cnt, recs = records(r, eyes, opts, rays)
+    g = O.Grid(wl.scene, wl.part)
+    rep = P.check_render(g, wl.weights, wl.affine, wl.W, wl.H, wl.sigma_scale, F.camera_array(eyes), rays, wl.delta,
+                         wl.n_max, cnt, recs, got, tol=2e-2 if prec == "bf16" else 1e-4)
+    assert_render(rep, psnr_min=40.0 if prec == "bf16" else None, got=got)
+    r.close()

@@ -99,3 +99,41 @@ def test_static_bucket_limits_and_edges(roam):
     assert o[-1] == keys.size and o[1] == 1 and o[n_fields - 1] == n_fields - 1
     p = p.cpu().numpy().astype(np.int64)
     assert np.array_equal(np.sort(p), np.arange(keys.size))
+
+
+def test_static_bucket_drops_ids_beyond_n_fields_and_keeps_the_rest(roam):
+    """Ids >= n_fields are dropped: offsets[n_fields] counts the kept samples,
+    the kept ones are grouped as usual, and perm past the kept count is left
+    as it was."""
+    n_fields = 100
+    rng = np.random.default_rng(7)
+    keys = rng.integers(0, 130, 5000)
+    perm, off = _static_bucket(roam, torch.from_numpy(keys.astype(np.int16)).cuda(), n_fields)
+    torch.cuda.synchronize()
+    off = off.cpu().numpy().astype(np.int64)
+    perm = perm.cpu().numpy().astype(np.int64)
+    kept = keys < n_fields
+    assert off[-1] == kept.sum()
+    assert np.array_equal(off, np.concatenate([[0], np.cumsum(np.bincount(keys[kept], minlength=n_fields))]))
+    assert np.array_equal(np.sort(perm[:off[-1]]), np.nonzero(kept)[0])
+    assert (perm[off[-1]:] == -1).all()
+
+
+def test_static_bucket_allocates_no_device_memory(roam):
+    """Repeated calls with caller-owned buffers leave the device's free
+    memory exactly as it was (after a first call that looked the scratch
+    array up)."""
+    n_fields = 300
+    keys = torch.from_numpy(np.random.default_rng(9).integers(0, n_fields, 100000).astype(np.int16)).cuda()
+    perm = torch.empty(keys.shape[0], dtype=torch.int32, device="cuda")
+    off = torch.empty(n_fields + 1, dtype=torch.int32, device="cuda")
+    L = roam.load_library()
+    s = torch.cuda.current_stream().cuda_stream
+    assert L.roam_bucket_static(keys.data_ptr(), keys.shape[0], n_fields, perm.data_ptr(), off.data_ptr(), s) == 0
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    for _ in range(20):
+        assert L.roam_bucket_static(keys.data_ptr(), keys.shape[0], n_fields, perm.data_ptr(), off.data_ptr(), s) == 0
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
