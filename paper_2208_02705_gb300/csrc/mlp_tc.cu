@@ -36,6 +36,84 @@ namespace roam {
 
 namespace {
 
+// Packs e[first .. first + n) into the MMA's A words (BF16: elements 2c and
+// 2c + 1 in word c, low half first; E4M3: elements 4c .. 4c + 3 in word c);
+// the words whose elements all lie in that range.
+template <bool F8, int NW>
+__device__ __forceinline__ void pack_range(const float *e, uint32_t (&w)[NW], int first, int n)
+{
+    constexpr int per = F8 ? 4 : 2;
+#pragma unroll
+    for (int c = 0; c < NW; ++c) {
+        if (c * per < first || c * per + per > first + n) continue;
+        if constexpr (F8) w[c] = pack_e4m3x4(e[4 * c], e[4 * c + 1], e[4 * c + 2], e[4 * c + 3]);
+        else w[c] = pack_bf16(e[2 * c], e[2 * c + 1]);
+    }
+}
+
+// A block of the encoding F(v) = [v, sin(2^k pi v), cos(2^k pi v)] (k < L,
+// three sines then three cosines per k), frequency after frequency so that
+// each word is packed as soon as its elements exist (few live registers).
+// Layout: `lead` leading constant-1 elements, then F(v) (3 + 6 L), then
+// `trail_one` constant 1, then zeros up to 32 * NB elements.
+template <bool F8, int L, int kLead, bool kTrailOne, int NE>
+__device__ __forceinline__ void encode_packed(const float (&v)[3], uint32_t (&w)[F8 ? NE / 4 : NE / 2])
+{
+    constexpr int NW = F8 ? NE / 4 : NE / 2;
+    float e[NE];
+#pragma unroll
+    for (int q = 0; q < NE; ++q) e[q] = 0.f;
+#pragma unroll
+    for (int q = 0; q < kLead; ++q) e[q] = 1.0f;
+    e[kLead] = v[0]; e[kLead + 1] = v[1]; e[kLead + 2] = v[2];
+    if (kTrailOne) e[kLead + 3 + 6 * L] = 1.0f;
+    float sp[3], cp[3];
+#pragma unroll
+    for (int k = 0; k < L; ++k) {
+        // direct evaluation at k = 0 and k = 5, angle doubling in between
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            float sn, cs;
+            if (k == 0 || k == 5) {
+                sincospi_fast(v[a] * (float)(1 << k), sn, cs);
+            } else {
+                sn = 2.0f * sp[a] * cp[a];
+                cs = fmaf(-2.0f * sp[a], sp[a], 1.0f);
+            }
+            sp[a] = sn;
+            cp[a] = cs;
+            e[kLead + 3 + 6 * k + a] = sn;
+            e[kLead + 6 + 6 * k + a] = cs;
+        }
+        pack_range<F8, NW>(e, w, 0, kLead + 9 + 6 * k);
+    }
+    pack_range<F8, NW>(e, w, 0, NE);
+}
+
+__device__ __forceinline__ uint32_t tmem_ld1(uint32_t taddr)
+{
+    uint32_t r;
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x1.b32 {%0}, [%1];" : "=r"(r) : "r"(taddr));
+    return r;
+}
+
+// 32 (BF16: 16 words, two x8 stores; E4M3: 8 words, one x8 store) ... of A
+template <bool F8>
+__device__ __forceinline__ void st_words32(uint32_t tArow, int c, const uint32_t *w)
+{
+    if constexpr (F8) {
+        uint32_t o[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) o[q] = w[q];
+        tmem_st8(tArow + 8 * c, o);
+    } else {
+        uint32_t o[16];
+#pragma unroll
+        for (int q = 0; q < 16; ++q) o[q] = w[q];
+        tmem_st16(tArow + 16 * c, o);
+    }
+}
+
 // Persistent kernel, one CTA per SM, kSlots tiles in flight.  Slot s is
 // warpgroup s: its 128 threads encode and run the epilogues of their tile
 // (one row each), and its first thread issues the tile's MMAs itself --
@@ -164,26 +242,11 @@ __global__ void __launch_bounds__(TcShape<W, H, F8>::kSlots * 128, 1)
         {
             const float xl[3] = {fmaf(__ldg(aff + 0), sm.px, __ldg(aff + 3)), fmaf(__ldg(aff + 1), sm.py, __ldg(aff + 4)),
                                  fmaf(__ldg(aff + 2), sm.pz, __ldg(aff + 5))};
-            float e[64];
-            e[0] = xl[0]; e[1] = xl[1]; e[2] = xl[2];
-#pragma unroll
-            for (int a = 0; a < 3; ++a) {
-                float sn[10], cs[10];
-                encode1<10>(xl[a], sn, cs);
-#pragma unroll
-                for (int k = 0; k < 10; ++k) {
-                    e[3 + 6 * k + a] = sn[k];
-                    e[6 + 6 * k + a] = cs[k];
-                }
-            }
-            e[63] = 1.0f;        // rows past the tile's count compute garbage that is never stored
-#pragma unroll
-            for (int c = 0; c < 2; ++c) {
-                float v[32];
-#pragma unroll
-                for (int q = 0; q < 32; ++q) v[q] = e[32 * c + q];
-                st_act32<F8, false>(tArow, c, v);
-            }
+            // rows past the tile's count compute garbage that is never stored
+            uint32_t w[F8 ? 16 : 32];
+            encode_packed<F8, 10, 0, true, 64>(xl, w);
+            st_words32<F8>(tArow, 0, w);
+            st_words32<F8>(tArow, 1, w + (F8 ? 8 : 16));
         }
         // the next tile's gathers overlap this tile's layers
         stage_index(pend, b, tl, row, g + 1 < g1);
@@ -210,7 +273,7 @@ __global__ void __launch_bounds__(TcShape<W, H, F8>::kSlots * 128, 1)
                     const uint32_t idesc = F8 ? idesc_e4m3(N) : idesc_bf16(N);
                     const uint32_t ba = imga + S::offset(l);
                     // one MMA per 32 bytes of K: 4 per 128-byte chunk, 8 TMEM columns of A each
-#pragma unroll 1
+#pragma unroll 4
                     for (int ks = 0; ks < K / S::kKS; ++ks) {
                         const int ch = ks >> 2, kin = ks & 3;
                         umma_ta<F8>(tslot, tA + (uint32_t)(ks * 8), sdesc(ba + ch * N * 128 + kin * 32), idesc,
@@ -230,27 +293,28 @@ __global__ void __launch_bounds__(TcShape<W, H, F8>::kSlots * 128, 1)
                 continue;
             }
             tc_fence_after();
-            uint32_t r[W / 16][16];
-#pragma unroll
-            for (int c = 0; c < W / 16; ++c) tmem_ld16_nowait(trow + 16 * c, r[c]);
-            uint32_t rs[16];
-            if (l == H) tmem_ld16_nowait(trow + W, rs);
-            tmem_wait_ld();
-            tc_fence_before();
             // the FP32 per-layer table, where this layer's epilogue uses it
             const bool use_tab = S::kTab && (F8 || (l >= 1 && l <= H));
             const float *tsc = tab + l * 2 * S::kTabStride, *tbi = tsc + S::kTabStride;
-            if (use_tab && !img_seen) {
+            if ((use_tab || l == H + 1) && !img_seen) {
                 mbar_wait(&bar_w, (n_changes - 1) & 1u, abortp, status, false, wait_ns);
                 img_seen = true;
             }
             if (l < H + 1) {
-                // next activations: head features stay linear, every other layer ReLU
+                // next activations, 32 columns at a time (few live registers):
+                // head features stay linear, every other layer ReLU
 #pragma unroll
                 for (int c = 0; c < W / 32; ++c) {
+                    uint32_t r0[16], r1[16];
+                    tmem_ld16_nowait(trow + 32 * c, r0);
+                    tmem_ld16_nowait(trow + 32 * c + 16, r1);
+                    tmem_wait_ld();
                     float v[32];
 #pragma unroll
-                    for (int q = 0; q < 32; ++q) v[q] = __uint_as_float(r[(32 * c + q) >> 4][(32 * c + q) & 15]);
+                    for (int q = 0; q < 16; ++q) {
+                        v[q] = __uint_as_float(r0[q]);
+                        v[16 + q] = __uint_as_float(r1[q]);
+                    }
                     if constexpr (S::kTab) {
                         if (use_tab) {
 #pragma unroll
@@ -273,41 +337,29 @@ __global__ void __launch_bounds__(TcShape<W, H, F8>::kSlots * 128, 1)
                 }
                 if (l == H) {
                     // density from column W of the head
-                    float sl = __uint_as_float(rs[0]);
+                    float sl = __uint_as_float(tmem_ld1(trow + W));
+                    tmem_wait_ld();
                     if (use_tab) sl = F8 ? fmaf(sl, tsc[W], tbi[W]) : sl + tbi[W];
                     sigma = sig_scale * (act == ROAM_RELU ? fmaxf(sl, 0.f) : softplus_f(sl));
                 }
                 if (l == 0) {
                     // tail of A from here on: [1 | F(d) | 0 0 0 0] at columns W .. W+31
-                    float e[32];
-                    e[0] = 1.0f;
                     const float dv[3] = {sm.dx, sm.dy, sm.dz};
-                    e[1] = dv[0]; e[2] = dv[1]; e[3] = dv[2];
-#pragma unroll
-                    for (int a = 0; a < 3; ++a) {
-                        float sn[4], cs[4];
-                        encode1<4>(dv[a], sn, cs);
-#pragma unroll
-                        for (int k = 0; k < 4; ++k) {
-                            e[4 + 6 * k + a] = sn[k];
-                            e[7 + 6 * k + a] = cs[k];
-                        }
-                    }
-                    e[28] = e[29] = e[30] = e[31] = 0.f;
-                    st_act32<F8, false>(tArow, W / 32, e);
+                    uint32_t w[F8 ? 8 : 16];
+                    encode_packed<F8, 4, 1, false, 32>(dv, w);
+                    st_words32<F8>(tArow, W / 32, w);
                 }
             } else {
                 // colour layer: g = relu(z) in FP32, then rgb = sigmoid(Wo g + bo) with
                 // the FP32 output table at the end of the shared image (this thread
-                // waits for the image itself before reading it with generic loads)
-                if (!img_seen) {
-                    mbar_wait(&bar_w, (n_changes - 1) & 1u, abortp, status, false, wait_ns);
-                    img_seen = true;
-                }
+                // has waited for the image itself before reading it with generic loads)
                 const float4 *wo = reinterpret_cast<const float4 *>(IMG + S::kMatBytes);
                 float4 acc = wo[W];
 #pragma unroll
                 for (int c = 0; c < W / 16; ++c) {
+                    uint32_t r[16];
+                    tmem_ld16_nowait(trow + 16 * c, r);
+                    tmem_wait_ld();
                     float sc[16], bi[16];
 #pragma unroll
                     for (int q = 0; q < 16; ++q) { sc[q] = 1.f; bi[q] = 0.f; }
@@ -322,7 +374,7 @@ __global__ void __launch_bounds__(TcShape<W, H, F8>::kSlots * 128, 1)
                     }
 #pragma unroll
                     for (int q = 0; q < 16; ++q) {
-                        const float z = __uint_as_float(r[c][q]);
+                        const float z = __uint_as_float(r[q]);
                         const float gk = fmaxf(F8 ? fmaf(z, sc[q], bi[q]) : z, 0.f);
                         const float4 wk = wo[16 * c + q];
                         acc.x = fmaf(wk.x, gk, acc.x);
@@ -332,6 +384,7 @@ __global__ void __launch_bounds__(TcShape<W, H, F8>::kSlots * 128, 1)
                 }
                 if (valid) out[sm.idx] = make_float4(sigma, sigmoid_f(acc.x), sigmoid_f(acc.y), sigmoid_f(acc.z));
             }
+            tc_fence_before();
             if (l == 0) stage_record(pend, src);
             if (l == 1) stage_ray(pend, src);
         }

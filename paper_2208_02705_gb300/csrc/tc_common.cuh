@@ -283,8 +283,11 @@ __device__ __forceinline__ void encode1(float v, float (&s)[L], float (&c)[L])
     }
 }
 
-__device__ __forceinline__ float softplus_f(float s) { return s > 20.f ? s : log1pf(__expf(s)); }
-__device__ __forceinline__ float sigmoid_f(float s) { return 1.f / (1.f + __expf(-s)); }
+// log(1 + e^s) and 1 / (1 + e^-s) with the hardware exp2/log2 and the fast
+// division (a few units of 2^-22 absolute: far inside the BF16/FP8 outputs'
+// rounding); softplus(s) = s past s = 15 (the difference is below 4e-7)
+__device__ __forceinline__ float softplus_f(float s) { return s > 15.f ? s : __logf(1.f + __expf(s)); }
+__device__ __forceinline__ float sigmoid_f(float s) { return __fdividef(1.f, 1.f + __expf(-s)); }
 
 // Named barrier over n threads that also ORs a flag across them: every
 // participant gets the same answer, so an abort leaves all of them together.

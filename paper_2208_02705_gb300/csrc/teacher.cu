@@ -583,7 +583,9 @@ __global__ void __launch_bounds__(256) k_teacher_simt(const float *__restrict__ 
                 for (int k = 0; k < kTC; ++k)
                     for (int c = 0; c < 3; ++c) z[c] = fmaf(X[q][k], Wo[3 * k + c], z[c]);
                 const int64_t i = base + q;
-                if (i < n) out[i] = make_float4(sig[q], sigmoid_f(z[0]), sigmoid_f(z[1]), sigmoid_f(z[2]));
+                if (i < n)
+                    out[i] = make_float4(sig[q], 1.f / (1.f + expf(-z[0])), 1.f / (1.f + expf(-z[1])),
+                                         1.f / (1.f + expf(-z[2])));
             }
         }
         __syncthreads();
