@@ -384,13 +384,14 @@ def multiview_bench(roam, F, torch, args, stream, flush):
     r = roam.Roam(torch.cuda.current_device())
     r.load_workload(wl)
     base = roam.render_opts(wl.delta, wl.n_max, precision=roam.ROAM_BF16)
-    R, tune_ms = r.tune_round_size(wl.cams, base, stream=stream)
-    opts = roam.render_opts(wl.delta, wl.n_max, precision=roam.ROAM_BF16, round_size=R)
-    gopts = roam.render_opts(wl.delta, wl.n_max, precision=roam.ROAM_BF16, round_size=R, use_graph=True)
+    R, R0, tune_ms = r.tune_round_size(wl.cams, base, stream=stream)
+    opts = roam.render_opts(wl.delta, wl.n_max, precision=roam.ROAM_BF16, round_size=R, first_round_size=R0)
+    gopts = roam.render_opts(wl.delta, wl.n_max, precision=roam.ROAM_BF16, round_size=R, first_round_size=R0,
+                             use_graph=True)
     steps = max(3, args.steps // 2)
     out = {"workload": "floor384_kd2048_mixed_w32_64_128_h3, 32 views (24 equirect 512x256..2048x1024, "
                        "8 perspective 1280x720)", "rays_per_batch": int(sum(c.n_pixels for c in wl.cams)),
-           "round_size_tuned": R, "tuned_render_ms": tune_ms}
+           "round_size_tuned": R, "first_round_size_tuned": R0, "tuned_render_ms": tune_ms}
     for _ in range(2):
         r.render(wl.cams, gopts, stream=stream)
     tot_g, per_g = time_steps(r, wl.cams, gopts, steps, 0, flush, stream)
@@ -626,6 +627,9 @@ def main():
     ap.add_argument("--views", default="both", choices=["both", "equirect", "perspective"])
     ap.add_argument("--precision", default=None, choices=["bf16", "f32"],
                     help="with --quick: the arithmetic of the timed loop (default BF16 tensor cores)")
+    ap.add_argument("--rounds", default=None,
+                    help="FIRST,LATER: round sizes of the headline render instead of the library's tuner "
+                         "(profilers use it for a fixed launch sequence)")
     ap.add_argument("--section", default=None, choices=["train", "distill"],
                     help="run one secondary section alone and print its JSON (for profilers)")
     args = ap.parse_args()
@@ -672,7 +676,13 @@ def main():
             head_prec, dtype = roam.ROAM_BF16, "bf16"
         except roam.RoamError:
             head_prec, dtype = roam.ROAM_F32, "f32"
-    opts = roam.render_opts(wl.delta, wl.n_max, precision=head_prec)
+    # round sizes from the library's tuner (set-up, before the timed region)
+    if args.rounds:
+        R0, R = (int(x) for x in args.rounds.split(","))
+    else:
+        R, R0, _ = r.tune_round_size(wl.cams, roam.render_opts(wl.delta, wl.n_max, precision=head_prec),
+                                     stream=stream)
+    opts = roam.render_opts(wl.delta, wl.n_max, precision=head_prec, round_size=R, first_round_size=R0)
 
     # ---- headline: K timed steps, event-timed per-kernel record on ----
     for _ in range(args.warmup):
@@ -706,7 +716,8 @@ def main():
         if rank == 0:
             print(json.dumps({"quick": True, "metric": METRIC, "value": value, "unit": UNIT, "dtype": dtype,
                               "ms_per_step": ms_per_step, "views": views, "kernels": prof, "clocks": clocks,
-                              "evaluated_per_step": int(evaluated_per_step), "rounds": int(st.n_rounds)}),
+                              "evaluated_per_step": int(evaluated_per_step), "rounds": int(st.n_rounds),
+                              "round_sizes": [R0, R]}),
                   flush=True)
         r.close()
         return 0
@@ -817,7 +828,8 @@ def main():
                 "vs_baseline": None, "dtype": dtype, "data": "synthetic (seeded generators)",
                 "config": workload_config(wl, views),
                 "samples_per_step": {"composited": int(used_per_step), "evaluated": int(evaluated_per_step),
-                                     "rays": int(st.n_rays), "rounds": int(st.n_rounds)},
+                                     "rays": int(st.n_rays), "rounds": int(st.n_rounds),
+                                     "round_sizes_tuned": {"first": R0, "later": R}},
                 "frame_ms": frame,
                 "fp32_simt": {"value": f32_value, "unit": UNIT, "ms_per_step": t32 / max(3, args.steps // 2)},
                 "accuracy_vs_oracle": acc, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,

@@ -102,6 +102,10 @@ typedef struct {
     int32_t use_graph;    /* 1: roam_render captures its launch sequence into a CUDA graph
                              (once per configuration: view sizes, options, output pointers)
                              and replays it on later calls; 0: plain launches */
+    int32_t first_round_size; /* kept samples marched per ray in the first round (at most
+                             round_size), 0 = round_size.  The render's result does not
+                             depend on the round sizes; the work does: samples marched past
+                             a ray's termination within a round are evaluated for nothing */
 } roam_render_opts;
 
 /* Counters of the last render / training forward (read with a sync). */
@@ -276,15 +280,18 @@ roam_status roam_distill_loss(roam_ctx *ctx, const float *student, const float *
 roam_status roam_mlp_backward(roam_ctx *ctx, const float *p, const float *d, const uint16_t *field, int64_t n,
                               int precision, const float *dl_dout, float *grad, void *stream);
 
-/* Chooses the round size (kept samples marched per live ray per round) for
+/* Chooses the round sizes (kept samples marched per live ray per round) for
  * this camera batch and these options: renders the batch once per candidate
- * (4, 8, 16, ... up to n_max, while the workspace fits in half the free
- * device memory and slot ids in 32 bits) after one warm-up render each,
- * timing with CUDA events on `stream`, and returns the fastest in
- * *best_round_size (its time in *best_ms, may be NULL).  Pass it back as
- * roam_render_opts.round_size.  Synchronous. */
+ * round size (4, 8, 16, ... up to n_max, while the workspace fits in half
+ * the free device memory and slot ids in 32 bits), then, with the fastest,
+ * once per smaller first-round size (4, 8, ...), each after one warm-up
+ * render, timing with CUDA events on `stream`.  Returns the fastest pair in
+ * *best_round_size and *best_first_round_size (may be NULL), its time in
+ * *best_ms (may be NULL).  Pass them back as roam_render_opts.round_size and
+ * .first_round_size.  Synchronous. */
 roam_status roam_tune_round_size(roam_ctx *ctx, const roam_camera *cams, int n_views, const roam_render_opts *opts,
-                                 int32_t *best_round_size, float *best_ms, void *stream);
+                                 int32_t *best_round_size, int32_t *best_first_round_size, float *best_ms,
+                                 void *stream);
 
 /* Counters of the last roam_render / roam_train_forward (synchronises); the
  * single-step entry points and the backward passes keep counters of their

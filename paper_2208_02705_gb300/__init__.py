@@ -68,7 +68,7 @@ def occ_params(p_hit: float = 0.7, p_miss: float = 0.4, l_min: float = -2.0, l_m
 class roam_render_opts(ctypes.Structure):
     _fields_ = [("delta", ctypes.c_float), ("n_max", ctypes.c_int32), ("t_stop", ctypes.c_float),
                 ("bg", ctypes.c_float * 3), ("precision", ctypes.c_int32), ("round_size", ctypes.c_int32),
-                ("use_graph", ctypes.c_int32)]
+                ("use_graph", ctypes.c_int32), ("first_round_size", ctypes.c_int32)]
 
 
 class roam_stats(ctypes.Structure):
@@ -107,7 +107,7 @@ def load_library(path: str = LIB_PATH):
     L.roam_load_fields.argtypes = [vp, i32, vp, i64, vp, i32]
     L.roam_load_weights.argtypes = [vp, P(roam_mlp_desc), vp, i32]
     L.roam_load_weights_mixed.argtypes = [vp, P(roam_mlp_desc), vp, vp, i32]
-    L.roam_tune_round_size.argtypes = [vp, vp, i32, P(roam_render_opts), vp, vp, vp]
+    L.roam_tune_round_size.argtypes = [vp, vp, i32, P(roam_render_opts), vp, vp, vp, vp]
     L.roam_occupancy_update.argtypes = [vp, vp, i32, vp, vp, P(roam_occ_params), vp, vp, vp]
     L.roam_assign_fields.argtypes = [vp, i32, vp, vp, vp]
     L.roam_teacher_load.argtypes = [vp, vp, vp, i32]
@@ -180,7 +180,8 @@ def camera_array(cams: Sequence) -> ctypes.Array:
 
 
 def render_opts(delta: float, n_max: int, t_stop: float = 1e-4, bg=(0.0, 0.0, 0.0),
-                precision: int = ROAM_F32, round_size: int = 0, use_graph: bool = False) -> roam_render_opts:
+                precision: int = ROAM_F32, round_size: int = 0, use_graph: bool = False,
+                first_round_size: int = 0) -> roam_render_opts:
     o = roam_render_opts()
     o.delta = float(delta)
     o.n_max = int(n_max)
@@ -190,6 +191,7 @@ def render_opts(delta: float, n_max: int, t_stop: float = 1e-4, bg=(0.0, 0.0, 0.
     o.precision = int(precision)
     o.round_size = int(round_size)
     o.use_graph = int(bool(use_graph))
+    o.first_round_size = int(first_round_size)
     return o
 
 
@@ -330,13 +332,15 @@ class Roam:
                                   stream_handle))
 
     def tune_round_size(self, cams, opts: roam_render_opts, stream=None):
-        """roam_tune_round_size: (best round size, its render time in ms)."""
+        """roam_tune_round_size: (best round size, best first-round size, its
+        render time in ms)."""
         arr = camera_array(cams)
         best = ctypes.c_int32()
+        best0 = ctypes.c_int32()
         ms = ctypes.c_float()
         _check(self.L.roam_tune_round_size(self.h, arr, len(cams), ctypes.byref(opts), ctypes.byref(best),
-                                           ctypes.byref(ms), _stream(stream)))
-        return int(best.value), float(ms.value)
+                                           ctypes.byref(best0), ctypes.byref(ms), _stream(stream)))
+        return int(best.value), int(best0.value), float(ms.value)
 
     def occupancy_update(self, cams, depth, opacity, logit, bits=None, params=None, stream=None):
         """roam_occupancy_update: one scan per camera of (depth, opacity)

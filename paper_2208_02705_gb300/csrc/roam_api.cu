@@ -339,6 +339,7 @@ roam_status check_opts(const roam_ctx *c, const roam_render_opts *o)
     if ((o->precision == ROAM_BF16 && !all_tc(c, false)) || (o->precision == ROAM_FP8 && !all_tc(c, true)))
         return fail(ROAM_ERR_UNSUPPORTED, "tensor-core path not available for W=%d H=%d", c->md.width, c->md.n_hidden);
     if (o->round_size < 0) return fail(ROAM_ERR_ARG, "round_size must be >= 0");
+    if (o->first_round_size < 0) return fail(ROAM_ERR_ARG, "first_round_size must be >= 0");
     if (o->use_graph != 0 && o->use_graph != 1) return fail(ROAM_ERR_ARG, "use_graph must be 0 or 1");
     return ROAM_OK;
 }
@@ -507,16 +508,19 @@ roam_status run_mlp(roam_ctx *c, int precision, const SampleSrc &src, const Buck
 
 // The render / training-forward pipeline: rounds of march -> bucket -> MLP ->
 // composite; each round marches at most R more kept samples of every live ray.
+int n_rounds_of(int n_max, int R0, int R) { return 1 + (n_max > R0 ? (n_max - R0 + R - 1) / R : 0); }
+
+// R0 kept samples per live ray in the first round, R in every later one
 roam_status run_rounds(roam_ctx *c, const uint32_t *rays, int64_t n_rays, const roam_render_opts *o, float *rgb,
-                       float *depth, float *opacity, int R, cudaStream_t s)
+                       float *depth, float *opacity, int R0, int R, cudaStream_t s)
 {
-    const int n_rounds = (o->n_max + R - 1) / R;
+    const int n_rounds = n_rounds_of(o->n_max, R0, R);
     MarchParams mp{};
     mp.cams = c->cams.p;
     mp.n_views = c->n_views;
     mp.rays = rays;
     mp.n_rays = (uint32_t)n_rays;
-    mp.R = R;
+    mp.R = R0;
     mp.n_max = o->n_max;
     mp.delta = o->delta;
     mp.flat = 0;
@@ -530,6 +534,8 @@ roam_status run_rounds(roam_ctx *c, const uint32_t *rays, int64_t n_rays, const 
     const int grid = grid_blocks(c, 4);
     uint32_t *lives[2] = {c->live0.p, c->live1.p};
     for (int r = 0; r < n_rounds; ++r) {
+        const int Rr = r == 0 ? R0 : R;
+        mp.R = Rr;
         mp.init = r == 0;
         mp.live = r == 0 ? nullptr : lives[r & 1];
         mp.live_count = r == 0 ? nullptr : &c->ctr->live_count[r & 1];
@@ -540,7 +546,7 @@ roam_status run_rounds(roam_ctx *c, const uint32_t *rays, int64_t n_rays, const 
         ROAM_TRY(launched("march"));
         {
             ProfScope ps(c, P_BUCKET, s);
-            launch_bucket_ready(mp.cnt, mp.recs, mp.live_count, mp.n_rays, R, 1, c->n_fields, tile_of(o->precision), b,
+            launch_bucket_ready(mp.cnt, mp.recs, mp.live_count, mp.n_rays, Rr, 1, c->n_fields, tile_of(o->precision), b,
                                 c->ctr, grid, s, classes_of(c, o->precision));
         }
         ROAM_TRY(launched("bucket"));
@@ -549,7 +555,7 @@ roam_status run_rounds(roam_ctx *c, const uint32_t *rays, int64_t n_rays, const 
         src.recs = mp.recs;
         src.live = mp.live;
         src.live_count = mp.live_count;
-        src.R = R;
+        src.R = Rr;
         src.st = mp.st;
         src.delta = o->delta;
         src.accurate = mp.accurate;
@@ -576,11 +582,19 @@ int round_size(const roam_render_opts *o, int64_t n_rays)
     return R;
 }
 
+// the first round's size: opts->first_round_size (0: the round size), at most
+// the round size and n_max
+int first_round_size(const roam_render_opts *o, int R)
+{
+    const int R0 = o->first_round_size > 0 ? o->first_round_size : R;
+    return std::min(std::min(R0, R), o->n_max);
+}
+
 // The launch sequence of one render (counter resets + every round) as a CUDA
 // graph on the context's own stream, captured for a configuration and
 // replayed while it holds; forked from and joined back to the caller's stream.
 roam_status render_graph(roam_ctx *c, int64_t n_pix, const roam_render_opts *o, float *rgb, float *depth,
-                         float *opacity, int R, cudaStream_t s)
+                         float *opacity, int R0, int R, cudaStream_t s)
 {
     if (!c->gstream) {
         ROAM_CUDA(cudaStreamCreateWithFlags(&c->gstream, cudaStreamNonBlocking));
@@ -594,6 +608,7 @@ roam_status render_graph(roam_ctx *c, int64_t n_pix, const roam_render_opts *o, 
     memcpy(&f[3], &o->bg[1], 4);
     memcpy(&f[4], &o->bg[2], 4);
     const std::vector<uint64_t> key = {c->gen, g_alloc_gen.load(), (uint64_t)n_pix, (uint64_t)c->n_views, (uint64_t)R,
+                                       (uint64_t)R0,
                                        (uint64_t)o->n_max, (uint64_t)o->precision, f[0], f[1], f[2], f[3], f[4],
                                        (uint64_t)(uintptr_t)rgb, (uint64_t)(uintptr_t)depth,
                                        (uint64_t)(uintptr_t)opacity};
@@ -606,7 +621,7 @@ roam_status render_graph(roam_ctx *c, int64_t n_pix, const roam_render_opts *o, 
         ROAM_CUDA(cudaStreamBeginCapture(g, cudaStreamCaptureModeThreadLocal));
         cudaMemsetAsync(c->ctr, 0, sizeof(Counters), g);
         cudaMemsetAsync(c->hist.p, 0, (size_t)c->n_fields * sizeof(uint32_t), g);
-        const roam_status st = run_rounds(c, nullptr, n_pix, o, rgb, depth, opacity, R, g);
+        const roam_status st = run_rounds(c, nullptr, n_pix, o, rgb, depth, opacity, R0, R, g);
         cudaGraph_t graph = nullptr;
         const cudaError_t e = cudaStreamEndCapture(g, &graph);
         if (st != ROAM_OK) {
@@ -1049,6 +1064,7 @@ roam_status roam_render(roam_ctx *c, const roam_camera *cams, int n_views, const
     int64_t n_pix = 0;
     ROAM_TRY(upload_cams(c, cams, n_views, opts->delta, &n_pix, s));
     const int R = round_size(opts, n_pix);
+    const int R0 = first_round_size(opts, R);
     ROAM_TRY(ensure_rays(c, n_pix, R));
     float *d_rgb = rgb, *d_depth = depth, *d_op = opacity;
     if (!out_on_device) {
@@ -1057,15 +1073,15 @@ roam_status roam_render(roam_ctx *c, const roam_camera *cams, int n_views, const
         if (opacity) { ROAM_TRY(ensure(c->o_op, (size_t)n_pix)); d_op = c->o_op.p; }
     }
     if (opts->use_graph && !c->prof) {
-        ROAM_TRY(render_graph(c, n_pix, opts, d_rgb, d_depth, d_op, R, s));
+        ROAM_TRY(render_graph(c, n_pix, opts, d_rgb, d_depth, d_op, R0, R, s));
     } else {
         ROAM_CUDA(cudaMemsetAsync(c->ctr, 0, sizeof(Counters), s));
         ROAM_CUDA(cudaMemsetAsync(c->hist.p, 0, (size_t)c->n_fields * sizeof(uint32_t), s));
-        ROAM_TRY(run_rounds(c, nullptr, n_pix, opts, d_rgb, d_depth, d_op, R, s));
+        ROAM_TRY(run_rounds(c, nullptr, n_pix, opts, d_rgb, d_depth, d_op, R0, R, s));
     }
     c->last = s;
     c->last_rays = n_pix;
-    c->last_rounds = (opts->n_max + R - 1) / R;
+    c->last_rounds = n_rounds_of(opts->n_max, R0, R);
     c->train_rays = 0;
     if (!out_on_device) {
         if (rgb) ROAM_CUDA(cudaMemcpyAsync(rgb, d_rgb, 12 * (size_t)n_pix, cudaMemcpyDeviceToHost, s));
@@ -1079,7 +1095,8 @@ roam_status roam_render(roam_ctx *c, const roam_camera *cams, int n_views, const
 }
 
 roam_status roam_tune_round_size(roam_ctx *c, const roam_camera *cams, int n_views, const roam_render_opts *opts,
-                                 int32_t *best_round_size, float *best_ms, void *stream)
+                                 int32_t *best_round_size, int32_t *best_first_round_size, float *best_ms,
+                                 void *stream)
 {
     ROAM_TRY(set_dev(c));
     ROAM_TRY(check_ready(c));
@@ -1096,29 +1113,47 @@ roam_status roam_tune_round_size(roam_ctx *c, const roam_camera *cams, int n_vie
     cudaEvent_t e0, e1;
     ROAM_CUDA(cudaEventCreate(&e0));
     ROAM_CUDA(cudaEventCreate(&e1));
-    int best = 0;
-    float best_t = 0.f;
     roam_status st = ROAM_OK;
-    for (int R = 4; R <= opts->n_max && R <= 256 && st == ROAM_OK; R *= 2) {
+    // one warm-up render, then one timed render of this (first round, round) pair
+    auto time_pair = [&](int R0, int R, float &t) {
         roam_render_opts o = *opts;
         o.round_size = R;
+        o.first_round_size = R0;
         o.use_graph = 0;
-        const int Ruse = round_size(&o, n_pix);
-        if (Ruse != R) break;                                  // 32-bit slot ids
-        if ((size_t)((n_pix + 31) & ~31LL) * (size_t)R > have / 2) break;   // leave half the memory free
-        float t = 0.f;
-        for (int rep = 0; rep < 2 && st == ROAM_OK; ++rep) {    // warm-up, then timed
+        for (int rep = 0; rep < 2 && st == ROAM_OK; ++rep) {
             if ((st = ensure_rays(c, n_pix, R)) != ROAM_OK) break;
             cudaEventRecord(e0, s);
             cudaMemsetAsync(c->ctr, 0, sizeof(Counters), s);
             cudaMemsetAsync(c->hist.p, 0, (size_t)c->n_fields * sizeof(uint32_t), s);
-            st = run_rounds(c, nullptr, n_pix, &o, c->o_rgb.p, nullptr, nullptr, R, s);
+            st = run_rounds(c, nullptr, n_pix, &o, c->o_rgb.p, nullptr, nullptr, R0, R, s);
             cudaEventRecord(e1, s);
             if (cudaEventSynchronize(e1) != cudaSuccess) st = fail(ROAM_ERR_CUDA, "tuning render failed");
             cudaEventElapsedTime(&t, e0, e1);
         }
+    };
+    int best = 0, best0 = 0;
+    float best_t = 0.f;
+    // the round size, every round alike
+    for (int R = 4; R <= opts->n_max && R <= 256 && st == ROAM_OK; R *= 2) {
+        roam_render_opts o = *opts;
+        o.round_size = R;
+        if (round_size(&o, n_pix) != R) break;                                // 32-bit slot ids
+        if ((size_t)((n_pix + 31) & ~31LL) * (size_t)R > have / 2) break;   // leave half the memory free
+        float t = 0.f;
+        time_pair(R, R, t);
         if (st == ROAM_OK && (best == 0 || t < best_t)) {
-            best = R;
+            best = best0 = R;
+            best_t = t;
+        }
+    }
+    // then a smaller first round: most rays stop at their first surface, and
+    // the samples a round marches past a ray's termination are evaluated for
+    // nothing
+    for (int R0 = 4; best > 0 && R0 < best && st == ROAM_OK; R0 *= 2) {
+        float t = 0.f;
+        time_pair(R0, best, t);
+        if (st == ROAM_OK && t < best_t) {
+            best0 = R0;
             best_t = t;
         }
     }
@@ -1129,6 +1164,7 @@ roam_status roam_tune_round_size(roam_ctx *c, const roam_camera *cams, int n_vie
     c->last = s;
     c->last_rays = n_pix;
     *best_round_size = best;
+    if (best_first_round_size) *best_first_round_size = best0;
     if (best_ms) *best_ms = best_t;
     ROAM_CUDA(cudaMemcpy(c->h_ctr, c->ctr, sizeof(Counters), cudaMemcpyDeviceToHost));
     return status_of(c->h_ctr->status);
@@ -1538,7 +1574,7 @@ roam_status roam_train_forward(roam_ctx *c, const roam_camera *cams, int n_views
     ROAM_TRY(ensure_rays(c, n_rays, R));
     ROAM_CUDA(cudaMemsetAsync(c->ctr, 0, sizeof(Counters), s));
     ROAM_CUDA(cudaMemsetAsync(c->hist.p, 0, (size_t)c->n_fields * sizeof(uint32_t), s));
-    ROAM_TRY(run_rounds(c, rays, n_rays, opts, rgb, nullptr, nullptr, R, s));
+    ROAM_TRY(run_rounds(c, rays, n_rays, opts, rgb, nullptr, nullptr, R, R, s));
     c->last = s;
     c->last_rays = n_rays;
     c->last_rounds = 1;

@@ -254,18 +254,23 @@ __global__ void __launch_bounds__(kTThreads, 1)
         if (lane == 0) {
             uint32_t i = 0;
             bool ok = true;
-            for (int64_t t = blockIdx.x; t < n_tiles && ok; t += gridDim.x)
-                for (int c = 0; c < kTChunks && ok; ++c, ++i) {
-                    const uint32_t s = i % kTStages;
-                    if (i >= (uint32_t)kTStages)
-                        ok = mbar_wait(&S.empty[s], ((i / kTStages) - 1) & 1u, abortp, status);
-                    if (!ok) break;
-                    const int64_t off = chunk_off(c);
-                    const uint32_t bytes = (uint32_t)(chunk_off(c + 1) - off);
-                    mbar_expect_tx(&S.full[s], bytes);
-                    for (uint32_t b = 0; b < bytes; b += 16384)
-                        bulk_g2s(ring + (size_t)s * kTChunk + b, img + off + b, 16384u, &S.full[s]);
+            for (int64_t t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
+                // the chunks in image order: a running offset (N x 128 bytes each)
+                int64_t off = 0;
+                for (int l = 0; l < kTcLayers && ok; ++l) {
+                    const TcLayer L = tc_layer(l);
+                    const uint32_t bytes = (uint32_t)L.N * 128u;
+                    for (int c = 0; c < L.chunks && ok; ++c, ++i, off += bytes) {
+                        const uint32_t s = i % kTStages;
+                        if (i >= (uint32_t)kTStages)
+                            ok = mbar_wait(&S.empty[s], ((i / kTStages) - 1) & 1u, abortp, status);
+                        if (!ok) break;
+                        mbar_expect_tx(&S.full[s], bytes);
+                        for (uint32_t b = 0; b < bytes; b += 16384)
+                            bulk_g2s(ring + (size_t)s * kTChunk + b, img + off + b, 16384u, &S.full[s]);
+                    }
                 }
+            }
             if (!ok) {
                 // copies that may still be in flight: the last kTStages issued
                 const uint32_t i0 = i > (uint32_t)kTStages ? i - kTStages : 0u;
@@ -366,22 +371,25 @@ __global__ void __launch_bounds__(kTThreads, 1)
                 }
                 tc_fence_after();
                 if (l < kTcLayers - 1) {
-                    // 128 outputs of this half, in two passes of 64
+                    // 128 outputs of this half, in four passes of 32 (few live registers)
                     float ps = 0.f;
 #pragma unroll 1
-                    for (int g = 0; g < 2; ++g) {
-                        const int c0 = h * 128 + g * 64;
-                        uint32_t r[4][16];
-#pragma unroll
-                        for (int c = 0; c < 4; ++c) tmem_ld16_nowait(tDrow + (uint32_t)(c0 + 16 * c), r[c]);
+                    for (int g = 0; g < 4; ++g) {
+                        const int c0 = h * 128 + g * 32;
+                        uint32_t r0[16], r1[16];
+                        tmem_ld16_nowait(tDrow + (uint32_t)c0, r0);
+                        tmem_ld16_nowait(tDrow + (uint32_t)(c0 + 16), r1);
                         tmem_wait_ld();
-                        float v[64];
+                        float v[32];
 #pragma unroll
-                        for (int j = 0; j < 64; ++j) v[j] = __uint_as_float(r[j >> 4][j & 15]);
+                        for (int j = 0; j < 16; ++j) {
+                            v[j] = __uint_as_float(r0[j]);
+                            v[16 + j] = __uint_as_float(r1[j]);
+                        }
                         if (L.tab >= 0) {
                             const float4 *b4 = reinterpret_cast<const float4 *>(tab + L.tab * kTW + c0);
 #pragma unroll
-                            for (int j = 0; j < 16; ++j) {
+                            for (int j = 0; j < 8; ++j) {
                                 const float4 bb = __ldg(b4 + j);
                                 v[4 * j] += bb.x; v[4 * j + 1] += bb.y; v[4 * j + 2] += bb.z; v[4 * j + 3] += bb.w;
                             }
@@ -390,7 +398,7 @@ __global__ void __launch_bounds__(kTThreads, 1)
                             // density head on layer 8's FP32 output (no activation on it)
                             const float4 *w4 = reinterpret_cast<const float4 *>(tab + 7 * kTW + c0);
 #pragma unroll
-                            for (int j = 0; j < 16; ++j) {
+                            for (int j = 0; j < 8; ++j) {
                                 const float4 ww = __ldg(w4 + j);
                                 ps = fmaf(ww.x, v[4 * j], ps);
                                 ps = fmaf(ww.y, v[4 * j + 1], ps);
@@ -398,14 +406,8 @@ __global__ void __launch_bounds__(kTThreads, 1)
                                 ps = fmaf(ww.w, v[4 * j + 3], ps);
                             }
                         }
-#pragma unroll
-                        for (int c = 0; c < 2; ++c) {
-                            float u[32];
-#pragma unroll
-                            for (int j = 0; j < 32; ++j) u[j] = v[32 * c + j];
-                            if (L.relu) st_act32<false, true>(tArow, (c0 >> 5) + c, u);
-                            else st_act32<false, false>(tArow, (c0 >> 5) + c, u);
-                        }
+                        if (L.relu) st_act32<false, true>(tArow, c0 >> 5, v);
+                        else st_act32<false, false>(tArow, c0 >> 5, v);
                     }
                     if (enc_x) st_block(tArow, kColFx, enc);
                     if (l == 7) {
@@ -415,20 +417,22 @@ __global__ void __launch_bounds__(kTThreads, 1)
                     }
                 } else {
                     // layer 10 (64 of its 128 outputs per half), ReLU, then this
-                    // half's share of the 3-output layer in FP32
-                    uint32_t r[4][16];
-#pragma unroll
-                    for (int c = 0; c < 4; ++c) tmem_ld16_nowait(tDrow + (uint32_t)(h * 64 + 16 * c), r[c]);
-                    tmem_wait_ld();
+                    // half's share of the 3-output layer in FP32, 16 columns a pass
                     const float4 *wo = reinterpret_cast<const float4 *>(tab + 8 * kTW + 4);
                     float ar = 0.f, ag = 0.f, ab = 0.f;
+#pragma unroll 1
+                    for (int c = 0; c < 4; ++c) {
+                        uint32_t r[16];
+                        tmem_ld16_nowait(tDrow + (uint32_t)(h * 64 + 16 * c), r);
+                        tmem_wait_ld();
 #pragma unroll
-                    for (int j = 0; j < 64; ++j) {
-                        const float g = fmaxf(__uint_as_float(r[j >> 4][j & 15]), 0.f);
-                        const float4 ww = __ldg(wo + h * 64 + j);
-                        ar = fmaf(ww.x, g, ar);
-                        ag = fmaf(ww.y, g, ag);
-                        ab = fmaf(ww.z, g, ab);
+                        for (int j = 0; j < 16; ++j) {
+                            const float g = fmaxf(__uint_as_float(r[j]), 0.f);
+                            const float4 ww = __ldg(wo + h * 64 + 16 * c + j);
+                            ar = fmaf(ww.x, g, ar);
+                            ag = fmaf(ww.y, g, ag);
+                            ab = fmaf(ww.z, g, ab);
+                        }
                     }
                     S.red[h][row][1] = ar;
                     S.red[h][row][2] = ag;

@@ -41,12 +41,35 @@ def test_binding_lists_every_declared_symbol():
     assert sorted(roam.ENTRY_POINTS) == declared_entry_points()
 
 
-def test_binding_structs_match_header_sizes():
+def test_binding_structs_match_header_layouts(tmp_path):
+    """Every ctypes structure of the binding has the size and field offsets
+    that a C compiler gives the header's struct (gcc on include/roam.h)."""
+    import shutil
+    import subprocess
     import paper_2208_02705_gb300 as roam
-    assert ctypes.sizeof(roam.roam_camera) == 64
-    assert ctypes.sizeof(roam.roam_render_opts) == 36
-    assert ctypes.sizeof(roam.roam_grid_desc) == 28
-    assert ctypes.sizeof(roam.roam_mlp_desc) == 16
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("gcc not available")
+    structs = ["roam_grid_desc", "roam_mlp_desc", "roam_camera", "roam_render_opts", "roam_stats",
+               "roam_kernel_time", "roam_adam_cfg", "roam_occ_params"]
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "roam.h"', "int main(void) {"]
+    for name in structs:
+        lines.append(f'printf("{name} size %zu\\n", sizeof({name}));')
+        for fname, _ in getattr(roam, name)._fields_:
+            lines.append(f'printf("{name} {fname} %zu\\n", offsetof({name}, {fname}));')
+    lines.append("return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.check_call([gcc, "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")
+    for row in out:
+        if not row:
+            continue
+        name, what, val = row.split()
+        cls = getattr(roam, name)
+        got = ctypes.sizeof(cls) if what == "size" else getattr(cls, what).offset
+        assert got == int(val), (name, what, got, val)
 
 
 def test_library_built_for_sm103a_only(lib_path):

@@ -200,17 +200,33 @@ def test_render_room32_f32(roam, room, room32, room32_grid):
     assert_render(rep, depth_tol=1e-4 * max(1.0, float(np.abs(depth.cpu().numpy()).max())), opacity_tol=1e-4)
 
 
-def test_render_round_schedule_is_invisible(roam, room, room32):
-    """Rounds change the work done, never the result: bit-identical images."""
+@pytest.mark.parametrize("precision", ["f32", "bf16"])
+def test_render_round_schedule_is_invisible(roam, room, room32, precision):
+    """Rounds (and a smaller first round) change the work done, never the
+    result: bit-identical images and composited-sample counts."""
+    prec = roam.ROAM_F32 if precision == "f32" else roam.ROAM_BF16
     outs = []
-    for R in (1, 7, 32, 64):
-        opts = roam.render_opts(room32.delta, room32.n_max, round_size=R)
+    for R, R0 in ((1, 0), (7, 0), (32, 0), (64, 0), (32, 4), (16, 5), (64, 8)):
+        opts = roam.render_opts(room32.delta, room32.n_max, round_size=R, first_round_size=R0, precision=prec)
         rgb, depth, op = room.render(room32.cams, opts)
-        outs.append((rgb.clone(), depth.clone(), op.clone()))
-    torch.cuda.synchronize()
+        torch.cuda.synchronize()
+        outs.append((rgb.clone(), depth.clone(), op.clone(), room.get_stats().n_used))
     for o in outs[1:]:
-        for a, b in zip(outs[0], o):
+        for a, b in zip(outs[0][:3], o[:3]):
             assert torch.equal(a, b)
+        assert o[3] == outs[0][3]
+
+
+def test_round_size_tuner_picks_a_valid_pair(roam, room, room32):
+    base = roam.render_opts(room32.delta, room32.n_max, precision=roam.ROAM_BF16)
+    R, R0, ms = room.tune_round_size(room32.cams, base)
+    assert 4 <= R <= room32.n_max and 4 <= R0 <= R and ms > 0
+    ref = [x.clone() for x in room.render(room32.cams, base)]
+    tuned = room.render(room32.cams, roam.render_opts(room32.delta, room32.n_max, precision=roam.ROAM_BF16,
+                                                      round_size=R, first_round_size=R0))
+    torch.cuda.synchronize()
+    for a, b in zip(ref, tuned):
+        assert torch.equal(a, b)
 
 
 @pytest.mark.parametrize("precision", ["f32", "bf16"])
