@@ -12,8 +12,14 @@
 //      tiles of one field and are added to the global FP32 gradient (one
 //      atomic per parameter) when the field changes.  The MMAs of one
 //      backward group write independent accumulators, so up to three warps
-//      issue them side by side; every warp's lane 0 commits to the group's
+//      issue them side by side; lane 0 of warps 0..3 commits to the group's
 //      barrier.
+// Sixteen warps share every epilogue: the four warps of one TMEM lane
+// quarter each take a quarter of the row's columns (W / 4), so a layer's
+// TMEM-to-shared-memory pass is a quarter as long per thread and each SM
+// sub-partition has four warps to hide its latencies.  The colour layer's
+// 3-output reduction meets in shared memory; one CTA barrier per MMA group
+// both publishes the epilogue's stores and agrees on every thread's wait.
 //
 // Every activation tile exists once, in the 128-byte-swizzled layout with
 // samples as rows and 64 features per 128-byte row ("natural" layout).  Read
@@ -38,6 +44,8 @@ namespace roam {
 namespace {
 
 constexpr int kChunk = 16384;       // one 64-column chunk of 128 rows
+constexpr int kGroups = 4;          // column groups: threads per tile row
+constexpr int kBwThreads = 128 * kGroups;
 
 template <int W, int H>
 struct BwShape {
@@ -88,18 +96,126 @@ __device__ __forceinline__ void ld16f(uint32_t taddr, float (&v)[16])
     for (int q = 0; q < 16; ++q) v[q] = __uint_as_float(r[q]);
 }
 
-// N consecutive TMEM columns of this thread's lane as floats, one wait for all
+// N (8 or 16) consecutive TMEM columns of this thread's lane as floats
 template <int N>
-__device__ __forceinline__ void ldNf(uint32_t taddr, float (&v)[N])
+__device__ __forceinline__ void ldcf(uint32_t taddr, float (&v)[N])
 {
-    uint32_t r[N / 16][16];
+    static_assert(N == 8 || N == 16, "one x8 or x16 load");
+    if constexpr (N == 16) {
+        ld16f(taddr, v);
+    } else {
+        uint32_t r[8];
+        asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                     : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                     : "r"(taddr));
+        tmem_wait_ld();
 #pragma unroll
-    for (int c = 0; c < N / 16; ++c) tmem_ld16_nowait(taddr + (uint32_t)(16 * c), r[c]);
-    tmem_wait_ld();
+        for (int q = 0; q < 8; ++q) v[q] = __uint_as_float(r[q]);
+    }
+}
+
+constexpr int kFreqX = (kPeX - 3) / 6;     // frequencies of F(x)
+
+// frequency k of F(x) fills columns [3 + 6k, 9 + 6k) of X_0
+__host__ __device__ constexpr bool freq_meets(int k, int lo, int hi) { return 3 + 6 * k < hi && 9 + 6 * k > lo; }
+__host__ __device__ constexpr int freq_last(int lo, int hi)
+{
+    int r = -1;
+    for (int k = 0; k < kFreqX; ++k)
+        if (freq_meets(k, lo, hi)) r = k;
+    return r;
+}
+__host__ __device__ constexpr int freq_first(int lo, int hi)
+{
+    for (int k = 0; k < kFreqX; ++k)
+        if (freq_meets(k, lo, hi)) return k;
+    return kFreqX;
+}
+
+// Columns [16 G, 16 G + 16) of X_0 = [x | sin, cos (2^k pi x), k < 10 | 1]
+// as 8 packed BF16 pairs.  The same arithmetic as the forward kernel's
+// encoding (direct evaluation at k = 0 and k = 5, angle doubling in
+// between), so the recomputed chain sees the forward's operands bit for bit;
+// only the frequencies this block's columns (or their doubling chain) need
+// are evaluated.
+template <int G>
+__device__ __forceinline__ void enc_x0(const float (&xl)[3], uint32_t (&p)[8])
+{
+    constexpr int lo = 16 * G, hi = lo + 16;
+    constexpr int k_hi = freq_last(lo, hi);
+    constexpr int k_start = freq_first(lo, hi) >= 5 ? 5 : 0;
+    float e[16];
 #pragma unroll
-    for (int c = 0; c < N / 16; ++c)
+    for (int q = 0; q < 16; ++q) e[q] = 0.f;
 #pragma unroll
-        for (int q = 0; q < 16; ++q) v[16 * c + q] = __uint_as_float(r[c][q]);
+    for (int a = 0; a < 3; ++a)
+        if (a >= lo && a < hi) e[a - lo] = xl[a];
+    if (63 >= lo && 63 < hi) e[63 - lo] = 1.0f;
+    float sp[3] = {0.f, 0.f, 0.f}, cp[3] = {1.f, 1.f, 1.f};
+#pragma unroll
+    for (int k = k_start; k <= k_hi; ++k) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            float sn, cs;
+            if (k == 0 || k == 5) {
+                sincospi_fast(xl[a] * (float)(1 << k), sn, cs);
+            } else {
+                sn = 2.0f * sp[a] * cp[a];
+                cs = fmaf(-2.0f * sp[a], sp[a], 1.0f);
+            }
+            sp[a] = sn;
+            cp[a] = cs;
+            const int cs_col = 3 + 6 * k + a, cc_col = 6 + 6 * k + a;
+            if (cs_col >= lo && cs_col < hi) e[cs_col - lo] = sn;
+            if (cc_col >= lo && cc_col < hi) e[cc_col - lo] = cs;
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < 8; ++q) p[q] = pack_bf16(e[2 * q], e[2 * q + 1]);
+}
+
+// The MMA groups of the adjoint, fully unrolled: each operand descriptor is
+// built once and stepped by compile-time offsets (16-byte units), so that an
+// N <= 64 MMA issues in its ~25 ns slot instead of ~80 ns with a descriptor
+// rebuilt per instruction.
+//   forward layer: D[s][n] = sum_k X[s][k] W[n][k]; K-major A (X, then the
+//   tail chunk T past column 64) and B (the image), K / 16 MMAs
+template <int K, int N>
+__device__ __forceinline__ void mma_fwd(uint32_t tD, uint32_t xa, uint32_t st, uint32_t ba)
+{
+    constexpr uint32_t idesc = idesc_bf16_t(N, 0, 0);
+    const uint64_t dx = sdesc(xa), dt = sdesc(st), db = sdesc(ba);
+#pragma unroll
+    for (int ks = 0; ks < K / 16; ++ks) {
+        const int ch = ks >> 2, kin = ks & 3;
+        umma_ss(tD, (ch == 0 ? dx : dt) + (uint64_t)(kin * 2), db + (uint64_t)((ch * N * 128 + kin * 32) >> 4), idesc,
+                ks > 0 ? 1u : 0u);
+    }
+}
+//   wgrad: D_w[k][n] (+)= sum_s X[s][k] dZ[s][n]; both operands MN-major,
+//   8 MMAs of 16 samples (two 8-row groups, 2048 bytes) each
+template <int N>
+__device__ __forceinline__ void mma_wgrad(uint32_t td, uint32_t xa, uint32_t lbo_x, uint32_t dza, uint32_t dz_lbo,
+                                          uint32_t acc0)
+{
+    constexpr uint32_t idesc = idesc_bf16_t(N, 1, 1);
+    const uint64_t da = sdesc_mn(xa, lbo_x), db = sdesc_mn(dza, dz_lbo);
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+        umma_ss(td, da + (uint64_t)(j * 128), db + (uint64_t)(j * 128), idesc, (j > 0 || acc0) ? 1u : 0u);
+}
+//   dgrad: D[s][k] = sum_n dZ[s][n] W[n][k], k < W; A = dZ K-major (chunks
+//   16 KB apart), B = the image read MN-major, Kn / 16 MMAs
+template <int W, int Kn>
+__device__ __forceinline__ void mma_dgrad(uint32_t tD, uint32_t sdz, uint32_t ba)
+{
+    constexpr uint32_t idesc = idesc_bf16_t(W, 0, 1);
+    const uint64_t da = sdesc(sdz), db = sdesc_mn(ba, 1024u);
+#pragma unroll
+    for (int ks = 0; ks < Kn / 16; ++ks) {
+        const int ch = ks >> 2, kin = ks & 3;
+        umma_ss(tD, da + (uint64_t)((ch * kChunk + kin * 32) >> 4), db + (uint64_t)(ks * 128), idesc, ks > 0 ? 1u : 0u);
+    }
 }
 
 // Where feature row k of wgrad accumulator l lands in the API layout (per
@@ -148,13 +264,15 @@ __device__ __forceinline__ RowMap row_map(int l, int k)
 }
 
 template <int W, int H>
-__global__ void __launch_bounds__(128, 1)
+__global__ void __launch_bounds__(kBwThreads, 1)
     k_mlp_bwd_tc(const void *wimg, int64_t img_bytes, const float *affine, float sig_scale, int act, int64_t P,
                  SampleSrc src, BucketBufs b, Counters *ctr, const float4 *gsr, float *grad)
 {
     using S = TcShape<W, H, false>;
     using B = BwShape<W, H>;
     constexpr int kLayers = S::kLayers;              // tensor-core layers of the forward chain
+    constexpr int CW = W / kGroups;                   // columns of one thread's share of a row
+    constexpr int CU = CW / 8;                        // ... in 16-byte units
     extern __shared__ uint8_t smem_raw[];
     __shared__ uint64_t bar_d, bar_w;
     __shared__ uint32_t tmem_slot;
@@ -165,16 +283,20 @@ __global__ void __launch_bounds__(128, 1)
     uint8_t *IMG = sm;
     uint8_t *T = sm + B::kOffT;
     uint8_t *DZ = sm + B::kOffDZ;
+    uint8_t *PART = DZ + kChunk;                      // units 2..5 of dZ chunk 1: no MMA reads them
     const uint32_t sIMG = base, sX = base + B::kOffX, sT = base + B::kOffT, sDZ = base + B::kOffDZ;
     const int tid = threadIdx.x, warp = tid >> 5;
-    const int row = tid;                               // TMEM lane == tile row == sample
+    const int quarter = warp & 3;                     // TMEM lane quarter this warp may access
+    const int g = warp >> 2;                          // column group
+    const int row = quarter * 32 + (tid & 31);        // TMEM lane == tile row == sample
+    const int c0 = g * CW;                            // first column of this thread's share
     const bool issuer = tid == 0;                     // forward chain
-    const bool lead = (tid & 31) == 0;                // every warp's lane 0 commits each MMA group
+    const bool lead = (tid & 31) == 0 && warp < 4;    // warps 0..3 commit each MMA group (issuers: warps 0..2)
     volatile int *abortp = &abort_flag;
     uint32_t *status = &ctr->status;
 
     if (tid == 0) {
-        mbar_init(&bar_d, 4);                         // one commit per warp leader
+        mbar_init(&bar_d, 4);                         // one commit per lead
         mbar_init(&bar_w, 1);
         abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -185,15 +307,16 @@ __global__ void __launch_bounds__(128, 1)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
-    // the tail chunk only pads the wgrad operands at W = 32: keep it finite
-    if (W < 64)
-        for (int q = tid; q < kChunk / 16; q += 128) reinterpret_cast<uint4 *>(T)[q] = make_uint4(0u, 0u, 0u, 0u);
+    // T: at W = 64 its columns 32..63 stay zero (features 96..127 of the
+    // wgrad operands); at W = 32 all of it only pads those operands
+    for (int q = tid; q < kChunk / 16; q += kBwThreads) reinterpret_cast<uint4 *>(T)[q] = make_uint4(0u, 0u, 0u, 0u);
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = tmem_slot;
-    const uint32_t tlane = (uint32_t)(warp * 32) << 16;
+    const uint32_t tlane = (uint32_t)(quarter * 32) << 16;
     const uint32_t tD = tmem;
+    const uint32_t tDc = tD + tlane + (uint32_t)c0;   // this thread's share of D
 
     const uint32_t n_tiles = ctr->n_tiles;
     const uint32_t t0 = (uint32_t)((uint64_t)n_tiles * blockIdx.x / gridDim.x);
@@ -205,8 +328,17 @@ __global__ void __launch_bounds__(128, 1)
     bool wnew = true;                    // the wgrad accumulators hold nothing yet
     bool aborted = false;
 
-    // issue, commit and wait: true when the MMAs landed
-    auto mma_wait = [&]() -> bool {
+    // every thread's generic shared-memory stores become visible to the
+    // MMAs; the barrier also agrees on `good` (every thread's last wait)
+    auto publish = [&](bool good) -> bool {
+        fence_async_smem();
+        tc_fence_before();
+        const bool all = __syncthreads_and(good) != 0;
+        tc_fence_after();
+        return all;
+    };
+    // commit the MMAs just issued and wait for them: true when they landed
+    auto land = [&]() -> bool {
         if (lead) {
             umma_commit(&bar_d);
             ++n_commits;
@@ -214,25 +346,18 @@ __global__ void __launch_bounds__(128, 1)
         const bool got = mbar_wait(&bar_d, d_ph, abortp, status);
         if (lead && got) ++n_waits;
         d_ph ^= 1u;
-        const bool all = __syncthreads_and(got) != 0;
         tc_fence_after();
-        return all;
+        return got;
     };
-    // every thread's generic shared-memory stores become visible to the MMAs
-    auto publish = [&]() {
-        fence_async_smem();
-        tc_fence_before();
-        __syncthreads();
-        tc_fence_after();
-    };
-    // flush the wgrad accumulators of field f to the global gradient
+    // flush the wgrad accumulators of field f to the global gradient; the
+    // 16-column pieces of each layer go round the column groups
     auto flush = [&](uint32_t f) {
         float *gf = grad + (int64_t)f * P;
 #pragma unroll 1
         for (int l = 0; l < H + 3; ++l) {
             const RowMap m = row_map<W, H>(l, row);
 #pragma unroll 1
-            for (int c = 0; c < B::wN(l); c += 16) {
+            for (int c = 16 * g; c < B::wN(l); c += 16 * kGroups) {
                 float v[16];
                 ld16f(tmem + tlane + (uint32_t)(B::wcol(l) + c), v);
                 if (m.base < 0) continue;
@@ -300,118 +425,72 @@ __global__ void __launch_bounds__(128, 1)
         const float4 dl = valid ? gsr[smp.idx] : make_float4(0.f, 0.f, 0.f, 0.f);
         const float *aff = affine + 6 * (int64_t)tl.field;
 
-        // ---- X_0 = [F(x_loc) | 1] and the tail [1 | F(d) | 0] ----
+        // ---- this thread's 16 columns of X_0 = [F(x_loc) | 1]; group 0 also
+        // the tail [1 | F(d) | 0] ----
         uint32_t tailp[16];
         {
             const float xl[3] = {fmaf(__ldg(aff + 0), smp.px, __ldg(aff + 3)),
                                  fmaf(__ldg(aff + 1), smp.py, __ldg(aff + 4)),
                                  fmaf(__ldg(aff + 2), smp.pz, __ldg(aff + 5))};
-            float e[64];
-            e[0] = xl[0]; e[1] = xl[1]; e[2] = xl[2];
-#pragma unroll
-            for (int a = 0; a < 3; ++a) {
-                float sn[10], cs[10];
-                encode1<10>(xl[a], sn, cs);
-#pragma unroll
-                for (int k = 0; k < 10; ++k) {
-                    e[3 + 6 * k + a] = sn[k];
-                    e[6 + 6 * k + a] = cs[k];
-                }
+            uint32_t p[8];
+            switch (g) {
+            case 0: enc_x0<0>(xl, p); break;
+            case 1: enc_x0<1>(xl, p); break;
+            case 2: enc_x0<2>(xl, p); break;
+            default: enc_x0<3>(xl, p); break;
             }
-            e[63] = 1.0f;
-            uint32_t p[32];
-#pragma unroll
-            for (int q = 0; q < 32; ++q) p[q] = pack_bf16(e[2 * q], e[2 * q + 1]);
-            st_units<8>(sm + B::kOffX, row, 0, p);
-
-            float ft[32];
-            ft[0] = 1.0f;
-            const float dv[3] = {smp.dx, smp.dy, smp.dz};
-            ft[1] = dv[0]; ft[2] = dv[1]; ft[3] = dv[2];
-#pragma unroll
-            for (int a = 0; a < 3; ++a) {
-                float sn[4], cs[4];
-                encode1<4>(dv[a], sn, cs);
-#pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    ft[4 + 6 * k + a] = sn[k];
-                    ft[7 + 6 * k + a] = cs[k];
-                }
-            }
-            ft[28] = ft[29] = ft[30] = ft[31] = 0.f;
-#pragma unroll
-            for (int q = 0; q < 16; ++q) tailp[q] = pack_bf16(ft[2 * q], ft[2 * q + 1]);
-            if (W == 64) {
-                uint32_t z[16];
-#pragma unroll
-                for (int q = 0; q < 16; ++q) z[q] = 0u;
-                st_units<4>(T, row, 0, tailp);
-                st_units<4>(T, row, 4, z);
+            st_units<2>(sm + B::kOffX, row, 2 * g, p);
+            if (g == 0) {
+                const float dv[3] = {smp.dx, smp.dy, smp.dz};
+                encode_packed<false, 4, 1, false, 32>(dv, tailp);
+                if constexpr (W == 64) st_units<4>(T, row, 0, tailp);
             }
         }
-        // row `row` of X_i: the tail at W = 32 (columns 32..63); the
-        // activations go in 16-column pieces (units 2c/16, 2c/16 + 1)
+        // row `row` of X_i: the tail at W = 32 (columns 32..63), by group 0
         auto store_tail = [&](int i) {
-            if constexpr (W == 32) st_units<4>(sm + B::kOffX + i * kChunk, row, 4, tailp);
+            if constexpr (W == 32)
+                if (g == 0) st_units<4>(sm + B::kOffX + i * kChunk, row, 4, tailp);
         };
         // ---- forward chain ----
         float s_logit = 0.f;
         float dsig = 0.f;
         bool ok = true;
 #pragma unroll 1
-        for (int l = 0; l < kLayers && ok; ++l) {
-            publish();
+        for (int l = 0; l < kLayers; ++l) {
+            ok = publish(ok);
+            if (!ok) break;
             if (issuer) {
-                const int K = S::K(l), N = S::N(l);
-                const uint32_t idesc = idesc_bf16_t(N, 0, 0);
                 const uint32_t xa = sX + (uint32_t)(l * kChunk);
                 const uint32_t ba = sIMG + (uint32_t)S::offset(l);
-#pragma unroll 1
-                for (int ks = 0; ks < K / 16; ++ks) {
-                    const int ch = ks >> 2, kin = ks & 3;
-                    const uint32_t a = (ch == 0 ? xa : sT) + (uint32_t)(kin * 32);
-                    umma_ss(tD, sdesc(a), sdesc(ba + (uint32_t)(ch * N * 128 + kin * 32)), idesc, ks > 0 ? 1u : 0u);
-                }
+                if (l == 0) mma_fwd<S::K(0), W>(tD, xa, sT, ba);
+                else if (l < H) mma_fwd<S::K_HID, W>(tD, xa, sT, ba);
+                else if (l == H) mma_fwd<S::K_HID, S::N_HEAD>(tD, xa, sT, ba);
+                else mma_fwd<S::K_COL, W>(tD, xa, sT, ba);
             }
             if (l == 0) stage_index(pend, b, tl_nx, row, more);
             if (l == 1) stage_record(pend, src);
             if (l == 2) stage_ray(pend, src);
-            ok = mma_wait();
-            if (!ok) break;
+            ok = land();
             if (l < H) {
                 // next hidden input: ReLU
-                uint8_t *xc = sm + B::kOffX + (l + 1) * kChunk;
+                float va[CW];
+                ldcf<CW>(tDc, va);
+                uint32_t p[CW / 2];
 #pragma unroll
-                for (int cb = 0; cb < W; cb += 32) {
-                    float va[32];
-                    ldNf<32>(tD + tlane + (uint32_t)cb, va);
-#pragma unroll
-                    for (int c = 0; c < 32; c += 16) {
-                        uint32_t p[8];
-#pragma unroll
-                        for (int q = 0; q < 8; ++q) p[q] = pack_bf16_relu(va[c + 2 * q], va[c + 2 * q + 1]);
-                        st_units<2>(xc, row, (cb + c) / 8, p);
-                    }
-                }
+                for (int q = 0; q < CW / 2; ++q) p[q] = pack_bf16_relu(va[2 * q], va[2 * q + 1]);
+                st_units<CU>(sm + B::kOffX + (l + 1) * kChunk, row, c0 / 8, p);
                 store_tail(l + 1);
             } else if (l == H) {
                 // head: features (linear) -> colour input, column W = density logit
-                uint8_t *xc = sm + B::kOffX + (H + 1) * kChunk;
+                float va[CW];
+                ldcf<CW>(tDc, va);
+                uint32_t p[CW / 2];
 #pragma unroll
-                for (int cb = 0; cb < W; cb += 32) {
-                    float va[32];
-                    ldNf<32>(tD + tlane + (uint32_t)cb, va);
-#pragma unroll
-                    for (int c = 0; c < 32; c += 16) {
-                        uint32_t p[8];
-#pragma unroll
-                        for (int q = 0; q < 8; ++q) p[q] = pack_bf16(va[c + 2 * q], va[c + 2 * q + 1]);
-                        st_units<2>(xc, row, (cb + c) / 8, p);
-                    }
-                }
-                {
-                    float v[16];
-                    ld16f(tD + tlane + (uint32_t)W, v);
+                for (int q = 0; q < CW / 2; ++q) p[q] = pack_bf16(va[2 * q], va[2 * q + 1]);
+                st_units<CU>(sm + B::kOffX + (H + 1) * kChunk, row, c0 / 8, p);
+                if (g == 0) {
+                    float v[8];
+                    ldcf<8>(tD + tlane + (uint32_t)W, v);
                     s_logit = v[0];
                 }
                 store_tail(H + 1);
@@ -419,167 +498,159 @@ __global__ void __launch_bounds__(128, 1)
                 // colour: z -> g = relu(z) (X_g), rgb = sigmoid(Wo g + bo) in FP32, then
                 // the output layer's adjoint and dZ of the colour layer
                 const float4 *wo = reinterpret_cast<const float4 *>(IMG + S::kMatBytes);
+                float va[CW];
+                ldcf<CW>(tDc, va);
+                float ax = 0.f, ay = 0.f, az = 0.f;
+#pragma unroll
+                for (int k = 0; k < CW; ++k) {
+                    const float gk = fmaxf(va[k], 0.f);
+                    const float4 wk = wo[c0 + k];
+                    ax = fmaf(wk.x, gk, ax);
+                    ay = fmaf(wk.y, gk, ay);
+                    az = fmaf(wk.z, gk, az);
+                }
+                // the four groups' partial sums of the row meet in shared
+                // memory; everyone adds them in group order
+                *reinterpret_cast<float4 *>(PART + sw_off(row, 2 + g)) = make_float4(ax, ay, az, 0.f);
+                asm volatile("bar.sync %0, %1;" ::"r"(1 + quarter), "r"(32 * kGroups) : "memory");
                 float4 acc = wo[W];
 #pragma unroll
-                for (int cb = 0; cb < W; cb += 32) {
-                    float va[32];
-                    ldNf<32>(tD + tlane + (uint32_t)cb, va);
-#pragma unroll
-                    for (int k = 0; k < 32; ++k) {
-                        const float gk = fmaxf(va[k], 0.f);
-                        const float4 wk = wo[cb + k];
-                        acc.x = fmaf(wk.x, gk, acc.x);
-                        acc.y = fmaf(wk.y, gk, acc.y);
-                        acc.z = fmaf(wk.z, gk, acc.z);
-                    }
+                for (int q = 0; q < kGroups; ++q) {
+                    const float4 pp = *reinterpret_cast<const float4 *>(PART + sw_off(row, 2 + q));
+                    acc.x += pp.x;
+                    acc.y += pp.y;
+                    acc.z += pp.z;
                 }
                 const float r0 = sigmoid_f(acc.x), r1 = sigmoid_f(acc.y), r2 = sigmoid_f(acc.z);
                 const float dz0 = dl.y * r0 * (1.f - r0), dz1 = dl.z * r1 * (1.f - r1), dz2 = dl.w * r2 * (1.f - r2);
-                dsig = dl.x * sig_scale *
-                       (act == ROAM_RELU ? (s_logit > 0.f ? 1.f : 0.f) : sigmoid_f(s_logit));
-                uint8_t *xg = sm + B::kOffX + (H + 2) * kChunk;
+                uint32_t pg[CW / 2], pd[CW / 2];
 #pragma unroll
-                for (int c = 0; c < W; c += 16) {
-                    float va[16];
-                    ld16f(tD + tlane + (uint32_t)c, va);     // re-read: cheaper than holding all W in registers
-                    uint32_t pg[8], pd[8];
+                for (int q = 0; q < CW / 2; ++q) {
+                    float gg[2], dd[2];
 #pragma unroll
-                    for (int q = 0; q < 8; ++q) {
-                        float gg[2], dd[2];
-#pragma unroll
-                        for (int h = 0; h < 2; ++h) {
-                            const float zk = va[2 * q + h];
-                            const float4 wk = wo[c + 2 * q + h];
-                            gg[h] = fmaxf(zk, 0.f);
-                            dd[h] = zk > 0.f ? fmaf(wk.x, dz0, fmaf(wk.y, dz1, wk.z * dz2)) : 0.f;
-                        }
-                        pg[q] = pack_bf16(gg[0], gg[1]);
-                        pd[q] = pack_bf16(dd[0], dd[1]);
+                    for (int h = 0; h < 2; ++h) {
+                        const float zk = va[2 * q + h];
+                        const float4 wk = wo[c0 + 2 * q + h];
+                        gg[h] = fmaxf(zk, 0.f);
+                        dd[h] = zk > 0.f ? fmaf(wk.x, dz0, fmaf(wk.y, dz1, wk.z * dz2)) : 0.f;
                     }
-                    st_units<2>(xg, row, c / 8, pg);
-                    // dZ: colour rows in chunk 0 (columns 0..W-1), the 3-output layer's in chunk 1
-                    st_units<2>(DZ, row, c / 8, pd);
+                    pg[q] = pack_bf16(gg[0], gg[1]);
+                    pd[q] = pack_bf16(dd[0], dd[1]);
                 }
+                st_units<CU>(sm + B::kOffX + (H + 2) * kChunk, row, c0 / 8, pg);
+                // dZ: colour rows in chunk 0 (columns 0..W-1), the 3-output layer's in chunk 1
+                st_units<CU>(DZ, row, c0 / 8, pd);
                 store_tail(H + 2);
-                if constexpr (W == 32) {
+                if (g == 0) {
+                    dsig = dl.x * sig_scale * (act == ROAM_RELU ? (s_logit > 0.f ? 1.f : 0.f) : sigmoid_f(s_logit));
+                    if constexpr (W == 32) {
+                        uint32_t z4[16];
+#pragma unroll
+                        for (int q = 0; q < 16; ++q) z4[q] = 0u;
+                        st_units<4>(DZ, row, 4, z4);
+                    }
+                    uint32_t po[8];
+                    po[0] = pack_bf16(dz0, dz1);
+                    po[1] = pack_bf16(dz2, 0.f);
+#pragma unroll
+                    for (int q = 2; q < 8; ++q) po[q] = 0u;
+                    st_units<2>(DZ + kChunk, row, 0, po);
+                }
+            }
+        }
+        // ---- backward chain ----
+        const uint32_t wacc0 = wnew ? 0u : 1u;
+        // wgrad of layer l into its accumulator (N = its outputs)
+        auto issue_wgrad = [&](int l, uint32_t dza, uint32_t dz_lbo) {
+            const uint32_t xa = sX + (uint32_t)(l * kChunk);
+            const uint32_t td = tmem + (uint32_t)B::wcol(l);
+            if (l == H + 2) mma_wgrad<16>(td, xa, sT - xa, dza, dz_lbo, wacc0);
+            else if (l == H) mma_wgrad<S::N_HEAD>(td, xa, sT - xa, dza, dz_lbo, wacc0);
+            else mma_wgrad<W>(td, xa, sT - xa, dza, dz_lbo, wacc0);
+        };
+        // reads this thread's share of dX (D) and writes dZ of the layer
+        // below: masked by that layer's ReLU (X_i > 0) when i > 0, and at the
+        // head also the density column (group 0)
+        auto next_dz = [&](int i, bool relu, bool head) {
+            const uint8_t *xc = sm + B::kOffX + i * kChunk;
+            float va[CW];
+            ldcf<CW>(tDc, va);
+            uint32_t mk[CW / 2];
+#pragma unroll
+            for (int u = 0; u < CU; ++u) {
+                uint4 m = make_uint4(0xffffffffu, 0xffffffffu, 0xffffffffu, 0xffffffffu);
+                if (relu) m = *reinterpret_cast<const uint4 *>(xc + sw_off(row, c0 / 8 + u));
+                mk[4 * u] = m.x; mk[4 * u + 1] = m.y; mk[4 * u + 2] = m.z; mk[4 * u + 3] = m.w;
+            }
+            uint32_t p[CW / 2];
+#pragma unroll
+            for (int q = 0; q < CW / 2; ++q) {
+                float a = va[2 * q], bb = va[2 * q + 1];
+                if (relu) {
+                    if ((mk[q] & 0xffffu) == 0u) a = 0.f;
+                    if ((mk[q] >> 16) == 0u) bb = 0.f;
+                }
+                p[q] = pack_bf16(a, bb);
+            }
+            st_units<CU>(DZ, row, c0 / 8, p);
+            if (g == 0) {
+                if constexpr (W == 64) {
+                    if (head) {
+                        uint32_t po[8];
+                        po[0] = pack_bf16(dsig, 0.f);
+#pragma unroll
+                        for (int q = 1; q < 8; ++q) po[q] = 0u;
+                        st_units<2>(DZ + kChunk, row, 0, po);
+                    }
+                } else {
                     uint32_t z4[16];
 #pragma unroll
                     for (int q = 0; q < 16; ++q) z4[q] = 0u;
+                    if (head) z4[0] = pack_bf16(dsig, 0.f);
                     st_units<4>(DZ, row, 4, z4);
                 }
-                uint32_t po[8];
-                po[0] = pack_bf16(dz0, dz1);
-                po[1] = pack_bf16(dz2, 0.f);
-#pragma unroll
-                for (int q = 2; q < 8; ++q) po[q] = 0u;
-                st_units<2>(DZ + kChunk, row, 0, po);
             }
+        };
+
+        // output and colour layers (the barrier also agrees on the forward's last wait)
+        bool ok2 = publish(ok);
+        if (ok2) {
+            // independent accumulators, so three warps issue them side by side
+            if (tid == 0) issue_wgrad(H + 2, sDZ + kChunk, 1024u);
+            if (tid == 32) issue_wgrad(H + 1, sDZ, 1024u);
+            if (tid == 64) mma_dgrad<W, W>(tD, sDZ, sIMG + (uint32_t)S::offset(H + 1));
+            ok2 = land();
+            next_dz(H + 1, false, true);          // dZ of the head: [d feat | d logit | 0]
+            // head
+            ok2 = publish(ok2);
         }
-        if (!ok) {
+        if (ok2) {
+            if (tid == 0) issue_wgrad(H, sDZ, (uint32_t)kChunk);
+            if (tid == 32) mma_dgrad<W, S::N_HEAD>(tD, sDZ, sIMG + (uint32_t)S::offset(H));
+            ok2 = land();
+            next_dz(H, true, false);
+            // hidden layers H-1 .. 1
+#pragma unroll 1
+            for (int l = H - 1; l >= 1; --l) {
+                ok2 = publish(ok2);
+                if (!ok2) break;
+                if (tid == 0) issue_wgrad(l, sDZ, 1024u);
+                if (tid == 32) mma_dgrad<W, W>(tD, sDZ, sIMG + (uint32_t)S::offset(l));
+                ok2 = land();
+                next_dz(l, true, false);
+            }
+            ok2 = publish(ok2);
+        }
+        // first layer: wgrad only
+        if (ok2) {
+            if (issuer) issue_wgrad(0, sDZ, 1024u);
+            ok2 = land();
+            ok2 = __syncthreads_and(ok2) != 0;
+        }
+        if (!ok2) {
             aborted = true;
             break;
         }
-
-        // ---- backward chain ----
-        const uint32_t wacc0 = wnew ? 0u : 1u;
-        // wgrad of layer l: D_w(l)[k][n] += sum_s X[s][k] dZ[s][n]
-        auto issue_wgrad = [&](int l, uint32_t xa, uint32_t dza, uint32_t dz_lbo) {
-            const int N = B::wN(l);
-            const uint32_t idesc = idesc_bf16_t(N, 1, 1);
-            const uint32_t lbo_x = sT - xa;
-            const uint32_t td = tmem + (uint32_t)B::wcol(l);
-#pragma unroll 1
-            for (int j = 0; j < 8; ++j)
-                umma_ss(td, sdesc_mn(xa + (uint32_t)(j * 2048), lbo_x),
-                        sdesc_mn(dza + (uint32_t)(j * 2048), dz_lbo), idesc, (j > 0 || wacc0) ? 1u : 0u);
-        };
-        // dgrad of layer l: D[s][k] = sum_n dZ[s][n] W_l[n][k], k < W, over Kn outputs
-        auto issue_dgrad = [&](int l, int Kn) {
-            const uint32_t idesc = idesc_bf16_t(W, 0, 1);
-            const uint32_t ba = sIMG + (uint32_t)S::offset(l);
-#pragma unroll 1
-            for (int ks = 0; ks < Kn / 16; ++ks) {
-                const int ch = ks >> 2, kin = ks & 3;
-                umma_ss(tD, sdesc(sDZ + (uint32_t)(ch * kChunk + kin * 32)), sdesc_mn(ba + (uint32_t)(ks * 2048), 1024u),
-                        idesc, ks > 0 ? 1u : 0u);
-            }
-        };
-        // reads dX (W columns of D) and writes dZ of the layer below: masked by
-        // that layer's ReLU (X_i > 0) when i > 0, and at the head also the density column
-        auto next_dz = [&](int i, bool relu, bool head) {
-            const uint8_t *xc = sm + B::kOffX + i * kChunk;
-#pragma unroll
-            for (int cb = 0; cb < W; cb += 32) {
-                float va[32];
-                ldNf<32>(tD + tlane + (uint32_t)cb, va);
-#pragma unroll
-                for (int c0 = 0; c0 < 32; c0 += 16) {
-                    const int c = cb + c0;
-                    uint4 m0 = make_uint4(0u, 0u, 0u, 0u), m1 = m0;
-                    if (relu) {
-                        m0 = *reinterpret_cast<const uint4 *>(xc + sw_off(row, c / 8));
-                        m1 = *reinterpret_cast<const uint4 *>(xc + sw_off(row, c / 8 + 1));
-                    }
-                    const uint32_t mk[8] = {m0.x, m0.y, m0.z, m0.w, m1.x, m1.y, m1.z, m1.w};
-                    uint32_t p[8];
-#pragma unroll
-                    for (int q = 0; q < 8; ++q) {
-                        float a = va[c0 + 2 * q], bb = va[c0 + 2 * q + 1];
-                        if (relu) {
-                            if ((mk[q] & 0xffffu) == 0u) a = 0.f;
-                            if ((mk[q] >> 16) == 0u) bb = 0.f;
-                        }
-                        p[q] = pack_bf16(a, bb);
-                    }
-                    st_units<2>(DZ, row, c / 8, p);
-                }
-            }
-            if constexpr (W == 64) {
-                if (head) {
-                    uint32_t po[8];
-                    po[0] = pack_bf16(dsig, 0.f);
-#pragma unroll
-                    for (int q = 1; q < 8; ++q) po[q] = 0u;
-                    st_units<2>(DZ + kChunk, row, 0, po);
-                }
-            } else {
-                uint32_t z4[16];
-#pragma unroll
-                for (int q = 0; q < 16; ++q) z4[q] = 0u;
-                if (head) z4[0] = pack_bf16(dsig, 0.f);
-                st_units<4>(DZ, row, 4, z4);
-            }
-        };
-
-        // output and colour layers
-        publish();
-        // independent accumulators, so three warps issue them side by side
-        if (tid == 0) issue_wgrad(H + 2, sX + (uint32_t)((H + 2) * kChunk), sDZ + kChunk, 1024u);
-        if (tid == 32) issue_wgrad(H + 1, sX + (uint32_t)((H + 1) * kChunk), sDZ, 1024u);
-        if (tid == 64) issue_dgrad(H + 1, W);
-        if (!mma_wait()) { aborted = true; break; }
-        next_dz(H + 1, false, true);          // dZ of the head: [d feat | d logit | 0]
-        // head
-        publish();
-        if (tid == 0) issue_wgrad(H, sX + (uint32_t)(H * kChunk), sDZ, (uint32_t)kChunk);
-        if (tid == 32) issue_dgrad(H, S::N_HEAD);
-        if (!mma_wait()) { aborted = true; break; }
-        next_dz(H, true, false);
-        // hidden layers H-1 .. 1
-        bool ok2 = true;
-#pragma unroll 1
-        for (int l = H - 1; l >= 1; --l) {
-            publish();
-            if (tid == 0) issue_wgrad(l, sX + (uint32_t)(l * kChunk), sDZ, 1024u);
-            if (tid == 32) issue_dgrad(l, W);
-            if (!mma_wait()) { ok2 = false; break; }
-            next_dz(l, true, false);
-        }
-        if (!ok2) { aborted = true; break; }
-        // first layer: wgrad only
-        publish();
-        if (issuer) issue_wgrad(0, sX, sDZ, 1024u);
-        if (!mma_wait()) { aborted = true; break; }
         wnew = false;
         if (more) nxt = stage_finish(pend, src);
     }
@@ -602,7 +673,7 @@ void launch_bt(const MlpWeights &w, const SampleSrc &src, const BucketBufs &b, C
     const int smem = 1024 + BwShape<W, H>::kSmem;
     static int smem_set[kMaxDevices] = {};
     raise_smem_limit((const void *)k_mlp_bwd_tc<W, H>, smem, smem_set);
-    k_mlp_bwd_tc<W, H><<<n_sm, 128, smem, s>>>(w.wimg, w.img_bytes, w.affine, w.sigma_scale, w.act, w.P, src, b, ctr,
+    k_mlp_bwd_tc<W, H><<<n_sm, kBwThreads, smem, s>>>(w.wimg, w.img_bytes, w.affine, w.sigma_scale, w.act, w.P, src, b, ctr,
                                                 gsr, grad);
 }
 

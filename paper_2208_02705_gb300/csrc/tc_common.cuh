@@ -173,6 +173,25 @@ __device__ __forceinline__ void umma_ta(uint32_t d_tmem, uint32_t a_tmem, uint64
     }
 }
 
+// One layer's K loop with A in TMEM, fully unrolled: the B descriptor is
+// built once and stepped by compile-time offsets (its 14-bit start-address
+// field, in 16-byte units, cannot carry: every operand lies inside the CTA's
+// shared memory).  A descriptor rebuilt for every instruction triples the
+// issue time of an N <= 64 MMA (about 80 against 25 ns on GB300), which
+// then bounds the whole chain.
+template <bool F8, int K, int N>
+__device__ __forceinline__ void umma_chain_ta(uint32_t d_tmem, uint32_t a_tmem, uint32_t b_saddr)
+{
+    constexpr int kKS = F8 ? 32 : 16;                // K of one MMA (32 bytes)
+    constexpr uint32_t idesc = F8 ? idesc_e4m3(N) : idesc_bf16(N);
+    static_assert(K % kKS == 0, "whole MMAs");
+    const uint64_t db = sdesc(b_saddr);
+#pragma unroll
+    for (int ks = 0; ks < K / kKS; ++ks)
+        umma_ta<F8>(d_tmem, a_tmem + (uint32_t)(ks * 8),
+                    db + (uint64_t)(((ks >> 2) * N * 128 + (ks & 3) * 32) >> 4), idesc, ks > 0 ? 1u : 0u);
+}
+
 __device__ __forceinline__ void tmem_ld16_nowait(uint32_t taddr, uint32_t (&r)[16])
 {
     asm volatile(
@@ -281,6 +300,60 @@ __device__ __forceinline__ void encode1(float v, float (&s)[L], float (&c)[L])
             c[k] = fmaf(-2.0f * sp, sp, 1.0f);
         }
     }
+}
+
+// Packs e[first .. first + n) into the MMA's A words (BF16: elements 2c and
+// 2c + 1 in word c, low half first; E4M3: elements 4c .. 4c + 3 in word c);
+// the words whose elements all lie in that range.
+template <bool F8, int NW>
+__device__ __forceinline__ void pack_range(const float *e, uint32_t (&w)[NW], int first, int n)
+{
+    constexpr int per = F8 ? 4 : 2;
+#pragma unroll
+    for (int c = 0; c < NW; ++c) {
+        if (c * per < first || c * per + per > first + n) continue;
+        if constexpr (F8) w[c] = pack_e4m3x4(e[4 * c], e[4 * c + 1], e[4 * c + 2], e[4 * c + 3]);
+        else w[c] = pack_bf16(e[2 * c], e[2 * c + 1]);
+    }
+}
+
+// A block of the encoding F(v) = [v, sin(2^k pi v), cos(2^k pi v)] (k < L,
+// three sines then three cosines per k), frequency after frequency so that
+// each word is packed as soon as its elements exist (few live registers).
+// Layout: `lead` leading constant-1 elements, then F(v) (3 + 6 L), then
+// `trail_one` constant 1, then zeros up to 32 * NB elements.
+template <bool F8, int L, int kLead, bool kTrailOne, int NE>
+__device__ __forceinline__ void encode_packed(const float (&v)[3], uint32_t (&w)[F8 ? NE / 4 : NE / 2])
+{
+    constexpr int NW = F8 ? NE / 4 : NE / 2;
+    float e[NE];
+#pragma unroll
+    for (int q = 0; q < NE; ++q) e[q] = 0.f;
+#pragma unroll
+    for (int q = 0; q < kLead; ++q) e[q] = 1.0f;
+    e[kLead] = v[0]; e[kLead + 1] = v[1]; e[kLead + 2] = v[2];
+    if (kTrailOne) e[kLead + 3 + 6 * L] = 1.0f;
+    float sp[3], cp[3];
+#pragma unroll
+    for (int k = 0; k < L; ++k) {
+        // direct evaluation at k = 0 and k = 5, angle doubling in between
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            float sn, cs;
+            if (k == 0 || k == 5) {
+                sincospi_fast(v[a] * (float)(1 << k), sn, cs);
+            } else {
+                sn = 2.0f * sp[a] * cp[a];
+                cs = fmaf(-2.0f * sp[a], sp[a], 1.0f);
+            }
+            sp[a] = sn;
+            cp[a] = cs;
+            e[kLead + 3 + 6 * k + a] = sn;
+            e[kLead + 6 + 6 * k + a] = cs;
+        }
+        pack_range<F8, NW>(e, w, 0, kLead + 9 + 6 * k);
+    }
+    pack_range<F8, NW>(e, w, 0, NE);
 }
 
 // log(1 + e^s) and 1 / (1 + e^-s) with the hardware exp2/log2 and the fast

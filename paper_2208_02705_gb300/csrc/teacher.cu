@@ -296,11 +296,17 @@ __global__ void __launch_bounds__(kTThreads, 1)
                         const uint32_t s = i % kTStages;
                         ok = mbar_wait(&S.full[s], (i / kTStages) & 1u, abortp, status);
                         if (!ok) break;
-                        const uint32_t sa = smem_u32(ring + (size_t)s * kTChunk);
+                        // the chunk's (up to) four K steps: consecutive A columns (the
+                        // colour layer's F(x) block starts on a chunk boundary) and one
+                        // B descriptor stepped by 32 bytes, unrolled
+                        const uint64_t db = sdesc(smem_u32(ring + (size_t)s * kTChunk));
+                        const uint32_t a0 = tA + (uint32_t)a_col_of(l, 4 * c);
                         const int ks = min(4, L.ksteps - 4 * c);
-                        for (int kk = 0; kk < ks; ++kk)
-                            umma_ta<false>(tD, tA + (uint32_t)a_col_of(l, 4 * c + kk), sdesc(sa + kk * 32), idesc,
-                                           (c | kk) ? 1u : 0u);
+#pragma unroll
+                        for (int kk = 0; kk < 4; ++kk)
+                            if (kk < ks)
+                                umma_ta<false>(tD, a0 + (uint32_t)(kk * 8), db + (uint64_t)(kk * 2), idesc,
+                                               (c | kk) ? 1u : 0u);
                         umma_commit(&S.empty[s]);
                         any = true;
                     }
