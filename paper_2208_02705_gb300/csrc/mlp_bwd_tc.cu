@@ -271,6 +271,7 @@ __global__ void __launch_bounds__(kBwThreads, 1)
     using S = TcShape<W, H, false>;
     using B = BwShape<W, H>;
     constexpr int kLayers = S::kLayers;              // tensor-core layers of the forward chain
+    constexpr int kStageRec = kLayers >= 5 ? 2 : 1;  // the layer that gathers the next tile's records
     constexpr int CW = W / kGroups;                   // columns of one thread's share of a row
     constexpr int CU = CW / 8;                        // ... in 16-byte units
     extern __shared__ uint8_t smem_raw[];
@@ -337,12 +338,15 @@ __global__ void __launch_bounds__(kBwThreads, 1)
         tc_fence_after();
         return all;
     };
-    // commit the MMAs just issued and wait for them: true when they landed
-    auto land = [&]() -> bool {
+    // commit the MMAs just issued (before anything that may stall on a load)
+    auto commit = [&]() {
         if (lead) {
             umma_commit(&bar_d);
             ++n_commits;
         }
+    };
+    // wait for the committed group: true when it landed
+    auto land = [&]() -> bool {
         const bool got = mbar_wait(&bar_d, d_ph, abortp, status);
         if (lead && got) ++n_waits;
         d_ph ^= 1u;
@@ -373,20 +377,23 @@ __global__ void __launch_bounds__(kBwThreads, 1)
         tc_fence_before();
     };
 
-    // the next tile's sample is gathered in stages during this tile's forward
-    // layers (index, then record and ray, then position), so no stage waits
-    // on its own load
-    Tile tl_cur{0u, 0u, 0u, 0u};
+    // the next tile's sample is gathered in stages spread over this tile's
+    // MMA groups (index, then record and ray, then position, each two groups
+    // after the load it depends on); tile descriptors come two tiles ahead
+    Tile tl_cur{0u, 0u, 0u, 0u}, tl_ahead{0u, 0u, 0u, 0u};
     SampleIn nxt{0u, 0.f, 0.f, 0.f, 0.f, 0.f, 1.f};
     Pending pend{};
     if (t0 < t1) {
         tl_cur = b.tiles[t0];
+        if (t0 + 1 < t1) tl_ahead = b.tiles[t0 + 1];
         nxt = fetch_sample(src, b, tl_cur, row);
     }
+    float aff[6] = {1.f, 1.f, 1.f, 0.f, 0.f, 0.f};   // the current field's affine map
     for (uint32_t t = t0; t < t1 && !aborted; ++t) {
         const Tile tl = tl_cur;
         const bool more = t + 1 < t1;
-        const Tile tl_nx = more ? b.tiles[t + 1] : Tile{0u, 0u, 0u, 0u};
+        const Tile tl_nx = tl_ahead;
+        tl_ahead = t + 2 < t1 ? b.tiles[t + 2] : Tile{0u, 0u, 0u, 0u};
         const SampleIn smp = nxt;
         tl_cur = tl_nx;
         if (tl.count == 0) {
@@ -408,6 +415,10 @@ __global__ void __launch_bounds__(kBwThreads, 1)
                 }
                 w_pending = true;
             }
+            // the field's affine map lands while the image does
+            const float *af = affine + 6 * (int64_t)tl.field;
+#pragma unroll
+            for (int q = 0; q < 6; ++q) aff[q] = __ldg(af + q);
             // everyone waits for the image: the epilogues read its FP32 output table
             const bool ok = mbar_wait(&bar_w, w_ph, abortp, status);
             if (tid == 0 && ok) w_pending = false;
@@ -423,15 +434,13 @@ __global__ void __launch_bounds__(kBwThreads, 1)
         // ---- the sample ----
         const bool valid = (uint32_t)row < tl.count;
         const float4 dl = valid ? gsr[smp.idx] : make_float4(0.f, 0.f, 0.f, 0.f);
-        const float *aff = affine + 6 * (int64_t)tl.field;
 
         // ---- this thread's 16 columns of X_0 = [F(x_loc) | 1]; group 0 also
         // the tail [1 | F(d) | 0] ----
         uint32_t tailp[16];
         {
-            const float xl[3] = {fmaf(__ldg(aff + 0), smp.px, __ldg(aff + 3)),
-                                 fmaf(__ldg(aff + 1), smp.py, __ldg(aff + 4)),
-                                 fmaf(__ldg(aff + 2), smp.pz, __ldg(aff + 5))};
+            const float xl[3] = {fmaf(aff[0], smp.px, aff[3]), fmaf(aff[1], smp.py, aff[4]),
+                                 fmaf(aff[2], smp.pz, aff[5])};
             uint32_t p[8];
             switch (g) {
             case 0: enc_x0<0>(xl, p); break;
@@ -467,9 +476,10 @@ __global__ void __launch_bounds__(kBwThreads, 1)
                 else if (l == H) mma_fwd<S::K_HID, S::N_HEAD>(tD, xa, sT, ba);
                 else mma_fwd<S::K_COL, W>(tD, xa, sT, ba);
             }
+            commit();
             if (l == 0) stage_index(pend, b, tl_nx, row, more);
-            if (l == 1) stage_record(pend, src);
-            if (l == 2) stage_ray(pend, src);
+            if (l == kStageRec) stage_record(pend, src);
+            if (l == kLayers - 1) stage_ray(pend, src);
             ok = land();
             if (l < H) {
                 // next hidden input: ReLU
@@ -619,6 +629,7 @@ __global__ void __launch_bounds__(kBwThreads, 1)
             if (tid == 0) issue_wgrad(H + 2, sDZ + kChunk, 1024u);
             if (tid == 32) issue_wgrad(H + 1, sDZ, 1024u);
             if (tid == 64) mma_dgrad<W, W>(tD, sDZ, sIMG + (uint32_t)S::offset(H + 1));
+            commit();
             ok2 = land();
             next_dz(H + 1, false, true);          // dZ of the head: [d feat | d logit | 0]
             // head
@@ -627,6 +638,7 @@ __global__ void __launch_bounds__(kBwThreads, 1)
         if (ok2) {
             if (tid == 0) issue_wgrad(H, sDZ, (uint32_t)kChunk);
             if (tid == 32) mma_dgrad<W, S::N_HEAD>(tD, sDZ, sIMG + (uint32_t)S::offset(H));
+            commit();
             ok2 = land();
             next_dz(H, true, false);
             // hidden layers H-1 .. 1
@@ -636,7 +648,8 @@ __global__ void __launch_bounds__(kBwThreads, 1)
                 if (!ok2) break;
                 if (tid == 0) issue_wgrad(l, sDZ, 1024u);
                 if (tid == 32) mma_dgrad<W, W>(tD, sDZ, sIMG + (uint32_t)S::offset(l));
-                ok2 = land();
+                commit();
+            ok2 = land();
                 next_dz(l, true, false);
             }
             ok2 = publish(ok2);
@@ -644,6 +657,7 @@ __global__ void __launch_bounds__(kBwThreads, 1)
         // first layer: wgrad only
         if (ok2) {
             if (issuer) issue_wgrad(0, sDZ, 1024u);
+            commit();
             ok2 = land();
             ok2 = __syncthreads_and(ok2) != 0;
         }

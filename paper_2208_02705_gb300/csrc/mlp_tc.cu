@@ -77,6 +77,7 @@ __global__ void __launch_bounds__(TcShape<W, H, F8>::kSlots * 128, 1)
     using S = TcShape<W, H, F8>;
     constexpr int kSlots = S::kSlots;
     constexpr int kLayers = S::kLayers;
+    constexpr int kStageRec = kLayers >= 4 ? 1 : 0;  // the layer after which the next tile's records are gathered
     constexpr int kCols = S::kSlotCols;
     constexpr int kTmemAlloc = kSlots * kCols <= 32 ? 32 : (kSlots * kCols <= 64 ? 64 :
                                (kSlots * kCols <= 128 ? 128 : (kSlots * kCols <= 256 ? 256 : 512)));
@@ -327,8 +328,9 @@ __global__ void __launch_bounds__(TcShape<W, H, F8>::kSlots * 128, 1)
                 if (valid) out[sm.idx] = make_float4(sigma, sigmoid_f(acc.x), sigmoid_f(acc.y), sigmoid_f(acc.z));
             }
             tc_fence_before();
-            if (l == 0) stage_record(pend, src);
-            if (l == 1) stage_ray(pend, src);
+            // each gather stage a layer or more after the load it depends on
+            if (l == kStageRec) stage_record(pend, src);
+            if (l == kLayers - 2) stage_ray(pend, src);
         }
         if (!aborted) nxt = stage_finish(pend, src);
     }
