@@ -225,6 +225,15 @@ def time_steps(r, cams, opts, steps, warmup, flush, stream):
     return total, per
 
 
+def peaks_bf16():
+    """Dense BF16 burst TFLOP/s: the driver's measurement on this machine, else
+    the recipe's fallback (1.9 PFLOP/s)."""
+    try:
+        return float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["bf16_tflops"])
+    except (OSError, ValueError, KeyError):
+        return 1900.0
+
+
 def train_step_bench(roam, F, torch, wl, args, stream):
     """One fine-tuning step = forward (BF16 tensor cores) + L2 loss + adjoint
     (composite + BF16 tensor-core MLP adjoint) + Adam, on 65,536 rays of 16
@@ -273,6 +282,7 @@ def train_step_bench(roam, F, torch, wl, args, stream):
     r.close()
     out = {"workload": "floor256_kd512_w64h3, 16 equirect 1024x512 views, 65536 random rays, teacher+N(0,0.01^2) targets",
            "ms_per_step": ms, "rays_per_s": n / (ms / 1000.0), "samples_per_step": int(st.n_samples),
+           "composited_per_step": int(st.n_used),
            "loss_first_last": [float(losses[0]), float(losses[-1])],
            "kernels": {k: {"launches": v[0], "ms": round(v[1], 3)} for k, v in prof.items()},
            "precision": "forward BF16 tcgen05, adjoint BF16 tcgen05 (FP32 accumulation), FP32 master weights"}
@@ -282,8 +292,12 @@ def train_step_bench(roam, F, torch, wl, args, stream):
         macs = macs_per_sample(wl.W, wl.H)
         flops = 2.0 * (3 * macs - wl.W * 63)
         per_launch_s = bw[1] / bw[0] / 1000.0
-        samples = st.n_samples
-        out["mlp_adjoint"] = {"flops_per_sample": flops, "tflops": flops * samples / per_launch_s / 1e12,
+        # the adjoint runs over the composited samples (each ray's samples up
+        # to its termination, the ones the loss reaches), not every evaluated one
+        samples = st.n_used
+        out["mlp_adjoint"] = {"flops_per_sample": flops, "samples_per_launch": int(samples),
+                              "tflops": flops * samples / per_launch_s / 1e12,
+                              "frac_of_bf16_peak": flops * samples / per_launch_s / 1e12 / peaks_bf16(),
                               "ms_per_launch": bw[1] / bw[0]}
     return out
 

@@ -172,6 +172,120 @@ __device__ __forceinline__ int view_of(const DevCamera *cams, int n_views, uint3
     return lo;
 }
 
+// The ray of live slot i (ray index `ray`) at the start of its round: on
+// the first round built from its pixel and clipped against the grid box
+// (state initialised), later read back from the ray state.  False for a bad
+// (view, pixel) request, whose state is cleared and status flagged.  `lead`
+// selects the thread that writes the state (all callers compute the same values).
+__device__ __forceinline__ bool ray_begin(const GridDev &g, const MarchParams &p, uint32_t i, uint32_t ray, bool lead,
+                                          float3 &o, float3 &d, uint32_t &jn, uint32_t &je, uint32_t &nk)
+{
+    const float delta = p.delta;
+    if (p.init) {
+        uint32_t view, pix;
+        if (p.rays) {
+            view = p.rays[2 * ray];
+            pix = p.rays[2 * ray + 1];
+            if (view >= (uint32_t)p.n_views ||
+                pix >= (uint32_t)p.cams[view].width * (uint32_t)p.cams[view].height) {
+                if (lead) atomicOr(&p.ctr->status, kStatusBadSample);
+                if (lead) p.cnt[i] = 0;
+                if (lead) p.st.j_next[ray] = 0;
+                if (lead) p.st.j_end[ray] = 0;
+                if (lead) p.st.n_kept[ray] = 0;
+                if (lead) p.st.acc[ray] = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (lead) p.st.tw[ray] = make_float2(1.f, 0.f);
+                if (lead) p.st.orig[ray] = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (lead) p.st.dir[ray] = make_float4(0.f, 0.f, 1.f, 0.f);
+                return false;
+            }
+        } else {
+            view = (uint32_t)view_of(p.cams, p.n_views, ray);
+            pix = ray - p.cams[view].pix_start;
+        }
+        make_ray(p.cams[view], pix, o, d);
+        if (p.accurate) {
+            double3 dd;
+            make_ray64(p.cams[view], pix, dd);
+            d = make_float3((float)dd.x, (float)dd.y, (float)dd.z);
+            if (lead)
+                p.st.dir_lo[ray] = make_float4((float)(dd.x - (double)d.x), (float)(dd.y - (double)d.y),
+                                               (float)(dd.z - (double)d.z), 0.f);
+        }
+        if (lead) p.st.orig[ray] = make_float4(o.x, o.y, o.z, 0.f);
+        if (lead) p.st.dir[ray] = make_float4(d.x, d.y, d.z, 0.f);
+        // clip against the grid box in voxel units
+        const float og[3] = {(o.x - g.origin[0]) * g.inv_vox, (o.y - g.origin[1]) * g.inv_vox,
+                             (o.z - g.origin[2]) * g.inv_vox};
+        const float dg[3] = {d.x * g.inv_vox, d.y * g.inv_vox, d.z * g.inv_vox};
+        const float ext[3] = {(float)g.gx, (float)g.gy, (float)g.gz};
+        float t0 = 0.f, t1 = 3.0e38f;
+        bool miss = false;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            if (dg[a] == 0.f) {
+                if (og[a] < 0.f || og[a] >= ext[a]) miss = true;
+            } else {
+                float ta = (0.f - og[a]) / dg[a], tb = (ext[a] - og[a]) / dg[a];
+                if (ta > tb) { const float s = ta; ta = tb; tb = s; }
+                t0 = fmaxf(t0, ta);
+                t1 = fminf(t1, tb);
+            }
+        }
+        if (miss || t1 < t0) {
+            jn = je = 0;
+        } else {
+            const float js = floorf(t0 / delta - 0.5f) - 1.0f;
+            jn = js > 0.f ? (uint32_t)js : 0u;
+            je = (uint32_t)fmaxf(ceilf(t1 / delta - 0.5f) + 2.0f, 0.f);
+        }
+        nk = 0;
+        if (lead) p.st.j_end[ray] = je;
+        if (lead) p.st.acc[ray] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (lead) p.st.tw[ray] = make_float2(1.f, 0.f);
+    } else {
+        const float4 o4 = p.st.orig[ray], d4 = p.st.dir[ray];
+        o = make_float3(o4.x, o4.y, o4.z);
+        d = make_float3(d4.x, d4.y, d4.z);
+        jn = p.st.j_next[ray];
+        je = p.st.j_end[ray];
+        nk = p.st.n_kept[ray];
+    }
+    return true;
+}
+
+// First sample past the empty space around sample j's voxel (ix, iy, iz)
+// (clamped to je): out of an empty voxel to the first sample past its exit
+// face; out of an empty brick to the first sample past the exit of the cube
+// of bricks within Chebyshev distance dd - 1 (all empty; voxel units, clamped
+// to the grid), minus one sample so that a sample rounded onto that face is
+// still tested.  One code path for both jumps (fewer divergent branches).
+__device__ __forceinline__ uint32_t empty_jump(const GridDev &g, int dd, int ix, int iy, int iz, float ogx, float ogy,
+                                               float ogz, float dgx, float dgy, float dgz, float idx, float idy,
+                                               float idz, float delta, uint32_t je)
+{
+    const int bxi = ix >> kBrickShift, byi = iy >> kBrickShift, bzi = iz >> kBrickShift;
+    float ex, ey, ez, back;
+    if (dd > 0) {
+        const int r = dd - 1;
+        ex = dgx > 0.f ? (float)(min(bxi + r + 1, g.bx) << kBrickShift) : (float)(max(bxi - r, 0) << kBrickShift);
+        ey = dgy > 0.f ? (float)(min(byi + r + 1, g.by) << kBrickShift) : (float)(max(byi - r, 0) << kBrickShift);
+        ez = dgz > 0.f ? (float)(min(bzi + r + 1, g.bz) << kBrickShift) : (float)(max(bzi - r, 0) << kBrickShift);
+        back = 1.0f;
+    } else {
+        ex = dgx > 0.f ? (float)(ix + 1) : (float)ix;
+        ey = dgy > 0.f ? (float)(iy + 1) : (float)iy;
+        ez = dgz > 0.f ? (float)(iz + 1) : (float)iz;
+        back = 0.0f;
+    }
+    float te = 3.0e38f;
+    if (dgx != 0.f) te = fminf(te, (ex - ogx) * idx);
+    if (dgy != 0.f) te = fminf(te, (ey - ogy) * idy);
+    if (dgz != 0.f) te = fminf(te, (ez - ogz) * idz);
+    const float jf = ceilf(te / delta - 0.5f) - back;
+    return jf > (float)je ? je : (jf > 0.f ? (uint32_t)jf : 0u);
+}
+
 // Sample j of a ray sits at t_j = (j + 1/2) delta and is kept iff its voxel
 // floor((o + t_j d - origin) / vox) is inside the grid and occupied.  The
 // walk tests samples in occupied voxels one by one and jumps over empty
@@ -203,75 +317,7 @@ __global__ void __launch_bounds__(256) k_march(GridDev g, MarchParams p)
         const uint32_t ray = p.live ? p.live[i] : i;
         float3 o, d;
         uint32_t jn, je, nk;
-        if (p.init) {
-            uint32_t view, pix;
-            if (p.rays) {
-                view = p.rays[2 * ray];
-                pix = p.rays[2 * ray + 1];
-                if (view >= (uint32_t)p.n_views ||
-                    pix >= (uint32_t)p.cams[view].width * (uint32_t)p.cams[view].height) {
-                    atomicOr(&p.ctr->status, kStatusBadSample);
-                    p.cnt[i] = 0;
-                    p.st.j_next[ray] = 0;
-                    p.st.j_end[ray] = 0;
-                    p.st.n_kept[ray] = 0;
-                    p.st.acc[ray] = make_float4(0.f, 0.f, 0.f, 0.f);
-                    p.st.tw[ray] = make_float2(1.f, 0.f);
-                    p.st.orig[ray] = make_float4(0.f, 0.f, 0.f, 0.f);
-                    p.st.dir[ray] = make_float4(0.f, 0.f, 1.f, 0.f);
-                    continue;
-                }
-            } else {
-                view = (uint32_t)view_of(p.cams, p.n_views, ray);
-                pix = ray - p.cams[view].pix_start;
-            }
-            make_ray(p.cams[view], pix, o, d);
-            if (p.accurate) {
-                double3 dd;
-                make_ray64(p.cams[view], pix, dd);
-                d = make_float3((float)dd.x, (float)dd.y, (float)dd.z);
-                p.st.dir_lo[ray] = make_float4((float)(dd.x - (double)d.x), (float)(dd.y - (double)d.y),
-                                               (float)(dd.z - (double)d.z), 0.f);
-            }
-            p.st.orig[ray] = make_float4(o.x, o.y, o.z, 0.f);
-            p.st.dir[ray] = make_float4(d.x, d.y, d.z, 0.f);
-            // clip against the grid box in voxel units
-            const float og[3] = {(o.x - g.origin[0]) * g.inv_vox, (o.y - g.origin[1]) * g.inv_vox,
-                                 (o.z - g.origin[2]) * g.inv_vox};
-            const float dg[3] = {d.x * g.inv_vox, d.y * g.inv_vox, d.z * g.inv_vox};
-            const float ext[3] = {(float)g.gx, (float)g.gy, (float)g.gz};
-            float t0 = 0.f, t1 = 3.0e38f;
-            bool miss = false;
-#pragma unroll
-            for (int a = 0; a < 3; ++a) {
-                if (dg[a] == 0.f) {
-                    if (og[a] < 0.f || og[a] >= ext[a]) miss = true;
-                } else {
-                    float ta = (0.f - og[a]) / dg[a], tb = (ext[a] - og[a]) / dg[a];
-                    if (ta > tb) { const float s = ta; ta = tb; tb = s; }
-                    t0 = fmaxf(t0, ta);
-                    t1 = fminf(t1, tb);
-                }
-            }
-            if (miss || t1 < t0) {
-                jn = je = 0;
-            } else {
-                const float js = floorf(t0 / delta - 0.5f) - 1.0f;
-                jn = js > 0.f ? (uint32_t)js : 0u;
-                je = (uint32_t)fmaxf(ceilf(t1 / delta - 0.5f) + 2.0f, 0.f);
-            }
-            nk = 0;
-            p.st.j_end[ray] = je;
-            p.st.acc[ray] = make_float4(0.f, 0.f, 0.f, 0.f);
-            p.st.tw[ray] = make_float2(1.f, 0.f);
-        } else {
-            const float4 o4 = p.st.orig[ray], d4 = p.st.dir[ray];
-            o = make_float3(o4.x, o4.y, o4.z);
-            d = make_float3(d4.x, d4.y, d4.z);
-            jn = p.st.j_next[ray];
-            je = p.st.j_end[ray];
-            nk = p.st.n_kept[ray];
-        }
+        if (!ray_begin(g, p, i, ray, true, o, d, jn, je, nk)) continue;
         const float ogx = (o.x - g.origin[0]) * g.inv_vox, ogy = (o.y - g.origin[1]) * g.inv_vox,
                     ogz = (o.z - g.origin[2]) * g.inv_vox;
         const float dgx = d.x * g.inv_vox, dgy = d.y * g.inv_vox, dgz = d.z * g.inv_vox;
@@ -292,31 +338,7 @@ __global__ void __launch_bounds__(256) k_march(GridDev g, MarchParams p)
             const uint32_t b = (uint32_t)(ix & 31);
             const uint32_t w = dd > 0 ? 0u : __ldg(&g.bits[wi]);
             if (!((w >> b) & 1u)) {
-                // empty space, one code path for both jumps (fewer divergent
-                // branches per step): out of an empty voxel to the first sample
-                // past its exit face; out of an empty brick to the first sample
-                // past the exit of the cube of bricks within Chebyshev distance
-                // dd - 1 (all empty; voxel units, clamped to the grid), minus one
-                // sample so that a sample rounded onto that face is still tested
-                float ex, ey, ez, back;
-                if (dd > 0) {
-                    const int r = dd - 1;
-                    ex = dgx > 0.f ? (float)(min(bxi + r + 1, g.bx) << kBrickShift) : (float)(max(bxi - r, 0) << kBrickShift);
-                    ey = dgy > 0.f ? (float)(min(byi + r + 1, g.by) << kBrickShift) : (float)(max(byi - r, 0) << kBrickShift);
-                    ez = dgz > 0.f ? (float)(min(bzi + r + 1, g.bz) << kBrickShift) : (float)(max(bzi - r, 0) << kBrickShift);
-                    back = 1.0f;
-                } else {
-                    ex = dgx > 0.f ? (float)(ix + 1) : (float)ix;
-                    ey = dgy > 0.f ? (float)(iy + 1) : (float)iy;
-                    ez = dgz > 0.f ? (float)(iz + 1) : (float)iz;
-                    back = 0.0f;
-                }
-                float te = 3.0e38f;
-                if (dgx != 0.f) te = fminf(te, (ex - ogx) * idx);
-                if (dgy != 0.f) te = fminf(te, (ey - ogy) * idy);
-                if (dgz != 0.f) te = fminf(te, (ez - ogz) * idz);
-                const float jf = ceilf(te / delta - 0.5f) - back;
-                const uint32_t jj = jf > (float)je ? je : (jf > 0.f ? (uint32_t)jf : 0u);
+                const uint32_t jj = empty_jump(g, dd, ix, iy, iz, ogx, ogy, ogz, dgx, dgy, dgz, idx, idy, idz, delta, je);
                 jn = jj > jn + 1 ? jj : jn + 1;
                 continue;
             }
@@ -345,6 +367,7 @@ __global__ void __launch_bounds__(256) k_march(GridDev g, MarchParams p)
             if (s_hist[f]) atomicAdd(&p.hist[f], s_hist[f]);
     }
 }
+
 
 }  // namespace
 

@@ -42,33 +42,71 @@
 namespace roam {
 
 namespace {
-
 constexpr int kChunk = 16384;       // one 64-column chunk of 128 rows
-constexpr int kGroups = 4;          // column groups: threads per tile row
-constexpr int kBwThreads = 128 * kGroups;
+constexpr int kChains = 2;          // independent tile chains per CTA
+constexpr int kChainThreads = 256;  // 8 warps: 2 column groups x 4 TMEM lane quarters
+constexpr int kBwThreads = kChains * kChainThreads;
 
 template <int W, int H>
 struct BwShape {
     using S = TcShape<W, H, false>;
     static_assert(S::kFold, "the tensor-core adjoint folds every bias into the MMAs (BF16, W <= 64)");
-    static constexpr int kNX = H + 3;                 // X_0 .. X_{H+1}, X_g
+    static constexpr int kNBuf = H + 4;               // activation chunks shared by the two chains
     static constexpr int kOffX = S::kImageAlloc;
-    static constexpr int kOffT = kOffX + kNX * kChunk;
-    static constexpr int kOffDZ = kOffT + kChunk;
-    static constexpr int kSmem = kOffDZ + 2 * kChunk;
-    // TMEM: D (forward / dgrad accumulator) at column 0, then one wgrad
+    static constexpr int kOffDZ = kOffX + kNBuf * kChunk;
+    static constexpr int kOffT = kOffDZ + kChunk;     // after dZ: the head's dZ columns past 64 live in T
+    static constexpr int kSmem = kOffT + kChunk;
+    // TMEM: each chain's D (forward / dgrad accumulator), then one wgrad
     // accumulator per layer l = 0 .. H+2 (H+2 = the 3-output layer)
     static constexpr int kDCols = S::N_HEAD;
     __host__ __device__ static constexpr int wN(int l) { return l == H ? S::N_HEAD : (l == H + 2 ? 16 : W); }
     __host__ __device__ static constexpr int wcol(int l)
     {
-        int c = kDCols;
+        int c = kChains * kDCols;
         for (int i = 0; i < l; ++i) c += wN(i);
         return c;
     }
     static constexpr int kCols = wcol(H + 3);
-    static_assert(kCols <= 512, "TMEM holds D and every layer's wgrad accumulator");
+    static_assert(kCols <= 512, "TMEM holds both chains' D and every layer's wgrad accumulator");
+    // physical chunk of X_j for a tile of chain parity p: even tiles use
+    // 0 .. H+2, odd tiles H+3 for X_0 and H+3-j for j >= 1, so X_j of one
+    // chain reuses the chunk of the other chain's X_{H+3-j}
+    __host__ __device__ static constexpr int buf(int p, int j) { return p == 0 ? j : (j == 0 ? H + 3 : H + 3 - j); }
 };
+
+// Progress of a chain through its current tile, in one word:
+// (tile index within the CTA's run + 1) << 4 | n, where n = 0 when the
+// tile has started (its field's image is in place), n = 2 when its colour
+// and output wgrads have landed (X_{H+2}, X_{H+1} and the tail's F(d)
+// columns are free), n = H + 3 - l once X_l is free (its mask read by the
+// epilogue of layer l), and n = H + 3 when the tile is done (X_0, dZ and
+// every wgrad MMA).  Words only grow.
+__host__ __device__ constexpr uint32_t prog_word(uint32_t u_rel, uint32_t n) { return ((u_rel + 1u) << 4) | n; }
+
+// Waits until the other chain's progress word reaches `need`; false on an
+// abort (flagged by any thread) or after the wait limit.
+__device__ __forceinline__ bool wait_prog(const volatile uint32_t *p, uint32_t need, volatile int *abort_flag,
+                                          uint32_t *status)
+{
+    if (*p >= need) {
+        __threadfence_block();
+        return true;
+    }
+    const unsigned long long t0 = now_ns();
+    for (;;) {
+        __nanosleep(32);
+        if (*p >= need) {
+            __threadfence_block();
+            return true;
+        }
+        if (*abort_flag) return false;
+        if (now_ns() - t0 > kWaitNs) {
+            *abort_flag = 1;
+            atomicOr(status, kStatusTimeout);
+            return false;
+        }
+    }
+}
 
 // byte offset of 16-byte unit u (8 BF16 elements) of row r within a chunk
 __device__ __forceinline__ uint32_t sw_off(int r, int u)
@@ -204,18 +242,18 @@ __device__ __forceinline__ void mma_wgrad(uint32_t td, uint32_t xa, uint32_t lbo
     for (int j = 0; j < 8; ++j)
         umma_ss(td, da + (uint64_t)(j * 128), db + (uint64_t)(j * 128), idesc, (j > 0 || acc0) ? 1u : 0u);
 }
-//   dgrad: D[s][k] = sum_n dZ[s][n] W[n][k], k < W; A = dZ K-major (chunks
-//   16 KB apart), B = the image read MN-major, Kn / 16 MMAs
+//   dgrad: D[s][k] = sum_n dZ[s][n] W[n][k], k < W; A = dZ K-major (its
+//   columns 64..79, the head's, at sdz_hi), B = the image read MN-major,
+//   Kn / 16 MMAs
 template <int W, int Kn>
-__device__ __forceinline__ void mma_dgrad(uint32_t tD, uint32_t sdz, uint32_t ba)
+__device__ __forceinline__ void mma_dgrad(uint32_t tD, uint32_t sdz, uint32_t sdz_hi, uint32_t ba)
 {
+    static_assert(Kn <= 80, "dZ columns 64..79 at most past the first chunk");
     constexpr uint32_t idesc = idesc_bf16_t(W, 0, 1);
-    const uint64_t da = sdesc(sdz), db = sdesc_mn(ba, 1024u);
+    const uint64_t da = sdesc(sdz), dh = sdesc(sdz_hi), db = sdesc_mn(ba, 1024u);
 #pragma unroll
-    for (int ks = 0; ks < Kn / 16; ++ks) {
-        const int ch = ks >> 2, kin = ks & 3;
-        umma_ss(tD, da + (uint64_t)((ch * kChunk + kin * 32) >> 4), db + (uint64_t)(ks * 128), idesc, ks > 0 ? 1u : 0u);
-    }
+    for (int ks = 0; ks < Kn / 16; ++ks)
+        umma_ss(tD, (ks < 4 ? da + (uint64_t)(ks * 2) : dh), db + (uint64_t)(ks * 128), idesc, ks > 0 ? 1u : 0u);
 }
 
 // Where feature row k of wgrad accumulator l lands in the API layout (per
@@ -263,6 +301,7 @@ __device__ __forceinline__ RowMap row_map(int l, int k)
     return m;
 }
 
+
 template <int W, int H>
 __global__ void __launch_bounds__(kBwThreads, 1)
     k_mlp_bwd_tc(const void *wimg, int64_t img_bytes, const float *affine, float sig_scale, int act, int64_t P,
@@ -271,35 +310,43 @@ __global__ void __launch_bounds__(kBwThreads, 1)
     using S = TcShape<W, H, false>;
     using B = BwShape<W, H>;
     constexpr int kLayers = S::kLayers;              // tensor-core layers of the forward chain
-    constexpr int kStageRec = kLayers >= 5 ? 2 : 1;  // the layer that gathers the next tile's records
-    constexpr int CW = W / kGroups;                   // columns of one thread's share of a row
-    constexpr int CU = CW / 8;                        // ... in 16-byte units
+    constexpr int kStageRec = kLayers >= 5 ? 2 : 1;  // the layer that gathers the chain's next records
+    constexpr int CW = W / 2;                        // columns of one thread's share of a row
+    constexpr int NSB = CW / 16;                     // ... in 16-column sub-blocks
+    constexpr uint32_t kFull = (uint32_t)(H + 3);
     extern __shared__ uint8_t smem_raw[];
-    __shared__ uint64_t bar_d, bar_w;
-    __shared__ uint32_t tmem_slot;
+    __shared__ uint64_t bar_d[kChains], bar_w;
+    __shared__ uint32_t tmem_slot, img_field, n_img;
+    __shared__ volatile uint32_t prog[kChains];
     __shared__ int abort_flag;
 
     const uint32_t base = (smem_u32(smem_raw) + 1023u) & ~1023u;
     uint8_t *sm = smem_raw + (base - smem_u32(smem_raw));
     uint8_t *IMG = sm;
-    uint8_t *T = sm + B::kOffT;
     uint8_t *DZ = sm + B::kOffDZ;
-    uint8_t *PART = DZ + kChunk;                      // units 2..5 of dZ chunk 1: no MMA reads them
-    const uint32_t sIMG = base, sX = base + B::kOffX, sT = base + B::kOffT, sDZ = base + B::kOffDZ;
-    const int tid = threadIdx.x, warp = tid >> 5;
+    uint8_t *T = sm + B::kOffT;
+    const uint32_t sIMG = base, sX = base + B::kOffX, sDZ = base + B::kOffDZ, sT = base + B::kOffT;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int chain = warp >> 3;                      // tiles t0 + chain, t0 + chain + 2, ...
+    const int cw = warp & 7;                          // warp within the chain
     const int quarter = warp & 3;                     // TMEM lane quarter this warp may access
-    const int g = warp >> 2;                          // column group
-    const int row = quarter * 32 + (tid & 31);        // TMEM lane == tile row == sample
+    const int g = cw >> 2;                            // column group within the chain
+    const int row = quarter * 32 + lane;              // TMEM lane == tile row == sample
     const int c0 = g * CW;                            // first column of this thread's share
-    const bool issuer = tid == 0;                     // forward chain
-    const bool lead = (tid & 31) == 0 && warp < 4;    // warps 0..3 commit each MMA group (issuers: warps 0..2)
+    const int ctid = tid & (kChainThreads - 1);
+    const bool lead = lane == 0 && cw < 4;            // commits each MMA group (issuers: chain warps 0..2)
     volatile int *abortp = &abort_flag;
     uint32_t *status = &ctr->status;
 
     if (tid == 0) {
-        mbar_init(&bar_d, 4);                         // one commit per lead
+        mbar_init(&bar_d[0], 4);
+        mbar_init(&bar_d[1], 4);
         mbar_init(&bar_w, 1);
         abort_flag = 0;
+        img_field = 0xffffffffu;
+        n_img = 0;
+        prog[0] = 0u;
+        prog[1] = 0u;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 0) {
@@ -308,62 +355,88 @@ __global__ void __launch_bounds__(kBwThreads, 1)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
-    // T: at W = 64 its columns 32..63 stay zero (features 96..127 of the
-    // wgrad operands); at W = 32 all of it only pads those operands
+    // T: zero, with the constant-1 column 0 that the hidden, head and colour
+    // layers' bias rows read (W = 64; at W = 32 T only pads the wgrad operands)
     for (int q = tid; q < kChunk / 16; q += kBwThreads) reinterpret_cast<uint4 *>(T)[q] = make_uint4(0u, 0u, 0u, 0u);
+    __syncthreads();
+    if (W == 64 && tid < 128) *reinterpret_cast<uint32_t *>(T + sw_off(tid, 0)) = pack_bf16(1.0f, 0.f);
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = tmem_slot;
     const uint32_t tlane = (uint32_t)(quarter * 32) << 16;
-    const uint32_t tD = tmem;
-    const uint32_t tDc = tD + tlane + (uint32_t)c0;   // this thread's share of D
+    const uint32_t tD = tmem + (uint32_t)(chain * B::kDCols);
+    const uint32_t tDc = tD + tlane + (uint32_t)c0;   // this thread's share of its chain's D
+    // every wgrad accumulator starts at zero (the MMAs always accumulate)
+    {
+        uint32_t z[16];
+#pragma unroll
+        for (int q = 0; q < 16; ++q) z[q] = 0u;
+        for (int l = 0; l < H + 3; ++l)
+            for (int c = 16 * (warp >> 2); c < B::wN(l); c += 64) tmem_st16(tmem + tlane + (uint32_t)(B::wcol(l) + c), z);
+        tmem_wait_st();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
 
     const uint32_t n_tiles = ctr->n_tiles;
     const uint32_t t0 = (uint32_t)((uint64_t)n_tiles * blockIdx.x / gridDim.x);
     const uint32_t t1 = (uint32_t)((uint64_t)n_tiles * (blockIdx.x + 1) / gridDim.x);
+    const volatile uint32_t *other = &prog[chain ^ 1];
 
-    uint32_t d_ph = 0, w_ph = 0, n_commits = 0, n_waits = 0;
-    bool w_pending = false;              // an image load in flight (thread 0's view)
-    uint32_t cur = 0xffffffffu;
-    bool wnew = true;                    // the wgrad accumulators hold nothing yet
+    uint32_t d_ph = 0, n_commits = 0, n_waits = 0;
+    bool w_pending = false;              // an image load in flight (the issuing thread's view)
     bool aborted = false;
 
-    // every thread's generic shared-memory stores become visible to the
-    // MMAs; the barrier also agrees on `good` (every thread's last wait)
+
+    // the chain's barrier: its threads' generic shared-memory stores become
+    // visible to the MMAs, and it agrees on `good` (every thread's last wait)
     auto publish = [&](bool good) -> bool {
         fence_async_smem();
         tc_fence_before();
-        const bool all = __syncthreads_and(good) != 0;
+        const bool bad = named_sync_or(1 + chain, kChainThreads, !good || *abortp);
         tc_fence_after();
-        return all;
+        return !bad;
     };
-    // commit the MMAs just issued (before anything that may stall on a load)
     auto commit = [&]() {
         if (lead) {
-            umma_commit(&bar_d);
+            umma_commit(&bar_d[chain]);
             ++n_commits;
         }
     };
-    // wait for the committed group: true when it landed
+    // wait for the chain's committed group: true when it landed
     auto land = [&]() -> bool {
-        const bool got = mbar_wait(&bar_d, d_ph, abortp, status);
+        const bool got = mbar_wait(&bar_d[chain], d_ph, abortp, status);
         if (lead && got) ++n_waits;
         d_ph ^= 1u;
         tc_fence_after();
         return got;
     };
-    // flush the wgrad accumulators of field f to the global gradient; the
-    // 16-column pieces of each layer go round the column groups
-    auto flush = [&](uint32_t f) {
+    // the chain's progress word (by its first thread, after whatever the
+    // word promises has happened for every thread of the chain)
+    auto progress = [&](uint32_t u_rel, uint32_t n) {
+        if (ctid == 0) {
+            __threadfence_block();
+            prog[chain] = prog_word(u_rel, n);
+        }
+    };
+    // add the wgrad accumulators of field f to the global gradient and clear
+    // them; the 16-column pieces of each layer go round `ng` column groups
+    auto flush = [&](uint32_t f, int gid, int ng) {
         float *gf = grad + (int64_t)f * P;
+        uint32_t z[16];
+#pragma unroll
+        for (int q = 0; q < 16; ++q) z[q] = 0u;
 #pragma unroll 1
         for (int l = 0; l < H + 3; ++l) {
             const RowMap m = row_map<W, H>(l, row);
 #pragma unroll 1
-            for (int c = 16 * g; c < B::wN(l); c += 16 * kGroups) {
+            for (int c = 16 * gid; c < B::wN(l); c += 16 * ng) {
+                const uint32_t ta = tmem + tlane + (uint32_t)(B::wcol(l) + c);
                 float v[16];
-                ld16f(tmem + tlane + (uint32_t)(B::wcol(l) + c), v);
+                ld16f(ta, v);
+                tmem_st16(ta, z);
                 if (m.base < 0) continue;
 #pragma unroll
                 for (int q = 0; q < 16; ++q) {
@@ -374,39 +447,83 @@ __global__ void __launch_bounds__(kBwThreads, 1)
                 }
             }
         }
+        tmem_wait_st();
         tc_fence_before();
     };
+    // 16-byte unit u of row `row` in chunk X_j of a tile of parity p
+    auto xchunk = [&](int p, int j) -> uint8_t * { return sm + B::kOffX + B::buf(p, j) * kChunk; };
+    auto xaddr = [&](int p, int j) -> uint32_t { return sX + (uint32_t)(B::buf(p, j) * kChunk); };
 
-    // the next tile's sample is gathered in stages spread over this tile's
-    // MMA groups (index, then record and ray, then position, each two groups
-    // after the load it depends on); tile descriptors come two tiles ahead
-    Tile tl_cur{0u, 0u, 0u, 0u}, tl_ahead{0u, 0u, 0u, 0u};
+
+    // the chain's tiles t0 + chain, t0 + chain + 2, ...: the current one, the
+    // next (its sample gathered in stages during this one) and the one after
+    Tile tl_cur{0u, 0u, 0u, 0u}, tl_nx{0u, 0u, 0u, 0u};
     SampleIn nxt{0u, 0.f, 0.f, 0.f, 0.f, 0.f, 1.f};
     Pending pend{};
-    if (t0 < t1) {
-        tl_cur = b.tiles[t0];
-        if (t0 + 1 < t1) tl_ahead = b.tiles[t0 + 1];
+    float aff_n[6] = {1.f, 1.f, 1.f, 0.f, 0.f, 0.f};  // the next tile's affine map
+    auto load_aff = [&](const Tile &tt) {
+        if (tt.count == 0) return;
+        const float *af = affine + 6 * (int64_t)tt.field;
+#pragma unroll
+        for (int q = 0; q < 6; ++q) aff_n[q] = __ldg(af + q);
+    };
+    if (t0 + chain < t1) {
+        tl_cur = b.tiles[t0 + chain];
         nxt = fetch_sample(src, b, tl_cur, row);
+        load_aff(tl_cur);
+        if (t0 + chain + kChains < t1) tl_nx = b.tiles[t0 + chain + kChains];
     }
-    float aff[6] = {1.f, 1.f, 1.f, 0.f, 0.f, 0.f};   // the current field's affine map
-    for (uint32_t t = t0; t < t1 && !aborted; ++t) {
+    uint32_t w_pend_ph = 0;
+    bool good = true;                    // this thread's last wait
+#pragma unroll 1
+    for (uint32_t t = t0 + chain; t < t1 && !aborted; t += kChains) {
+        const uint32_t u_rel = t - t0;
         const Tile tl = tl_cur;
-        const bool more = t + 1 < t1;
-        const Tile tl_nx = tl_ahead;
-        tl_ahead = t + 2 < t1 ? b.tiles[t + 2] : Tile{0u, 0u, 0u, 0u};
+        const bool more = t + kChains < t1;
+        const Tile tl_next = tl_nx;
+        tl_nx = t + 2 * kChains < t1 ? b.tiles[t + 2 * kChains] : Tile{0u, 0u, 0u, 0u};
+        tl_cur = tl_next;
         const SampleIn smp = nxt;
-        tl_cur = tl_nx;
+        float aff[6];
+#pragma unroll
+        for (int q = 0; q < 6; ++q) aff[q] = aff_n[q];
         if (tl.count == 0) {
-            if (more) nxt = fetch_sample(src, b, tl_nx, row);
+            // keeps the run's order: done once the tile before it is
+            bool ok = good && (u_rel == 0 || wait_prog(other, prog_word(u_rel - 1, kFull), abortp, status));
+            if (!publish(ok)) {
+                aborted = true;
+                break;
+            }
+            progress(u_rel, kFull);
+            if (more) {
+                nxt = fetch_sample(src, b, tl_next, row);
+                load_aff(tl_next);
+            }
             continue;
         }
-        if (tl.field != cur) {
-            if (cur != 0xffffffffu && !wnew) flush(cur);
-            // generic reads of the old image (the epilogue tables) come before
-            // the bulk copy that overwrites it
-            fence_async_smem();
-            __syncthreads();
-            if (tid == 0) {
+        // the tile before has settled the image (its field is img_field)
+        bool ok = good && (u_rel == 0 || wait_prog(other, prog_word(u_rel - 1, 0), abortp, status));
+        if (!publish(ok)) {
+            aborted = true;
+            break;
+        }
+        if (tl.field != img_field) {
+            // a new field: every tile of the old one done, its gradient
+            // flushed, then this field's image
+            ok = u_rel == 0 || wait_prog(other, prog_word(u_rel - 1, kFull), abortp, status);
+            if (!publish(ok)) {
+                aborted = true;
+                break;
+            }
+            if (img_field != 0xffffffffu) flush(img_field, g, 2);
+            // generic reads of the old image come before the bulk copy that
+            // overwrites it (the other chain fenced its own before its last word)
+            if (!publish(true)) {
+                aborted = true;
+                break;
+            }
+            const uint32_t wph = n_img & 1u;
+            if (ctid == 0) {
                 mbar_expect_tx(&bar_w, (uint32_t)S::kImageBytes);
                 const uint8_t *gsrc = reinterpret_cast<const uint8_t *>(wimg) + (int64_t)tl.field * img_bytes;
                 for (int off = 0; off < S::kImageBytes; off += 16384) {
@@ -414,62 +531,65 @@ __global__ void __launch_bounds__(kBwThreads, 1)
                     bulk_g2s(IMG + off, gsrc + off, (uint32_t)nb, &bar_w);
                 }
                 w_pending = true;
+                w_pend_ph = wph;
             }
-            // the field's affine map lands while the image does
-            const float *af = affine + 6 * (int64_t)tl.field;
-#pragma unroll
-            for (int q = 0; q < 6; ++q) aff[q] = __ldg(af + q);
-            // everyone waits for the image: the epilogues read its FP32 output table
-            const bool ok = mbar_wait(&bar_w, w_ph, abortp, status);
-            if (tid == 0 && ok) w_pending = false;
-            w_ph ^= 1u;
-            if (!__syncthreads_and(ok)) {
+            ok = mbar_wait(&bar_w, wph, abortp, status);
+            if (ctid == 0 && ok) w_pending = false;
+            if (!publish(ok)) {
                 aborted = true;
                 break;
             }
-            cur = tl.field;
-            wnew = true;
+            if (ctid == 0) {
+                img_field = tl.field;
+                n_img = n_img + 1u;
+            }
         }
+        progress(u_rel, 0);
 
         // ---- the sample ----
         const bool valid = (uint32_t)row < tl.count;
         const float4 dl = valid ? gsr[smp.idx] : make_float4(0.f, 0.f, 0.f, 0.f);
-
-        // ---- this thread's 16 columns of X_0 = [F(x_loc) | 1]; group 0 also
-        // the tail [1 | F(d) | 0] ----
+        // ---- this thread's 32 columns of X_0 = [F(x_loc) | 1] (its own
+        // chunk: no wait); at W = 32 group 0 also packs the tail
+        // [1 | F(d) | 0] that every X_i carries ----
         uint32_t tailp[16];
         {
             const float xl[3] = {fmaf(aff[0], smp.px, aff[3]), fmaf(aff[1], smp.py, aff[4]),
                                  fmaf(aff[2], smp.pz, aff[5])};
+            uint8_t *x0 = xchunk(chain, 0);
             uint32_t p[8];
-            switch (g) {
-            case 0: enc_x0<0>(xl, p); break;
-            case 1: enc_x0<1>(xl, p); break;
-            case 2: enc_x0<2>(xl, p); break;
-            default: enc_x0<3>(xl, p); break;
-            }
-            st_units<2>(sm + B::kOffX, row, 2 * g, p);
             if (g == 0) {
-                const float dv[3] = {smp.dx, smp.dy, smp.dz};
-                encode_packed<false, 4, 1, false, 32>(dv, tailp);
-                if constexpr (W == 64) st_units<4>(T, row, 0, tailp);
+                enc_x0<0>(xl, p);
+                st_units<2>(x0, row, 0, p);
+                enc_x0<1>(xl, p);
+                st_units<2>(x0, row, 2, p);
+                if constexpr (W == 32) {
+                    const float dv[3] = {smp.dx, smp.dy, smp.dz};
+                    encode_packed<false, 4, 1, false, 32>(dv, tailp);
+                }
+            } else {
+                enc_x0<2>(xl, p);
+                st_units<2>(x0, row, 4, p);
+                enc_x0<3>(xl, p);
+                st_units<2>(x0, row, 6, p);
             }
         }
-        // row `row` of X_i: the tail at W = 32 (columns 32..63), by group 0
+        // the tail of X_i at W = 32 (columns 32..63), by group 0
         auto store_tail = [&](int i) {
             if constexpr (W == 32)
-                if (g == 0) st_units<4>(sm + B::kOffX + i * kChunk, row, 4, tailp);
+                if (g == 0) st_units<4>(xchunk(chain, i), row, 4, tailp);
         };
+
+
         // ---- forward chain ----
         float s_logit = 0.f;
         float dsig = 0.f;
-        bool ok = true;
 #pragma unroll 1
         for (int l = 0; l < kLayers; ++l) {
             ok = publish(ok);
             if (!ok) break;
-            if (issuer) {
-                const uint32_t xa = sX + (uint32_t)(l * kChunk);
+            if (ctid == 0) {
+                const uint32_t xa = xaddr(chain, l);
                 const uint32_t ba = sIMG + (uint32_t)S::offset(l);
                 if (l == 0) mma_fwd<S::K(0), W>(tD, xa, sT, ba);
                 else if (l < H) mma_fwd<S::K_HID, W>(tD, xa, sT, ba);
@@ -477,79 +597,112 @@ __global__ void __launch_bounds__(kBwThreads, 1)
                 else mma_fwd<S::K_COL, W>(tD, xa, sT, ba);
             }
             commit();
-            if (l == 0) stage_index(pend, b, tl_nx, row, more);
+            if (l == 0) stage_index(pend, b, tl_next, row, more);
             if (l == kStageRec) stage_record(pend, src);
-            if (l == kLayers - 1) stage_ray(pend, src);
+            if (l == kLayers - 1) {
+                stage_ray(pend, src);
+                if (more) load_aff(tl_next);
+            }
             ok = land();
+            // the chunk this epilogue writes held the other chain's X_{H+3-j}
+            // (the colour layer also writes dZ and the tail's columns 64..127)
+            const int j = l + 1;
+            const uint32_t need = l == kLayers - 1 ? kFull : (uint32_t)(j > 2 ? j : 2);
+            if (ok && u_rel > 0) ok = wait_prog(other, prog_word(u_rel - 1, need), abortp, status);
             if (l < H) {
                 // next hidden input: ReLU
-                float va[CW];
-                ldcf<CW>(tDc, va);
-                uint32_t p[CW / 2];
+                uint8_t *xc = xchunk(chain, l + 1);
 #pragma unroll
-                for (int q = 0; q < CW / 2; ++q) p[q] = pack_bf16_relu(va[2 * q], va[2 * q + 1]);
-                st_units<CU>(sm + B::kOffX + (l + 1) * kChunk, row, c0 / 8, p);
+                for (int sb = 0; sb < NSB; ++sb) {
+                    float va[16];
+                    ldcf<16>(tDc + (uint32_t)(16 * sb), va);
+                    uint32_t p[8];
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) p[q] = pack_bf16_relu(va[2 * q], va[2 * q + 1]);
+                    st_units<2>(xc, row, (c0 + 16 * sb) / 8, p);
+                }
                 store_tail(l + 1);
             } else if (l == H) {
                 // head: features (linear) -> colour input, column W = density logit
-                float va[CW];
-                ldcf<CW>(tDc, va);
-                uint32_t p[CW / 2];
+                uint8_t *xc = xchunk(chain, H + 1);
 #pragma unroll
-                for (int q = 0; q < CW / 2; ++q) p[q] = pack_bf16(va[2 * q], va[2 * q + 1]);
-                st_units<CU>(sm + B::kOffX + (H + 1) * kChunk, row, c0 / 8, p);
+                for (int sb = 0; sb < NSB; ++sb) {
+                    float va[16];
+                    ldcf<16>(tDc + (uint32_t)(16 * sb), va);
+                    uint32_t p[8];
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) p[q] = pack_bf16(va[2 * q], va[2 * q + 1]);
+                    st_units<2>(xc, row, (c0 + 16 * sb) / 8, p);
+                }
                 if (g == 0) {
                     float v[8];
                     ldcf<8>(tD + tlane + (uint32_t)W, v);
                     s_logit = v[0];
                 }
                 store_tail(H + 1);
-            } else {
+            }
+            // this tile's F(d) in the shared tail, once the other chain's
+            // colour wgrad no longer reads it (with X_2)
+            if (W == 64 && l == 1 && g == 0) {
+                const float dv[3] = {smp.dx, smp.dy, smp.dz};
+                encode_packed<false, 4, 1, false, 32>(dv, tailp);
+                st_units<4>(T, row, 0, tailp);
+            }
+            if (l == kLayers - 1) {
                 // colour: z -> g = relu(z) (X_g), rgb = sigmoid(Wo g + bo) in FP32, then
                 // the output layer's adjoint and dZ of the colour layer
                 const float4 *wo = reinterpret_cast<const float4 *>(IMG + S::kMatBytes);
-                float va[CW];
-                ldcf<CW>(tDc, va);
                 float ax = 0.f, ay = 0.f, az = 0.f;
 #pragma unroll
-                for (int k = 0; k < CW; ++k) {
-                    const float gk = fmaxf(va[k], 0.f);
-                    const float4 wk = wo[c0 + k];
-                    ax = fmaf(wk.x, gk, ax);
-                    ay = fmaf(wk.y, gk, ay);
-                    az = fmaf(wk.z, gk, az);
+                for (int sb = 0; sb < NSB; ++sb) {
+                    float va[16];
+                    ldcf<16>(tDc + (uint32_t)(16 * sb), va);
+#pragma unroll
+                    for (int k = 0; k < 16; ++k) {
+                        const float gk = fmaxf(va[k], 0.f);
+                        const float4 wk = wo[c0 + 16 * sb + k];
+                        ax = fmaf(wk.x, gk, ax);
+                        ay = fmaf(wk.y, gk, ay);
+                        az = fmaf(wk.z, gk, az);
+                    }
                 }
-                // the four groups' partial sums of the row meet in shared
-                // memory; everyone adds them in group order
-                *reinterpret_cast<float4 *>(PART + sw_off(row, 2 + g)) = make_float4(ax, ay, az, 0.f);
-                asm volatile("bar.sync %0, %1;" ::"r"(1 + quarter), "r"(32 * kGroups) : "memory");
+                // the two column groups' partial sums of the row meet in
+                // units 6 and 7 of the tail (no MMA reads those as anything
+                // but ignored feature rows); both add them in group order
+                *reinterpret_cast<float4 *>(T + sw_off(row, 6 + g)) = make_float4(ax, ay, az, 0.f);
+                asm volatile("bar.sync %0, %1;" ::"r"(3 + 4 * chain + quarter), "r"(64) : "memory");
                 float4 acc = wo[W];
 #pragma unroll
-                for (int q = 0; q < kGroups; ++q) {
-                    const float4 pp = *reinterpret_cast<const float4 *>(PART + sw_off(row, 2 + q));
+                for (int q = 0; q < 2; ++q) {
+                    const float4 pp = *reinterpret_cast<const float4 *>(T + sw_off(row, 6 + q));
                     acc.x += pp.x;
                     acc.y += pp.y;
                     acc.z += pp.z;
                 }
                 const float r0 = sigmoid_f(acc.x), r1 = sigmoid_f(acc.y), r2 = sigmoid_f(acc.z);
                 const float dz0 = dl.y * r0 * (1.f - r0), dz1 = dl.z * r1 * (1.f - r1), dz2 = dl.w * r2 * (1.f - r2);
-                uint32_t pg[CW / 2], pd[CW / 2];
+                uint8_t *xg = xchunk(chain, H + 2);
 #pragma unroll
-                for (int q = 0; q < CW / 2; ++q) {
-                    float gg[2], dd[2];
+                for (int sb = 0; sb < NSB; ++sb) {
+                    float va[16];
+                    ldcf<16>(tDc + (uint32_t)(16 * sb), va);     // re-read: cheaper than holding them
+                    uint32_t pg[8], pd[8];
 #pragma unroll
-                    for (int h = 0; h < 2; ++h) {
-                        const float zk = va[2 * q + h];
-                        const float4 wk = wo[c0 + 2 * q + h];
-                        gg[h] = fmaxf(zk, 0.f);
-                        dd[h] = zk > 0.f ? fmaf(wk.x, dz0, fmaf(wk.y, dz1, wk.z * dz2)) : 0.f;
+                    for (int q = 0; q < 8; ++q) {
+                        float gg[2], dd[2];
+#pragma unroll
+                        for (int h = 0; h < 2; ++h) {
+                            const float zk = va[2 * q + h];
+                            const float4 wk = wo[c0 + 16 * sb + 2 * q + h];
+                            gg[h] = fmaxf(zk, 0.f);
+                            dd[h] = zk > 0.f ? fmaf(wk.x, dz0, fmaf(wk.y, dz1, wk.z * dz2)) : 0.f;
+                        }
+                        pg[q] = pack_bf16(gg[0], gg[1]);
+                        pd[q] = pack_bf16(dd[0], dd[1]);
                     }
-                    pg[q] = pack_bf16(gg[0], gg[1]);
-                    pd[q] = pack_bf16(dd[0], dd[1]);
+                    st_units<2>(xg, row, (c0 + 16 * sb) / 8, pg);
+                    st_units<2>(DZ, row, (c0 + 16 * sb) / 8, pd);     // dZ of the colour layer
                 }
-                st_units<CU>(sm + B::kOffX + (H + 2) * kChunk, row, c0 / 8, pg);
-                // dZ: colour rows in chunk 0 (columns 0..W-1), the 3-output layer's in chunk 1
-                st_units<CU>(DZ, row, c0 / 8, pd);
                 store_tail(H + 2);
                 if (g == 0) {
                     dsig = dl.x * sig_scale * (act == ROAM_RELU ? (s_logit > 0.f ? 1.f : 0.f) : sigmoid_f(s_logit));
@@ -559,50 +712,58 @@ __global__ void __launch_bounds__(kBwThreads, 1)
                         for (int q = 0; q < 16; ++q) z4[q] = 0u;
                         st_units<4>(DZ, row, 4, z4);
                     }
+                    // dZ of the 3-output layer: units 4..5 of the tail
                     uint32_t po[8];
                     po[0] = pack_bf16(dz0, dz1);
                     po[1] = pack_bf16(dz2, 0.f);
 #pragma unroll
                     for (int q = 2; q < 8; ++q) po[q] = 0u;
-                    st_units<2>(DZ + kChunk, row, 0, po);
+                    st_units<2>(T, row, 4, po);
                 }
             }
         }
+
+
         // ---- backward chain ----
-        const uint32_t wacc0 = wnew ? 0u : 1u;
-        // wgrad of layer l into its accumulator (N = its outputs)
-        auto issue_wgrad = [&](int l, uint32_t dza, uint32_t dz_lbo) {
-            const uint32_t xa = sX + (uint32_t)(l * kChunk);
+        // wgrad of layer l into its accumulator (N = its outputs); the dZ
+        // operand's second 64-column block (the head's columns 64..79) sits
+        // at byte 64 of the tail's rows
+        auto issue_wgrad = [&](int l, uint32_t dza) {
+            const uint32_t xa = xaddr(chain, l);
             const uint32_t td = tmem + (uint32_t)B::wcol(l);
-            if (l == H + 2) mma_wgrad<16>(td, xa, sT - xa, dza, dz_lbo, wacc0);
-            else if (l == H) mma_wgrad<S::N_HEAD>(td, xa, sT - xa, dza, dz_lbo, wacc0);
-            else mma_wgrad<W>(td, xa, sT - xa, dza, dz_lbo, wacc0);
+            if (l == H + 2) mma_wgrad<16>(td, xa, sT - xa, dza, 1024u, 1u);
+            else if (l == H) mma_wgrad<S::N_HEAD>(td, xa, sT - xa, dza, sT + 64u - dza, 1u);
+            else mma_wgrad<W>(td, xa, sT - xa, dza, 1024u, 1u);
         };
-        // reads this thread's share of dX (D) and writes dZ of the layer
-        // below: masked by that layer's ReLU (X_i > 0) when i > 0, and at the
-        // head also the density column (group 0)
+        // reads this thread's share of dX (its chain's D) and writes dZ of the
+        // layer below: masked by that layer's ReLU (X_i > 0) when i > 0, and
+        // at the head also the density column (group 0)
         auto next_dz = [&](int i, bool relu, bool head) {
-            const uint8_t *xc = sm + B::kOffX + i * kChunk;
-            float va[CW];
-            ldcf<CW>(tDc, va);
-            uint32_t mk[CW / 2];
+            const uint8_t *xc = xchunk(chain, i);
 #pragma unroll
-            for (int u = 0; u < CU; ++u) {
-                uint4 m = make_uint4(0xffffffffu, 0xffffffffu, 0xffffffffu, 0xffffffffu);
-                if (relu) m = *reinterpret_cast<const uint4 *>(xc + sw_off(row, c0 / 8 + u));
-                mk[4 * u] = m.x; mk[4 * u + 1] = m.y; mk[4 * u + 2] = m.z; mk[4 * u + 3] = m.w;
-            }
-            uint32_t p[CW / 2];
+            for (int sb = 0; sb < NSB; ++sb) {
+                const int u0 = (c0 + 16 * sb) / 8;
+                float va[16];
+                ldcf<16>(tDc + (uint32_t)(16 * sb), va);
+                uint32_t mk[8];
 #pragma unroll
-            for (int q = 0; q < CW / 2; ++q) {
-                float a = va[2 * q], bb = va[2 * q + 1];
-                if (relu) {
-                    if ((mk[q] & 0xffffu) == 0u) a = 0.f;
-                    if ((mk[q] >> 16) == 0u) bb = 0.f;
+                for (int u = 0; u < 2; ++u) {
+                    uint4 m = make_uint4(0xffffffffu, 0xffffffffu, 0xffffffffu, 0xffffffffu);
+                    if (relu) m = *reinterpret_cast<const uint4 *>(xc + sw_off(row, u0 + u));
+                    mk[4 * u] = m.x; mk[4 * u + 1] = m.y; mk[4 * u + 2] = m.z; mk[4 * u + 3] = m.w;
                 }
-                p[q] = pack_bf16(a, bb);
+                uint32_t p[8];
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    float a = va[2 * q], bb = va[2 * q + 1];
+                    if (relu) {
+                        if ((mk[q] & 0xffffu) == 0u) a = 0.f;
+                        if ((mk[q] >> 16) == 0u) bb = 0.f;
+                    }
+                    p[q] = pack_bf16(a, bb);
+                }
+                st_units<2>(DZ, row, u0, p);
             }
-            st_units<CU>(DZ, row, c0 / 8, p);
             if (g == 0) {
                 if constexpr (W == 64) {
                     if (head) {
@@ -610,7 +771,7 @@ __global__ void __launch_bounds__(kBwThreads, 1)
                         po[0] = pack_bf16(dsig, 0.f);
 #pragma unroll
                         for (int q = 1; q < 8; ++q) po[q] = 0u;
-                        st_units<2>(DZ + kChunk, row, 0, po);
+                        st_units<2>(T, row, 4, po);
                     }
                 } else {
                     uint32_t z4[16];
@@ -626,18 +787,19 @@ __global__ void __launch_bounds__(kBwThreads, 1)
         bool ok2 = publish(ok);
         if (ok2) {
             // independent accumulators, so three warps issue them side by side
-            if (tid == 0) issue_wgrad(H + 2, sDZ + kChunk, 1024u);
-            if (tid == 32) issue_wgrad(H + 1, sDZ, 1024u);
-            if (tid == 64) mma_dgrad<W, W>(tD, sDZ, sIMG + (uint32_t)S::offset(H + 1));
+            if (ctid == 0) issue_wgrad(H + 2, sT + 64u);
+            if (ctid == 32) issue_wgrad(H + 1, sDZ);
+            if (ctid == 64) mma_dgrad<W, W>(tD, sDZ, sT + 64u, sIMG + (uint32_t)S::offset(H + 1));
             commit();
             ok2 = land();
+            if (ok2) progress(u_rel, 2);          // X_{H+2}, X_{H+1} and F(d) no longer read
             next_dz(H + 1, false, true);          // dZ of the head: [d feat | d logit | 0]
-            // head
             ok2 = publish(ok2);
         }
         if (ok2) {
-            if (tid == 0) issue_wgrad(H, sDZ, (uint32_t)kChunk);
-            if (tid == 32) mma_dgrad<W, S::N_HEAD>(tD, sDZ, sIMG + (uint32_t)S::offset(H));
+            // head
+            if (ctid == 0) issue_wgrad(H, sDZ);
+            if (ctid == 32) mma_dgrad<W, S::N_HEAD>(tD, sDZ, sT + 64u, sIMG + (uint32_t)S::offset(H));
             commit();
             ok2 = land();
             next_dz(H, true, false);
@@ -646,32 +808,35 @@ __global__ void __launch_bounds__(kBwThreads, 1)
             for (int l = H - 1; l >= 1; --l) {
                 ok2 = publish(ok2);
                 if (!ok2) break;
-                if (tid == 0) issue_wgrad(l, sDZ, 1024u);
-                if (tid == 32) mma_dgrad<W, W>(tD, sDZ, sIMG + (uint32_t)S::offset(l));
+                progress(u_rel, (uint32_t)(H + 2 - l));   // X_{l+1}: its mask was read above
+                if (ctid == 0) issue_wgrad(l, sDZ);
+                if (ctid == 32) mma_dgrad<W, W>(tD, sDZ, sT + 64u, sIMG + (uint32_t)S::offset(l));
                 commit();
-            ok2 = land();
+                ok2 = land();
                 next_dz(l, true, false);
             }
             ok2 = publish(ok2);
         }
-        // first layer: wgrad only
-        if (ok2) {
-            if (issuer) issue_wgrad(0, sDZ, 1024u);
-            commit();
-            ok2 = land();
-            ok2 = __syncthreads_and(ok2) != 0;
-        }
+        // every ok2 here is a barrier's verdict, the same for the whole chain
         if (!ok2) {
             aborted = true;
             break;
         }
-        wnew = false;
+        // first layer: wgrad only
+        progress(u_rel, (uint32_t)(H + 2));               // X_1 free
+        if (ctid == 0) issue_wgrad(0, sDZ);
+        commit();
+        good = land();                                    // agreed at the next tile's first barrier
+        if (good) progress(u_rel, kFull);                 // X_0, dZ, the tail and every wgrad
         if (more) nxt = stage_finish(pend, src);
     }
-    if (!aborted && cur != 0xffffffffu && !wnew) flush(cur);
+    // both chains done: the last field's gradient, by every thread
+    const bool any_abort = __syncthreads_or(aborted || *abortp) != 0;
+    tc_fence_after();
+    if (!any_abort && img_field != 0xffffffffu) flush(img_field, warp >> 2, 4);
     // drain before TMEM is freed: a commit whose wait gave up, an image load nobody waited for
-    if (lead && n_commits > n_waits) mbar_wait(&bar_d, (n_commits - 1) & 1u, abortp, status, true);
-    if (tid == 0 && w_pending) mbar_wait(&bar_w, w_ph ^ 1u, abortp, status, true);
+    if (lead && n_commits > n_waits) mbar_wait(&bar_d[chain], (n_commits - 1) & 1u, abortp, status, true);
+    if (ctid == 0 && w_pending) mbar_wait(&bar_w, w_pend_ph, abortp, status, true);
     tc_fence_before();
     __syncthreads();
     if (warp == 0) {
