@@ -760,6 +760,20 @@ def main():
     mlp_key = "mlp_bf16_tcgen05" if head_prec == roam.ROAM_BF16 else "mlp_f32_simt"
     shares = {k: {"launches": v[0], "ms": round(v[1], 4), "share": round(v[1] / sum(x[1] for x in prof.values()), 4)}
               for k, v in prof.items()}
+    # the HBM-side kernels: algorithmic bytes over the timed region's launches
+    # (lower bounds: the march writes a 4 B record per evaluated sample and
+    # 64 B of ray state per ray; the bucket reads 8 B and writes 4 B per
+    # sample; the composite reads 16 B of (sigma, rgb) and a 4 B record per
+    # sample and writes 20 B per ray), against the measured copy rate
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    n_rays_step = sum(c.n_pixels for c in wl.cams)
+    alg = {"march": 4 * evaluated_per_step + 64 * n_rays_step, "bucket": 12 * evaluated_per_step,
+           "composite": 20 * evaluated_per_step + 20 * n_rays_step}
+    for k, nbytes in alg.items():
+        if k in prof and prof[k][1] > 0:
+            gbs = nbytes * args.steps / (prof[k][1] / 1000.0) / 1e9
+            shares[k].update({"alg_bytes_per_step": int(nbytes), "alg_gbs": round(gbs, 1),
+                              "frac_of_hbm": round(gbs / hbm, 4)})
     dom = max(prof.items(), key=lambda kv: kv[1][1])[0] if prof else mlp_key
     launches, mlp_ms = prof.get(mlp_key, (0, float("nan")))
     flops = 2.0 * macs_per_sample(wl.W, wl.H) * evaluated_per_step * args.steps
