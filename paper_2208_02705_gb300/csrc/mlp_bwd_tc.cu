@@ -12,14 +12,17 @@
 //      tiles of one field and are added to the global FP32 gradient (one
 //      atomic per parameter) when the field changes.  The MMAs of one
 //      backward group write independent accumulators, so up to three warps
-//      issue them side by side; lane 0 of warps 0..3 commits to the group's
-//      barrier.
-// Sixteen warps share every epilogue: the four warps of one TMEM lane
-// quarter each take a quarter of the row's columns (W / 4), so a layer's
-// TMEM-to-shared-memory pass is a quarter as long per thread and each SM
-// sub-partition has four warps to hide its latencies.  The colour layer's
-// 3-output reduction meets in shared memory; one CTA barrier per MMA group
-// both publishes the epilogue's stores and agrees on every thread's wait.
+//      issue them side by side.
+// Two chains of 8 warps carry alternate tiles (t0 + chain, + 2, ...): while
+// one recomputes its tile's forward, the other runs the previous tile's
+// backward, so the commit round trips of one chain overlap the other's
+// epilogues.  Each chain has its own accumulator D, barrier and MMA
+// mbarrier; within a chain the two warps of one TMEM lane quarter take half
+// of the row's columns each.  The chains share the weight image (their
+// tiles are of one field: a field change drains them), the wgrad
+// accumulators, a pool of H + 4 activation chunks, dZ and the tail chunk;
+// a progress word per chain orders every reuse (see prog_word), so wgrad
+// accumulation stays in tile order.
 //
 // Every activation tile exists once, in the 128-byte-swizzled layout with
 // samples as rows and 64 features per 128-byte row ("natural" layout).  Read
@@ -31,12 +34,15 @@
 // MMAs as in the forward kernel (a constant-1 feature column), so their
 // gradients come out of the wgrad accumulators as one more feature row.
 //
-// Shared memory (W = 64): the image, X_0 (encoding), X_1..X_H (hidden
-// inputs), X_{H+1} (colour input), X_g (colour output), each one 64-column
-// chunk; a tail chunk T = [1 | F(d) | 0] that continues every row past
-// column 64 (the second K chunk of the hidden, head and colour layers); and
-// dZ (two chunks).  At W = 32 the tail sits inside each chunk (columns
-// 32..63) and T only pads the M = 128 wgrad operand.
+// Shared memory (W = 64): the image; H + 4 chunks of 64 columns for the
+// two chains' X_0 (encoding), X_1..X_H (hidden inputs), X_{H+1} (colour
+// input) and X_g (colour output); dZ (one chunk); and the tail chunk T whose
+// columns 0..31 hold [1 | F(d) | 0] of the tile in its colour layer (the
+// second K chunk of the hidden, head and colour layers), columns 32..47 the
+// head's dZ columns 64..79 or the output layer's dZ, columns 48..63 the
+// colour layer's partial sums.  At W = 32 the tail [1 | F(d) | 0] sits inside
+// each chunk (columns 32..63) and T only pads the M = 128 wgrad operand
+// besides holding the output layer's dZ and the partial sums.
 #include "tc_common.cuh"
 
 namespace roam {
