@@ -22,6 +22,9 @@ struct SlotIter {
     __device__ uint64_t total() const { return (uint64_t)((n_live + 31u) >> 5) * R * 32u; }
     // slot ids fit in 32 bits (the round size is chosen so), so the column
     // arithmetic stays 32-bit
+    // (the record is read whether or not slot s holds one -- every slot
+    // below total() lies inside the slot array -- so that it and the
+    // ray's count are loaded side by side, not one after the other)
     __device__ bool valid(uint64_t s, uint32_t &key) const
     {
         const uint32_t lane = (uint32_t)(s & 31u);
@@ -29,8 +32,9 @@ struct SlotIter {
         const uint32_t q = col / R;
         const uint32_t k = col - q * R;
         const uint32_t i = q * 32u + lane;
-        if (i >= n_live || k >= cnt[i]) return false;
-        key = recs[s] >> 16;
+        const uint32_t rec = __ldg(recs + s);
+        if (i >= n_live || k >= __ldg(cnt + i)) return false;
+        key = rec >> 16;
         return true;
     }
 };
