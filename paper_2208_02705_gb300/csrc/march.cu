@@ -333,17 +333,21 @@ __global__ void __launch_bounds__(256) k_march(GridDev g, MarchParams p)
                 continue;
             }
             const int bxi = ix >> kBrickShift, byi = iy >> kBrickShift, bzi = iz >> kBrickShift;
-            const int dd = __ldg(&g.brick_dist[((int64_t)bzi * g.by + byi) * g.bx + bxi]);
+            // the brick's distance, the voxel's bit word and its rank prefix
+            // side by side (the word is inside the grid), not one after the other
             const int64_t wi = ((int64_t)iz * g.gy + iy) * g.wpr + (ix >> 5);
+            const int dd = __ldg(&g.brick_dist[((int64_t)bzi * g.by + byi) * g.bx + bxi]);
+            const uint32_t wraw = __ldg(&g.bits[wi]);
+            const uint32_t pre = __ldg(&g.prefix[wi]);
             const uint32_t b = (uint32_t)(ix & 31);
-            const uint32_t w = dd > 0 ? 0u : __ldg(&g.bits[wi]);
+            const uint32_t w = dd > 0 ? 0u : wraw;
             if (!((w >> b) & 1u)) {
                 const uint32_t jj = empty_jump(g, dd, ix, iy, iz, ogx, ogy, ogz, dgx, dgy, dgz, idx, idy, idz, delta, je);
                 jn = jj > jn + 1 ? jj : jn + 1;
                 continue;
             }
             {
-                const uint32_t rank = __ldg(&g.prefix[wi]) + (uint32_t)__popc(w & ((1u << b) - 1u));
+                const uint32_t rank = pre + (uint32_t)__popc(w & ((1u << b) - 1u));
                 uint32_t f = __ldg(&g.labels[rank]);
                 if (f >= (uint32_t)g.n_fields) {
                     atomicOr(&p.ctr->status, kStatusBadLabel);
