@@ -485,9 +485,52 @@ __global__ void k_pack_tc(const float *__restrict__ w32, int n_fields, int64_t P
     }
 }
 
+// Where parameter q of a field (API layout) sits in its BF16 image: the byte
+// offset of its element, or -1 - r for entry r of the FP32 3-output table.
+template <int W, int H>
+__device__ __forceinline__ int image_slot(const ApiLayout &o, int64_t q)
+{
+    using S = TcShape<W, H, false>;
+    int l, nr, k;
+    if (q < o.hid) {
+        const int r = (int)(q - o.l1);
+        l = 0;
+        if (r < W * kPeX) { nr = r / kPeX; k = r % kPeX; }
+        else { nr = r - W * kPeX; k = kPeX; }
+    } else if (q < o.head) {
+        const int64_t r0 = q - o.hid;
+        l = 1 + (int)(r0 / (W * W + W));
+        const int r = (int)(r0 % (W * W + W));
+        if (r < W * W) { nr = r / W; k = r % W; }
+        else { nr = r - W * W; k = W; }
+    } else if (q < o.col) {
+        const int r = (int)(q - o.head);
+        int ar;
+        l = H;
+        if (r < (1 + W) * W) { ar = r / W; k = r % W; }
+        else { ar = r - (1 + W) * W; k = W; }
+        nr = ar == 0 ? W : ar - 1;          // image rows: W features, then the density logit
+    } else if (q < o.out) {
+        const int r = (int)(q - o.col), kc = W + kPeD;
+        l = H + 1;
+        if (r < W * kc) { nr = r / kc; const int ka = r % kc; k = ka < W ? ka : ka + 1; }
+        else { nr = r - W * kc; k = W; }
+    } else {
+        // the FP32 3-output layer: [W][4] then bias[4]
+        const int r = (int)(q - o.out);
+        return -1 - (r < 3 * W ? 4 * (r % W) + r / W : 4 * W + (r - 3 * W));
+    }
+    const int N = S::N(l);
+    return S::offset(l) + (k / S::kCE) * N * 128 + (nr >> 3) * 1024 + (nr & 7) * 128 +
+           ((((k % S::kCE) >> 3) ^ (nr & 7)) << 4) + (k & 7) * 2;
+}
+
 // Adam on the FP32 masters fused with the refresh of the BF16 image (every
-// bias folded into the MMA: W <= 64): one thread per parameter updates it
-// and writes its one image element (or its FP32 output-table entry).
+// bias folded into the MMA: W <= 64): one thread per four parameters (vector
+// loads and stores of the masters, moments and gradient), each written into
+// its image element (or its FP32 output-table entry).  The step is
+// w -= (lr / bc1) m / (sqrt(v / bc2) + eps) with one correctly rounded
+// reciprocal (within a few units of 2^-24 of the two divisions).
 template <int W, int H>
 __global__ void k_adam_tc(float *__restrict__ w, float *__restrict__ m, float *__restrict__ v,
                           const float *__restrict__ g, int n_fields, int64_t P, uint8_t *__restrict__ img,
@@ -498,54 +541,44 @@ __global__ void k_adam_tc(float *__restrict__ w, float *__restrict__ m, float *_
     const ApiLayout o(W, H);
     const int64_t f = blockIdx.y;                      // one grid row per field: no 64-bit division
     if (f >= n_fields) return;
-    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < P; q += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t i = f * P + q;
-        const float gi = g[i];
-        const float mi = fmaf(b1, m[i], (1.f - b1) * gi);
-        const float vi = fmaf(b2, v[i], (1.f - b2) * gi * gi);
-        m[i] = mi;
-        v[i] = vi;
-        const float wi = w[i] - lr * (mi / bc1) / (sqrtf(vi / bc2) + eps);
-        w[i] = wi;
-        // where this parameter sits in the field's image
-        uint8_t *dst = img + f * img_bytes;
-        int l, nr, k;
-        if (q < o.hid) {
-            const int r = (int)(q - o.l1);
-            l = 0;
-            if (r < W * kPeX) { nr = r / kPeX; k = r % kPeX; }
-            else { nr = r - W * kPeX; k = kPeX; }
-        } else if (q < o.head) {
-            const int64_t r0 = q - o.hid;
-            l = 1 + (int)(r0 / (W * W + W));
-            const int r = (int)(r0 % (W * W + W));
-            if (r < W * W) { nr = r / W; k = r % W; }
-            else { nr = r - W * W; k = W; }
-        } else if (q < o.col) {
-            const int r = (int)(q - o.head);
-            int ar;
-            l = H;
-            if (r < (1 + W) * W) { ar = r / W; k = r % W; }
-            else { ar = r - (1 + W) * W; k = W; }
-            nr = ar == 0 ? W : ar - 1;          // image rows: W features, then the density logit
-        } else if (q < o.out) {
-            const int r = (int)(q - o.col), kc = W + kPeD;
-            l = H + 1;
-            if (r < W * kc) { nr = r / kc; const int ka = r % kc; k = ka < W ? ka : ka + 1; }
-            else { nr = r - W * kc; k = W; }
+    const float lr_t = lr / bc1, inv_bc2 = 1.f / bc2;
+    uint8_t *dst = img + f * img_bytes;
+    auto update = [&](int64_t q, float gi, float &mi, float &vi, float &wi) {
+        mi = fmaf(b1, mi, (1.f - b1) * gi);
+        vi = fmaf(b2, vi, (1.f - b2) * gi * gi);
+        wi = wi - lr_t * mi * __frcp_rn(sqrtf(vi * inv_bc2) + eps);
+        const int at = image_slot<W, H>(o, q);
+        if (at < 0) {
+            reinterpret_cast<float *>(dst + S::kMatBytes)[-1 - at] = wi;
         } else {
-            // the FP32 3-output layer: [W][4] then bias[4]
-            const int r = (int)(q - o.out);
-            float *tab = reinterpret_cast<float *>(dst + S::kMatBytes);
-            if (r < 3 * W) tab[4 * (r % W) + r / W] = wi;
-            else tab[4 * W + (r - 3 * W)] = wi;
-            continue;
+            const uint32_t bits = __float_as_uint(wi);
+            *reinterpret_cast<uint16_t *>(dst + at) = (uint16_t)((bits + 0x7fffu + ((bits >> 16) & 1u)) >> 16);
         }
-        const int N = S::N(l);
-        const int off = S::offset(l) + (k / S::kCE) * N * 128 + (nr >> 3) * 1024 + (nr & 7) * 128 +
-                        ((((k % S::kCE) >> 3) ^ (nr & 7)) << 4) + (k & 7) * 2;
-        const uint32_t bits = __float_as_uint(wi);
-        *reinterpret_cast<uint16_t *>(dst + off) = (uint16_t)((bits + 0x7fffu + ((bits >> 16) & 1u)) >> 16);
+    };
+    const int64_t q0 = 4 * ((int64_t)blockIdx.x * blockDim.x + threadIdx.x);
+    if (q0 >= P) return;
+    const int64_t i0 = f * P + q0;
+    if (q0 + 4 <= P && (i0 & 3) == 0) {
+        float4 g4 = *reinterpret_cast<const float4 *>(g + i0);
+        float4 m4 = *reinterpret_cast<const float4 *>(m + i0);
+        float4 v4 = *reinterpret_cast<const float4 *>(v + i0);
+        float4 w4 = *reinterpret_cast<const float4 *>(w + i0);
+        update(q0, g4.x, m4.x, v4.x, w4.x);
+        update(q0 + 1, g4.y, m4.y, v4.y, w4.y);
+        update(q0 + 2, g4.z, m4.z, v4.z, w4.z);
+        update(q0 + 3, g4.w, m4.w, v4.w, w4.w);
+        *reinterpret_cast<float4 *>(m + i0) = m4;
+        *reinterpret_cast<float4 *>(v + i0) = v4;
+        *reinterpret_cast<float4 *>(w + i0) = w4;
+    } else {
+        for (int64_t q = q0; q < q0 + 4 && q < P; ++q) {
+            const int64_t i = f * P + q;
+            float mi = m[i], vi = v[i], wi = w[i];
+            update(q, g[i], mi, vi, wi);
+            m[i] = mi;
+            v[i] = vi;
+            w[i] = wi;
+        }
     }
 }
 
@@ -626,7 +659,7 @@ bool launch_adam_tc(float *w32, float *m, float *v, const float *g, int n_fields
     if (n_fields > 65535) return false;           // one grid row per field
 #define ROAM_ADAM_CASE(WW, HH)                                                                                   \
     if (W == WW && H == HH) {                                                                                  \
-        const dim3 grid((unsigned)((P + 255) / 256), (unsigned)n_fields);                                       \
+        const dim3 grid((unsigned)((P + 1023) / 1024), (unsigned)n_fields);                                     \
         k_adam_tc<WW, HH><<<grid, 256, 0, s>>>(w32, m, v, g, n_fields, P, (uint8_t *)wimg, img_bytes, lr, b1, b2, \
                                                eps, bc1, bc2);                                                 \
         return true;                                                                                           \
