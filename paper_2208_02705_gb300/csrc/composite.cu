@@ -123,11 +123,19 @@ __global__ void k_composite_flat(int64_t n_rays, int n_max, const uint32_t *coun
 //   dC/dsigma_i = delta (T_{i+1} c_i - sum_{i<j<=I} w_j c_j - T_end bg).
 // Pass 1 repeats the forward arithmetic to find I, T_end and the composited
 // colour; pass 2 emits per slot (dL/dsigma, dL/dc) and the used count.
+// With `hist`, pass 1 also counts each composited sample's field (a block
+// histogram added into hist), the histogram the backward bucketing needs.
 __global__ void __launch_bounds__(256) k_composite_bwd(int64_t n_rays, int R, const uint32_t *cnt,
                                                        const uint32_t *recs, const float4 *sr, float delta,
                                                        float t_stop, float bg0, float bg1, float bg2,
-                                                       const float *dl_drgb, float4 *gsr, uint32_t *cnt_used)
+                                                       const float *dl_drgb, float4 *gsr, uint32_t *cnt_used,
+                                                       uint32_t *hist, int n_fields)
 {
+    extern __shared__ uint32_t s_hist[];
+    if (hist) {
+        for (int f = threadIdx.x; f < n_fields; f += blockDim.x) s_hist[f] = 0u;
+        __syncthreads();
+    }
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_rays; i += (int64_t)gridDim.x * blockDim.x) {
         const uint32_t c = cnt[i];
         float T = 1.f, sw = 0.f;
@@ -136,8 +144,9 @@ __global__ void __launch_bounds__(256) k_composite_bwd(int64_t n_rays, int R, co
         for (uint32_t k = 0; k < c; ++k) {
             const uint32_t s = slot_of((uint32_t)i, k, (uint32_t)R);
             const float4 v = sr[s];
-            const uint32_t j = recs[s] & 0xffffu;
-            step(v, ((float)j + 0.5f) * delta, delta, T, sw, acc);
+            const uint32_t rec = recs[s];
+            step(v, ((float)(rec & 0xffffu) + 0.5f) * delta, delta, T, sw, acc);
+            if (hist) atomicAdd(&s_hist[rec >> 16], 1u);
             used = k + 1;
             if (T < t_stop) break;
         }
@@ -163,19 +172,25 @@ __global__ void __launch_bounds__(256) k_composite_bwd(int64_t n_rays, int R, co
         }
         cnt_used[i] = used;
     }
+    if (hist) {
+        __syncthreads();
+        for (int f = threadIdx.x; f < n_fields; f += blockDim.x)
+            if (s_hist[f]) atomicAdd(&hist[f], s_hist[f]);
+    }
 }
 
 }  // namespace
 
 void launch_composite_bwd(int64_t n_rays, int R, const uint32_t *cnt, const uint32_t *recs, const float4 *sr,
                           float delta, float t_stop, const float *bg, const float *dl_drgb, float4 *gsr,
-                          uint32_t *cnt_used, cudaStream_t s)
+                          uint32_t *cnt_used, uint32_t *hist, int n_fields, cudaStream_t s)
 {
     int64_t blocks = (n_rays + 255) / 256;
     if (blocks > 8192) blocks = 8192;
     if (blocks < 1) blocks = 1;
-    k_composite_bwd<<<(unsigned)blocks, 256, 0, s>>>(n_rays, R, cnt, recs, sr, delta, t_stop, bg[0], bg[1], bg[2],
-                                                     dl_drgb, gsr, cnt_used);
+    const size_t smem = hist ? (size_t)n_fields * sizeof(uint32_t) : 0;
+    k_composite_bwd<<<(unsigned)blocks, 256, smem, s>>>(n_rays, R, cnt, recs, sr, delta, t_stop, bg[0], bg[1], bg[2],
+                                                        dl_drgb, gsr, cnt_used, hist, n_fields);
 }
 
 void launch_composite_round(const MarchParams &mp, const float4 *sr, uint32_t *next_live, uint32_t *next_count,

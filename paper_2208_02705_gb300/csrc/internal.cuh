@@ -245,7 +245,7 @@ void launch_composite_flat(int64_t n_rays, int n_max, const uint32_t *count, con
 
 void launch_composite_bwd(int64_t n_rays, int R, const uint32_t *cnt, const uint32_t *recs, const float4 *sr,
                           float delta, float t_stop, const float *bg, const float *dl_drgb, float4 *gsr,
-                          uint32_t *cnt_used, cudaStream_t s);
+                          uint32_t *cnt_used, uint32_t *hist, int n_fields, cudaStream_t s);
 void launch_mlp_bwd_simt(const MlpWeights &w, const SampleSrc &src, const BucketBufs &b, Counters *ctr,
                          const float4 *gsr, float *grad, int grid, cudaStream_t s);
 bool mlp_bwd_supported(int W, int H);

@@ -1596,18 +1596,26 @@ roam_status roam_train_backward(roam_ctx *c, const float *dl_drgb, float *grad, 
     const roam_render_opts &o = c->train_opts;
     const size_t slots = ((size_t)(n + 31) & ~(size_t)31) * (size_t)R;
     ROAM_TRY(ensure(c->gsr, slots));
+    // the composite's adjoint also counts the composited samples per field,
+    // so the backward bucketing needs no histogram pass of its own
+    const bool fused_hist = (size_t)c->n_fields * sizeof(uint32_t) <= 48 * 1024;
+    if (fused_hist) ROAM_CUDA(cudaMemsetAsync(c->hist.p, 0, (size_t)c->n_fields * sizeof(uint32_t), s));
     {
         ProfScope ps(c, P_COMPOSITE_BWD, s);
         launch_composite_bwd(n, R, c->cnt.p, c->recs.p, c->sr.p, o.delta, o.t_stop, o.bg, dl_drgb, c->gsr.p,
-                             c->live1.p, s);
+                             c->live1.p, fused_hist ? c->hist.p : nullptr, c->n_fields, s);
     }
     ROAM_TRY(launched("composite_bwd"));
     ROAM_CUDA(cudaMemsetAsync(c->aux, 0, sizeof(Counters), s));
     const BucketBufs b = bucket_of(c);
     {
         ProfScope ps(c, P_BUCKET, s);
-        launch_bucket(c->live1.p, c->recs.p, nullptr, (uint32_t)n, R, 1, nullptr, c->n_fields, 128, b, c->aux,
-                      grid_blocks(c, 4), s, c->cb);
+        if (fused_hist)
+            launch_bucket_ready(c->live1.p, c->recs.p, nullptr, (uint32_t)n, R, 1, c->n_fields, 128, b, c->aux,
+                                grid_blocks(c, 4), s, c->cb);
+        else
+            launch_bucket(c->live1.p, c->recs.p, nullptr, (uint32_t)n, R, 1, nullptr, c->n_fields, 128, b, c->aux,
+                          grid_blocks(c, 4), s, c->cb);
     }
     ROAM_TRY(launched("bucket"));
     ROAM_CUDA(cudaMemsetAsync(grad, 0, (size_t)(c->ws[0].P * c->n_fields) * sizeof(float), s));
