@@ -158,6 +158,9 @@ struct roam_ctx {
     cudaEvent_t cam_ev[kCamRing] = {};
     bool cam_pending[kCamRing] = {};
     int cam_slot = 0;
+    std::vector<DevCamera> cams_dev;        // what the device camera buffer holds (the last copy)
+    int cams_dev_n = 0;                     // its number of views (0: nothing copied yet)
+    int cams_dev_slot = -1;                 // the ring slot whose event follows that copy
     Counters *ctr = nullptr;        // the last render / training forward (roam_get_stats)
     Counters *aux = nullptr;        // the other calls (single steps, backward passes): ctr + 1
     Counters *h_ctr = nullptr;
@@ -394,10 +397,20 @@ roam_status upload_cams(roam_ctx *c, const roam_camera *cams, int n_views, float
         total += (int64_t)k.width * k.height;
         if (total > (int64_t)0x7fffffff) return fail(ROAM_ERR_ARG, "too many pixels");
     }
-    ROAM_TRY(ensure(c->cams, (size_t)n_views));
-    ROAM_CUDA(cudaMemcpyAsync(c->cams.p, c->h_cams, sizeof(DevCamera) * n_views, cudaMemcpyHostToDevice, s));
-    ROAM_CUDA(cudaEventRecord(c->cam_ev[slot], s));
-    c->cam_pending[slot] = true;
+    const size_t bytes = sizeof(DevCamera) * (size_t)n_views;
+    if (n_views == c->cams_dev_n && memcmp(c->h_cams, c->cams_dev.data(), bytes) == 0) {
+        // the device already holds these cameras: order this stream after
+        // that copy instead of copying again
+        ROAM_CUDA(cudaStreamWaitEvent(s, c->cam_ev[c->cams_dev_slot], 0));
+    } else {
+        ROAM_TRY(ensure(c->cams, (size_t)n_views));
+        ROAM_CUDA(cudaMemcpyAsync(c->cams.p, c->h_cams, bytes, cudaMemcpyHostToDevice, s));
+        ROAM_CUDA(cudaEventRecord(c->cam_ev[slot], s));
+        c->cam_pending[slot] = true;
+        c->cams_dev.assign(c->h_cams, c->h_cams + n_views);
+        c->cams_dev_n = n_views;
+        c->cams_dev_slot = slot;
+    }
     *n_pix = total;
     c->n_views = n_views;
     return ROAM_OK;
