@@ -335,8 +335,10 @@ __global__ void __launch_bounds__(256) k_march(GridDev g, MarchParams p)
             const int bxi = ix >> kBrickShift, byi = iy >> kBrickShift, bzi = iz >> kBrickShift;
             // the brick's distance, the voxel's bit word and its rank prefix
             // side by side (the word is inside the grid), not one after the other
-            const int64_t wi = ((int64_t)iz * g.gy + iy) * g.wpr + (ix >> 5);
-            const int dd = __ldg(&g.brick_dist[((int64_t)bzi * g.by + byi) * g.bx + bxi]);
+            // (grids are at most 2048^3 voxels: word and brick indices fit 32 bits)
+            const uint32_t wi = ((uint32_t)iz * (uint32_t)g.gy + (uint32_t)iy) * (uint32_t)g.wpr + ((uint32_t)ix >> 5);
+            const int dd = __ldg(&g.brick_dist[((uint32_t)bzi * (uint32_t)g.by + (uint32_t)byi) * (uint32_t)g.bx +
+                                               (uint32_t)bxi]);
             const uint32_t wraw = __ldg(&g.bits[wi]);
             const uint32_t pre = __ldg(&g.prefix[wi]);
             const uint32_t b = (uint32_t)(ix & 31);
