@@ -262,7 +262,7 @@ __device__ __forceinline__ bool ray_begin(const GridDev &g, const MarchParams &p
 // still tested.  One code path for both jumps (fewer divergent branches).
 __device__ __forceinline__ uint32_t empty_jump(const GridDev &g, int dd, int ix, int iy, int iz, float ogx, float ogy,
                                                float ogz, float dgx, float dgy, float dgz, float idx, float idy,
-                                               float idz, float delta, uint32_t je)
+                                               float idz, float inv_delta, uint32_t je)
 {
     const int bxi = ix >> kBrickShift, byi = iy >> kBrickShift, bzi = iz >> kBrickShift;
     float ex, ey, ez, back;
@@ -282,7 +282,7 @@ __device__ __forceinline__ uint32_t empty_jump(const GridDev &g, int dd, int ix,
     if (dgx != 0.f) te = fminf(te, (ex - ogx) * idx);
     if (dgy != 0.f) te = fminf(te, (ey - ogy) * idy);
     if (dgz != 0.f) te = fminf(te, (ez - ogz) * idz);
-    const float jf = ceilf(te / delta - 0.5f) - back;
+    const float jf = ceilf(te * inv_delta - 0.5f) - back;
     return jf > (float)je ? je : (jf > 0.f ? (uint32_t)jf : 0u);
 }
 
@@ -322,6 +322,7 @@ __global__ void __launch_bounds__(256) k_march(GridDev g, MarchParams p)
                     ogz = (o.z - g.origin[2]) * g.inv_vox;
         const float dgx = d.x * g.inv_vox, dgy = d.y * g.inv_vox, dgz = d.z * g.inv_vox;
         const float idx = 1.0f / dgx, idy = 1.0f / dgy, idz = 1.0f / dgz;
+        const float inv_delta = 1.0f / delta;   // (the jump's sample index: a product, not a division per step)
         uint32_t em = 0;
         const uint32_t R = (uint32_t)p.R, n_max = (uint32_t)p.n_max;
         while (jn < je && em < R && nk < n_max) {
@@ -344,7 +345,8 @@ __global__ void __launch_bounds__(256) k_march(GridDev g, MarchParams p)
             const uint32_t b = (uint32_t)(ix & 31);
             const uint32_t w = dd > 0 ? 0u : wraw;
             if (!((w >> b) & 1u)) {
-                const uint32_t jj = empty_jump(g, dd, ix, iy, iz, ogx, ogy, ogz, dgx, dgy, dgz, idx, idy, idz, delta, je);
+                const uint32_t jj =
+                    empty_jump(g, dd, ix, iy, iz, ogx, ogy, ogz, dgx, dgy, dgz, idx, idy, idz, inv_delta, je);
                 jn = jj > jn + 1 ? jj : jn + 1;
                 continue;
             }
