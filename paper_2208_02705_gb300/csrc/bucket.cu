@@ -29,7 +29,7 @@ struct SlotIter {
     {
         const uint32_t lane = (uint32_t)(s & 31u);
         const uint32_t col = (uint32_t)(s >> 5);
-        const uint32_t q = col / R;
+        const uint32_t q = group_of(col, R);
         const uint32_t k = col - q * R;
         const uint32_t i = q * 32u + lane;
         const uint32_t rec = __ldg(recs + s);

@@ -124,6 +124,14 @@ __host__ __device__ inline uint32_t slot_of(uint32_t i, uint32_t k, uint32_t R)
     return ((i >> 5) * R + k) * 32u + (i & 31u);
 }
 
+// Inverse of the column part of slot_of: the 32-ray group of slot column col
+// (= slot >> 5), i.e. col / R.  Power-of-two round sizes (the ones the round
+// tuner picks) take a shift instead of the integer division.
+__device__ __forceinline__ uint32_t group_of(uint32_t col, uint32_t R)
+{
+    return (R & (R - 1u)) == 0u ? col >> (31 - __clz(R)) : col / R;
+}
+
 struct MarchParams {
     const DevCamera *cams;
     int n_views;
