@@ -44,6 +44,7 @@
 // each chunk (columns 32..63) and T only pads the M = 128 wgrad operand
 // besides holding the output layer's dZ and the partial sums.
 #include "tc_common.cuh"
+#include <cuda_bf16.h>
 
 namespace roam {
 
@@ -138,6 +139,19 @@ __device__ __forceinline__ void ld16f(uint32_t taddr, float (&v)[16])
     tmem_wait_ld();
 #pragma unroll
     for (int q = 0; q < 16; ++q) v[q] = __uint_as_float(r[q]);
+}
+
+// 0xffff in each 16-bit half of x (two BF16 activations) that is > 0, else
+// 0: the ReLU derivative as a mask for a packed BF16 pair
+__device__ __forceinline__ uint32_t relu_mask(uint32_t x)
+{
+    return __hgt2_mask(*reinterpret_cast<const __nv_bfloat162 *>(&x), __float2bfloat162_rn(0.f));
+}
+
+// one arrival without a transaction (no tcgen05 work to track)
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
 // N (8 or 16) consecutive TMEM columns of this thread's lane as floats
@@ -321,7 +335,7 @@ __global__ void __launch_bounds__(kBwThreads, 1)
     constexpr int NSB = CW / 16;                     // ... in 16-column sub-blocks
     constexpr uint32_t kFull = (uint32_t)(H + 3);
     extern __shared__ uint8_t smem_raw[];
-    __shared__ uint64_t bar_d[kChains], bar_w;
+    __shared__ uint64_t bar_d[kChains], bar_g[kChains], bar_w;
     __shared__ uint32_t tmem_slot, img_field, n_img;
     __shared__ volatile uint32_t prog[kChains];
     __shared__ int abort_flag;
@@ -347,6 +361,8 @@ __global__ void __launch_bounds__(kBwThreads, 1)
     if (tid == 0) {
         mbar_init(&bar_d[0], 4);
         mbar_init(&bar_d[1], 4);
+        mbar_init(&bar_g[0], 2);
+        mbar_init(&bar_g[1], 2);
         mbar_init(&bar_w, 1);
         abort_flag = 0;
         img_field = 0xffffffffu;
@@ -391,7 +407,8 @@ __global__ void __launch_bounds__(kBwThreads, 1)
     const uint32_t t1 = (uint32_t)((uint64_t)n_tiles * (blockIdx.x + 1) / gridDim.x);
     const volatile uint32_t *other = &prog[chain ^ 1];
 
-    uint32_t d_ph = 0, n_commits = 0, n_waits = 0;
+    uint32_t d_ph = 0, g_ph = 0;
+    int d_open = -1, g_open = -1;        // a lead's committed phase not yet waited for
     bool w_pending = false;              // an image load in flight (the issuing thread's view)
     bool aborted = false;
 
@@ -408,14 +425,37 @@ __global__ void __launch_bounds__(kBwThreads, 1)
     auto commit = [&]() {
         if (lead) {
             umma_commit(&bar_d[chain]);
-            ++n_commits;
+            d_open = (int)d_ph;
+        }
+    };
+    // a backward group: the wgrad issuers (chain warps 0 and 1) commit to
+    // bar_g and only arrive on bar_d, so that bar_d lands with the dgrad
+    // (warp 2) and the dX epilogue overlaps the wgrad MMAs
+    auto commit_split = [&]() {
+        if (lead) {
+            if (cw < 2) {
+                umma_commit(&bar_g[chain]);
+                g_open = (int)g_ph;
+                mbar_arrive(&bar_d[chain]);
+            } else {
+                umma_commit(&bar_d[chain]);
+                d_open = (int)d_ph;
+            }
         }
     };
     // wait for the chain's committed group: true when it landed
     auto land = [&]() -> bool {
         const bool got = mbar_wait(&bar_d[chain], d_ph, abortp, status);
-        if (lead && got) ++n_waits;
+        if (got) d_open = -1;
         d_ph ^= 1u;
+        tc_fence_after();
+        return got;
+    };
+    // ... and for its wgrad MMAs (before dZ, the tail or an X they read is rewritten)
+    auto land_g = [&]() -> bool {
+        const bool got = mbar_wait(&bar_g[chain], g_ph, abortp, status);
+        if (got) g_open = -1;
+        g_ph ^= 1u;
         tc_fence_after();
         return got;
     };
@@ -741,35 +781,35 @@ __global__ void __launch_bounds__(kBwThreads, 1)
             else if (l == H) mma_wgrad<S::N_HEAD>(td, xa, sT - xa, dza, sT + 64u - dza, 1u);
             else mma_wgrad<W>(td, xa, sT - xa, dza, 1024u, 1u);
         };
-        // reads this thread's share of dX (its chain's D) and writes dZ of the
-        // layer below: masked by that layer's ReLU (X_i > 0) when i > 0, and
-        // at the head also the density column (group 0)
-        auto next_dz = [&](int i, bool relu, bool head) {
+        // dZ of the layer below from this thread's share of dX (its chain's
+        // D), masked by that layer's ReLU (X_i > 0) when i > 0: packed into
+        // registers while the group's wgrad MMAs still read dZ ...
+        auto dz_of = [&](int i, bool relu, uint32_t (&p)[NSB][8]) {
             const uint8_t *xc = xchunk(chain, i);
 #pragma unroll
             for (int sb = 0; sb < NSB; ++sb) {
                 const int u0 = (c0 + 16 * sb) / 8;
                 float va[16];
                 ldcf<16>(tDc + (uint32_t)(16 * sb), va);
-                uint32_t mk[8];
 #pragma unroll
-                for (int u = 0; u < 2; ++u) {
-                    uint4 m = make_uint4(0xffffffffu, 0xffffffffu, 0xffffffffu, 0xffffffffu);
-                    if (relu) m = *reinterpret_cast<const uint4 *>(xc + sw_off(row, u0 + u));
-                    mk[4 * u] = m.x; mk[4 * u + 1] = m.y; mk[4 * u + 2] = m.z; mk[4 * u + 3] = m.w;
-                }
-                uint32_t p[8];
+                for (int q = 0; q < 8; ++q) p[sb][q] = pack_bf16(va[2 * q], va[2 * q + 1]);
+                if (relu) {
 #pragma unroll
-                for (int q = 0; q < 8; ++q) {
-                    float a = va[2 * q], bb = va[2 * q + 1];
-                    if (relu) {
-                        if ((mk[q] & 0xffffu) == 0u) a = 0.f;
-                        if ((mk[q] >> 16) == 0u) bb = 0.f;
+                    for (int u = 0; u < 2; ++u) {
+                        const uint4 m = *reinterpret_cast<const uint4 *>(xc + sw_off(row, u0 + u));
+                        p[sb][4 * u] &= relu_mask(m.x);
+                        p[sb][4 * u + 1] &= relu_mask(m.y);
+                        p[sb][4 * u + 2] &= relu_mask(m.z);
+                        p[sb][4 * u + 3] &= relu_mask(m.w);
                     }
-                    p[q] = pack_bf16(a, bb);
                 }
-                st_units<2>(DZ, row, u0, p);
             }
+        };
+        // ... and stored once they have landed; at the head also the
+        // density column (group 0)
+        auto dz_store = [&](const uint32_t (&p)[NSB][8], bool head) {
+#pragma unroll
+            for (int sb = 0; sb < NSB; ++sb) st_units<2>(DZ, row, (c0 + 16 * sb) / 8, p[sb]);
             if (g == 0) {
                 if constexpr (W == 64) {
                     if (head) {
@@ -796,19 +836,27 @@ __global__ void __launch_bounds__(kBwThreads, 1)
             if (ctid == 0) issue_wgrad(H + 2, sT + 64u);
             if (ctid == 32) issue_wgrad(H + 1, sDZ);
             if (ctid == 64) mma_dgrad<W, W>(tD, sDZ, sT + 64u, sIMG + (uint32_t)S::offset(H + 1));
-            commit();
+            commit_split();
             ok2 = land();
+            uint32_t p[NSB][8];
+            dz_of(H + 1, false, p);               // dZ of the head: [d feat | d logit | 0]
+            const bool gw = land_g();
+            ok2 = ok2 && gw;
             if (ok2) progress(u_rel, 2);          // X_{H+2}, X_{H+1} and F(d) no longer read
-            next_dz(H + 1, false, true);          // dZ of the head: [d feat | d logit | 0]
+            dz_store(p, true);
             ok2 = publish(ok2);
         }
         if (ok2) {
             // head
             if (ctid == 0) issue_wgrad(H, sDZ);
-            if (ctid == 32) mma_dgrad<W, S::N_HEAD>(tD, sDZ, sT + 64u, sIMG + (uint32_t)S::offset(H));
-            commit();
+            if (ctid == 64) mma_dgrad<W, S::N_HEAD>(tD, sDZ, sT + 64u, sIMG + (uint32_t)S::offset(H));
+            commit_split();
             ok2 = land();
-            next_dz(H, true, false);
+            uint32_t p[NSB][8];
+            dz_of(H, true, p);
+            const bool gw = land_g();
+            ok2 = ok2 && gw;
+            dz_store(p, false);
             // hidden layers H-1 .. 1
 #pragma unroll 1
             for (int l = H - 1; l >= 1; --l) {
@@ -816,10 +864,13 @@ __global__ void __launch_bounds__(kBwThreads, 1)
                 if (!ok2) break;
                 progress(u_rel, (uint32_t)(H + 2 - l));   // X_{l+1}: its mask was read above
                 if (ctid == 0) issue_wgrad(l, sDZ);
-                if (ctid == 32) mma_dgrad<W, W>(tD, sDZ, sT + 64u, sIMG + (uint32_t)S::offset(l));
-                commit();
+                if (ctid == 64) mma_dgrad<W, W>(tD, sDZ, sT + 64u, sIMG + (uint32_t)S::offset(l));
+                commit_split();
                 ok2 = land();
-                next_dz(l, true, false);
+                dz_of(l, true, p);
+                const bool gl = land_g();
+                ok2 = ok2 && gl;
+                dz_store(p, false);
             }
             ok2 = publish(ok2);
         }
@@ -841,7 +892,8 @@ __global__ void __launch_bounds__(kBwThreads, 1)
     tc_fence_after();
     if (!any_abort && img_field != 0xffffffffu) flush(img_field, warp >> 2, 4);
     // drain before TMEM is freed: a commit whose wait gave up, an image load nobody waited for
-    if (lead && n_commits > n_waits) mbar_wait(&bar_d[chain], (n_commits - 1) & 1u, abortp, status, true);
+    if (lead && d_open >= 0) mbar_wait(&bar_d[chain], (uint32_t)d_open, abortp, status, true);
+    if (lead && g_open >= 0) mbar_wait(&bar_g[chain], (uint32_t)g_open, abortp, status, true);
     if (ctid == 0 && w_pending) mbar_wait(&bar_w, w_pend_ph, abortp, status, true);
     tc_fence_before();
     __syncthreads();
