@@ -697,27 +697,38 @@ __global__ void __launch_bounds__(kBwThreads, 1)
             if (l == kLayers - 1) {
                 // colour: z -> g = relu(z) (X_g), rgb = sigmoid(Wo g + bo) in FP32, then
                 // the output layer's adjoint and dZ of the colour layer
-                const float4 *wo = reinterpret_cast<const float4 *>(IMG + S::kMatBytes);
-                float ax = 0.f, ay = 0.f, az = 0.f;
+                // the FP32 table's rows c over k: each float4 load is one
+                // colour's weights for four k (the even and odd k summed apart
+                // by packed FMAs, then together)
+                const float *wo = reinterpret_cast<const float *>(IMG + S::kMatBytes);
+                float2 ax = make_float2(0.f, 0.f), ay = ax, az = ax;
 #pragma unroll
                 for (int sb = 0; sb < NSB; ++sb) {
                     float va[16];
                     ldcf<16>(tDc + (uint32_t)(16 * sb), va);
 #pragma unroll
-                    for (int k = 0; k < 16; ++k) {
-                        const float gk = fmaxf(va[k], 0.f);
-                        const float4 wk = wo[c0 + 16 * sb + k];
-                        ax = fmaf(wk.x, gk, ax);
-                        ay = fmaf(wk.y, gk, ay);
-                        az = fmaf(wk.z, gk, az);
+                    for (int q = 0; q < 4; ++q) {
+                        const int k = c0 + 16 * sb + 4 * q;
+                        const float2 g01 = make_float2(fmaxf(va[4 * q], 0.f), fmaxf(va[4 * q + 1], 0.f));
+                        const float2 g23 = make_float2(fmaxf(va[4 * q + 2], 0.f), fmaxf(va[4 * q + 3], 0.f));
+                        const float4 wx = *reinterpret_cast<const float4 *>(wo + k);
+                        ax = __ffma2_rn(make_float2(wx.x, wx.y), g01, ax);
+                        ax = __ffma2_rn(make_float2(wx.z, wx.w), g23, ax);
+                        const float4 wy = *reinterpret_cast<const float4 *>(wo + W + k);
+                        ay = __ffma2_rn(make_float2(wy.x, wy.y), g01, ay);
+                        ay = __ffma2_rn(make_float2(wy.z, wy.w), g23, ay);
+                        const float4 wz = *reinterpret_cast<const float4 *>(wo + 2 * W + k);
+                        az = __ffma2_rn(make_float2(wz.x, wz.y), g01, az);
+                        az = __ffma2_rn(make_float2(wz.z, wz.w), g23, az);
                     }
                 }
                 // the two column groups' partial sums of the row meet in
                 // units 6 and 7 of the tail (no MMA reads those as anything
                 // but ignored feature rows); both add them in group order
-                *reinterpret_cast<float4 *>(T + sw_off(row, 6 + g)) = make_float4(ax, ay, az, 0.f);
+                *reinterpret_cast<float4 *>(T + sw_off(row, 6 + g)) =
+                    make_float4(ax.x + ax.y, ay.x + ay.y, az.x + az.y, 0.f);
                 asm volatile("bar.sync %0, %1;" ::"r"(3 + 4 * chain + quarter), "r"(64) : "memory");
-                float4 acc = wo[W];
+                float4 acc = *reinterpret_cast<const float4 *>(wo + 4 * W);
 #pragma unroll
                 for (int q = 0; q < 2; ++q) {
                     const float4 pp = *reinterpret_cast<const float4 *>(T + sw_off(row, 6 + q));
@@ -727,6 +738,7 @@ __global__ void __launch_bounds__(kBwThreads, 1)
                 }
                 const float r0 = sigmoid_f(acc.x), r1 = sigmoid_f(acc.y), r2 = sigmoid_f(acc.z);
                 const float dz0 = dl.y * r0 * (1.f - r0), dz1 = dl.z * r1 * (1.f - r1), dz2 = dl.w * r2 * (1.f - r2);
+                const float2 dz0p = make_float2(dz0, dz0), dz1p = make_float2(dz1, dz1), dz2p = make_float2(dz2, dz2);
                 uint8_t *xg = xchunk(chain, H + 2);
 #pragma unroll
                 for (int sb = 0; sb < NSB; ++sb) {
@@ -734,17 +746,23 @@ __global__ void __launch_bounds__(kBwThreads, 1)
                     ldcf<16>(tDc + (uint32_t)(16 * sb), va);     // re-read: cheaper than holding them
                     uint32_t pg[8], pd[8];
 #pragma unroll
-                    for (int q = 0; q < 8; ++q) {
-                        float gg[2], dd[2];
-#pragma unroll
-                        for (int h = 0; h < 2; ++h) {
-                            const float zk = va[2 * q + h];
-                            const float4 wk = wo[c0 + 16 * sb + 2 * q + h];
-                            gg[h] = fmaxf(zk, 0.f);
-                            dd[h] = zk > 0.f ? fmaf(wk.x, dz0, fmaf(wk.y, dz1, wk.z * dz2)) : 0.f;
-                        }
-                        pg[q] = pack_bf16(gg[0], gg[1]);
-                        pd[q] = pack_bf16(dd[0], dd[1]);
+                    for (int q = 0; q < 4; ++q) {
+                        const int k = c0 + 16 * sb + 4 * q;
+                        const float4 wx = *reinterpret_cast<const float4 *>(wo + k);
+                        const float4 wy = *reinterpret_cast<const float4 *>(wo + W + k);
+                        const float4 wz = *reinterpret_cast<const float4 *>(wo + 2 * W + k);
+                        // dL/dg_k = sum_c Wo[c][k] dz_c, for k and k + 1 at once
+                        float2 d01 = __fmul2_rn(make_float2(wz.x, wz.y), dz2p);
+                        d01 = __ffma2_rn(make_float2(wy.x, wy.y), dz1p, d01);
+                        d01 = __ffma2_rn(make_float2(wx.x, wx.y), dz0p, d01);
+                        float2 d23 = __fmul2_rn(make_float2(wz.z, wz.w), dz2p);
+                        d23 = __ffma2_rn(make_float2(wy.z, wy.w), dz1p, d23);
+                        d23 = __ffma2_rn(make_float2(wx.z, wx.w), dz0p, d23);
+                        const float z0 = va[4 * q], z1 = va[4 * q + 1], z2 = va[4 * q + 2], z3 = va[4 * q + 3];
+                        pg[2 * q] = pack_bf16_relu(z0, z1);
+                        pg[2 * q + 1] = pack_bf16_relu(z2, z3);
+                        pd[2 * q] = pack_bf16(z0 > 0.f ? d01.x : 0.f, z1 > 0.f ? d01.y : 0.f);
+                        pd[2 * q + 1] = pack_bf16(z2 > 0.f ? d23.x : 0.f, z3 > 0.f ? d23.y : 0.f);
                     }
                     st_units<2>(xg, row, (c0 + 16 * sb) / 8, pg);
                     st_units<2>(DZ, row, (c0 + 16 * sb) / 8, pd);     // dZ of the colour layer

@@ -296,8 +296,11 @@ __global__ void __launch_bounds__(TcShape<W, H, F8>::kSlots * 128, 1)
                 // colour layer: g = relu(z) in FP32, then rgb = sigmoid(Wo g + bo) with
                 // the FP32 output table at the end of the shared image (this thread
                 // has waited for the image itself before reading it with generic loads)
-                const float4 *wo = reinterpret_cast<const float4 *>(IMG + S::kMatBytes);
-                float4 acc = wo[W];
+                // table rows c over k: each float4 load gives one colour's weights
+                // for four k, two pairs for the packed FMAs (the even and odd k
+                // summed apart, then together with the bias)
+                const float *wo = reinterpret_cast<const float *>(IMG + S::kMatBytes);
+                float2 ax = make_float2(0.f, 0.f), ay = ax, az = ax;
 #pragma unroll
                 for (int c = 0; c < W / 16; ++c) {
                     uint32_t r[16];
@@ -315,16 +318,30 @@ __global__ void __launch_bounds__(TcShape<W, H, F8>::kSlots * 128, 1)
                             bi[4 * q] = bb.x; bi[4 * q + 1] = bb.y; bi[4 * q + 2] = bb.z; bi[4 * q + 3] = bb.w;
                         }
                     }
+                    float gk[16];
 #pragma unroll
                     for (int q = 0; q < 16; ++q) {
                         const float z = __uint_as_float(r[q]);
-                        const float gk = fmaxf(F8 ? fmaf(z, sc[q], bi[q]) : z, 0.f);
-                        const float4 wk = wo[16 * c + q];
-                        acc.x = fmaf(wk.x, gk, acc.x);
-                        acc.y = fmaf(wk.y, gk, acc.y);
-                        acc.z = fmaf(wk.z, gk, acc.z);
+                        gk[q] = fmaxf(F8 ? fmaf(z, sc[q], bi[q]) : z, 0.f);
+                    }
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const int k = 16 * c + 4 * q;
+                        const float2 g01 = make_float2(gk[4 * q], gk[4 * q + 1]);
+                        const float2 g23 = make_float2(gk[4 * q + 2], gk[4 * q + 3]);
+                        const float4 wx = *reinterpret_cast<const float4 *>(wo + k);
+                        ax = __ffma2_rn(make_float2(wx.x, wx.y), g01, ax);
+                        ax = __ffma2_rn(make_float2(wx.z, wx.w), g23, ax);
+                        const float4 wy = *reinterpret_cast<const float4 *>(wo + W + k);
+                        ay = __ffma2_rn(make_float2(wy.x, wy.y), g01, ay);
+                        ay = __ffma2_rn(make_float2(wy.z, wy.w), g23, ay);
+                        const float4 wz = *reinterpret_cast<const float4 *>(wo + 2 * W + k);
+                        az = __ffma2_rn(make_float2(wz.x, wz.y), g01, az);
+                        az = __ffma2_rn(make_float2(wz.z, wz.w), g23, az);
                     }
                 }
+                const float4 bo = *reinterpret_cast<const float4 *>(wo + 4 * W);
+                const float4 acc = make_float4(bo.x + (ax.x + ax.y), bo.y + (ay.x + ay.y), bo.z + (az.x + az.y), 0.f);
                 if (valid) out[sm.idx] = make_float4(sigma, sigmoid_f(acc.x), sigmoid_f(acc.y), sigmoid_f(acc.z));
             }
             tc_fence_before();
@@ -467,7 +484,7 @@ __global__ void k_pack_tc(const float *__restrict__ w32, int n_fields, int64_t P
             reinterpret_cast<uint16_t *>(dst)[g % per] = (uint16_t)(r >> 16);
         }
     }
-    // FP32 output layer after the operands: [W][4] (weights of the 3 colours, pad 0), then bias[4]
+    // FP32 output layer after the operands: [4][W] (weights of the 3 colours over k, a zero row), then bias[4]
     const int nout = 4 * W + 4;
     for (int64_t gi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; gi < (int64_t)n_fields * nout;
          gi += (int64_t)gridDim.x * blockDim.x) {
@@ -476,7 +493,7 @@ __global__ void k_pack_tc(const float *__restrict__ w32, int n_fields, int64_t P
         const float *wf = w32 + f * P;
         float v = 0.f;
         if (q < 4 * W) {
-            const int k = q / 4, c = q % 4;
+            const int c = q / W, k = q % W;
             if (c < 3) v = wf[o.out + (int64_t)c * W + k];
         } else if (q - 4 * W < 3) {
             v = wf[o.out + 3 * W + (q - 4 * W)];
@@ -516,9 +533,9 @@ __device__ __forceinline__ int image_slot(const ApiLayout &o, int64_t q)
         if (r < W * kc) { nr = r / kc; const int ka = r % kc; k = ka < W ? ka : ka + 1; }
         else { nr = r - W * kc; k = W; }
     } else {
-        // the FP32 3-output layer: [W][4] then bias[4]
+        // the FP32 3-output layer: [4][W] (its API rows c, then a zero row) then bias[4]
         const int r = (int)(q - o.out);
-        return -1 - (r < 3 * W ? 4 * (r % W) + r / W : 4 * W + (r - 3 * W));
+        return -1 - (r < 3 * W ? r : 4 * W + (r - 3 * W));
     }
     const int N = S::N(l);
     return S::offset(l) + (k / S::kCE) * N * 128 + (nr >> 3) * 1024 + (nr & 7) * 128 +

@@ -38,7 +38,8 @@ struct TcShape {
         return o;
     }
     static constexpr int kMatBytes = offset(H + 2);
-    // after the MMA operands: FP32 output layer, [W][4] (3 outputs + pad) then bias[4]
+    // after the MMA operands: FP32 output layer, [4][W] (the 3 outputs' weight
+    // rows over k, then a zero row: float4 loads along k) then bias[4]
     static constexpr int kOutBytes = (4 * W + 4) * 4;
     // then (kTab) per layer l: scale[kTabStride] and bias[kTabStride]; the
     // head's entry W is its density logit
