@@ -325,7 +325,14 @@ __global__ void __launch_bounds__(256) k_march(GridDev g, MarchParams p)
         const float inv_delta = 1.0f / delta;   // (the jump's sample index: a product, not a division per step)
         uint32_t em = 0;
         const uint32_t R = (uint32_t)p.R, n_max = (uint32_t)p.n_max;
-        while (jn < je && em < R && nk < n_max) {
+        // records this round may keep (the round's size and the ray's budget in one bound)
+        const uint32_t lim = nk < n_max ? min(R, n_max - nk) : 0u;
+        // slot of record em: s0 + em * s_step
+        const uint32_t s0 = p.flat ? i * R : slot_of(i, 0u, R), s_step = p.flat ? 1u : 32u;
+        // the histogram takes runs of one field (a ray crosses few fields),
+        // not one shared-memory atomic per record
+        uint32_t run_f = 0u, run_n = 0u;
+        while (jn < je && em < lim) {
             const float t = ((float)jn + 0.5f) * delta;
             const float gxf = fmaf(t, dgx, ogx), gyf = fmaf(t, dgy, ogy), gzf = fmaf(t, dgz, ogz);
             const int ix = __float2int_rd(gxf), iy = __float2int_rd(gyf), iz = __float2int_rd(gzf);
@@ -357,17 +364,23 @@ __global__ void __launch_bounds__(256) k_march(GridDev g, MarchParams p)
                     atomicOr(&p.ctr->status, kStatusBadLabel);
                     f = 0;
                 }
-                const uint32_t s = p.flat ? i * R + em : slot_of(i, em, R);
-                p.recs[s] = jn | (f << 16);
-                if (p.hist) atomicAdd(&s_hist[f], 1u);
+                p.recs[s0 + em * s_step] = jn | (f << 16);
+                if (p.hist) {
+                    if (f != run_f) {
+                        if (run_n) atomicAdd(&s_hist[run_f], run_n);
+                        run_f = f;
+                        run_n = 0u;
+                    }
+                    ++run_n;
+                }
                 ++em;
-                ++nk;
             }
             ++jn;
         }
+        if (p.hist && run_n) atomicAdd(&s_hist[run_f], run_n);
         p.cnt[i] = em;
         p.st.j_next[ray] = jn;
-        p.st.n_kept[ray] = nk;
+        p.st.n_kept[ray] = nk + em;
     }
     if (p.hist) {
         __syncthreads();
