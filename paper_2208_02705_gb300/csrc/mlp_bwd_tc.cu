@@ -209,23 +209,31 @@ __device__ __forceinline__ void enc_x0(const float (&xl)[3], uint32_t (&p)[8])
     for (int a = 0; a < 3; ++a)
         if (a >= lo && a < hi) e[a - lo] = xl[a];
     if (63 >= lo && 63 < hi) e[63 - lo] = 1.0f;
-    float sp[3] = {0.f, 0.f, 0.f}, cp[3] = {1.f, 1.f, 1.f};
+    // (x, y) as packed pairs (each half rounded as the scalar operation), z alone
+    float2 s01 = make_float2(0.f, 0.f), c01 = make_float2(1.f, 1.f);
+    float s2 = 0.f, c2 = 1.f;
 #pragma unroll
     for (int k = k_start; k <= k_hi; ++k) {
+        if (k == 0 || k == 5) {
+            sincospi_fast(xl[0] * (float)(1 << k), s01.x, c01.x);
+            sincospi_fast(xl[1] * (float)(1 << k), s01.y, c01.y);
+            sincospi_fast(xl[2] * (float)(1 << k), s2, c2);
+        } else {
+            const float2 t01 = __fmul2_rn(make_float2(2.0f, 2.0f), s01);
+            const float2 sn01 = __fmul2_rn(t01, c01);
+            c01 = __ffma2_rn(make_float2(-t01.x, -t01.y), s01, make_float2(1.0f, 1.0f));
+            s01 = sn01;
+            const float t2 = 2.0f * s2;
+            const float sn2 = t2 * c2;
+            c2 = fmaf(-t2, s2, 1.0f);
+            s2 = sn2;
+        }
+        const float sn[3] = {s01.x, s01.y, s2}, cs[3] = {c01.x, c01.y, c2};
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-            float sn, cs;
-            if (k == 0 || k == 5) {
-                sincospi_fast(xl[a] * (float)(1 << k), sn, cs);
-            } else {
-                sn = 2.0f * sp[a] * cp[a];
-                cs = fmaf(-2.0f * sp[a], sp[a], 1.0f);
-            }
-            sp[a] = sn;
-            cp[a] = cs;
             const int cs_col = 3 + 6 * k + a, cc_col = 6 + 6 * k + a;
-            if (cs_col >= lo && cs_col < hi) e[cs_col - lo] = sn;
-            if (cc_col >= lo && cc_col < hi) e[cc_col - lo] = cs;
+            if (cs_col >= lo && cs_col < hi) e[cs_col - lo] = sn[a];
+            if (cc_col >= lo && cc_col < hi) e[cc_col - lo] = cs[a];
         }
     }
 #pragma unroll

@@ -301,11 +301,15 @@ __global__ void __launch_bounds__(TcShape<W, H, F8>::kSlots * 128, 1)
                 // summed apart, then together with the bias)
                 const float *wo = reinterpret_cast<const float *>(IMG + S::kMatBytes);
                 float2 ax = make_float2(0.f, 0.f), ay = ax, az = ax;
+                // chunk c + 1's TMEM load in flight during chunk c's FMAs
+                uint32_t ra[16], rb[16];
+                tmem_ld16_nowait(trow, ra);
+                tmem_wait_ld();
 #pragma unroll
                 for (int c = 0; c < W / 16; ++c) {
-                    uint32_t r[16];
-                    tmem_ld16_nowait(trow + 16 * c, r);
-                    tmem_wait_ld();
+                    uint32_t(&r)[16] = (c & 1) ? rb : ra;
+                    uint32_t(&nxt)[16] = (c & 1) ? ra : rb;
+                    if (c + 1 < W / 16) tmem_ld16_nowait(trow + 16 * (c + 1), nxt);
                     float sc[16], bi[16];
 #pragma unroll
                     for (int q = 0; q < 16; ++q) { sc[q] = 1.f; bi[q] = 0.f; }
@@ -339,6 +343,7 @@ __global__ void __launch_bounds__(TcShape<W, H, F8>::kSlots * 128, 1)
                         az = __ffma2_rn(make_float2(wz.x, wz.y), g01, az);
                         az = __ffma2_rn(make_float2(wz.z, wz.w), g23, az);
                     }
+                    if (c + 1 < W / 16) tmem_wait_ld();
                 }
                 const float4 bo = *reinterpret_cast<const float4 *>(wo + 4 * W);
                 const float4 acc = make_float4(bo.x + (ax.x + ax.y), bo.y + (ay.x + ay.y), bo.z + (az.x + az.y), 0.f);

@@ -284,25 +284,6 @@ __device__ __forceinline__ void sincospi_fast(float y, float &s, float &c)
     __sincosf(3.14159265358979f * r, &s, &c);
 }
 
-// F(v) for one coordinate, frequencies 2^0 .. 2^(L-1): direct evaluation at
-// k = 0 and k = 5, angle doubling (sin 2a = 2 sin a cos a,
-// cos 2a = 1 - 2 sin^2 a) in between, so the doubling error stays below
-// 2^4 times the direct error.
-template <int L>
-__device__ __forceinline__ void encode1(float v, float (&s)[L], float (&c)[L])
-{
-#pragma unroll
-    for (int k = 0; k < L; ++k) {
-        if (k == 0 || k == 5) {
-            sincospi_fast(v * (float)(1 << k), s[k], c[k]);     // exact scaling by 2^k
-        } else {
-            const float sp = s[k - 1], cp = c[k - 1];
-            s[k] = 2.0f * sp * cp;
-            c[k] = fmaf(-2.0f * sp, sp, 1.0f);
-        }
-    }
-}
-
 // Packs e[first .. first + n) into the MMA's A words (BF16: elements 2c and
 // 2c + 1 in word c, low half first; E4M3: elements 4c .. 4c + 3 in word c);
 // the words whose elements all lie in that range.
@@ -334,24 +315,28 @@ __device__ __forceinline__ void encode_packed(const float (&v)[3], uint32_t (&w)
     for (int q = 0; q < kLead; ++q) e[q] = 1.0f;
     e[kLead] = v[0]; e[kLead + 1] = v[1]; e[kLead + 2] = v[2];
     if (kTrailOne) e[kLead + 3 + 6 * L] = 1.0f;
-    float sp[3], cp[3];
+    // (x, y) as packed pairs (each half rounded as the scalar operation), z alone
+    float2 s01 = make_float2(0.f, 0.f), c01 = s01;
+    float s2 = 0.f, c2 = 0.f;
 #pragma unroll
     for (int k = 0; k < L; ++k) {
         // direct evaluation at k = 0 and k = 5, angle doubling in between
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            float sn, cs;
-            if (k == 0 || k == 5) {
-                sincospi_fast(v[a] * (float)(1 << k), sn, cs);
-            } else {
-                sn = 2.0f * sp[a] * cp[a];
-                cs = fmaf(-2.0f * sp[a], sp[a], 1.0f);
-            }
-            sp[a] = sn;
-            cp[a] = cs;
-            e[kLead + 3 + 6 * k + a] = sn;
-            e[kLead + 6 + 6 * k + a] = cs;
+        if (k == 0 || k == 5) {
+            sincospi_fast(v[0] * (float)(1 << k), s01.x, c01.x);
+            sincospi_fast(v[1] * (float)(1 << k), s01.y, c01.y);
+            sincospi_fast(v[2] * (float)(1 << k), s2, c2);
+        } else {
+            const float2 t01 = __fmul2_rn(make_float2(2.0f, 2.0f), s01);
+            const float2 sn01 = __fmul2_rn(t01, c01);
+            c01 = __ffma2_rn(make_float2(-t01.x, -t01.y), s01, make_float2(1.0f, 1.0f));
+            s01 = sn01;
+            const float t2 = 2.0f * s2;
+            const float sn2 = t2 * c2;
+            c2 = fmaf(-t2, s2, 1.0f);
+            s2 = sn2;
         }
+        e[kLead + 3 + 6 * k] = s01.x; e[kLead + 4 + 6 * k] = s01.y; e[kLead + 5 + 6 * k] = s2;
+        e[kLead + 6 + 6 * k] = c01.x; e[kLead + 7 + 6 * k] = c01.y; e[kLead + 8 + 6 * k] = c2;
         pack_range<F8, NW>(e, w, 0, kLead + 9 + 6 * k);
     }
     pack_range<F8, NW>(e, w, 0, NE);
