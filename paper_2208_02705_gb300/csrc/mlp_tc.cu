@@ -264,11 +264,13 @@ __global__ void __launch_bounds__(TcShape<W, H, F8>::kSlots * 128, 1)
                             for (int q = 0; q < 8; ++q) {
                                 const float4 bb = reinterpret_cast<const float4 *>(tbi + 32 * c)[q];
                                 if constexpr (F8) {
+                                    // y = s D + b as packed pairs (each half rounded as fmaf)
                                     const float4 ss = reinterpret_cast<const float4 *>(tsc + 32 * c)[q];
-                                    v[4 * q] = fmaf(v[4 * q], ss.x, bb.x);
-                                    v[4 * q + 1] = fmaf(v[4 * q + 1], ss.y, bb.y);
-                                    v[4 * q + 2] = fmaf(v[4 * q + 2], ss.z, bb.z);
-                                    v[4 * q + 3] = fmaf(v[4 * q + 3], ss.w, bb.w);
+                                    const float2 v01 = __ffma2_rn(make_float2(v[4 * q], v[4 * q + 1]),
+                                                                  make_float2(ss.x, ss.y), make_float2(bb.x, bb.y));
+                                    const float2 v23 = __ffma2_rn(make_float2(v[4 * q + 2], v[4 * q + 3]),
+                                                                  make_float2(ss.z, ss.w), make_float2(bb.z, bb.w));
+                                    v[4 * q] = v01.x; v[4 * q + 1] = v01.y; v[4 * q + 2] = v23.x; v[4 * q + 3] = v23.y;
                                 } else {
                                     v[4 * q] += bb.x; v[4 * q + 1] += bb.y; v[4 * q + 2] += bb.z; v[4 * q + 3] += bb.w;
                                 }
@@ -310,23 +312,23 @@ __global__ void __launch_bounds__(TcShape<W, H, F8>::kSlots * 128, 1)
                     uint32_t(&r)[16] = (c & 1) ? rb : ra;
                     uint32_t(&nxt)[16] = (c & 1) ? ra : rb;
                     if (c + 1 < W / 16) tmem_ld16_nowait(trow + 16 * (c + 1), nxt);
-                    float sc[16], bi[16];
-#pragma unroll
-                    for (int q = 0; q < 16; ++q) { sc[q] = 1.f; bi[q] = 0.f; }
+                    float gk[16];
                     if constexpr (F8) {
+                        // y = s z + b per channel, packed pairs (each half rounded as fmaf)
 #pragma unroll
                         for (int q = 0; q < 4; ++q) {
                             const float4 ss = reinterpret_cast<const float4 *>(tsc + 16 * c)[q];
                             const float4 bb = reinterpret_cast<const float4 *>(tbi + 16 * c)[q];
-                            sc[4 * q] = ss.x; sc[4 * q + 1] = ss.y; sc[4 * q + 2] = ss.z; sc[4 * q + 3] = ss.w;
-                            bi[4 * q] = bb.x; bi[4 * q + 1] = bb.y; bi[4 * q + 2] = bb.z; bi[4 * q + 3] = bb.w;
+                            const float2 y01 = __ffma2_rn(make_float2(__uint_as_float(r[4 * q]), __uint_as_float(r[4 * q + 1])),
+                                                          make_float2(ss.x, ss.y), make_float2(bb.x, bb.y));
+                            const float2 y23 = __ffma2_rn(make_float2(__uint_as_float(r[4 * q + 2]), __uint_as_float(r[4 * q + 3])),
+                                                          make_float2(ss.z, ss.w), make_float2(bb.z, bb.w));
+                            gk[4 * q] = fmaxf(y01.x, 0.f); gk[4 * q + 1] = fmaxf(y01.y, 0.f);
+                            gk[4 * q + 2] = fmaxf(y23.x, 0.f); gk[4 * q + 3] = fmaxf(y23.y, 0.f);
                         }
-                    }
-                    float gk[16];
+                    } else {
 #pragma unroll
-                    for (int q = 0; q < 16; ++q) {
-                        const float z = __uint_as_float(r[q]);
-                        gk[q] = fmaxf(F8 ? fmaf(z, sc[q], bi[q]) : z, 0.f);
+                        for (int q = 0; q < 16; ++q) gk[q] = fmaxf(__uint_as_float(r[q]), 0.f);
                     }
 #pragma unroll
                     for (int q = 0; q < 4; ++q) {
