@@ -248,16 +248,12 @@ __global__ void __launch_bounds__(TcShape<W, H, F8>::kSlots * 128, 1)
                 // head features stay linear, every other layer ReLU
 #pragma unroll
                 for (int c = 0; c < W / 32; ++c) {
-                    uint32_t r0[16], r1[16];
-                    tmem_ld16_nowait(trow + 32 * c, r0);
-                    tmem_ld16_nowait(trow + 32 * c + 16, r1);
+                    uint32_t r32[32];
+                    tmem_ld32_nowait(trow + 32 * c, r32);
                     tmem_wait_ld();
                     float v[32];
 #pragma unroll
-                    for (int q = 0; q < 16; ++q) {
-                        v[q] = __uint_as_float(r0[q]);
-                        v[16 + q] = __uint_as_float(r1[q]);
-                    }
+                    for (int q = 0; q < 32; ++q) v[q] = __uint_as_float(r32[q]);
                     if constexpr (S::kTab) {
                         if (use_tab) {
 #pragma unroll
