@@ -226,6 +226,16 @@ __global__ void __launch_bounds__(TcShape<W, H, F8>::kSlots * 128, 1)
                 umma_commit(&bar_d[slot]);
                 ++n_commits;
             }
+            // the tail of A from here on, [1 | F(d) | 0 0 0 0] at elements
+            // W .. W+31: at W >= 64 in L1's shadow (L1, K = 64, does not read
+            // those elements), at W = 32 (they are L1's input) after L1 landed
+            auto store_tail = [&]() {
+                const float dv[3] = {sm.dx, sm.dy, sm.dz};
+                uint32_t w[F8 ? 8 : 16];
+                encode_packed<F8, 4, 1, false, 32>(dv, w);
+                st_words32<F8>(tArow, W / 32, w);
+            };
+            if (W >= 64 && l == 0) store_tail();
             const bool got = mbar_wait(&bar_d[slot], d_ph, abortp, status, false, wait_ns);
             if (issuer && got) ++n_waits;
             d_ph ^= 1u;
@@ -276,19 +286,13 @@ __global__ void __launch_bounds__(TcShape<W, H, F8>::kSlots * 128, 1)
                     if (l == H) st_act32<F8, false>(tArow, c, v);
                     else st_act32<F8, true>(tArow, c, v);
                 }
+                if (W < 64 && l == 0) store_tail();
                 if (l == H) {
                     // density from column W of the head
                     float sl = __uint_as_float(tmem_ld1(trow + W));
                     tmem_wait_ld();
                     if (use_tab) sl = F8 ? fmaf(sl, tsc[W], tbi[W]) : sl + tbi[W];
                     sigma = sig_scale * (act == ROAM_RELU ? fmaxf(sl, 0.f) : softplus_f(sl));
-                }
-                if (l == 0) {
-                    // tail of A from here on: [1 | F(d) | 0 0 0 0] at columns W .. W+31
-                    const float dv[3] = {sm.dx, sm.dy, sm.dz};
-                    uint32_t w[F8 ? 8 : 16];
-                    encode_packed<F8, 4, 1, false, 32>(dv, w);
-                    st_words32<F8>(tArow, W / 32, w);
                 }
             } else {
                 // colour layer: g = relu(z) in FP32, then rgb = sigmoid(Wo g + bo) with
