@@ -16,8 +16,11 @@
 // Two chains of 8 warps carry alternate tiles (t0 + chain, + 2, ...): while
 // one recomputes its tile's forward, the other runs the previous tile's
 // backward, so the commit round trips of one chain overlap the other's
-// epilogues.  Each chain has its own accumulator D, barrier and MMA
-// mbarrier; within a chain the two warps of one TMEM lane quarter take half
+// epilogues.  Each chain has its own accumulator D, barrier and two MMA
+// mbarriers: in a backward group the dgrad MMAs land on one, the wgrad MMAs
+// on the other, so the dX epilogue (TMEM load, ReLU mask, packing) runs
+// while the wgrad MMAs still read dZ, and dZ is rewritten once both have
+// landed.  Within a chain the two warps of one TMEM lane quarter take half
 // of the row's columns each.  The chains share the weight image (their
 // tiles are of one field: a field change drains them), the wgrad
 // accumulators, a pool of H + 4 activation chunks, dZ and the tail chunk;
