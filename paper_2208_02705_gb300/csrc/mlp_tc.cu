@@ -254,6 +254,22 @@ __global__ void __launch_bounds__(TcShape<W, H, F8>::kSlots * 128, 1)
                 img_seen = true;
             }
             if (l < H + 1) {
+                if constexpr (W == 64 && !S::kTab) {
+                    // both 32-column halves in flight before one wait
+                    uint32_t ra[32], rb[32];
+                    tmem_ld32_nowait(trow, ra);
+                    tmem_ld32_nowait(trow + 32, rb);
+                    tmem_wait_ld();
+                    float v[32];
+#pragma unroll
+                    for (int q = 0; q < 32; ++q) v[q] = __uint_as_float(ra[q]);
+                    if (l == H) st_act32<F8, false>(tArow, 0, v);
+                    else st_act32<F8, true>(tArow, 0, v);
+#pragma unroll
+                    for (int q = 0; q < 32; ++q) v[q] = __uint_as_float(rb[q]);
+                    if (l == H) st_act32<F8, false>(tArow, 1, v);
+                    else st_act32<F8, true>(tArow, 1, v);
+                } else {
                 // next activations, 32 columns at a time (few live registers):
                 // head features stay linear, every other layer ReLU
 #pragma unroll
@@ -285,6 +301,7 @@ __global__ void __launch_bounds__(TcShape<W, H, F8>::kSlots * 128, 1)
                     }
                     if (l == H) st_act32<F8, false>(tArow, c, v);
                     else st_act32<F8, true>(tArow, c, v);
+                }
                 }
                 if (W < 64 && l == 0) store_tail();
                 if (l == H) {
