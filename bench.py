@@ -795,9 +795,9 @@ def main():
         bound, src = "alu", "152 SMs x 128 FP32 lanes x 2 FLOP x max SM clock"
     # DRAM traffic per launch: bytes per evaluated sample from an ncu capture of
     # this kernel on the 1024x512 equirect view of the same scene (dram bytes
-    # read + written over one render's 4 launches: 253.5 MB for 8,372,992
+    # read + written over one render's 4 launches: 254.1 MB for 8,372,992
     # evaluated samples), scaled by the samples of this run's launches
-    traffic = 30.28 * evaluated_per_step * args.steps / launches if (launches and head_prec == roam.ROAM_BF16) \
+    traffic = 30.35 * evaluated_per_step * args.steps / launches if (launches and head_prec == roam.ROAM_BF16) \
         else None
     roofline = {"kernel": mlp_key, "bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "peak_source": src, "traffic": traffic,
