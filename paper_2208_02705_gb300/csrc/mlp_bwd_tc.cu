@@ -151,6 +151,14 @@ __device__ __forceinline__ uint32_t relu_mask(uint32_t x)
     return __hgt2_mask(*reinterpret_cast<const __nv_bfloat162 *>(&x), __float2bfloat162_rn(0.f));
 }
 
+// one TMEM column of this thread's lane (complete after tcgen05.wait::ld)
+__device__ __forceinline__ uint32_t tmem_ld1_nowait(uint32_t taddr)
+{
+    uint32_t r;
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x1.b32 {%0}, [%1];" : "=r"(r) : "r"(taddr));
+    return r;
+}
+
 // one arrival without a transaction (no tcgen05 work to track)
 __device__ __forceinline__ void mbar_arrive(uint64_t *bar)
 {
@@ -682,20 +690,20 @@ __global__ void __launch_bounds__(kBwThreads, 1)
             } else if (l == H) {
                 // head: features (linear) -> colour input, column W = density logit
                 uint8_t *xc = xchunk(chain, H + 1);
+                // (group 0 loads the logit with its last sub-block: one wait)
+                uint32_t s_raw = 0u;
 #pragma unroll
                 for (int sb = 0; sb < NSB; ++sb) {
-                    float va[16];
-                    ldcf<16>(tDc + (uint32_t)(16 * sb), va);
+                    uint32_t r[16];
+                    tmem_ld16_nowait(tDc + (uint32_t)(16 * sb), r);
+                    if (g == 0 && sb == NSB - 1) s_raw = tmem_ld1_nowait(tD + tlane + (uint32_t)W);
+                    tmem_wait_ld();
                     uint32_t p[8];
 #pragma unroll
-                    for (int q = 0; q < 8; ++q) p[q] = pack_bf16(va[2 * q], va[2 * q + 1]);
+                    for (int q = 0; q < 8; ++q) p[q] = pack_bf16(__uint_as_float(r[2 * q]), __uint_as_float(r[2 * q + 1]));
                     st_units<2>(xc, row, (c0 + 16 * sb) / 8, p);
                 }
-                if (g == 0) {
-                    float v[8];
-                    ldcf<8>(tD + tlane + (uint32_t)W, v);
-                    s_logit = v[0];
-                }
+                if (g == 0) s_logit = __uint_as_float(s_raw);
                 store_tail(H + 1);
             }
             // this tile's F(d) in the shared tail, once the other chain's
